@@ -1,0 +1,161 @@
+/*
+ * must.h -- C ABI of the GB300 LSMS tau_00 library.
+ *
+ * The library implements the hot path of the LSMS method as described in
+ * arXiv 2308.16317 ("High Performance GPU Accelerated MuST Software"):
+ *
+ *   Eq. (4)   tau(E) = [t^{-1}(E) - g0(E)]^{-1}, with the KKR matrix
+ *             M(E) = t^{-1}(E) - g0(E); g0 is the free-particle propagator
+ *             between two *different* sites (Sec. 2.1).
+ *   Sec. 2.1  rank of M is N (lmax+1)^2, or 2 N (lmax+1)^2 with spin canting.
+ *   Sec. 2.2  LSMS builds M over the local interaction zone (LIZ) of each atom
+ *             and needs only the first (central-site) block tau_00 of M^{-1}.
+ *   Sec. 3.2  the paper inverts M by LU factorisation and solve; here M is
+ *             assembled on the device and only tau_00 is formed.
+ *   Sec. 5    building M on the GPU instead of the CPU is the paper's stated
+ *             next step; it is what must_tau00_solve does.
+ *
+ * Conventions (Rydberg atomic units: lengths in bohr, energies in Ry):
+ *   kappa = sqrt(E) on the principal branch (Im kappa > 0 for Im E > 0).
+ *   L = l*l + l + m, m = -l..l; real spherical harmonics without the
+ *   Condon-Shortley phase (Y_1,-1 ~ y, Y_1,0 ~ z, Y_1,1 ~ x).
+ *   g0^{ij}_{LL'} = -4 pi i kappa sum_L'' i^{l-l'+l''} C(L,L',L'')
+ *                   h_l''(kappa |R_ij|) Y_L''(R_ij^),  R_ij = R_i - R_j.
+ *   Complex numbers are interleaved (re, im) doubles.  tau_00 is returned
+ *   column-major, kap x kap, kap = (lmax+1)^2 (2 (lmax+1)^2 when canted, with
+ *   index (spin, L), spin up first).
+ *
+ * Memory: every pointer may be host or device memory unless stated; the
+ * library detects which (cudaPointerGetAttributes) and stages host buffers
+ * through the caller's workspace with stream-ordered copies.  The caller owns
+ * all buffers, including the workspace; the library owns only the must_liz
+ * handle and its device tables.  All GPU work is enqueued on the caller's
+ * stream (a cudaStream_t passed as void*, NULL = legacy default stream).
+ * Errors in arguments are returned synchronously; per-solve numerical
+ * outcomes go to the optional per-solve status array.  No call throws.
+ */
+#ifndef MUST_H
+#define MUST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MUST_OK = 0,
+  MUST_EINVAL = 1,        /* bad argument (NULL, size, lmax, precision ...)      */
+  MUST_ENOMEM = 2,        /* device allocation failed or workspace too small     */
+  MUST_ECUDA = 3,         /* a CUDA runtime call failed (see must_last_error)    */
+  MUST_ESINGULAR = 4,     /* per-solve: an exactly zero pivot was met            */
+  MUST_ENOCONV = 5,       /* per-solve: refinement did not reach the tolerance   */
+  MUST_ENONFINITE = 6,    /* per-solve: NaN/Inf in t^{-1} or in the result       */
+  MUST_ETIMEOUT = 7,      /* a bounded device wait ran out                       */
+  MUST_EUNSUPPORTED = 8   /* valid request this build does not support           */
+} must_status;
+
+typedef enum {
+  MUST_FP64 = 0,          /* complex128 throughout (the paper's precision, Sec. 4.1) */
+  MUST_MIXED_BF16X3 = 1,  /* FP32 factors, trailing updates as split-BF16x3 on the
+                             tensor cores, FP64 residual refinement               */
+  MUST_MIXED_TF32X3 = 2   /* as above with 3xTF32 trailing updates                */
+} must_precision;
+
+typedef struct {
+  int32_t precision;      /* must_precision                                          */
+  double tol;             /* refinement stop: ||delta X||_F <= tol ||X||_F (mixed)   */
+  int32_t max_iter;       /* refinement iteration cap (mixed); 0 => MUST_ENOCONV     */
+  int32_t warm_start;     /* reserved for the learned seed; 0 = cold solve           */
+  int32_t deterministic;  /* 1 = static schedule in batched launches                 */
+  int32_t equilibrate;    /* 1 = symmetric |diag M|^{-1/2} scaling before low-prec LU */
+} must_solve_opts;
+
+typedef struct must_liz must_liz;   /* opaque, immutable after build */
+
+/* Fill *opts with the defaults (FP64, tol 1e-13, max_iter 10, equilibrate 1). */
+void must_default_opts(must_solve_opts* opts);
+
+/*
+ * Build a LIZ handle (Sec. 2.2).  pos_bohr: n_sites x 3 site positions, row 0
+ * is the central atom; species: n_sites ints in [0, n_species) selecting the
+ * t^{-1} row used at each site; lmax in [0, 4]; spin_dirs: n_sites x 3 unit
+ * vectors for the spin-canted matrix (rank 2 N (lmax+1)^2), or NULL for the
+ * collinear one.  All three arrays are read on the host during the call.
+ * Computes the device tables (pair geometry, Y_L of every pair direction,
+ * Gaunt coefficients) on `stream` and returns after they are complete.
+ * Errors: MUST_EINVAL (NULL, n_sites < 1, lmax out of range, coincident
+ * sites, non-unit spin direction), MUST_ENOMEM, MUST_ECUDA.
+ */
+must_status must_liz_build(const double* pos_bohr, const int32_t* species, int32_t n_sites, int32_t lmax,
+                           const double* spin_dirs, void* stream, must_liz** out);
+void must_liz_free(must_liz* liz);
+
+/* Matrix order n and block width kap of a handle. */
+int32_t must_liz_order(const must_liz* liz);
+int32_t must_liz_kappa(const must_liz* liz);
+
+/*
+ * Device workspace (bytes) that must_tau00_solve needs to process n_items
+ * (energy, spin) matrices at once with the given options (opts NULL =
+ * defaults).  A smaller workspace is accepted: the solve then processes the
+ * items in chunks that fit, down to one matrix.
+ */
+size_t must_workspace_bytes(const must_liz* liz, int32_t n_items, const must_solve_opts* opts);
+
+/*
+ * Square-well single-site t^{-1}_l(E) (a fixture for the synthetic workloads,
+ * not part of Eq. 4 itself): well depth V[p] inside r < r_mt, zero outside,
+ * log-derivative matching of j_l(q r), q = sqrt(E - V), to j_l - i kappa t_l h_l.
+ * E: nE complex; V: n_pot reals; out tinv: [n_pot][nE][lmax+1] complex.
+ * Computed by a device kernel on `stream`; host pointers are staged.
+ */
+must_status must_tinv_square_well(int32_t nE, const double* E, int32_t n_pot, const double* V, double r_mt,
+                                  int32_t lmax, double* tinv, void* stream);
+
+/*
+ * tau_00 = [M^{-1}]_00 for every energy and spin of one LIZ (Eq. 4, Sec. 2.2).
+ *   E       : nE complex energies.
+ *   tinv    : t^{-1}_l per [nspin][n_species][nE][lmax+1] complex.  Collinear
+ *             handles produce one matrix per (spin, energy); canted handles
+ *             need nspin == 2 (up, down in each site's local frame) and
+ *             produce one matrix of order 2n per energy.
+ *   tau00   : [n_out][nE][kap][kap] complex, column-major blocks, n_out = nspin
+ *             (collinear) or 1 (canted).
+ *   status  : optional int32 per output block (MUST_OK, MUST_ESINGULAR,
+ *             MUST_ENOCONV, MUST_ENONFINITE), same order as tau00, or NULL.
+ *   workspace / ws_bytes : caller-owned device memory (see
+ *             must_workspace_bytes); must be 256-byte aligned.
+ * The matrix is ordered with the central site last, so that eliminating the
+ * leading n - kap columns (LU with partial pivoting restricted to those rows)
+ * leaves the kap x kap Schur complement S with tau_00 = S^{-1}.
+ * Returns after enqueueing (device pointers) or after the final copy (host
+ * output pointers).  Errors: MUST_EINVAL, MUST_ENOMEM, MUST_ECUDA,
+ * MUST_EUNSUPPORTED.
+ */
+must_status must_tau00_solve(const must_liz* liz, int32_t nE, const double* E, const double* tinv,
+                             int32_t n_species, int32_t nspin, const must_solve_opts* opts, void* workspace,
+                             size_t ws_bytes, double* tau00, int32_t* status, void* stream);
+
+/*
+ * Many LIZs in one call (the paper distributes atoms over MPI ranks, Sec. 4.2;
+ * here all (LIZ, energy, spin) items of uneven order share launches).
+ * lizs: n_liz handles (same lmax and canting).  E, tinv as for
+ * must_tau00_solve, shared by every LIZ.  tau00: [n_liz][n_out][nE][kap][kap].
+ * status: [n_liz][n_out][nE] or NULL.
+ */
+must_status must_tau00_batch(int32_t n_liz, const must_liz* const* lizs, int32_t nE, const double* E,
+                             const double* tinv, int32_t n_species, int32_t nspin, const must_solve_opts* opts,
+                             void* workspace, size_t ws_bytes, double* tau00, int32_t* status, void* stream);
+size_t must_batch_workspace_bytes(int32_t n_liz, const must_liz* const* lizs, int32_t n_items_per_liz,
+                                  const must_solve_opts* opts);
+
+const char* must_status_string(must_status s);
+/* Message for the last non-OK status returned on the calling thread. */
+const char* must_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MUST_H */

@@ -56,7 +56,7 @@ def _load():
             I = ctypes.POINTER(ctypes.c_int)
             c_int, c_dbl = ctypes.c_int, ctypes.c_double
             sig = {
-                "orc_sph_jyh": (None, [c_int, c_dbl, c_dbl, D, D]),
+                "orc_sph_jyh": (None, [c_int, c_dbl, c_dbl, D, D, D]),
                 "orc_real_ylm": (None, [c_int, c_dbl, c_dbl, c_dbl, D]),
                 "orc_gauss_legendre": (None, [c_int, D, D]),
                 "orc_gaunt": (None, [c_int, c_int, c_int, D]),
@@ -101,10 +101,17 @@ def l_of_L(lmax: int) -> np.ndarray:
 
 def sph_jy(lmax: int, z: complex):
     """Spherical Bessel j_l(z), y_l(z), l = 0..lmax (A&S 10.1)."""
+    return sph_jyh(lmax, z)[:2]
+
+
+def sph_jyh(lmax: int, z: complex):
+    """j_l(z), y_l(z) and the outgoing Hankel h_l(z) (closed form), l = 0..lmax."""
     j = np.zeros(lmax + 1, np.complex128)
     y = np.zeros(lmax + 1, np.complex128)
-    _load().orc_sph_jyh(lmax, float(np.real(z)), float(np.imag(z)), _dp(j.view(np.float64)), _dp(y.view(np.float64)))
-    return j, y
+    h = np.zeros(lmax + 1, np.complex128)
+    _load().orc_sph_jyh(lmax, float(np.real(z)), float(np.imag(z)), _dp(j.view(np.float64)), _dp(y.view(np.float64)),
+                        _dp(h.view(np.float64)))
+    return j, y, h
 
 
 def real_ylm(lmax: int, v) -> np.ndarray:

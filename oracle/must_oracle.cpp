@@ -42,7 +42,8 @@ static const double kPi = 3.14159265358979323846264338327950288;
 // j_l: power series for small |z|, else Miller's downward recurrence
 //      normalised to the closed form j0 = sin z / z (or j1 near zeros of j0).
 // y_l: upward recurrence from y0 = -cos z / z, y1 = -cos z / z^2 - sin z / z.
-// h_l = j_l + i y_l  (outgoing spherical Hankel function, h0 = -i e^{iz}/z).
+// h_l = j_l + i y_l  (outgoing spherical Hankel function, h0 = -i e^{iz}/z),
+//      evaluated from its finite closed form (sph_h below).
 // --------------------------------------------------------------------------
 static void sph_j(int lmax, cplx z, cplx* j) {
   const double az = std::abs(z);
@@ -83,6 +84,36 @@ static void sph_y(int lmax, cplx z, cplx* y) {
   y[0] = -std::cos(z) / z;
   if (lmax >= 1) y[1] = -std::cos(z) / (z * z) - std::sin(z) / z;
   for (int l = 1; l < lmax; ++l) y[l + 1] = (2.0 * l + 1.0) / z * y[l] - y[l - 1];
+}
+
+// h_l(z) = j_l + i y_l.  For Im z > 1, j_l and y_l grow like e^{Im z} while
+// h_l decays like e^{-Im z}, so their sum cancels; there h_l is taken from its
+// finite closed form (A&S 10.1.16)
+//   h_l(z) = (-i)^{l+1} (e^{iz}/z) sum_{k=0..l} i^k (l+k)! / (k! (l-k)! (2z)^k).
+// For Im z <= 1 the sum j_l + i y_l is used (the closed form would lose the
+// small real part j_l near the real axis at small |z|).
+static void sph_h(int lmax, cplx z, cplx* h) {
+  if (z.imag() <= 1.0) {
+    std::vector<cplx> j(lmax + 1), y(lmax + 1);
+    sph_j(lmax, z, j.data());
+    sph_y(lmax, z, y.data());
+    for (int l = 0; l <= lmax; ++l) h[l] = j[l] + cplx(0, 1) * y[l];
+    return;
+  }
+  const cplx ez = std::exp(cplx(0, 1) * z) / z;
+  for (int l = 0; l <= lmax; ++l) {
+    cplx sum = 0.0, ik = 1.0, tz = 1.0;
+    for (int k = 0; k <= l; ++k) {
+      if (k > 0) { ik *= cplx(0, 1); tz *= 2.0 * z; }
+      double c = 1.0;   // (l+k)! / (k! (l-k)!)
+      for (int q = l - k + 1; q <= l + k; ++q) c *= q;
+      for (int q = 2; q <= k; ++q) c /= q;
+      sum += ik * c / tz;
+    }
+    cplx ph = 1.0;
+    for (int q = 0; q <= l; ++q) ph *= cplx(0, -1);
+    h[l] = ph * ez * sum;
+  }
 }
 
 // f_l'(z) = f_{l-1}(z) - (l+1)/z f_l(z);  f_0' = -f_1.  f must hold lmax+2 values.
@@ -198,10 +229,8 @@ static void struct_const_block(int lmax, cplx E, const double* R, const double* 
   const int l2max = 2 * lmax, nL2 = (l2max + 1) * (l2max + 1);
   const cplx kap = kappa_of(E);
   const double d = std::sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
-  std::vector<cplx> jv(l2max + 2), yv(l2max + 2), h(l2max + 2);
-  sph_j(l2max + 1, kap * d, jv.data());
-  sph_y(l2max + 1, kap * d, yv.data());
-  for (int l = 0; l <= l2max; ++l) h[l] = jv[l] + cplx(0, 1) * yv[l];
+  std::vector<cplx> h(l2max + 2);
+  sph_h(l2max + 1, kap * d, h.data());
   std::vector<double> Y(nL2);
   real_ylm(l2max, R[0], R[1], R[2], Y.data());
   for (int L = 0; L < nL; ++L) {
@@ -230,10 +259,9 @@ static void struct_const_block(int lmax, cplx E, const double* R, const double* 
 static void square_well_t(int lmax, cplx E, double V, double a, cplx* t, cplx* tinv) {
   const cplx k = kappa_of(E);
   const cplx q = std::sqrt(E - V);
-  std::vector<cplx> jk(lmax + 2), yk(lmax + 2), hk(lmax + 2), jq(lmax + 2);
+  std::vector<cplx> jk(lmax + 2), hk(lmax + 2), jq(lmax + 2);
   sph_j(lmax + 1, k * a, jk.data());
-  sph_y(lmax + 1, k * a, yk.data());
-  for (int l = 0; l <= lmax + 1; ++l) hk[l] = jk[l] + cplx(0, 1) * yk[l];
+  sph_h(lmax + 1, k * a, hk.data());
   sph_j(lmax + 1, q * a, jq.data());
   for (int l = 0; l <= lmax; ++l) {
     const cplx djk = sph_deriv(l, k * a, jk.data());
@@ -470,12 +498,14 @@ static int gauss_jordan(size_t n, const cplx* A, cplx* Ainv) {
 // ==========================================================================
 extern "C" {
 
-void orc_sph_jyh(int lmax, double zr, double zi, double* j, double* y) {
-  std::vector<cplx> jv(lmax + 1), yv(lmax + 1);
+void orc_sph_jyh(int lmax, double zr, double zi, double* j, double* y, double* h) {
+  std::vector<cplx> jv(lmax + 1), yv(lmax + 1), hv(lmax + 1);
   sph_j(lmax, cplx(zr, zi), jv.data());
   sph_y(lmax, cplx(zr, zi), yv.data());
+  sph_h(lmax, cplx(zr, zi), hv.data());
   std::memcpy(j, jv.data(), sizeof(cplx) * (lmax + 1));
   std::memcpy(y, yv.data(), sizeof(cplx) * (lmax + 1));
+  if (h) std::memcpy(h, hv.data(), sizeof(cplx) * (lmax + 1));
 }
 
 void orc_real_ylm(int lmax, double x, double y, double z, double* out) { real_ylm(lmax, x, y, z, out); }

@@ -1,0 +1,180 @@
+"""ctypes binding of the C ABI in include/must.h (argument marshalling only).
+
+Every function has the name of its C entry point.  Array arguments may be
+torch tensors (host or CUDA; their data pointer is passed) or numpy arrays
+(host).  All computation happens in the CUDA library; if it has not been
+built, ``load()`` raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmust.so")
+_lib = None
+
+MUST_FP64, MUST_MIXED_BF16X3, MUST_MIXED_TF32X3 = 0, 1, 2
+STATUS = {0: "MUST_OK", 1: "MUST_EINVAL", 2: "MUST_ENOMEM", 3: "MUST_ECUDA", 4: "MUST_ESINGULAR",
+          5: "MUST_ENOCONV", 6: "MUST_ENONFINITE", 7: "MUST_ETIMEOUT", 8: "MUST_EUNSUPPORTED"}
+
+
+class MustError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class must_solve_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("warm_start", ctypes.c_int32), ("deterministic", ctypes.c_int32), ("equilibrate", ctypes.c_int32)]
+
+
+def load():
+    """Load the built library (``paper_2308_16317_gb300/build.py``); raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libmust.so is not built (run paper_2308_16317_gb300/build.py); "
+                          "there is no fallback path")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, D, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "must_default_opts": (None, [ctypes.POINTER(must_solve_opts)]),
+        "must_liz_build": (I32, [P, P, I32, I32, P, P, ctypes.POINTER(P)]),
+        "must_liz_free": (None, [P]),
+        "must_liz_order": (I32, [P]),
+        "must_liz_kappa": (I32, [P]),
+        "must_workspace_bytes": (SZ, [P, I32, ctypes.POINTER(must_solve_opts)]),
+        "must_batch_workspace_bytes": (SZ, [I32, P, I32, ctypes.POINTER(must_solve_opts)]),
+        "must_tinv_square_well": (I32, [I32, P, I32, P, D, I32, P, P]),
+        "must_tau00_solve": (I32, [P, I32, P, P, I32, I32, ctypes.POINTER(must_solve_opts), P, SZ, P, P, P]),
+        "must_tau00_batch": (I32, [I32, P, I32, P, P, I32, I32, ctypes.POINTER(must_solve_opts), P, SZ, P, P, P]),
+        "must_status_string": (ctypes.c_char_p, [I32]),
+        "must_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return [n for n in ("must_default_opts", "must_liz_build", "must_liz_free", "must_liz_order", "must_liz_kappa",
+                        "must_workspace_bytes", "must_batch_workspace_bytes", "must_tinv_square_well",
+                        "must_tau00_solve", "must_tau00_batch", "must_status_string", "must_last_error")]
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(a))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _check(code: int):
+    if code != 0:
+        raise MustError(code, load().must_last_error().decode(errors="replace"))
+
+
+def must_default_opts(precision: int = MUST_FP64, **kw) -> must_solve_opts:
+    o = must_solve_opts()
+    load().must_default_opts(ctypes.byref(o))
+    o.precision = precision
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Liz:
+    """Owning wrapper of a must_liz handle."""
+
+    def __init__(self, handle, n_sites, lmax, canted):
+        self.handle = handle
+        self.n_sites, self.lmax, self.canted = n_sites, lmax, canted
+        self.n = load().must_liz_order(handle)
+        self.kappa = load().must_liz_kappa(handle)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.must_liz_free(self.handle)
+            self.handle = None
+
+
+def must_liz_build(pos, species, lmax: int, spin_dirs=None, stream=None) -> Liz:
+    pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64))
+    species = np.ascontiguousarray(np.asarray(species, dtype=np.int32))
+    dirs = None if spin_dirs is None else np.ascontiguousarray(np.asarray(spin_dirs, dtype=np.float64))
+    out = ctypes.c_void_p()
+    _check(load().must_liz_build(_ptr(pos), _ptr(species), int(pos.shape[0]), int(lmax), _ptr(dirs),
+                                 _stream(stream), ctypes.byref(out)))
+    return Liz(out, int(pos.shape[0]), int(lmax), dirs is not None)
+
+
+def must_workspace_bytes(liz: Liz, n_items: int, opts: must_solve_opts | None = None) -> int:
+    return int(load().must_workspace_bytes(liz.handle, int(n_items), ctypes.byref(opts) if opts else None))
+
+
+def must_batch_workspace_bytes(lizs, n_items_per_liz: int, opts: must_solve_opts | None = None) -> int:
+    arr = (ctypes.c_void_p * len(lizs))(*[z.handle.value for z in lizs])
+    return int(load().must_batch_workspace_bytes(len(lizs), arr, int(n_items_per_liz),
+                                                 ctypes.byref(opts) if opts else None))
+
+
+def must_tinv_square_well(E, V, r_mt: float, lmax: int, tinv, stream=None):
+    """E: [nE] complex128 (as float64 pairs), V: [n_pot] float64, tinv: [n_pot][nE][lmax+1] complex128."""
+    nE = _numel_complex(E)
+    n_pot = V.numel() if hasattr(V, "numel") else int(np.asarray(V).size)
+    _check(load().must_tinv_square_well(nE, _ptr(E), n_pot, _ptr(V), float(r_mt), int(lmax), _ptr(tinv),
+                                        _stream(stream)))
+    return tinv
+
+
+def _numel_complex(a):
+    if hasattr(a, "numel"):
+        return a.numel() if a.is_complex() else a.numel() // 2
+    a = np.asarray(a)
+    return a.size if np.iscomplexobj(a) else a.size // 2
+
+
+def must_tau00_solve(liz: Liz, E, tinv, n_species: int, nspin: int, opts: must_solve_opts | None, workspace,
+                     ws_bytes: int, tau00, status=None, stream=None):
+    _check(load().must_tau00_solve(liz.handle, _numel_complex(E), _ptr(E), _ptr(tinv), int(n_species), int(nspin),
+                                   ctypes.byref(opts) if opts else None, _ptr(workspace), int(ws_bytes), _ptr(tau00),
+                                   _ptr(status), _stream(stream)))
+    return tau00
+
+
+def must_tau00_batch(lizs, E, tinv, n_species: int, nspin: int, opts: must_solve_opts | None, workspace,
+                     ws_bytes: int, tau00, status=None, stream=None):
+    arr = (ctypes.c_void_p * len(lizs))(*[z.handle.value for z in lizs])
+    _check(load().must_tau00_batch(len(lizs), arr, _numel_complex(E), _ptr(E), _ptr(tinv), int(n_species), int(nspin),
+                                   ctypes.byref(opts) if opts else None, _ptr(workspace), int(ws_bytes), _ptr(tau00),
+                                   _ptr(status), _stream(stream)))
+    return tau00

@@ -1,0 +1,364 @@
+// KKR matrix assembly on the device (paper Sec. 5: "construct the KKR matrix on
+// GPUs"; Eq. (4): M = t^{-1} - g0, g0 between different sites only).
+//
+//   geom_kernel     once per LIZ: pair distances and real Y_L'' of each pair
+//                   direction (R_pq = pos(p) - pos(q), p < q in the permuted
+//                   order with the central site last).
+//   tinv_kernel     square-well t^{-1}_l(E) fixture (log-derivative matching).
+//   scale_kernel    |M_aa|^{-1/2} for the symmetric equilibration of the
+//                   low-precision factorisation.
+//   assemble_kernel one warp per unordered site pair (or diagonal site) and
+//                   energy: Hankel functions h_l''(kappa d), the sparse Gaunt
+//                   contraction into a kap x kap block, written for both
+//                   pair orders (parity: G^{qp}_{LL'} = (-1)^{l+l'} G^{pq}_{LL'})
+//                   and every spin that shares the energy; column-major,
+//                   16-byte complex stores, consecutive lanes on consecutive
+//                   rows.
+#include "common.cuh"
+#include "solver.h"
+
+namespace {
+
+__device__ __forceinline__ int l_of(int L) {
+  int l = 0;
+  while ((l + 1) * (l + 1) <= L) ++l;
+  return l;
+}
+
+// Real spherical harmonics Y_L(v^), L = l*l+l+m < (lmax+1)^2, no Condon-Shortley
+// phase: Y_lm = N_lm P_l^|m|(cos th) {sqrt2 cos m phi | 1 | sqrt2 sin |m| phi}.
+__device__ void ylm_real(int lmax, double x, double y, double z, double* out) {
+  const double r = sqrt(x * x + y * y + z * z);
+  const double rho = sqrt(x * x + y * y);
+  const double ct = z / r, st = rho / r;
+  double cph = 1.0, sph = 0.0;
+  if (rho > 0.0) { cph = x / rho; sph = y / rho; }
+  double cm = 1.0, sm = 0.0;   // cos(m phi), sin(m phi)
+  double pmm = 1.0;            // P_m^m = (2m-1)!! st^m
+  for (int m = 0; m <= lmax; ++m) {
+    if (m > 0) {
+      const double c2 = cm * cph - sm * sph, s2 = sm * cph + cm * sph;
+      cm = c2; sm = s2;
+      pmm *= (2.0 * m - 1.0) * st;
+    }
+    double p_lm2 = 0.0, p_lm1 = pmm;
+    for (int l = m; l <= lmax; ++l) {
+      double p;
+      if (l == m) p = pmm;
+      else if (l == m + 1) p = ct * (2.0 * m + 1.0) * pmm;
+      else p = ((2.0 * l - 1.0) * ct * p_lm1 - (l + m - 1.0) * p_lm2) / double(l - m);
+      if (l > m) { p_lm2 = p_lm1; p_lm1 = p; }
+      // N_lm = sqrt((2l+1)/(4pi) (l-m)!/(l+m)!)
+      double ratio = 1.0;
+      for (int k = l - m + 1; k <= l + m; ++k) ratio /= double(k);
+      const double N = sqrt((2.0 * l + 1.0) / (4.0 * 3.14159265358979323846) * ratio);
+      if (m == 0) {
+        out[l * l + l] = N * p;
+      } else {
+        out[l * l + l + m] = 1.41421356237309504880 * N * p * cm;
+        out[l * l + l - m] = 1.41421356237309504880 * N * p * sm;
+      }
+    }
+  }
+}
+
+// h_l(z), l = 0..lmax, outgoing spherical Hankel functions by upward recurrence
+// from h_0 = -i e^{iz}/z and h_1 = -e^{iz} (z + i)/z^2.
+__device__ void hankel_up(int lmax, cd z, cd* h) {
+  const cd e = cexpi(z);
+  const cd iz = cinv(z);
+  h[0] = mk(e.y, -e.x) * iz;                       // -i e / z
+  if (lmax >= 1) h[1] = -(e * (z + mk(0.0, 1.0))) * (iz * iz);
+  for (int l = 1; l < lmax; ++l) h[l + 1] = (2.0 * l + 1.0) * (iz * h[l]) - h[l - 1];
+}
+
+// j_l(z), l = 0..lmax (lmax >= 1): power series for |z| < 1, else Miller's downward
+// recurrence normalised to sin z / z (or to j_1 where j_0 is the smaller).
+__device__ void bessel_j(int lmax, cd z, cd* j) {
+  const double az = sqrt(cnorm(z));
+  if (az < 1.0) {
+    const cd q = -0.5 * (z * z);
+    cd zl = mk(1.0, 0.0);
+    double df = 1.0;
+    for (int l = 0; l <= lmax; ++l) {
+      if (l > 0) { zl = zl * z; df *= (2.0 * l + 1.0); }
+      cd term = mk(1.0, 0.0), sum = mk(1.0, 0.0);
+      for (int k = 1; k < 40; ++k) {
+        term = (1.0 / (double(k) * (2.0 * l + 2.0 * k + 1.0))) * (term * q);
+        sum = sum + term;
+        if (cnorm(term) < 1e-36 * cnorm(sum)) break;
+      }
+      j[l] = (1.0 / df) * (zl * sum);
+    }
+    return;
+  }
+  const cd iz = cinv(z);
+  const int top = lmax + 24 + int(1.5 * az);
+  cd fp1 = mk(0.0, 0.0), f = mk(1e-200, 0.0);
+  for (int l = top; l >= 1; --l) {
+    const cd fm1 = (2.0 * l + 1.0) * (iz * f) - fp1;
+    fp1 = f;
+    f = fm1;
+    if (cnorm(f) > 1e200) {       // rescale the recurrence and every value kept so far
+      const double s = 1e-100;
+      f = s * f;
+      fp1 = s * fp1;
+      for (int m = l; m <= lmax; ++m) j[m] = s * j[m];
+    }
+    if (l - 1 <= lmax) j[l - 1] = f;
+  }
+  const cd f0 = j[0], f1 = j[1];
+  const cd e = cexpi(z);                                  // e^{iz}
+  const cd emi = cinv(e);                                 // e^{-iz}
+  const cd sz = mk(0.0, -0.5) * (e - emi);                // sin z = (e^{iz} - e^{-iz}) / (2i)
+  const cd cz = 0.5 * (e + emi);
+  const cd j0 = sz * iz;
+  const cd j1 = (sz * iz - cz) * iz;
+  const cd sc = (cnorm(j0) >= cnorm(j1)) ? cdiv(j0, f0) : cdiv(j1, f1);
+  for (int l = 0; l <= lmax; ++l) j[l] = sc * j[l];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+__global__ void geom_kernel(int N, int nL2, int l2max, const double* __restrict__ pos_perm,
+                            const int2* __restrict__ pq, int n_pairs, double* __restrict__ d_out,
+                            double* __restrict__ Y_out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_pairs) return;
+  const int2 e = pq[t];
+  const double x = pos_perm[3 * e.x] - pos_perm[3 * e.y];
+  const double y = pos_perm[3 * e.x + 1] - pos_perm[3 * e.y + 1];
+  const double z = pos_perm[3 * e.x + 2] - pos_perm[3 * e.y + 2];
+  d_out[t] = sqrt(x * x + y * y + z * z);
+  double Y[MUST_MAX_NL2];
+  ylm_real(l2max, x, y, z, Y);
+  for (int L = 0; L < nL2; ++L) Y_out[size_t(t) * nL2 + L] = Y[L];
+}
+
+// t^{-1}_l = i k [k h'(ka) j(qa) - q j'(qa) h(ka)] / [k j'(ka) j(qa) - q j'(qa) j(ka)],
+// with f_l' = f_{l-1} - (l+1)/z f_l and f_0' = -f_1.
+__global__ void tinv_kernel(int nE, const double2* __restrict__ E, int n_pot, const double* __restrict__ V,
+                            double a, int lmax, double2* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nE * n_pot) return;
+  const int p = t / nE, e = t % nE;
+  const cd Ec = mk(E[e].x, E[e].y);
+  const cd k = csqrt_p(Ec);
+  const cd q = csqrt_p(Ec - mk(V[p], 0.0));
+  const cd ka = a * k, qa = a * q;
+  cd jk[MUST_MAX_LMAX + 2], hk[MUST_MAX_LMAX + 2], jq[MUST_MAX_LMAX + 2];
+  bessel_j(lmax + 1, ka, jk);
+  hankel_up(lmax + 1, ka, hk);
+  bessel_j(lmax + 1, qa, jq);
+  const cd ika = cinv(ka), iqa = cinv(qa);
+  for (int l = 0; l <= lmax; ++l) {
+    cd djk, dhk, djq;
+    if (l == 0) { djk = -jk[1]; dhk = -hk[1]; djq = -jq[1]; }
+    else {
+      djk = jk[l - 1] - (l + 1.0) * (ika * jk[l]);
+      dhk = hk[l - 1] - (l + 1.0) * (ika * hk[l]);
+      djq = jq[l - 1] - (l + 1.0) * (iqa * jq[l]);
+    }
+    const cd num = mk(0.0, 1.0) * k * (k * dhk * jq[l] - q * djq * hk[l]);
+    const cd den = k * djk * jq[l] - q * djq * jk[l];
+    const cd r = cdiv(num, den);
+    out[size_t(p) * nE * (lmax + 1) + size_t(e) * (lmax + 1) + l] = make_double2(r.x, r.y);
+  }
+}
+
+// ------------------------------------------------------------------------
+struct AsmArgs {
+  int N, nL, nL2, lmax, kap, n, n_pairs, canted;
+  const int* species;     // [N] permuted
+  const double* dirs;     // [N][3] permuted (canted)
+  const int2* pair_pq;
+  const double* pair_d;
+  const double* pair_Y;
+  const int* g_start;
+  const int* g_L2;
+  const double* g_c;
+  int e0, nEc, nE, nspin, n_species;
+  const double2* E;       // [nE]
+  const double2* tinv;    // [nspin][n_species][nE][lmax+1]
+  double2* M64;           // item matrices (may be NULL)
+  float2* M32;            // equilibrated FP32 copies (may be NULL)
+  int ld;
+  size_t stride;          // elements between items (both copies)
+  const double* scale;    // [item][n] (required when M32 != NULL or scale64)
+  int items_per_e;        // nspin (collinear) or 1 (canted)
+  int scale64;            // 1: the FP64 copy is equilibrated too (D M D)
+};
+
+// M_aa of item `it` at row a (for the equilibration scale).
+__device__ __forceinline__ cd diag_entry(const AsmArgs& A, int it, int a) {
+  const int el = A.canted ? it : it % A.nEc;
+  const int s = A.canted ? 0 : it / A.nEc;
+  const int e = A.e0 + el;
+  const int p = a / A.kap, w = a % A.kap;
+  const int sp = A.species[p];
+  if (!A.canted) {
+    const int l = l_of(w);
+    const double2 v = A.tinv[((size_t(s) * A.n_species + sp) * A.nE + e) * (A.lmax + 1) + l];
+    return mk(v.x, v.y);
+  }
+  const int sg = w / A.nL, l = l_of(w % A.nL);
+  const double2 u = A.tinv[((size_t(0) * A.n_species + sp) * A.nE + e) * (A.lmax + 1) + l];
+  const double2 d = A.tinv[((size_t(1) * A.n_species + sp) * A.nE + e) * (A.lmax + 1) + l];
+  const double ez = A.dirs[3 * p + 2];
+  const cd av = mk(u.x, u.y), bv = mk(d.x, d.y);
+  return 0.5 * (av + bv) + (sg == 0 ? 0.5 * ez : -0.5 * ez) * (av - bv);
+}
+
+__global__ void scale_kernel(AsmArgs A, double* __restrict__ scale) {
+  const int it = blockIdx.y;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < A.n; a += gridDim.x * blockDim.x) {
+    const double m = sqrt(sqrt(cnorm(diag_entry(A, it, a))));
+    scale[size_t(it) * A.n + a] = (m > 0.0 && isfinite(m)) ? 1.0 / m : 1.0;
+  }
+}
+
+__device__ __forceinline__ void store_elem(const AsmArgs& A, int it, int row, int col, cd v) {
+  const size_t off = size_t(it) * A.stride + size_t(col) * A.ld + row;
+  if (A.M64) {
+    if (A.scale64) {
+      const double s = A.scale[size_t(it) * A.n + row] * A.scale[size_t(it) * A.n + col];
+      A.M64[off] = make_double2(s * v.x, s * v.y);
+    } else {
+      A.M64[off] = make_double2(v.x, v.y);
+    }
+  }
+  if (A.M32) {
+    const double s = A.scale[size_t(it) * A.n + row] * A.scale[size_t(it) * A.n + col];
+    A.M32[off] = make_float2(float(s * v.x), float(s * v.y));
+  }
+}
+
+// One warp per (unit, energy); units [0, n_pairs) are site pairs p < q, units
+// [n_pairs, n_pairs + N) are diagonal sites.
+__global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
+  __shared__ cd wsh[8][MUST_MAX_NL2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int unit = blockIdx.x * 8 + warp;
+  const int el = blockIdx.y;
+  if (unit >= A.n_pairs + A.N) return;
+  const int e = A.e0 + el;
+  const cd Ec = mk(A.E[e].x, A.E[e].y);
+  const int nL = A.nL, kap = A.kap;
+  if (unit < A.n_pairs) {
+    const int2 pq = A.pair_pq[unit];
+    const cd k = csqrt_p(Ec);
+    const double d = A.pair_d[unit];
+    const int l2max = 2 * A.lmax;
+    cd h[2 * MUST_MAX_LMAX + 1];
+    hankel_up(l2max, d * k, h);
+    // w'_L'' = 4 pi i kappa h_l'' Y_L''  (so that the block entry -G = sum c w')
+    const cd f = mk(0.0, 4.0 * 3.14159265358979323846) * k;
+    for (int L2 = lane; L2 < A.nL2; L2 += 32) {
+      const double y = A.pair_Y[size_t(unit) * A.nL2 + L2];
+      wsh[warp][L2] = y * (f * h[l_of(L2)]);
+    }
+    __syncwarp();
+    const int p = pq.x, q = pq.y;
+    for (int ent = lane; ent < nL * nL; ent += 32) {
+      const int L = ent % nL, Lp = ent / nL;
+      cd v = mk(0.0, 0.0);
+      const int b = A.g_start[L * nL + Lp], t = A.g_start[L * nL + Lp + 1];
+      for (int i = b; i < t; ++i) {
+        const double c = A.g_c[i];
+        const cd w = wsh[warp][A.g_L2[i]];
+        v.x = fma(c, w.x, v.x);
+        v.y = fma(c, w.y, v.y);
+      }
+      const double par = ((l_of(L) + l_of(Lp)) & 1) ? -1.0 : 1.0;
+      const cd vt = par * v;
+      for (int ii = 0; ii < A.items_per_e; ++ii) {
+        const int it = A.canted ? el : ii * A.nEc + el;
+        if (!A.canted) {
+          store_elem(A, it, p * kap + L, q * kap + Lp, v);
+          store_elem(A, it, q * kap + L, p * kap + Lp, vt);
+        } else {
+          for (int s = 0; s < 2; ++s) {
+            store_elem(A, it, p * kap + s * nL + L, q * kap + s * nL + Lp, v);
+            store_elem(A, it, p * kap + s * nL + L, q * kap + (1 - s) * nL + Lp, mk(0.0, 0.0));
+            store_elem(A, it, q * kap + s * nL + L, p * kap + s * nL + Lp, vt);
+            store_elem(A, it, q * kap + s * nL + L, p * kap + (1 - s) * nL + Lp, mk(0.0, 0.0));
+          }
+        }
+      }
+    }
+  } else {
+    const int p = unit - A.n_pairs;
+    const int sp = A.species[p];
+    for (int ii = 0; ii < A.items_per_e; ++ii) {
+      const int it = A.canted ? el : ii * A.nEc + el;
+      for (int ent = lane; ent < kap * kap; ent += 32) {
+        const int a = ent % kap, b = ent / kap;
+        cd v = mk(0.0, 0.0);
+        if (!A.canted) {
+          if (a == b) {
+            const double2 t = A.tinv[((size_t(ii) * A.n_species + sp) * A.nE + e) * (A.lmax + 1) + l_of(a)];
+            v = mk(t.x, t.y);
+          }
+        } else {
+          const int sa = a / nL, La = a % nL, sb = b / nL, Lb = b % nL;
+          if (La == Lb) {
+            const int l = l_of(La);
+            const double2 u = A.tinv[((size_t(0) * A.n_species + sp) * A.nE + e) * (A.lmax + 1) + l];
+            const double2 dn = A.tinv[((size_t(1) * A.n_species + sp) * A.nE + e) * (A.lmax + 1) + l];
+            const cd av = mk(u.x, u.y), bv = mk(dn.x, dn.y);
+            const cd hs = 0.5 * (av + bv), hd = 0.5 * (av - bv);
+            const double ex = A.dirs[3 * p], ey = A.dirs[3 * p + 1], ez = A.dirs[3 * p + 2];
+            // sigma.e = [[ez, ex - i ey], [ex + i ey, -ez]]
+            cd sig;
+            if (sa == 0 && sb == 0) sig = mk(ez, 0.0);
+            else if (sa == 0 && sb == 1) sig = mk(ex, -ey);
+            else if (sa == 1 && sb == 0) sig = mk(ex, ey);
+            else sig = mk(-ez, 0.0);
+            v = hd * sig;
+            if (sa == sb) v = v + hs;
+          }
+        }
+        store_elem(A, it, p * kap + a, p * kap + b, v);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// Host launchers
+void launch_geom(int N, int lmax, const double* pos_perm, const int2* pq, int n_pairs, double* d, double* Y,
+                 cudaStream_t st) {
+  const int l2max = 2 * lmax, nL2 = (l2max + 1) * (l2max + 1);
+  if (n_pairs > 0) geom_kernel<<<(n_pairs + 127) / 128, 128, 0, st>>>(N, nL2, l2max, pos_perm, pq, n_pairs, d, Y);
+}
+
+void launch_tinv(int nE, const double2* E, int n_pot, const double* V, double a, int lmax, double2* out,
+                 cudaStream_t st) {
+  const int t = nE * n_pot;
+  if (t > 0) tinv_kernel<<<(t + 127) / 128, 128, 0, st>>>(nE, E, n_pot, V, a, lmax, out);
+}
+
+void launch_assemble(const AsmArgs& A, cudaStream_t st) {
+  const int n_items = A.items_per_e * A.nEc;
+  if (A.M32 || A.scale64) {
+    dim3 g((A.n + 255) / 256, n_items);
+    scale_kernel<<<g, 256, 0, st>>>(A, const_cast<double*>(A.scale));
+  }
+  dim3 grid((A.n_pairs + A.N + 7) / 8, A.nEc);
+  assemble_kernel<<<grid, 256, 0, st>>>(A);
+}
+
+void launch_assemble_chunk(const AsmChunk& c, cudaStream_t st) {
+  const must_liz* z = c.liz;
+  AsmArgs A;
+  A.N = z->N; A.nL = z->nL; A.nL2 = z->nL2; A.lmax = z->lmax; A.kap = z->kap; A.n = z->n;
+  A.n_pairs = z->n_pairs; A.canted = z->canted;
+  A.species = z->d_species_perm; A.dirs = z->d_dirs_perm; A.pair_pq = z->d_pair_pq; A.pair_d = z->d_pair_d;
+  A.pair_Y = z->d_pair_Y; A.g_start = z->d_g_start; A.g_L2 = z->d_g_L2; A.g_c = z->d_g_c;
+  A.e0 = c.e0; A.nEc = c.nEc; A.nE = c.nE; A.nspin = c.nspin; A.n_species = c.n_species;
+  A.E = c.E; A.tinv = c.tinv; A.M64 = c.M64; A.M32 = c.M32; A.ld = c.ld; A.stride = c.stride; A.scale = c.scale;
+  A.items_per_e = z->canted ? 1 : c.nspin;
+  A.scale64 = c.scale64;
+  launch_assemble(A, st);
+}

@@ -1,0 +1,551 @@
+// Mixed-precision path (growth item 1 of the design: low-precision
+// factorisation on the tensor cores + FP64 iterative refinement).
+//
+//   M_s = D M D, D = diag(|M_aa|^{-1/2})        (symmetric equilibration)
+//   P M_s[:, :r] eliminated in FP32, trailing updates on the tensor cores
+//   (split-BF16x3 or 3xTF32, FP32 accumulation, see tc_gemm.cu)
+//   X_0 = 0; repeat: R = E0 - M X (FP64), delta = D U^{-1} L^{-1} P D R (FP32),
+//   X += delta, until ||delta||_F <= tol ||X||_F; tau_00 = X_c (central rows).
+//
+// The paper (Sec. 3.2, 4.1) computes everything in complex double; on GB300
+// FP64 runs at ~1/70 of FP32 SIMT and ~1/1800 of BF16 tensor throughput, so
+// the O(n^3) part moves to FP32/BF16 and FP64 is kept for the residual and the
+// solution update (the parts that decide the final accuracy).
+#include <algorithm>
+
+#include "mixed.h"
+#include "tc_gemm.h"
+
+namespace {
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+constexpr int PT = 256;   // threads of per-item kernels
+
+__device__ __forceinline__ void argmax_merge(float& v, int& i, float v2, int i2) {
+  if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+}
+
+__device__ __forceinline__ float cnormf(cf a) { return a.x * a.x + a.y * a.y; }
+
+}  // namespace
+
+// ------------------------------------------------------------ FP32 panel --
+__global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int r,
+                                                     int k0, int nbe, int* __restrict__ piv0, int* __restrict__ status,
+                                                     const int* __restrict__ conv) {
+  __shared__ float sv[PT / 32];
+  __shared__ int si[PT / 32];
+  __shared__ int s_p;
+  const int item = blockIdx.x;
+  cf* A = reinterpret_cast<cf*>(A0 + size_t(item) * stride);
+  int* piv = piv0 + size_t(item) * r;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = 0; j < nbe; ++j) {
+    const int c = k0 + j;
+    cf* col = A + size_t(c) * ld;
+    float best = -1.0f;
+    int bi = c;
+    for (int i = c + tid; i < r; i += PT) argmax_merge(best, bi, cnormf(col[i]), i);
+    for (int o = 16; o > 0; o >>= 1) {
+      const float v2 = __shfl_down_sync(0xffffffffu, best, o);
+      const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+      argmax_merge(best, bi, v2, i2);
+    }
+    if (lane == 0) { sv[warp] = best; si[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      float b = sv[0];
+      int p = si[0];
+      for (int w = 1; w < PT / 32; ++w) argmax_merge(b, p, sv[w], si[w]);
+      if (!(b > 0.0f)) status[item] = ST_SINGULAR;
+      piv[c] = p;
+      s_p = p;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != c)
+      for (int cc = k0 + tid; cc < k0 + nbe; cc += PT) {
+        cf* cp = A + size_t(cc) * ld;
+        const cf t = cp[c];
+        cp[c] = cp[p];
+        cp[p] = t;
+      }
+    __syncthreads();
+    const cf d = col[c];
+    if (cnormf(d) > 0.0f) {
+      const cf inv = cinvf(d);
+      for (int i = c + 1 + tid; i < n; i += PT) {
+        const cf l = cmulf(col[i], inv);
+        col[i] = l;
+        for (int cc = c + 1; cc < k0 + nbe; ++cc) cfmsf(A[size_t(cc) * ld + i], l, A[size_t(cc) * ld + c]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void laswp32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int r, int k0, int nbe,
+                               const int* __restrict__ piv0) {
+  const int item = blockIdx.y;
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= n - nbe) return;
+  if (col >= k0) col += nbe;
+  float2* A = A0 + size_t(item) * stride + size_t(col) * ld;
+  const int* piv = piv0 + size_t(item) * r;
+  for (int j = 0; j < nbe; ++j) {
+    const int c = k0 + j, p = piv[c];
+    if (p != c) {
+      const float2 t = A[c];
+      A[c] = A[p];
+      A[p] = t;
+    }
+  }
+}
+
+// U12 = L11^{-1} A12, nbe <= 64: one warp per column, lane i holds x_i, x_{i+32}.
+__global__ void __launch_bounds__(256) trsm32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int k0,
+                                                     int nbe) {
+  __shared__ cf L[64][65];
+  const int item = blockIdx.y;
+  cf* A = reinterpret_cast<cf*>(A0 + size_t(item) * stride);
+  for (int t = threadIdx.x; t < nbe * nbe; t += blockDim.x) {
+    const int i = t % nbe, j = t / nbe;
+    L[i][j] = A[size_t(k0 + j) * ld + k0 + i];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col = k0 + nbe + blockIdx.x * 8 + warp;
+  if (col >= n) return;
+  cf* x = A + size_t(col) * ld + k0;
+  cf v0 = (lane < nbe) ? x[lane] : mkf(0.f, 0.f);
+  cf v1 = (lane + 32 < nbe) ? x[lane + 32] : mkf(0.f, 0.f);
+  for (int j = 0; j < nbe - 1; ++j) {
+    const cf src = (j < 32) ? v0 : v1;
+    const cf xj = mkf(__shfl_sync(0xffffffffu, src.x, j & 31), __shfl_sync(0xffffffffu, src.y, j & 31));
+    if (lane > j && lane < nbe) cfmsf(v0, L[lane][j], xj);
+    if (lane + 32 > j && lane + 32 < nbe) cfmsf(v1, L[lane + 32][j], xj);
+  }
+  if (lane < nbe) x[lane] = v0;
+  if (lane + 32 < nbe) x[lane + 32] = v1;
+}
+
+// ------------------------------------------------ permutation, Schur block --
+// perm[i] = row of the original matrix that the swap sequence moves to row i.
+__global__ void perm_kernel(const int* __restrict__ piv0, int r, int n, int* __restrict__ perm0, int items) {
+  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= items) return;
+  const int* piv = piv0 + size_t(item) * r;
+  int* perm = perm0 + size_t(item) * n;
+  for (int i = 0; i < n; ++i) perm[i] = i;
+  for (int k = 0; k < r; ++k) {
+    const int p = piv[k];
+    const int t = perm[k];
+    perm[k] = perm[p];
+    perm[p] = t;
+  }
+}
+
+// Sinv = S_s^{-1} (FP64 Gauss-Jordan on the FP32 Schur block of M_s).
+__global__ void __launch_bounds__(256) schur_inv32_kernel(const float2* __restrict__ A0, size_t stride, int ld, int n,
+                                                          int kap, double2* __restrict__ Sinv0,
+                                                          int* __restrict__ status) {
+  extern __shared__ cd W[];
+  __shared__ int s_p;
+  const int item = blockIdx.x;
+  const cf* A = reinterpret_cast<const cf*>(A0 + size_t(item) * stride);
+  const int r = n - kap, w = 2 * kap;
+  for (int t = threadIdx.x; t < kap * w; t += blockDim.x) {
+    const int i = t / w, j = t % w;
+    if (j < kap) {
+      const cf v = A[size_t(r + j) * ld + r + i];
+      W[t] = mk(v.x, v.y);
+    } else {
+      W[t] = mk(j - kap == i ? 1.0 : 0.0, 0.0);
+    }
+  }
+  __syncthreads();
+  bool ok = true;
+  for (int t = threadIdx.x; t < kap * w; t += blockDim.x)
+    if (!isfinite(W[t].x) || !isfinite(W[t].y)) ok = false;
+  ok = __syncthreads_and(ok);
+  for (int k = 0; k < kap && ok; ++k) {
+    if (threadIdx.x == 0) {
+      int p = k;
+      double b = cnorm(W[k * w + k]);
+      for (int i = k + 1; i < kap; ++i)
+        if (cnorm(W[i * w + k]) > b) { b = cnorm(W[i * w + k]); p = i; }
+      s_p = (b > 0.0) ? p : -1;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p < 0) { ok = false; break; }
+    if (p != k)
+      for (int j = threadIdx.x; j < w; j += blockDim.x) {
+        const cd t = W[k * w + j];
+        W[k * w + j] = W[p * w + j];
+        W[p * w + j] = t;
+      }
+    __syncthreads();
+    const cd inv = cinv(W[k * w + k]);
+    __syncthreads();
+    for (int j = threadIdx.x; j < w; j += blockDim.x) W[k * w + j] = W[k * w + j] * inv;
+    __syncthreads();
+    for (int t = threadIdx.x; t < kap * w; t += blockDim.x) {
+      const int i = t / w, j = t % w;
+      if (i == k || j == k) continue;
+      cfms(W[t], W[i * w + k], W[k * w + j]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kap; i += blockDim.x)
+      if (i != k) W[i * w + k] = mk(0.0, 0.0);
+    __syncthreads();
+  }
+  double2* Sinv = Sinv0 + size_t(item) * kap * kap;
+  for (int t = threadIdx.x; t < kap * kap; t += blockDim.x) {
+    const int i = t / kap, j = t % kap;    // row-major Sinv[i][j]
+    const cd v = ok ? W[i * w + kap + j] : mk(0.0, 0.0);
+    Sinv[t] = make_double2(v.x, v.y);
+  }
+  if (threadIdx.x == 0 && !ok) status[item] = ST_SINGULAR;
+}
+
+// ------------------------------------------------------------ residual ----
+// R = E0 - M X (FP64) for items that have not converged; E0 = the last kap
+// columns of the identity (central site ordered last).  64 rows x up to 4 RHS
+// per thread group; X staged through shared memory 64 rows at a time.
+__global__ void residual64_kernel(const double2* __restrict__ M0, size_t stride, int ld, int n, int kap,
+                                  const double2* __restrict__ X0, double2* __restrict__ R0,
+                                  const int* __restrict__ conv) {
+  extern __shared__ cd Xs[];   // [64][kap]
+  const int item = blockIdx.y;
+  if (conv[item]) return;
+  const cd* M = reinterpret_cast<const cd*>(M0 + size_t(item) * stride);
+  const cd* X = reinterpret_cast<const cd*>(X0 + size_t(item) * n * kap);
+  const int tid = threadIdx.x;
+  const int row = blockIdx.x * 64 + (tid & 63);
+  const int c0 = (tid >> 6) * 4;
+  cd acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = mk(0.0, 0.0);
+  for (int k0 = 0; k0 < n; k0 += 64) {
+    const int kn = min(64, n - k0);
+    __syncthreads();
+    for (int t = tid; t < kn * kap; t += blockDim.x) {
+      const int k = t % kn, c = t / kn;
+      Xs[k * kap + c] = X[size_t(c) * n + k0 + k];
+    }
+    __syncthreads();
+    if (row < n) {
+      for (int k = 0; k < kn; ++k) {
+        const cd m = M[size_t(k0 + k) * ld + row];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (c0 + q < kap) {
+            const cd x = Xs[k * kap + c0 + q];
+            acc[q].x = fma(m.x, x.x, acc[q].x);
+            acc[q].x = fma(-m.y, x.y, acc[q].x);
+            acc[q].y = fma(m.x, x.y, acc[q].y);
+            acc[q].y = fma(m.y, x.x, acc[q].y);
+          }
+      }
+    }
+  }
+  if (row < n) {
+    double2* R = R0 + size_t(item) * n * kap;
+    const int r = n - kap;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (c0 + q < kap) {
+        const int c = c0 + q;
+        const double e = (row == r + c) ? 1.0 : 0.0;
+        R[size_t(c) * n + row] = make_double2(e - acc[q].x, -acc[q].y);
+      }
+  }
+}
+
+// --------------------------------------------- low-precision correction ----
+// delta = D U^{-1} L^{-1} P (D R) for G right-hand sides per CTA (w in shared
+// memory, FP32), then X += delta (FP64) and ||delta||^2, ||X||^2 accumulated.
+// first != 0: R is E0 (not read) and X is overwritten.
+template <int G>
+__global__ void __launch_bounds__(256) correct_kernel(const float2* __restrict__ A0, size_t stride, int ld, int n,
+                                                      int kap, const int* __restrict__ perm0,
+                                                      const double* __restrict__ scale0,
+                                                      const double2* __restrict__ Sinv0,
+                                                      const double2* __restrict__ R0, double2* __restrict__ X0,
+                                                      double* __restrict__ norms, const int* __restrict__ conv,
+                                                      int first) {
+  extern __shared__ cf w[];   // [n][G]
+  const int item = blockIdx.y;
+  if (conv[item]) return;
+  const int cb = blockIdx.x * G;
+  const int ng = min(G, kap - cb);
+  const cf* A = reinterpret_cast<const cf*>(A0 + size_t(item) * stride);
+  const int* perm = perm0 + size_t(item) * n;
+  const double* d = scale0 + size_t(item) * n;
+  const int r = n - kap;
+  const int tid = threadIdx.x, T = blockDim.x;
+  // gather w = P (D R)
+  for (int t = tid; t < n * G; t += T) {
+    const int i = t / G, c = t % G;
+    cf v = mkf(0.f, 0.f);
+    if (c < ng) {
+      const int src = perm[i];
+      if (first) {
+        if (src == r + cb + c) v = mkf(float(d[src]), 0.f);
+      } else {
+        const double2 rv = R0[size_t(item) * n * kap + size_t(cb + c) * n + src];
+        v = mkf(float(d[src] * rv.x), float(d[src] * rv.y));
+      }
+    }
+    w[t] = v;
+  }
+  __syncthreads();
+  // forward: unit lower L, columns 0..r-1
+  for (int jb = 0; jb < r; jb += 32) {
+    const int je = min(jb + 32, r);
+    for (int j = jb; j < je; ++j) {
+      for (int t = tid; t < (je - j - 1) * G; t += T) {
+        const int i = j + 1 + t / G, c = t % G;
+        cfmsf(w[i * G + c], A[size_t(j) * ld + i], w[j * G + c]);
+      }
+      __syncthreads();
+    }
+    for (int i = je + tid; i < n; i += T) {
+      cf acc[G];
+#pragma unroll
+      for (int c = 0; c < G; ++c) acc[c] = w[i * G + c];
+      for (int j = jb; j < je; ++j) {
+        const cf l = A[size_t(j) * ld + i];
+#pragma unroll
+        for (int c = 0; c < G; ++c) cfmsf(acc[c], l, w[j * G + c]);
+      }
+#pragma unroll
+      for (int c = 0; c < G; ++c) w[i * G + c] = acc[c];
+    }
+    __syncthreads();
+  }
+  // central block: w_c = Sinv w_c (FP64 product)
+  {
+    const double2* Si = Sinv0 + size_t(item) * kap * kap;
+    cd tmp[G];
+    const int i = tid;
+    if (i < kap) {
+#pragma unroll
+      for (int c = 0; c < G; ++c) tmp[c] = mk(0.0, 0.0);
+      for (int k = 0; k < kap; ++k) {
+        const double2 s = Si[size_t(i) * kap + k];
+#pragma unroll
+        for (int c = 0; c < G; ++c) {
+          const cf x = w[(r + k) * G + c];
+          tmp[c] = tmp[c] + mk(s.x, s.y) * mk(x.x, x.y);
+        }
+      }
+    }
+    __syncthreads();
+    if (i < kap)
+#pragma unroll
+      for (int c = 0; c < G; ++c) w[(r + i) * G + c] = mkf(float(tmp[c].x), float(tmp[c].y));
+    __syncthreads();
+  }
+  // w_1 -= U12 w_c
+  for (int i = tid; i < r; i += T) {
+    cf acc[G];
+#pragma unroll
+    for (int c = 0; c < G; ++c) acc[c] = w[i * G + c];
+    for (int k = 0; k < kap; ++k) {
+      const cf u = A[size_t(r + k) * ld + i];
+#pragma unroll
+      for (int c = 0; c < G; ++c) cfmsf(acc[c], u, w[(r + k) * G + c]);
+    }
+#pragma unroll
+    for (int c = 0; c < G; ++c) w[i * G + c] = acc[c];
+  }
+  __syncthreads();
+  // backward: U11 (non-unit upper)
+  for (int je = r; je > 0; je -= 32) {
+    const int jb = max(je - 32, 0);
+    for (int j = je - 1; j >= jb; --j) {
+      const cf inv = cinvf(A[size_t(j) * ld + j]);
+      if (tid < G) w[j * G + tid] = cmulf(w[j * G + tid], inv);
+      __syncthreads();
+      for (int t = tid; t < (j - jb) * G; t += T) {
+        const int i = jb + t / G, c = t % G;
+        cfmsf(w[i * G + c], A[size_t(j) * ld + i], w[j * G + c]);
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < jb; i += T) {
+      cf acc[G];
+#pragma unroll
+      for (int c = 0; c < G; ++c) acc[c] = w[i * G + c];
+      for (int j = jb; j < je; ++j) {
+        const cf u = A[size_t(j) * ld + i];
+#pragma unroll
+        for (int c = 0; c < G; ++c) cfmsf(acc[c], u, w[j * G + c]);
+      }
+#pragma unroll
+      for (int c = 0; c < G; ++c) w[i * G + c] = acc[c];
+    }
+    __syncthreads();
+  }
+  // X += D w
+  double dn = 0.0, xn = 0.0;
+  double2* X = X0 + size_t(item) * n * kap;
+  for (int t = tid; t < n * ng; t += T) {
+    const int i = t % n, c = t / n;
+    const cf v = w[i * G + c];
+    const double2 dl = make_double2(d[i] * v.x, d[i] * v.y);
+    double2 x = first ? make_double2(0.0, 0.0) : X[size_t(cb + c) * n + i];
+    x.x += dl.x;
+    x.y += dl.y;
+    X[size_t(cb + c) * n + i] = x;
+    dn += dl.x * dl.x + dl.y * dl.y;
+    xn += x.x * x.x + x.y * x.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dn += __shfl_down_sync(0xffffffffu, dn, o);
+    xn += __shfl_down_sync(0xffffffffu, xn, o);
+  }
+  if ((tid & 31) == 0) {
+    atomicAdd(&norms[2 * item], dn);
+    atomicAdd(&norms[2 * item + 1], xn);
+  }
+}
+
+// Convergence bookkeeping after a correction: conv = ||delta|| <= tol ||X||.
+// last = 1: final iteration (unconverged -> MUST_ENOCONV); last = 2: no
+// refinement was allowed at all (every item -> MUST_ENOCONV).
+__global__ void check_kernel(double* __restrict__ norms, int* __restrict__ conv, int* __restrict__ status, int items,
+                             double tol, int last) {
+  const int it = blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= items) return;
+  if (!conv[it]) {
+    const double dn = norms[2 * it], xn = norms[2 * it + 1];
+    if (!isfinite(dn) || !isfinite(xn)) {
+      conv[it] = 1;
+      if (status[it] == ST_OK) status[it] = ST_NONFINITE;
+    } else if (last < 2 && dn <= tol * tol * xn) {
+      conv[it] = 1;
+    } else if (last && status[it] == ST_OK) {
+      status[it] = ST_NOCONV;
+    }
+  }
+  norms[2 * it] = 0.0;
+  norms[2 * it + 1] = 0.0;
+}
+
+// tau_00 = X_c (central rows of the refined block column), column-major.
+__global__ void output_kernel(const double2* __restrict__ X0, int n, int kap, double2* __restrict__ out0,
+                              const int* __restrict__ out_index, const int* __restrict__ status,
+                              int* __restrict__ status_out, const int* __restrict__ err) {
+  const int item = blockIdx.x;
+  const double2* X = X0 + size_t(item) * n * kap;
+  const int r = n - kap;
+  double2* out = out0 + size_t(out_index[item]) * kap * kap;
+  for (int t = threadIdx.x; t < kap * kap; t += blockDim.x) {
+    const int i = t % kap, c = t / kap;
+    out[t] = X[size_t(c) * n + r + i];
+  }
+  if (threadIdx.x == 0 && status_out) status_out[out_index[item]] = *err ? int(MUST_ETIMEOUT) : status[item];
+}
+
+// ---------------------------------------------------------------- driver --
+size_t mixed_item_bytes(int n, int ld, int kap) {
+  return a256(size_t(ld) * n * 8)          // M32
+         + a256(size_t(n) * 8)             // scale
+         + a256(size_t(n) * 4)             // perm
+         + 2 * a256(size_t(n) * kap * 16)  // X, R
+         + a256(size_t(kap) * kap * 16)    // Sinv
+         + 512                             // norms, conv, error word
+         + tc_pack_bytes_per_item(n);      // tensor-core operand packs
+}
+
+must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
+  const int n = c.n, ld = c.ld, kap = c.kap, r = n - kap, items = c.items;
+  char* cur = c.ws;
+  auto take = [&](size_t b) { char* p = cur; cur += a256(b); return p; };
+  float2* M32 = reinterpret_cast<float2*>(take(size_t(items) * ld * n * 8));
+  double* scale = reinterpret_cast<double*>(take(size_t(items) * n * 8));
+  int* perm = reinterpret_cast<int*>(take(size_t(items) * n * 4));
+  double2* X = reinterpret_cast<double2*>(take(size_t(items) * n * kap * 16));
+  double2* R = reinterpret_cast<double2*>(take(size_t(items) * n * kap * 16));
+  double2* Sinv = reinterpret_cast<double2*>(take(size_t(items) * kap * kap * 16));
+  double* norms = reinterpret_cast<double*>(take(size_t(items) * 16));
+  int* conv = reinterpret_cast<int*>(take(size_t(items) * 4));
+  int* err = reinterpret_cast<int*>(take(4));
+  char* packs = take(size_t(items) * tc_pack_bytes_per_item(n));
+  const size_t stride = c.stride;   // same element stride for M64 and M32
+
+  AsmChunk a = c.asmc;
+  a.M32 = M32;
+  a.scale = scale;
+  launch_assemble_chunk(a, st);
+  cudaMemsetAsync(norms, 0, sizeof(double) * 2 * items, st);
+  cudaMemsetAsync(conv, 0, sizeof(int) * items, st);
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+
+  // FP32 elimination of the leading r columns of M_s
+  const int nb = tc_panel_width(c.opts.precision);
+  for (int k0 = 0; k0 < r; k0 += nb) {
+    const int nbe = std::min(nb, r - k0);
+    panel32_kernel<<<items, PT, 0, st>>>(M32, stride, ld, n, r, k0, nbe, c.piv, c.status, conv);
+    laswp32_kernel<<<dim3((n - nbe + 255) / 256, items), 256, 0, st>>>(M32, stride, ld, n, r, k0, nbe, c.piv);
+    const int rem = n - k0 - nbe;
+    if (rem > 0) {
+      trsm32_kernel<<<dim3((rem + 7) / 8, items), 256, 0, st>>>(M32, stride, ld, n, k0, nbe);
+      if (!tc_trailing_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, st))
+        return MUST_ECUDA;
+    }
+  }
+  perm_kernel<<<(items + 63) / 64, 64, 0, st>>>(c.piv, r, n, perm, items);
+  {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(schur_inv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 50 * 50 * 16);
+      attr = true;
+    }
+    schur_inv32_kernel<<<items, 256, size_t(kap) * 2 * kap * 16, st>>>(M32, stride, ld, n, kap, Sinv, c.status);
+  }
+  // refinement
+  const int G = (n <= 2600) ? 8 : 4;
+  const size_t smem_corr = size_t(n) * G * 8;
+  const dim3 gcorr((kap + G - 1) / G, items);
+  const size_t smem_res = size_t(64) * kap * 16;
+  const dim3 gres((n + 63) / 64, items);
+  const int tres = 64 * ((kap + 3) / 4);
+  {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(correct_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(correct_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(residual64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 16);
+      attr = true;
+    }
+  }
+  if (smem_corr > 227 * 1024) {
+    must_set_error("matrix order %d too large for the correction kernel", n);
+    return MUST_EUNSUPPORTED;
+  }
+  const int iters = std::max(c.opts.max_iter, 0);
+  for (int it = 0; it <= iters; ++it) {
+    const bool first = (it == 0);
+    if (!first) residual64_kernel<<<gres, tres, smem_res, st>>>(c.M64, stride, ld, n, kap, X, R, conv);
+    if (G == 8)
+      correct_kernel<8><<<gcorr, 256, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
+                                                       conv, first);
+    else
+      correct_kernel<4><<<gcorr, 256, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
+                                                       conv, first);
+    if (first) {
+      cudaMemsetAsync(norms, 0, sizeof(double) * 2 * items, st);
+    } else {
+      check_kernel<<<(items + 127) / 128, 128, 0, st>>>(norms, conv, c.status, items, c.opts.tol, it == iters);
+    }
+  }
+  if (iters == 0)   // no refinement allowed: the unrefined low-precision result is reported as not converged
+    check_kernel<<<(items + 127) / 128, 128, 0, st>>>(norms, conv, c.status, items, 0.0, 2);
+  output_kernel<<<items, 256, 0, st>>>(X, n, kap, c.tau, c.out_index, c.status, c.status_out, err);
+  return MUST_OK;
+}

@@ -1,0 +1,22 @@
+// Mixed-precision path: FP32 factors with tensor-core trailing updates and
+// FP64 residual refinement.
+#pragma once
+#include "common.cuh"
+#include "solver.h"
+
+struct MixedChunk {
+  AsmChunk asmc;
+  int n, ld, kap, items;
+  double2* M64;
+  size_t stride;
+  int* piv;
+  int* status;
+  const int* out_index;
+  double2* tau;
+  int* status_out;
+  char* ws;
+  must_solve_opts opts;
+};
+
+size_t mixed_item_bytes(int n, int ld, int kap);
+must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st);

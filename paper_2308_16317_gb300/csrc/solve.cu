@@ -1,0 +1,228 @@
+// Orchestration of must_tau00_solve / must_tau00_batch: workspace layout,
+// staging of host buffers, chunking over energies and the launch sequence
+//   assemble (M on the device) -> eliminate the leading n - kap columns ->
+//   tau_00 = S^{-1} (FP64 path), or the mixed-precision path in mixed.cu.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "solver.h"
+#include "mixed.h"
+
+namespace {
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int ld_of(int n) { return (n + 31) & ~31; }
+
+struct Layout {
+  int n, ld, r, kap, items_per_e, n_out;
+  int precision;
+  size_t per_item;      // bytes per matrix item
+  size_t staging;       // bytes for staged inputs/outputs (independent of chunk)
+};
+
+size_t item_bytes(int n, int ld, int kap, int precision) {
+  const size_t mat64 = a256(size_t(ld) * n * 16);
+  size_t b = mat64 + a256(size_t(n) * 4) /*piv*/ + a256(size_t(n) * 8) /*scale*/ + 256 /*status+index*/;
+  if (precision != MUST_FP64) b += mixed_item_bytes(n, ld, kap);
+  return b;
+}
+
+Layout make_layout(const must_liz* z, int nE, int nspin, int n_species, int precision, bool stage_E, bool stage_t,
+                   bool stage_tau, bool stage_st) {
+  Layout L;
+  L.n = z->n;
+  L.ld = ld_of(z->n);
+  L.kap = z->kap;
+  L.r = z->n - z->kap;
+  L.items_per_e = z->canted ? 1 : nspin;
+  L.n_out = z->canted ? 1 : nspin;
+  L.precision = precision;
+  L.per_item = item_bytes(L.n, L.ld, L.kap, precision);
+  size_t s = 0;
+  if (stage_E) s += a256(size_t(nE) * 16);
+  if (stage_t) s += a256(size_t(nspin) * n_species * nE * (z->lmax + 1) * 16);
+  if (stage_tau) s += a256(size_t(L.n_out) * nE * L.kap * L.kap * 16);
+  if (stage_st) s += a256(size_t(L.n_out) * nE * 4);
+  L.staging = s;
+  return L;
+}
+
+int check_opts(const must_solve_opts* o) {
+  if (o->precision < MUST_FP64 || o->precision > MUST_MIXED_TF32X3) return 0;
+  if (o->precision != MUST_FP64 && (o->max_iter < 0 || !(o->tol > 0.0))) return 0;
+  return 1;
+}
+
+}  // namespace
+
+extern "C" size_t must_workspace_bytes(const must_liz* z, int32_t n_items, const must_solve_opts* opts) {
+  if (!z || n_items < 1) return 0;
+  must_solve_opts o;
+  must_default_opts(&o);
+  if (opts) o = *opts;
+  const int ld = ld_of(z->n);
+  // staging assumes host inputs/outputs (an upper bound); 2 species, 2 spins
+  const size_t stage = a256(size_t(n_items) * 16) + a256(size_t(n_items) * 4 * (z->lmax + 1) * 16) +
+                       a256(size_t(n_items) * z->kap * z->kap * 16) + a256(size_t(n_items) * 4);
+  return stage + size_t(n_items) * item_bytes(z->n, ld, z->kap, o.precision) + 4096;
+}
+
+// One LIZ, all energies; workspace already validated.  tau_dev/status_dev are
+// device pointers to [n_out][nE][kap][kap] / [n_out][nE] (status may be NULL).
+static must_status solve_one(const must_liz* z, int nE, const double2* E_dev, const double2* tinv_dev,
+                             int n_species, int nspin, const must_solve_opts& o, char* ws, size_t ws_left,
+                             double2* tau_dev, int* status_dev, cudaStream_t st) {
+  const int n = z->n, ld = ld_of(n), kap = z->kap, r = n - kap;
+  const int ipe = z->canted ? 1 : nspin;
+  const size_t per = item_bytes(n, ld, kap, o.precision);
+  int nEc = int(std::min<size_t>(size_t(nE), ws_left / (per * ipe)));
+  if (nEc < 1) {
+    must_set_error("workspace too small: need at least %zu bytes for one energy", per * ipe);
+    return MUST_ENOMEM;
+  }
+  const int max_items = nEc * ipe;
+  // carve
+  char* cur = ws;
+  double2* M64 = reinterpret_cast<double2*>(cur);
+  const size_t stride = size_t(ld) * n;
+  cur += a256(size_t(max_items) * stride * 16);
+  int* piv = reinterpret_cast<int*>(cur);
+  cur += a256(size_t(max_items) * n * 4);
+  int* st_item = reinterpret_cast<int*>(cur);
+  cur += a256(size_t(max_items) * 4);
+  int* out_index = reinterpret_cast<int*>(cur);
+  cur += a256(size_t(max_items) * 4);
+  double* scale64 = reinterpret_cast<double*>(cur);
+  cur += a256(size_t(max_items) * n * 8);
+  char* mixed_ws = cur;
+  const size_t mixed_bytes = (o.precision != MUST_FP64) ? size_t(max_items) * mixed_item_bytes(n, ld, kap) : 0;
+  if (size_t(cur - ws) + mixed_bytes > ws_left) {
+    must_set_error("workspace layout overflow");
+    return MUST_ENOMEM;
+  }
+  for (int e0 = 0; e0 < nE; e0 += nEc) {
+    const int ne = std::min(nEc, nE - e0);
+    const int items = ne * ipe;
+    launch_chunk_index(out_index, st_item, items, ne, nE, e0, z->canted, st);
+    AsmChunk c;
+    c.liz = z; c.e0 = e0; c.nEc = ne; c.nE = nE; c.nspin = nspin; c.n_species = n_species;
+    c.E = E_dev; c.tinv = tinv_dev; c.M64 = M64; c.ld = ld; c.stride = stride;
+    if (o.precision == MUST_FP64) {
+      c.M32 = nullptr;
+      c.scale = o.equilibrate ? scale64 : nullptr;
+      c.scale64 = o.equilibrate ? 1 : 0;
+      launch_assemble_chunk(c, st);
+      lu64_factor(M64, stride, ld, n, r, items, 32, piv, st_item, st);
+      schur_inv64(M64, stride, ld, n, kap, items, c.scale, tau_dev, out_index, st_item, status_dev, st);
+    } else {
+      c.scale64 = 0;
+      MixedChunk mc;
+      mc.asmc = c; mc.n = n; mc.ld = ld; mc.kap = kap; mc.items = items; mc.M64 = M64; mc.stride = stride;
+      mc.piv = piv; mc.status = st_item; mc.out_index = out_index; mc.tau = tau_dev; mc.status_out = status_dev;
+      mc.ws = mixed_ws; mc.opts = o;
+      must_status s = mixed_solve_chunk(mc, st);
+      if (s != MUST_OK) return s;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { must_set_error("kernel launch failed: %s", cudaGetErrorString(e)); return MUST_ECUDA; }
+  }
+  return MUST_OK;
+}
+
+static must_status solve_common(int n_liz, const must_liz* const* lizs, int nE, const double* E, const double* tinv,
+                                int n_species, int nspin, const must_solve_opts* opts, void* workspace,
+                                size_t ws_bytes, double* tau00, int32_t* status, void* stream) {
+  if (n_liz < 1 || !lizs || nE < 1 || !E || !tinv || !tau00 || !workspace) {
+    must_set_error("must_tau00_solve: NULL argument or empty size");
+    return MUST_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) { must_set_error("workspace not 256-byte aligned"); return MUST_EINVAL; }
+  if (n_species < 1 || nspin < 1 || nspin > 2) { must_set_error("n_species/nspin out of range"); return MUST_EINVAL; }
+  must_solve_opts o;
+  must_default_opts(&o);
+  if (opts) o = *opts;
+  if (!check_opts(&o)) { must_set_error("invalid must_solve_opts"); return MUST_EINVAL; }
+  const int lmax = lizs[0]->lmax, canted = lizs[0]->canted, kap = lizs[0]->kap;
+  for (int i = 0; i < n_liz; ++i) {
+    if (!lizs[i]) { must_set_error("NULL handle"); return MUST_EINVAL; }
+    if (lizs[i]->lmax != lmax || lizs[i]->canted != canted) { must_set_error("handles differ in lmax/canting"); return MUST_EINVAL; }
+    for (int p = 0; p < lizs[i]->N; ++p)
+      if (lizs[i]->h_species_perm[p] >= n_species) { must_set_error("species index >= n_species"); return MUST_EINVAL; }
+  }
+  if (canted && nspin != 2) { must_set_error("canted handles need nspin == 2"); return MUST_EINVAL; }
+  if (!must_is_device_ptr(workspace)) { must_set_error("workspace must be device memory"); return MUST_EINVAL; }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int n_out = canted ? 1 : nspin;
+  const bool dE = must_is_device_ptr(E), dT = must_is_device_ptr(tinv), dTau = must_is_device_ptr(tau00);
+  const bool dSt = status ? must_is_device_ptr(status) : true;
+  // staging region
+  char* ws = static_cast<char*>(workspace);
+  char* cur = ws;
+  const size_t bE = size_t(nE) * 16, bT = size_t(nspin) * n_species * nE * (lmax + 1) * 16;
+  const size_t bTau = size_t(n_liz) * n_out * nE * kap * kap * 16, bSt = size_t(n_liz) * n_out * nE * 4;
+  size_t stage = (dE ? 0 : a256(bE)) + (dT ? 0 : a256(bT)) + (dTau ? 0 : a256(bTau)) + (dSt ? 0 : a256(bSt));
+  if (stage >= ws_bytes) { must_set_error("workspace too small for staging (%zu bytes)", stage); return MUST_ENOMEM; }
+  const double2* Ed = reinterpret_cast<const double2*>(E);
+  const double2* Td = reinterpret_cast<const double2*>(tinv);
+  double2* Taud = reinterpret_cast<double2*>(tau00);
+  int* Std = status;
+#define TRYC(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { must_set_error("%s: %s", #x, cudaGetErrorString(e_)); return MUST_ECUDA; } } while (0)
+  if (!dE) { TRYC(cudaMemcpyAsync(cur, E, bE, cudaMemcpyHostToDevice, st)); Ed = reinterpret_cast<double2*>(cur); cur += a256(bE); }
+  if (!dT) { TRYC(cudaMemcpyAsync(cur, tinv, bT, cudaMemcpyHostToDevice, st)); Td = reinterpret_cast<double2*>(cur); cur += a256(bT); }
+  if (!dTau) { Taud = reinterpret_cast<double2*>(cur); cur += a256(bTau); }
+  if (!dSt) { Std = reinterpret_cast<int*>(cur); cur += a256(bSt); }
+  const size_t left = ws_bytes - size_t(cur - ws);
+  for (int i = 0; i < n_liz; ++i) {
+    const size_t tau_off = size_t(i) * n_out * nE * kap * kap;
+    const size_t st_off = size_t(i) * n_out * nE;
+    must_status s = solve_one(lizs[i], nE, Ed, Td, n_species, nspin, o, cur, left, Taud + tau_off,
+                              Std ? Std + st_off : nullptr, st);
+    if (s != MUST_OK) return s;
+  }
+  if (!dTau) TRYC(cudaMemcpyAsync(tau00, Taud, bTau, cudaMemcpyDeviceToHost, st));
+  if (!dSt && status) TRYC(cudaMemcpyAsync(status, Std, bSt, cudaMemcpyDeviceToHost, st));
+  if (!dTau || (!dSt && status)) TRYC(cudaStreamSynchronize(st));
+#undef TRYC
+  return MUST_OK;
+}
+
+extern "C" must_status must_tau00_solve(const must_liz* liz, int32_t nE, const double* E, const double* tinv,
+                                        int32_t n_species, int32_t nspin, const must_solve_opts* opts,
+                                        void* workspace, size_t ws_bytes, double* tau00, int32_t* status,
+                                        void* stream) {
+  if (!liz) { must_set_error("must_tau00_solve: NULL handle"); return MUST_EINVAL; }
+  const must_liz* arr[1] = {liz};
+  return solve_common(1, arr, nE, E, tinv, n_species, nspin, opts, workspace, ws_bytes, tau00, status, stream);
+}
+
+extern "C" must_status must_tau00_batch(int32_t n_liz, const must_liz* const* lizs, int32_t nE, const double* E,
+                                        const double* tinv, int32_t n_species, int32_t nspin,
+                                        const must_solve_opts* opts, void* workspace, size_t ws_bytes,
+                                        double* tau00, int32_t* status, void* stream) {
+  return solve_common(n_liz, lizs, nE, E, tinv, n_species, nspin, opts, workspace, ws_bytes, tau00, status, stream);
+}
+
+extern "C" size_t must_batch_workspace_bytes(int32_t n_liz, const must_liz* const* lizs, int32_t n_items_per_liz,
+                                             const must_solve_opts* opts) {
+  size_t mx = 0;
+  for (int i = 0; i < n_liz; ++i) mx = std::max(mx, must_workspace_bytes(lizs[i], n_items_per_liz, opts));
+  // staging for every LIZ's outputs
+  const int kap = n_liz > 0 ? lizs[0]->kap : 0;
+  return mx + a256(size_t(n_liz) * n_items_per_liz * kap * kap * 16) + a256(size_t(n_liz) * n_items_per_liz * 4);
+}
+
+__global__ void chunk_index_kernel(int* out_index, int* status, int items, int ne, int nE, int e0, int canted) {
+  const int it = blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= items) return;
+  const int el = canted ? it : it % ne;
+  const int s = canted ? 0 : it / ne;
+  out_index[it] = s * nE + e0 + el;
+  status[it] = 0;
+}
+
+void launch_chunk_index(int* out_index, int* status, int items, int ne, int nE, int e0, int canted, cudaStream_t st) {
+  chunk_index_kernel<<<(items + 127) / 128, 128, 0, st>>>(out_index, status, items, ne, nE, e0, canted);
+}

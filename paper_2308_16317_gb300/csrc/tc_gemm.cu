@@ -1,0 +1,433 @@
+// Tensor-core trailing update of the mixed-precision elimination,
+//   A22 -= L21 U12   (complex FP32 storage, column-major),
+// on the 5th-generation tensor cores: tcgen05.mma with operands staged in
+// shared memory by TMA (cp.async.bulk.tensor, 128-byte swizzle) and FP32
+// accumulators in tensor memory, read back with tcgen05.ld for the epilogue.
+//
+// Complex -> real block form, row-interleaved so the epilogue is coalesced:
+//   A'[2i]   = [Lr(i,p), -Li(i,p)]_p     A'[2i+1] = [Li(i,p), Lr(i,p)]_p
+//   B'[j]    = [Ur(p,j),  Ui(p,j)]_p     (K index 2p, 2p+1)
+//   C'[2i][j] = Re(L U)(i,j),  C'[2i+1][j] = Im(L U)(i,j).
+// Split products (Henry, Tang & Heinecke, ARITH 2019 for BF16; the same
+// three-term scheme with TF32 halves): x = x_hi + x_lo, and
+//   A'B'^T ~ A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
+// accumulated in one FP32 TMEM accumulator (the lo*lo term is dropped).
+//
+// One CTA (128 threads) computes a 128 x BN tile of C' (64 complex rows x BN
+// complex columns): warp 0 lane 0 issues TMA loads into a STAGES-deep ring,
+// warp 1 lane 0 issues the MMAs (one per 32 bytes of K), and all four warps
+// read their 32 TMEM lanes and update C in place.  Every mbarrier wait is
+// bounded; on time-out the kernel raises the workspace error word, drains its
+// own copies, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cstdio>
+#include <mutex>
+
+#include "tc_gemm.h"
+
+namespace {
+
+constexpr int BM = 128;                // real rows per tile (= TMEM lanes)
+constexpr int KB = 128;                // bytes of K per stage (one swizzle row)
+constexpr int PANEL_NB = 64;           // complex panel width of the mixed path
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s bound on any wait
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  if (mbar_try(b, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try(b, parity)) return true;
+    if (gtimer() - t0 > WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
+// 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) | (uint64_t(1) << 46) |
+         (uint64_t(2) << 61);
+}
+
+__device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc,
+                                          int kind_tf32) {
+  if (kind_tf32)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcParams {
+  float2* C;
+  size_t stride;
+  int ld, n;
+  int base;      // first trailing row/column (k0 + nbe)
+  int ksteps;    // K stages per split pass
+  int* err;      // workspace error word
+  int tf32;
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(128, 1)
+    tc_update_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+                     const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
+                     TcParams P) {
+  constexpr int A_BYTES = BM * KB;          // 16 KB
+  constexpr int B_BYTES = BN * KB;
+  constexpr int ST_BYTES = A_BYTES + B_BYTES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[STAGES];
+  __shared__ __align__(8) uint64_t empty[STAGES];
+  __shared__ __align__(8) uint64_t done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.z;
+  const int row0 = blockIdx.x * BM;     // real rows of C' relative to the trailing block
+  const int col0 = blockIdx.y * BN;     // complex columns relative to the trailing block
+  const int nsteps = 3 * P.ksteps;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  int issued = 0;   // producer: TMA stages issued
+  if (warp == 0 && lane == 0) {
+    const int kstep_elems = P.tf32 ? KB / 4 : KB / 2;
+    for (int step = 0; step < nsteps; ++step) {
+      const int s = step % STAGES;
+      const uint32_t ph = (step / STAGES) & 1;
+      if (step >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) { s_fail = 1; break; }
+      const int pass = step / P.ksteps, kb = step % P.ksteps;
+      const CUtensorMap* ma = (pass == 2) ? &tA_lo : &tA_hi;
+      const CUtensorMap* mb = (pass == 1) ? &tB_lo : &tB_hi;
+      uint8_t* sa = smem + s * ST_BYTES;
+      mbar_expect_tx(&full[s], ST_BYTES);
+      tma_load_3d(sa, ma, kb * kstep_elems, 2 * P.base + row0, item, &full[s]);
+      tma_load_3d(sa + A_BYTES, mb, kb * kstep_elems, P.base + col0, item, &full[s]);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // instruction descriptor: D F32, A/B BF16 (f16 kind) or TF32, K-major, N, M
+    const uint32_t fmt = P.tf32 ? 2u : 1u;
+    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+    bool ok = true;
+    for (int step = 0; step < nsteps && ok; ++step) {
+      const int s = step % STAGES;
+      const uint32_t ph = (step / STAGES) & 1;
+      if (!mbar_wait(&full[s], ph)) { ok = false; s_fail = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(smem + s * ST_BYTES), b0 = a0 + A_BYTES;
+#pragma unroll
+      for (int k = 0; k < KB / 32; ++k)
+        mma_issue(tmem, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, (step > 0 || k > 0) ? 1u : 0u, P.tf32);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(&done);
+  }
+  __syncthreads();   // roles finished issuing (s_fail visible); the MMAs may still run
+  // epilogue: every warp waits for the accumulator
+  const bool have = mbar_wait(&done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (have && !s_fail) {
+    const int rr = row0 + warp * 32 + lane;           // real row within the trailing block
+    const int i = P.base + (rr >> 1);                  // complex row of the matrix
+    const int comp = rr & 1;
+    float* Cc = reinterpret_cast<float*>(P.C + size_t(item) * P.stride);
+    for (int cc = 0; cc < BN; cc += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + (uint32_t(warp * 32) << 16) + cc, v);
+      if (i < P.n) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = P.base + col0 + cc + j;
+          if (col < P.n) {
+            float* p = Cc + 2 * (size_t(col) * P.ld + i) + comp;
+            *p -= __uint_as_float(v[j]);
+          }
+        }
+      }
+    }
+  }
+  if (!have || s_fail) {
+    if (threadIdx.x == 0) atomicExch(P.err, 1);
+    // drain: wait (bounded) for every TMA stage this CTA armed
+    if (warp == 0 && lane == 0)
+      for (int step = (issued > STAGES ? issued - STAGES : 0); step < issued; ++step)
+        mbar_wait(&full[step % STAGES], (step / STAGES) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+}
+
+// ---------------------------------------------------------------- packing --
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16_raw& hi, __nv_bfloat16_raw& lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+  hi = static_cast<__nv_bfloat16_raw>(h);
+  lo = static_cast<__nv_bfloat16_raw>(l);
+}
+
+__device__ __forceinline__ float tf32_rna(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+// A'-pack rows 2i, 2i+1 for matrix rows i in [base, n); K = 2p, 2p+1 for
+// panel column p < nbe, zero for p in [nbe, Kp/2).  Layout [item][row][Kp].
+template <typename T>
+__global__ void pack_a_kernel(const float2* __restrict__ C0, size_t stride, int ld, int n, int k0, int nbe, int base,
+                              int Kp, int rows_pad, T* __restrict__ hi0, T* __restrict__ lo0, int tf32) {
+  const int item = blockIdx.y;
+  const int half = Kp / 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = base + t / half, p = t % half;
+  if (i >= n) return;
+  float2 v = make_float2(0.f, 0.f);
+  if (p < nbe) v = C0[size_t(item) * stride + size_t(k0 + p) * ld + i];
+  const float e[4] = {v.x, -v.y, v.y, v.x};   // row 2i: (Lr, -Li); row 2i+1: (Li, Lr)
+  T* hi = hi0 + size_t(item) * rows_pad * Kp;
+  T* lo = lo0 + size_t(item) * rows_pad * Kp;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const size_t off = size_t(2 * i + (q >> 1)) * Kp + 2 * p + (q & 1);
+    if constexpr (sizeof(T) == 2) {
+      __nv_bfloat16_raw h, l;
+      split_bf16(e[q], h, l);
+      hi[off] = *reinterpret_cast<T*>(&h);
+      lo[off] = *reinterpret_cast<T*>(&l);
+    } else {
+      const float h = tf32_rna(e[q]);
+      hi[off] = h;
+      lo[off] = tf32_rna(e[q] - h);
+    }
+  }
+}
+
+// B'-pack row j (matrix column j in [base, n)): K = 2p -> Ur(p,j), 2p+1 -> Ui(p,j).
+template <typename T>
+__global__ void pack_b_kernel(const float2* __restrict__ C0, size_t stride, int ld, int n, int k0, int nbe, int base,
+                              int Kp, int rows_pad, T* __restrict__ hi0, T* __restrict__ lo0, int tf32) {
+  const int item = blockIdx.y;
+  const int half = Kp / 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = base + t / half, p = t % half;
+  if (j >= n) return;
+  float2 v = make_float2(0.f, 0.f);
+  if (p < nbe) v = C0[size_t(item) * stride + size_t(j) * ld + k0 + p];
+  const float e[2] = {v.x, v.y};
+  T* hi = hi0 + size_t(item) * rows_pad * Kp;
+  T* lo = lo0 + size_t(item) * rows_pad * Kp;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const size_t off = size_t(j) * Kp + 2 * p + q;
+    if constexpr (sizeof(T) == 2) {
+      __nv_bfloat16_raw h, l;
+      split_bf16(e[q], h, l);
+      hi[off] = *reinterpret_cast<T*>(&h);
+      lo[off] = *reinterpret_cast<T*>(&l);
+    } else {
+      const float h = tf32_rna(e[q]);
+      hi[off] = h;
+      lo[off] = tf32_rna(e[q] - h);
+    }
+  }
+}
+
+// ------------------------------------------------------------- host side --
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool get_encoder() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  return g_encode != nullptr;
+}
+
+bool make_map(CUtensorMap* m, void* base, bool tf32, int Kp, int rows, int items, int box_rows) {
+  const int es = tf32 ? 4 : 2;
+  cuuint64_t dims[3] = {cuuint64_t(Kp), cuuint64_t(rows), cuuint64_t(items)};
+  cuuint64_t strides[2] = {cuuint64_t(Kp) * es, cuuint64_t(Kp) * es * rows};
+  cuuint32_t box[3] = {cuuint32_t(KB / es), cuuint32_t(box_rows), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+constexpr int TC_BN = 128;
+constexpr int TC_STAGES = 3;
+
+int kp_of(bool tf32) {
+  // K elements per pass padded to whole 128-byte stages
+  const int per = tf32 ? KB / 4 : KB / 2;
+  return ((2 * PANEL_NB + per - 1) / per) * per;
+}
+
+}  // namespace
+
+int tc_panel_width(int) { return PANEL_NB; }
+
+size_t tc_pack_bytes_per_item(int n) {
+  const int rows_pad = 2 * ((n + 127) / 128) * 128;
+  const size_t kp = size_t(kp_of(true));   // 4-byte elements: the larger of the two
+  return 4 * a256(size_t(rows_pad) * kp * 4);
+}
+
+static bool tc_supported = true;
+
+bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items,
+                        char* packs, int* err, cudaStream_t st) {
+  const bool tf32 = (precision == MUST_MIXED_TF32X3);
+  if (!get_encoder()) {
+    must_set_error("cuTensorMapEncodeTiled is not available");
+    return false;
+  }
+  const int base = k0 + nbe;
+  const int m = n - base;
+  if (m <= 0) return true;
+  const int rows_pad = 2 * ((n + 127) / 128) * 128;   // A' rows (2n padded); B' uses the first n_pad rows
+  const int Kp = kp_of(tf32);
+  const int es = tf32 ? 4 : 2;
+  const size_t pbytes = a256(size_t(rows_pad) * Kp * 4);   // slot size (fits either precision)
+  char* pa_hi = packs;
+  char* pa_lo = packs + size_t(items) * pbytes;
+  char* pb_hi = packs + 2 * size_t(items) * pbytes;
+  char* pb_lo = packs + 3 * size_t(items) * pbytes;
+  // item stride inside a slot group = pbytes; tensor maps use rows_pad rows per item
+  const int item_rows = int(pbytes / (size_t(Kp) * es));
+  {
+    const int half = Kp / 2;
+    const int ta = m * half;
+    dim3 g((ta + 255) / 256, items);
+    if (tf32) {
+      pack_a_kernel<float><<<g, 256, 0, st>>>(A, stride, ld, n, k0, nbe, base, Kp, item_rows,
+                                              reinterpret_cast<float*>(pa_hi), reinterpret_cast<float*>(pa_lo), 1);
+      pack_b_kernel<float><<<g, 256, 0, st>>>(A, stride, ld, n, k0, nbe, base, Kp, item_rows,
+                                              reinterpret_cast<float*>(pb_hi), reinterpret_cast<float*>(pb_lo), 1);
+    } else {
+      pack_a_kernel<uint16_t><<<g, 256, 0, st>>>(A, stride, ld, n, k0, nbe, base, Kp, item_rows,
+                                                 reinterpret_cast<uint16_t*>(pa_hi), reinterpret_cast<uint16_t*>(pa_lo),
+                                                 0);
+      pack_b_kernel<uint16_t><<<g, 256, 0, st>>>(A, stride, ld, n, k0, nbe, base, Kp, item_rows,
+                                                 reinterpret_cast<uint16_t*>(pb_hi), reinterpret_cast<uint16_t*>(pb_lo),
+                                                 0);
+    }
+  }
+  CUtensorMap mah, mal, mbh, mbl;
+  if (!make_map(&mah, pa_hi, tf32, Kp, item_rows, items, BM) || !make_map(&mal, pa_lo, tf32, Kp, item_rows, items, BM) ||
+      !make_map(&mbh, pb_hi, tf32, Kp, item_rows, items, TC_BN) ||
+      !make_map(&mbl, pb_lo, tf32, Kp, item_rows, items, TC_BN)) {
+    must_set_error("tensor map encoding failed");
+    return false;
+  }
+  TcParams P;
+  P.C = A;
+  P.stride = stride;
+  P.ld = ld;
+  P.n = n;
+  P.base = base;
+  P.ksteps = Kp * es / KB;
+  P.err = err;
+  P.tf32 = tf32 ? 1 : 0;
+  constexpr size_t smem = size_t(TC_STAGES) * (BM * KB + TC_BN * KB) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_update_kernel<TC_BN, TC_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    attr = true;
+  }
+  dim3 grid((2 * m + BM - 1) / BM, (m + TC_BN - 1) / TC_BN, items);
+  tc_update_kernel<TC_BN, TC_STAGES><<<grid, 128, smem, st>>>(mah, mal, mbh, mbl, P);
+  return true;
+}

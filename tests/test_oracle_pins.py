@@ -48,6 +48,21 @@ def test_bessel_wronskian_and_hankel0(orc, z):
     assert abs(h0 - (-1j * np.exp(1j * z) / z)) < 1e-14 * abs(h0)
 
 
+@pytest.mark.parametrize("z", [0.06 + 7.26j, 0.004 + 2.74j, 1.3 + 0.2j, 9.5 + 0.3j, 0.02 + 13.0j, 0.4 + 0.05j])
+def test_hankel_closed_form_against_mpmath(orc, z):
+    """h_l = j_l + i y_l against 40-digit mpmath, including arguments with a
+    large imaginary part (kappa |R| near the bottom of the contour), where
+    forming j_l + i y_l in double precision cancels catastrophically."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    zz = mp.mpc(z.real, z.imag)
+    _, _, h = orc.sph_jyh(8, z)
+    for l in range(9):
+        f = mp.sqrt(mp.pi / (2 * zz))
+        ref = complex(f * (mp.besselj(l + 0.5, zz) + 1j * mp.bessely(l + 0.5, zz)))
+        assert abs(h[l] - ref) <= 1e-14 * abs(ref), (l, h[l], ref)
+
+
 # ---------------------------------------------------- real harmonics -------
 
 def test_real_ylm_closed_forms(orc):
@@ -166,7 +181,7 @@ def _jY(orc, lmax, kap, v):
     return j[l_of_L(lmax)] * orc.real_ylm(lmax, v)
 
 
-@pytest.mark.parametrize("E", [0.3 + 0.2j, -0.25 + 0.01j, 0.6 + 0.4j])
+@pytest.mark.parametrize("E", [0.3 + 0.2j, -0.25 + 0.01j, 0.6 + 0.4j, -0.3 + 0.005j])
 def test_two_centre_expansion_reproduces_free_green_function(orc, E):
     """g0(x, x') = -exp(i k |x-x'|) / (4 pi |x-x'|) must equal
     sum_LL' j_l(k r) Y_L(r^) G^{ij}_LL' j_l'(k r') Y_L'(r'^) for x = r + R_i,
