@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the LSMS tau_00 hot path on GB300.
+
+One step = every (energy, spin) tau_00 of a 135-site fcc LIZ at lmax = 3
+(n = 2160): 32 contour energies x 2 spins = 64 solves, each covering device
+assembly of M = t^{-1} - g0, elimination of the leading n - 16 columns and
+tau_00 (plus FP64 refinement on the mixed path).  Prints one JSON line.
+
+  python bench.py [--gpus N --steps K --warmup W] [--precision bf16x3|tf32x3|fp64]
+  python bench.py --impl reference ...   (the CPU oracle on the host cores)
+
+Multi-GPU (torchrun): every rank solves its own LIZ (independent problems,
+weak scaling, no collective on the data path); the barrier and the max over
+ranks are for timing only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "τ_00 solves/sec at N_LIZ=135,l_max=3 (n=2160) vs plain FP64; % tensor peak"
+UNIT = "solves/s"
+PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
+FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (profiling recipe); DFMA/DMMA microbenchmark: 1.01-1.05
+FP32_PEAK_TFLOPS = 80.5      # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (measured FFMA: 75)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=5)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def traffic_from_profiles(kernel_key: str, source: str):
+    """DRAM bytes per launch recorded in profiles/<kernel_key>.txt, if the kernel
+    source it was captured from is unchanged (sha256 line); else None."""
+    path = os.path.join(ROOT, "profiles", kernel_key + ".txt")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+    vals = {}
+    for ln in open(path):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def phase_work(phase: str, n: int, kap: int, nb: int, items: int, precision: str):
+    """Algorithmic work of `items` matrices in one phase of one step:
+    (amount, unit, bound, kernel source, profile key)."""
+    r = n - kap
+    if phase == "trailing_update":
+        # complex MACs of A22 -= L21 U12 over all panels; tensor flops = 24 per
+        # complex MAC for the 3-term split (4 real MACs x 3 products x 2)
+        macs = 0
+        for k0 in range(0, r, nb):
+            nbe = min(nb, r - k0)
+            m = n - k0 - nbe
+            macs += m * m * nbe
+        per = 24 if precision != "fp64" else 8
+        return macs * per * items, "flop", "tensor" if precision != "fp64" else "alu", \
+            "paper_2308_16317_gb300/csrc/tc_gemm.cu" if precision != "fp64" else \
+            "paper_2308_16317_gb300/csrc/lu64.cu", "tc_update_kernel_fcc135"
+    if phase == "residual":
+        return 8.0 * n * n * kap * items, "flop", "alu", "paper_2308_16317_gb300/csrc/mixed.cu", \
+            "residual64_kernel_fcc135"
+    if phase == "correction":
+        return 8.0 * n * n * kap * items, "flop", "alu", "paper_2308_16317_gb300/csrc/mixed.cu", \
+            "correct_kernel_fcc135"
+    if phase == "assemble":
+        bpe = 16 + (8 if precision != "fp64" else 0)
+        return float(n) * n * bpe * items, "byte", "hbm", "paper_2308_16317_gb300/csrc/assemble.cu", \
+            "assemble_kernel_fcc135"
+    if phase == "panel":
+        fl = 0
+        for k0 in range(0, r, nb):
+            nbe = min(nb, r - k0)
+            fl += 8 * (n - k0) * nbe * nbe / 2
+        return fl * items, "flop", "alu", "paper_2308_16317_gb300/csrc/mixed.cu", "panel32_kernel_fcc135"
+    return None
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2308_16317_gb300 import binding as B
+    from paper_2308_16317_gb300 import build as libbuild
+    from paper_2308_16317_gb300 import workload as wl
+    from paper_2308_16317_gb300.runner import Session, blocks_to_numpy
+    libbuild.build()
+    B.load()
+    w = wl.liz135(seed=wl.SEED_BASE + 2 + rank)
+    s = Session(w, device="cuda:%d" % local)
+    n, kap = s.lizs[0].n, s.kap
+    items = len(w.energies) * s.nspin
+    prec = args.precision
+    opts = B.must_default_opts(PREC[prec])
+    nb = 64 if prec != "fp64" else 32
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream(dev)
+    out = s.alloc_out(1)
+    for _ in range(args.warmup):
+        s.solve(opts, out=out)
+    torch.cuda.synchronize(dev)
+    st0 = out[1].cpu().numpy()
+
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    B.must_profile_enable(True)
+    B.must_profile_read()
+    l0 = B.must_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.solve(opts, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    l1 = B.must_launch_count()
+    prof = B.must_profile_read()
+    B.must_profile_enable(False)
+    clocks = sampler.stop() if rank == 0 else None
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    ms_step = ms_total / args.steps
+    value = items * ws * args.steps / (ms_total / 1e3)
+    tau_fast = blocks_to_numpy(out[0][0])
+    status = out[1].cpu().numpy()
+
+    # roofline of the dominant phase (largest measured share of the step)
+    peaks, peak_kind = load_peaks()
+    dom = max((k for k in prof if k not in ("other",)), key=lambda k: prof[k][0])
+    roofline = None
+    pw = phase_work(dom, n, kap, nb, 1, prec)
+    if pw is not None:
+        per_item, unit, bound, src, key = pw
+        ms_d, launches_d, items_d = prof[dom]
+        if dom in ("residual", "correction"):
+            total = per_item * items_d                      # items actually processed (device counted)
+        else:
+            total = per_item * items * args.steps           # whole-step work of this phase
+        achieved = total / (ms_d / 1e3)
+        if bound == "tensor":
+            peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")) * 1e12
+            punit, scale = "TFLOP/s", 1e12
+        elif bound == "hbm":
+            peak = peaks["hbm_gbs"] * 1e9
+            punit, scale = "GB/s", 1e9
+        else:
+            peak = (FP64_PEAK_TFLOPS if dom == "residual" or prec == "fp64" else FP32_PEAK_TFLOPS) * 1e12
+            punit, scale = "TFLOP/s", 1e12
+        traffic = traffic_from_profiles(key, src)
+        roofline = {"kernel_phase": dom, "bound": bound, "achieved": achieved / scale, "peak": peak / scale,
+                    "unit": punit, "frac": achieved / peak, "traffic": traffic,
+                    "peak_source": (peak_kind + " (MEASURED_PEAKS)") if bound in ("tensor", "hbm")
+                    else "nominal FP64/FP32 from unit counts and clocks",
+                    "algorithmic_per_launch": total / max(launches_d, 1),
+                    "avg_launch_ms": ms_d / max(launches_d, 1), "launches": launches_d,
+                    "share_of_step": ms_d / (ms_total if ws == 1 else ms_total)}
+    phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+              for k, v in prof.items() if v[1] > 0}
+
+    # plain FP64 path on the same workload (the comparison the metric names)
+    fp64 = None
+    max_err = None
+    if prec != "fp64" and args.fp64_steps > 0:
+        o64 = B.must_default_opts(0)
+        out64 = s.alloc_out(1)
+        s.solve(o64, out=out64)
+        torch.cuda.synchronize(dev)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            s.solve(o64, out=out64)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        fms = max_over_ranks(f0.elapsed_time(f1)) / args.fp64_steps
+        fp64 = {"value": items * ws / (fms / 1e3), "ms_per_step": fms}
+        t64 = blocks_to_numpy(out64[0][0])
+        max_err = float((np.linalg.norm(tau_fast - t64, axis=(-2, -1)) / np.linalg.norm(t64, axis=(-2, -1))).max())
+
+    # end to end through the C ABI with pinned host buffers
+    E_h = torch.tensor(np.asarray(w.energies), dtype=torch.complex128).pin_memory()
+    T_h = s.tinv.cpu().pin_memory()
+    tau_h = torch.empty((s.n_out, len(w.energies), kap, kap), dtype=torch.complex128).pin_memory()
+    sta_h = torch.empty((s.n_out, len(w.energies)), dtype=torch.int32).pin_memory()
+    wsb = B.must_workspace_bytes(s.lizs[0], items, opts)
+    wsp = s.workspace(wsb)
+    B.must_tau00_solve(s.lizs[0], E_h, T_h, s.n_species, s.nspin, opts, wsp, wsb, tau_h, sta_h)
+    barrier()
+    t0 = time.perf_counter()
+    e_steps = max(1, min(args.steps, 5))
+    for _ in range(e_steps):
+        B.must_tau00_solve(s.lizs[0], E_h, T_h, s.n_species, s.nspin, opts, wsp, wsb, tau_h, sta_h)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": items * ws * e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(E_h.numel() * 16 + T_h.numel() * 16),
+           "d2h_bytes_per_step": int(tau_h.numel() * 16 + sta_h.numel() * 4)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_sample)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"bf16x3": "bf16x3+f32, f64 refinement", "tf32x3": "tf32x3+f32, f64 refinement",
+                                           "fp64": "f64"}[prec],
+            "data": "synthetic (seeded fcc 50/50 random alloy, square-well t-matrices)",
+            "config": {"workload": "fcc135 LIZ, lmax=3, n=2160, 32 contour energies x 2 spins = 64 tau_00 solves/step",
+                       "n": n, "n_liz": int(w.lizs[0].n_sites), "lmax": w.lmax, "solves_per_step": items,
+                       "precision": prec, "l2": "inputs larger than L2 (%.1f GB of matrices per step)" % (
+                           items * n * n * (24 if prec != "fp64" else 16) / 1e9)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(l1 - l0),
+            "clocks": clocks, "plain_fp64": fp64, "max_rel_err_vs_fp64": max_err,
+            "status_ok": bool((status == 0).all() and (st0 == 0).all()), "phases": phases,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, sample: int):
+    """The oracle on the host cores: `sample` (energy, spin) solves of the same
+    LIZ, one per thread, timed end to end."""
+    import oracle
+    oracle.build()
+    cores = sample if sample > 0 else min(16, os.cpu_count() or 1)
+    nE = len(w.energies)
+    items = [((k % 2), (k * 7) % nE) for k in range(cores)]
+    liz = w.lizs[0]
+    E = np.array([w.energies[e] for _, e in items])
+    ti = np.array([oracle.site_tinv(w.lmax, w.energies[e], w.site_depths(liz, s), w.r_mt) for s, e in items])
+    t0 = time.perf_counter()
+    _, _, used = oracle.tau00_batch(liz.pos, w.lmax, E, ti, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": len(items) / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
+            "sample": "%d of the 64 (energy, spin) solves of the n=2160 LIZ, one per thread, %.1f s" % (len(items), dt)}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2308_16317_gb300 import workload as wl
+    w = wl.liz135()
+    cores = args.cpu_sample if args.cpu_sample > 0 else min(16, os.cpu_count() or 1)
+    for _ in range(args.warmup):
+        cpu_baseline(w, max(1, cores // 4))
+    times = []
+    solves = 0
+    for _ in range(args.steps):
+        c = cpu_baseline(w, cores)
+        solves += cores
+        times.append(cores / c["value"])
+    total = sum(times)
+    value = solves / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded fcc 50/50 random alloy, square-well t-matrices)",
+            "config": {"workload": "fcc135 LIZ, lmax=3, n=2160, 32 contour energies x 2 spins = 64 tau_00 solves/step",
+                       "n": 2160, "n_liz": 135, "lmax": 3, "solves_per_step": cores,
+                       "note": "each step is a bounded sample: %d solves, one per host thread" % cores},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d steps x %d solves of the n=2160 LIZ" % (args.steps, cores)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -151,6 +151,23 @@ must_status must_tau00_batch(int32_t n_liz, const must_liz* const* lizs, int32_t
 size_t must_batch_workspace_bytes(int32_t n_liz, const must_liz* const* lizs, int32_t n_items_per_liz,
                                   const must_solve_opts* opts);
 
+/*
+ * Instrumentation (not part of the paper's method).  When enabled, CUDA
+ * events are recorded on the launching stream around each phase of the path
+ * (0 assemble, 1 panel, 2 row_swap, 3 trsm, 4 pack, 5 trailing_update,
+ * 6 schur_inverse, 7 residual, 8 correction, 9 other).  must_profile_read
+ * waits for the recorded events (it synchronises the device), writes per
+ * phase the summed milliseconds, the kernel launches and the matrix items
+ * those launches processed (the refinement phases count only items that were
+ * not yet converged) into ms / launches / items [n_phases] (any may be
+ * NULL), clears them and returns the number of phases.  must_launch_count
+ * returns the number of kernels this library has launched in the process.
+ */
+void must_profile_enable(int on);
+int must_profile_read(double* ms, long long* launches, long long* items, int n_phases);
+long long must_launch_count(void);
+const char* must_phase_name(int phase);
+
 const char* must_status_string(must_status s);
 /* Message for the last non-OK status returned on the calling thread. */
 const char* must_last_error(void);

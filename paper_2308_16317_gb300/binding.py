@@ -53,6 +53,10 @@ def load():
         "must_tinv_square_well": (I32, [I32, P, I32, P, D, I32, P, P]),
         "must_tau00_solve": (I32, [P, I32, P, P, I32, I32, ctypes.POINTER(must_solve_opts), P, SZ, P, P, P]),
         "must_tau00_batch": (I32, [I32, P, I32, P, P, I32, I32, ctypes.POINTER(must_solve_opts), P, SZ, P, P, P]),
+        "must_profile_enable": (None, [ctypes.c_int]),
+        "must_profile_read": (ctypes.c_int, [P, P, P, ctypes.c_int]),
+        "must_launch_count": (ctypes.c_longlong, []),
+        "must_phase_name": (ctypes.c_char_p, [ctypes.c_int]),
         "must_status_string": (ctypes.c_char_p, [I32]),
         "must_last_error": (ctypes.c_char_p, []),
     }
@@ -67,7 +71,8 @@ def load():
 def exported_symbols():
     return [n for n in ("must_default_opts", "must_liz_build", "must_liz_free", "must_liz_order", "must_liz_kappa",
                         "must_workspace_bytes", "must_batch_workspace_bytes", "must_tinv_square_well",
-                        "must_tau00_solve", "must_tau00_batch", "must_status_string", "must_last_error")]
+                        "must_tau00_solve", "must_tau00_batch", "must_status_string", "must_last_error",
+                        "must_profile_enable", "must_profile_read", "must_launch_count", "must_phase_name")]
 
 
 def _ptr(a):
@@ -101,6 +106,25 @@ def _stream(stream):
 def _check(code: int):
     if code != 0:
         raise MustError(code, load().must_last_error().decode(errors="replace"))
+
+
+def must_profile_enable(on: bool):
+    load().must_profile_enable(1 if on else 0)
+
+
+def must_profile_read():
+    """{phase name: (milliseconds, launches, items)} since the last read."""
+    n = 16
+    ms = (ctypes.c_double * n)()
+    la = (ctypes.c_longlong * n)()
+    it = (ctypes.c_longlong * n)()
+    k = load().must_profile_read(ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(la, ctypes.c_void_p),
+                                 ctypes.cast(it, ctypes.c_void_p), n)
+    return {load().must_phase_name(p).decode(): (ms[p], la[p], it[p]) for p in range(k)}
+
+
+def must_launch_count() -> int:
+    return int(load().must_launch_count())
 
 
 def must_default_opts(precision: int = MUST_FP64, **kw) -> must_solve_opts:

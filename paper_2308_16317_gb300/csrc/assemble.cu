@@ -16,6 +16,7 @@
 //                   rows.
 #include "common.cuh"
 #include "solver.h"
+#include "prof.h"
 
 namespace {
 
@@ -330,23 +331,32 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
 void launch_geom(int N, int lmax, const double* pos_perm, const int2* pq, int n_pairs, double* d, double* Y,
                  cudaStream_t st) {
   const int l2max = 2 * lmax, nL2 = (l2max + 1) * (l2max + 1);
-  if (n_pairs > 0) geom_kernel<<<(n_pairs + 127) / 128, 128, 0, st>>>(N, nL2, l2max, pos_perm, pq, n_pairs, d, Y);
+  if (n_pairs > 0) {
+    geom_kernel<<<(n_pairs + 127) / 128, 128, 0, st>>>(N, nL2, l2max, pos_perm, pq, n_pairs, d, Y);
+    prof_launched(PH_OTHER, 1);
+  }
 }
 
 void launch_tinv(int nE, const double2* E, int n_pot, const double* V, double a, int lmax, double2* out,
                  cudaStream_t st) {
   const int t = nE * n_pot;
-  if (t > 0) tinv_kernel<<<(t + 127) / 128, 128, 0, st>>>(nE, E, n_pot, V, a, lmax, out);
+  if (t > 0) {
+    tinv_kernel<<<(t + 127) / 128, 128, 0, st>>>(nE, E, n_pot, V, a, lmax, out);
+    prof_launched(PH_OTHER, 1);
+  }
 }
 
 void launch_assemble(const AsmArgs& A, cudaStream_t st) {
+  ProfScope ps(PH_ASSEMBLE, st);
   const int n_items = A.items_per_e * A.nEc;
   if (A.M32 || A.scale64) {
     dim3 g((A.n + 255) / 256, n_items);
     scale_kernel<<<g, 256, 0, st>>>(A, const_cast<double*>(A.scale));
+    prof_launched(PH_ASSEMBLE, 1);
   }
   dim3 grid((A.n_pairs + A.N + 7) / 8, A.nEc);
   assemble_kernel<<<grid, 256, 0, st>>>(A);
+  prof_launched(PH_ASSEMBLE, 1, n_items);
 }
 
 void launch_assemble_chunk(const AsmChunk& c, cudaStream_t st) {

@@ -16,6 +16,7 @@
 //                   1.05 TFLOP/s as DFMA, measured).
 //   schur_inv_kernel  tau_00 = S^{-1} by Gauss-Jordan with partial pivoting.
 #include "common.cuh"
+#include "prof.h"
 
 #define LU64_T 256
 
@@ -271,13 +272,27 @@ void lu64_factor(double2* A, size_t stride, int ld, int n, int r, int n_items, i
   }
   for (int k0 = 0; k0 < r; k0 += nb) {
     const int nbe = (r - k0 < nb) ? (r - k0) : nb;
-    panel64_kernel<<<n_items, LU64_T, 0, st>>>(A, stride, ld, n, r, k0, nbe, piv, status);
-    laswp64_kernel<<<dim3((n - nbe + 255) / 256, n_items), 256, 0, st>>>(A, stride, ld, n, r, k0, nbe, piv);
+    {
+      ProfScope ps(PH_PANEL, st);
+      panel64_kernel<<<n_items, LU64_T, 0, st>>>(A, stride, ld, n, r, k0, nbe, piv, status);
+      prof_launched(PH_PANEL, 1, n_items);
+    }
+    {
+      ProfScope ps(PH_SWAP, st);
+      laswp64_kernel<<<dim3((n - nbe + 255) / 256, n_items), 256, 0, st>>>(A, stride, ld, n, r, k0, nbe, piv);
+      prof_launched(PH_SWAP, 1, n_items);
+    }
     const int rem = n - k0 - nbe;
     if (rem > 0) {
-      trsm64_kernel<<<dim3((rem + 7) / 8, n_items), 256, 0, st>>>(A, stride, ld, n, k0, nbe);
+      {
+        ProfScope ps(PH_TRSM, st);
+        trsm64_kernel<<<dim3((rem + 7) / 8, n_items), 256, 0, st>>>(A, stride, ld, n, k0, nbe);
+        prof_launched(PH_TRSM, 1, n_items);
+      }
+      ProfScope ps(PH_UPDATE, st);
       const int tiles = (rem + 63) / 64;
       gemm64_kernel<<<dim3(tiles, tiles, n_items), 256, 2 * 32 * 64 * 16, st>>>(A, stride, ld, n, k0, nbe);
+      prof_launched(PH_UPDATE, 1, n_items);
     }
   }
 }
@@ -290,5 +305,7 @@ void schur_inv64(const double2* A, size_t stride, int ld, int n, int kap, int n_
     cudaFuncSetAttribute(schur_inv64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 50 * 50 * 16);
     attr = true;
   }
+  ProfScope ps(PH_SCHUR, st);
   schur_inv64_kernel<<<n_items, 256, smem, st>>>(A, stride, ld, n, kap, scale, out, out_index, status, status_out);
+  prof_launched(PH_SCHUR, 1, n_items);
 }

@@ -15,6 +15,7 @@
 
 #include "mixed.h"
 #include "tc_gemm.h"
+#include "prof.h"
 
 namespace {
 
@@ -216,10 +217,11 @@ __global__ void __launch_bounds__(256) schur_inv32_kernel(const float2* __restri
 // per thread group; X staged through shared memory 64 rows at a time.
 __global__ void residual64_kernel(const double2* __restrict__ M0, size_t stride, int ld, int n, int kap,
                                   const double2* __restrict__ X0, double2* __restrict__ R0,
-                                  const int* __restrict__ conv) {
+                                  const int* __restrict__ conv, unsigned long long* __restrict__ work) {
   extern __shared__ cd Xs[];   // [64][kap]
   const int item = blockIdx.y;
   if (conv[item]) return;
+  if (work && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(work, 1ull);
   const cd* M = reinterpret_cast<const cd*>(M0 + size_t(item) * stride);
   const cd* X = reinterpret_cast<const cd*>(X0 + size_t(item) * n * kap);
   const int tid = threadIdx.x;
@@ -275,10 +277,11 @@ __global__ void __launch_bounds__(256) correct_kernel(const float2* __restrict__
                                                       const double2* __restrict__ Sinv0,
                                                       const double2* __restrict__ R0, double2* __restrict__ X0,
                                                       double* __restrict__ norms, const int* __restrict__ conv,
-                                                      int first) {
+                                                      int first, unsigned long long* __restrict__ work) {
   extern __shared__ cf w[];   // [n][G]
   const int item = blockIdx.y;
   if (conv[item]) return;
+  if (work && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(work, 1ull);
   const int cb = blockIdx.x * G;
   const int ng = min(G, kap - cb);
   const cf* A = reinterpret_cast<const cf*>(A0 + size_t(item) * stride);
@@ -490,23 +493,38 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   const int nb = tc_panel_width(c.opts.precision);
   for (int k0 = 0; k0 < r; k0 += nb) {
     const int nbe = std::min(nb, r - k0);
-    panel32_kernel<<<items, PT, 0, st>>>(M32, stride, ld, n, r, k0, nbe, c.piv, c.status, conv);
-    laswp32_kernel<<<dim3((n - nbe + 255) / 256, items), 256, 0, st>>>(M32, stride, ld, n, r, k0, nbe, c.piv);
+    {
+      ProfScope ps(PH_PANEL, st);
+      panel32_kernel<<<items, PT, 0, st>>>(M32, stride, ld, n, r, k0, nbe, c.piv, c.status, conv);
+      prof_launched(PH_PANEL, 1, items);
+    }
+    {
+      ProfScope ps(PH_SWAP, st);
+      laswp32_kernel<<<dim3((n - nbe + 255) / 256, items), 256, 0, st>>>(M32, stride, ld, n, r, k0, nbe, c.piv);
+      prof_launched(PH_SWAP, 1, items);
+    }
     const int rem = n - k0 - nbe;
     if (rem > 0) {
-      trsm32_kernel<<<dim3((rem + 7) / 8, items), 256, 0, st>>>(M32, stride, ld, n, k0, nbe);
+      {
+        ProfScope ps(PH_TRSM, st);
+        trsm32_kernel<<<dim3((rem + 7) / 8, items), 256, 0, st>>>(M32, stride, ld, n, k0, nbe);
+        prof_launched(PH_TRSM, 1, items);
+      }
       if (!tc_trailing_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, st))
         return MUST_ECUDA;
     }
   }
-  perm_kernel<<<(items + 63) / 64, 64, 0, st>>>(c.piv, r, n, perm, items);
   {
+    ProfScope ps_schur(PH_SCHUR, st);
+    perm_kernel<<<(items + 63) / 64, 64, 0, st>>>(c.piv, r, n, perm, items);
+    prof_launched(PH_SCHUR, 1);
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(schur_inv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 50 * 50 * 16);
       attr = true;
     }
     schur_inv32_kernel<<<items, 256, size_t(kap) * 2 * kap * 16, st>>>(M32, stride, ld, n, kap, Sinv, c.status);
+    prof_launched(PH_SCHUR, 1, items);
   }
   // refinement
   const int G = (n <= 2600) ? 8 : 4;
@@ -531,21 +549,32 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   const int iters = std::max(c.opts.max_iter, 0);
   for (int it = 0; it <= iters; ++it) {
     const bool first = (it == 0);
-    if (!first) residual64_kernel<<<gres, tres, smem_res, st>>>(c.M64, stride, ld, n, kap, X, R, conv);
-    if (G == 8)
-      correct_kernel<8><<<gcorr, 256, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
-                                                       conv, first);
-    else
-      correct_kernel<4><<<gcorr, 256, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
-                                                       conv, first);
+    if (!first) {
+      ProfScope ps(PH_RESIDUAL, st);
+      residual64_kernel<<<gres, tres, smem_res, st>>>(c.M64, stride, ld, n, kap, X, R, conv,
+                                                      prof_work_counter(PH_RESIDUAL));
+      prof_launched(PH_RESIDUAL, 1);
+    }
+    {
+      ProfScope ps(PH_CORRECT, st);
+      if (G == 8)
+        correct_kernel<8><<<gcorr, 256, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
+                                                         conv, first, prof_work_counter(PH_CORRECT));
+      else
+        correct_kernel<4><<<gcorr, 256, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
+                                                         conv, first, prof_work_counter(PH_CORRECT));
+      prof_launched(PH_CORRECT, 1);
+    }
     if (first) {
       cudaMemsetAsync(norms, 0, sizeof(double) * 2 * items, st);
     } else {
       check_kernel<<<(items + 127) / 128, 128, 0, st>>>(norms, conv, c.status, items, c.opts.tol, it == iters);
+      prof_launched(PH_OTHER, 1);
     }
   }
   if (iters == 0)   // no refinement allowed: the unrefined low-precision result is reported as not converged
     check_kernel<<<(items + 127) / 128, 128, 0, st>>>(norms, conv, c.status, items, 0.0, 2);
   output_kernel<<<items, 256, 0, st>>>(X, n, kap, c.tau, c.out_index, c.status, c.status_out, err);
+  prof_launched(PH_OTHER, 1);
   return MUST_OK;
 }

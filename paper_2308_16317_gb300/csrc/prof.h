@@ -1,0 +1,39 @@
+// Phase timers and launch counting (see prof.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+enum MustPhase {
+  PH_ASSEMBLE = 0,
+  PH_PANEL,
+  PH_SWAP,
+  PH_TRSM,
+  PH_PACK,
+  PH_UPDATE,
+  PH_SCHUR,
+  PH_RESIDUAL,
+  PH_CORRECT,
+  PH_OTHER,
+  PH_COUNT
+};
+
+// Records CUDA events around the enclosed launches when profiling is on.
+class ProfScope {
+ public:
+  ProfScope(int phase, cudaStream_t st);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  int phase_;
+  cudaStream_t st_;
+  void* a_;
+};
+
+// Count n kernel launches of a phase that together process `items` matrices
+// (0 when the kernels count their own items through prof_work_counter).
+void prof_launched(int phase, int n, long long items = 0);
+
+// Device counter (items processed) for phases whose work depends on data
+// (refinement kernels skip converged items), or NULL when profiling is off.
+unsigned long long* prof_work_counter(int phase);

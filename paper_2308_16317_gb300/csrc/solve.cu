@@ -9,6 +9,7 @@
 #include "common.cuh"
 #include "solver.h"
 #include "mixed.h"
+#include "prof.h"
 
 namespace {
 
@@ -225,4 +226,5 @@ __global__ void chunk_index_kernel(int* out_index, int* status, int items, int n
 
 void launch_chunk_index(int* out_index, int* status, int items, int ne, int nE, int e0, int canted, cudaStream_t st) {
   chunk_index_kernel<<<(items + 127) / 128, 128, 0, st>>>(out_index, status, items, ne, nE, e0, canted);
+  prof_launched(PH_OTHER, 1);
 }

@@ -27,6 +27,7 @@
 #include <mutex>
 
 #include "tc_gemm.h"
+#include "prof.h"
 
 namespace {
 
@@ -388,6 +389,7 @@ bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, 
   // item stride inside a slot group = pbytes; tensor maps use rows_pad rows per item
   const int item_rows = int(pbytes / (size_t(Kp) * es));
   {
+    ProfScope ps(PH_PACK, st);
     const int half = Kp / 2;
     const int ta = m * half;
     dim3 g((ta + 255) / 256, items);
@@ -404,6 +406,7 @@ bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, 
                                                  reinterpret_cast<uint16_t*>(pb_hi), reinterpret_cast<uint16_t*>(pb_lo),
                                                  0);
     }
+    prof_launched(PH_PACK, 2, items);
   }
   CUtensorMap mah, mal, mbh, mbl;
   if (!make_map(&mah, pa_hi, tf32, Kp, item_rows, items, BM) || !make_map(&mal, pa_lo, tf32, Kp, item_rows, items, BM) ||
@@ -428,6 +431,8 @@ bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, 
     attr = true;
   }
   dim3 grid((2 * m + BM - 1) / BM, (m + TC_BN - 1) / TC_BN, items);
+  ProfScope ps(PH_UPDATE, st);
   tc_update_kernel<TC_BN, TC_STAGES><<<grid, 128, smem, st>>>(mah, mal, mbh, mbl, P);
+  prof_launched(PH_UPDATE, 1, items);
   return true;
 }
