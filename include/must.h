@@ -152,6 +152,30 @@ size_t must_batch_workspace_bytes(int32_t n_liz, const must_liz* const* lizs, in
                                   const must_solve_opts* opts);
 
 /*
+ * Allocation-free FP64 solve.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory while they run (their
+ * device memory is owned by another allocator, or allocation is forbidden
+ * where they call from), so they cannot supply the workspace that
+ * must_tau00_solve needs.  It computes the same result as must_tau00_solve
+ * with MUST_FP64 and default options, using a scratch array compiled into
+ * the library: must_static_scratch_bytes() bytes (160 MiB, enough for one
+ * energy of both spins at n = 2160) of device memory that every GPU which
+ * loads the library holds until the process exits.  It calls no allocator.
+ *   E, tinv, tau00, status : as for must_tau00_solve, but all must be device
+ *                            memory (host buffers are rejected, MUST_EINVAL).
+ * A LIZ whose one-energy working set exceeds the scratch is rejected with
+ * MUST_EINVAL and a message naming the sizes.  The first call on each device
+ * looks up the scratch address (cudaGetSymbolAddress) with that device
+ * current; make it before any stream capture.  Every call shares the one
+ * scratch array, which keeps the previous call's contents; calls whose GPU
+ * work overlaps (other streams or host threads) race on it and must be
+ * serialised by the caller.
+ */
+must_status must_tau00_solve_static(const must_liz* liz, int32_t nE, const double* E, const double* tinv,
+                                    int32_t n_species, int32_t nspin, double* tau00, int32_t* status, void* stream);
+size_t must_static_scratch_bytes(void);
+
+/*
  * Instrumentation (not part of the paper's method).  When enabled, CUDA
  * events are recorded on the launching stream around each phase of the path
  * (0 assemble, 1 panel, 2 row_swap, 3 trsm, 4 pack, 5 trailing_update,

@@ -53,6 +53,8 @@ def load():
         "must_tinv_square_well": (I32, [I32, P, I32, P, D, I32, P, P]),
         "must_tau00_solve": (I32, [P, I32, P, P, I32, I32, ctypes.POINTER(must_solve_opts), P, SZ, P, P, P]),
         "must_tau00_batch": (I32, [I32, P, I32, P, P, I32, I32, ctypes.POINTER(must_solve_opts), P, SZ, P, P, P]),
+        "must_tau00_solve_static": (I32, [P, I32, P, P, I32, I32, P, P, P]),
+        "must_static_scratch_bytes": (SZ, []),
         "must_profile_enable": (None, [ctypes.c_int]),
         "must_profile_read": (ctypes.c_int, [P, P, P, ctypes.c_int]),
         "must_launch_count": (ctypes.c_longlong, []),
@@ -72,7 +74,8 @@ def exported_symbols():
     return [n for n in ("must_default_opts", "must_liz_build", "must_liz_free", "must_liz_order", "must_liz_kappa",
                         "must_workspace_bytes", "must_batch_workspace_bytes", "must_tinv_square_well",
                         "must_tau00_solve", "must_tau00_batch", "must_status_string", "must_last_error",
-                        "must_profile_enable", "must_profile_read", "must_launch_count", "must_phase_name")]
+                        "must_profile_enable", "must_profile_read", "must_launch_count", "must_phase_name",
+                        "must_tau00_solve_static", "must_static_scratch_bytes")]
 
 
 def _ptr(a):
@@ -202,3 +205,16 @@ def must_tau00_batch(lizs, E, tinv, n_species: int, nspin: int, opts: must_solve
                                    ctypes.byref(opts) if opts else None, _ptr(workspace), int(ws_bytes), _ptr(tau00),
                                    _ptr(status), _stream(stream)))
     return tau00
+
+
+def must_tau00_solve_static(liz: Liz, E, tinv, n_species: int, nspin: int, tau00, status=None, stream=None):
+    """FP64 solve in the library's own static scratch: for callers that cannot
+    allocate a workspace.  All arrays must be device memory; calls that overlap
+    on the GPU share (and race on) the one scratch array."""
+    _check(load().must_tau00_solve_static(liz.handle, _numel_complex(E), _ptr(E), _ptr(tinv), int(n_species),
+                                          int(nspin), _ptr(tau00), _ptr(status), _stream(stream)))
+    return tau00
+
+
+def must_static_scratch_bytes() -> int:
+    return int(load().must_static_scratch_bytes())

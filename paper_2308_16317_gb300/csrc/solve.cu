@@ -4,6 +4,7 @@
 //   tau_00 = S^{-1} (FP64 path), or the mixed-precision path in mixed.cu.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -227,4 +228,91 @@ __global__ void chunk_index_kernel(int* out_index, int* status, int items, int n
 void launch_chunk_index(int* out_index, int* status, int items, int ne, int nE, int e0, int canted, cudaStream_t st) {
   chunk_index_kernel<<<(items + 127) / 128, 128, 0, st>>>(out_index, status, items, ne, nE, e0, canted);
   prof_launched(PH_OTHER, 1);
+}
+
+// --------------------------------------------------------------------------
+// Allocation-free entry point (no counterpart in the paper).
+//
+// Some callers cannot allocate device memory while they run: a host code that
+// has handed all device memory to its own pool allocator, a solver called
+// from inside a region where allocation is forbidden (another library's
+// callback, a real-time loop that must not block on the allocator), or a
+// language binding with no way to obtain a device buffer.  For them the FP64
+// solve can run in a scratch area that lives in the library itself: a
+// file-scope device array of MUST_STATIC_SCRATCH_BYTES, allocated when the
+// library's GPU code is loaded on a device and held until the process exits.
+//
+// The array's name is only a host-side stand-in in host code, so its device
+// address is looked up with cudaGetSymbolAddress once per device (with that
+// device current) on the first call made on that device; make that first call
+// before any stream capture.  All calls share the one array and it keeps the
+// last call's contents, so two calls whose GPU work overlaps (different
+// streams, or different host threads) race on it: serialise them.
+#define MUST_STATIC_SCRATCH_BYTES (size_t(160) << 20)
+
+static __device__ __align__(256) unsigned char g_must_static_scratch[MUST_STATIC_SCRATCH_BYTES];
+
+static void* static_scratch_address(must_status* err) {
+  static std::mutex mu;
+  static void* addr[256] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    must_set_error("must_tau00_solve_static: no current CUDA device");
+    *err = MUST_ECUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_must_static_scratch);
+    if (e != cudaSuccess || !p) {
+      must_set_error("must_tau00_solve_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      *err = MUST_ECUDA;
+      return nullptr;
+    }
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+extern "C" size_t must_static_scratch_bytes(void) { return MUST_STATIC_SCRATCH_BYTES; }
+
+extern "C" must_status must_tau00_solve_static(const must_liz* z, int32_t nE, const double* E, const double* tinv,
+                                               int32_t n_species, int32_t nspin, double* tau00, int32_t* status,
+                                               void* stream) {
+  if (!z || nE < 1 || !E || !tinv || !tau00) {
+    must_set_error("must_tau00_solve_static: NULL argument or empty size");
+    return MUST_EINVAL;
+  }
+  if (n_species < 1 || nspin < 1 || nspin > 2 || (z->canted && nspin != 2)) {
+    must_set_error("must_tau00_solve_static: n_species/nspin out of range");
+    return MUST_EINVAL;
+  }
+  for (int p = 0; p < z->N; ++p)
+    if (z->h_species_perm[p] >= n_species) {
+      must_set_error("must_tau00_solve_static: species index >= n_species");
+      return MUST_EINVAL;
+    }
+  if (!must_is_device_ptr(E) || !must_is_device_ptr(tinv) || !must_is_device_ptr(tau00) ||
+      (status && !must_is_device_ptr(status))) {
+    must_set_error("must_tau00_solve_static: E, tinv, tau00 and status must be device memory");
+    return MUST_EINVAL;
+  }
+  // one energy (both spins of a collinear LIZ) must fit in the scratch
+  const int ld = ld_of(z->n), ipe = z->canted ? 1 : nspin;
+  const size_t need = size_t(ipe) * item_bytes(z->n, ld, z->kap, MUST_FP64) + 4 * 256;
+  if (need > MUST_STATIC_SCRATCH_BYTES) {
+    must_set_error("must_tau00_solve_static: matrix order %d needs %zu bytes of scratch per energy, more than the "
+                   "%zu-byte static scratch; use must_tau00_solve with a caller workspace",
+                   z->n, need, size_t(MUST_STATIC_SCRATCH_BYTES));
+    return MUST_EINVAL;
+  }
+  must_status err = MUST_OK;
+  char* ws = static_cast<char*>(static_scratch_address(&err));
+  if (!ws) return err;
+  must_solve_opts o;
+  must_default_opts(&o);   // FP64 path with equilibration
+  return solve_one(z, nE, reinterpret_cast<const double2*>(E), reinterpret_cast<const double2*>(tinv), n_species,
+                   nspin, o, ws, MUST_STATIC_SCRATCH_BYTES, reinterpret_cast<double2*>(tau00), status,
+                   static_cast<cudaStream_t>(stream));
 }
