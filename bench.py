@@ -182,7 +182,7 @@ def run_ours(args):
     n, kap = s.lizs[0].n, s.kap
     items = len(w.energies) * s.nspin
     prec = args.precision
-    opts = B.must_default_opts(PREC[prec])
+    opts = B.must_default_opts(PREC[prec], residual=1 if args.residual == "df" else 0)
     nb = 64 if prec != "fp64" else 32
 
     def barrier():
@@ -316,7 +316,7 @@ def run_ours(args):
             "data": "synthetic (seeded fcc 50/50 random alloy, square-well t-matrices)",
             "config": {"workload": "fcc135 LIZ, lmax=3, n=2160, 32 contour energies x 2 spins = 64 tau_00 solves/step",
                        "n": n, "n_liz": int(w.lizs[0].n_sites), "lmax": w.lmax, "solves_per_step": items,
-                       "precision": prec, "l2": "inputs larger than L2 (%.1f GB of matrices per step)" % (
+                       "precision": prec, "residual": args.residual if prec != "fp64" else None, "l2": "inputs larger than L2 (%.1f GB of matrices per step)" % (
                            items * n * n * (24 if prec != "fp64" else 16) / 1e9)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(l1 - l0),
             "clocks": clocks, "plain_fp64": fp64, "max_rel_err_vs_fp64": max_err,
@@ -383,6 +383,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
+    ap.add_argument("--residual", default="df", choices=["fp64", "df"],
+                    help="refinement residual: FP64 (DFMA) or double-float FP32 pairs")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0)

@@ -65,16 +65,21 @@ typedef enum {
 
 typedef struct {
   int32_t precision;      /* must_precision                                          */
-  double tol;             /* refinement stop: ||delta X||_F <= tol ||X||_F (mixed)   */
+  double tol;             /* refinement stop: ||delta X||_F <= tol ||X||_F (mixed); the
+                             refinement also stops when corrections stop shrinking   */
   int32_t max_iter;       /* refinement iteration cap (mixed); 0 => MUST_ENOCONV     */
   int32_t warm_start;     /* reserved for the learned seed; 0 = cold solve           */
   int32_t deterministic;  /* 1 = static schedule in batched launches                 */
   int32_t equilibrate;    /* 1 = symmetric |diag M|^{-1/2} scaling before low-prec LU */
+  int32_t residual;       /* mixed paths: 0 = FP64 residual (DFMA); 1 = residual in
+                             double-float (unevaluated FP32 pairs, ~48-bit, on the
+                             FP32 pipes, ~6x the GB300 FP64 rate)                 */
 } must_solve_opts;
 
 typedef struct must_liz must_liz;   /* opaque, immutable after build */
 
-/* Fill *opts with the defaults (FP64, tol 1e-13, max_iter 10, equilibrate 1). */
+/* Fill *opts with the defaults (FP64, tol 1e-10, max_iter 10, equilibrate 1,
+   FP64 residual). */
 void must_default_opts(must_solve_opts* opts);
 
 /*

@@ -29,7 +29,8 @@ class MustError(RuntimeError):
 
 class must_solve_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
-                ("warm_start", ctypes.c_int32), ("deterministic", ctypes.c_int32), ("equilibrate", ctypes.c_int32)]
+                ("warm_start", ctypes.c_int32), ("deterministic", ctypes.c_int32), ("equilibrate", ctypes.c_int32),
+                ("residual", ctypes.c_int32)]
 
 
 def load():

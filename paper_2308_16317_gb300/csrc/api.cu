@@ -48,11 +48,12 @@ extern "C" {
 void must_default_opts(must_solve_opts* o) {
   if (!o) return;
   o->precision = MUST_FP64;
-  o->tol = 1e-13;
+  o->tol = 1e-10;
   o->max_iter = 10;
   o->warm_start = 0;
   o->deterministic = 0;
   o->equilibrate = 1;
+  o->residual = 0;
 }
 
 const char* must_status_string(must_status s) {

@@ -189,6 +189,7 @@ struct AsmArgs {
   const double* scale;    // [item][n] (required when M32 != NULL or scale64)
   int items_per_e;        // nspin (collinear) or 1 (canted)
   int scale64;            // 1: the FP64 copy is equilibrated too (D M D)
+  int m64_df;             // 1: the M64 buffer holds M as FP32 pairs (hi.re, hi.im, lo.re, lo.im)
 };
 
 // M_aa of item `it` at row a (for the equilibration scale).
@@ -221,7 +222,10 @@ __global__ void scale_kernel(AsmArgs A, double* __restrict__ scale) {
 
 __device__ __forceinline__ void store_elem(const AsmArgs& A, int it, int row, int col, cd v) {
   const size_t off = size_t(it) * A.stride + size_t(col) * A.ld + row;
-  if (A.M64) {
+  if (A.M64 && A.m64_df) {
+    const float hr = float(v.x), hi = float(v.y);
+    reinterpret_cast<float4*>(A.M64)[off] = make_float4(hr, hi, float(v.x - double(hr)), float(v.y - double(hi)));
+  } else if (A.M64) {
     if (A.scale64) {
       const double s = A.scale[size_t(it) * A.n + row] * A.scale[size_t(it) * A.n + col];
       A.M64[off] = make_double2(s * v.x, s * v.y);
@@ -370,5 +374,6 @@ void launch_assemble_chunk(const AsmChunk& c, cudaStream_t st) {
   A.E = c.E; A.tinv = c.tinv; A.M64 = c.M64; A.M32 = c.M32; A.ld = c.ld; A.stride = c.stride; A.scale = c.scale;
   A.items_per_e = z->canted ? 1 : c.nspin;
   A.scale64 = c.scale64;
+  A.m64_df = c.m64_df;
   launch_assemble(A, st);
 }

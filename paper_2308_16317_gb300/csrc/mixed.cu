@@ -32,19 +32,28 @@ __device__ __forceinline__ float cnormf(cf a) { return a.x * a.x + a.y * a.y; }
 }  // namespace
 
 // ------------------------------------------------------------ FP32 panel --
+// Right-looking factorisation of the panel columns [k0, k0+nbe) (nbe <= 64)
+// of one matrix per CTA.  Per column: warp-shuffle argmax of |z|^2 over the
+// pivot-eligible rows [c, r), row swap inside the panel, pivot row staged in
+// shared memory, then every row below loads its whole remaining panel row
+// into registers (independent loads in flight), scales and updates it, and
+// stores it back.
+constexpr int PANEL_W = 64;
+
 __global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int r,
                                                      int k0, int nbe, int* __restrict__ piv0, int* __restrict__ status,
                                                      const int* __restrict__ conv) {
   __shared__ float sv[PT / 32];
   __shared__ int si[PT / 32];
   __shared__ int s_p;
+  __shared__ cf prow[PANEL_W];
   const int item = blockIdx.x;
   cf* A = reinterpret_cast<cf*>(A0 + size_t(item) * stride);
   int* piv = piv0 + size_t(item) * r;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int j = 0; j < nbe; ++j) {
     const int c = k0 + j;
-    cf* col = A + size_t(c) * ld;
+    const cf* col = A + size_t(c) * ld;
     float best = -1.0f;
     int bi = c;
     for (int i = c + tid; i < r; i += PT) argmax_merge(best, bi, cnormf(col[i]), i);
@@ -65,6 +74,7 @@ __global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, si
     }
     __syncthreads();
     const int p = s_p;
+    const int width = k0 + nbe - c;   // columns c .. k0+nbe-1
     if (p != c)
       for (int cc = k0 + tid; cc < k0 + nbe; cc += PT) {
         cf* cp = A + size_t(cc) * ld;
@@ -73,13 +83,24 @@ __global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, si
         cp[p] = t;
       }
     __syncthreads();
-    const cf d = col[c];
+    for (int q = tid; q < width; q += PT) prow[q] = A[size_t(c + q) * ld + c];
+    __syncthreads();
+    const cf d = prow[0];
     if (cnormf(d) > 0.0f) {
       const cf inv = cinvf(d);
       for (int i = c + 1 + tid; i < n; i += PT) {
-        const cf l = cmulf(col[i], inv);
-        col[i] = l;
-        for (int cc = c + 1; cc < k0 + nbe; ++cc) cfmsf(A[size_t(cc) * ld + i], l, A[size_t(cc) * ld + c]);
+        cf v[PANEL_W];
+#pragma unroll
+        for (int q = 0; q < PANEL_W; ++q)
+          if (q < width) v[q] = A[size_t(c + q) * ld + i];
+        const cf l = cmulf(v[0], inv);
+        A[size_t(c) * ld + i] = l;
+#pragma unroll
+        for (int q = 1; q < PANEL_W; ++q)
+          if (q < width) {
+            cfmsf(v[q], l, prow[q]);
+            A[size_t(c + q) * ld + i] = v[q];
+          }
       }
     }
     __syncthreads();
@@ -266,6 +287,77 @@ __global__ void residual64_kernel(const double2* __restrict__ M0, size_t stride,
   }
 }
 
+// Double-float residual: M stored as unevaluated FP32 pairs (hi + lo carries
+// ~48 bits), X split into pairs on the fly; each product ah*bh is split into
+// its rounded value and exact error (FMA), the running sum is kept as a pair
+// with Knuth's TwoSum, and the cross terms ah*bl + al*bh go to the low word.
+// The product lo*lo (~2^-48 relative) is dropped.
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float e = fmaf(ah, bh, -p);
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(t, e));
+  sl = fmaf(ah, bl, sl);
+  sl = fmaf(al, bh, sl);
+}
+
+__global__ void residual_df_kernel(const float4* __restrict__ M0, size_t stride, int ld, int n, int kap,
+                                   const double2* __restrict__ X0, double2* __restrict__ R0,
+                                   const int* __restrict__ conv, unsigned long long* __restrict__ work) {
+  extern __shared__ float4 Xd[];   // [64][kap]: (re_hi, im_hi, re_lo, im_lo)
+  const int item = blockIdx.y;
+  if (conv[item]) return;
+  if (work && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(work, 1ull);
+  const float4* M = M0 + size_t(item) * stride;
+  const double2* X = X0 + size_t(item) * n * kap;
+  const int tid = threadIdx.x;
+  const int row = blockIdx.x * 64 + (tid & 63);
+  const int c0 = (tid >> 6) * 4;
+  float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
+  for (int k0 = 0; k0 < n; k0 += 64) {
+    const int kn = min(64, n - k0);
+    __syncthreads();
+    for (int t = tid; t < kn * kap; t += blockDim.x) {
+      const int k = t % kn, c = t / kn;
+      const double2 x = X[size_t(c) * n + k0 + k];
+      const float xr = float(x.x), xi = float(x.y);
+      Xd[k * kap + c] = make_float4(xr, xi, float(x.x - double(xr)), float(x.y - double(xi)));
+    }
+    __syncthreads();
+    if (row < n) {
+      for (int k = 0; k < kn; ++k) {
+        const float4 m = M[size_t(k0 + k) * ld + row];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (c0 + q < kap) {
+            const float4 x = Xd[k * kap + c0 + q];
+            // re += mr xr - mi xi ; im += mr xi + mi xr
+            df_mac(rh[q], rl[q], m.x, m.z, x.x, x.z);
+            df_mac(rh[q], rl[q], -m.y, -m.w, x.y, x.w);
+            df_mac(ih[q], il[q], m.x, m.z, x.y, x.w);
+            df_mac(ih[q], il[q], m.y, m.w, x.x, x.z);
+          }
+      }
+    }
+  }
+  if (row < n) {
+    double2* R = R0 + size_t(item) * n * kap;
+    const int r = n - kap;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (c0 + q < kap) {
+        const int c = c0 + q;
+        const double e = (row == r + c) ? 1.0 : 0.0;
+        R[size_t(c) * n + row] = make_double2(e - (double(rh[q]) + double(rl[q])), -(double(ih[q]) + double(il[q])));
+      }
+  }
+}
+
 // --------------------------------------------- low-precision correction ----
 // delta = D U^{-1} L^{-1} P (D R) for G right-hand sides per CTA (w in shared
 // memory, FP32), then X += delta (FP64) and ||delta||^2, ||X||^2 accumulated.
@@ -420,8 +512,8 @@ __global__ void __launch_bounds__(256) correct_kernel(const float2* __restrict__
 // Convergence bookkeeping after a correction: conv = ||delta|| <= tol ||X||.
 // last = 1: final iteration (unconverged -> MUST_ENOCONV); last = 2: no
 // refinement was allowed at all (every item -> MUST_ENOCONV).
-__global__ void check_kernel(double* __restrict__ norms, int* __restrict__ conv, int* __restrict__ status, int items,
-                             double tol, int last) {
+__global__ void check_kernel(double* __restrict__ norms, double* __restrict__ prev, int* __restrict__ conv,
+                             int* __restrict__ status, int items, double tol, int last) {
   const int it = blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= items) return;
   if (!conv[it]) {
@@ -431,9 +523,15 @@ __global__ void check_kernel(double* __restrict__ norms, int* __restrict__ conv,
       if (status[it] == ST_OK) status[it] = ST_NONFINITE;
     } else if (last < 2 && dn <= tol * tol * xn) {
       conv[it] = 1;
+    } else if (last < 2 && prev[it] > 0.0 && dn > 0.25 * prev[it]) {
+      // corrections no longer shrink (|delta| ratio > 1/2): the residual's own
+      // rounding floor is reached above tol; stop and report it
+      conv[it] = 1;
+      if (status[it] == ST_OK) status[it] = ST_NOCONV;
     } else if (last && status[it] == ST_OK) {
       status[it] = ST_NOCONV;
     }
+    prev[it] = dn;
   }
   norms[2 * it] = 0.0;
   norms[2 * it + 1] = 0.0;
@@ -461,7 +559,7 @@ size_t mixed_item_bytes(int n, int ld, int kap) {
          + a256(size_t(n) * 4)             // perm
          + 2 * a256(size_t(n) * kap * 16)  // X, R
          + a256(size_t(kap) * kap * 16)    // Sinv
-         + 512                             // norms, conv, error word
+         + 768                             // norms, previous norms, conv, error word
          + tc_pack_bytes_per_item(n);      // tensor-core operand packs
 }
 
@@ -476,6 +574,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   double2* R = reinterpret_cast<double2*>(take(size_t(items) * n * kap * 16));
   double2* Sinv = reinterpret_cast<double2*>(take(size_t(items) * kap * kap * 16));
   double* norms = reinterpret_cast<double*>(take(size_t(items) * 16));
+  double* prevn = reinterpret_cast<double*>(take(size_t(items) * 8));
   int* conv = reinterpret_cast<int*>(take(size_t(items) * 4));
   int* err = reinterpret_cast<int*>(take(4));
   char* packs = take(size_t(items) * tc_pack_bytes_per_item(n));
@@ -486,6 +585,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   a.scale = scale;
   launch_assemble_chunk(a, st);
   cudaMemsetAsync(norms, 0, sizeof(double) * 2 * items, st);
+  cudaMemsetAsync(prevn, 0, sizeof(double) * items, st);
   cudaMemsetAsync(conv, 0, sizeof(int) * items, st);
   cudaMemsetAsync(err, 0, sizeof(int), st);
 
@@ -539,6 +639,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       cudaFuncSetAttribute(correct_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       cudaFuncSetAttribute(correct_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       cudaFuncSetAttribute(residual64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 16);
+      cudaFuncSetAttribute(residual_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 16);
       attr = true;
     }
   }
@@ -551,8 +652,13 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     const bool first = (it == 0);
     if (!first) {
       ProfScope ps(PH_RESIDUAL, st);
-      residual64_kernel<<<gres, tres, smem_res, st>>>(c.M64, stride, ld, n, kap, X, R, conv,
-                                                      prof_work_counter(PH_RESIDUAL));
+      if (c.opts.residual == 1)
+        residual_df_kernel<<<gres, tres, size_t(64) * kap * 16, st>>>(reinterpret_cast<const float4*>(c.M64), stride,
+                                                                        ld, n, kap, X, R, conv,
+                                                                        prof_work_counter(PH_RESIDUAL));
+      else
+        residual64_kernel<<<gres, tres, smem_res, st>>>(c.M64, stride, ld, n, kap, X, R, conv,
+                                                        prof_work_counter(PH_RESIDUAL));
       prof_launched(PH_RESIDUAL, 1);
     }
     {
@@ -568,12 +674,13 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     if (first) {
       cudaMemsetAsync(norms, 0, sizeof(double) * 2 * items, st);
     } else {
-      check_kernel<<<(items + 127) / 128, 128, 0, st>>>(norms, conv, c.status, items, c.opts.tol, it == iters);
+      check_kernel<<<(items + 127) / 128, 128, 0, st>>>(norms, prevn, conv, c.status, items, c.opts.tol,
+                                                         it == iters);
       prof_launched(PH_OTHER, 1);
     }
   }
   if (iters == 0)   // no refinement allowed: the unrefined low-precision result is reported as not converged
-    check_kernel<<<(items + 127) / 128, 128, 0, st>>>(norms, conv, c.status, items, 0.0, 2);
+    check_kernel<<<(items + 127) / 128, 128, 0, st>>>(norms, prevn, conv, c.status, items, 0.0, 2);
   output_kernel<<<items, 256, 0, st>>>(X, n, kap, c.tau, c.out_index, c.status, c.status_out, err);
   prof_launched(PH_OTHER, 1);
   return MUST_OK;

@@ -23,6 +23,7 @@ struct AsmChunk {
   size_t stride;
   double* scale;
   int scale64;      // equilibrate the FP64 copy as well (FP64 path)
+  int m64_df;       // store the unscaled matrix as FP32 pairs (double-float residual)
 };
 void launch_assemble_chunk(const AsmChunk& c, cudaStream_t st);
 

@@ -210,14 +210,26 @@ __global__ void __launch_bounds__(128, 1)
     mma_commit(&done);
   }
   __syncthreads();   // roles finished issuing (s_fail visible); the MMAs may still run
+  // prefetch this thread's C row segment while the MMAs run: real row rr of
+  // the tile is complex row i, component comp (re/im) -> consecutive lanes hit
+  // consecutive floats of a column (coalesced)
+  const int rr = row0 + warp * 32 + lane;
+  const int i = P.base + (rr >> 1);
+  const int comp = rr & 1;
+  float* Cc = reinterpret_cast<float*>(P.C + size_t(item) * P.stride);
+  float cv[BN];
+  if (i < P.n) {
+#pragma unroll
+    for (int j = 0; j < BN; ++j) {
+      const int col = P.base + col0 + j;
+      cv[j] = (col < P.n) ? Cc[2 * (size_t(col) * P.ld + i) + comp] : 0.f;
+    }
+  }
   // epilogue: every warp waits for the accumulator
   const bool have = mbar_wait(&done, 0);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (have && !s_fail) {
-    const int rr = row0 + warp * 32 + lane;           // real row within the trailing block
-    const int i = P.base + (rr >> 1);                  // complex row of the matrix
-    const int comp = rr & 1;
-    float* Cc = reinterpret_cast<float*>(P.C + size_t(item) * P.stride);
+#pragma unroll
     for (int cc = 0; cc < BN; cc += 32) {
       uint32_t v[32];
       tmem_ld32(tmem + (uint32_t(warp * 32) << 16) + cc, v);
@@ -225,10 +237,7 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = P.base + col0 + cc + j;
-          if (col < P.n) {
-            float* p = Cc + 2 * (size_t(col) * P.ld + i) + comp;
-            *p -= __uint_as_float(v[j]);
-          }
+          if (col < P.n) Cc[2 * (size_t(col) * P.ld + i) + comp] = cv[cc + j] - __uint_as_float(v[j]);
         }
       }
     }
