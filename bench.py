@@ -35,6 +35,7 @@ UNIT = "solves/s"
 PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (profiling recipe); DFMA/DMMA microbenchmark: 1.01-1.05
 FP32_PEAK_TFLOPS = 80.5      # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (measured FFMA: 75)
+FP32_INSTR_PEAK = 40.3       # T FP32 instructions/s: 152 SMs x 128 lanes x 2.07 GHz
 
 
 def dist_env():
@@ -251,6 +252,11 @@ def run_ours(args):
         elif bound == "hbm":
             peak = peaks["hbm_gbs"] * 1e9
             punit, scale = "GB/s", 1e9
+        elif dom == "residual" and args.residual == "df":
+            # double-float residual: 48 FP32 instructions per complex MAC (8 FP64-equivalent flops)
+            achieved = achieved / 8.0 * 48.0
+            peak = FP32_INSTR_PEAK * 1e12
+            punit, scale = "Tinstr/s (FP32)", 1e12
         else:
             peak = (FP64_PEAK_TFLOPS if dom == "residual" or prec == "fp64" else FP32_PEAK_TFLOPS) * 1e12
             punit, scale = "TFLOP/s", 1e12

@@ -32,13 +32,18 @@ __device__ __forceinline__ float cnormf(cf a) { return a.x * a.x + a.y * a.y; }
 }  // namespace
 
 // ------------------------------------------------------------ FP32 panel --
-// Right-looking factorisation of the panel columns [k0, k0+nbe) (nbe <= 64)
-// of one matrix per CTA.  Per column: warp-shuffle argmax of |z|^2 over the
-// pivot-eligible rows [c, r), row swap inside the panel, pivot row staged in
-// shared memory, then every row below loads its whole remaining panel row
-// into registers (independent loads in flight), scales and updates it, and
-// stores it back.
+// Factorisation of the panel columns [k0, k0+nbe) (nbe <= 64) of one matrix
+// per CTA, blocked into leaves of LEAF columns (right-looking at two levels):
+//   for each leaf: factor its columns one by one (warp-shuffle argmax of
+//   |z|^2 over the pivot-eligible rows [c, r), row swap across the whole
+//   panel, rank-1 update restricted to the leaf), then solve the leaf's rows
+//   of the remaining panel columns (U block, staged in shared memory) and
+//   update the rows below with one pass over the remaining columns.
+// Each row update loads the row segment into registers with independent
+// loads.  Panel traffic ~ m (nbe^2/(2 LEAF) + nbe LEAF/2) elements instead of
+// m nbe^2/2 for column-at-a-time updates of the whole panel.
 constexpr int PANEL_W = 64;
+constexpr int LEAF = 8;
 
 __global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int r,
                                                      int k0, int nbe, int* __restrict__ piv0, int* __restrict__ status,
@@ -46,61 +51,120 @@ __global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, si
   __shared__ float sv[PT / 32];
   __shared__ int si[PT / 32];
   __shared__ int s_p;
-  __shared__ cf prow[PANEL_W];
+  __shared__ cf prow[LEAF];
+  __shared__ cf Ub[LEAF][PANEL_W];     // leaf rows of the remaining panel columns
+  __shared__ cf Ll[LEAF][LEAF];        // leaf's unit-lower top block
   const int item = blockIdx.x;
   cf* A = reinterpret_cast<cf*>(A0 + size_t(item) * stride);
   int* piv = piv0 + size_t(item) * r;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int j = 0; j < nbe; ++j) {
-    const int c = k0 + j;
-    const cf* col = A + size_t(c) * ld;
-    float best = -1.0f;
-    int bi = c;
-    for (int i = c + tid; i < r; i += PT) argmax_merge(best, bi, cnormf(col[i]), i);
-    for (int o = 16; o > 0; o >>= 1) {
-      const float v2 = __shfl_down_sync(0xffffffffu, best, o);
-      const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
-      argmax_merge(best, bi, v2, i2);
-    }
-    if (lane == 0) { sv[warp] = best; si[warp] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      float b = sv[0];
-      int p = si[0];
-      for (int w = 1; w < PT / 32; ++w) argmax_merge(b, p, sv[w], si[w]);
-      if (!(b > 0.0f)) status[item] = ST_SINGULAR;
-      piv[c] = p;
-      s_p = p;
-    }
-    __syncthreads();
-    const int p = s_p;
-    const int width = k0 + nbe - c;   // columns c .. k0+nbe-1
-    if (p != c)
-      for (int cc = k0 + tid; cc < k0 + nbe; cc += PT) {
-        cf* cp = A + size_t(cc) * ld;
-        const cf t = cp[c];
-        cp[c] = cp[p];
-        cp[p] = t;
+  const int pend = k0 + nbe;
+  for (int lb = 0; lb < nbe; lb += LEAF) {
+    const int c0 = k0 + lb;
+    const int lw = min(LEAF, nbe - lb);
+    const int le = c0 + lw;             // leaf columns [c0, le)
+    // (a) leaf columns one by one
+    for (int c = c0; c < le; ++c) {
+      const cf* col = A + size_t(c) * ld;
+      float best = -1.0f;
+      int bi = c;
+      for (int i = c + tid; i < r; i += PT) argmax_merge(best, bi, cnormf(col[i]), i);
+      for (int o = 16; o > 0; o >>= 1) {
+        const float v2 = __shfl_down_sync(0xffffffffu, best, o);
+        const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+        argmax_merge(best, bi, v2, i2);
       }
-    __syncthreads();
-    for (int q = tid; q < width; q += PT) prow[q] = A[size_t(c + q) * ld + c];
-    __syncthreads();
-    const cf d = prow[0];
-    if (cnormf(d) > 0.0f) {
-      const cf inv = cinvf(d);
-      for (int i = c + 1 + tid; i < n; i += PT) {
-        cf v[PANEL_W];
+      if (lane == 0) { sv[warp] = best; si[warp] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        float b = sv[0];
+        int p = si[0];
+        for (int w = 1; w < PT / 32; ++w) argmax_merge(b, p, sv[w], si[w]);
+        if (!(b > 0.0f)) status[item] = ST_SINGULAR;
+        piv[c] = p;
+        s_p = p;
+      }
+      __syncthreads();
+      const int p = s_p;
+      if (p != c)
+        for (int cc = k0 + tid; cc < pend; cc += PT) {
+          cf* cp = A + size_t(cc) * ld;
+          const cf t = cp[c];
+          cp[c] = cp[p];
+          cp[p] = t;
+        }
+      __syncthreads();
+      const int width = le - c;
+      if (tid < width) prow[tid] = A[size_t(c + tid) * ld + c];
+      __syncthreads();
+      const cf d = prow[0];
+      if (cnormf(d) > 0.0f) {
+        const cf inv = cinvf(d);
+        for (int i = c + 1 + tid; i < n; i += PT) {
+          cf v[LEAF];
 #pragma unroll
-        for (int q = 0; q < PANEL_W; ++q)
-          if (q < width) v[q] = A[size_t(c + q) * ld + i];
-        const cf l = cmulf(v[0], inv);
-        A[size_t(c) * ld + i] = l;
+          for (int q = 0; q < LEAF; ++q)
+            if (q < width) v[q] = A[size_t(c + q) * ld + i];
+          const cf l = cmulf(v[0], inv);
+          A[size_t(c) * ld + i] = l;
 #pragma unroll
-        for (int q = 1; q < PANEL_W; ++q)
-          if (q < width) {
-            cfmsf(v[q], l, prow[q]);
-            A[size_t(c + q) * ld + i] = v[q];
-          }
+          for (int q = 1; q < LEAF; ++q)
+            if (q < width) {
+              cfmsf(v[q], l, prow[q]);
+              A[size_t(c + q) * ld + i] = v[q];
+            }
+        }
+      }
+      __syncthreads();
+    }
+    const int rest = pend - le;          // remaining panel columns [le, pend)
+    if (rest <= 0) continue;
+    // (b) U block: rows [c0, le) of the remaining columns, L_leaf^{-1} A
+    for (int t = tid; t < lw * lw; t += PT) {
+      const int i = t % lw, j = t / lw;
+      Ll[i][j] = A[size_t(c0 + j) * ld + c0 + i];
+    }
+    __syncthreads();
+    if (tid < rest) {
+      const int cc = le + tid;
+      cf x[LEAF];
+#pragma unroll
+      for (int i = 0; i < LEAF; ++i)
+        if (i < lw) x[i] = A[size_t(cc) * ld + c0 + i];
+#pragma unroll
+      for (int i = 1; i < LEAF; ++i)
+        if (i < lw)
+#pragma unroll
+          for (int j = 0; j < LEAF; ++j)
+            if (j < i) cfmsf(x[i], Ll[i][j], x[j]);
+#pragma unroll
+      for (int i = 0; i < LEAF; ++i)
+        if (i < lw) {
+          A[size_t(cc) * ld + c0 + i] = x[i];
+          Ub[i][tid] = x[i];
+        }
+    }
+    __syncthreads();
+    // (c) rows below the leaf: A[i, rest] -= L[i, leaf] U[leaf, rest]
+    for (int i = le + tid; i < n; i += PT) {
+      cf l[LEAF];
+#pragma unroll
+      for (int j = 0; j < LEAF; ++j)
+        if (j < lw) l[j] = A[size_t(c0 + j) * ld + i];
+      for (int q0 = 0; q0 < rest; q0 += 16) {
+        cf v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (q0 + q < rest) v[q] = A[size_t(le + q0 + q) * ld + i];
+#pragma unroll
+        for (int j = 0; j < LEAF; ++j)
+          if (j < lw)
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (q0 + q < rest) cfmsf(v[q], l[j], Ub[j][q0 + q]);
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (q0 + q < rest) A[size_t(le + q0 + q) * ld + i] = v[q];
       }
     }
     __syncthreads();
@@ -362,6 +426,11 @@ __global__ void residual_df_kernel(const float4* __restrict__ M0, size_t stride,
 // delta = D U^{-1} L^{-1} P (D R) for G right-hand sides per CTA (w in shared
 // memory, FP32), then X += delta (FP64) and ||delta||^2, ||X||^2 accumulated.
 // first != 0: R is E0 (not read) and X is overwritten.
+// Blocked substitution with 32-row blocks: the block's 32x32 triangle is
+// staged in shared memory and solved by one warp (lane = row, shuffles
+// broadcast the solved entries); all threads then apply the block to the
+// remaining rows, each loading its row segment of L (or U) with independent
+// loads.
 template <int G>
 __global__ void __launch_bounds__(256) correct_kernel(const float2* __restrict__ A0, size_t stride, int ld, int n,
                                                       int kap, const int* __restrict__ perm0,
@@ -371,6 +440,7 @@ __global__ void __launch_bounds__(256) correct_kernel(const float2* __restrict__
                                                       double* __restrict__ norms, const int* __restrict__ conv,
                                                       int first, unsigned long long* __restrict__ work) {
   extern __shared__ cf w[];   // [n][G]
+  __shared__ cf Tb[32][33];   // staged diagonal block
   const int item = blockIdx.y;
   if (conv[item]) return;
   if (work && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(work, 1ull);
@@ -380,7 +450,7 @@ __global__ void __launch_bounds__(256) correct_kernel(const float2* __restrict__
   const int* perm = perm0 + size_t(item) * n;
   const double* d = scale0 + size_t(item) * n;
   const int r = n - kap;
-  const int tid = threadIdx.x, T = blockDim.x;
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
   // gather w = P (D R)
   for (int t = tid; t < n * G; t += T) {
     const int i = t / G, c = t % G;
@@ -397,25 +467,44 @@ __global__ void __launch_bounds__(256) correct_kernel(const float2* __restrict__
     w[t] = v;
   }
   __syncthreads();
-  // forward: unit lower L, columns 0..r-1
+  // forward: unit lower L, columns 0..r-1, rows 0..n-1
   for (int jb = 0; jb < r; jb += 32) {
-    const int je = min(jb + 32, r);
-    for (int j = jb; j < je; ++j) {
-      for (int t = tid; t < (je - j - 1) * G; t += T) {
-        const int i = j + 1 + t / G, c = t % G;
-        cfmsf(w[i * G + c], A[size_t(j) * ld + i], w[j * G + c]);
-      }
-      __syncthreads();
+    const int bs = min(32, r - jb), je = jb + bs;
+    for (int t = tid; t < 32 * 32; t += T) {
+      const int ii = t & 31, jj = t >> 5;
+      if (ii < bs && jj < bs) Tb[ii][jj] = A[size_t(jb + jj) * ld + jb + ii];
     }
+    __syncthreads();
+    if (warp == 0) {
+      cf v[G];
+#pragma unroll
+      for (int c = 0; c < G; ++c) v[c] = (lane < bs) ? w[(jb + lane) * G + c] : mkf(0.f, 0.f);
+      for (int j = 0; j < bs - 1; ++j) {
+        const cf l = (lane > j && lane < bs) ? Tb[lane][j] : mkf(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < G; ++c) {
+          const cf xj = mkf(__shfl_sync(0xffffffffu, v[c].x, j), __shfl_sync(0xffffffffu, v[c].y, j));
+          cfmsf(v[c], l, xj);
+        }
+      }
+      if (lane < bs)
+#pragma unroll
+        for (int c = 0; c < G; ++c) w[(jb + lane) * G + c] = v[c];
+    }
+    __syncthreads();
     for (int i = je + tid; i < n; i += T) {
+      cf lrow[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < bs) lrow[j] = A[size_t(jb + j) * ld + i];
       cf acc[G];
 #pragma unroll
       for (int c = 0; c < G; ++c) acc[c] = w[i * G + c];
-      for (int j = jb; j < je; ++j) {
-        const cf l = A[size_t(j) * ld + i];
 #pragma unroll
-        for (int c = 0; c < G; ++c) cfmsf(acc[c], l, w[j * G + c]);
-      }
+      for (int j = 0; j < 32; ++j)
+        if (j < bs)
+#pragma unroll
+          for (int c = 0; c < G; ++c) cfmsf(acc[c], lrow[j], w[(jb + j) * G + c]);
 #pragma unroll
       for (int c = 0; c < G; ++c) w[i * G + c] = acc[c];
     }
@@ -430,11 +519,11 @@ __global__ void __launch_bounds__(256) correct_kernel(const float2* __restrict__
 #pragma unroll
       for (int c = 0; c < G; ++c) tmp[c] = mk(0.0, 0.0);
       for (int k = 0; k < kap; ++k) {
-        const double2 s = Si[size_t(i) * kap + k];
+        const double2 sv = Si[size_t(i) * kap + k];
 #pragma unroll
         for (int c = 0; c < G; ++c) {
           const cf x = w[(r + k) * G + c];
-          tmp[c] = tmp[c] + mk(s.x, s.y) * mk(x.x, x.y);
+          tmp[c] = tmp[c] + mk(sv.x, sv.y) * mk(x.x, x.y);
         }
       }
     }
@@ -458,28 +547,48 @@ __global__ void __launch_bounds__(256) correct_kernel(const float2* __restrict__
     for (int c = 0; c < G; ++c) w[i * G + c] = acc[c];
   }
   __syncthreads();
-  // backward: U11 (non-unit upper)
+  // backward: U11 (non-unit upper), blocks from the bottom
   for (int je = r; je > 0; je -= 32) {
-    const int jb = max(je - 32, 0);
-    for (int j = je - 1; j >= jb; --j) {
-      const cf inv = cinvf(A[size_t(j) * ld + j]);
-      if (tid < G) w[j * G + tid] = cmulf(w[j * G + tid], inv);
-      __syncthreads();
-      for (int t = tid; t < (j - jb) * G; t += T) {
-        const int i = jb + t / G, c = t % G;
-        cfmsf(w[i * G + c], A[size_t(j) * ld + i], w[j * G + c]);
-      }
-      __syncthreads();
+    const int jb = max(je - 32, 0), bs = je - jb;
+    for (int t = tid; t < 32 * 32; t += T) {
+      const int ii = t & 31, jj = t >> 5;
+      if (ii < bs && jj < bs) Tb[ii][jj] = A[size_t(jb + jj) * ld + jb + ii];
     }
+    __syncthreads();
+    if (warp == 0) {
+      cf v[G];
+#pragma unroll
+      for (int c = 0; c < G; ++c) v[c] = (lane < bs) ? w[(jb + lane) * G + c] : mkf(0.f, 0.f);
+      const cf dinv = (lane < bs) ? cinvf(Tb[lane][lane]) : mkf(0.f, 0.f);
+      for (int j = bs - 1; j >= 0; --j) {
+        if (lane == j)
+#pragma unroll
+          for (int c = 0; c < G; ++c) v[c] = cmulf(v[c], dinv);
+        const cf u = (lane < j) ? Tb[lane][j] : mkf(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < G; ++c) {
+          const cf xj = mkf(__shfl_sync(0xffffffffu, v[c].x, j), __shfl_sync(0xffffffffu, v[c].y, j));
+          cfmsf(v[c], u, xj);
+        }
+      }
+      if (lane < bs)
+#pragma unroll
+        for (int c = 0; c < G; ++c) w[(jb + lane) * G + c] = v[c];
+    }
+    __syncthreads();
     for (int i = tid; i < jb; i += T) {
+      cf urow[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < bs) urow[j] = A[size_t(jb + j) * ld + i];
       cf acc[G];
 #pragma unroll
       for (int c = 0; c < G; ++c) acc[c] = w[i * G + c];
-      for (int j = jb; j < je; ++j) {
-        const cf u = A[size_t(j) * ld + i];
 #pragma unroll
-        for (int c = 0; c < G; ++c) cfmsf(acc[c], u, w[j * G + c]);
-      }
+      for (int j = 0; j < 32; ++j)
+        if (j < bs)
+#pragma unroll
+          for (int c = 0; c < G; ++c) cfmsf(acc[c], urow[j], w[(jb + j) * G + c]);
 #pragma unroll
       for (int c = 0; c < G; ++c) w[i * G + c] = acc[c];
     }
@@ -636,14 +745,14 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   {
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(correct_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      cudaFuncSetAttribute(correct_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(correct_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(correct_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(residual64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 16);
       cudaFuncSetAttribute(residual_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 16);
       attr = true;
     }
   }
-  if (smem_corr > 227 * 1024) {
+  if (smem_corr > 200 * 1024) {
     must_set_error("matrix order %d too large for the correction kernel", n);
     return MUST_EUNSUPPORTED;
   }
