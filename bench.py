@@ -178,7 +178,7 @@ def run_ours(args):
     from paper_2308_16317_gb300.runner import Session, blocks_to_numpy
     libbuild.build()
     B.load()
-    w = wl.liz135(seed=wl.SEED_BASE + 2 + rank)
+    w = wl.liz135(seed=wl.SEED_BASE + 2 + rank, n_e=args.n_energies)
     s = Session(w, device="cuda:%d" % local)
     n, kap = s.lizs[0].n, s.kap
     items = len(w.energies) * s.nspin
@@ -394,6 +394,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0)
+    ap.add_argument("--n-energies", type=int, default=32,
+                    help="contour energies per step (32 = the benchmark workload; fewer for ncu captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
