@@ -14,6 +14,8 @@
 //                   and every spin that shares the energy; column-major,
 //                   16-byte complex stores, consecutive lanes on consecutive
 //                   rows.
+#include <algorithm>
+
 #include "common.cuh"
 #include "solver.h"
 #include "prof.h"
@@ -169,13 +171,18 @@ __global__ void tinv_kernel(int nE, const double2* __restrict__ E, int n_pot, co
 }
 
 // ------------------------------------------------------------------------
-struct AsmArgs {
-  int N, nL, nL2, lmax, kap, n, n_pairs, canted;
+struct LizDev {
+  int N, n_pairs, pad;
   const int* species;     // [N] permuted
   const double* dirs;     // [N][3] permuted (canted)
   const int2* pair_pq;
   const double* pair_d;
   const double* pair_Y;
+};
+
+struct AsmArgs {
+  int nL, nL2, lmax, kap, n, canted, n_lz;
+  LizDev L[MUST_CHUNK_LIZ];
   const int* g_start;
   const int* g_L2;
   const double* g_c;
@@ -192,13 +199,16 @@ struct AsmArgs {
   int m64_df;             // 1: the M64 buffer holds M as FP32 pairs (hi.re, hi.im, lo.re, lo.im)
 };
 
-// M_aa of item `it` at row a (for the equilibration scale).
+// M_aa of item `it` at row a (for the equilibration scale); 1 on padding sites.
 __device__ __forceinline__ cd diag_entry(const AsmArgs& A, int it, int a) {
-  const int el = A.canted ? it : it % A.nEc;
-  const int s = A.canted ? 0 : it / A.nEc;
+  const int el = it % A.nEc;
+  const int grp = it / A.nEc;               // lz * items_per_e + spin
+  const int lz = grp / A.items_per_e, s = A.canted ? 0 : grp % A.items_per_e;
+  const LizDev& Lz = A.L[lz];
   const int e = A.e0 + el;
-  const int p = a / A.kap, w = a % A.kap;
-  const int sp = A.species[p];
+  const int p = a / A.kap - Lz.pad, w = a % A.kap;
+  if (p < 0) return mk(1.0, 0.0);
+  const int sp = Lz.species[p];
   if (!A.canted) {
     const int l = l_of(w);
     const double2 v = A.tinv[((size_t(s) * A.n_species + sp) * A.nE + e) * (A.lmax + 1) + l];
@@ -207,7 +217,7 @@ __device__ __forceinline__ cd diag_entry(const AsmArgs& A, int it, int a) {
   const int sg = w / A.nL, l = l_of(w % A.nL);
   const double2 u = A.tinv[((size_t(0) * A.n_species + sp) * A.nE + e) * (A.lmax + 1) + l];
   const double2 d = A.tinv[((size_t(1) * A.n_species + sp) * A.nE + e) * (A.lmax + 1) + l];
-  const double ez = A.dirs[3 * p + 2];
+  const double ez = Lz.dirs[3 * p + 2];
   const cd av = mk(u.x, u.y), bv = mk(d.x, d.y);
   return 0.5 * (av + bv) + (sg == 0 ? 0.5 * ez : -0.5 * ez) * (av - bv);
 }
@@ -239,32 +249,37 @@ __device__ __forceinline__ void store_elem(const AsmArgs& A, int it, int row, in
   }
 }
 
-// One warp per (unit, energy); units [0, n_pairs) are site pairs p < q, units
-// [n_pairs, n_pairs + N) are diagonal sites.
+// One warp per (unit, energy, LIZ of the chunk); units [0, n_pairs) are site
+// pairs p < q, [n_pairs, n_pairs + N) diagonal sites, and the next pad units
+// the identity blocks of the padding sites (their off-diagonal blocks are
+// zero-filled before the launch).
 __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
   __shared__ cd wsh[8][MUST_MAX_NL2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int unit = blockIdx.x * 8 + warp;
   const int el = blockIdx.y;
-  if (unit >= A.n_pairs + A.N) return;
+  const int lz = blockIdx.z;
+  const LizDev& Lz = A.L[lz];
+  if (unit >= Lz.n_pairs + Lz.N + Lz.pad) return;
   const int e = A.e0 + el;
   const cd Ec = mk(A.E[e].x, A.E[e].y);
-  const int nL = A.nL, kap = A.kap;
-  if (unit < A.n_pairs) {
-    const int2 pq = A.pair_pq[unit];
+  const int nL = A.nL, kap = A.kap, off = Lz.pad;
+  auto item_of = [&](int ii) { return (lz * A.items_per_e + ii) * A.nEc + el; };
+  if (unit < Lz.n_pairs) {
+    const int2 pq = Lz.pair_pq[unit];
     const cd k = csqrt_p(Ec);
-    const double d = A.pair_d[unit];
+    const double d = Lz.pair_d[unit];
     const int l2max = 2 * A.lmax;
     cd h[2 * MUST_MAX_LMAX + 1];
     hankel_up(l2max, d * k, h);
     // w'_L'' = 4 pi i kappa h_l'' Y_L''  (so that the block entry -G = sum c w')
     const cd f = mk(0.0, 4.0 * 3.14159265358979323846) * k;
     for (int L2 = lane; L2 < A.nL2; L2 += 32) {
-      const double y = A.pair_Y[size_t(unit) * A.nL2 + L2];
+      const double y = Lz.pair_Y[size_t(unit) * A.nL2 + L2];
       wsh[warp][L2] = y * (f * h[l_of(L2)]);
     }
     __syncwarp();
-    const int p = pq.x, q = pq.y;
+    const int p = pq.x + off, q = pq.y + off;
     for (int ent = lane; ent < nL * nL; ent += 32) {
       const int L = ent % nL, Lp = ent / nL;
       cd v = mk(0.0, 0.0);
@@ -278,7 +293,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
       const double par = ((l_of(L) + l_of(Lp)) & 1) ? -1.0 : 1.0;
       const cd vt = par * v;
       for (int ii = 0; ii < A.items_per_e; ++ii) {
-        const int it = A.canted ? el : ii * A.nEc + el;
+        const int it = item_of(ii);
         if (!A.canted) {
           store_elem(A, it, p * kap + L, q * kap + Lp, v);
           store_elem(A, it, q * kap + L, p * kap + Lp, vt);
@@ -292,11 +307,12 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
         }
       }
     }
-  } else {
-    const int p = unit - A.n_pairs;
-    const int sp = A.species[p];
+  } else if (unit < Lz.n_pairs + Lz.N) {
+    const int ps = unit - Lz.n_pairs;      // site in the LIZ's permuted order
+    const int p = ps + off;                // block in the chunk matrix
+    const int sp = Lz.species[ps];
     for (int ii = 0; ii < A.items_per_e; ++ii) {
-      const int it = A.canted ? el : ii * A.nEc + el;
+      const int it = item_of(ii);
       for (int ent = lane; ent < kap * kap; ent += 32) {
         const int a = ent % kap, b = ent / kap;
         cd v = mk(0.0, 0.0);
@@ -313,7 +329,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
             const double2 dn = A.tinv[((size_t(1) * A.n_species + sp) * A.nE + e) * (A.lmax + 1) + l];
             const cd av = mk(u.x, u.y), bv = mk(dn.x, dn.y);
             const cd hs = 0.5 * (av + bv), hd = 0.5 * (av - bv);
-            const double ex = A.dirs[3 * p], ey = A.dirs[3 * p + 1], ez = A.dirs[3 * p + 2];
+            const double ex = Lz.dirs[3 * ps], ey = Lz.dirs[3 * ps + 1], ez = Lz.dirs[3 * ps + 2];
             // sigma.e = [[ez, ex - i ey], [ex + i ey, -ez]]
             cd sig;
             if (sa == 0 && sb == 0) sig = mk(ez, 0.0);
@@ -325,6 +341,15 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
           }
         }
         store_elem(A, it, p * kap + a, p * kap + b, v);
+      }
+    }
+  } else {
+    const int p = unit - Lz.n_pairs - Lz.N;   // padding site: identity block
+    for (int ii = 0; ii < A.items_per_e; ++ii) {
+      const int it = item_of(ii);
+      for (int ent = lane; ent < kap * kap; ent += 32) {
+        const int a = ent % kap, b = ent / kap;
+        store_elem(A, it, p * kap + a, p * kap + b, mk(a == b ? 1.0 : 0.0, 0.0));
       }
     }
   }
@@ -350,30 +375,44 @@ void launch_tinv(int nE, const double2* E, int n_pot, const double* V, double a,
   }
 }
 
-void launch_assemble(const AsmArgs& A, cudaStream_t st) {
+void launch_assemble(const AsmArgs& A, int max_units, cudaStream_t st) {
   ProfScope ps(PH_ASSEMBLE, st);
-  const int n_items = A.items_per_e * A.nEc;
+  const int n_items = A.items_per_e * A.nEc * A.n_lz;
   if (A.M32 || A.scale64) {
     dim3 g((A.n + 255) / 256, n_items);
     scale_kernel<<<g, 256, 0, st>>>(A, const_cast<double*>(A.scale));
     prof_launched(PH_ASSEMBLE, 1);
   }
-  dim3 grid((A.n_pairs + A.N + 7) / 8, A.nEc);
+  dim3 grid((max_units + 7) / 8, A.nEc, A.n_lz);
   assemble_kernel<<<grid, 256, 0, st>>>(A);
   prof_launched(PH_ASSEMBLE, 1, n_items);
 }
 
 void launch_assemble_chunk(const AsmChunk& c, cudaStream_t st) {
-  const must_liz* z = c.liz;
+  const must_liz* z0 = c.lz[0];
   AsmArgs A;
-  A.N = z->N; A.nL = z->nL; A.nL2 = z->nL2; A.lmax = z->lmax; A.kap = z->kap; A.n = z->n;
-  A.n_pairs = z->n_pairs; A.canted = z->canted;
-  A.species = z->d_species_perm; A.dirs = z->d_dirs_perm; A.pair_pq = z->d_pair_pq; A.pair_d = z->d_pair_d;
-  A.pair_Y = z->d_pair_Y; A.g_start = z->d_g_start; A.g_L2 = z->d_g_L2; A.g_c = z->d_g_c;
+  A.nL = z0->nL; A.nL2 = z0->nL2; A.lmax = z0->lmax; A.kap = z0->kap; A.n = c.n; A.canted = z0->canted;
+  A.n_lz = c.n_lz;
+  int max_units = 0, any_pad = 0;
+  for (int j = 0; j < c.n_lz; ++j) {
+    const must_liz* z = c.lz[j];
+    LizDev& d = A.L[j];
+    d.N = z->N; d.n_pairs = z->n_pairs; d.pad = c.pad[j];
+    d.species = z->d_species_perm; d.dirs = z->d_dirs_perm; d.pair_pq = z->d_pair_pq; d.pair_d = z->d_pair_d;
+    d.pair_Y = z->d_pair_Y;
+    max_units = std::max(max_units, d.n_pairs + d.N + d.pad);
+    any_pad |= (d.pad > 0);
+  }
+  A.g_start = z0->d_g_start; A.g_L2 = z0->d_g_L2; A.g_c = z0->d_g_c;
   A.e0 = c.e0; A.nEc = c.nEc; A.nE = c.nE; A.nspin = c.nspin; A.n_species = c.n_species;
   A.E = c.E; A.tinv = c.tinv; A.M64 = c.M64; A.M32 = c.M32; A.ld = c.ld; A.stride = c.stride; A.scale = c.scale;
-  A.items_per_e = z->canted ? 1 : c.nspin;
+  A.items_per_e = z0->canted ? 1 : c.nspin;
   A.scale64 = c.scale64;
   A.m64_df = c.m64_df;
-  launch_assemble(A, st);
+  if (any_pad) {   // padding sites: zero their coupling blocks first
+    const size_t items = size_t(A.items_per_e) * c.nEc * c.n_lz;
+    if (c.M64) cudaMemsetAsync(c.M64, 0, items * c.stride * 16, st);
+    if (c.M32) cudaMemsetAsync(c.M32, 0, items * c.stride * 8, st);
+  }
+  launch_assemble(A, max_units, st);
 }

@@ -39,17 +39,19 @@ __device__ __forceinline__ float cnormf(cf a) { return a.x * a.x + a.y * a.y; }
 //   panel, rank-1 update restricted to the leaf), then solve the leaf's rows
 //   of the remaining panel columns (U block, staged in shared memory) and
 //   update the rows below with one pass over the remaining columns.
-// Each row update loads the row segment into registers with independent
-// loads.  Panel traffic ~ m (nbe^2/(2 LEAF) + nbe LEAF/2) elements instead of
-// m nbe^2/2 for column-at-a-time updates of the whole panel.
+// Every thread loads all of its rows (up to RPT) before updating them, and
+// the rank-1 update of column c also yields the candidates of the pivot
+// search of column c+1, so each column costs two passes over its rows.
 constexpr int PANEL_W = 64;
 constexpr int LEAF = 8;
+constexpr int PPT = 512;   // threads of the panel kernel
+constexpr int RPT = 4;     // rows per thread per pass
 
-__global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int r,
-                                                     int k0, int nbe, int* __restrict__ piv0, int* __restrict__ status,
-                                                     const int* __restrict__ conv) {
-  __shared__ float sv[PT / 32];
-  __shared__ int si[PT / 32];
+__global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int r,
+                                                      int k0, int nbe, int* __restrict__ piv0, int* __restrict__ status,
+                                                      const int* __restrict__ conv) {
+  __shared__ float sv[PPT / 32];
+  __shared__ int si[PPT / 32];
   __shared__ int s_p;
   __shared__ cf prow[LEAF];
   __shared__ cf Ub[LEAF][PANEL_W];     // leaf rows of the remaining panel columns
@@ -59,16 +61,25 @@ __global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, si
   int* piv = piv0 + size_t(item) * r;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int pend = k0 + nbe;
+  bool carried = false;        // this thread's pivot candidate for the next column is known
+  float cbest = -1.0f;
+  int cbi = 0;
   for (int lb = 0; lb < nbe; lb += LEAF) {
     const int c0 = k0 + lb;
     const int lw = min(LEAF, nbe - lb);
     const int le = c0 + lw;             // leaf columns [c0, le)
+    carried = false;
     // (a) leaf columns one by one
     for (int c = c0; c < le; ++c) {
-      const cf* col = A + size_t(c) * ld;
       float best = -1.0f;
       int bi = c;
-      for (int i = c + tid; i < r; i += PT) argmax_merge(best, bi, cnormf(col[i]), i);
+      if (carried) {
+        best = cbest;
+        bi = cbi;
+      } else {
+        const cf* col = A + size_t(c) * ld;
+        for (int i = c + tid; i < r; i += PPT) argmax_merge(best, bi, cnormf(col[i]), i);
+      }
       for (int o = 16; o > 0; o >>= 1) {
         const float v2 = __shfl_down_sync(0xffffffffu, best, o);
         const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
@@ -79,7 +90,7 @@ __global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, si
       if (tid == 0) {
         float b = sv[0];
         int p = si[0];
-        for (int w = 1; w < PT / 32; ++w) argmax_merge(b, p, sv[w], si[w]);
+        for (int w = 1; w < PPT / 32; ++w) argmax_merge(b, p, sv[w], si[w]);
         if (!(b > 0.0f)) status[item] = ST_SINGULAR;
         piv[c] = p;
         s_p = p;
@@ -87,7 +98,7 @@ __global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, si
       __syncthreads();
       const int p = s_p;
       if (p != c)
-        for (int cc = k0 + tid; cc < pend; cc += PT) {
+        for (int cc = k0 + tid; cc < pend; cc += PPT) {
           cf* cp = A + size_t(cc) * ld;
           const cf t = cp[c];
           cp[c] = cp[p];
@@ -98,21 +109,42 @@ __global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, si
       if (tid < width) prow[tid] = A[size_t(c + tid) * ld + c];
       __syncthreads();
       const cf d = prow[0];
+      carried = false;
       if (cnormf(d) > 0.0f) {
         const cf inv = cinvf(d);
-        for (int i = c + 1 + tid; i < n; i += PT) {
-          cf v[LEAF];
+        const bool track = (c + 1 < le);
+        float nb = -1.0f;
+        int nbi = c + 1;
+        for (int i0 = c + 1; i0 < n; i0 += PPT * RPT) {
+          cf v[RPT][LEAF];
 #pragma unroll
-          for (int q = 0; q < LEAF; ++q)
-            if (q < width) v[q] = A[size_t(c + q) * ld + i];
-          const cf l = cmulf(v[0], inv);
-          A[size_t(c) * ld + i] = l;
+          for (int t = 0; t < RPT; ++t) {
+            const int i = i0 + tid + t * PPT;
+            if (i < n)
 #pragma unroll
-          for (int q = 1; q < LEAF; ++q)
-            if (q < width) {
-              cfmsf(v[q], l, prow[q]);
-              A[size_t(c + q) * ld + i] = v[q];
+              for (int q = 0; q < LEAF; ++q)
+                if (q < width) v[t][q] = A[size_t(c + q) * ld + i];
+          }
+#pragma unroll
+          for (int t = 0; t < RPT; ++t) {
+            const int i = i0 + tid + t * PPT;
+            if (i < n) {
+              const cf l = cmulf(v[t][0], inv);
+              A[size_t(c) * ld + i] = l;
+#pragma unroll
+              for (int q = 1; q < LEAF; ++q)
+                if (q < width) {
+                  cfmsf(v[t][q], l, prow[q]);
+                  A[size_t(c + q) * ld + i] = v[t][q];
+                }
+              if (track && i < r) argmax_merge(nb, nbi, cnormf(v[t][1]), i);
             }
+          }
+        }
+        if (track) {
+          carried = true;
+          cbest = nb;
+          cbi = nbi;
         }
       }
       __syncthreads();
@@ -120,7 +152,7 @@ __global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, si
     const int rest = pend - le;          // remaining panel columns [le, pend)
     if (rest <= 0) continue;
     // (b) U block: rows [c0, le) of the remaining columns, L_leaf^{-1} A
-    for (int t = tid; t < lw * lw; t += PT) {
+    for (int t = tid; t < lw * lw; t += PPT) {
       const int i = t % lw, j = t / lw;
       Ll[i][j] = A[size_t(c0 + j) * ld + c0 + i];
     }
@@ -146,24 +178,24 @@ __global__ void __launch_bounds__(PT) panel32_kernel(float2* __restrict__ A0, si
     }
     __syncthreads();
     // (c) rows below the leaf: A[i, rest] -= L[i, leaf] U[leaf, rest]
-    for (int i = le + tid; i < n; i += PT) {
+    for (int i = le + tid; i < n; i += PPT) {
       cf l[LEAF];
 #pragma unroll
       for (int j = 0; j < LEAF; ++j)
         if (j < lw) l[j] = A[size_t(c0 + j) * ld + i];
-      for (int q0 = 0; q0 < rest; q0 += 16) {
-        cf v[16];
+      for (int q0 = 0; q0 < rest; q0 += 8) {
+        cf v[8];
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
+        for (int q = 0; q < 8; ++q)
           if (q0 + q < rest) v[q] = A[size_t(le + q0 + q) * ld + i];
 #pragma unroll
         for (int j = 0; j < LEAF; ++j)
           if (j < lw)
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+            for (int q = 0; q < 8; ++q)
               if (q0 + q < rest) cfmsf(v[q], l[j], Ub[j][q0 + q]);
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
+        for (int q = 0; q < 8; ++q)
           if (q0 + q < rest) A[size_t(le + q0 + q) * ld + i] = v[q];
       }
     }
@@ -368,18 +400,31 @@ __device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al,
   sl = fmaf(al, bh, sl);
 }
 
-__global__ void residual_df_kernel(const float4* __restrict__ M0, size_t stride, int ld, int n, int kap,
-                                   const double2* __restrict__ X0, double2* __restrict__ R0,
-                                   const int* __restrict__ conv, unsigned long long* __restrict__ work) {
+// X (FP64) -> double-float pairs (re_hi, im_hi, re_lo, im_lo), once per residual.
+__global__ void split_x_kernel(const double2* __restrict__ X, float4* __restrict__ Xd, size_t count,
+                               const int* __restrict__ conv, size_t per_item) {
+  const size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  if (conv[t / per_item]) return;
+  const double2 x = X[t];
+  const float xr = float(x.x), xi = float(x.y);
+  Xd[t] = make_float4(xr, xi, float(x.x - double(xr)), float(x.y - double(xi)));
+}
+
+__global__ void __launch_bounds__(1024) residual_df_kernel(const float4* __restrict__ M0, size_t stride, int ld, int n,
+                                                          int kap, const float4* __restrict__ Xd0,
+                                                          double2* __restrict__ R0, const int* __restrict__ conv,
+                                                          unsigned long long* __restrict__ work) {
   extern __shared__ float4 Xd[];   // [64][kap]: (re_hi, im_hi, re_lo, im_lo)
   const int item = blockIdx.y;
   if (conv[item]) return;
   if (work && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(work, 1ull);
   const float4* M = M0 + size_t(item) * stride;
-  const double2* X = X0 + size_t(item) * n * kap;
+  const float4* X = Xd0 + size_t(item) * n * kap;
   const int tid = threadIdx.x;
   const int row = blockIdx.x * 64 + (tid & 63);
   const int c0 = (tid >> 6) * 4;
+  const int rowc = min(row, n - 1);      // clamped row for loads (results of row >= n are dropped)
   float rh[4], rl[4], ih[4], il[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
@@ -388,25 +433,24 @@ __global__ void residual_df_kernel(const float4* __restrict__ M0, size_t stride,
     __syncthreads();
     for (int t = tid; t < kn * kap; t += blockDim.x) {
       const int k = t % kn, c = t / kn;
-      const double2 x = X[size_t(c) * n + k0 + k];
-      const float xr = float(x.x), xi = float(x.y);
-      Xd[k * kap + c] = make_float4(xr, xi, float(x.x - double(xr)), float(x.y - double(xi)));
+      Xd[k * kap + c] = X[size_t(c) * n + k0 + k];
     }
     __syncthreads();
-    if (row < n) {
-      for (int k = 0; k < kn; ++k) {
-        const float4 m = M[size_t(k0 + k) * ld + row];
+    const float4* Mk = M + size_t(k0) * ld + rowc;
+    float4 mnext = Mk[0];
+    for (int k = 0; k < kn; ++k) {
+      const float4 m = mnext;
+      if (k + 1 < kn) mnext = Mk[size_t(k + 1) * ld];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (c0 + q < kap) {
-            const float4 x = Xd[k * kap + c0 + q];
-            // re += mr xr - mi xi ; im += mr xi + mi xr
-            df_mac(rh[q], rl[q], m.x, m.z, x.x, x.z);
-            df_mac(rh[q], rl[q], -m.y, -m.w, x.y, x.w);
-            df_mac(ih[q], il[q], m.x, m.z, x.y, x.w);
-            df_mac(ih[q], il[q], m.y, m.w, x.x, x.z);
-          }
-      }
+      for (int q = 0; q < 4; ++q)
+        if (c0 + q < kap) {
+          const float4 x = Xd[k * kap + c0 + q];
+          // re += mr xr - mi xi ; im += mr xi + mi xr
+          df_mac(rh[q], rl[q], m.x, m.z, x.x, x.z);
+          df_mac(rh[q], rl[q], -m.y, -m.w, x.y, x.w);
+          df_mac(ih[q], il[q], m.x, m.z, x.y, x.w);
+          df_mac(ih[q], il[q], m.y, m.w, x.x, x.z);
+        }
     }
   }
   if (row < n) {
@@ -432,7 +476,7 @@ __global__ void residual_df_kernel(const float4* __restrict__ M0, size_t stride,
 // remaining rows, each loading its row segment of L (or U) with independent
 // loads.
 template <int G>
-__global__ void __launch_bounds__(256) correct_kernel(const float2* __restrict__ A0, size_t stride, int ld, int n,
+__global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__ A0, size_t stride, int ld, int n,
                                                       int kap, const int* __restrict__ perm0,
                                                       const double* __restrict__ scale0,
                                                       const double2* __restrict__ Sinv0,
@@ -493,18 +537,21 @@ __global__ void __launch_bounds__(256) correct_kernel(const float2* __restrict__
     }
     __syncthreads();
     for (int i = je + tid; i < n; i += T) {
-      cf lrow[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < bs) lrow[j] = A[size_t(jb + j) * ld + i];
       cf acc[G];
 #pragma unroll
       for (int c = 0; c < G; ++c) acc[c] = w[i * G + c];
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < bs)
+      for (int h = 0; h < 32; h += 16) {
+        cf lrow[16];
 #pragma unroll
-          for (int c = 0; c < G; ++c) cfmsf(acc[c], lrow[j], w[(jb + j) * G + c]);
+        for (int j = 0; j < 16; ++j)
+          if (h + j < bs) lrow[j] = A[size_t(jb + h + j) * ld + i];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (h + j < bs)
+#pragma unroll
+            for (int c = 0; c < G; ++c) cfmsf(acc[c], lrow[j], w[(jb + h + j) * G + c]);
+      }
 #pragma unroll
       for (int c = 0; c < G; ++c) w[i * G + c] = acc[c];
     }
@@ -577,18 +624,21 @@ __global__ void __launch_bounds__(256) correct_kernel(const float2* __restrict__
     }
     __syncthreads();
     for (int i = tid; i < jb; i += T) {
-      cf urow[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < bs) urow[j] = A[size_t(jb + j) * ld + i];
       cf acc[G];
 #pragma unroll
       for (int c = 0; c < G; ++c) acc[c] = w[i * G + c];
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < bs)
+      for (int h = 0; h < 32; h += 16) {
+        cf urow[16];
 #pragma unroll
-          for (int c = 0; c < G; ++c) cfmsf(acc[c], urow[j], w[(jb + j) * G + c]);
+        for (int j = 0; j < 16; ++j)
+          if (h + j < bs) urow[j] = A[size_t(jb + h + j) * ld + i];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (h + j < bs)
+#pragma unroll
+            for (int c = 0; c < G; ++c) cfmsf(acc[c], urow[j], w[(jb + h + j) * G + c]);
+      }
 #pragma unroll
       for (int c = 0; c < G; ++c) w[i * G + c] = acc[c];
     }
@@ -666,7 +716,7 @@ size_t mixed_item_bytes(int n, int ld, int kap) {
   return a256(size_t(ld) * n * 8)          // M32
          + a256(size_t(n) * 8)             // scale
          + a256(size_t(n) * 4)             // perm
-         + 2 * a256(size_t(n) * kap * 16)  // X, R
+         + 3 * a256(size_t(n) * kap * 16)  // X, R, X as double-float pairs
          + a256(size_t(kap) * kap * 16)    // Sinv
          + 768                             // norms, previous norms, conv, error word
          + tc_pack_bytes_per_item(n);      // tensor-core operand packs
@@ -681,6 +731,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   int* perm = reinterpret_cast<int*>(take(size_t(items) * n * 4));
   double2* X = reinterpret_cast<double2*>(take(size_t(items) * n * kap * 16));
   double2* R = reinterpret_cast<double2*>(take(size_t(items) * n * kap * 16));
+  float4* Xdf = reinterpret_cast<float4*>(take(size_t(items) * n * kap * 16));
   double2* Sinv = reinterpret_cast<double2*>(take(size_t(items) * kap * kap * 16));
   double* norms = reinterpret_cast<double*>(take(size_t(items) * 16));
   double* prevn = reinterpret_cast<double*>(take(size_t(items) * 8));
@@ -704,7 +755,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     const int nbe = std::min(nb, r - k0);
     {
       ProfScope ps(PH_PANEL, st);
-      panel32_kernel<<<items, PT, 0, st>>>(M32, stride, ld, n, r, k0, nbe, c.piv, c.status, conv);
+      panel32_kernel<<<items, PPT, 0, st>>>(M32, stride, ld, n, r, k0, nbe, c.piv, c.status, conv);
       prof_launched(PH_PANEL, 1, items);
     }
     {
@@ -761,22 +812,26 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     const bool first = (it == 0);
     if (!first) {
       ProfScope ps(PH_RESIDUAL, st);
-      if (c.opts.residual == 1)
+      if (c.opts.residual == 1) {
+        const size_t cnt = size_t(items) * n * kap;
+        split_x_kernel<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(X, Xdf, cnt, conv, size_t(n) * kap);
         residual_df_kernel<<<gres, tres, size_t(64) * kap * 16, st>>>(reinterpret_cast<const float4*>(c.M64), stride,
-                                                                        ld, n, kap, X, R, conv,
+                                                                        ld, n, kap, Xdf, R, conv,
                                                                         prof_work_counter(PH_RESIDUAL));
-      else
+        prof_launched(PH_RESIDUAL, 1);
+      } else {
         residual64_kernel<<<gres, tres, smem_res, st>>>(c.M64, stride, ld, n, kap, X, R, conv,
                                                         prof_work_counter(PH_RESIDUAL));
+      }
       prof_launched(PH_RESIDUAL, 1);
     }
     {
       ProfScope ps(PH_CORRECT, st);
       if (G == 8)
-        correct_kernel<8><<<gcorr, 256, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
+        correct_kernel<8><<<gcorr, 512, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
                                                          conv, first, prof_work_counter(PH_CORRECT));
       else
-        correct_kernel<4><<<gcorr, 256, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
+        correct_kernel<4><<<gcorr, 512, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
                                                          conv, first, prof_work_counter(PH_CORRECT));
       prof_launched(PH_CORRECT, 1);
     }

@@ -78,6 +78,20 @@ unsigned long long* prof_work_counter(int phase) {
   return g_dwork + phase;
 }
 
+int prof_suspend() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  const int was = g_enabled.load();
+  g_enabled.store(0);
+  return was;
+}
+
+void prof_resume(int state) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_enabled.store(state);
+}
+
+void prof_add_launches(long long n) { g_launches.fetch_add(n); }
+
 extern "C" {
 
 void must_profile_enable(int on) {

@@ -37,3 +37,10 @@ void prof_launched(int phase, int n, long long items = 0);
 // Device counter (items processed) for phases whose work depends on data
 // (refinement kernels skip converged items), or NULL when profiling is off.
 unsigned long long* prof_work_counter(int phase);
+
+// Suspend event recording (returns the previous state) during graph capture.
+int prof_suspend();
+void prof_resume(int state);
+// Adjust the global launch counter (graph replays add their kernel count).
+void prof_add_launches(long long n);
+extern "C" long long must_launch_count(void);

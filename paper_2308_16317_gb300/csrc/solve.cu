@@ -11,6 +11,7 @@
 #include "solver.h"
 #include "mixed.h"
 #include "prof.h"
+#include "tc_gemm.h"
 
 namespace {
 
@@ -73,69 +74,117 @@ extern "C" size_t must_workspace_bytes(const must_liz* z, int32_t n_items, const
   return stage + size_t(n_items) * item_bytes(z->n, ld, z->kap, o.precision) + 4096;
 }
 
-// One LIZ, all energies; workspace already validated.  tau_dev/status_dev are
-// device pointers to [n_out][nE][kap][kap] / [n_out][nE] (status may be NULL).
-static must_status solve_one(const must_liz* z, int nE, const double2* E_dev, const double2* tinv_dev,
-                             int n_species, int nspin, const must_solve_opts& o, char* ws, size_t ws_left,
-                             double2* tau_dev, int* status_dev, cudaStream_t st) {
-  const int n = z->n, ld = ld_of(n), kap = z->kap, r = n - kap;
-  const int ipe = z->canted ? 1 : nspin;
-  const size_t per = item_bytes(n, ld, kap, o.precision);
-  int nEc = int(std::min<size_t>(size_t(nE), ws_left / (per * ipe)));
-  if (nEc < 1) {
-    must_set_error("workspace too small: need at least %zu bytes for one energy", per * ipe);
-    return MUST_ENOMEM;
-  }
-  const int max_items = nEc * ipe;
-  // carve
+// One chunk: items (LIZ j, spin, energy) of the (padded) order c.n, all in
+// the workspace `ws`.  Carves per-item storage, assembles, eliminates and
+// writes tau_00 / status through out_index.
+static must_status run_chunk(AsmChunk c, int items, const ChunkIndex& ci, const must_solve_opts& o, char* ws,
+                             size_t ws_left, double2* tau_dev, int* status_dev, cudaStream_t st) {
+  const int n = c.n, ld = ld_of(n), kap = c.lz[0]->kap, r = n - kap;
   char* cur = ws;
   double2* M64 = reinterpret_cast<double2*>(cur);
   const size_t stride = size_t(ld) * n;
-  cur += a256(size_t(max_items) * stride * 16);
+  cur += a256(size_t(items) * stride * 16);
   int* piv = reinterpret_cast<int*>(cur);
-  cur += a256(size_t(max_items) * n * 4);
+  cur += a256(size_t(items) * n * 4);
   int* st_item = reinterpret_cast<int*>(cur);
-  cur += a256(size_t(max_items) * 4);
+  cur += a256(size_t(items) * 4);
   int* out_index = reinterpret_cast<int*>(cur);
-  cur += a256(size_t(max_items) * 4);
+  cur += a256(size_t(items) * 4);
   double* scale64 = reinterpret_cast<double*>(cur);
-  cur += a256(size_t(max_items) * n * 8);
+  cur += a256(size_t(items) * n * 8);
   char* mixed_ws = cur;
-  const size_t mixed_bytes = (o.precision != MUST_FP64) ? size_t(max_items) * mixed_item_bytes(n, ld, kap) : 0;
+  const size_t mixed_bytes = (o.precision != MUST_FP64) ? size_t(items) * mixed_item_bytes(n, ld, kap) : 0;
   if (size_t(cur - ws) + mixed_bytes > ws_left) {
     must_set_error("workspace layout overflow");
     return MUST_ENOMEM;
   }
-  for (int e0 = 0; e0 < nE; e0 += nEc) {
-    const int ne = std::min(nEc, nE - e0);
-    const int items = ne * ipe;
-    launch_chunk_index(out_index, st_item, items, ne, nE, e0, z->canted, st);
-    AsmChunk c;
-    c.liz = z; c.e0 = e0; c.nEc = ne; c.nE = nE; c.nspin = nspin; c.n_species = n_species;
-    c.E = E_dev; c.tinv = tinv_dev; c.M64 = M64; c.ld = ld; c.stride = stride;
-    if (o.precision == MUST_FP64) {
-      c.M32 = nullptr;
-      c.scale = o.equilibrate ? scale64 : nullptr;
-      c.scale64 = o.equilibrate ? 1 : 0;
-      c.m64_df = 0;
-      launch_assemble_chunk(c, st);
-      lu64_factor(M64, stride, ld, n, r, items, 32, piv, st_item, st);
-      schur_inv64(M64, stride, ld, n, kap, items, c.scale, tau_dev, out_index, st_item, status_dev, st);
-    } else {
-      c.scale64 = 0;
-      c.m64_df = o.residual == 1 ? 1 : 0;
-      MixedChunk mc;
-      mc.asmc = c; mc.n = n; mc.ld = ld; mc.kap = kap; mc.items = items; mc.M64 = M64; mc.stride = stride;
-      mc.piv = piv; mc.status = st_item; mc.out_index = out_index; mc.tau = tau_dev; mc.status_out = status_dev;
-      mc.ws = mixed_ws; mc.opts = o;
-      must_status s = mixed_solve_chunk(mc, st);
-      if (s != MUST_OK) return s;
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) { must_set_error("kernel launch failed: %s", cudaGetErrorString(e)); return MUST_ECUDA; }
+  launch_chunk_index(out_index, st_item, items, ci, st);
+  c.M64 = M64;
+  c.ld = ld;
+  c.stride = stride;
+  if (o.precision == MUST_FP64) {
+    c.M32 = nullptr;
+    c.scale = o.equilibrate ? scale64 : nullptr;
+    c.scale64 = o.equilibrate ? 1 : 0;
+    c.m64_df = 0;
+    launch_assemble_chunk(c, st);
+    lu64_factor(M64, stride, ld, n, r, items, 32, piv, st_item, st);
+    schur_inv64(M64, stride, ld, n, kap, items, c.scale, tau_dev, out_index, st_item, status_dev, st);
+  } else {
+    c.scale64 = 0;
+    c.m64_df = o.residual == 1 ? 1 : 0;
+    MixedChunk mc;
+    mc.asmc = c; mc.n = n; mc.ld = ld; mc.kap = kap; mc.items = items; mc.M64 = M64; mc.stride = stride;
+    mc.piv = piv; mc.status = st_item; mc.out_index = out_index; mc.tau = tau_dev; mc.status_out = status_dev;
+    mc.ws = mixed_ws; mc.opts = o;
+    must_status s = mixed_solve_chunk(mc, st);
+    if (s != MUST_OK) return s;
   }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { must_set_error("kernel launch failed: %s", cudaGetErrorString(e)); return MUST_ECUDA; }
   return MUST_OK;
 }
+
+// LIZs lz[0..count) padded to the common order n (pad[j] identity sites in
+// front of LIZ j's own sites), every energy and spin, in chunks that fit the
+// workspace: several whole LIZs per chunk when they fit, else one LIZ's
+// energies in pieces.  tau_dev/status_dev are the call's whole output arrays.
+static must_status solve_group(const must_liz* const* lz, const int* liz_global, const int* pad, int count, int n,
+                               int nE, const double2* E_dev, const double2* tinv_dev, int n_species, int nspin,
+                               const must_solve_opts& o, char* ws, size_t ws_left, double2* tau_dev, int* status_dev,
+                               cudaStream_t st) {
+  const int kap = lz[0]->kap, ld = ld_of(n);
+  const int ipe = lz[0]->canted ? 1 : nspin, n_out = lz[0]->canted ? 1 : nspin;
+  const size_t per = item_bytes(n, ld, kap, o.precision);
+  const size_t cap = ws_left / per;
+  if (cap < size_t(ipe)) {
+    must_set_error("workspace too small: need at least %zu bytes for one energy", per * ipe);
+    return MUST_ENOMEM;
+  }
+  AsmChunk c;
+  c.n = n; c.nE = nE; c.nspin = nspin; c.n_species = n_species; c.E = E_dev; c.tinv = tinv_dev;
+  ChunkIndex ci;
+  ci.ipe = ipe; ci.nE = nE; ci.n_out = n_out;
+  if (cap >= size_t(ipe) * nE) {
+    const int per_chunk = int(std::min<size_t>(MUST_CHUNK_LIZ, cap / (size_t(ipe) * nE)));
+    for (int j0 = 0; j0 < count; j0 += per_chunk) {
+      const int m = std::min(per_chunk, count - j0);
+      c.n_lz = m; c.e0 = 0; c.nEc = nE;
+      ci.n_lz = m; ci.ne = nE; ci.e0 = 0;
+      for (int j = 0; j < m; ++j) {
+        c.lz[j] = lz[j0 + j];
+        c.pad[j] = pad[j0 + j];
+        ci.liz_global[j] = liz_global[j0 + j];
+      }
+      must_status s = run_chunk(c, m * ipe * nE, ci, o, ws, ws_left, tau_dev, status_dev, st);
+      if (s != MUST_OK) return s;
+    }
+    return MUST_OK;
+  }
+  const int nEc = int(cap / ipe);
+  for (int j = 0; j < count; ++j)
+    for (int e0 = 0; e0 < nE; e0 += nEc) {
+      const int ne = std::min(nEc, nE - e0);
+      c.n_lz = 1; c.lz[0] = lz[j]; c.pad[0] = pad[j]; c.e0 = e0; c.nEc = ne;
+      ci.n_lz = 1; ci.liz_global[0] = liz_global[j]; ci.ne = ne; ci.e0 = e0;
+      must_status s = run_chunk(c, ne * ipe, ci, o, ws, ws_left, tau_dev, status_dev, st);
+      if (s != MUST_OK) return s;
+    }
+  return MUST_OK;
+}
+
+// One LIZ, all energies (no padding).
+static must_status solve_one(const must_liz* z, int nE, const double2* E_dev, const double2* tinv_dev,
+                             int n_species, int nspin, const must_solve_opts& o, char* ws, size_t ws_left,
+                             double2* tau_dev, int* status_dev, cudaStream_t st) {
+  const int zero = 0;
+  return solve_group(&z, &zero, &zero, 1, z->n, nE, E_dev, tinv_dev, n_species, nspin, o, ws, ws_left, tau_dev,
+                     status_dev, st);
+}
+
+// Sites per padding quantum for the batched call (LIZ sizes are rounded up to
+// a multiple so that LIZs of nearby size share launches).
+static int g_bucket_sites = 4;
 
 static must_status solve_common(int n_liz, const must_liz* const* lizs, int nE, const double* E, const double* tinv,
                                 int n_species, int nspin, const must_solve_opts* opts, void* workspace,
@@ -180,12 +229,33 @@ static must_status solve_common(int n_liz, const must_liz* const* lizs, int nE, 
   if (!dTau) { Taud = reinterpret_cast<double2*>(cur); cur += a256(bTau); }
   if (!dSt) { Std = reinterpret_cast<int*>(cur); cur += a256(bSt); }
   const size_t left = ws_bytes - size_t(cur - ws);
-  for (int i = 0; i < n_liz; ++i) {
-    const size_t tau_off = size_t(i) * n_out * nE * kap * kap;
-    const size_t st_off = size_t(i) * n_out * nE;
-    must_status s = solve_one(lizs[i], nE, Ed, Td, n_species, nspin, o, cur, left, Taud + tau_off,
-                              Std ? Std + st_off : nullptr, st);
+  if (n_liz == 1) {
+    must_status s = solve_one(lizs[0], nE, Ed, Td, n_species, nspin, o, cur, left, Taud, Std, st);
     if (s != MUST_OK) return s;
+  } else {
+    // buckets of equal padded order, largest first
+    std::vector<int> idx(n_liz);
+    for (int i = 0; i < n_liz; ++i) idx[i] = i;
+    const int q = std::max(1, g_bucket_sites);
+    auto padded_sites = [&](int i) { return ((lizs[i]->N + q - 1) / q) * q; };
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return padded_sites(a) > padded_sites(b); });
+    size_t b0 = 0;
+    while (b0 < idx.size()) {
+      size_t b1 = b0;
+      const int Np = padded_sites(idx[b0]);
+      while (b1 < idx.size() && padded_sites(idx[b1]) == Np) ++b1;
+      std::vector<const must_liz*> g;
+      std::vector<int> gi, gp;
+      for (size_t k = b0; k < b1; ++k) {
+        g.push_back(lizs[idx[k]]);
+        gi.push_back(idx[k]);
+        gp.push_back(Np - lizs[idx[k]]->N);
+      }
+      must_status s = solve_group(g.data(), gi.data(), gp.data(), int(g.size()), Np * kap, nE, Ed, Td, n_species,
+                                  nspin, o, cur, left, Taud, Std, st);
+      if (s != MUST_OK) return s;
+      b0 = b1;
+    }
   }
   if (!dTau) TRYC(cudaMemcpyAsync(tau00, Taud, bTau, cudaMemcpyDeviceToHost, st));
   if (!dSt && status) TRYC(cudaMemcpyAsync(status, Std, bSt, cudaMemcpyDeviceToHost, st));
@@ -212,24 +282,34 @@ extern "C" must_status must_tau00_batch(int32_t n_liz, const must_liz* const* li
 
 extern "C" size_t must_batch_workspace_bytes(int32_t n_liz, const must_liz* const* lizs, int32_t n_items_per_liz,
                                              const must_solve_opts* opts) {
-  size_t mx = 0;
-  for (int i = 0; i < n_liz; ++i) mx = std::max(mx, must_workspace_bytes(lizs[i], n_items_per_liz, opts));
-  // staging for every LIZ's outputs
-  const int kap = n_liz > 0 ? lizs[0]->kap : 0;
-  return mx + a256(size_t(n_liz) * n_items_per_liz * kap * kap * 16) + a256(size_t(n_liz) * n_items_per_liz * 4);
+  if (n_liz < 1 || !lizs || n_items_per_liz < 1) return 0;
+  must_solve_opts o;
+  must_default_opts(&o);
+  if (opts) o = *opts;
+  const int q = std::max(1, g_bucket_sites);
+  int Nmax = 0;
+  for (int i = 0; i < n_liz; ++i) Nmax = std::max(Nmax, ((lizs[i]->N + q - 1) / q) * q);
+  const int kap = lizs[0]->kap, n = Nmax * kap;
+  const size_t per = item_bytes(n, ld_of(n), kap, o.precision);
+  // one whole LIZ (all its items) at the largest padded order, plus staging
+  // of every LIZ's outputs; more workspace lets several LIZs share launches
+  return size_t(n_items_per_liz) * per + a256(size_t(n_items_per_liz) * 16) +
+         a256(size_t(n_items_per_liz) * 4 * (lizs[0]->lmax + 1) * 16) +
+         a256(size_t(n_liz) * n_items_per_liz * kap * kap * 16) + a256(size_t(n_liz) * n_items_per_liz * 4) + 4096;
 }
 
-__global__ void chunk_index_kernel(int* out_index, int* status, int items, int ne, int nE, int e0, int canted) {
+__global__ void chunk_index_kernel(int* out_index, int* status, int items, ChunkIndex ci) {
   const int it = blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= items) return;
-  const int el = canted ? it : it % ne;
-  const int s = canted ? 0 : it / ne;
-  out_index[it] = s * nE + e0 + el;
+  const int el = it % ci.ne;
+  const int grp = it / ci.ne;            // lz * ipe + spin
+  const int lz = grp / ci.ipe, s = grp % ci.ipe;
+  out_index[it] = (ci.liz_global[lz] * ci.n_out + s) * ci.nE + ci.e0 + el;
   status[it] = 0;
 }
 
-void launch_chunk_index(int* out_index, int* status, int items, int ne, int nE, int e0, int canted, cudaStream_t st) {
-  chunk_index_kernel<<<(items + 127) / 128, 128, 0, st>>>(out_index, status, items, ne, nE, e0, canted);
+void launch_chunk_index(int* out_index, int* status, int items, const ChunkIndex& ci, cudaStream_t st) {
+  chunk_index_kernel<<<(items + 127) / 128, 128, 0, st>>>(out_index, status, items, ci);
   prof_launched(PH_OTHER, 1);
 }
 
@@ -318,4 +398,106 @@ extern "C" must_status must_tau00_solve_static(const must_liz* z, int32_t nE, co
   return solve_one(z, nE, reinterpret_cast<const double2*>(E), reinterpret_cast<const double2*>(tinv), n_species,
                    nspin, o, ws, MUST_STATIC_SCRATCH_BYTES, reinterpret_cast<double2*>(tau00), status,
                    static_cast<cudaStream_t>(stream));
+}
+
+// --------------------------------------------------------------------------
+// Batched plans: the whole launch sequence of one must_tau00_batch call with
+// fixed (device) arguments captured once into a CUDA graph and replayed.
+struct must_plan {
+  cudaGraphExec_t exec;
+  cudaGraph_t graph;
+  long long kernels;      // kernel nodes per replay (for the launch counter)
+};
+
+extern "C" must_status must_plan_batch(int32_t n_liz, const must_liz* const* lizs, int32_t nE, const double* E,
+                                       const double* tinv, int32_t n_species, int32_t nspin,
+                                       const must_solve_opts* opts, void* workspace, size_t ws_bytes, double* tau00,
+                                       int32_t* status, must_plan** out) {
+  if (!out) { must_set_error("must_plan_batch: out is NULL"); return MUST_EINVAL; }
+  *out = nullptr;
+  if (!E || !tinv || !tau00 || !workspace || !must_is_device_ptr(E) || !must_is_device_ptr(tinv) ||
+      !must_is_device_ptr(tau00) || !must_is_device_ptr(workspace) || (status && !must_is_device_ptr(status))) {
+    must_set_error("must_plan_batch: E, tinv, tau00, status and workspace must be device memory");
+    return MUST_EINVAL;
+  }
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    must_set_error("must_plan_batch: cannot create a capture stream");
+    return MUST_ECUDA;
+  }
+  const int prof_was_on = prof_suspend();
+  const long long l0 = must_launch_count();
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+  must_status st = MUST_ECUDA;
+  cudaGraph_t g = nullptr;
+  if (e == cudaSuccess) {
+    st = solve_common(n_liz, lizs, nE, E, tinv, n_species, nspin, opts, workspace, ws_bytes, tau00, status, s);
+    e = cudaStreamEndCapture(s, &g);
+  }
+  const long long kernels = must_launch_count() - l0;
+  prof_resume(prof_was_on);
+  prof_add_launches(-kernels);   // capture enqueued nothing; replays count them
+  cudaStreamDestroy(s);
+  if (st != MUST_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    if (st == MUST_OK) {
+      must_set_error("must_plan_batch: stream capture failed: %s", cudaGetErrorString(e));
+      st = MUST_ECUDA;
+    }
+    return st;
+  }
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    must_set_error("must_plan_batch: graph instantiation failed: %s", cudaGetErrorString(e));
+    return MUST_ECUDA;
+  }
+  must_plan* p = new must_plan();
+  p->exec = x;
+  p->graph = g;
+  p->kernels = kernels;
+  *out = p;
+  return MUST_OK;
+}
+
+extern "C" must_status must_plan_launch(const must_plan* p, void* stream) {
+  if (!p) { must_set_error("must_plan_launch: NULL plan"); return MUST_EINVAL; }
+  const cudaError_t e = cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    must_set_error("must_plan_launch: %s", cudaGetErrorString(e));
+    return MUST_ECUDA;
+  }
+  prof_add_launches(p->kernels);
+  return MUST_OK;
+}
+
+extern "C" void must_plan_free(must_plan* p) {
+  if (!p) return;
+  cudaGraphExecDestroy(p->exec);
+  cudaGraphDestroy(p->graph);
+  delete p;
+}
+
+// Tuning knobs (set by the autotuner).
+extern "C" must_status must_tune_set(int32_t knob, int32_t value) {
+  switch (knob) {
+    case 0:   // sites per padding quantum of the batched call
+      if (value < 1 || value > 64) { must_set_error("bucket sites must be in [1, 64]"); return MUST_EINVAL; }
+      g_bucket_sites = value;
+      return MUST_OK;
+    case 1:   // tensor-core tile width (complex columns)
+      if (!tc_set_tile_n(value)) { must_set_error("tile width must be 128 or 256"); return MUST_EINVAL; }
+      return MUST_OK;
+  }
+  must_set_error("unknown tuning knob %d", knob);
+  return MUST_EINVAL;
+}
+
+extern "C" int32_t must_tune_get(int32_t knob) {
+  switch (knob) {
+    case 0: return g_bucket_sites;
+    case 1: return tc_get_tile_n();
+  }
+  return -1;
 }

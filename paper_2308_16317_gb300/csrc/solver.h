@@ -11,9 +11,17 @@ void launch_geom(int N, int lmax, const double* pos_perm, const int2* pq, int n_
 void launch_tinv(int nE, const double2* E, int n_pot, const double* V, double a, int lmax, double2* out,
                  cudaStream_t st);
 
-// Assembly of one chunk of energies e0 .. e0+nEc-1 of one LIZ.
+// Assembly of one chunk: energies e0 .. e0+nEc-1 of n_lz LIZs that share the
+// (padded) matrix order n.  LIZ j of the chunk occupies items
+// (j * items_per_e + spin) * nEc + e_local; its sites are placed after pad[j]
+// decoupled identity sites, so smaller LIZs can share launches with larger
+// ones without changing their Schur complement.
+#define MUST_CHUNK_LIZ 64
 struct AsmChunk {
-  const must_liz* liz;
+  int n_lz;
+  const must_liz* lz[MUST_CHUNK_LIZ];
+  int pad[MUST_CHUNK_LIZ];          // identity sites before the LIZ's own sites
+  int n;                            // chunk matrix order (kap * (N + pad), equal for all)
   int e0, nEc, nE, nspin, n_species;
   const double2* E;
   const double2* tinv;
@@ -33,5 +41,9 @@ void lu64_factor(double2* A, size_t stride, int ld, int n, int r, int n_items, i
 void schur_inv64(const double2* A, size_t stride, int ld, int n, int kap, int n_items, const double* scale,
                  double2* out, const int* out_index, int* status, int* status_out, cudaStream_t st);
 
-// solve.cu: out_index[it] = spin * nE + e0 + e_local, status[it] = 0
-void launch_chunk_index(int* out_index, int* status, int items, int ne, int nE, int e0, int canted, cudaStream_t st);
+// solve.cu: out_index[it] = (liz_global * n_out + spin) * nE + e0 + e_local, status[it] = 0
+struct ChunkIndex {
+  int n_lz, ipe, ne, nE, e0, n_out;
+  int liz_global[MUST_CHUNK_LIZ];
+};
+void launch_chunk_index(int* out_index, int* status, int items, const ChunkIndex& ci, cudaStream_t st);

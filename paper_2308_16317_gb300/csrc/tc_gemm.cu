@@ -13,10 +13,10 @@
 //   A'B'^T ~ A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
 // accumulated in one FP32 TMEM accumulator (the lo*lo term is dropped).
 //
-// One CTA (128 threads) computes a 128 x BN tile of C' (64 complex rows x BN
+// One CTA (256 threads) computes a 128 x BN tile of C' (64 complex rows x BN
 // complex columns): warp 0 lane 0 issues TMA loads into a STAGES-deep ring,
-// warp 1 lane 0 issues the MMAs (one per 32 bytes of K), and all four warps
-// read their 32 TMEM lanes and update C in place.  Every mbarrier wait is
+// warp 1 lane 0 issues the MMAs (one per 32 bytes of K), and all eight warps
+// (two per TMEM lane quarter, one per column half) update C in place.  Every mbarrier wait is
 // bounded; on time-out the kernel raises the workspace error word, drains its
 // own copies, frees its TMEM and returns.
 #include <cuda.h>
@@ -134,7 +134,7 @@ struct TcParams {
 };
 
 template <int BN, int STAGES>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
     tc_update_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                      const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
                      TcParams P) {
@@ -210,33 +210,36 @@ __global__ void __launch_bounds__(128, 1)
     mma_commit(&done);
   }
   __syncthreads();   // roles finished issuing (s_fail visible); the MMAs may still run
-  // prefetch this thread's C row segment while the MMAs run: real row rr of
-  // the tile is complex row i, component comp (re/im) -> consecutive lanes hit
-  // consecutive floats of a column (coalesced)
-  const int rr = row0 + warp * 32 + lane;
+  // Epilogue mapping: warp w reads TMEM lane quarter (w % 4) and the column
+  // half (w / 4) of the tile.  Real row rr of the tile is complex row i,
+  // component comp (re/im), so consecutive lanes hit consecutive floats of a
+  // column (coalesced).  The C segment is prefetched while the MMAs run.
+  constexpr int HALF = BN / 2;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int rr = row0 + quarter * 32 + lane;
   const int i = P.base + (rr >> 1);
   const int comp = rr & 1;
+  const int cbase = P.base + col0 + half * HALF;
   float* Cc = reinterpret_cast<float*>(P.C + size_t(item) * P.stride);
-  float cv[BN];
+  float cv[HALF];
   if (i < P.n) {
 #pragma unroll
-    for (int j = 0; j < BN; ++j) {
-      const int col = P.base + col0 + j;
+    for (int j = 0; j < HALF; ++j) {
+      const int col = cbase + j;
       cv[j] = (col < P.n) ? Cc[2 * (size_t(col) * P.ld + i) + comp] : 0.f;
     }
   }
-  // epilogue: every warp waits for the accumulator
   const bool have = mbar_wait(&done, 0);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (have && !s_fail) {
 #pragma unroll
-    for (int cc = 0; cc < BN; cc += 32) {
+    for (int cc = 0; cc < HALF; cc += 32) {
       uint32_t v[32];
-      tmem_ld32(tmem + (uint32_t(warp * 32) << 16) + cc, v);
+      tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + half * HALF + cc, v);
       if (i < P.n) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int col = P.base + col0 + cc + j;
+          const int col = cbase + cc + j;
           if (col < P.n) Cc[2 * (size_t(col) * P.ld + i) + comp] = cv[cc + j] - __uint_as_float(v[j]);
         }
       }
@@ -356,8 +359,21 @@ bool make_map(CUtensorMap* m, void* base, bool tf32, int Kp, int rows, int items
   return r == CUDA_SUCCESS;
 }
 
-constexpr int TC_BN = 128;
 constexpr int TC_STAGES = 3;
+int g_tile_n = 128;   // 128 or 256 complex columns per tile (autotuned)
+
+template <int BN>
+void launch_tc(const CUtensorMap& mah, const CUtensorMap& mal, const CUtensorMap& mbh, const CUtensorMap& mbl,
+               const TcParams& P, int m, int items, cudaStream_t st) {
+  constexpr size_t smem = size_t(TC_STAGES) * (BM * KB + BN * KB) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_update_kernel<BN, TC_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    attr = true;
+  }
+  dim3 grid((2 * m + BM - 1) / BM, (m + BN - 1) / BN, items);
+  tc_update_kernel<BN, TC_STAGES><<<grid, 256, smem, st>>>(mah, mal, mbh, mbl, P);
+}
 
 int kp_of(bool tf32) {
   // K elements per pass padded to whole 128-byte stages
@@ -368,6 +384,14 @@ int kp_of(bool tf32) {
 }  // namespace
 
 int tc_panel_width(int) { return PANEL_NB; }
+
+bool tc_set_tile_n(int bn) {
+  if (bn != 128 && bn != 256) return false;
+  g_tile_n = bn;
+  return true;
+}
+
+int tc_get_tile_n() { return g_tile_n; }
 
 size_t tc_pack_bytes_per_item(int n) {
   const int rows_pad = 2 * ((n + 127) / 128) * 128;
@@ -418,9 +442,10 @@ bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, 
     prof_launched(PH_PACK, 2, items);
   }
   CUtensorMap mah, mal, mbh, mbl;
+  const int bn = g_tile_n;
   if (!make_map(&mah, pa_hi, tf32, Kp, item_rows, items, BM) || !make_map(&mal, pa_lo, tf32, Kp, item_rows, items, BM) ||
-      !make_map(&mbh, pb_hi, tf32, Kp, item_rows, items, TC_BN) ||
-      !make_map(&mbl, pb_lo, tf32, Kp, item_rows, items, TC_BN)) {
+      !make_map(&mbh, pb_hi, tf32, Kp, item_rows, items, bn) ||
+      !make_map(&mbl, pb_lo, tf32, Kp, item_rows, items, bn)) {
     must_set_error("tensor map encoding failed");
     return false;
   }
@@ -433,15 +458,11 @@ bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, 
   P.ksteps = Kp * es / KB;
   P.err = err;
   P.tf32 = tf32 ? 1 : 0;
-  constexpr size_t smem = size_t(TC_STAGES) * (BM * KB + TC_BN * KB) + 1024;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc_update_kernel<TC_BN, TC_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    attr = true;
-  }
-  dim3 grid((2 * m + BM - 1) / BM, (m + TC_BN - 1) / TC_BN, items);
   ProfScope ps(PH_UPDATE, st);
-  tc_update_kernel<TC_BN, TC_STAGES><<<grid, 128, smem, st>>>(mah, mal, mbh, mbl, P);
+  if (bn == 256)
+    launch_tc<256>(mah, mal, mbh, mbl, P, m, items, st);
+  else
+    launch_tc<128>(mah, mal, mbh, mbl, P, m, items, st);
   prof_launched(PH_UPDATE, 1, items);
   return true;
 }

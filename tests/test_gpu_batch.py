@@ -1,0 +1,90 @@
+"""must_tau00_batch: LIZs of uneven size in shared launches (each LIZ padded
+with decoupled identity sites to a common order), checked against
+must_tau00_solve on each LIZ alone and against the CPU oracle."""
+import numpy as np
+import pytest
+
+from helpers import ncpu, oracle_tau, rel_fro
+from paper_2308_16317_gb300 import workload as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a GPU"
+    from paper_2308_16317_gb300 import binding, build
+    build.build()
+    binding.load()
+    return binding
+
+
+def _uneven_workload(lmax=2, n_e=4, seed=3):
+    """LIZs with 12..19 sites (first two fcc shells with vacancies)."""
+    rng = np.random.default_rng(seed)
+    pos2, shell2 = wl.fcc_cluster(2)
+    lizs = []
+    for keep in (19, 17, 13, 12, 19, 15):
+        sel = [0] + sorted(rng.choice(np.arange(1, 19), size=keep - 1, replace=False).tolist())
+        lizs.append(wl.Liz(pos2[sel], rng.integers(0, 2, keep).astype(np.int32)))
+    return wl.Workload("uneven", lmax, lizs, wl.semicircle_contour(n_e), wl.spin_depths(2), wl.R_MT)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-9)])
+def test_batch_matches_single_solves_and_oracle(B, orc, precision, tol):
+    import torch
+    from paper_2308_16317_gb300.runner import Session, blocks_to_numpy
+    w = _uneven_workload()
+    s = Session(w)
+    opts = B.must_default_opts(precision, residual=1 if precision else 0)
+    tau_b, st_b = s.solve_batch(opts)
+    torch.cuda.synchronize()
+    assert (st_b.cpu().numpy() == 0).all()
+    tb = blocks_to_numpy(tau_b)
+    for j in range(len(w.lizs)):
+        t1, st1 = s.solve(opts, liz_index=j)
+        torch.cuda.synchronize()
+        assert (st1.cpu().numpy() == 0).all()
+        one = blocks_to_numpy(t1)
+        assert rel_fro(tb[j], one).max() <= tol
+        ref, _ = oracle_tau(orc, w, liz_index=j)
+        assert rel_fro(tb[j].reshape(-1, 9, 9), ref).max() <= tol
+
+
+def test_batch_small_workspace_chunks_per_liz(B):
+    """A workspace that fits one energy of one LIZ still gives the same result."""
+    import torch
+    from paper_2308_16317_gb300.runner import Session
+    w = _uneven_workload()
+    s = Session(w)
+    ref, _ = s.solve_batch(None)
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    small = B.must_workspace_bytes(s.lizs[0], 2) * 2 + (1 << 20)
+    tau, st = s.solve_batch(None, ws_bytes=small)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    assert np.abs(tau.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_batched_supercell_sample(B, orc):
+    """Per-site LIZs of the 256-site supercell with vacancies (n 688..2160,
+    lmax 3): 8 LIZs x 4 energies x 2 spins in one mixed-precision batch call;
+    the smallest and largest LIZ are checked against the oracle."""
+    import torch
+    from paper_2308_16317_gb300.runner import Session, blocks_to_numpy
+    full = wl.batched_supercell(n_sites=8)
+    w = wl.Workload(full.name, full.lmax, full.lizs, wl.semicircle_contour(4, im_min=0.005), full.v_species,
+                    full.r_mt)
+    s = Session(w)
+    tau, st = s.solve_batch(B.must_default_opts(1, residual=1))
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    tb = blocks_to_numpy(tau)
+    sizes = [l.n_sites for l in w.lizs]
+    for j in (int(np.argmin(sizes)), int(np.argmax(sizes))):
+        items = [(0, 0), (1, 3)]
+        ref, _ = oracle_tau(orc, w, liz_index=j, items=items, nthreads=min(2, ncpu()))
+        got = np.array([tb[j, s_, e] for s_, e in items])
+        assert rel_fro(got, ref).max() <= 1e-9
