@@ -334,6 +334,73 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_supercell(args):
+    """Batched uneven LIZs (per-site LIZs of the 256-site supercell, n 688..2160),
+    one captured plan per precision, replayed every step."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2308_16317_gb300 import binding as B
+    from paper_2308_16317_gb300 import build as libbuild
+    from paper_2308_16317_gb300 import workload as wl
+    from paper_2308_16317_gb300.runner import Session, blocks_to_numpy
+    libbuild.build()
+    B.load()
+    full = wl.batched_supercell()
+    lizs = full.lizs[rank * args.n_lizs:(rank + 1) * args.n_lizs]
+    w = wl.Workload(full.name, full.lmax, lizs, wl.semicircle_contour(args.n_energies, im_min=0.005), full.v_species,
+                    full.r_mt)
+    s = Session(w, device="cuda:%d" % local)
+    items = len(w.energies) * s.nspin * len(lizs)
+
+    def timed_plan(opts, steps, warm):
+        nbytes = B.must_batch_workspace_bytes(s.lizs, len(w.energies) * s.nspin, opts)
+        wsp = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        tau, st = s.alloc_out(len(lizs))
+        plan = B.must_plan_batch(s.lizs, s.E, s.tinv, s.n_species, s.nspin, opts, wsp, nbytes, tau, st)
+        for _ in range(warm):
+            B.must_plan_launch(plan)
+        torch.cuda.synchronize(dev)
+        l0 = B.must_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            B.must_plan_launch(plan)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1), B.must_launch_count() - l0, tau, st
+
+    prec = args.precision
+    opts = B.must_default_opts(PREC[prec], residual=1 if args.residual == "df" else 0)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, launches, tau, st = timed_plan(opts, args.steps, args.warmup)
+    clocks = sampler.stop()
+    fp64 = None
+    err = None
+    if prec != "fp64" and args.fp64_steps > 0:
+        ms64, _, tau64, _ = timed_plan(B.must_default_opts(0), args.fp64_steps, 1)
+        fp64 = {"value": items * args.fp64_steps / (ms64 / 1e3), "ms_per_step": ms64 / args.fp64_steps}
+        a, b = blocks_to_numpy(tau), blocks_to_numpy(tau64)
+        err = float((np.linalg.norm(a - b, axis=(-2, -1)) / np.linalg.norm(b, axis=(-2, -1))).max())
+    sizes = [z.n for z in s.lizs]
+    line = {"metric": "tau_00 solves/sec, batched uneven LIZs (supercell, n %d..%d)" % (min(sizes), max(sizes)),
+            "value": items * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": "supercell256 per-site LIZs with vacancies, lmax=3", "lizs": len(lizs),
+                       "energies": len(w.energies), "spins": s.nspin, "solves_per_step": items,
+                       "n_min": min(sizes), "n_max": max(sizes), "precision": prec, "residual": args.residual,
+                       "launch": "captured CUDA graph (must_plan_batch), replayed per step",
+                       "bucket_sites": B.must_tune_get(0), "tile_n": B.must_tune_get(1)},
+            "gpu_launches": int(launches), "clocks": clocks, "plain_fp64_batched": fp64,
+            "max_rel_err_vs_fp64": err, "status_ok": bool((st.cpu().numpy() == 0).all())}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def cpu_baseline(w, sample: int):
     """The oracle on the host cores: `sample` (energy, spin) solves of the same
     LIZ, one per thread, timed end to end."""
@@ -394,6 +461,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0)
+    ap.add_argument("--workload", default="liz135", choices=["liz135", "supercell"],
+                    help="liz135: the benchmark workload; supercell: per-site LIZs of the 256-site supercell "
+                         "with vacancies (uneven n), batched and replayed as a captured plan")
+    ap.add_argument("--n-lizs", type=int, default=32, help="supercell mode: LIZs per step")
     ap.add_argument("--n-energies", type=int, default=32,
                     help="contour energies per step (32 = the benchmark workload; fewer for ncu captures)")
     args = ap.parse_args()
@@ -401,6 +472,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "supercell":
+        run_supercell(args)
     else:
         run_ours(args)
 

@@ -157,6 +157,34 @@ size_t must_batch_workspace_bytes(int32_t n_liz, const must_liz* const* lizs, in
                                   const must_solve_opts* opts);
 
 /*
+ * Batched plan (the batched launch of the design, captured in a CUDA graph):
+ * the complete launch sequence of one must_tau00_batch call with these
+ * arguments is captured once into a CUDA graph; must_plan_launch replays it
+ * on `stream`, so repeated solves with new contents in the same E / tinv
+ * buffers (an SCF loop, a benchmark) pay no per-kernel launch cost.  All
+ * pointers must be device memory and stay valid while the plan exists.
+ * Errors: MUST_EINVAL (host pointers, as for must_tau00_batch), MUST_ECUDA
+ * (capture or instantiation failed).
+ */
+typedef struct must_plan must_plan;
+must_status must_plan_batch(int32_t n_liz, const must_liz* const* lizs, int32_t nE, const double* E,
+                            const double* tinv, int32_t n_species, int32_t nspin, const must_solve_opts* opts,
+                            void* workspace, size_t ws_bytes, double* tau00, int32_t* status, must_plan** out);
+must_status must_plan_launch(const must_plan* plan, void* stream);
+void must_plan_free(must_plan* plan);
+
+/*
+ * Tuning knobs (set by the project's autotuner, paper_2308_16317_gb300/autotune.py):
+ *   knob 0: sites per padding quantum when must_tau00_batch groups LIZs of
+ *           uneven size (1..64, default 4);
+ *   knob 1: complex columns per tensor-core tile of the trailing update
+ *           (128 or 256, default 128).
+ * Process-wide; set them between calls, not while solves are being enqueued.
+ */
+must_status must_tune_set(int32_t knob, int32_t value);
+int32_t must_tune_get(int32_t knob);
+
+/*
  * Allocation-free FP64 solve.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory while they run (their
  * device memory is owned by another allocator, or allocation is forbidden

@@ -1,0 +1,97 @@
+"""Autotuner for the batched tau_00 path.
+
+Times every combination of the library's tuning knobs (must_tune_set) on a
+sample batch and keeps the fastest, caching the choice in a JSON file keyed
+by GPU, precision and workload shape so later runs apply it without
+re-measuring.  Knobs:
+  bucket_sites  sites per padding quantum when LIZs of uneven size are
+                grouped into shared launches (padding costs flops, finer
+                quanta cost launches);
+  tile_n        complex columns per tensor-core tile of the trailing update.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+
+KNOBS = {"bucket_sites": 0, "tile_n": 1}
+CANDIDATES = {"bucket_sites": [1, 2, 4, 8], "tile_n": [128, 256]}
+
+
+def search(run, set_knob, candidates=None, reps: int = 2):
+    """Grid search: for each combination, set the knobs, run once to warm up,
+    then `reps` timed runs (run() returns milliseconds).  Returns
+    (best_setting, [(setting, ms), ...])."""
+    candidates = candidates or CANDIDATES
+    names = sorted(candidates)
+    results = []
+    for combo in itertools.product(*(candidates[k] for k in names)):
+        setting = dict(zip(names, combo))
+        for k, v in setting.items():
+            set_knob(KNOBS[k], v)
+        run()
+        ms = min(run() for _ in range(max(1, reps)))
+        results.append((setting, ms))
+    best = min(results, key=lambda x: x[1])[0]
+    for k, v in best.items():
+        set_knob(KNOBS[k], v)
+    return best, results
+
+
+def cache_key(gpu: str, precision: int, lmax: int, n_max: int, items: int) -> str:
+    return "%s|prec%d|lmax%d|nmax%d|items%d" % (gpu, precision, lmax, n_max, items)
+
+
+def load(path: str) -> dict:
+    if path and os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+def save(path: str, key: str, best: dict, results) -> None:
+    data = load(path)
+    data[key] = {"best": best, "measured_ms": [[s, ms] for s, ms in results]}
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def apply(path: str, key: str, set_knob) -> bool:
+    entry = load(path).get(key)
+    if not entry:
+        return False
+    for k, v in entry["best"].items():
+        set_knob(KNOBS[k], v)
+    return True
+
+
+def tune_session(session, opts, cache_path: str | None = None, reps: int = 2, candidates=None):
+    """Tune the knobs for must_tau00_batch on `session`'s LIZs (device timing
+    with CUDA events); reuse a cached choice for the same key if present."""
+    import torch
+
+    from . import binding as B
+    items = len(session.w.energies) * (1 if session.w.canted else session.nspin)
+    n_max = max(z.n for z in session.lizs)
+    key = cache_key(torch.cuda.get_device_name(), int(opts.precision) if opts else 0, session.w.lmax, n_max,
+                    items * len(session.lizs))
+    if cache_path and apply(cache_path, key, B.must_tune_set):
+        return load(cache_path)[key]["best"], None
+    out = session.alloc_out(len(session.lizs))
+
+    def run():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        session.solve_batch(opts, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    best, results = search(run, B.must_tune_set, candidates, reps)
+    if cache_path:
+        save(cache_path, key, best, results)
+    return best, results

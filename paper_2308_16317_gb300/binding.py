@@ -55,6 +55,12 @@ def load():
         "must_tau00_solve": (I32, [P, I32, P, P, I32, I32, ctypes.POINTER(must_solve_opts), P, SZ, P, P, P]),
         "must_tau00_batch": (I32, [I32, P, I32, P, P, I32, I32, ctypes.POINTER(must_solve_opts), P, SZ, P, P, P]),
         "must_tau00_solve_static": (I32, [P, I32, P, P, I32, I32, P, P, P]),
+        "must_plan_batch": (I32, [I32, P, I32, P, P, I32, I32, ctypes.POINTER(must_solve_opts), P, SZ, P, P,
+                                  ctypes.POINTER(P)]),
+        "must_plan_launch": (I32, [P, P]),
+        "must_plan_free": (None, [P]),
+        "must_tune_set": (I32, [I32, I32]),
+        "must_tune_get": (I32, [I32]),
         "must_static_scratch_bytes": (SZ, []),
         "must_profile_enable": (None, [ctypes.c_int]),
         "must_profile_read": (ctypes.c_int, [P, P, P, ctypes.c_int]),
@@ -76,7 +82,8 @@ def exported_symbols():
                         "must_workspace_bytes", "must_batch_workspace_bytes", "must_tinv_square_well",
                         "must_tau00_solve", "must_tau00_batch", "must_status_string", "must_last_error",
                         "must_profile_enable", "must_profile_read", "must_launch_count", "must_phase_name",
-                        "must_tau00_solve_static", "must_static_scratch_bytes")]
+                        "must_tau00_solve_static", "must_static_scratch_bytes", "must_plan_batch",
+                        "must_plan_launch", "must_plan_free", "must_tune_set", "must_tune_get")]
 
 
 def _ptr(a):
@@ -219,3 +226,38 @@ def must_tau00_solve_static(liz: Liz, E, tinv, n_species: int, nspin: int, tau00
 
 def must_static_scratch_bytes() -> int:
     return int(load().must_static_scratch_bytes())
+
+
+class Plan:
+    """Owning wrapper of a must_plan (a captured batched launch)."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep          # buffers the graph refers to
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.must_plan_free(self.handle)
+            self.handle = None
+
+
+def must_plan_batch(lizs, E, tinv, n_species: int, nspin: int, opts, workspace, ws_bytes: int, tau00,
+                    status=None) -> Plan:
+    arr = (ctypes.c_void_p * len(lizs))(*[z.handle.value for z in lizs])
+    out = ctypes.c_void_p()
+    _check(load().must_plan_batch(len(lizs), arr, _numel_complex(E), _ptr(E), _ptr(tinv), int(n_species),
+                                  int(nspin), ctypes.byref(opts) if opts else None, _ptr(workspace), int(ws_bytes),
+                                  _ptr(tau00), _ptr(status), ctypes.byref(out)))
+    return Plan(out, (lizs, E, tinv, workspace, tau00, status))
+
+
+def must_plan_launch(plan: Plan, stream=None):
+    _check(load().must_plan_launch(plan.handle, _stream(stream)))
+
+
+def must_tune_set(knob: int, value: int):
+    _check(load().must_tune_set(int(knob), int(value)))
+
+
+def must_tune_get(knob: int) -> int:
+    return int(load().must_tune_get(int(knob)))

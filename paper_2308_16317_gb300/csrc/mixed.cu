@@ -33,27 +33,33 @@ __device__ __forceinline__ float cnormf(cf a) { return a.x * a.x + a.y * a.y; }
 
 // ------------------------------------------------------------ FP32 panel --
 // Factorisation of the panel columns [k0, k0+nbe) (nbe <= 64) of one matrix
-// per CTA, blocked into leaves of LEAF columns (right-looking at two levels):
-//   for each leaf: factor its columns one by one (warp-shuffle argmax of
-//   |z|^2 over the pivot-eligible rows [c, r), row swap across the whole
-//   panel, rank-1 update restricted to the leaf), then solve the leaf's rows
-//   of the remaining panel columns (U block, staged in shared memory) and
-//   update the rows below with one pass over the remaining columns.
-// Every thread loads all of its rows (up to RPT) before updating them, and
-// the rank-1 update of column c also yields the candidates of the pivot
-// search of column c+1, so each column costs two passes over its rows.
+// per CTA, blocked into leaves of lw columns (right-looking at two levels):
+//   (a) the leaf's rows [c0, n) are copied into shared memory and its columns
+//       are factored there one by one (warp-shuffle argmax of |z|^2 over the
+//       pivot-eligible rows [c, r), row swap inside the leaf, rank-1 update),
+//       then written back;
+//   (a') the leaf's interchanges are applied to the other panel columns;
+//   (b) the leaf's rows of the remaining panel columns: L_leaf^{-1} A (U block,
+//       staged in shared memory);
+//   (c) the rows below: A[i, rest] -= L[i, leaf] U[leaf, rest], one pass.
+// lw = min(8, what fits in the shared-memory budget for this n).
 constexpr int PANEL_W = 64;
 constexpr int LEAF = 8;
-constexpr int PPT = 512;   // threads of the panel kernel
-constexpr int RPT = 4;     // rows per thread per pass
+constexpr int PPT = 512;                       // threads of the panel kernel
+constexpr size_t PANEL_SMEM = 200 * 1024;      // leaf buffer budget (bytes)
+
+__host__ __device__ inline int leaf_width(int n) {
+  const int fit = int(PANEL_SMEM / (size_t(n) * sizeof(float2)));
+  return fit < LEAF ? (fit < 1 ? 1 : fit) : LEAF;
+}
 
 __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int r,
                                                       int k0, int nbe, int* __restrict__ piv0, int* __restrict__ status,
                                                       const int* __restrict__ conv) {
+  extern __shared__ cf Lf[];           // leaf, column-major [lw][mrows]
   __shared__ float sv[PPT / 32];
   __shared__ int si[PPT / 32];
   __shared__ int s_p;
-  __shared__ cf prow[LEAF];
   __shared__ cf Ub[LEAF][PANEL_W];     // leaf rows of the remaining panel columns
   __shared__ cf Ll[LEAF][LEAF];        // leaf's unit-lower top block
   const int item = blockIdx.x;
@@ -61,25 +67,22 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
   int* piv = piv0 + size_t(item) * r;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int pend = k0 + nbe;
-  bool carried = false;        // this thread's pivot candidate for the next column is known
-  float cbest = -1.0f;
-  int cbi = 0;
-  for (int lb = 0; lb < nbe; lb += LEAF) {
+  const int LW = leaf_width(n);
+  for (int lb = 0; lb < nbe; lb += LW) {
     const int c0 = k0 + lb;
-    const int lw = min(LEAF, nbe - lb);
+    const int lw = min(LW, nbe - lb);
     const int le = c0 + lw;             // leaf columns [c0, le)
-    carried = false;
-    // (a) leaf columns one by one
-    for (int c = c0; c < le; ++c) {
+    const int mrows = n - c0;           // leaf rows [c0, n)
+    const int pr = r - c0;              // pivot-eligible local rows [j, pr)
+    // (a) leaf into shared memory
+    for (int q = 0; q < lw; ++q)
+      for (int ii = tid; ii < mrows; ii += PPT) Lf[q * mrows + ii] = A[size_t(c0 + q) * ld + c0 + ii];
+    __syncthreads();
+    for (int j = 0; j < lw; ++j) {
+      cf* colj = Lf + j * mrows;
       float best = -1.0f;
-      int bi = c;
-      if (carried) {
-        best = cbest;
-        bi = cbi;
-      } else {
-        const cf* col = A + size_t(c) * ld;
-        for (int i = c + tid; i < r; i += PPT) argmax_merge(best, bi, cnormf(col[i]), i);
-      }
+      int bi = j;
+      for (int ii = j + tid; ii < pr; ii += PPT) argmax_merge(best, bi, cnormf(colj[ii]), ii);
       for (int o = 16; o > 0; o >>= 1) {
         const float v2 = __shfl_down_sync(0xffffffffu, best, o);
         const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
@@ -92,69 +95,50 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
         int p = si[0];
         for (int w = 1; w < PPT / 32; ++w) argmax_merge(b, p, sv[w], si[w]);
         if (!(b > 0.0f)) status[item] = ST_SINGULAR;
-        piv[c] = p;
+        piv[c0 + j] = c0 + p;
         s_p = p;
       }
       __syncthreads();
       const int p = s_p;
-      if (p != c)
-        for (int cc = k0 + tid; cc < pend; cc += PPT) {
-          cf* cp = A + size_t(cc) * ld;
-          const cf t = cp[c];
-          cp[c] = cp[p];
-          cp[p] = t;
-        }
+      if (p != j && tid < lw) {
+        const cf t = Lf[tid * mrows + j];
+        Lf[tid * mrows + j] = Lf[tid * mrows + p];
+        Lf[tid * mrows + p] = t;
+      }
       __syncthreads();
-      const int width = le - c;
-      if (tid < width) prow[tid] = A[size_t(c + tid) * ld + c];
-      __syncthreads();
-      const cf d = prow[0];
-      carried = false;
+      const cf d = colj[j];
       if (cnormf(d) > 0.0f) {
         const cf inv = cinvf(d);
-        const bool track = (c + 1 < le);
-        float nb = -1.0f;
-        int nbi = c + 1;
-        for (int i0 = c + 1; i0 < n; i0 += PPT * RPT) {
-          cf v[RPT][LEAF];
-#pragma unroll
-          for (int t = 0; t < RPT; ++t) {
-            const int i = i0 + tid + t * PPT;
-            if (i < n)
-#pragma unroll
-              for (int q = 0; q < LEAF; ++q)
-                if (q < width) v[t][q] = A[size_t(c + q) * ld + i];
-          }
-#pragma unroll
-          for (int t = 0; t < RPT; ++t) {
-            const int i = i0 + tid + t * PPT;
-            if (i < n) {
-              const cf l = cmulf(v[t][0], inv);
-              A[size_t(c) * ld + i] = l;
-#pragma unroll
-              for (int q = 1; q < LEAF; ++q)
-                if (q < width) {
-                  cfmsf(v[t][q], l, prow[q]);
-                  A[size_t(c + q) * ld + i] = v[t][q];
-                }
-              if (track && i < r) argmax_merge(nb, nbi, cnormf(v[t][1]), i);
-            }
-          }
-        }
-        if (track) {
-          carried = true;
-          cbest = nb;
-          cbi = nbi;
+        for (int ii = j + 1 + tid; ii < mrows; ii += PPT) {
+          const cf l = cmulf(colj[ii], inv);
+          colj[ii] = l;
+          for (int q = j + 1; q < lw; ++q) cfmsf(Lf[q * mrows + ii], l, Lf[q * mrows + j]);
         }
       }
       __syncthreads();
     }
+    for (int q = 0; q < lw; ++q)
+      for (int ii = tid; ii < mrows; ii += PPT) A[size_t(c0 + q) * ld + c0 + ii] = Lf[q * mrows + ii];
+    // (a') the leaf's interchanges on the other panel columns
+    for (int cc = k0 + tid; cc < pend; cc += PPT) {
+      if (cc >= c0 && cc < le) continue;
+      cf* colc = A + size_t(cc) * ld;
+      for (int j = 0; j < lw; ++j) {
+        const int c = c0 + j, p = piv[c];
+        if (p != c) {
+          const cf t = colc[c];
+          colc[c] = colc[p];
+          colc[p] = t;
+        }
+      }
+    }
+    __syncthreads();
     const int rest = pend - le;          // remaining panel columns [le, pend)
     if (rest <= 0) continue;
     // (b) U block: rows [c0, le) of the remaining columns, L_leaf^{-1} A
     for (int t = tid; t < lw * lw; t += PPT) {
-      const int i = t % lw, j = t / lw;
-      Ll[i][j] = A[size_t(c0 + j) * ld + c0 + i];
+      const int i = t % lw, jj = t / lw;
+      Ll[i][jj] = A[size_t(c0 + jj) * ld + c0 + i];
     }
     __syncthreads();
     if (tid < rest) {
@@ -167,8 +151,8 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
       for (int i = 1; i < LEAF; ++i)
         if (i < lw)
 #pragma unroll
-          for (int j = 0; j < LEAF; ++j)
-            if (j < i) cfmsf(x[i], Ll[i][j], x[j]);
+          for (int jj = 0; jj < LEAF; ++jj)
+            if (jj < i) cfmsf(x[i], Ll[i][jj], x[jj]);
 #pragma unroll
       for (int i = 0; i < LEAF; ++i)
         if (i < lw) {
@@ -181,19 +165,19 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
     for (int i = le + tid; i < n; i += PPT) {
       cf l[LEAF];
 #pragma unroll
-      for (int j = 0; j < LEAF; ++j)
-        if (j < lw) l[j] = A[size_t(c0 + j) * ld + i];
+      for (int jj = 0; jj < LEAF; ++jj)
+        if (jj < lw) l[jj] = A[size_t(c0 + jj) * ld + i];
       for (int q0 = 0; q0 < rest; q0 += 8) {
         cf v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           if (q0 + q < rest) v[q] = A[size_t(le + q0 + q) * ld + i];
 #pragma unroll
-        for (int j = 0; j < LEAF; ++j)
-          if (j < lw)
+        for (int jj = 0; jj < LEAF; ++jj)
+          if (jj < lw)
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-              if (q0 + q < rest) cfmsf(v[q], l[j], Ub[j][q0 + q]);
+              if (q0 + q < rest) cfmsf(v[q], l[jj], Ub[jj][q0 + q]);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           if (q0 + q < rest) A[size_t(le + q0 + q) * ld + i] = v[q];
@@ -750,12 +734,20 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   cudaMemsetAsync(err, 0, sizeof(int), st);
 
   // FP32 elimination of the leading r columns of M_s
+  {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(panel32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(PANEL_SMEM));
+      attr = true;
+    }
+  }
   const int nb = tc_panel_width(c.opts.precision);
   for (int k0 = 0; k0 < r; k0 += nb) {
     const int nbe = std::min(nb, r - k0);
     {
       ProfScope ps(PH_PANEL, st);
-      panel32_kernel<<<items, PPT, 0, st>>>(M32, stride, ld, n, r, k0, nbe, c.piv, c.status, conv);
+      panel32_kernel<<<items, PPT, size_t(leaf_width(n)) * n * sizeof(float2), st>>>(M32, stride, ld, n, r, k0,
+                                                                                      nbe, c.piv, c.status, conv);
       prof_launched(PH_PANEL, 1, items);
     }
     {

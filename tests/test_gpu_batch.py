@@ -88,3 +88,93 @@ def test_batched_supercell_sample(B, orc):
         ref, _ = oracle_tau(orc, w, liz_index=j, items=items, nthreads=min(2, ncpu()))
         got = np.array([tb[j, s_, e] for s_, e in items])
         assert rel_fro(got, ref).max() <= 1e-9
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_plan_replay_matches_batch_call(B, precision):
+    """A captured plan, replayed twice (with new t^{-1} contents in the same
+    buffer in between), matches must_tau00_batch on the same inputs."""
+    import torch
+    from paper_2308_16317_gb300.runner import Session
+    w = _uneven_workload()
+    s = Session(w)
+    opts = B.must_default_opts(precision, residual=1 if precision else 0)
+    ref, _ = s.solve_batch(opts)
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    items = len(w.energies) * s.nspin
+    nb = B.must_batch_workspace_bytes(s.lizs, items, opts)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    tau, st = s.alloc_out(len(s.lizs))
+    plan = B.must_plan_batch(s.lizs, s.E, s.tinv, s.n_species, s.nspin, opts, ws, nb, tau, st)
+    l0 = B.must_launch_count()
+    B.must_plan_launch(plan)
+    torch.cuda.synchronize()
+    assert B.must_launch_count() > l0
+    assert (st.cpu().numpy() == 0).all()
+    assert np.abs(tau.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    # new t^{-1} (deeper wells) in the same buffer: the replay follows it
+    saved = s.tinv.clone()
+    V = torch.tensor((np.asarray(w.v_species) - 0.1).reshape(-1), device="cuda")
+    B.must_tinv_square_well(s.E, V, w.r_mt, w.lmax, s.tinv)
+    ref2, _ = s.solve_batch(opts)
+    B.must_plan_launch(plan)
+    torch.cuda.synchronize()
+    assert np.abs(tau.cpu().numpy() - ref2.cpu().numpy()).max() <= 1e-12 * np.abs(ref2.cpu().numpy()).max()
+    assert np.abs(ref2.cpu().numpy() - ref).max() > 1e-3 * np.abs(ref).max()
+    s.tinv.copy_(saved)
+
+
+def test_tuning_knobs_change_nothing_numerically(B):
+    import torch
+    from paper_2308_16317_gb300.runner import Session
+    w = _uneven_workload()
+    s = Session(w)
+    opts = B.must_default_opts(1, residual=1)
+    ref, _ = s.solve_batch(opts)
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    old = (B.must_tune_get(0), B.must_tune_get(1))
+    try:
+        for bucket, tile in ((1, 256), (8, 128)):
+            B.must_tune_set(0, bucket)
+            B.must_tune_set(1, tile)
+            tau, st = s.solve_batch(opts)
+            torch.cuda.synchronize()
+            assert (st.cpu().numpy() == 0).all()
+            assert rel_fro(tau.cpu().numpy(), ref).max() <= 1e-9
+        with pytest.raises(B.MustError):
+            B.must_tune_set(1, 96)
+    finally:
+        B.must_tune_set(0, old[0])
+        B.must_tune_set(1, old[1])
+
+
+def test_autotuner_on_uneven_batch(B, tmp_path):
+    """The tuner measures every knob combination on the device, caches the
+    fastest, and the tuned setting still solves correctly."""
+    import os
+    import torch
+    from paper_2308_16317_gb300 import autotune
+    from paper_2308_16317_gb300.runner import Session
+    w = _uneven_workload()
+    s = Session(w)
+    opts = B.must_default_opts(1, residual=1)
+    ref, _ = s.solve_batch(opts)
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    old = (B.must_tune_get(0), B.must_tune_get(1))
+    try:
+        path = os.path.join(tmp_path, "tune.json")
+        best, results = autotune.tune_session(s, opts, cache_path=path, reps=1)
+        assert len(results) == 8 and all(ms > 0 for _, ms in results)
+        assert B.must_tune_get(0) == best["bucket_sites"] and B.must_tune_get(1) == best["tile_n"]
+        again, none = autotune.tune_session(s, opts, cache_path=path)
+        assert again == best and none is None
+        tau, st = s.solve_batch(opts)
+        torch.cuda.synchronize()
+        assert (st.cpu().numpy() == 0).all()
+        assert rel_fro(tau.cpu().numpy(), ref).max() <= 1e-9
+    finally:
+        B.must_tune_set(0, old[0])
+        B.must_tune_set(1, old[1])
