@@ -209,6 +209,73 @@ must_status must_tau00_solve_static(const must_liz* liz, int32_t nE, const doubl
 size_t must_static_scratch_bytes(void);
 
 /*
+ * Learned warm start (design growth item 4; the paper has no learned part).
+ * A small MLP, three linear layers with SiLU between them, BF16 weights with
+ * FP32 accumulation and FP32 master weights / Adam moments, trained and
+ * evaluated by the library's own kernels.  It predicts tau_00(E_k) from
+ * tau_00 at the neighbouring contour energies E_{k-1}, E_{k+1}, the three
+ * energies, the spin and the LIZ's species occupancy; the prediction can seed
+ * the refinement of must_tau00_solve_seeded, whose plain solve is the
+ * fallback and the judge of its error.
+ *   must_mlp_create   n_in inputs, hidden width, n_out outputs, largest batch,
+ *                     seed of the initial weights (device allocation).
+ *   must_mlp_forward  y[batch][n_out] = net(x[batch][n_in]) (device FP32).
+ *   must_mlp_gradients / must_mlp_train_step: mean over the batch of the
+ *                     squared error against target[batch][n_out]; gradients
+ *                     in the parameter layout W1[H][I] b1 W2[H][H] b2 W3[O][H]
+ *                     b3 (host or device), loss as one double (host/device).
+ *   must_mlp_get/set_params, must_mlp_save/load: FP32 master weights (and
+ *                     Adam state for save/load; set_params resets Adam).
+ *   must_mlp_features: x for n samples from tau_prev / tau_next
+ *                     ([n][kap][kap] complex, device), E3 ([n][3] complex:
+ *                     E_{k-1}, E_k, E_{k+1}), spin ([n] float, +-1), occupancy
+ *                     ([n][n_occ] float); also the per-sample scale and the
+ *                     interpolation (tau_prev + tau_next)/2.  n_in must equal
+ *                     4 kap^2 + n_occ + 8.
+ *   must_mlp_apply    tau_pred = interp + scale * y; must_mlp_targets the
+ *                     inverse map (training targets from solved tau).
+ */
+typedef struct must_mlp must_mlp;
+must_status must_mlp_create(int32_t n_in, int32_t hidden, int32_t n_out, int32_t max_batch, uint64_t seed,
+                            must_mlp** out);
+void must_mlp_free(must_mlp* net);
+size_t must_mlp_param_count(const must_mlp* net);
+must_status must_mlp_get_params(const must_mlp* net, float* params, void* stream);
+must_status must_mlp_set_params(must_mlp* net, const float* params, void* stream);
+must_status must_mlp_forward(const must_mlp* net, int32_t batch, const float* x, float* y, void* stream);
+must_status must_mlp_gradients(must_mlp* net, int32_t batch, const float* x, const float* target, float* grads,
+                               double* loss, void* stream);
+must_status must_mlp_train_step(must_mlp* net, int32_t batch, const float* x, const float* target, float lr,
+                                double* loss, void* stream);
+must_status must_mlp_save(const must_mlp* net, const char* path);
+must_status must_mlp_load(must_mlp* net, const char* path);
+must_status must_mlp_features(int32_t n, int32_t kap, const double* tau_prev, const double* tau_next,
+                              const double* E3, const float* spin, const float* occ, int32_t n_occ, int32_t n_in,
+                              float* x, float* scale, double* interp, void* stream);
+must_status must_mlp_apply(int32_t n, int32_t kap, const float* y, int32_t n_out, const float* scale,
+                           const double* interp, double* tau_pred, void* stream);
+must_status must_mlp_targets(int32_t n, int32_t kap, const double* tau, const float* scale, const double* interp,
+                             float* y, int32_t n_out, void* stream);
+
+/*
+ * Seeded solve (learned warm start).  As must_tau00_solve on a mixed-precision
+ * path, but items with seed_mask[block] != 0 start the refinement from a
+ * block column built from the predicted tau_seed[block] (kap x kap,
+ * column-major, same indexing as tau00): X_c = tau_seed and, for every other
+ * row, the single-scattering term X_i = -M_ii^{-1} sum_q M_{i,c q} tau_seed.
+ * The seed is accepted only if ||E0 - M X||_F <= 1e-3 ||E0||_F; otherwise (and
+ * for unmasked items) the plain low-precision solve starts the refinement,
+ * which then runs to the same tolerance either way, so the plain solve is the
+ * fallback and the judge of the seed.  seed_used (optional) receives 1 where
+ * the seed was accepted.  tau_seed, seed_mask, seed_used and tau00 must be
+ * device memory.  Errors: as must_tau00_solve; MUST_EINVAL for MUST_FP64.
+ */
+must_status must_tau00_solve_seeded(const must_liz* liz, int32_t nE, const double* E, const double* tinv,
+                                    int32_t n_species, int32_t nspin, const must_solve_opts* opts, void* workspace,
+                                    size_t ws_bytes, const double* tau_seed, const int32_t* seed_mask, double* tau00,
+                                    int32_t* status, int32_t* seed_used, void* stream);
+
+/*
  * Instrumentation (not part of the paper's method).  When enabled, CUDA
  * events are recorded on the launching stream around each phase of the path
  * (0 assemble, 1 panel, 2 row_swap, 3 trsm, 4 pack, 5 trailing_update,

@@ -60,6 +60,21 @@ def load():
         "must_plan_launch": (I32, [P, P]),
         "must_plan_free": (None, [P]),
         "must_tune_set": (I32, [I32, I32]),
+        "must_tau00_solve_seeded": (I32, [P, I32, P, P, I32, I32, ctypes.POINTER(must_solve_opts), P, SZ, P, P, P,
+                                          P, P, P]),
+        "must_mlp_create": (I32, [I32, I32, I32, I32, ctypes.c_uint64, ctypes.POINTER(P)]),
+        "must_mlp_free": (None, [P]),
+        "must_mlp_param_count": (SZ, [P]),
+        "must_mlp_get_params": (I32, [P, P, P]),
+        "must_mlp_set_params": (I32, [P, P, P]),
+        "must_mlp_forward": (I32, [P, I32, P, P, P]),
+        "must_mlp_gradients": (I32, [P, I32, P, P, P, P, P]),
+        "must_mlp_train_step": (I32, [P, I32, P, P, ctypes.c_float, P, P]),
+        "must_mlp_save": (I32, [P, ctypes.c_char_p]),
+        "must_mlp_load": (I32, [P, ctypes.c_char_p]),
+        "must_mlp_features": (I32, [I32, I32, P, P, P, P, P, I32, I32, P, P, P, P]),
+        "must_mlp_apply": (I32, [I32, I32, P, I32, P, P, P, P]),
+        "must_mlp_targets": (I32, [I32, I32, P, P, P, P, I32, P]),
         "must_tune_get": (I32, [I32]),
         "must_static_scratch_bytes": (SZ, []),
         "must_profile_enable": (None, [ctypes.c_int]),
@@ -83,7 +98,11 @@ def exported_symbols():
                         "must_tau00_solve", "must_tau00_batch", "must_status_string", "must_last_error",
                         "must_profile_enable", "must_profile_read", "must_launch_count", "must_phase_name",
                         "must_tau00_solve_static", "must_static_scratch_bytes", "must_plan_batch",
-                        "must_plan_launch", "must_plan_free", "must_tune_set", "must_tune_get")]
+                        "must_plan_launch", "must_plan_free", "must_tune_set", "must_tune_get",
+                        "must_mlp_create", "must_mlp_free", "must_mlp_param_count", "must_mlp_get_params",
+                        "must_mlp_set_params", "must_mlp_forward", "must_mlp_gradients", "must_mlp_train_step",
+                        "must_mlp_save", "must_mlp_load", "must_mlp_features", "must_mlp_apply", "must_mlp_targets",
+                        "must_tau00_solve_seeded")]
 
 
 def _ptr(a):
@@ -261,3 +280,78 @@ def must_tune_set(knob: int, value: int):
 
 def must_tune_get(knob: int) -> int:
     return int(load().must_tune_get(int(knob)))
+
+
+class Mlp:
+    """Owning wrapper of a must_mlp (the warm-start network)."""
+
+    def __init__(self, n_in: int, hidden: int, n_out: int, max_batch: int, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().must_mlp_create(int(n_in), int(hidden), int(n_out), int(max_batch), int(seed), ctypes.byref(h)))
+        self.handle, self.n_in, self.hidden, self.n_out, self.max_batch = h, n_in, hidden, n_out, max_batch
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.must_mlp_free(self.handle)
+            self.handle = None
+
+    def param_count(self) -> int:
+        return int(load().must_mlp_param_count(self.handle))
+
+
+def must_mlp_get_params(net: Mlp, out, stream=None):
+    _check(load().must_mlp_get_params(net.handle, _ptr(out), _stream(stream)))
+    return out
+
+
+def must_mlp_set_params(net: Mlp, params, stream=None):
+    _check(load().must_mlp_set_params(net.handle, _ptr(params), _stream(stream)))
+
+
+def must_mlp_forward(net: Mlp, x, y, stream=None):
+    _check(load().must_mlp_forward(net.handle, int(x.shape[0]), _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def must_mlp_gradients(net: Mlp, x, target, grads=None, loss=None, stream=None):
+    _check(load().must_mlp_gradients(net.handle, int(x.shape[0]), _ptr(x), _ptr(target), _ptr(grads), _ptr(loss),
+                                     _stream(stream)))
+
+
+def must_mlp_train_step(net: Mlp, x, target, lr: float, loss=None, stream=None):
+    _check(load().must_mlp_train_step(net.handle, int(x.shape[0]), _ptr(x), _ptr(target), float(lr), _ptr(loss),
+                                      _stream(stream)))
+
+
+def must_mlp_save(net: Mlp, path: str):
+    _check(load().must_mlp_save(net.handle, path.encode()))
+
+
+def must_mlp_load(net: Mlp, path: str):
+    _check(load().must_mlp_load(net.handle, path.encode()))
+
+
+def must_mlp_features(kap: int, tau_prev, tau_next, E3, spin, occ, n_in: int, x, scale, interp, stream=None):
+    n = int(tau_prev.shape[0])
+    n_occ = int(occ.shape[1]) if occ is not None else 0
+    _check(load().must_mlp_features(n, int(kap), _ptr(tau_prev), _ptr(tau_next), _ptr(E3), _ptr(spin), _ptr(occ),
+                                    n_occ, int(n_in), _ptr(x), _ptr(scale), _ptr(interp), _stream(stream)))
+
+
+def must_mlp_apply(kap: int, y, scale, interp, tau_pred, stream=None):
+    _check(load().must_mlp_apply(int(y.shape[0]), int(kap), _ptr(y), int(y.shape[1]), _ptr(scale), _ptr(interp),
+                                 _ptr(tau_pred), _stream(stream)))
+
+
+def must_mlp_targets(kap: int, tau, scale, interp, y, stream=None):
+    _check(load().must_mlp_targets(int(y.shape[0]), int(kap), _ptr(tau), _ptr(scale), _ptr(interp), _ptr(y),
+                                   int(y.shape[1]), _stream(stream)))
+
+
+def must_tau00_solve_seeded(liz: Liz, E, tinv, n_species: int, nspin: int, opts, workspace, ws_bytes: int, tau_seed,
+                            seed_mask, tau00, status=None, seed_used=None, stream=None):
+    _check(load().must_tau00_solve_seeded(liz.handle, _numel_complex(E), _ptr(E), _ptr(tinv), int(n_species),
+                                          int(nspin), ctypes.byref(opts) if opts else None, _ptr(workspace),
+                                          int(ws_bytes), _ptr(tau_seed), _ptr(seed_mask), _ptr(tau00), _ptr(status),
+                                          _ptr(seed_used), _stream(stream)))
+    return tau00

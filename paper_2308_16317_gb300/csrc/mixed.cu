@@ -466,11 +466,13 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
                                                       const double2* __restrict__ Sinv0,
                                                       const double2* __restrict__ R0, double2* __restrict__ X0,
                                                       double* __restrict__ norms, const int* __restrict__ conv,
-                                                      int first, unsigned long long* __restrict__ work) {
+                                                      int first_all, const int* __restrict__ first_flags,
+                                                      unsigned long long* __restrict__ work) {
   extern __shared__ cf w[];   // [n][G]
   __shared__ cf Tb[32][33];   // staged diagonal block
   const int item = blockIdx.y;
   if (conv[item]) return;
+  const int first = first_flags ? first_flags[item] : first_all;
   if (work && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(work, 1ull);
   const int cb = blockIdx.x * G;
   const int ng = min(G, kap - cb);
@@ -695,6 +697,82 @@ __global__ void output_kernel(const double2* __restrict__ X0, int n, int kap, do
   if (threadIdx.x == 0 && status_out) status_out[out_index[item]] = *err ? int(MUST_ETIMEOUT) : status[item];
 }
 
+// ------------------------------------------------------ learned warm start --
+// Seed block column from a predicted tau^_00: X_c = tau^, and for every other
+// row the single-scattering term of row i of M X = E0 (keeping only the
+// coupling to the centre): X_i = -M_ii^{-1} sum_q M_{i,r+q} tau^_{q c}.
+// M is the unscaled matrix (FP64 or double-float pairs).  Items without a
+// seed get their first_flags set to 1 (cold start) and are skipped.
+__global__ void seed_x_kernel(const void* __restrict__ M0, int m_df, size_t stride, int ld, int n, int kap,
+                              const double2* __restrict__ seed, const int* __restrict__ mask,
+                              const int* __restrict__ out_index, double2* __restrict__ X0, int* __restrict__ skip) {
+  const int item = blockIdx.y;
+  const int oi = out_index[item];
+  if (!mask[oi]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) skip[item] = 1;
+    return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) skip[item] = 0;
+  const int r = n - kap;
+  const double2* tau = seed + size_t(oi) * kap * kap;
+  double2* X = X0 + size_t(item) * n * kap;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  auto Mel = [&](int row, int col) -> cd {
+    const size_t off = size_t(item) * stride + size_t(col) * ld + row;
+    if (m_df) {
+      const float4 f = reinterpret_cast<const float4*>(M0)[off];
+      return mk(double(f.x) + double(f.z), double(f.y) + double(f.w));
+    }
+    const double2 d = reinterpret_cast<const double2*>(M0)[off];
+    return mk(d.x, d.y);
+  };
+  if (i >= r) {
+    for (int c = 0; c < kap; ++c) X[size_t(c) * n + i] = tau[size_t(c) * kap + (i - r)];
+    return;
+  }
+  const cd dinv = cinv(Mel(i, i));
+  cd mc[MUST_MAX_NL * 2];
+  for (int q = 0; q < kap; ++q) mc[q] = Mel(i, r + q);
+  for (int c = 0; c < kap; ++c) {
+    cd acc = mk(0.0, 0.0);
+    for (int q = 0; q < kap; ++q) {
+      const double2 t = tau[size_t(c) * kap + q];
+      acc = acc + mc[q] * mk(t.x, t.y);
+    }
+    const cd x = -(dinv * acc);
+    X[size_t(c) * n + i] = make_double2(x.x, x.y);
+  }
+}
+
+// Residual gate: accept the seed if ||E0 - M X^||_F <= 1e-3 ||E0||_F
+// (||E0||_F^2 = kap); rejected or absent seeds start cold (first = 1).
+__global__ void seed_gate_kernel(const double2* __restrict__ R0, int n, int kap, const int* __restrict__ skip,
+                                 int* __restrict__ first, int* __restrict__ used, const int* __restrict__ out_index) {
+  __shared__ double red[32];
+  const int item = blockIdx.x;
+  if (skip[item]) {
+    if (threadIdx.x == 0) {
+      first[item] = 1;
+      if (used) used[out_index[item]] = 0;
+    }
+    return;
+  }
+  const double2* R = R0 + size_t(item) * n * kap;
+  double s = 0.0;
+  for (size_t t = threadIdx.x; t < size_t(n) * kap; t += blockDim.x) s += R[t].x * R[t].x + R[t].y * R[t].y;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < int(blockDim.x) / 32; ++w) tot += red[w];
+    const int ok = isfinite(tot) && tot <= 1e-6 * kap;
+    first[item] = ok ? 0 : 1;
+    if (used) used[out_index[item]] = ok;
+  }
+}
+
 // ---------------------------------------------------------------- driver --
 size_t mixed_item_bytes(int n, int ld, int kap) {
   return a256(size_t(ld) * n * 8)          // M32
@@ -702,7 +780,7 @@ size_t mixed_item_bytes(int n, int ld, int kap) {
          + a256(size_t(n) * 4)             // perm
          + 3 * a256(size_t(n) * kap * 16)  // X, R, X as double-float pairs
          + a256(size_t(kap) * kap * 16)    // Sinv
-         + 768                             // norms, previous norms, conv, error word
+         + 1280                            // norms, previous norms, conv, error word, seed flags
          + tc_pack_bytes_per_item(n);      // tensor-core operand packs
 }
 
@@ -721,6 +799,8 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   double* prevn = reinterpret_cast<double*>(take(size_t(items) * 8));
   int* conv = reinterpret_cast<int*>(take(size_t(items) * 4));
   int* err = reinterpret_cast<int*>(take(4));
+  int* first_flags = reinterpret_cast<int*>(take(size_t(items) * 4));
+  int* skip = reinterpret_cast<int*>(take(size_t(items) * 4));
   char* packs = take(size_t(items) * tc_pack_bytes_per_item(n));
   const size_t stride = c.stride;   // same element stride for M64 and M32
 
@@ -800,6 +880,25 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     return MUST_EUNSUPPORTED;
   }
   const int iters = std::max(c.opts.max_iter, 0);
+  const bool seeded = c.seed && c.seed_mask;
+  if (seeded) {
+    // X = X^ from the predicted tau_00, R = E0 - M X^ for seeded items, gate
+    ProfScope ps(PH_OTHER, st);
+    seed_x_kernel<<<dim3((n + 127) / 128, items), 128, 0, st>>>(c.M64, c.opts.residual == 1, stride, ld, n, kap,
+                                                                c.seed, c.seed_mask, c.out_index, X, skip);
+    if (c.opts.residual == 1) {
+      const size_t cnt = size_t(items) * n * kap;
+      split_x_kernel<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(X, Xdf, cnt, skip, size_t(n) * kap);
+      residual_df_kernel<<<gres, tres, size_t(64) * kap * 16, st>>>(reinterpret_cast<const float4*>(c.M64), stride,
+                                                                      ld, n, kap, Xdf, R, skip, nullptr);
+      prof_launched(PH_OTHER, 2);
+    } else {
+      residual64_kernel<<<gres, tres, smem_res, st>>>(c.M64, stride, ld, n, kap, X, R, skip, nullptr);
+      prof_launched(PH_OTHER, 1);
+    }
+    seed_gate_kernel<<<items, 256, 0, st>>>(R, n, kap, skip, first_flags, c.seed_used, c.out_index);
+    prof_launched(PH_OTHER, 2);
+  }
   for (int it = 0; it <= iters; ++it) {
     const bool first = (it == 0);
     if (!first) {
@@ -821,10 +920,12 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       ProfScope ps(PH_CORRECT, st);
       if (G == 8)
         correct_kernel<8><<<gcorr, 512, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
-                                                         conv, first, prof_work_counter(PH_CORRECT));
+                                                         conv, first, (first && seeded) ? first_flags : nullptr,
+                                                         prof_work_counter(PH_CORRECT));
       else
         correct_kernel<4><<<gcorr, 512, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
-                                                         conv, first, prof_work_counter(PH_CORRECT));
+                                                         conv, first, (first && seeded) ? first_flags : nullptr,
+                                                         prof_work_counter(PH_CORRECT));
       prof_launched(PH_CORRECT, 1);
     }
     if (first) {

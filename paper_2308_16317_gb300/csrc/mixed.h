@@ -16,6 +16,10 @@ struct MixedChunk {
   int* status_out;
   char* ws;
   must_solve_opts opts;
+  // learned warm start (NULL when absent): per output block, indexed like tau
+  const double2* seed;      // [n_out*nE][kap][kap] column-major
+  const int* seed_mask;     // 1 = try the seed
+  int* seed_used;           // 1 = the seed passed the residual gate
 };
 
 size_t mixed_item_bytes(int n, int ld, int kap);

@@ -74,6 +74,14 @@ extern "C" size_t must_workspace_bytes(const must_liz* z, int32_t n_items, const
   return stage + size_t(n_items) * item_bytes(z->n, ld, z->kap, o.precision) + 4096;
 }
 
+// Seeds of must_tau00_solve_seeded for the call in progress on this thread.
+struct SeedArgs {
+  const double2* seed;
+  const int* mask;
+  int* used;
+};
+static thread_local const SeedArgs* g_seed = nullptr;
+
 // One chunk: items (LIZ j, spin, energy) of the (padded) order c.n, all in
 // the workspace `ws`.  Carves per-item storage, assembles, eliminates and
 // writes tau_00 / status through out_index.
@@ -117,6 +125,9 @@ static must_status run_chunk(AsmChunk c, int items, const ChunkIndex& ci, const 
     mc.asmc = c; mc.n = n; mc.ld = ld; mc.kap = kap; mc.items = items; mc.M64 = M64; mc.stride = stride;
     mc.piv = piv; mc.status = st_item; mc.out_index = out_index; mc.tau = tau_dev; mc.status_out = status_dev;
     mc.ws = mixed_ws; mc.opts = o;
+    mc.seed = g_seed ? g_seed->seed : nullptr;
+    mc.seed_mask = g_seed ? g_seed->mask : nullptr;
+    mc.seed_used = g_seed ? g_seed->used : nullptr;
     must_status s = mixed_solve_chunk(mc, st);
     if (s != MUST_OK) return s;
   }
@@ -500,4 +511,32 @@ extern "C" int32_t must_tune_get(int32_t knob) {
     case 1: return tc_get_tile_n();
   }
   return -1;
+}
+
+// --------------------------------------------------------------------------
+// Seeded solve (learned warm start): see include/must.h.
+extern "C" must_status must_tau00_solve_seeded(const must_liz* liz, int32_t nE, const double* E, const double* tinv,
+                                               int32_t n_species, int32_t nspin, const must_solve_opts* opts,
+                                               void* workspace, size_t ws_bytes, const double* tau_seed,
+                                               const int32_t* seed_mask, double* tau00, int32_t* status,
+                                               int32_t* seed_used, void* stream) {
+  must_solve_opts o;
+  must_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.precision == MUST_FP64) {
+    must_set_error("must_tau00_solve_seeded: the seed enters the refinement of a mixed-precision path");
+    return MUST_EINVAL;
+  }
+  if (!liz || !tau_seed || !seed_mask || !must_is_device_ptr(tau_seed) || !must_is_device_ptr(seed_mask) ||
+      (seed_used && !must_is_device_ptr(seed_used)) || !must_is_device_ptr(tau00)) {
+    must_set_error("must_tau00_solve_seeded: tau_seed, seed_mask, seed_used and tau00 must be device memory");
+    return MUST_EINVAL;
+  }
+  SeedArgs a{reinterpret_cast<const double2*>(tau_seed), seed_mask, seed_used};
+  g_seed = &a;
+  const must_liz* arr[1] = {liz};
+  must_status s = solve_common(1, arr, nE, E, tinv, n_species, nspin, &o, workspace, ws_bytes, tau00, status,
+                               stream);
+  g_seed = nullptr;
+  return s;
 }
