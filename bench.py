@@ -401,6 +401,108 @@ def run_supercell(args):
         print(json.dumps(line))
 
 
+def run_warmstart(args):
+    """Learned warm start end to end: tau_00 training data from the method on
+    seeded random 135-site LIZs, training with the library's kernels, then on
+    the supercell's per-site LIZs: prediction error of the network vs linear
+    interpolation, residual-gate acceptance of the seeds, and the throughput
+    of the seeded schedule (even points cold, odd points seeded) vs solving
+    every point cold."""
+    import torch
+    from paper_2308_16317_gb300 import binding as B
+    from paper_2308_16317_gb300 import build as libbuild
+    from paper_2308_16317_gb300 import warmstart as wsm
+    from paper_2308_16317_gb300 import workload as wl
+    from paper_2308_16317_gb300.runner import Session
+    libbuild.build()
+    B.load()
+    opts = B.must_default_opts(PREC[args.precision], residual=1 if args.residual == "df" else 0)
+    t0 = time.perf_counter()
+    train_w = wsm.random_liz_workload(100000, args.train_lizs)
+    tau_tr = wsm.solve_all(train_w, opts)
+    t_gen = time.perf_counter() - t0
+    model = wsm.WarmStart(max_batch=1024)
+    tp, tn, tt, E3, sp, oc = wsm.samples_from_solution(tau_tr, train_w)
+    x, scale, interp = model.features(tp, tn, E3, sp, oc)
+    y = model.targets(tt, scale, interp)
+    t0 = time.perf_counter()
+    hist = model.train(x, y, epochs=30, batch=256, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del tau_tr, x, y
+    full = wl.batched_supercell()
+    ev = wl.Workload(full.name, full.lmax, full.lizs[:args.n_lizs], wl.semicircle_contour(32, im_min=0.005),
+                     full.v_species, full.r_mt)
+    nE = len(ev.energies)
+    even = [k for k in range(nE) if k not in wsm.predicted_points(nE)]
+    odd = wsm.predicted_points(nE)
+    e_net, e_lin, used_all, t_cold, t_seed, n_solves, max_dev = [], [], [], 0.0, 0.0, 0, 0.0
+
+    def ev_sub(lizs, ks):
+        return wl.Workload(ev.name, ev.lmax, lizs, ev.energies[ks], ev.v_species, ev.r_mt)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), out
+
+    for j, liz in enumerate(ev.lizs):
+        s_all = Session(ev_sub([liz], list(range(nE))))
+        ms_c, (tau_c, st_c) = timed(lambda: s_all.solve(opts))
+        s_even = Session(ev_sub([liz], even))
+        s_odd = Session(ev_sub([liz], odd))
+        ms_e, (tau_e, _) = timed(lambda: s_even.solve(opts))
+        # predict the odd points from their solved neighbours
+        te = tau_e.transpose(-1, -2)                      # [n_out][len(even)][kap][kap] (row, col)
+        pos = {k: i for i, k in enumerate(even)}
+        prev = torch.stack([te[s_, pos[k - 1]] for s_ in range(2) for k in odd])
+        nxt = torch.stack([te[s_, pos[k + 1]] for s_ in range(2) for k in odd])
+        Et = torch.tensor(np.asarray(ev.energies), device=prev.device)
+        E3 = torch.stack([torch.stack([Et[k - 1], Et[k], Et[k + 1]]) for _ in range(2) for k in odd]).contiguous()
+        spin = torch.tensor([1.0] * len(odd) + [-1.0] * len(odd), dtype=torch.float32, device=prev.device)
+        occ = torch.tensor(np.stack([wsm.occupancy(liz)] * (2 * len(odd))), device=prev.device)
+        ms_p, (pred, interp) = timed(lambda: model.predict(prev.contiguous(), nxt.contiguous(), E3, spin, occ))
+        seed = pred.reshape(2, len(odd), 16, 16).transpose(-1, -2).contiguous()   # column-major blocks
+        mask = torch.ones((2, len(odd)), dtype=torch.int32, device=prev.device)
+        items = 2 * len(odd)
+        nb = B.must_workspace_bytes(s_odd.lizs[0], items, opts)
+        wsp = torch.empty(nb, dtype=torch.uint8, device=prev.device)
+        tau_o, st_o = s_odd.alloc_out(1)
+        used = torch.zeros((2, len(odd)), dtype=torch.int32, device=prev.device)
+        ms_o, _ = timed(lambda: B.must_tau00_solve_seeded(s_odd.lizs[0], s_odd.E, s_odd.tinv, s_odd.n_species,
+                                                          s_odd.nspin, opts, wsp, nb, seed, mask, tau_o[0], st_o[0],
+                                                          used))
+        truth = tau_c.transpose(-1, -2)[0][:, odd].reshape(items, 16, 16)
+        e_net += wsm.rel_err(pred, truth).tolist()
+        e_lin += wsm.rel_err(interp, truth).tolist()
+        used_all += used.flatten().tolist()
+        got = tau_o[0].transpose(-1, -2).reshape(items, 16, 16)
+        max_dev = max(max_dev, float(wsm.rel_err(got, truth).max()))
+        t_cold += ms_c
+        t_seed += ms_e + ms_p + ms_o
+        n_solves += 2 * nE
+    line = {"metric": "learned warm start on batched supercell LIZs", "impl": "gb300",
+            "train": {"lizs": args.train_lizs, "samples": int(tp.shape[0]), "generate_s": t_gen, "train_s": t_train,
+                      "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1]},
+            "eval": {"lizs": len(ev.lizs), "predicted_points": len(e_net),
+                     "median_rel_err_network": float(np.median(e_net)),
+                     "median_rel_err_interpolation": float(np.median(e_lin)),
+                     "p95_rel_err_network": float(np.percentile(e_net, 95)),
+                     "p95_rel_err_interpolation": float(np.percentile(e_lin, 95)),
+                     "prediction_gain": float(np.median(e_lin) / np.median(e_net)),
+                     "seed_acceptance": float(np.mean(used_all)),
+                     "seeded_vs_cold_max_rel_diff": max_dev,
+                     "solves_per_s_cold": n_solves / (t_cold / 1e3),
+                     "solves_per_s_seeded_schedule": n_solves / (t_seed / 1e3)},
+            "precision": args.precision, "residual": args.residual}
+    print(json.dumps(line))
+
+
 def cpu_baseline(w, sample: int):
     """The oracle on the host cores: `sample` (energy, spin) solves of the same
     LIZ, one per thread, timed end to end."""
@@ -461,10 +563,12 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0)
-    ap.add_argument("--workload", default="liz135", choices=["liz135", "supercell"],
+    ap.add_argument("--workload", default="liz135", choices=["liz135", "supercell", "warmstart"],
                     help="liz135: the benchmark workload; supercell: per-site LIZs of the 256-site supercell "
                          "with vacancies (uneven n), batched and replayed as a captured plan")
-    ap.add_argument("--n-lizs", type=int, default=32, help="supercell mode: LIZs per step")
+    ap.add_argument("--n-lizs", type=int, default=32, help="supercell / warmstart mode: evaluation LIZs")
+    ap.add_argument("--train-lizs", type=int, default=400,
+                    help="warmstart mode: random 135-site training LIZs (x 2 spins x 15 predicted points)")
     ap.add_argument("--n-energies", type=int, default=32,
                     help="contour energies per step (32 = the benchmark workload; fewer for ncu captures)")
     args = ap.parse_args()
@@ -474,6 +578,8 @@ def main():
         run_reference(args)
     elif args.workload == "supercell":
         run_supercell(args)
+    elif args.workload == "warmstart":
+        run_warmstart(args)
     else:
         run_ours(args)
 

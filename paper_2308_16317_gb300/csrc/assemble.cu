@@ -194,6 +194,7 @@ struct AsmArgs {
   int ld;
   size_t stride;          // elements between items (both copies)
   const double* scale;    // [item][n] (required when M32 != NULL or scale64)
+  const float* scale32;   // [item][n] FP32 copy of scale (mixed path)
   int items_per_e;        // nspin (collinear) or 1 (canted)
   int scale64;            // 1: the FP64 copy is equilibrated too (D M D)
   int m64_df;             // 1: the M64 buffer holds M as FP32 pairs (hi.re, hi.im, lo.re, lo.im)
@@ -222,30 +223,60 @@ __device__ __forceinline__ cd diag_entry(const AsmArgs& A, int it, int a) {
   return 0.5 * (av + bv) + (sg == 0 ? 0.5 * ez : -0.5 * ez) * (av - bv);
 }
 
-__global__ void scale_kernel(AsmArgs A, double* __restrict__ scale) {
+__global__ void scale_kernel(AsmArgs A, double* __restrict__ scale, float* __restrict__ scale32) {
   const int it = blockIdx.y;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < A.n; a += gridDim.x * blockDim.x) {
     const double m = sqrt(sqrt(cnorm(diag_entry(A, it, a))));
-    scale[size_t(it) * A.n + a] = (m > 0.0 && isfinite(m)) ? 1.0 / m : 1.0;
+    const double sc = (m > 0.0 && isfinite(m)) ? 1.0 / m : 1.0;
+    scale[size_t(it) * A.n + a] = sc;
+    if (scale32) scale32[size_t(it) * A.n + a] = float(sc);
+  }
+}
+
+// v -> (hi, lo) with hi + lo carrying 24 + 24 significant bits, built from the
+// bit fields of the double with integer operations (hi: v truncated to a
+// float's significand; lo: the remaining 29 bits, rounded to a float), so
+// the split costs no FP64-pipe conversions.  Values outside the normal float
+// range fall back to the conversion instructions.
+__device__ __forceinline__ void split_df(double v, float& hi, float& lo) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int e = int((b >> 52) & 0x7FF);
+  if (e >= 949 && e <= 1150) {
+    const unsigned sign = unsigned(b >> 63) << 31;
+    hi = __uint_as_float(sign | (unsigned(e - 896) << 23) | unsigned((b >> 29) & 0x7FFFFF));
+    const float m = __uint2float_rn(unsigned(b & 0x1FFFFFFFull));            // low 29 bits
+    const float p2 = __uint_as_float(unsigned(e - 948) << 23);                // 2^(e - 1075)
+    lo = __uint_as_float(__float_as_uint(m * p2) | sign);
+  } else if (e < 949) {   // |v| < 2^-74: negligible next to any row of M
+    hi = float(v);
+    lo = 0.f;
+  } else {
+    hi = float(v);
+    lo = float(v - double(hi));
   }
 }
 
 __device__ __forceinline__ void store_elem(const AsmArgs& A, int it, int row, int col, cd v) {
   const size_t off = size_t(it) * A.stride + size_t(col) * A.ld + row;
-  if (A.M64 && A.m64_df) {
-    const float hr = float(v.x), hi = float(v.y);
-    reinterpret_cast<float4*>(A.M64)[off] = make_float4(hr, hi, float(v.x - double(hr)), float(v.y - double(hi)));
-  } else if (A.M64) {
+  if (A.M64 && A.M32 && !A.m64_df) A.M64[off] = make_double2(v.x, v.y);   // FP64 residual copy
+  if (A.M32 || (A.M64 && A.m64_df)) {
+    float hr, lr, hi, li;
+    split_df(v.x, hr, lr);
+    split_df(v.y, hi, li);
+    if (A.M64 && A.m64_df) reinterpret_cast<float4*>(A.M64)[off] = make_float4(hr, hi, lr, li);
+    if (A.M32) {
+      const float s = A.scale32[size_t(it) * A.n + row] * A.scale32[size_t(it) * A.n + col];
+      A.M32[off] = make_float2(hr * s + lr * s, hi * s + li * s);
+    }
+    return;
+  }
+  if (A.M64) {
     if (A.scale64) {
       const double s = A.scale[size_t(it) * A.n + row] * A.scale[size_t(it) * A.n + col];
       A.M64[off] = make_double2(s * v.x, s * v.y);
     } else {
       A.M64[off] = make_double2(v.x, v.y);
     }
-  }
-  if (A.M32) {
-    const double s = A.scale[size_t(it) * A.n + row] * A.scale[size_t(it) * A.n + col];
-    A.M32[off] = make_float2(float(s * v.x), float(s * v.y));
   }
 }
 
@@ -380,7 +411,7 @@ void launch_assemble(const AsmArgs& A, int max_units, cudaStream_t st) {
   const int n_items = A.items_per_e * A.nEc * A.n_lz;
   if (A.M32 || A.scale64) {
     dim3 g((A.n + 255) / 256, n_items);
-    scale_kernel<<<g, 256, 0, st>>>(A, const_cast<double*>(A.scale));
+    scale_kernel<<<g, 256, 0, st>>>(A, const_cast<double*>(A.scale), const_cast<float*>(A.scale32));
     prof_launched(PH_ASSEMBLE, 1);
   }
   dim3 grid((max_units + 7) / 8, A.nEc, A.n_lz);
@@ -406,6 +437,7 @@ void launch_assemble_chunk(const AsmChunk& c, cudaStream_t st) {
   A.g_start = z0->d_g_start; A.g_L2 = z0->d_g_L2; A.g_c = z0->d_g_c;
   A.e0 = c.e0; A.nEc = c.nEc; A.nE = c.nE; A.nspin = c.nspin; A.n_species = c.n_species;
   A.E = c.E; A.tinv = c.tinv; A.M64 = c.M64; A.M32 = c.M32; A.ld = c.ld; A.stride = c.stride; A.scale = c.scale;
+  A.scale32 = c.scale32;
   A.items_per_e = z0->canted ? 1 : c.nspin;
   A.scale64 = c.scale64;
   A.m64_df = c.m64_df;

@@ -668,6 +668,10 @@ __global__ void check_kernel(double* __restrict__ norms, double* __restrict__ pr
       if (status[it] == ST_OK) status[it] = ST_NONFINITE;
     } else if (last < 2 && dn <= tol * tol * xn) {
       conv[it] = 1;
+    } else if (last < 2 && prev[it] > 0.0 && dn <= 0.25 * prev[it] && dn * dn <= tol * tol * xn * prev[it]) {
+      // linear convergence at rate rho = |delta_k| / |delta_{k-1}| <= 1/2: the
+      // error left after this correction is ~rho |delta_k| <= tol |X|
+      conv[it] = 1;
     } else if (last < 2 && prev[it] > 0.0 && dn > 0.25 * prev[it]) {
       // corrections no longer shrink (|delta| ratio > 1/2): the residual's own
       // rounding floor is reached above tol; stop and report it
@@ -678,6 +682,16 @@ __global__ void check_kernel(double* __restrict__ norms, double* __restrict__ pr
     }
     prev[it] = dn;
   }
+  norms[2 * it] = 0.0;
+  norms[2 * it + 1] = 0.0;
+}
+
+// After the first (unrefined) solve: remember |delta_0|^2 = |X_0|^2 as the
+// previous correction, and clear the accumulators.
+__global__ void first_norms_kernel(double* __restrict__ norms, double* __restrict__ prev, int items) {
+  const int it = blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= items) return;
+  prev[it] = norms[2 * it];
   norms[2 * it] = 0.0;
   norms[2 * it + 1] = 0.0;
 }
@@ -777,6 +791,7 @@ __global__ void seed_gate_kernel(const double2* __restrict__ R0, int n, int kap,
 size_t mixed_item_bytes(int n, int ld, int kap) {
   return a256(size_t(ld) * n * 8)          // M32
          + a256(size_t(n) * 8)             // scale
+         + a256(size_t(n) * 4)             // scale (FP32)
          + a256(size_t(n) * 4)             // perm
          + 3 * a256(size_t(n) * kap * 16)  // X, R, X as double-float pairs
          + a256(size_t(kap) * kap * 16)    // Sinv
@@ -790,6 +805,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   auto take = [&](size_t b) { char* p = cur; cur += a256(b); return p; };
   float2* M32 = reinterpret_cast<float2*>(take(size_t(items) * ld * n * 8));
   double* scale = reinterpret_cast<double*>(take(size_t(items) * n * 8));
+  float* scale32 = reinterpret_cast<float*>(take(size_t(items) * n * 4));
   int* perm = reinterpret_cast<int*>(take(size_t(items) * n * 4));
   double2* X = reinterpret_cast<double2*>(take(size_t(items) * n * kap * 16));
   double2* R = reinterpret_cast<double2*>(take(size_t(items) * n * kap * 16));
@@ -807,6 +823,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   AsmChunk a = c.asmc;
   a.M32 = M32;
   a.scale = scale;
+  a.scale32 = scale32;
   launch_assemble_chunk(a, st);
   cudaMemsetAsync(norms, 0, sizeof(double) * 2 * items, st);
   cudaMemsetAsync(prevn, 0, sizeof(double) * items, st);
@@ -929,7 +946,8 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       prof_launched(PH_CORRECT, 1);
     }
     if (first) {
-      cudaMemsetAsync(norms, 0, sizeof(double) * 2 * items, st);
+      first_norms_kernel<<<(items + 127) / 128, 128, 0, st>>>(norms, prevn, items);
+      prof_launched(PH_OTHER, 1);
     } else {
       check_kernel<<<(items + 127) / 128, 128, 0, st>>>(norms, prevn, conv, c.status, items, c.opts.tol,
                                                          it == iters);

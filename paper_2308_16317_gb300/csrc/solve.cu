@@ -112,6 +112,7 @@ static must_status run_chunk(AsmChunk c, int items, const ChunkIndex& ci, const 
   c.stride = stride;
   if (o.precision == MUST_FP64) {
     c.M32 = nullptr;
+    c.scale32 = nullptr;
     c.scale = o.equilibrate ? scale64 : nullptr;
     c.scale64 = o.equilibrate ? 1 : 0;
     c.m64_df = 0;

@@ -30,6 +30,7 @@ struct AsmChunk {
   int ld;
   size_t stride;
   double* scale;
+  float* scale32;   // FP32 copy of scale (mixed path; NULL otherwise)
   int scale64;      // equilibrate the FP64 copy as well (FP64 path)
   int m64_df;       // store the unscaled matrix as FP32 pairs (double-float residual)
 };
