@@ -477,7 +477,7 @@ def run_warmstart(args):
         ms_o, _ = timed(lambda: B.must_tau00_solve_seeded(s_odd.lizs[0], s_odd.E, s_odd.tinv, s_odd.n_species,
                                                           s_odd.nspin, opts, wsp, nb, seed, mask, tau_o[0], st_o[0],
                                                           used))
-        truth = tau_c.transpose(-1, -2)[0][:, odd].reshape(items, 16, 16)
+        truth = tau_c.transpose(-1, -2)[:, odd].reshape(items, 16, 16)     # [spin][odd k] order
         e_net += wsm.rel_err(pred, truth).tolist()
         e_lin += wsm.rel_err(interp, truth).tolist()
         used_all += used.flatten().tolist()

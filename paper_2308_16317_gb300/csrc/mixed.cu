@@ -787,6 +787,39 @@ __global__ void seed_gate_kernel(const double2* __restrict__ R0, int n, int kap,
   }
 }
 
+// Per-thread side stream (highest priority) and two events for the panel
+// look-ahead of the elimination, created on first use on each device.
+namespace {
+struct SideStream {
+  int dev = -1;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e1 = nullptr, e2 = nullptr;
+};
+thread_local SideStream g_side;
+}  // namespace
+
+static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (g_side.s == nullptr || g_side.dev != dev) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    SideStream n;
+    n.dev = dev;
+    if (cudaStreamCreateWithPriority(&n.s, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&n.e1, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&n.e2, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    g_side = n;
+  }
+  *s = g_side.s;
+  *e1 = g_side.e1;
+  *e2 = g_side.e2;
+  return true;
+}
+
 // ---------------------------------------------------------------- driver --
 size_t mixed_item_bytes(int n, int ld, int kap) {
   return a256(size_t(ld) * n * 8)          // M32
@@ -839,14 +872,28 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     }
   }
   const int nb = tc_panel_width(c.opts.precision);
+  // Look-ahead: the trailing update of step k is split so that the columns of
+  // panel k+1 (the first tile) are updated first; panel k+1 then runs on a
+  // high-priority side stream while the rest of the update streams through
+  // HBM, and the main stream waits for it before the next row swaps.
+  cudaStream_t ss = nullptr;
+  cudaEvent_t ev_next = nullptr, ev_panel = nullptr;
+  const bool lookahead = side_stream(&ss, &ev_next, &ev_panel);
+  const size_t panel_smem = size_t(leaf_width(n)) * n * sizeof(float2);
+  const int bn = tc_tile_n();
+  auto launch_panel = [&](int k, int w, cudaStream_t s) {
+    ProfScope ps(PH_PANEL, s);
+    panel32_kernel<<<items, PPT, panel_smem, s>>>(M32, stride, ld, n, r, k, w, c.piv, c.status, conv);
+    prof_launched(PH_PANEL, 1, items);
+  };
+  bool panel_ready = false;   // panel k0 already launched on the side stream
   for (int k0 = 0; k0 < r; k0 += nb) {
     const int nbe = std::min(nb, r - k0);
-    {
-      ProfScope ps(PH_PANEL, st);
-      panel32_kernel<<<items, PPT, size_t(leaf_width(n)) * n * sizeof(float2), st>>>(M32, stride, ld, n, r, k0,
-                                                                                      nbe, c.piv, c.status, conv);
-      prof_launched(PH_PANEL, 1, items);
-    }
+    if (panel_ready)
+      cudaStreamWaitEvent(st, ev_panel, 0);
+    else
+      launch_panel(k0, nbe, st);
+    panel_ready = false;
     {
       ProfScope ps(PH_SWAP, st);
       laswp32_kernel<<<dim3((n - nbe + 255) / 256, items), 256, 0, st>>>(M32, stride, ld, n, r, k0, nbe, c.piv);
@@ -859,8 +906,22 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
         trsm32_kernel<<<dim3((rem + 7) / 8, items), 256, 0, st>>>(M32, stride, ld, n, k0, nbe);
         prof_launched(PH_TRSM, 1, items);
       }
-      if (!tc_trailing_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, st))
-        return MUST_ECUDA;
+      if (!tc_pack(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, st)) return MUST_ECUDA;
+      const int k1 = k0 + nbe;
+      if (lookahead && k1 < r && rem > bn) {
+        if (!tc_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, 0, bn, st))
+          return MUST_ECUDA;
+        cudaEventRecord(ev_next, st);
+        cudaStreamWaitEvent(ss, ev_next, 0);
+        launch_panel(k1, std::min(nb, r - k1), ss);
+        cudaEventRecord(ev_panel, ss);
+        panel_ready = true;
+        if (!tc_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, bn, -1, st))
+          return MUST_ECUDA;
+      } else {
+        if (!tc_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, 0, -1, st))
+          return MUST_ECUDA;
+      }
     }
   }
   {

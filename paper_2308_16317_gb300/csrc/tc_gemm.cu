@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -131,6 +132,7 @@ struct TcParams {
   int ksteps;    // K stages per split pass
   int* err;      // workspace error word
   int tf32;
+  int col_tile0; // first column tile of this launch
 };
 
 template <int BN, int STAGES>
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(256, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.z;
   const int row0 = blockIdx.x * BM;     // real rows of C' relative to the trailing block
-  const int col0 = blockIdx.y * BN;     // complex columns relative to the trailing block
+  const int col0 = (blockIdx.y + P.col_tile0) * BN;   // complex columns relative to the trailing block
   const int nsteps = 3 * P.ksteps;
 
   if (threadIdx.x == 0) {
@@ -364,14 +366,14 @@ int g_tile_n = 128;   // 128 or 256 complex columns per tile (autotuned)
 
 template <int BN>
 void launch_tc(const CUtensorMap& mah, const CUtensorMap& mal, const CUtensorMap& mbh, const CUtensorMap& mbl,
-               const TcParams& P, int m, int items, cudaStream_t st) {
+               const TcParams& P, int m, int items, int col_tiles, cudaStream_t st) {
   constexpr size_t smem = size_t(TC_STAGES) * (BM * KB + BN * KB) + 1024;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(tc_update_kernel<BN, TC_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     attr = true;
   }
-  dim3 grid((2 * m + BM - 1) / BM, (m + BN - 1) / BN, items);
+  dim3 grid((2 * m + BM - 1) / BM, col_tiles, items);
   tc_update_kernel<BN, TC_STAGES><<<grid, 256, smem, st>>>(mah, mal, mbh, mbl, P);
 }
 
@@ -401,51 +403,76 @@ size_t tc_pack_bytes_per_item(int n) {
 
 static bool tc_supported = true;
 
-bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items,
-                        char* packs, int* err, cudaStream_t st) {
-  const bool tf32 = (precision == MUST_MIXED_TF32X3);
+int tc_tile_n() { return g_tile_n; }
+
+namespace {
+struct PackGeom {
+  bool tf32;
+  int base, m, rows_pad, Kp, es, item_rows;
+  size_t pbytes;
+  char *pa_hi, *pa_lo, *pb_hi, *pb_lo;
+};
+PackGeom pack_geom(int precision, int n, int k0, int nbe, int items, char* packs) {
+  PackGeom g;
+  g.tf32 = (precision == MUST_MIXED_TF32X3);
+  g.base = k0 + nbe;
+  g.m = n - g.base;
+  g.rows_pad = 2 * ((n + 127) / 128) * 128;
+  g.Kp = kp_of(g.tf32);
+  g.es = g.tf32 ? 4 : 2;
+  g.pbytes = a256(size_t(g.rows_pad) * g.Kp * 4);
+  g.pa_hi = packs;
+  g.pa_lo = packs + size_t(items) * g.pbytes;
+  g.pb_hi = packs + 2 * size_t(items) * g.pbytes;
+  g.pb_lo = packs + 3 * size_t(items) * g.pbytes;
+  g.item_rows = int(g.pbytes / (size_t(g.Kp) * g.es));
+  return g;
+}
+}  // namespace
+
+bool tc_pack(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
+             cudaStream_t st) {
+  const PackGeom g = pack_geom(precision, n, k0, nbe, items, packs);
+  if (g.m <= 0) return true;
+  ProfScope ps(PH_PACK, st);
+  const int half = g.Kp / 2;
+  const int ta = g.m * half;
+  dim3 grid((ta + 255) / 256, items);
+  if (g.tf32) {
+    pack_a_kernel<float><<<grid, 256, 0, st>>>(A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows,
+                                               reinterpret_cast<float*>(g.pa_hi), reinterpret_cast<float*>(g.pa_lo), 1);
+    pack_b_kernel<float><<<grid, 256, 0, st>>>(A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows,
+                                               reinterpret_cast<float*>(g.pb_hi), reinterpret_cast<float*>(g.pb_lo), 1);
+  } else {
+    pack_a_kernel<uint16_t><<<grid, 256, 0, st>>>(A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows,
+                                                  reinterpret_cast<uint16_t*>(g.pa_hi),
+                                                  reinterpret_cast<uint16_t*>(g.pa_lo), 0);
+    pack_b_kernel<uint16_t><<<grid, 256, 0, st>>>(A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows,
+                                                  reinterpret_cast<uint16_t*>(g.pb_hi),
+                                                  reinterpret_cast<uint16_t*>(g.pb_lo), 0);
+  }
+  prof_launched(PH_PACK, 2, items);
+  return true;
+}
+
+bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
+               int* err, int col_lo, int col_hi, cudaStream_t st) {
   if (!get_encoder()) {
     must_set_error("cuTensorMapEncodeTiled is not available");
     return false;
   }
-  const int base = k0 + nbe;
-  const int m = n - base;
-  if (m <= 0) return true;
-  const int rows_pad = 2 * ((n + 127) / 128) * 128;   // A' rows (2n padded); B' uses the first n_pad rows
-  const int Kp = kp_of(tf32);
-  const int es = tf32 ? 4 : 2;
-  const size_t pbytes = a256(size_t(rows_pad) * Kp * 4);   // slot size (fits either precision)
-  char* pa_hi = packs;
-  char* pa_lo = packs + size_t(items) * pbytes;
-  char* pb_hi = packs + 2 * size_t(items) * pbytes;
-  char* pb_lo = packs + 3 * size_t(items) * pbytes;
-  // item stride inside a slot group = pbytes; tensor maps use rows_pad rows per item
-  const int item_rows = int(pbytes / (size_t(Kp) * es));
-  {
-    ProfScope ps(PH_PACK, st);
-    const int half = Kp / 2;
-    const int ta = m * half;
-    dim3 g((ta + 255) / 256, items);
-    if (tf32) {
-      pack_a_kernel<float><<<g, 256, 0, st>>>(A, stride, ld, n, k0, nbe, base, Kp, item_rows,
-                                              reinterpret_cast<float*>(pa_hi), reinterpret_cast<float*>(pa_lo), 1);
-      pack_b_kernel<float><<<g, 256, 0, st>>>(A, stride, ld, n, k0, nbe, base, Kp, item_rows,
-                                              reinterpret_cast<float*>(pb_hi), reinterpret_cast<float*>(pb_lo), 1);
-    } else {
-      pack_a_kernel<uint16_t><<<g, 256, 0, st>>>(A, stride, ld, n, k0, nbe, base, Kp, item_rows,
-                                                 reinterpret_cast<uint16_t*>(pa_hi), reinterpret_cast<uint16_t*>(pa_lo),
-                                                 0);
-      pack_b_kernel<uint16_t><<<g, 256, 0, st>>>(A, stride, ld, n, k0, nbe, base, Kp, item_rows,
-                                                 reinterpret_cast<uint16_t*>(pb_hi), reinterpret_cast<uint16_t*>(pb_lo),
-                                                 0);
-    }
-    prof_launched(PH_PACK, 2, items);
-  }
-  CUtensorMap mah, mal, mbh, mbl;
+  const PackGeom g = pack_geom(precision, n, k0, nbe, items, packs);
+  if (g.m <= 0) return true;
   const int bn = g_tile_n;
-  if (!make_map(&mah, pa_hi, tf32, Kp, item_rows, items, BM) || !make_map(&mal, pa_lo, tf32, Kp, item_rows, items, BM) ||
-      !make_map(&mbh, pb_hi, tf32, Kp, item_rows, items, bn) ||
-      !make_map(&mbl, pb_lo, tf32, Kp, item_rows, items, bn)) {
+  const int tiles = (g.m + bn - 1) / bn;
+  const int t0 = col_lo / bn;
+  const int t1 = (col_hi < 0) ? tiles : std::min(tiles, (col_hi + bn - 1) / bn);
+  if (t1 <= t0) return true;
+  CUtensorMap mah, mal, mbh, mbl;
+  if (!make_map(&mah, g.pa_hi, g.tf32, g.Kp, g.item_rows, items, BM) ||
+      !make_map(&mal, g.pa_lo, g.tf32, g.Kp, g.item_rows, items, BM) ||
+      !make_map(&mbh, g.pb_hi, g.tf32, g.Kp, g.item_rows, items, bn) ||
+      !make_map(&mbl, g.pb_lo, g.tf32, g.Kp, g.item_rows, items, bn)) {
     must_set_error("tensor map encoding failed");
     return false;
   }
@@ -454,15 +481,22 @@ bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, 
   P.stride = stride;
   P.ld = ld;
   P.n = n;
-  P.base = base;
-  P.ksteps = Kp * es / KB;
+  P.base = g.base;
+  P.ksteps = g.Kp * g.es / KB;
   P.err = err;
-  P.tf32 = tf32 ? 1 : 0;
+  P.tf32 = g.tf32 ? 1 : 0;
+  P.col_tile0 = t0;
   ProfScope ps(PH_UPDATE, st);
   if (bn == 256)
-    launch_tc<256>(mah, mal, mbh, mbl, P, m, items, st);
+    launch_tc<256>(mah, mal, mbh, mbl, P, g.m, items, t1 - t0, st);
   else
-    launch_tc<128>(mah, mal, mbh, mbl, P, m, items, st);
+    launch_tc<128>(mah, mal, mbh, mbl, P, g.m, items, t1 - t0, st);
   prof_launched(PH_UPDATE, 1, items);
   return true;
+}
+
+bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items,
+                        char* packs, int* err, cudaStream_t st) {
+  return tc_pack(precision, A, stride, ld, n, k0, nbe, items, packs, st) &&
+         tc_update(precision, A, stride, ld, n, k0, nbe, items, packs, err, 0, -1, st);
 }

@@ -6,6 +6,15 @@ int tc_panel_width(int precision);
 size_t tc_pack_bytes_per_item(int n);
 // Returns false (with must_set_error) if the update could not be launched.
 // err: device word set to 1 by any CTA whose bounded waits ran out.
+// The update is split in two calls: tc_pack (operands of panel step k0) and
+// tc_update over the complex columns [base + col_lo, base + col_hi) of the
+// trailing block (col_hi < 0: to the end); col_lo/col_hi are rounded to the
+// tile width, which tc_tile_n() returns.
+bool tc_pack(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
+             cudaStream_t st);
+bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
+               int* err, int col_lo, int col_hi, cudaStream_t st);
+int tc_tile_n();
 bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items,
                         char* packs, int* err, cudaStream_t st);
 
