@@ -503,6 +503,37 @@ def run_warmstart(args):
     print(json.dumps(line))
 
 
+def run_cusolver_context(args):
+    """Context only: the paper's own method (LU + solve in complex128, Sec. 3.2)
+    through PyTorch's vendor-library path on this GPU, at the benchmark's
+    matrix order with 16 right-hand sides.  The cost of LU + solve depends
+    only on n, so a random well-conditioned complex128 matrix stands in for M.
+    Not the library's path; reported beside it."""
+    import torch
+    n = 2160
+    batch = 8
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = (torch.randn(batch, n, n, dtype=torch.float64, device="cuda", generator=g)
+         + 1j * torch.randn(batch, n, n, dtype=torch.float64, device="cuda", generator=g)
+         + n * torch.eye(n, dtype=torch.complex128, device="cuda"))
+    Bm = torch.zeros(batch, n, 16, dtype=torch.complex128, device="cuda")
+    Bm[:, n - 16:, :] = torch.eye(16, dtype=torch.complex128, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        torch.linalg.solve(A, Bm)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        torch.linalg.solve(A, Bm)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"metric": "context: vendor complex128 LU + solve (torch.linalg.solve), n=2160, 16 RHS",
+                      "value": batch / (ms / 1e3), "unit": UNIT, "ms_per_batch": ms, "batch": batch,
+                      "tflops_8_3_n3": batch * 8 / 3 * n ** 3 / (ms / 1e3) / 1e12}))
+
+
 def cpu_baseline(w, sample: int):
     """The oracle on the host cores: `sample` (energy, spin) solves of the same
     LIZ, one per thread, timed end to end."""
@@ -563,7 +594,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0)
-    ap.add_argument("--workload", default="liz135", choices=["liz135", "supercell", "warmstart"],
+    ap.add_argument("--workload", default="liz135", choices=["liz135", "supercell", "warmstart", "cusolver"],
                     help="liz135: the benchmark workload; supercell: per-site LIZs of the 256-site supercell "
                          "with vacancies (uneven n), batched and replayed as a captured plan")
     ap.add_argument("--n-lizs", type=int, default=32, help="supercell / warmstart mode: evaluation LIZs")
@@ -580,6 +611,8 @@ def main():
         run_supercell(args)
     elif args.workload == "warmstart":
         run_warmstart(args)
+    elif args.workload == "cusolver":
+        run_cusolver_context(args)
     else:
         run_ours(args)
 
