@@ -129,25 +129,30 @@ def traffic_from_profiles(kernel_key: str, source: str):
         return None
 
 
-def phase_work(phase: str, n: int, kap: int, nb: int, items: int, precision: str):
+def phase_work(phase: str, n: int, kap: int, nb: int, items: int, precision: str, residual: str = "df"):
     """Algorithmic work of `items` matrices in one phase of one step:
     (amount, unit, bound, kernel source, profile key)."""
     r = n - kap
     if phase == "trailing_update":
-        # complex MACs of A22 -= L21 U12 over all panels; tensor flops = 24 per
-        # complex MAC for the 3-term split (4 real MACs x 3 products x 2)
+        if precision != "fp64":
+            # HBM-bound on the mixed path: every panel step reads and writes the
+            # m x m complex-FP32 trailing block once (16 B per element)
+            byts = 0
+            for k0 in range(0, r, nb):
+                nbe = min(nb, r - k0)
+                m = n - k0 - nbe
+                byts += 16 * m * m
+            return float(byts) * items, "byte", "hbm", "paper_2308_16317_gb300/csrc/tc_gemm.cu", \
+                "tc_update_kernel_fcc135"
         macs = 0
         for k0 in range(0, r, nb):
             nbe = min(nb, r - k0)
             m = n - k0 - nbe
             macs += m * m * nbe
-        per = 24 if precision != "fp64" else 8
-        return macs * per * items, "flop", "tensor" if precision != "fp64" else "alu", \
-            "paper_2308_16317_gb300/csrc/tc_gemm.cu" if precision != "fp64" else \
-            "paper_2308_16317_gb300/csrc/lu64.cu", "tc_update_kernel_fcc135"
+        return macs * 8 * items, "flop", "alu", "paper_2308_16317_gb300/csrc/lu64.cu", "gemm64_kernel_fcc135"
     if phase == "residual":
         return 8.0 * n * n * kap * items, "flop", "alu", "paper_2308_16317_gb300/csrc/mixed.cu", \
-            "residual64_kernel_fcc135"
+            "residual_df_kernel_fcc135" if residual == "df" else "residual64_kernel_fcc135"
     if phase == "correction":
         return 8.0 * n * n * kap * items, "flop", "alu", "paper_2308_16317_gb300/csrc/mixed.cu", \
             "correct_kernel_fcc135"
@@ -237,7 +242,7 @@ def run_ours(args):
     peaks, peak_kind = load_peaks()
     dom = max((k for k in prof if k not in ("other",)), key=lambda k: prof[k][0])
     roofline = None
-    pw = phase_work(dom, n, kap, nb, 1, prec)
+    pw = phase_work(dom, n, kap, nb, 1, prec, args.residual)
     if pw is not None:
         per_item, unit, bound, src, key = pw
         ms_d, launches_d, items_d = prof[dom]
@@ -261,13 +266,25 @@ def run_ours(args):
             peak = (FP64_PEAK_TFLOPS if dom == "residual" or prec == "fp64" else FP32_PEAK_TFLOPS) * 1e12
             punit, scale = "TFLOP/s", 1e12
         traffic = traffic_from_profiles(key, src)
+        tensor_view = None
+        if dom == "trailing_update" and prec != "fp64":
+            # the same launches seen as tensor-core work: 24 tensor flops per complex MAC
+            # (4 real MACs x 3 split products x 2)
+            macs = 0
+            for k0 in range(0, n - kap, nb):
+                nbe = min(nb, n - kap - k0)
+                m = n - k0 - nbe
+                macs += m * m * nbe
+            tf = macs * 24.0 * items * args.steps / (ms_d / 1e3)
+            tp = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")) * 1e12
+            tensor_view = {"achieved": tf / 1e12, "peak": tp / 1e12, "unit": "TFLOP/s", "frac": tf / tp}
         roofline = {"kernel_phase": dom, "bound": bound, "achieved": achieved / scale, "peak": peak / scale,
                     "unit": punit, "frac": achieved / peak, "traffic": traffic,
                     "peak_source": (peak_kind + " (MEASURED_PEAKS)") if bound in ("tensor", "hbm")
                     else "nominal FP64/FP32 from unit counts and clocks",
                     "algorithmic_per_launch": total / max(launches_d, 1),
                     "avg_launch_ms": ms_d / max(launches_d, 1), "launches": launches_d,
-                    "share_of_step": ms_d / (ms_total if ws == 1 else ms_total)}
+                    "share_of_step": ms_d / (ms_total if ws == 1 else ms_total), "tensor_view": tensor_view}
     phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
               for k, v in prof.items() if v[1] > 0}
 
@@ -503,6 +520,54 @@ def run_warmstart(args):
     print(json.dumps(line))
 
 
+def run_canted(args):
+    """Spin-canted 135-site LIZ (M of order 2n = 4320), 32 energies down to
+    Im E = 0.00215: mixed-precision throughput, and per-energy error of the
+    mixed path against the plain FP64 path on the same GPU."""
+    import torch
+    from paper_2308_16317_gb300 import binding as B
+    from paper_2308_16317_gb300 import build as libbuild
+    from paper_2308_16317_gb300 import workload as wl
+    from paper_2308_16317_gb300.runner import Session, blocks_to_numpy
+    libbuild.build()
+    B.load()
+    w = wl.canted135(n_e=args.n_energies)
+    s = Session(w)
+    opts = B.must_default_opts(PREC[args.precision], residual=1 if args.residual == "df" else 0)
+    out = s.alloc_out(1)
+    for _ in range(args.warmup):
+        s.solve(opts, out=out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        s.solve(opts, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    tau = blocks_to_numpy(out[0][0])
+    st = out[1].cpu().numpy()
+    out64 = s.alloc_out(1)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record()
+    s.solve(B.must_default_opts(0), out=out64)
+    f1.record()
+    torch.cuda.synchronize()
+    ms64 = f0.elapsed_time(f1)
+    t64 = blocks_to_numpy(out64[0][0])
+    err = np.linalg.norm(tau - t64, axis=(-2, -1)) / np.linalg.norm(t64, axis=(-2, -1))
+    nE = len(w.energies)
+    print(json.dumps({"metric": "tau_00 solves/sec, spin-canted 135-site LIZ (order 2n = 4320)",
+                      "value": nE / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
+                      "precision": args.precision, "residual": args.residual,
+                      "plain_fp64": {"value": nE / (ms64 / 1e3), "ms_per_step": ms64},
+                      "status_ok": bool((st == 0).all()),
+                      "per_energy_rel_err_vs_fp64": [float(x) for x in err.ravel()],
+                      "im_E": [float(e.imag) for e in w.energies]}))
+
+
 def run_cusolver_context(args):
     """Context only: the paper's own method (LU + solve in complex128, Sec. 3.2)
     through PyTorch's vendor-library path on this GPU, at the benchmark's
@@ -594,7 +659,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0)
-    ap.add_argument("--workload", default="liz135", choices=["liz135", "supercell", "warmstart", "cusolver"],
+    ap.add_argument("--workload", default="liz135",
+                    choices=["liz135", "supercell", "warmstart", "cusolver", "canted"],
                     help="liz135: the benchmark workload; supercell: per-site LIZs of the 256-site supercell "
                          "with vacancies (uneven n), batched and replayed as a captured plan")
     ap.add_argument("--n-lizs", type=int, default=32, help="supercell / warmstart mode: evaluation LIZs")
@@ -613,6 +679,8 @@ def main():
         run_warmstart(args)
     elif args.workload == "cusolver":
         run_cusolver_context(args)
+    elif args.workload == "canted":
+        run_canted(args)
     else:
         run_ours(args)
 

@@ -178,7 +178,15 @@ void must_plan_free(must_plan* plan);
  *   knob 0: sites per padding quantum when must_tau00_batch groups LIZs of
  *           uneven size (1..64, default 4);
  *   knob 1: complex columns per tensor-core tile of the trailing update
- *           (128 or 256, default 128).
+ *           (128 or 256, default 128);
+ *   knob 2: trailing-update kernel for 128-column tiles: 1 (default) the
+ *           streamed kernel, whose CTAs each update a short run of tiles and
+ *           move C through shared memory with TMA loads and stores, 0 one CTA
+ *           per tile with C read and written from registers;
+ *   knob 3: tiles per CTA of the streamed kernel (1..64, default 8);
+ *   knob 4: panel look-ahead of the mixed path: 1 (default) factors panel
+ *           k+1 on a high-priority side stream while the rest of step k's
+ *           trailing update runs, 0 keeps every step on the caller's stream.
  * Process-wide; set them between calls, not while solves are being enqueued.
  */
 must_status must_tune_set(int32_t knob, int32_t value);

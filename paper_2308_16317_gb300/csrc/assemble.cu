@@ -186,6 +186,7 @@ struct AsmArgs {
   const int* g_start;
   const int* g_L2;
   const double* g_c;
+  int g_nnz;
   int e0, nEc, nE, nspin, n_species;
   const double2* E;       // [nE]
   const double2* tinv;    // [nspin][n_species][nE][lmax+1]
@@ -238,6 +239,13 @@ __global__ void scale_kernel(AsmArgs A, double* __restrict__ scale, float* __res
 // float's significand; lo: the remaining 29 bits, rounded to a float), so
 // the split costs no FP64-pipe conversions.  Values outside the normal float
 // range fall back to the conversion instructions.
+// Out-of-range values (rare): the conversion instructions.  Kept out of line
+// so that the common path of split_df carries no FP64 instructions.
+__device__ __noinline__ float2 split_df_slow(double v) {
+  const float hi = float(v);
+  return make_float2(hi, float(v - double(hi)));
+}
+
 __device__ __forceinline__ void split_df(double v, float& hi, float& lo) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
   const int e = int((b >> 52) & 0x7FF);
@@ -248,25 +256,35 @@ __device__ __forceinline__ void split_df(double v, float& hi, float& lo) {
     const float p2 = __uint_as_float(unsigned(e - 948) << 23);                // 2^(e - 1075)
     lo = __uint_as_float(__float_as_uint(m * p2) | sign);
   } else if (e < 949) {   // |v| < 2^-74: negligible next to any row of M
-    hi = float(v);
+    hi = __uint_as_float(unsigned(b >> 63) << 31);
     lo = 0.f;
   } else {
-    hi = float(v);
-    lo = float(v - double(hi));
+    const float2 r = split_df_slow(v);
+    hi = r.x;
+    lo = r.y;
   }
 }
 
-__device__ __forceinline__ void store_elem(const AsmArgs& A, int it, int row, int col, cd v) {
+// (re_hi, im_hi, re_lo, im_lo) of v.
+__device__ __forceinline__ float4 split_cd(cd v) {
+  float hr, lr, hi, li;
+  split_df(v.x, hr, lr);
+  split_df(v.y, hi, li);
+  return make_float4(hr, hi, lr, li);
+}
+
+__device__ __forceinline__ bool need_df(const AsmArgs& A) { return A.M32 || (A.M64 && A.m64_df); }
+
+// Store entry (row, col) of item it: v in FP64 and, when a FP32 copy or the
+// double-float M is kept, its split f = split_cd(v).
+__device__ __forceinline__ void store_elem(const AsmArgs& A, int it, int row, int col, cd v, float4 f) {
   const size_t off = size_t(it) * A.stride + size_t(col) * A.ld + row;
   if (A.M64 && A.M32 && !A.m64_df) A.M64[off] = make_double2(v.x, v.y);   // FP64 residual copy
-  if (A.M32 || (A.M64 && A.m64_df)) {
-    float hr, lr, hi, li;
-    split_df(v.x, hr, lr);
-    split_df(v.y, hi, li);
-    if (A.M64 && A.m64_df) reinterpret_cast<float4*>(A.M64)[off] = make_float4(hr, hi, lr, li);
+  if (need_df(A)) {
+    if (A.M64 && A.m64_df) reinterpret_cast<float4*>(A.M64)[off] = f;
     if (A.M32) {
       const float s = A.scale32[size_t(it) * A.n + row] * A.scale32[size_t(it) * A.n + col];
-      A.M32[off] = make_float2(hr * s + lr * s, hi * s + li * s);
+      A.M32[off] = make_float2(f.x * s + f.z * s, f.y * s + f.w * s);
     }
     return;
   }
@@ -280,65 +298,105 @@ __device__ __forceinline__ void store_elem(const AsmArgs& A, int it, int row, in
   }
 }
 
-// One warp per (unit, energy, LIZ of the chunk); units [0, n_pairs) are site
-// pairs p < q, [n_pairs, n_pairs + N) diagonal sites, and the next pad units
-// the identity blocks of the padding sites (their off-diagonal blocks are
-// zero-filled before the launch).
+__device__ __forceinline__ void store_elem(const AsmArgs& A, int it, int row, int col, cd v) {
+  store_elem(A, it, row, col, v, need_df(A) ? split_cd(v) : make_float4(0.f, 0.f, 0.f, 0.f));
+}
+
+// Grid (blocks, energy, LIZ of the chunk).  The first blocks of a LIZ take
+// PAIRS_PER_BLOCK site pairs p < q each: one thread per pair evaluates the
+// Hankel functions (FP64 exp/sincos/division: computed once per pair, not by
+// every lane), then each warp contracts the Gaunt table for its pairs.  The
+// remaining blocks give one warp to each diagonal site and each padding site
+// (identity block; their off-diagonal blocks are zero-filled before the
+// launch).
+constexpr int PAIRS_PER_BLOCK = 64;
+
+__host__ __device__ inline int asm_pair_blocks(int n_pairs) { return (n_pairs + PAIRS_PER_BLOCK - 1) / PAIRS_PER_BLOCK; }
+
 __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
   __shared__ cd wsh[8][MUST_MAX_NL2];
+  __shared__ cd hsh[PAIRS_PER_BLOCK][2 * MUST_MAX_LMAX + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int unit = blockIdx.x * 8 + warp;
   const int el = blockIdx.y;
   const int lz = blockIdx.z;
   const LizDev& Lz = A.L[lz];
-  if (unit >= Lz.n_pairs + Lz.N + Lz.pad) return;
   const int e = A.e0 + el;
   const cd Ec = mk(A.E[e].x, A.E[e].y);
   const int nL = A.nL, kap = A.kap, off = Lz.pad;
   auto item_of = [&](int ii) { return (lz * A.items_per_e + ii) * A.nEc + el; };
-  if (unit < Lz.n_pairs) {
-    const int2 pq = Lz.pair_pq[unit];
-    const cd k = csqrt_p(Ec);
-    const double d = Lz.pair_d[unit];
+  const int pb = asm_pair_blocks(Lz.n_pairs);
+  if (int(blockIdx.x) < pb) {
+    const int u0 = blockIdx.x * PAIRS_PER_BLOCK;
+    const int np = min(PAIRS_PER_BLOCK, Lz.n_pairs - u0);
     const int l2max = 2 * A.lmax;
-    cd h[2 * MUST_MAX_LMAX + 1];
-    hankel_up(l2max, d * k, h);
-    // w'_L'' = 4 pi i kappa h_l'' Y_L''  (so that the block entry -G = sum c w')
-    const cd f = mk(0.0, 4.0 * 3.14159265358979323846) * k;
-    for (int L2 = lane; L2 < A.nL2; L2 += 32) {
-      const double y = Lz.pair_Y[size_t(unit) * A.nL2 + L2];
-      wsh[warp][L2] = y * (f * h[l_of(L2)]);
+    // the Gaunt table in shared memory: [g_nnz] coefficients, [g_nnz] L'', [nL^2 + 1] row starts
+    extern __shared__ double gsm[];
+    double* gs_c = gsm;
+    int* gs_L2 = reinterpret_cast<int*>(gs_c + A.g_nnz);
+    int* gs_start = gs_L2 + A.g_nnz;
+    for (int i = threadIdx.x; i < A.g_nnz; i += blockDim.x) {
+      gs_c[i] = A.g_c[i];
+      gs_L2[i] = A.g_L2[i];
     }
-    __syncwarp();
-    const int p = pq.x + off, q = pq.y + off;
-    for (int ent = lane; ent < nL * nL; ent += 32) {
-      const int L = ent % nL, Lp = ent / nL;
-      cd v = mk(0.0, 0.0);
-      const int b = A.g_start[L * nL + Lp], t = A.g_start[L * nL + Lp + 1];
-      for (int i = b; i < t; ++i) {
-        const double c = A.g_c[i];
-        const cd w = wsh[warp][A.g_L2[i]];
-        v.x = fma(c, w.x, v.x);
-        v.y = fma(c, w.y, v.y);
+    for (int i = threadIdx.x; i <= nL * nL; i += blockDim.x) gs_start[i] = A.g_start[i];
+    if (int(threadIdx.x) < np) {
+      // 4 pi i kappa h_l''(kappa d), so that the block entry -G = sum c Y w
+      const cd k = csqrt_p(Ec);
+      const double d = Lz.pair_d[u0 + threadIdx.x];
+      cd h[2 * MUST_MAX_LMAX + 1];
+      hankel_up(l2max, d * k, h);
+      const cd f = mk(0.0, 4.0 * 3.14159265358979323846) * k;
+      for (int l = 0; l <= l2max; ++l) hsh[threadIdx.x][l] = f * h[l];
+    }
+    __syncthreads();
+    for (int pi = warp; pi < np; pi += 8) {
+      const int unit = u0 + pi;
+      const int2 pq = Lz.pair_pq[unit];
+      for (int L2 = lane; L2 < A.nL2; L2 += 32) {
+        const double y = Lz.pair_Y[size_t(unit) * A.nL2 + L2];
+        wsh[warp][L2] = y * hsh[pi][l_of(L2)];
       }
-      const double par = ((l_of(L) + l_of(Lp)) & 1) ? -1.0 : 1.0;
-      const cd vt = par * v;
-      for (int ii = 0; ii < A.items_per_e; ++ii) {
-        const int it = item_of(ii);
-        if (!A.canted) {
-          store_elem(A, it, p * kap + L, q * kap + Lp, v);
-          store_elem(A, it, q * kap + L, p * kap + Lp, vt);
-        } else {
-          for (int s = 0; s < 2; ++s) {
-            store_elem(A, it, p * kap + s * nL + L, q * kap + s * nL + Lp, v);
-            store_elem(A, it, p * kap + s * nL + L, q * kap + (1 - s) * nL + Lp, mk(0.0, 0.0));
-            store_elem(A, it, q * kap + s * nL + L, p * kap + s * nL + Lp, vt);
-            store_elem(A, it, q * kap + s * nL + L, p * kap + (1 - s) * nL + Lp, mk(0.0, 0.0));
+      __syncwarp();
+      const int p = pq.x + off, q = pq.y + off;
+      for (int ent = lane; ent < nL * nL; ent += 32) {
+        const int L = ent % nL, Lp = ent / nL;
+        cd v = mk(0.0, 0.0);
+        const int b = gs_start[L * nL + Lp], t = gs_start[L * nL + Lp + 1];
+        for (int i = b; i < t; ++i) {
+          const double c = gs_c[i];
+          const cd w = wsh[warp][gs_L2[i]];
+          v.x = fma(c, w.x, v.x);
+          v.y = fma(c, w.y, v.y);
+        }
+        // the transposed block by parity: G^{qp}_{LL'} = (-1)^{l+l'} G^{pq}_{LL'} (exact sign flips)
+        const bool odd = (l_of(L) + l_of(Lp)) & 1;
+        const cd vt = odd ? -v : v;
+        const float4 f = need_df(A) ? split_cd(v) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 ft = odd ? make_float4(-f.x, -f.y, -f.z, -f.w) : f;
+        const cd z0 = mk(0.0, 0.0);
+        const float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int ii = 0; ii < A.items_per_e; ++ii) {
+          const int it = item_of(ii);
+          if (!A.canted) {
+            store_elem(A, it, p * kap + L, q * kap + Lp, v, f);
+            store_elem(A, it, q * kap + L, p * kap + Lp, vt, ft);
+          } else {
+            for (int s = 0; s < 2; ++s) {
+              store_elem(A, it, p * kap + s * nL + L, q * kap + s * nL + Lp, v, f);
+              store_elem(A, it, p * kap + s * nL + L, q * kap + (1 - s) * nL + Lp, z0, f0);
+              store_elem(A, it, q * kap + s * nL + L, p * kap + s * nL + Lp, vt, ft);
+              store_elem(A, it, q * kap + s * nL + L, p * kap + (1 - s) * nL + Lp, z0, f0);
+            }
           }
         }
       }
+      __syncwarp();
     }
-  } else if (unit < Lz.n_pairs + Lz.N) {
+    return;
+  }
+  const int unit = Lz.n_pairs + (int(blockIdx.x) - pb) * 8 + warp;
+  if (unit >= Lz.n_pairs + Lz.N + Lz.pad) return;
+  if (unit < Lz.n_pairs + Lz.N) {
     const int ps = unit - Lz.n_pairs;      // site in the LIZ's permuted order
     const int p = ps + off;                // block in the chunk matrix
     const int sp = Lz.species[ps];
@@ -415,7 +473,8 @@ void launch_assemble(const AsmArgs& A, int max_units, cudaStream_t st) {
     prof_launched(PH_ASSEMBLE, 1);
   }
   dim3 grid((max_units + 7) / 8, A.nEc, A.n_lz);
-  assemble_kernel<<<grid, 256, 0, st>>>(A);
+  const size_t smem = size_t(A.g_nnz) * 12 + size_t(A.nL * A.nL + 1) * 4;
+  assemble_kernel<<<grid, 256, smem, st>>>(A);
   prof_launched(PH_ASSEMBLE, 1, n_items);
 }
 
@@ -431,9 +490,10 @@ void launch_assemble_chunk(const AsmChunk& c, cudaStream_t st) {
     d.N = z->N; d.n_pairs = z->n_pairs; d.pad = c.pad[j];
     d.species = z->d_species_perm; d.dirs = z->d_dirs_perm; d.pair_pq = z->d_pair_pq; d.pair_d = z->d_pair_d;
     d.pair_Y = z->d_pair_Y;
-    max_units = std::max(max_units, d.n_pairs + d.N + d.pad);
+    max_units = std::max(max_units, asm_pair_blocks(d.n_pairs) * 8 + d.N + d.pad);
     any_pad |= (d.pad > 0);
   }
+  A.g_nnz = z0->g_nnz;
   A.g_start = z0->d_g_start; A.g_L2 = z0->d_g_L2; A.g_c = z0->d_g_c;
   A.e0 = c.e0; A.nEc = c.nEc; A.nE = c.nE; A.nspin = c.nspin; A.n_species = c.n_species;
   A.E = c.E; A.tinv = c.tinv; A.M64 = c.M64; A.M32 = c.M32; A.ld = c.ld; A.stride = c.stride; A.scale = c.scale;

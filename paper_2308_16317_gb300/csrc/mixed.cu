@@ -798,6 +798,8 @@ struct SideStream {
 thread_local SideStream g_side;
 }  // namespace
 
+int g_lookahead = 1;   // tuning knob 4
+
 static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -878,7 +880,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   // HBM, and the main stream waits for it before the next row swaps.
   cudaStream_t ss = nullptr;
   cudaEvent_t ev_next = nullptr, ev_panel = nullptr;
-  const bool lookahead = side_stream(&ss, &ev_next, &ev_panel);
+  const bool lookahead = g_lookahead && side_stream(&ss, &ev_next, &ev_panel);
   const size_t panel_smem = size_t(leaf_width(n)) * n * sizeof(float2);
   const int bn = tc_tile_n();
   auto launch_panel = [&](int k, int w, cudaStream_t s) {

@@ -24,3 +24,7 @@ struct MixedChunk {
 
 size_t mixed_item_bytes(int n, int ld, int kap);
 must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st);
+
+// Tuning knob 4: 1 (default) factor panel k+1 on a high-priority side stream
+// while the rest of step k's trailing update runs; 0 keeps one stream.
+extern int g_lookahead;

@@ -501,6 +501,16 @@ extern "C" must_status must_tune_set(int32_t knob, int32_t value) {
     case 1:   // tensor-core tile width (complex columns)
       if (!tc_set_tile_n(value)) { must_set_error("tile width must be 128 or 256"); return MUST_EINVAL; }
       return MUST_OK;
+    case 2:   // streamed trailing-update kernel on/off
+      if (!tc_set_streamed(value)) { must_set_error("streamed-update switch must be 0 or 1"); return MUST_EINVAL; }
+      return MUST_OK;
+    case 3:   // tiles per CTA of the streamed kernel
+      if (!tc_set_run(value)) { must_set_error("tiles per CTA must be in [1, 64]"); return MUST_EINVAL; }
+      return MUST_OK;
+    case 4:   // panel look-ahead on a side stream
+      if (value != 0 && value != 1) { must_set_error("look-ahead switch must be 0 or 1"); return MUST_EINVAL; }
+      g_lookahead = value;
+      return MUST_OK;
   }
   must_set_error("unknown tuning knob %d", knob);
   return MUST_EINVAL;
@@ -510,6 +520,9 @@ extern "C" int32_t must_tune_get(int32_t knob) {
   switch (knob) {
     case 0: return g_bucket_sites;
     case 1: return tc_get_tile_n();
+    case 2: return tc_get_streamed();
+    case 3: return tc_get_run();
+    case 4: return g_lookahead;
   }
   return -1;
 }

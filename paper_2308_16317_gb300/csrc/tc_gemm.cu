@@ -13,7 +13,15 @@
 //   A'B'^T ~ A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
 // accumulated in one FP32 TMEM accumulator (the lo*lo term is dropped).
 //
-// One CTA (256 threads) computes a 128 x BN tile of C' (64 complex rows x BN
+// Two kernels share this scheme.  The streamed kernel (default) gives each
+// CTA a short run of 128 x 128 tiles and moves C itself through shared memory
+// with TMA (tile load, in-place update, tile store), double-buffering both the
+// C tile and the TMEM accumulator so that the load of tile t+1, the MMAs of
+// tile t+1 and the store of tile t overlap; the update is HBM-bound, and this
+// keeps C streaming without registers holding it.  The per-tile kernel below
+// is kept for 256-column tiles.
+//
+// Per-tile kernel: one CTA (256 threads) computes a 128 x BN tile of C' (64 complex rows x BN
 // complex columns): warp 0 lane 0 issues TMA loads into a STAGES-deep ring,
 // warp 1 lane 0 issues the MMAs (one per 32 bytes of K), and all eight warps
 // (two per TMEM lane quarter, one per column half) update C in place.  Every mbarrier wait is
@@ -85,6 +93,48 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
 }
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map), "r"(c0),
+               "r"(c1), "r"(c2), "r"(smem_u32(src))
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another role of the CTA has
+// flagged a failure (and flags one itself on time-out).
+__device__ __forceinline__ bool mbar_wait_f(uint64_t* b, uint32_t parity, volatile int* fail) {
+  if (mbar_try(b, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try(b, parity)) return true;
+    if (*fail) return false;
+    if (gtimer() - t0 > WAIT_NS) {
+      *fail = 1;
+      return false;
+    }
+  }
+}
+
+// OR of `flag` over the 256 epilogue threads (named barrier 1); every
+// epilogue thread reaches it once per tile whatever happened before.
+__device__ __forceinline__ bool epi_any(bool flag) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n barrier.cta.red.or.pred p, 1, 256, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"(flag ? 1u : 0u)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("barrier.cta.sync 1, 256;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
 // 1024 bytes apart (SBO), descriptor version 1.
@@ -259,6 +309,224 @@ __global__ void __launch_bounds__(256, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
 }
 
+// ------------------------------------------------------- streamed kernel --
+// Tiles of 128 real rows x 64 complex columns.  A CTA takes a run of up to
+// P.run consecutive row tiles of one column tile: the column block of U
+// (B_hi and B_lo for all K, 32 KB) is loaded once and stays in shared memory,
+// the A rows stream through a 3-stage ring (A_hi and A_lo of one 128-byte K
+// step per stage, so A_hi is fetched once for both products that use it), and
+// C tiles stream through 3 buffers: the epilogue's leader thread keeps two C
+// loads in flight while the tile in hand is updated and stored.
+constexpr int SBN = 64;                        // complex columns per tile
+constexpr int S_STAGES = 3;                    // A ring depth
+constexpr int S_CBUF = 3;                      // C tile buffers
+constexpr int C_TILE_BYTES = BM * SBN * 4;     // 128 floats x 64 columns
+constexpr int S_THREADS = 320;                 // producer, MMA, 8 epilogue warps
+constexpr int S_KSTEPS = 2;                    // 128-byte K steps per product (K = 2 x 64 complex)
+constexpr int SA_BYTES = BM * KB;              // one A operand K step
+constexpr int SB_BYTES = SBN * KB;             // one B operand K step
+constexpr int S_STAGE_BYTES = 2 * SA_BYTES;    // A_hi + A_lo
+constexpr int S_B_BYTES = 2 * S_KSTEPS * SB_BYTES;
+constexpr size_t S_SMEM = size_t(S_STAGES) * S_STAGE_BYTES + S_B_BYTES + size_t(S_CBUF) * C_TILE_BYTES + 1024;
+
+struct TcsParams {
+  int base;      // first trailing row/column (k0 + nbe)
+  int abase;     // base rounded down to even: row origin of the tiles (16-byte TMA rule)
+  int rt, ct;    // row tiles, column tiles of this launch
+  int col_tile0; // first column tile
+  int run;       // row tiles per CTA
+  int rruns;     // runs per column tile
+  int* err;
+  int tf32;
+};
+
+// CTA b: item, column tile and first row tile of its run; runs of one item
+// are numbered consecutively so the CTAs resident at a time share an item
+// and its packed operands stay in L2.
+__device__ __forceinline__ void run_coords(const TcsParams& P, int b, int& rt0, int& ntile, int& col0, int& item) {
+  const int rr = b % P.rruns;
+  const int c = (b / P.rruns) % P.ct;
+  item = b / (P.rruns * P.ct);
+  rt0 = rr * P.run;
+  ntile = min(P.run, P.rt - rt0);
+  col0 = (c + P.col_tile0) * SBN;
+}
+
+__global__ void __launch_bounds__(S_THREADS, 1)
+    tc_update_streamed(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+                       const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
+                       const __grid_constant__ CUtensorMap tC, TcsParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* bres = smem + S_STAGES * S_STAGE_BYTES;   // [hi k0, hi k1, lo k0, lo k1]
+  uint8_t* cbuf = bres + S_B_BYTES;
+  __shared__ __align__(8) uint64_t full[S_STAGES];
+  __shared__ __align__(8) uint64_t empty[S_STAGES];
+  __shared__ __align__(8) uint64_t bfull;        // resident B landed
+  __shared__ __align__(8) uint64_t cfull[S_CBUF]; // C tile landed
+  __shared__ __align__(8) uint64_t afull[2];     // accumulator ready
+  __shared__ __align__(8) uint64_t aempty[2];    // accumulator read out
+  __shared__ __align__(8) uint64_t mdone;        // every MMA of this CTA retired
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail_raw;
+  volatile int* s_fail = &s_fail_raw;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int rt0, ntile, col0, item;
+  run_coords(P, blockIdx.x, rt0, ntile, col0, item);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < S_CBUF; ++b) mbar_init(&cfull[b], 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&afull[b], 1);
+      mbar_init(&aempty[b], 8);
+    }
+    mbar_init(&bfull, 1);
+    mbar_init(&mdone, 1);
+    s_fail_raw = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(2 * SBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const int kstep_elems = P.tf32 ? KB / 4 : KB / 2;
+
+  if (warp == 0 && lane == 0) {
+    // producer: the resident B block once, then two A stages per tile
+    mbar_expect_tx(&bfull, S_B_BYTES);
+    for (int kb = 0; kb < S_KSTEPS; ++kb) {
+      tma_load_3d(bres + kb * SB_BYTES, &tB_hi, kb * kstep_elems, P.base + col0, item, &bfull);
+      tma_load_3d(bres + (S_KSTEPS + kb) * SB_BYTES, &tB_lo, kb * kstep_elems, P.base + col0, item, &bfull);
+    }
+    int gs = 0;
+    for (int lt = 0; lt < ntile; ++lt) {
+      const int row0 = (rt0 + lt) * BM;
+      bool ok = true;
+      for (int kb = 0; kb < S_KSTEPS; ++kb, ++gs) {
+        const int s = gs % S_STAGES;
+        if (gs >= S_STAGES && !mbar_wait_f(&empty[s], ((gs / S_STAGES) - 1) & 1, s_fail)) { ok = false; break; }
+        uint8_t* sa = smem + s * S_STAGE_BYTES;
+        mbar_expect_tx(&full[s], S_STAGE_BYTES);
+        tma_load_3d(sa, &tA_hi, kb * kstep_elems, 2 * P.abase + row0, item, &full[s]);
+        tma_load_3d(sa + SA_BYTES, &tA_lo, kb * kstep_elems, 2 * P.abase + row0, item, &full[s]);
+      }
+      if (!ok) break;
+    }
+    if (*s_fail) {
+      // drain: the last load armed on each barrier must land before the CTA exits
+      volatile int dummy = 0;
+      mbar_wait_f(&bfull, 0, &dummy);
+      for (int s = 0; s < S_STAGES && s < gs; ++s) {
+        const int cnt = (gs - s + S_STAGES - 1) / S_STAGES;   // loads armed on full[s]
+        mbar_wait_f(&full[s], (cnt - 1) & 1, &dummy);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: per K step, A_hi B_hi + A_hi B_lo + A_lo B_hi into accumulator lt & 1
+    const uint32_t fmt = P.tf32 ? 2u : 1u;
+    const uint32_t idesc =
+        (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(SBN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+    bool ok = mbar_wait_f(&bfull, 0, s_fail);
+    const uint32_t bh = smem_u32(bres), bl = bh + S_KSTEPS * SB_BYTES;
+    int gs = 0;
+    for (int lt = 0; lt < ntile && ok; ++lt) {
+      const int ab = lt & 1;
+      if (lt >= 2 && !mbar_wait_f(&aempty[ab], ((lt >> 1) - 1) & 1, s_fail)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc = tmem + uint32_t(ab * SBN);
+      for (int kb = 0; kb < S_KSTEPS; ++kb, ++gs) {
+        const int s = gs % S_STAGES;
+        if (!mbar_wait_f(&full[s], (gs / S_STAGES) & 1, s_fail)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = smem_u32(smem + s * S_STAGE_BYTES), al = ah + SA_BYTES;
+        const uint32_t bhk = bh + kb * SB_BYTES, blk = bl + kb * SB_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < KB / 32; ++kk) {
+          mma_issue(acc, sdesc(ah + 32 * kk), sdesc(bhk + 32 * kk), idesc, (kb > 0 || kk > 0) ? 1u : 0u, P.tf32);
+          mma_issue(acc, sdesc(ah + 32 * kk), sdesc(blk + 32 * kk), idesc, 1u, P.tf32);
+          mma_issue(acc, sdesc(al + 32 * kk), sdesc(bhk + 32 * kk), idesc, 1u, P.tf32);
+        }
+        mma_commit(&empty[s]);
+      }
+      if (ok) mma_commit(&afull[ab]);
+    }
+    // TMEM is freed only after every MMA issued here has retired
+    mma_commit(&mdone);
+    volatile int dummy = 0;
+    mbar_wait_f(&mdone, 0, &dummy);
+  } else if (warp >= 2) {
+    // epilogue: warp w reads TMEM lane quarter w % 4 and column half (w - 2) / 4;
+    // thread = one real row of the tile; C tile in shared memory [column][128 floats]
+    const int ew = warp - 2, quarter = warp & 3, half = ew >> 2;
+    const int x = quarter * 32 + lane;
+    const bool leader = (ew == 0 && lane == 0);
+    int c_issued = 0;
+    if (leader) {
+      for (; c_issued < S_CBUF && c_issued < ntile; ++c_issued) {
+        const int cb = c_issued;
+        mbar_expect_tx(&cfull[cb], C_TILE_BYTES);
+        tma_load_3d(cbuf + cb * C_TILE_BYTES, &tC, 2 * P.abase + (rt0 + c_issued) * BM, P.base + col0, item,
+                    &cfull[cb]);
+      }
+    }
+    for (int lt = 0; lt < ntile; ++lt) {
+      const int cb = lt % S_CBUF, ab = lt & 1;
+      bool bad = !mbar_wait_f(&cfull[cb], (lt / S_CBUF) & 1, s_fail);
+      bad = bad || !mbar_wait_f(&afull[ab], (lt >> 1) & 1, s_fail);
+      if (epi_any(bad)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row0 = (rt0 + lt) * BM;
+      float* cs = reinterpret_cast<float*>(cbuf + cb * C_TILE_BYTES);
+      const bool live = (2 * P.abase + row0 + x) >= 2 * P.base;   // rows above base stay as they are
+      uint32_t v[32];
+      tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(ab * SBN + half * 32), v);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&aempty[ab]);
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float* e = cs + (half * 32 + j) * BM + x;
+          *e = *e - __uint_as_float(v[j]);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      epi_sync();
+      if (leader) {
+        tma_store_3d(&tC, cs, 2 * P.abase + row0, P.base + col0, item);   // returns once the buffer is read
+        if (c_issued < ntile) {
+          mbar_expect_tx(&cfull[cb], C_TILE_BYTES);
+          tma_load_3d(cs, &tC, 2 * P.abase + (rt0 + c_issued) * BM, P.base + col0, item, &cfull[cb]);
+          ++c_issued;
+        }
+      }
+    }
+    if (leader && *s_fail) {
+      // drain the C loads still in flight
+      volatile int dummy = 0;
+      for (int cb = 0; cb < S_CBUF && cb < c_issued; ++cb) {
+        const int cnt = (c_issued - cb + S_CBUF - 1) / S_CBUF;
+        mbar_wait_f(&cfull[cb], (cnt - 1) & 1, &dummy);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && *s_fail) atomicExch(P.err, 1);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * SBN));
+}
+
 // ---------------------------------------------------------------- packing --
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16_raw& hi, __nv_bfloat16_raw& lo) {
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -361,8 +629,21 @@ bool make_map(CUtensorMap* m, void* base, bool tf32, int Kp, int rows, int items
   return r == CUDA_SUCCESS;
 }
 
+bool make_c_map(CUtensorMap* m, float2* C, int ld, size_t stride, int n, int items) {
+  cuuint64_t dims[3] = {cuuint64_t(2) * n, cuuint64_t(n), cuuint64_t(items)};
+  cuuint64_t strides[2] = {cuuint64_t(ld) * 8, cuuint64_t(stride) * 8};
+  cuuint32_t box[3] = {cuuint32_t(BM), cuuint32_t(SBN), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, C, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 constexpr int TC_STAGES = 3;
 int g_tile_n = 128;   // 128 or 256 complex columns per tile (autotuned)
+int g_streamed = 1;   // 1: streamed kernel (BF16 splits); 0: per-tile kernel
+int g_run = 8;        // row tiles per CTA of the streamed kernel
 
 template <int BN>
 void launch_tc(const CUtensorMap& mah, const CUtensorMap& mal, const CUtensorMap& mbh, const CUtensorMap& mbl,
@@ -375,6 +656,18 @@ void launch_tc(const CUtensorMap& mah, const CUtensorMap& mal, const CUtensorMap
   }
   dim3 grid((2 * m + BM - 1) / BM, col_tiles, items);
   tc_update_kernel<BN, TC_STAGES><<<grid, 256, smem, st>>>(mah, mal, mbh, mbl, P);
+}
+
+void launch_tc_streamed(const CUtensorMap& mah, const CUtensorMap& mal, const CUtensorMap& mbh,
+                        const CUtensorMap& mbl, const CUtensorMap& mc, const TcsParams& P, int items,
+                        cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_update_streamed, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S_SMEM));
+    attr = true;
+  }
+  const int grid = P.rruns * P.ct * items;
+  tc_update_streamed<<<grid, S_THREADS, S_SMEM, st>>>(mah, mal, mbh, mbl, mc, P);
 }
 
 int kp_of(bool tf32) {
@@ -394,6 +687,20 @@ bool tc_set_tile_n(int bn) {
 }
 
 int tc_get_tile_n() { return g_tile_n; }
+
+bool tc_set_streamed(int on) {
+  if (on != 0 && on != 1) return false;
+  g_streamed = on;
+  return true;
+}
+int tc_get_streamed() { return g_streamed; }
+
+bool tc_set_run(int run) {
+  if (run < 1 || run > 64) return false;
+  g_run = run;
+  return true;
+}
+int tc_get_run() { return g_run; }
 
 size_t tc_pack_bytes_per_item(int n) {
   const int rows_pad = 2 * ((n + 127) / 128) * 128;
@@ -463,7 +770,10 @@ bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, i
   }
   const PackGeom g = pack_geom(precision, n, k0, nbe, items, packs);
   if (g.m <= 0) return true;
-  const int bn = g_tile_n;
+  // The streamed kernel serves the BF16 splits (K = 2 x 128-byte steps per
+  // product); TF32 splits and 256-column tiles use the per-tile kernel.
+  const bool streamed = g_streamed && !g.tf32;
+  const int bn = streamed ? SBN : g_tile_n;
   const int tiles = (g.m + bn - 1) / bn;
   const int t0 = col_lo / bn;
   const int t1 = (col_hi < 0) ? tiles : std::min(tiles, (col_hi + bn - 1) / bn);
@@ -475,6 +785,35 @@ bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, i
       !make_map(&mbl, g.pb_lo, g.tf32, g.Kp, g.item_rows, items, bn)) {
     must_set_error("tensor map encoding failed");
     return false;
+  }
+  if (streamed) {
+    if (g.Kp * g.es / KB != S_KSTEPS) {
+      must_set_error("streamed update: unexpected K steps");
+      return false;
+    }
+    // rows of the tiles start at base rounded down to even, so that the
+    // first coordinate of every C tile (2 * abase + row0 floats) is a
+    // multiple of 16 bytes; a row above base is written back unchanged
+    const int abase = g.base & ~1;
+    CUtensorMap mc;
+    if (!make_c_map(&mc, A, ld, stride, n, items)) {
+      must_set_error("tensor map encoding failed (C)");
+      return false;
+    }
+    TcsParams S;
+    S.base = g.base;
+    S.abase = abase;
+    S.rt = (2 * (n - abase) + BM - 1) / BM;
+    S.ct = t1 - t0;
+    S.col_tile0 = t0;
+    S.run = std::min(g_run, S.rt);
+    S.rruns = (S.rt + S.run - 1) / S.run;
+    S.err = err;
+    S.tf32 = 0;
+    ProfScope ps(PH_UPDATE, st);
+    launch_tc_streamed(mah, mal, mbh, mbl, mc, S, items, st);
+    prof_launched(PH_UPDATE, 1, items);
+    return true;
   }
   TcParams P;
   P.C = A;

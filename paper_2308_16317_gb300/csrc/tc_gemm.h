@@ -21,3 +21,11 @@ bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, 
 // Tile width (complex columns) of the tensor-core update: 128 or 256.
 bool tc_set_tile_n(int bn);
 int tc_get_tile_n();
+
+// Trailing-update kernel for 128-column tiles: 1 = streamed (C staged through
+// shared memory by TMA, double-buffered accumulators), 0 = one CTA per tile.
+bool tc_set_streamed(int on);
+int tc_get_streamed();
+// Tiles per CTA of the streamed kernel (1..64).
+bool tc_set_run(int run);
+int tc_get_run();

@@ -89,3 +89,56 @@ def test_mixed_full_size_sampled(B, orc, residual):
     err = rel_fro(got, ref)
     print("per-energy rel err (bf16x3, residual %d):" % residual, dict(zip(map(str, items), err)))
     assert err.max() <= TOLMIX, err
+
+
+def test_mixed_canted_full_size_sampled(B, orc):
+    """Spin-canted 135-site LIZ (order 4320, kap = 32), unclamped contour
+    (Im E down to 0.00215): all 32 energies on the mixed path; the two
+    end-point energies, closest to the real axis, checked against the oracle."""
+    w = wl.canted135()
+    tau, st = _gpu_tau(B, w, 1, residual=1)
+    assert (st == 0).all() and np.isfinite(tau).all()
+    items = [0, 31]
+    ref, _ = oracle_tau(orc, w, items=items, nthreads=min(len(items), ncpu()))
+    got = np.array([tau[0, e] for e in items])
+    err = rel_fro(got, ref)
+    print("canted per-energy rel err:", dict(zip(items, err)))
+    assert err.max() <= TOLMIX, err
+
+
+@pytest.mark.parametrize("case", ["odd_base", "fcc135"])
+def test_streamed_update_matches_per_tile_kernel(B, orc, case):
+    """The streamed trailing-update kernel issues the same MMAs for every run
+    length, so tau_00 must agree bit for bit across run lengths; against the
+    one-CTA-per-tile kernel (which sums the three split products in another
+    order) it agrees to the refinement tolerance.  The 42-site l_max = 2 LIZ
+    has r = n - kap = 369, so the last panel step starts its trailing block at
+    an odd row (tiles then start one row above it)."""
+    if case == "odd_base":
+        pos, _ = wl.fcc_cluster(3)
+        pos = pos[:42]
+        rng = np.random.default_rng(11)
+        w = wl.Workload("odd_base", 2, [wl.Liz(pos, rng.integers(0, 2, 42).astype(np.int32))],
+                        wl.semicircle_contour(4), wl.spin_depths(2), wl.R_MT)
+    else:
+        w = wl.liz135(n_e=4)
+    old = (B.must_tune_get(2), B.must_tune_get(3))
+    taus = []
+    try:
+        for streamed, run in ((1, 8), (1, 1), (1, 64), (1, 3), (0, 8)):
+            B.must_tune_set(2, streamed)
+            B.must_tune_set(3, run)
+            tau, st = _gpu_tau(B, w, 1, residual=1)
+            assert (st == 0).all()
+            taus.append(tau)
+    finally:
+        B.must_tune_set(2, old[0])
+        B.must_tune_set(3, old[1])
+    for t in taus[1:4]:
+        assert np.array_equal(t, taus[0])
+    k = w.kappa()
+    assert rel_fro(taus[4].reshape(-1, k, k), taus[0].reshape(-1, k, k)).max() <= TOLMIX
+    if case == "odd_base":
+        ref, _ = oracle_tau(orc, w, nthreads=ncpu())
+        for t in (taus[0], taus[4]):
+            assert rel_fro(t.reshape(-1, k, k), ref).max() <= TOLMIX
