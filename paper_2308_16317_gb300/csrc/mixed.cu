@@ -62,6 +62,10 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
   __shared__ int s_p;
   __shared__ cf Ub[LEAF][PANEL_W];     // leaf rows of the remaining panel columns
   __shared__ cf Ll[LEAF][LEAF];        // leaf's unit-lower top block
+  __shared__ int s_nr;                 // rows touched by the leaf's interchanges
+  __shared__ int s_rows[2 * LEAF];     // ... their indices
+  __shared__ int s_src[2 * LEAF];      // ... and the row whose old value each receives
+  __shared__ cf s_tmp[PANEL_W * 2 * LEAF];
   const int item = blockIdx.x;
   cf* A = reinterpret_cast<cf*>(A0 + size_t(item) * stride);
   int* piv = piv0 + size_t(item) * r;
@@ -90,13 +94,21 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
       }
       if (lane == 0) { sv[warp] = best; si[warp] = bi; }
       __syncthreads();
-      if (tid == 0) {
-        float b = sv[0];
-        int p = si[0];
-        for (int w = 1; w < PPT / 32; ++w) argmax_merge(b, p, sv[w], si[w]);
-        if (!(b > 0.0f)) status[item] = ST_SINGULAR;
-        piv[c0 + j] = c0 + p;
-        s_p = p;
+      if (warp == 0) {
+        // (max |z|^2, lowest index) over the warps' candidates: the order of
+        // the merges does not change the winner
+        float b = (lane < PPT / 32) ? sv[lane] : -1.0f;
+        int p = (lane < PPT / 32) ? si[lane] : j;
+        for (int o = 16; o > 0; o >>= 1) {
+          const float v2 = __shfl_down_sync(0xffffffffu, b, o);
+          const int i2 = __shfl_down_sync(0xffffffffu, p, o);
+          argmax_merge(b, p, v2, i2);
+        }
+        if (lane == 0) {
+          if (!(b > 0.0f)) status[item] = ST_SINGULAR;
+          piv[c0 + j] = c0 + p;
+          s_p = p;
+        }
       }
       __syncthreads();
       const int p = s_p;
@@ -119,17 +131,45 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
     }
     for (int q = 0; q < lw; ++q)
       for (int ii = tid; ii < mrows; ii += PPT) A[size_t(c0 + q) * ld + c0 + ii] = Lf[q * mrows + ii];
-    // (a') the leaf's interchanges on the other panel columns
-    for (int cc = k0 + tid; cc < pend; cc += PPT) {
-      if (cc >= c0 && cc < le) continue;
-      cf* colc = A + size_t(cc) * ld;
+    // (a') the leaf's interchanges on the other panel columns.  The sequence
+    // of swaps permutes at most 2 lw rows; it is composed once and applied as
+    // a gather, so every column takes one round trip instead of lw.
+    if (tid == 0) {
+      int nr = 0;
+      int at[2 * LEAF];                  // at[k]: index into s_rows of the old row now at s_rows[k]
+      auto find_or_add = [&](int row) {
+        for (int k = 0; k < nr; ++k)
+          if (s_rows[k] == row) return k;
+        s_rows[nr] = row;
+        at[nr] = nr;
+        return nr++;
+      };
       for (int j = 0; j < lw; ++j) {
         const int c = c0 + j, p = piv[c];
-        if (p != c) {
-          const cf t = colc[c];
-          colc[c] = colc[p];
-          colc[p] = t;
-        }
+        if (p == c) continue;
+        const int kc = find_or_add(c), kp = find_or_add(p);
+        const int t = at[kc];
+        at[kc] = at[kp];
+        at[kp] = t;
+      }
+      for (int k = 0; k < nr; ++k) s_src[k] = s_rows[at[k]];
+      s_nr = nr;
+    }
+    __syncthreads();
+    const int nr = s_nr;
+    const int nother = nbe - lw;         // panel columns outside the leaf
+    if (nr > 0 && nother > 0) {
+      const int tot = nother * nr;
+      for (int t = tid; t < tot; t += PPT) {
+        const int oc = t / nr, k = t % nr;
+        const int cc = k0 + (oc < lb ? oc : oc + lw);
+        s_tmp[t] = A[size_t(cc) * ld + s_src[k]];
+      }
+      __syncthreads();
+      for (int t = tid; t < tot; t += PPT) {
+        const int oc = t / nr, k = t % nr;
+        const int cc = k0 + (oc < lb ? oc : oc + lw);
+        A[size_t(cc) * ld + s_rows[k]] = s_tmp[t];
       }
     }
     __syncthreads();
@@ -161,26 +201,42 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
         }
     }
     __syncthreads();
-    // (c) rows below the leaf: A[i, rest] -= L[i, leaf] U[leaf, rest]
-    for (int i = le + tid; i < n; i += PPT) {
-      cf l[LEAF];
+    // (c) rows below the leaf: A[i, rest] -= L[i, leaf] U[leaf, rest], two
+    // rows per pass so that twice the loads are in flight
+    for (int i0 = le + tid; i0 < n; i0 += 2 * PPT) {
+      const int i1 = i0 + PPT;
+      const bool has1 = i1 < n;
+      cf l0[LEAF], l1[LEAF];
 #pragma unroll
       for (int jj = 0; jj < LEAF; ++jj)
-        if (jj < lw) l[jj] = A[size_t(c0 + jj) * ld + i];
+        if (jj < lw) {
+          l0[jj] = A[size_t(c0 + jj) * ld + i0];
+          l1[jj] = has1 ? A[size_t(c0 + jj) * ld + i1] : mkf(0.f, 0.f);
+        }
       for (int q0 = 0; q0 < rest; q0 += 8) {
-        cf v[8];
+        cf v0[8], v1[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-          if (q0 + q < rest) v[q] = A[size_t(le + q0 + q) * ld + i];
+          if (q0 + q < rest) {
+            v0[q] = A[size_t(le + q0 + q) * ld + i0];
+            v1[q] = has1 ? A[size_t(le + q0 + q) * ld + i1] : mkf(0.f, 0.f);
+          }
 #pragma unroll
         for (int jj = 0; jj < LEAF; ++jj)
           if (jj < lw)
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-              if (q0 + q < rest) cfmsf(v[q], l[jj], Ub[jj][q0 + q]);
+              if (q0 + q < rest) {
+                const cf u = Ub[jj][q0 + q];
+                cfmsf(v0[q], l0[jj], u);
+                cfmsf(v1[q], l1[jj], u);
+              }
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-          if (q0 + q < rest) A[size_t(le + q0 + q) * ld + i] = v[q];
+          if (q0 + q < rest) {
+            A[size_t(le + q0 + q) * ld + i0] = v0[q];
+            if (has1) A[size_t(le + q0 + q) * ld + i1] = v1[q];
+          }
       }
     }
     __syncthreads();
@@ -206,6 +262,11 @@ __global__ void laswp32_kernel(float2* __restrict__ A0, size_t stride, int ld, i
 }
 
 // U12 = L11^{-1} A12, nbe <= 64: one warp per column, lane i holds x_i, x_{i+32}.
+// U12 = L11^{-1} A12 for the panel's nbe <= 64 rows: each block loads the unit
+// lower L11 once into shared memory and solves TRSM_COLS columns, one warp per
+// column at a time (the row index runs over the lanes).
+constexpr int TRSM_COLS = 64;
+
 __global__ void __launch_bounds__(256) trsm32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int k0,
                                                      int nbe) {
   __shared__ cf L[64][65];
@@ -217,19 +278,20 @@ __global__ void __launch_bounds__(256) trsm32_kernel(float2* __restrict__ A0, si
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int col = k0 + nbe + blockIdx.x * 8 + warp;
-  if (col >= n) return;
-  cf* x = A + size_t(col) * ld + k0;
-  cf v0 = (lane < nbe) ? x[lane] : mkf(0.f, 0.f);
-  cf v1 = (lane + 32 < nbe) ? x[lane + 32] : mkf(0.f, 0.f);
-  for (int j = 0; j < nbe - 1; ++j) {
-    const cf src = (j < 32) ? v0 : v1;
-    const cf xj = mkf(__shfl_sync(0xffffffffu, src.x, j & 31), __shfl_sync(0xffffffffu, src.y, j & 31));
-    if (lane > j && lane < nbe) cfmsf(v0, L[lane][j], xj);
-    if (lane + 32 > j && lane + 32 < nbe) cfmsf(v1, L[lane + 32][j], xj);
+  const int c_end = min(n, k0 + nbe + (int(blockIdx.x) + 1) * TRSM_COLS);
+  for (int col = k0 + nbe + blockIdx.x * TRSM_COLS + warp; col < c_end; col += 8) {
+    cf* x = A + size_t(col) * ld + k0;
+    cf v0 = (lane < nbe) ? x[lane] : mkf(0.f, 0.f);
+    cf v1 = (lane + 32 < nbe) ? x[lane + 32] : mkf(0.f, 0.f);
+    for (int j = 0; j < nbe - 1; ++j) {
+      const cf src = (j < 32) ? v0 : v1;
+      const cf xj = mkf(__shfl_sync(0xffffffffu, src.x, j & 31), __shfl_sync(0xffffffffu, src.y, j & 31));
+      if (lane > j && lane < nbe) cfmsf(v0, L[lane][j], xj);
+      if (lane + 32 > j && lane + 32 < nbe) cfmsf(v1, L[lane + 32][j], xj);
+    }
+    if (lane < nbe) x[lane] = v0;
+    if (lane + 32 < nbe) x[lane + 32] = v1;
   }
-  if (lane < nbe) x[lane] = v0;
-  if (lane + 32 < nbe) x[lane + 32] = v1;
 }
 
 // ------------------------------------------------ permutation, Schur block --
@@ -905,7 +967,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     if (rem > 0) {
       {
         ProfScope ps(PH_TRSM, st);
-        trsm32_kernel<<<dim3((rem + 7) / 8, items), 256, 0, st>>>(M32, stride, ld, n, k0, nbe);
+        trsm32_kernel<<<dim3((rem + TRSM_COLS - 1) / TRSM_COLS, items), 256, 0, st>>>(M32, stride, ld, n, k0, nbe);
         prof_launched(PH_TRSM, 1, items);
       }
       if (!tc_pack(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, st)) return MUST_ECUDA;

@@ -643,7 +643,7 @@ bool make_c_map(CUtensorMap* m, float2* C, int ld, size_t stride, int n, int ite
 constexpr int TC_STAGES = 3;
 int g_tile_n = 128;   // 128 or 256 complex columns per tile (autotuned)
 int g_streamed = 1;   // 1: streamed kernel (BF16 splits); 0: per-tile kernel
-int g_run = 8;        // row tiles per CTA of the streamed kernel
+int g_run = 16;       // row tiles per CTA of the streamed kernel
 
 template <int BN>
 void launch_tc(const CUtensorMap& mah, const CUtensorMap& mal, const CUtensorMap& mbh, const CUtensorMap& mbl,
