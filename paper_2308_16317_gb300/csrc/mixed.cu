@@ -559,8 +559,10 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
     w[t] = v;
   }
   __syncthreads();
-  // forward: unit lower L, columns 0..r-1, rows 0..n-1
-  for (int jb = 0; jb < r; jb += 32) {
+  // forward: unit lower L, columns 0..r-1, rows 0..n-1.  On the first solve
+  // w = P D E0 is zero in rows 0..r-1 (pivots stay among those rows), so the
+  // sweep would only subtract zeros: it is skipped.
+  for (int jb = 0; jb < (first ? 0 : r); jb += 32) {
     const int bs = min(32, r - jb), je = jb + bs;
     for (int t = tid; t < 32 * 32; t += T) {
       const int ii = t & 31, jj = t >> 5;
