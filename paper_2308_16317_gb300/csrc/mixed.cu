@@ -457,24 +457,32 @@ __global__ void split_x_kernel(const double2* __restrict__ X, float4* __restrict
   Xd[t] = make_float4(xr, xi, float(x.x - double(xr)), float(x.y - double(xi)));
 }
 
+// Grid (row blocks, items, K splits).  With one split the kernel writes
+// R = E0 - M X; with several, split z sums its share of the 64-column blocks
+// and writes the double-float partial (re_hi, re_lo, im_hi, im_lo) to P, which
+// residual_df_reduce_kernel adds up in split order.  Splitting K keeps the
+// last wave full when only a few items are still being refined.
 __global__ void __launch_bounds__(1024) residual_df_kernel(const float4* __restrict__ M0, size_t stride, int ld, int n,
                                                           int kap, const float4* __restrict__ Xd0,
-                                                          double2* __restrict__ R0, const int* __restrict__ conv,
+                                                          double2* __restrict__ R0, float4* __restrict__ P0,
+                                                          const int* __restrict__ conv,
                                                           unsigned long long* __restrict__ work) {
   extern __shared__ float4 Xd[];   // [64][kap]: (re_hi, im_hi, re_lo, im_lo)
   const int item = blockIdx.y;
   if (conv[item]) return;
-  if (work && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(work, 1ull);
+  if (work && blockIdx.x == 0 && blockIdx.z == 0 && threadIdx.x == 0) atomicAdd(work, 1ull);
   const float4* M = M0 + size_t(item) * stride;
   const float4* X = Xd0 + size_t(item) * n * kap;
   const int tid = threadIdx.x;
   const int row = blockIdx.x * 64 + (tid & 63);
   const int c0 = (tid >> 6) * 4;
   const int rowc = min(row, n - 1);      // clamped row for loads (results of row >= n are dropped)
+  const int nkb = (n + 63) / 64, ks = gridDim.z, z = blockIdx.z;
+  const int kb0 = int((long long)nkb * z / ks), kb1 = int((long long)nkb * (z + 1) / ks);
   float rh[4], rl[4], ih[4], il[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
-  for (int k0 = 0; k0 < n; k0 += 64) {
+  for (int k0 = kb0 * 64; k0 < min(n, kb1 * 64); k0 += 64) {
     const int kn = min(64, n - k0);
     __syncthreads();
     for (int t = tid; t < kn * kap; t += blockDim.x) {
@@ -500,6 +508,13 @@ __global__ void __launch_bounds__(1024) residual_df_kernel(const float4* __restr
     }
   }
   if (row < n) {
+    if (ks > 1) {
+      float4* P = P0 + (size_t(z) * gridDim.y + item) * size_t(n) * kap;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c0 + q < kap) P[size_t(c0 + q) * n + row] = make_float4(rh[q], rl[q], ih[q], il[q]);
+      return;
+    }
     double2* R = R0 + size_t(item) * n * kap;
     const int r = n - kap;
 #pragma unroll
@@ -510,6 +525,33 @@ __global__ void __launch_bounds__(1024) residual_df_kernel(const float4* __restr
         R[size_t(c) * n + row] = make_double2(e - (double(rh[q]) + double(rl[q])), -(double(ih[q]) + double(il[q])));
       }
   }
+}
+
+// (H, L) += (h, l): TwoSum on the high words, low words added.
+__device__ __forceinline__ void df_acc(float& H, float& L, float h, float l) {
+  const float s = H + h;
+  const float bb = s - H;
+  L += ((H - (s - bb)) + (h - bb)) + l;
+  H = s;
+}
+
+__global__ void residual_df_reduce_kernel(const float4* __restrict__ P0, int ks, int items, int n, int kap,
+                                          double2* __restrict__ R0, const int* __restrict__ conv) {
+  const int item = blockIdx.y;
+  if (conv[item]) return;
+  const size_t per = size_t(n) * kap;
+  const size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= per) return;
+  const float4 p = P0[size_t(item) * per + t];
+  float Hr = p.x, Lr = p.y, Hi = p.z, Li = p.w;
+  for (int z = 1; z < ks; ++z) {
+    const float4 q = P0[(size_t(z) * items + item) * per + t];
+    df_acc(Hr, Lr, q.x, q.y);
+    df_acc(Hi, Li, q.z, q.w);
+  }
+  const int c = int(t / n), row = int(t % n);
+  const double e = (row == n - kap + c) ? 1.0 : 0.0;
+  R0[size_t(item) * per + t] = make_double2(e - (double(Hr) + double(Lr)), -(double(Hi) + double(Li)));
 }
 
 // --------------------------------------------- low-precision correction ----
@@ -887,12 +929,15 @@ static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
 }
 
 // ---------------------------------------------------------------- driver --
+constexpr int RES_SPLIT = 4;   // K splits of the double-float residual
+
 size_t mixed_item_bytes(int n, int ld, int kap) {
   return a256(size_t(ld) * n * 8)          // M32
          + a256(size_t(n) * 8)             // scale
          + a256(size_t(n) * 4)             // scale (FP32)
          + a256(size_t(n) * 4)             // perm
          + 3 * a256(size_t(n) * kap * 16)  // X, R, X as double-float pairs
+         + RES_SPLIT * a256(size_t(n) * kap * 16)   // split-K residual partials
          + a256(size_t(kap) * kap * 16)    // Sinv
          + 1280                            // norms, previous norms, conv, error word, seed flags
          + tc_pack_bytes_per_item(n);      // tensor-core operand packs
@@ -909,6 +954,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   double2* X = reinterpret_cast<double2*>(take(size_t(items) * n * kap * 16));
   double2* R = reinterpret_cast<double2*>(take(size_t(items) * n * kap * 16));
   float4* Xdf = reinterpret_cast<float4*>(take(size_t(items) * n * kap * 16));
+  float4* Rpart = reinterpret_cast<float4*>(take(size_t(RES_SPLIT) * items * n * kap * 16));
   double2* Sinv = reinterpret_cast<double2*>(take(size_t(items) * kap * kap * 16));
   double* norms = reinterpret_cast<double*>(take(size_t(items) * 16));
   double* prevn = reinterpret_cast<double*>(take(size_t(items) * 8));
@@ -1025,6 +1071,16 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   }
   const int iters = std::max(c.opts.max_iter, 0);
   const bool seeded = c.seed && c.seed_mask;
+  // double-float residual with RES_SPLIT K splits and the in-order reduction
+  auto launch_residual_df = [&](const int* mask, unsigned long long* work, int phase) {
+    const dim3 g(gres.x, items, RES_SPLIT);
+    residual_df_kernel<<<g, tres, size_t(64) * kap * 16, st>>>(reinterpret_cast<const float4*>(c.M64), stride, ld,
+                                                               n, kap, Xdf, R, Rpart, mask, work);
+    const size_t per = size_t(n) * kap;
+    residual_df_reduce_kernel<<<dim3(unsigned((per + 255) / 256), items), 256, 0, st>>>(Rpart, RES_SPLIT, items, n,
+                                                                                     kap, R, mask);
+    prof_launched(phase, 2);
+  };
   if (seeded) {
     // X = X^ from the predicted tau_00, R = E0 - M X^ for seeded items, gate
     ProfScope ps(PH_OTHER, st);
@@ -1033,9 +1089,8 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     if (c.opts.residual == 1) {
       const size_t cnt = size_t(items) * n * kap;
       split_x_kernel<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(X, Xdf, cnt, skip, size_t(n) * kap);
-      residual_df_kernel<<<gres, tres, size_t(64) * kap * 16, st>>>(reinterpret_cast<const float4*>(c.M64), stride,
-                                                                      ld, n, kap, Xdf, R, skip, nullptr);
-      prof_launched(PH_OTHER, 2);
+      launch_residual_df(skip, nullptr, PH_OTHER);
+      prof_launched(PH_OTHER, 1);
     } else {
       residual64_kernel<<<gres, tres, smem_res, st>>>(c.M64, stride, ld, n, kap, X, R, skip, nullptr);
       prof_launched(PH_OTHER, 1);
@@ -1050,10 +1105,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       if (c.opts.residual == 1) {
         const size_t cnt = size_t(items) * n * kap;
         split_x_kernel<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(X, Xdf, cnt, conv, size_t(n) * kap);
-        residual_df_kernel<<<gres, tres, size_t(64) * kap * 16, st>>>(reinterpret_cast<const float4*>(c.M64), stride,
-                                                                        ld, n, kap, Xdf, R, conv,
-                                                                        prof_work_counter(PH_RESIDUAL));
-        prof_launched(PH_RESIDUAL, 1);
+        launch_residual_df(conv, prof_work_counter(PH_RESIDUAL), PH_RESIDUAL);
       } else {
         residual64_kernel<<<gres, tres, smem_res, st>>>(c.M64, stride, ld, n, kap, X, R, conv,
                                                         prof_work_counter(PH_RESIDUAL));
