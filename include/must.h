@@ -186,7 +186,9 @@ void must_plan_free(must_plan* plan);
  *   knob 3: row tiles per CTA of the streamed kernel (1..64, default 16);
  *   knob 4: panel look-ahead of the mixed path: 1 (default) factors panel
  *           k+1 on a high-priority side stream while the rest of step k's
- *           trailing update runs, 0 keeps every step on the caller's stream.
+ *           trailing update runs, 0 keeps every step on the caller's stream;
+ *   knob 5: right-hand sides per CTA of the mixed path's correction solve
+ *           (2, 4 or 8; 0, the default, takes 8 up to order 2600, else 4).
  * Process-wide; set them between calls, not while solves are being enqueued.
  */
 must_status must_tune_set(int32_t knob, int32_t value);

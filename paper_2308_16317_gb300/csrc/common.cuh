@@ -65,6 +65,13 @@ __device__ __forceinline__ void cfmsf(cf& a, cf b, cf c) {
   a.y = fmaf(-b.x, c.y, a.y);
   a.y = fmaf(-b.y, c.x, a.y);
 }
+// a += b c
+__device__ __forceinline__ void cfmaf_acc(cf& a, cf b, cf c) {
+  a.x = fmaf(b.x, c.x, a.x);
+  a.x = fmaf(-b.y, c.y, a.x);
+  a.y = fmaf(b.x, c.y, a.y);
+  a.y = fmaf(b.y, c.x, a.y);
+}
 __device__ __forceinline__ cf cmulf(cf a, cf b) { return mkf(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ cf cinvf(cf a) {
   if (fabsf(a.x) >= fabsf(a.y)) {

@@ -55,7 +55,7 @@ __host__ __device__ inline int leaf_width(int n) {
 
 __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int r,
                                                       int k0, int nbe, int* __restrict__ piv0, int* __restrict__ status,
-                                                      const int* __restrict__ conv) {
+                                                      const int* __restrict__ conv, float2* __restrict__ Linv0) {
   extern __shared__ cf Lf[];           // leaf, column-major [lw][mrows]
   __shared__ float sv[PPT / 32];
   __shared__ int si[PPT / 32];
@@ -241,6 +241,29 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
     }
     __syncthreads();
   }
+  // The inverse of the panel's unit lower L11 for the U12 solve, one warp per
+  // column of the inverse (forward substitution on the identity), with L11
+  // staged in the leaf buffer.
+  __syncthreads();
+  cf* L11 = Lf;                        // [64][65]
+  for (int t = tid; t < nbe * nbe; t += PPT) {
+    const int i = t % nbe, j = t / nbe;
+    L11[i * 65 + j] = A[size_t(k0 + j) * ld + k0 + i];
+  }
+  __syncthreads();
+  cf* Li = reinterpret_cast<cf*>(Linv0 + size_t(item) * 64 * 64);   // column-major [col][row]
+  for (int col = warp; col < 64; col += PPT / 32) {
+    cf v0 = mkf((lane == col && lane < nbe) ? 1.f : 0.f, 0.f);
+    cf v1 = mkf((lane + 32 == col && lane + 32 < nbe) ? 1.f : 0.f, 0.f);
+    for (int j = col; j < nbe - 1; ++j) {
+      const cf src = (j < 32) ? v0 : v1;
+      const cf xj = mkf(__shfl_sync(0xffffffffu, src.x, j & 31), __shfl_sync(0xffffffffu, src.y, j & 31));
+      if (lane > j && lane < nbe) cfmsf(v0, L11[lane * 65 + j], xj);
+      if (lane + 32 > j && lane + 32 < nbe) cfmsf(v1, L11[(lane + 32) * 65 + j], xj);
+    }
+    Li[col * 64 + lane] = v0;
+    Li[col * 64 + lane + 32] = v1;
+  }
 }
 
 __global__ void laswp32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int r, int k0, int nbe,
@@ -262,35 +285,56 @@ __global__ void laswp32_kernel(float2* __restrict__ A0, size_t stride, int ld, i
 }
 
 // U12 = L11^{-1} A12, nbe <= 64: one warp per column, lane i holds x_i, x_{i+32}.
-// U12 = L11^{-1} A12 for the panel's nbe <= 64 rows: each block loads the unit
-// lower L11 once into shared memory and solves TRSM_COLS columns, one warp per
-// column at a time (the row index runs over the lanes).
+// U12 = L11^{-1} A12 for the panel's nbe <= 64 rows as a dense lower-
+// triangular product per 64-column tile of A12, with the inverse of L11 that
+// the panel kernel leaves behind; every thread is busy (the substitution
+// applied column by column leaves most lanes idle and is issue-bound).
 constexpr int TRSM_COLS = 64;
+constexpr size_t TRSM_SMEM = size_t(64 * 64 + TRSM_COLS * 65) * sizeof(cf);
 
-__global__ void __launch_bounds__(256) trsm32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int k0,
-                                                     int nbe) {
-  __shared__ cf L[64][65];
+// One CTA per (64-column tile, item): x = Linv a for every column of the tile.
+// Thread t takes rows i and 63 - i (i = t % 32, so every thread sums 65 terms)
+// of TRSM_COLS / 8 columns.
+__global__ void __launch_bounds__(256) trsm_inv_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int k0,
+                                                       int nbe, const float2* __restrict__ Linv0) {
+  extern __shared__ cf tsm[];
+  cf (*Li)[64] = reinterpret_cast<cf (*)[64]>(tsm);                // [col j][row i]
+  cf (*Xs)[65] = reinterpret_cast<cf (*)[65]>(tsm + 64 * 64);      // [column][row]
   const int item = blockIdx.y;
   cf* A = reinterpret_cast<cf*>(A0 + size_t(item) * stride);
-  for (int t = threadIdx.x; t < nbe * nbe; t += blockDim.x) {
-    const int i = t % nbe, j = t / nbe;
-    L[i][j] = A[size_t(k0 + j) * ld + k0 + i];
+  const cf* Lg = reinterpret_cast<const cf*>(Linv0 + size_t(item) * 64 * 64);
+  const int c_beg = k0 + nbe + blockIdx.x * TRSM_COLS;
+  const int ncol = min(TRSM_COLS, n - c_beg);
+  for (int t = threadIdx.x; t < 64 * 64; t += blockDim.x) tsm[t] = Lg[t];
+  for (int t = threadIdx.x; t < ncol * 64; t += blockDim.x) {
+    const int i = t & 63, cc = t >> 6;
+    Xs[cc][i] = (i < nbe) ? A[size_t(c_beg + cc) * ld + k0 + i] : mkf(0.f, 0.f);
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c_end = min(n, k0 + nbe + (int(blockIdx.x) + 1) * TRSM_COLS);
-  for (int col = k0 + nbe + blockIdx.x * TRSM_COLS + warp; col < c_end; col += 8) {
-    cf* x = A + size_t(col) * ld + k0;
-    cf v0 = (lane < nbe) ? x[lane] : mkf(0.f, 0.f);
-    cf v1 = (lane + 32 < nbe) ? x[lane + 32] : mkf(0.f, 0.f);
-    for (int j = 0; j < nbe - 1; ++j) {
-      const cf src = (j < 32) ? v0 : v1;
-      const cf xj = mkf(__shfl_sync(0xffffffffu, src.x, j & 31), __shfl_sync(0xffffffffu, src.y, j & 31));
-      if (lane > j && lane < nbe) cfmsf(v0, L[lane][j], xj);
-      if (lane + 32 > j && lane + 32 < nbe) cfmsf(v1, L[lane + 32][j], xj);
+  const int i0 = threadIdx.x & 31, i1 = 63 - i0;
+  const int cg = threadIdx.x >> 5;     // 8 column groups
+  constexpr int CPT = TRSM_COLS / 8;
+  cf y0[CPT], y1[CPT];
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) y0[q] = y1[q] = mkf(0.f, 0.f);
+  for (int j = 0; j <= i1; ++j) {
+    const cf l1 = Li[j][i1];
+    const cf l0 = (j <= i0) ? Li[j][i0] : mkf(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const cf a = Xs[cg * CPT + q][j];
+      cfmaf_acc(y1[q], l1, a);
+      cfmaf_acc(y0[q], l0, a);
     }
-    if (lane < nbe) x[lane] = v0;
-    if (lane + 32 < nbe) x[lane + 32] = v1;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) {
+    const int cc = cg * CPT + q;
+    if (cc < ncol) {
+      if (i0 < nbe) A[size_t(c_beg + cc) * ld + k0 + i0] = y0[q];
+      if (i1 < nbe) A[size_t(c_beg + cc) * ld + k0 + i1] = y1[q];
+    }
   }
 }
 
@@ -905,6 +949,7 @@ thread_local SideStream g_side;
 }  // namespace
 
 int g_lookahead = 1;   // tuning knob 4
+int g_corr_rhs = 0;    // tuning knob 5 (0: by matrix order)
 
 static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
   int dev = 0;
@@ -939,6 +984,7 @@ size_t mixed_item_bytes(int n, int ld, int kap) {
          + 3 * a256(size_t(n) * kap * 16)  // X, R, X as double-float pairs
          + RES_SPLIT * a256(size_t(n) * kap * 16)   // split-K residual partials
          + a256(size_t(kap) * kap * 16)    // Sinv
+         + a256(size_t(64) * 64 * 8)       // inverse of the panel's L11
          + 1280                            // norms, previous norms, conv, error word, seed flags
          + tc_pack_bytes_per_item(n);      // tensor-core operand packs
 }
@@ -956,6 +1002,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   float4* Xdf = reinterpret_cast<float4*>(take(size_t(items) * n * kap * 16));
   float4* Rpart = reinterpret_cast<float4*>(take(size_t(RES_SPLIT) * items * n * kap * 16));
   double2* Sinv = reinterpret_cast<double2*>(take(size_t(items) * kap * kap * 16));
+  float2* Linv = reinterpret_cast<float2*>(take(size_t(items) * 64 * 64 * 8));
   double* norms = reinterpret_cast<double*>(take(size_t(items) * 16));
   double* prevn = reinterpret_cast<double*>(take(size_t(items) * 8));
   int* conv = reinterpret_cast<int*>(take(size_t(items) * 4));
@@ -980,6 +1027,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(panel32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(PANEL_SMEM));
+      cudaFuncSetAttribute(trsm_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TRSM_SMEM));
       attr = true;
     }
   }
@@ -991,11 +1039,11 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   cudaStream_t ss = nullptr;
   cudaEvent_t ev_next = nullptr, ev_panel = nullptr;
   const bool lookahead = g_lookahead && side_stream(&ss, &ev_next, &ev_panel);
-  const size_t panel_smem = size_t(leaf_width(n)) * n * sizeof(float2);
+  const size_t panel_smem = std::max(size_t(leaf_width(n)) * n, size_t(64 * 65)) * sizeof(float2);
   const int bn = tc_tile_n();
   auto launch_panel = [&](int k, int w, cudaStream_t s) {
     ProfScope ps(PH_PANEL, s);
-    panel32_kernel<<<items, PPT, panel_smem, s>>>(M32, stride, ld, n, r, k, w, c.piv, c.status, conv);
+    panel32_kernel<<<items, PPT, panel_smem, s>>>(M32, stride, ld, n, r, k, w, c.piv, c.status, conv, Linv);
     prof_launched(PH_PANEL, 1, items);
   };
   bool panel_ready = false;   // panel k0 already launched on the side stream
@@ -1015,7 +1063,8 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     if (rem > 0) {
       {
         ProfScope ps(PH_TRSM, st);
-        trsm32_kernel<<<dim3((rem + TRSM_COLS - 1) / TRSM_COLS, items), 256, 0, st>>>(M32, stride, ld, n, k0, nbe);
+        trsm_inv_kernel<<<dim3((rem + TRSM_COLS - 1) / TRSM_COLS, items), 256, TRSM_SMEM, st>>>(M32, stride, ld, n,
+                                                                                           k0, nbe, Linv);
         prof_launched(PH_TRSM, 1, items);
       }
       if (!tc_pack(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, st)) return MUST_ECUDA;
@@ -1049,7 +1098,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     prof_launched(PH_SCHUR, 1, items);
   }
   // refinement
-  const int G = (n <= 2600) ? 8 : 4;
+  const int G = g_corr_rhs ? g_corr_rhs : ((n <= 2600) ? 8 : 4);
   const size_t smem_corr = size_t(n) * G * 8;
   const dim3 gcorr((kap + G - 1) / G, items);
   const size_t smem_res = size_t(64) * kap * 16;
@@ -1060,6 +1109,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     if (!attr) {
       cudaFuncSetAttribute(correct_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(correct_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(correct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(residual64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 16);
       cudaFuncSetAttribute(residual_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 16);
       attr = true;
@@ -1114,14 +1164,17 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     }
     {
       ProfScope ps(PH_CORRECT, st);
+      const int* ff = (first && seeded) ? first_flags : nullptr;
+      unsigned long long* wc = prof_work_counter(PH_CORRECT);
       if (G == 8)
         correct_kernel<8><<<gcorr, 512, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
-                                                         conv, first, (first && seeded) ? first_flags : nullptr,
-                                                         prof_work_counter(PH_CORRECT));
-      else
+                                                         conv, first, ff, wc);
+      else if (G == 4)
         correct_kernel<4><<<gcorr, 512, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
-                                                         conv, first, (first && seeded) ? first_flags : nullptr,
-                                                         prof_work_counter(PH_CORRECT));
+                                                         conv, first, ff, wc);
+      else
+        correct_kernel<2><<<gcorr, 512, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
+                                                         conv, first, ff, wc);
       prof_launched(PH_CORRECT, 1);
     }
     if (first) {

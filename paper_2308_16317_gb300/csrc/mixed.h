@@ -28,3 +28,6 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st);
 // Tuning knob 4: 1 (default) factor panel k+1 on a high-priority side stream
 // while the rest of step k's trailing update runs; 0 keeps one stream.
 extern int g_lookahead;
+// Tuning knob 5: right-hand sides per CTA of the correction solve (2, 4 or 8;
+// 0 = 8 up to order 2600, else 4).
+extern int g_corr_rhs;

@@ -511,6 +511,13 @@ extern "C" must_status must_tune_set(int32_t knob, int32_t value) {
       if (value != 0 && value != 1) { must_set_error("look-ahead switch must be 0 or 1"); return MUST_EINVAL; }
       g_lookahead = value;
       return MUST_OK;
+    case 5:   // right-hand sides per CTA of the correction solve
+      if (value != 0 && value != 2 && value != 4 && value != 8) {
+        must_set_error("correction right-hand sides per CTA must be 0, 2, 4 or 8");
+        return MUST_EINVAL;
+      }
+      g_corr_rhs = value;
+      return MUST_OK;
   }
   must_set_error("unknown tuning knob %d", knob);
   return MUST_EINVAL;
@@ -523,6 +530,7 @@ extern "C" int32_t must_tune_get(int32_t knob) {
     case 2: return tc_get_streamed();
     case 3: return tc_get_run();
     case 4: return g_lookahead;
+    case 5: return g_corr_rhs;
   }
   return -1;
 }
