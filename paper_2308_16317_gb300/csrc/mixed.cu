@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
                                                       double* __restrict__ norms, const int* __restrict__ conv,
                                                       int first_all, const int* __restrict__ first_flags,
                                                       unsigned long long* __restrict__ work) {
-  extern __shared__ cf w[];   // [n][G]
+  extern __shared__ cf w[];   // [G][n] (right-hand side major: conflict-free row access)
   __shared__ cf Tb[32][33];   // staged diagonal block
   const int item = blockIdx.y;
   if (conv[item]) return;
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
   const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
   // gather w = P (D R)
   for (int t = tid; t < n * G; t += T) {
-    const int i = t / G, c = t % G;
+    const int i = t % n, c = t / n;
     cf v = mkf(0.f, 0.f);
     if (c < ng) {
       const int src = perm[i];
@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
         v = mkf(float(d[src] * rv.x), float(d[src] * rv.y));
       }
     }
-    w[t] = v;
+    w[c * n + i] = v;
   }
   __syncthreads();
   // forward: unit lower L, columns 0..r-1, rows 0..n-1.  On the first solve
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
     if (warp == 0) {
       cf v[G];
 #pragma unroll
-      for (int c = 0; c < G; ++c) v[c] = (lane < bs) ? w[(jb + lane) * G + c] : mkf(0.f, 0.f);
+      for (int c = 0; c < G; ++c) v[c] = (lane < bs) ? w[c * n + jb + lane] : mkf(0.f, 0.f);
       for (int j = 0; j < bs - 1; ++j) {
         const cf l = (lane > j && lane < bs) ? Tb[lane][j] : mkf(0.f, 0.f);
 #pragma unroll
@@ -669,13 +669,13 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
       }
       if (lane < bs)
 #pragma unroll
-        for (int c = 0; c < G; ++c) w[(jb + lane) * G + c] = v[c];
+        for (int c = 0; c < G; ++c) w[c * n + jb + lane] = v[c];
     }
     __syncthreads();
     for (int i = je + tid; i < n; i += T) {
       cf acc[G];
 #pragma unroll
-      for (int c = 0; c < G; ++c) acc[c] = w[i * G + c];
+      for (int c = 0; c < G; ++c) acc[c] = w[c * n + i];
 #pragma unroll
       for (int h = 0; h < 32; h += 16) {
         cf lrow[16];
@@ -686,10 +686,10 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
         for (int j = 0; j < 16; ++j)
           if (h + j < bs)
 #pragma unroll
-            for (int c = 0; c < G; ++c) cfmsf(acc[c], lrow[j], w[(jb + h + j) * G + c]);
+            for (int c = 0; c < G; ++c) cfmsf(acc[c], lrow[j], w[c * n + jb + h + j]);
       }
 #pragma unroll
-      for (int c = 0; c < G; ++c) w[i * G + c] = acc[c];
+      for (int c = 0; c < G; ++c) w[c * n + i] = acc[c];
     }
     __syncthreads();
   }
@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
         const double2 sv = Si[size_t(i) * kap + k];
 #pragma unroll
         for (int c = 0; c < G; ++c) {
-          const cf x = w[(r + k) * G + c];
+          const cf x = w[c * n + r + k];
           tmp[c] = tmp[c] + mk(sv.x, sv.y) * mk(x.x, x.y);
         }
       }
@@ -713,21 +713,21 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
     __syncthreads();
     if (i < kap)
 #pragma unroll
-      for (int c = 0; c < G; ++c) w[(r + i) * G + c] = mkf(float(tmp[c].x), float(tmp[c].y));
+      for (int c = 0; c < G; ++c) w[c * n + r + i] = mkf(float(tmp[c].x), float(tmp[c].y));
     __syncthreads();
   }
   // w_1 -= U12 w_c
   for (int i = tid; i < r; i += T) {
     cf acc[G];
 #pragma unroll
-    for (int c = 0; c < G; ++c) acc[c] = w[i * G + c];
+    for (int c = 0; c < G; ++c) acc[c] = w[c * n + i];
     for (int k = 0; k < kap; ++k) {
       const cf u = A[size_t(r + k) * ld + i];
 #pragma unroll
-      for (int c = 0; c < G; ++c) cfmsf(acc[c], u, w[(r + k) * G + c]);
+      for (int c = 0; c < G; ++c) cfmsf(acc[c], u, w[c * n + r + k]);
     }
 #pragma unroll
-    for (int c = 0; c < G; ++c) w[i * G + c] = acc[c];
+    for (int c = 0; c < G; ++c) w[c * n + i] = acc[c];
   }
   __syncthreads();
   // backward: U11 (non-unit upper), blocks from the bottom
@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
     if (warp == 0) {
       cf v[G];
 #pragma unroll
-      for (int c = 0; c < G; ++c) v[c] = (lane < bs) ? w[(jb + lane) * G + c] : mkf(0.f, 0.f);
+      for (int c = 0; c < G; ++c) v[c] = (lane < bs) ? w[c * n + jb + lane] : mkf(0.f, 0.f);
       const cf dinv = (lane < bs) ? cinvf(Tb[lane][lane]) : mkf(0.f, 0.f);
       for (int j = bs - 1; j >= 0; --j) {
         if (lane == j)
@@ -756,13 +756,13 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
       }
       if (lane < bs)
 #pragma unroll
-        for (int c = 0; c < G; ++c) w[(jb + lane) * G + c] = v[c];
+        for (int c = 0; c < G; ++c) w[c * n + jb + lane] = v[c];
     }
     __syncthreads();
     for (int i = tid; i < jb; i += T) {
       cf acc[G];
 #pragma unroll
-      for (int c = 0; c < G; ++c) acc[c] = w[i * G + c];
+      for (int c = 0; c < G; ++c) acc[c] = w[c * n + i];
 #pragma unroll
       for (int h = 0; h < 32; h += 16) {
         cf urow[16];
@@ -773,10 +773,10 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
         for (int j = 0; j < 16; ++j)
           if (h + j < bs)
 #pragma unroll
-            for (int c = 0; c < G; ++c) cfmsf(acc[c], urow[j], w[(jb + h + j) * G + c]);
+            for (int c = 0; c < G; ++c) cfmsf(acc[c], urow[j], w[c * n + jb + h + j]);
       }
 #pragma unroll
-      for (int c = 0; c < G; ++c) w[i * G + c] = acc[c];
+      for (int c = 0; c < G; ++c) w[c * n + i] = acc[c];
     }
     __syncthreads();
   }
@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(512) correct_kernel(const float2* __restrict__
   double2* X = X0 + size_t(item) * n * kap;
   for (int t = tid; t < n * ng; t += T) {
     const int i = t % n, c = t / n;
-    const cf v = w[i * G + c];
+    const cf v = w[c * n + i];
     const double2 dl = make_double2(d[i] * v.x, d[i] * v.y);
     double2 x = first ? make_double2(0.0, 0.0) : X[size_t(cb + c) * n + i];
     x.x += dl.x;
