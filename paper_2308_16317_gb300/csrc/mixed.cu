@@ -340,18 +340,24 @@ __global__ void __launch_bounds__(256) trsm_inv_kernel(float2* __restrict__ A0, 
 
 // ------------------------------------------------ permutation, Schur block --
 // perm[i] = row of the original matrix that the swap sequence moves to row i.
-__global__ void perm_kernel(const int* __restrict__ piv0, int r, int n, int* __restrict__ perm0, int items) {
-  const int item = blockIdx.x * blockDim.x + threadIdx.x;
-  if (item >= items) return;
+// One CTA per item: the swaps are applied in order by one thread on a copy in
+// shared memory (they are sequential by nature), the rest is parallel.
+__global__ void perm_kernel(const int* __restrict__ piv0, int r, int n, int* __restrict__ perm0) {
+  extern __shared__ int pm[];
+  const int item = blockIdx.x;
   const int* piv = piv0 + size_t(item) * r;
   int* perm = perm0 + size_t(item) * n;
-  for (int i = 0; i < n; ++i) perm[i] = i;
-  for (int k = 0; k < r; ++k) {
-    const int p = piv[k];
-    const int t = perm[k];
-    perm[k] = perm[p];
-    perm[p] = t;
-  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) pm[i] = i;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < r; ++k) {
+      const int p = piv[k];
+      const int t = pm[k];
+      pm[k] = pm[p];
+      pm[p] = t;
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = pm[i];
 }
 
 // Sinv = S_s^{-1} (FP64 Gauss-Jordan on the FP32 Schur block of M_s).
@@ -1028,6 +1034,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     if (!attr) {
       cudaFuncSetAttribute(panel32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(PANEL_SMEM));
       cudaFuncSetAttribute(trsm_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TRSM_SMEM));
+      cudaFuncSetAttribute(perm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       attr = true;
     }
   }
@@ -1087,7 +1094,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   }
   {
     ProfScope ps_schur(PH_SCHUR, st);
-    perm_kernel<<<(items + 63) / 64, 64, 0, st>>>(c.piv, r, n, perm, items);
+    perm_kernel<<<items, 256, size_t(n) * 4, st>>>(c.piv, r, n, perm);
     prof_launched(PH_SCHUR, 1);
     static bool attr = false;
     if (!attr) {
