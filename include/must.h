@@ -183,7 +183,7 @@ void must_plan_free(must_plan* plan);
  *           streamed kernel, whose CTAs each update a short run of tiles and
  *           move C through shared memory with TMA loads and stores, 0 one CTA
  *           per tile with C read and written from registers;
- *   knob 3: row tiles per CTA of the streamed kernel (1..64, default 16);
+ *   knob 3: row tiles per CTA of the streamed kernel (1..64, default 32);
  *   knob 4: panel look-ahead of the mixed path: 1 (default) factors panel
  *           k+1 on a high-priority side stream while the rest of step k's
  *           trailing update runs, 0 keeps every step on the caller's stream;

@@ -122,19 +122,6 @@ __device__ __forceinline__ bool mbar_wait_f(uint64_t* b, uint32_t parity, volati
   }
 }
 
-// OR of `flag` over the 256 epilogue threads (named barrier 1); every
-// epilogue thread reaches it once per tile whatever happened before.
-__device__ __forceinline__ bool epi_any(bool flag) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n barrier.cta.red.or.pred p, 1, 256, q;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(r)
-      : "r"(flag ? 1u : 0u)
-      : "memory");
-  return r != 0;
-}
-
-__device__ __forceinline__ void epi_sync() { asm volatile("barrier.cta.sync 1, 256;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
 // 1024 bytes apart (SBO), descriptor version 1.
@@ -315,13 +302,14 @@ __global__ void __launch_bounds__(256, 1)
 // (B_hi and B_lo for all K, 32 KB) is loaded once and stays in shared memory,
 // the A rows stream through a 3-stage ring (A_hi and A_lo of one 128-byte K
 // step per stage, so A_hi is fetched once for both products that use it), and
-// C tiles stream through 3 buffers: the epilogue's leader thread keeps two C
-// loads in flight while the tile in hand is updated and stored.
+// C tiles stream through 3 buffers: a C-mover warp keeps two C loads in
+// flight, and stores each tile once the epilogue warps have updated it, so
+// the epilogue never waits on a store.
 constexpr int SBN = 64;                        // complex columns per tile
 constexpr int S_STAGES = 3;                    // A ring depth
 constexpr int S_CBUF = 3;                      // C tile buffers
 constexpr int C_TILE_BYTES = BM * SBN * 4;     // 128 floats x 64 columns
-constexpr int S_THREADS = 320;                 // producer, MMA, 8 epilogue warps
+constexpr int S_THREADS = 352;                 // producer, MMA, 8 epilogue warps, C mover
 constexpr int S_KSTEPS = 2;                    // 128-byte K steps per product (K = 2 x 64 complex)
 constexpr int SA_BYTES = BM * KB;              // one A operand K step
 constexpr int SB_BYTES = SBN * KB;             // one B operand K step
@@ -364,6 +352,7 @@ __global__ void __launch_bounds__(S_THREADS, 1)
   __shared__ __align__(8) uint64_t empty[S_STAGES];
   __shared__ __align__(8) uint64_t bfull;        // resident B landed
   __shared__ __align__(8) uint64_t cfull[S_CBUF]; // C tile landed
+  __shared__ __align__(8) uint64_t cdone[S_CBUF]; // C tile updated by the epilogue (8 warps)
   __shared__ __align__(8) uint64_t afull[2];     // accumulator ready
   __shared__ __align__(8) uint64_t aempty[2];    // accumulator read out
   __shared__ __align__(8) uint64_t mdone;        // every MMA of this CTA retired
@@ -380,7 +369,10 @@ __global__ void __launch_bounds__(S_THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < S_CBUF; ++b) mbar_init(&cfull[b], 1);
+    for (int b = 0; b < S_CBUF; ++b) {
+      mbar_init(&cfull[b], 1);
+      mbar_init(&cdone[b], 8);
+    }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&afull[b], 1);
       mbar_init(&aempty[b], 8);
@@ -465,26 +457,16 @@ __global__ void __launch_bounds__(S_THREADS, 1)
     mma_commit(&mdone);
     volatile int dummy = 0;
     mbar_wait_f(&mdone, 0, &dummy);
-  } else if (warp >= 2) {
+  } else if (warp >= 2 && warp < 10) {
     // epilogue: warp w reads TMEM lane quarter w % 4 and column half (w - 2) / 4;
-    // thread = one real row of the tile; C tile in shared memory [column][128 floats]
+    // thread = one real row of the tile; C tile in shared memory [column][128 floats].
+    // It never waits for stores: the C mover (warp 10) takes the tile from here.
     const int ew = warp - 2, quarter = warp & 3, half = ew >> 2;
     const int x = quarter * 32 + lane;
-    const bool leader = (ew == 0 && lane == 0);
-    int c_issued = 0;
-    if (leader) {
-      for (; c_issued < S_CBUF && c_issued < ntile; ++c_issued) {
-        const int cb = c_issued;
-        mbar_expect_tx(&cfull[cb], C_TILE_BYTES);
-        tma_load_3d(cbuf + cb * C_TILE_BYTES, &tC, 2 * P.abase + (rt0 + c_issued) * BM, P.base + col0, item,
-                    &cfull[cb]);
-      }
-    }
     for (int lt = 0; lt < ntile; ++lt) {
       const int cb = lt % S_CBUF, ab = lt & 1;
-      bool bad = !mbar_wait_f(&cfull[cb], (lt / S_CBUF) & 1, s_fail);
-      bad = bad || !mbar_wait_f(&afull[ab], (lt >> 1) & 1, s_fail);
-      if (epi_any(bad)) break;
+      if (!mbar_wait_f(&cfull[cb], (lt / S_CBUF) & 1, s_fail)) break;
+      if (!mbar_wait_f(&afull[ab], (lt >> 1) & 1, s_fail)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int row0 = (rt0 + lt) * BM;
       float* cs = reinterpret_cast<float*>(cbuf + cb * C_TILE_BYTES);
@@ -502,17 +484,32 @@ __global__ void __launch_bounds__(S_THREADS, 1)
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      epi_sync();
-      if (leader) {
-        tma_store_3d(&tC, cs, 2 * P.abase + row0, P.base + col0, item);   // returns once the buffer is read
-        if (c_issued < ntile) {
-          mbar_expect_tx(&cfull[cb], C_TILE_BYTES);
-          tma_load_3d(cs, &tC, 2 * P.abase + (rt0 + c_issued) * BM, P.base + col0, item, &cfull[cb]);
-          ++c_issued;
-        }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&cdone[cb]);
+    }
+  } else if (warp == 10 && lane == 0) {
+    // C mover: the first S_CBUF tile loads, then per tile: wait for the
+    // epilogue, store the tile, and once the store has read the buffer, load
+    // the tile S_CBUF ahead into it
+    int c_issued = 0;
+    for (; c_issued < S_CBUF && c_issued < ntile; ++c_issued) {
+      const int cb = c_issued;
+      mbar_expect_tx(&cfull[cb], C_TILE_BYTES);
+      tma_load_3d(cbuf + cb * C_TILE_BYTES, &tC, 2 * P.abase + (rt0 + c_issued) * BM, P.base + col0, item,
+                  &cfull[cb]);
+    }
+    for (int lt = 0; lt < ntile; ++lt) {
+      const int cb = lt % S_CBUF;
+      if (!mbar_wait_f(&cdone[cb], (lt / S_CBUF) & 1, s_fail)) break;
+      float* cs = reinterpret_cast<float*>(cbuf + cb * C_TILE_BYTES);
+      tma_store_3d(&tC, cs, 2 * P.abase + (rt0 + lt) * BM, P.base + col0, item);   // returns once read
+      if (c_issued < ntile) {
+        mbar_expect_tx(&cfull[cb], C_TILE_BYTES);
+        tma_load_3d(cs, &tC, 2 * P.abase + (rt0 + c_issued) * BM, P.base + col0, item, &cfull[cb]);
+        ++c_issued;
       }
     }
-    if (leader && *s_fail) {
+    if (*s_fail) {
       // drain the C loads still in flight
       volatile int dummy = 0;
       for (int cb = 0; cb < S_CBUF && cb < c_issued; ++cb) {
@@ -643,7 +640,7 @@ bool make_c_map(CUtensorMap* m, float2* C, int ld, size_t stride, int n, int ite
 constexpr int TC_STAGES = 3;
 int g_tile_n = 128;   // 128 or 256 complex columns per tile (autotuned)
 int g_streamed = 1;   // 1: streamed kernel (BF16 splits); 0: per-tile kernel
-int g_run = 16;       // row tiles per CTA of the streamed kernel
+int g_run = 32;       // row tiles per CTA of the streamed kernel
 
 template <int BN>
 void launch_tc(const CUtensorMap& mah, const CUtensorMap& mal, const CUtensorMap& mbh, const CUtensorMap& mbl,
