@@ -568,6 +568,59 @@ def run_canted(args):
                       "im_E": [float(e.imag) for e in w.energies]}))
 
 
+def run_paper_shapes(args):
+    """The paper's own ranks (Sec. 4.1, lmax = 4): a Ni30Au70-shaped 249-site LIZ
+    (n = 6225, two spins) and a CoCrFeMnNi-shaped canted 135-site LIZ
+    (n = 6750), 8 contour energies each; mixed-precision and plain FP64
+    throughput, and the mixed path's error against the FP64 path."""
+    import torch
+    from paper_2308_16317_gb300 import binding as B
+    from paper_2308_16317_gb300 import build as libbuild
+    from paper_2308_16317_gb300 import workload as wl
+    from paper_2308_16317_gb300.runner import Session, blocks_to_numpy
+    libbuild.build()
+    B.load()
+    res = {}
+    for name, w in (("niau249_n6225", wl.niau249(n_e=8)), ("cocrfemnni135_canted_n6750", wl.cocrfemnni135_canted(n_e=8))):
+        s = Session(w)
+        items = len(w.energies) * (1 if w.canted else s.nspin)
+        out = s.alloc_out(1)
+        opts = B.must_default_opts(PREC[args.precision], residual=1 if args.residual == "df" else 0)
+        for _ in range(max(1, args.warmup)):
+            s.solve(opts, out=out)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            s.solve(opts, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        tau = blocks_to_numpy(out[0][0])
+        ok = bool((out[1].cpu().numpy() == 0).all())
+        out64 = s.alloc_out(1)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record()
+        s.solve(B.must_default_opts(0), out=out64)
+        f1.record()
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        t64 = blocks_to_numpy(out64[0][0])
+        err = np.linalg.norm(tau - t64, axis=(-2, -1)) / np.linalg.norm(t64, axis=(-2, -1))
+        n = s.lizs[0].n
+        res[name] = {"n": int(n), "solves_per_step": items, "mixed_solves_per_s": items / (ms / 1e3),
+                     "mixed_ms_per_step": ms, "fp64_solves_per_s": items / (ms64 / 1e3), "fp64_ms_per_step": ms64,
+                     "fp64_lu_tflops": items * 8.0 / 3.0 * n ** 3 / (ms64 / 1e3) / 1e12,
+                     "max_rel_err_vs_fp64": float(err.max()), "status_ok": ok}
+        del s, out, out64
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "tau_00 solves/sec at the paper's ranks (lmax = 4)", "unit": UNIT,
+                      "precision": args.precision, "residual": args.residual, "steps": args.steps,
+                      "results": res}))
+
+
 def run_cusolver_context(args):
     """Context only: the paper's own method (LU + solve in complex128, Sec. 3.2)
     through PyTorch's vendor-library path on this GPU, at the benchmark's
@@ -660,7 +713,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0)
     ap.add_argument("--workload", default="liz135",
-                    choices=["liz135", "supercell", "warmstart", "cusolver", "canted"],
+                    choices=["liz135", "supercell", "warmstart", "cusolver", "canted", "paper"],
                     help="liz135: the benchmark workload; supercell: per-site LIZs of the 256-site supercell "
                          "with vacancies (uneven n), batched and replayed as a captured plan")
     ap.add_argument("--n-lizs", type=int, default=32, help="supercell / warmstart mode: evaluation LIZs")
@@ -681,6 +734,8 @@ def main():
         run_cusolver_context(args)
     elif args.workload == "canted":
         run_canted(args)
+    elif args.workload == "paper":
+        run_paper_shapes(args)
     else:
         run_ours(args)
 

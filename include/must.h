@@ -188,7 +188,8 @@ void must_plan_free(must_plan* plan);
  *           k+1 on a high-priority side stream while the rest of step k's
  *           trailing update runs, 0 keeps every step on the caller's stream;
  *   knob 5: right-hand sides per CTA of the mixed path's correction solve
- *           (2, 4 or 8; 0, the default, takes 8 up to order 2600, else 4).
+ *           (2, 4 or 8; 0, the default, takes the most that fit: 8 up to
+ *           order 3200, 4 up to 6400, 2 up to 12800).
  * Process-wide; set them between calls, not while solves are being enqueued.
  */
 must_status must_tune_set(int32_t knob, int32_t value);

@@ -1105,7 +1105,10 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     prof_launched(PH_SCHUR, 1, items);
   }
   // refinement
-  const int G = g_corr_rhs ? g_corr_rhs : ((n <= 2600) ? 8 : 4);
+  // right-hand sides per correction CTA: the knob, else the most whose FP32
+  // workspace (n x G complex) fits in 200 KB of shared memory
+  int G = g_corr_rhs;
+  if (!G) G = (size_t(n) * 8 * 8 <= 200 * 1024) ? 8 : (size_t(n) * 4 * 8 <= 200 * 1024) ? 4 : 2;
   const size_t smem_corr = size_t(n) * G * 8;
   const dim3 gcorr((kap + G - 1) / G, items);
   const size_t smem_res = size_t(64) * kap * 16;

@@ -29,5 +29,5 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st);
 // while the rest of step k's trailing update runs; 0 keeps one stream.
 extern int g_lookahead;
 // Tuning knob 5: right-hand sides per CTA of the correction solve (2, 4 or 8;
-// 0 = 8 up to order 2600, else 4).
+// 0 = the most that fit: 8 up to order 3200, 4 up to 6400, else 2).
 extern int g_corr_rhs;

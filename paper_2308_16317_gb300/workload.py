@@ -189,3 +189,37 @@ def random_liz(seed: int, max_shell: int = 7) -> Liz:
     rng = np.random.default_rng(seed)
     pos, _ = fcc_cluster(max_shell)
     return Liz(pos, rng.integers(0, 2, size=pos.shape[0]).astype(np.int32))
+
+
+# ---------------------------------------------------------------------------
+# The paper's own matrix shapes (Sec. 4.1): lmax = 4 (kappa = 25 per spin).
+# The alloys' potentials are not available; square wells of graded depths
+# stand in for the species, on the paper's lattice type, LIZ sizes and ranks.
+
+def _depths(n_species: int, nspin: int) -> np.ndarray:
+    """Well depths evenly spread over [V_A, V_B], split by spin as elsewhere."""
+    v = np.linspace(V_SPECIES[0], V_SPECIES[1], n_species)
+    if nspin == 1:
+        return v[None, :]
+    return np.stack([v - SPIN_SPLIT, v + SPIN_SPLIT])
+
+
+def niau249(seed: int = SEED_BASE + 6, n_e: int = 8) -> Workload:
+    """Ni30Au70-shaped LIZ: 249 sites (fcc shells 1-12), lmax = 4, rank
+    n = 6225; species Ni with probability 0.3 per site; two collinear spins."""
+    rng = np.random.default_rng(seed)
+    pos, _ = fcc_cluster(12)
+    species = (rng.random(pos.shape[0]) >= 0.3).astype(np.int32)   # 0 = Ni, 1 = Au
+    return Workload("niau249_lmax4", 4, [Liz(pos, species)], semicircle_contour(n_e, im_min=0.005),
+                    _depths(2, 2), R_MT)
+
+
+def cocrfemnni135_canted(seed: int = SEED_BASE + 7, n_e: int = 8) -> Workload:
+    """CoCrFeMnNi-shaped LIZ: 135 sites (shells 1-7), lmax = 4, five species
+    drawn uniformly, random moment directions: canted rank 2n = 6750."""
+    rng = np.random.default_rng(seed)
+    pos, _ = fcc_cluster(7)
+    species = rng.integers(0, 5, size=pos.shape[0]).astype(np.int32)
+    dirs = random_unit_vectors(rng, pos.shape[0])
+    return Workload("cocrfemnni135_lmax4_canted", 4, [Liz(pos, species, dirs)], semicircle_contour(n_e),
+                    _depths(5, 2), R_MT, canted=True)

@@ -66,3 +66,15 @@ def test_supercell_vacancy_recipe():
     # deterministic from the seed
     w_again = wl.batched_supercell()
     assert all(np.array_equal(a.species, b.species) for a, b in zip(w.lizs, w_again.lizs))
+
+
+def test_paper_shaped_workloads_have_the_paper_ranks():
+    """Sec. 4.1: NiAu rank 6225 (249 sites, lmax 4), CoCrFeMnNi canted rank 6750."""
+    w = wl.niau249()
+    assert w.lizs[0].pos.shape[0] * w.kappa() == 6225 and not w.canted
+    frac_ni = float((w.lizs[0].species == 0).mean())
+    assert 0.2 < frac_ni < 0.4
+    w = wl.cocrfemnni135_canted()
+    assert w.lizs[0].pos.shape[0] * w.kappa() == 6750 and w.canted
+    assert set(np.unique(w.lizs[0].species)) == set(range(5))
+    assert np.allclose(np.linalg.norm(w.lizs[0].dirs, axis=1), 1.0)
