@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "τ_00 solves/sec at N_LIZ=135,l_max=3 (n=2160) vs plain FP64; % tensor peak"
 UNIT = "solves/s"
 PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
+RES = {"fp64": 0, "df": 1, "int": 2}
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (profiling recipe); DFMA/DMMA microbenchmark: 1.01-1.05
 FP32_PEAK_TFLOPS = 80.5      # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (measured FFMA: 75)
 FP32_INSTR_PEAK = 40.3       # T FP32 instructions/s: 152 SMs x 128 lanes x 2.07 GHz
@@ -152,7 +153,8 @@ def phase_work(phase: str, n: int, kap: int, nb: int, items: int, precision: str
         return macs * 8 * items, "flop", "alu", "paper_2308_16317_gb300/csrc/lu64.cu", "gemm64_kernel_fcc135"
     if phase == "residual":
         return 8.0 * n * n * kap * items, "flop", "alu", "paper_2308_16317_gb300/csrc/mixed.cu", \
-            "residual_df_kernel_fcc135" if residual == "df" else "residual64_kernel_fcc135"
+            {"df": "residual_df_kernel_fcc135", "int": "residual_int_kernel_fcc135"}.get(residual,
+                                                                                       "residual64_kernel_fcc135")
     if phase == "correction":
         return 8.0 * n * n * kap * items, "flop", "alu", "paper_2308_16317_gb300/csrc/mixed.cu", \
             "correct_kernel_fcc135"
@@ -188,7 +190,7 @@ def run_ours(args):
     n, kap = s.lizs[0].n, s.kap
     items = len(w.energies) * s.nspin
     prec = args.precision
-    opts = B.must_default_opts(PREC[prec], residual=1 if args.residual == "df" else 0)
+    opts = B.must_default_opts(PREC[prec], residual=RES[args.residual])
     nb = 64 if prec != "fp64" else 32
 
     def barrier():
@@ -257,6 +259,12 @@ def run_ours(args):
         elif bound == "hbm":
             peak = peaks["hbm_gbs"] * 1e9
             punit, scale = "GB/s", 1e9
+        elif dom == "residual" and args.residual == "int":
+            # split-integer residual: per complex MAC 3 64-bit integer multiply-adds (a quarter of the FP32
+            # rate, 4 issue slots each) + 8 FFMA + ~3 for splitting M: ~23 FP32-slot equivalents
+            achieved = achieved / 8.0 * 23.0
+            peak = FP32_INSTR_PEAK * 1e12
+            punit, scale = "Tslots/s (FP32-equivalent)", 1e12
         elif dom == "residual" and args.residual == "df":
             # double-float residual: 48 FP32 instructions per complex MAC (8 FP64-equivalent flops)
             achieved = achieved / 8.0 * 48.0
@@ -390,7 +398,7 @@ def run_supercell(args):
         return e0.elapsed_time(e1), B.must_launch_count() - l0, tau, st
 
     prec = args.precision
-    opts = B.must_default_opts(PREC[prec], residual=1 if args.residual == "df" else 0)
+    opts = B.must_default_opts(PREC[prec], residual=RES[args.residual])
     sampler = ClockSampler(local)
     sampler.start()
     ms, launches, tau, st = timed_plan(opts, args.steps, args.warmup)
@@ -433,7 +441,7 @@ def run_warmstart(args):
     from paper_2308_16317_gb300.runner import Session
     libbuild.build()
     B.load()
-    opts = B.must_default_opts(PREC[args.precision], residual=1 if args.residual == "df" else 0)
+    opts = B.must_default_opts(PREC[args.precision], residual=RES[args.residual])
     t0 = time.perf_counter()
     train_w = wsm.random_liz_workload(100000, args.train_lizs)
     tau_tr = wsm.solve_all(train_w, opts)
@@ -533,7 +541,7 @@ def run_canted(args):
     B.load()
     w = wl.canted135(n_e=args.n_energies)
     s = Session(w)
-    opts = B.must_default_opts(PREC[args.precision], residual=1 if args.residual == "df" else 0)
+    opts = B.must_default_opts(PREC[args.precision], residual=RES[args.residual])
     out = s.alloc_out(1)
     for _ in range(args.warmup):
         s.solve(opts, out=out)
@@ -585,7 +593,7 @@ def run_paper_shapes(args):
         s = Session(w)
         items = len(w.energies) * (1 if w.canted else s.nspin)
         out = s.alloc_out(1)
-        opts = B.must_default_opts(PREC[args.precision], residual=1 if args.residual == "df" else 0)
+        opts = B.must_default_opts(PREC[args.precision], residual=RES[args.residual])
         for _ in range(max(1, args.warmup)):
             s.solve(opts, out=out)
         torch.cuda.synchronize()
@@ -707,8 +715,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
-    ap.add_argument("--residual", default="df", choices=["fp64", "df"],
-                    help="refinement residual: FP64 (DFMA) or double-float FP32 pairs")
+    ap.add_argument("--residual", default="int", choices=list(RES),
+                    help="refinement residual: FP64 (DFMA), double-float FP32 pairs, or split-integer")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0)

@@ -604,6 +604,184 @@ __global__ void residual_df_reduce_kernel(const float4* __restrict__ P0, int ks,
   R0[size_t(item) * per + t] = make_double2(e - (double(Hr) + double(Lr)), -(double(Hi) + double(Li)));
 }
 
+// Split-integer residual: the leading parts of the off-diagonal M and of X are
+// integers on common power-of-two scales, so their products and sums are
+// exact in 64-bit integer arithmetic, and only the remainders go through FP32:
+//   M~ = M 2^(23 - e_i) = A + rho    (e_i: exponent of row i of M without its
+//                                     diagonal entry, |M_ik| < 2^(e_i - 1), so
+//                                     |A| < 2^22 and |rho| <= 1/2)
+//   X~ = X 2^(23 - f_c) = B + sigma  (f_c: exponent of column c of X)
+//   M~ X~ = A B + (A sigma + rho X~)
+// A B takes three integer products per complex MAC (re = ArBr - AiBi,
+// im = (Ar + Ai)(Br + Bi) - ArBr - AiBi), the bracket FP32 FMAs.  The diagonal
+// entry, t^-1 of the site and often far above the rest of its row, is left
+// out of the integer scale and added in FP64.  M comes from the double-float
+// copy (hi + lo), split on the fly.  Same split-K grid and partial layout as
+// residual_df_kernel.
+struct __align__(16) XQ {
+  int br, bi, bs, pad;   // B (re, im) and B_re + B_im
+  float sr, si, xr, xi;  // sigma and X~ (FP32)
+};
+
+__global__ void row_exp_kernel(const float4* __restrict__ M0, size_t stride, int ld, int n, int* __restrict__ ex0) {
+  const int item = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4* M = M0 + size_t(item) * stride + i;
+  float mx = 0.f;
+#pragma unroll 8
+  for (int k = 0; k < n; ++k) {
+    const float4 v = M[size_t(k) * ld];
+    if (k != i) mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  const int e = (mx > 0.f && mx <= 3.0e38f) ? ilogbf(mx) + 2 : 0;
+  ex0[size_t(item) * n + i] = min(max(e, -90), 120);
+}
+
+// One block per (column c, item): f_c, then X~ = X 2^(23 - f_c) split into
+// B = rint(X~) and sigma = X~ - B (FP64 arithmetic on the small X).
+__global__ void __launch_bounds__(256) split_xq_kernel(const double2* __restrict__ X0, int n, int kap,
+                                                       XQ* __restrict__ Q0, int* __restrict__ fexp0,
+                                                       const int* __restrict__ conv) {
+  __shared__ double red[8];
+  const int c = blockIdx.x, item = blockIdx.y;
+  if (conv[item]) return;
+  const double2* X = X0 + (size_t(item) * kap + c) * n;
+  XQ* Q = Q0 + (size_t(item) * kap + c) * n;
+  double mx = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) mx = fmax(mx, fmax(fabs(X[k].x), fabs(X[k].y)));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = red[0];
+  for (int w = 1; w < int(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+  int f = (mx > 0.0 && mx <= 1e300) ? ilogb(mx) + 2 : 0;
+  f = min(max(f, -90), 120);
+  const double s = ldexp(1.0, 23 - f);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double xr = X[k].x * s, xi = X[k].y * s;
+    const double br = rint(xr), bi = rint(xi);
+    XQ q;
+    q.br = int(br);
+    q.bi = int(bi);
+    q.bs = q.br + q.bi;
+    q.pad = 0;
+    q.sr = float(xr - br);
+    q.si = float(xi - bi);
+    q.xr = float(xr);
+    q.xi = float(xi);
+    Q[k] = q;
+  }
+  if (threadIdx.x == 0) fexp0[size_t(item) * kap + c] = f;
+}
+
+// int64 (|v| < 2^62) -> hi + lo with hi the nearest float; lo the rest, rounded.
+__device__ __forceinline__ void ll_split(long long v, float& hi, float& lo) {
+  hi = __ll2float_rn(v);
+  lo = __ll2float_rn(v - __float2ll_rn(hi));
+}
+
+__global__ void __launch_bounds__(1024) residual_int_kernel(const float4* __restrict__ M0, size_t stride, int ld,
+                                                           int n, int kap, const XQ* __restrict__ Q0,
+                                                           const double2* __restrict__ X0,
+                                                           const int* __restrict__ rexp0,
+                                                           const int* __restrict__ fexp0, float4* __restrict__ P0,
+                                                           const int* __restrict__ conv,
+                                                           unsigned long long* __restrict__ work) {
+  extern __shared__ XQ Qs[];   // [64][kap]
+  const int item = blockIdx.y;
+  if (conv[item]) return;
+  if (work && blockIdx.x == 0 && blockIdx.z == 0 && threadIdx.x == 0) atomicAdd(work, 1ull);
+  const float4* M = M0 + size_t(item) * stride;
+  const XQ* Q = Q0 + size_t(item) * n * kap;
+  const int tid = threadIdx.x;
+  const int row = blockIdx.x * 64 + (tid & 63);
+  const int c0 = (tid >> 6) * 4;
+  const int rowc = min(row, n - 1);      // clamped row for loads (results of row >= n are dropped)
+  const int nkb = (n + 63) / 64, ks = gridDim.z, z = blockIdx.z;
+  const int kb0 = int((long long)nkb * z / ks), kb1 = int((long long)nkb * (z + 1) / ks);
+  const int e = rexp0[size_t(item) * n + rowc];
+  const float s = __int_as_float((150 - e) << 23);   // 2^(23 - e), exact
+  const float MAGIC = 12582912.0f;                   // 1.5 * 2^23: adding it rounds |t| < 2^22 to an integer
+  long long p1[4], p2[4], p3[4];
+  float cr[4], ci[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    p1[q] = p2[q] = p3[q] = 0;
+    cr[q] = ci[q] = 0.f;
+  }
+  for (int k0 = kb0 * 64; k0 < min(n, kb1 * 64); k0 += 64) {
+    const int kn = min(64, n - k0);
+    __syncthreads();
+    for (int t = tid; t < kn * kap; t += blockDim.x) {
+      const int k = t % kn, c = t / kn;
+      Qs[k * kap + c] = Q[size_t(c) * n + k0 + k];
+    }
+    __syncthreads();
+    const float4* Mk = M + size_t(k0) * ld + rowc;
+    float4 mnext = Mk[0];
+    for (int k = 0; k < kn; ++k) {
+      float4 m = mnext;
+      if (k + 1 < kn) mnext = Mk[size_t(k + 1) * ld];
+      if (k0 + k == rowc) m = make_float4(0.f, 0.f, 0.f, 0.f);   // the diagonal goes through FP64 below
+      const float tr = m.x * s, ti = m.y * s;
+      const float yr = tr + MAGIC, yi = ti + MAGIC;
+      const int ar = __float_as_int(yr) - __float_as_int(MAGIC), ai = __float_as_int(yi) - __float_as_int(MAGIC);
+      const int as = ar + ai;
+      const float fr = yr - MAGIC, fi = yi - MAGIC;                          // A as floats
+      const float rr = fmaf(m.z, s, tr - fr), ri = fmaf(m.w, s, ti - fi);   // rho
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c0 + q < kap) {
+          const XQ x = Qs[k * kap + c0 + q];
+          p1[q] += (long long)ar * x.br;
+          p2[q] += (long long)ai * x.bi;
+          p3[q] += (long long)as * x.bs;
+          cr[q] = fmaf(fr, x.sr, cr[q]);
+          cr[q] = fmaf(-fi, x.si, cr[q]);
+          cr[q] = fmaf(rr, x.xr, cr[q]);
+          cr[q] = fmaf(-ri, x.xi, cr[q]);
+          ci[q] = fmaf(fr, x.si, ci[q]);
+          ci[q] = fmaf(fi, x.sr, ci[q]);
+          ci[q] = fmaf(rr, x.xi, ci[q]);
+          ci[q] = fmaf(ri, x.xr, ci[q]);
+        }
+    }
+  }
+  if (row >= n) return;
+  const bool has_diag = (row >= kb0 * 64 && row < kb1 * 64);
+  double2 mii = make_double2(0.0, 0.0);
+  if (has_diag) {
+    const float4 d = M[size_t(row) * ld + row];
+    mii = make_double2(double(d.x) + double(d.z), double(d.y) + double(d.w));
+  }
+  float4* P = P0 + (size_t(z) * gridDim.y + item) * size_t(n) * kap;
+  const double2* X = X0 + size_t(item) * n * kap;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (c0 + q < kap) {
+      const int c = c0 + q;
+      const float sc = __int_as_float(min(max(81 + e + fexp0[size_t(item) * kap + c], 1), 254) << 23);
+      float Hr, Lr, Hi, Li, h, l;
+      ll_split(p1[q] - p2[q], Hr, Lr);
+      ll_split(p3[q] - p1[q] - p2[q], Hi, Li);
+      Hr *= sc; Lr *= sc; Hi *= sc; Li *= sc;
+      df_acc(Hr, Lr, cr[q] * sc, 0.f);
+      df_acc(Hi, Li, ci[q] * sc, 0.f);
+      if (has_diag) {
+        const double2 xv = X[size_t(c) * n + row];
+        const double dr = mii.x * xv.x - mii.y * xv.y, di = mii.x * xv.y + mii.y * xv.x;
+        h = float(dr);
+        l = float(dr - double(h));
+        df_acc(Hr, Lr, h, l);
+        h = float(di);
+        l = float(di - double(h));
+        df_acc(Hi, Li, h, l);
+      }
+      P[size_t(c) * n + row] = make_float4(Hr, Lr, Hi, Li);
+    }
+}
+
 // --------------------------------------------- low-precision correction ----
 // delta = D U^{-1} L^{-1} P (D R) for G right-hand sides per CTA (w in shared
 // memory, FP32), then X += delta (FP64) and ||delta||^2, ||X||^2 accumulated.
@@ -987,7 +1165,10 @@ size_t mixed_item_bytes(int n, int ld, int kap) {
          + a256(size_t(n) * 8)             // scale
          + a256(size_t(n) * 4)             // scale (FP32)
          + a256(size_t(n) * 4)             // perm
-         + 3 * a256(size_t(n) * kap * 16)  // X, R, X as double-float pairs
+         + 2 * a256(size_t(n) * kap * 16)  // X, R
+         + a256(size_t(n) * kap * 32)      // X split for the residual (double-float pairs or XQ)
+         + a256(size_t(n) * 4)             // row exponents (split-integer residual)
+         + a256(size_t(kap) * 4)           // column exponents (split-integer residual)
          + RES_SPLIT * a256(size_t(n) * kap * 16)   // split-K residual partials
          + a256(size_t(kap) * kap * 16)    // Sinv
          + a256(size_t(64) * 64 * 8)       // inverse of the panel's L11
@@ -1005,7 +1186,11 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   int* perm = reinterpret_cast<int*>(take(size_t(items) * n * 4));
   double2* X = reinterpret_cast<double2*>(take(size_t(items) * n * kap * 16));
   double2* R = reinterpret_cast<double2*>(take(size_t(items) * n * kap * 16));
-  float4* Xdf = reinterpret_cast<float4*>(take(size_t(items) * n * kap * 16));
+  char* Xsplit = take(size_t(items) * n * kap * 32);
+  float4* Xdf = reinterpret_cast<float4*>(Xsplit);
+  XQ* Xq = reinterpret_cast<XQ*>(Xsplit);
+  int* rexp = reinterpret_cast<int*>(take(size_t(items) * n * 4));
+  int* fexp = reinterpret_cast<int*>(take(size_t(items) * kap * 4));
   float4* Rpart = reinterpret_cast<float4*>(take(size_t(RES_SPLIT) * items * n * kap * 16));
   double2* Sinv = reinterpret_cast<double2*>(take(size_t(items) * kap * kap * 16));
   float2* Linv = reinterpret_cast<float2*>(take(size_t(items) * 64 * 64 * 8));
@@ -1122,6 +1307,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       cudaFuncSetAttribute(correct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(residual64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 16);
       cudaFuncSetAttribute(residual_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 16);
+      cudaFuncSetAttribute(residual_int_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 32);
       attr = true;
     }
   }
@@ -1134,21 +1320,39 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   // double-float residual with RES_SPLIT K splits and the in-order reduction
   auto launch_residual_df = [&](const int* mask, unsigned long long* work, int phase) {
     const dim3 g(gres.x, items, RES_SPLIT);
-    residual_df_kernel<<<g, tres, size_t(64) * kap * 16, st>>>(reinterpret_cast<const float4*>(c.M64), stride, ld,
-                                                               n, kap, Xdf, R, Rpart, mask, work);
+    if (c.opts.residual == 2)
+      residual_int_kernel<<<g, tres, size_t(64) * kap * sizeof(XQ), st>>>(
+          reinterpret_cast<const float4*>(c.M64), stride, ld, n, kap, Xq, X, rexp, fexp, Rpart, mask, work);
+    else
+      residual_df_kernel<<<g, tres, size_t(64) * kap * 16, st>>>(reinterpret_cast<const float4*>(c.M64), stride, ld,
+                                                                 n, kap, Xdf, R, Rpart, mask, work);
     const size_t per = size_t(n) * kap;
     residual_df_reduce_kernel<<<dim3(unsigned((per + 255) / 256), items), 256, 0, st>>>(Rpart, RES_SPLIT, items, n,
                                                                                      kap, R, mask);
     prof_launched(phase, 2);
   };
+  // X split for the residual: double-float pairs, or integer + FP32 remainder
+  auto launch_split_x = [&](const int* mask) {
+    if (c.opts.residual == 2) {
+      split_xq_kernel<<<dim3(kap, items), 256, 0, st>>>(X, n, kap, Xq, fexp, mask);
+    } else {
+      const size_t cnt = size_t(items) * n * kap;
+      split_x_kernel<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(X, Xdf, cnt, mask, size_t(n) * kap);
+    }
+  };
+  if (c.opts.residual == 2) {   // row exponents of M for the split-integer residual
+    ProfScope ps(PH_RESIDUAL, st);
+    row_exp_kernel<<<dim3((n + 127) / 128, items), 128, 0, st>>>(reinterpret_cast<const float4*>(c.M64), stride, ld,
+                                                                 n, rexp);
+    prof_launched(PH_RESIDUAL, 1);
+  }
   if (seeded) {
     // X = X^ from the predicted tau_00, R = E0 - M X^ for seeded items, gate
     ProfScope ps(PH_OTHER, st);
-    seed_x_kernel<<<dim3((n + 127) / 128, items), 128, 0, st>>>(c.M64, c.opts.residual == 1, stride, ld, n, kap,
+    seed_x_kernel<<<dim3((n + 127) / 128, items), 128, 0, st>>>(c.M64, c.opts.residual >= 1, stride, ld, n, kap,
                                                                 c.seed, c.seed_mask, c.out_index, X, skip);
-    if (c.opts.residual == 1) {
-      const size_t cnt = size_t(items) * n * kap;
-      split_x_kernel<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(X, Xdf, cnt, skip, size_t(n) * kap);
+    if (c.opts.residual >= 1) {
+      launch_split_x(skip);
       launch_residual_df(skip, nullptr, PH_OTHER);
       prof_launched(PH_OTHER, 1);
     } else {
@@ -1162,9 +1366,8 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     const bool first = (it == 0);
     if (!first) {
       ProfScope ps(PH_RESIDUAL, st);
-      if (c.opts.residual == 1) {
-        const size_t cnt = size_t(items) * n * kap;
-        split_x_kernel<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(X, Xdf, cnt, conv, size_t(n) * kap);
+      if (c.opts.residual >= 1) {
+        launch_split_x(conv);
         launch_residual_df(conv, prof_work_counter(PH_RESIDUAL), PH_RESIDUAL);
       } else {
         residual64_kernel<<<gres, tres, smem_res, st>>>(c.M64, stride, ld, n, kap, X, R, conv,

@@ -56,7 +56,7 @@ Layout make_layout(const must_liz* z, int nE, int nspin, int n_species, int prec
 int check_opts(const must_solve_opts* o) {
   if (o->precision < MUST_FP64 || o->precision > MUST_MIXED_TF32X3) return 0;
   if (o->precision != MUST_FP64 && (o->max_iter < 0 || !(o->tol > 0.0))) return 0;
-  if (o->residual < 0 || o->residual > 1) return 0;
+  if (o->residual < 0 || o->residual > 2) return 0;
   return 1;
 }
 
@@ -121,7 +121,7 @@ static must_status run_chunk(AsmChunk c, int items, const ChunkIndex& ci, const 
     schur_inv64(M64, stride, ld, n, kap, items, c.scale, tau_dev, out_index, st_item, status_dev, st);
   } else {
     c.scale64 = 0;
-    c.m64_df = o.residual == 1 ? 1 : 0;
+    c.m64_df = o.residual >= 1 ? 1 : 0;
     MixedChunk mc;
     mc.asmc = c; mc.n = n; mc.ld = ld; mc.kap = kap; mc.items = items; mc.M64 = M64; mc.stride = stride;
     mc.piv = piv; mc.status = st_item; mc.out_index = out_index; mc.tau = tau_dev; mc.status_out = status_dev;
