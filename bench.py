@@ -629,6 +629,55 @@ def run_paper_shapes(args):
                       "results": res}))
 
 
+def run_site_charge(args):
+    """The step after the path: the charge inside the centre's sphere, the
+    contour integral (Eq. 2) of the site Green's function (Eq. 3), from the
+    tau_00 of the 135-site workload on the unclamped 32-node semicircle.
+    Reports N per spin, the solve throughput and the charge kernel's time."""
+    import torch
+    from paper_2308_16317_gb300 import binding as B
+    from paper_2308_16317_gb300 import build as libbuild
+    from paper_2308_16317_gb300 import workload as wl
+    from paper_2308_16317_gb300.runner import Session
+    libbuild.build()
+    B.load()
+    w = wl.liz135(n_e=args.n_energies, im_min=None)
+    s = Session(w)
+    nE = len(w.energies)
+    E, wt = B.must_contour_weights(nE)
+    dev = torch.device("cuda")
+    Ed = torch.tensor(E, device=dev)
+    wd = torch.tensor(wt, device=dev)
+    V = torch.tensor([w.site_depths(w.lizs[0], sp)[0] for sp in range(s.nspin)], dtype=torch.float64, device=dev)
+    n_of_E = torch.zeros((s.nspin, nE), dtype=torch.float64, device=dev)
+    N = torch.zeros(s.nspin, dtype=torch.float64, device=dev)
+    opts = B.must_default_opts(PREC[args.precision], residual=RES[args.residual])
+    out = s.alloc_out(1)
+    for _ in range(args.warmup):
+        s.solve(opts, out=out)
+        B.must_site_charge(w.lmax, Ed, wd, V, w.r_mt, out[0][0], n_of_E, N)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    t_solve = t_charge = 0.0
+    for _ in range(args.steps):
+        e0.record()
+        s.solve(opts, out=out)
+        e1.record()
+        B.must_site_charge(w.lmax, Ed, wd, V, w.r_mt, out[0][0], n_of_E, N)
+        e2.record()
+        torch.cuda.synchronize()
+        t_solve += e0.elapsed_time(e1)
+        t_charge += e1.elapsed_time(e2)
+    items = nE * s.nspin
+    print(json.dumps({"metric": "site charge inside the centre sphere from tau_00 (contour integral of Eq. 2-3)",
+                      "N_per_spin": [float(x) for x in N.cpu().numpy()],
+                      "n_of_E_per_spin": n_of_E.cpu().numpy().tolist(),
+                      "solves_per_s": items * args.steps / (t_solve / 1e3),
+                      "charge_kernel_ms": t_charge / args.steps, "solve_ms": t_solve / args.steps,
+                      "precision": args.precision, "residual": args.residual,
+                      "status_ok": bool((out[1].cpu().numpy() == 0).all())}))
+
+
 def run_cusolver_context(args):
     """Context only: the paper's own method (LU + solve in complex128, Sec. 3.2)
     through PyTorch's vendor-library path on this GPU, at the benchmark's
@@ -721,7 +770,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0)
     ap.add_argument("--workload", default="liz135",
-                    choices=["liz135", "supercell", "warmstart", "cusolver", "canted", "paper"],
+                    choices=["liz135", "supercell", "warmstart", "cusolver", "canted", "paper", "charge"],
                     help="liz135: the benchmark workload; supercell: per-site LIZs of the 256-site supercell "
                          "with vacancies (uneven n), batched and replayed as a captured plan")
     ap.add_argument("--n-lizs", type=int, default=32, help="supercell / warmstart mode: evaluation LIZs")
@@ -744,6 +793,8 @@ def main():
         run_canted(args)
     elif args.workload == "paper":
         run_paper_shapes(args)
+    elif args.workload == "charge":
+        run_site_charge(args)
     else:
         run_ours(args)
 

@@ -174,6 +174,34 @@ must_status must_plan_launch(const must_plan* plan, void* stream);
 void must_plan_free(must_plan* plan);
 
 /*
+ * Energy-contour integration of the site charge (the step after the path:
+ * the charge of Eq. 2 from the site Green's function of Eq. 3).  Collinear
+ * LIZs only.
+ *
+ * must_contour_weights: host arrays.  E [n_e] complex (re, im pairs): the
+ * Gauss-Legendre nodes in the angle of the upper semicircle from e_bot to e_f
+ * (theta = pi/2 (1 - x_k), from e_bot to e_f); w [n_e] complex: the weights of
+ * int_{e_bot}^{e_f} f(E) dE along it, w_k = -(pi/2) W_k i r e^{i theta_k}.
+ *
+ * must_site_charge: for each of n_out output blocks s (the spins of one LIZ,
+ * tau00 laid out as must_tau00_solve returns it, [n_out][nE][kap][kap]
+ * column-major complex, kap = (lmax+1)^2), with the centre site a square
+ * well of depth V[s] and radius r_mt:
+ *   g_k    = int_sphere G(r, r; E_k) d^3r = sum_L tau_LL(E_k) F_l(E_k)
+ *            - sum_l (2l+1) I_l(E_k),
+ *   F_l = int_0^a Z_l^2 r^2 dr, I_l = int_0^a Z_l J_l r^2 dr, Z_l regular
+ *   (j_l/t_l - i kappa h_l outside), J_l irregular (j_l outside);
+ *   n_of_E[s][k] = -(1/pi) Im g_k (may be NULL); N[s] = -(1/pi) Im sum_k w_k g_k.
+ * The sign is that of the retarded G of this library (g0 = -e^{i kappa d} /
+ * (4 pi d)).  Every array must be device memory (MUST_EINVAL otherwise);
+ * asynchronous on `stream`.
+ */
+must_status must_contour_weights(int32_t n_e, double e_bot, double e_f, double* E, double* w);
+must_status must_site_charge(int32_t lmax, int32_t nE, const double* E, const double* w, int32_t n_out,
+                             const double* V, double r_mt, const double* tau00, double* n_of_E, double* N,
+                             void* stream);
+
+/*
  * Tuning knobs (set by the project's autotuner, paper_2308_16317_gb300/autotune.py):
  *   knob 0: sites per padding quantum when must_tau00_batch groups LIZs of
  *           uneven size (1..64, default 4);

@@ -76,6 +76,8 @@ def load():
         "must_mlp_apply": (I32, [I32, I32, P, I32, P, P, P, P]),
         "must_mlp_targets": (I32, [I32, I32, P, P, P, P, I32, P]),
         "must_tune_get": (I32, [I32]),
+        "must_contour_weights": (I32, [I32, D, D, P, P]),
+        "must_site_charge": (I32, [I32, I32, P, P, I32, P, D, P, P, P, P]),
         "must_static_scratch_bytes": (SZ, []),
         "must_profile_enable": (None, [ctypes.c_int]),
         "must_profile_read": (ctypes.c_int, [P, P, P, ctypes.c_int]),
@@ -102,7 +104,7 @@ def exported_symbols():
                         "must_mlp_create", "must_mlp_free", "must_mlp_param_count", "must_mlp_get_params",
                         "must_mlp_set_params", "must_mlp_forward", "must_mlp_gradients", "must_mlp_train_step",
                         "must_mlp_save", "must_mlp_load", "must_mlp_features", "must_mlp_apply", "must_mlp_targets",
-                        "must_tau00_solve_seeded")]
+                        "must_tau00_solve_seeded", "must_contour_weights", "must_site_charge")]
 
 
 def _ptr(a):
@@ -355,3 +357,20 @@ def must_tau00_solve_seeded(liz: Liz, E, tinv, n_species: int, nspin: int, opts,
                                           int(ws_bytes), _ptr(tau_seed), _ptr(seed_mask), _ptr(tau00), _ptr(status),
                                           _ptr(seed_used), _stream(stream)))
     return tau00
+
+
+def must_contour_weights(n_e: int, e_bot: float = -0.3, e_f: float = 0.7):
+    """(E, w): complex nodes and weights of int_{e_bot}^{e_f} f dE on the upper semicircle (host)."""
+    E = np.zeros(n_e, np.complex128)
+    w = np.zeros(n_e, np.complex128)
+    _check(load().must_contour_weights(int(n_e), float(e_bot), float(e_f), _ptr(E.view(np.float64)),
+                                       _ptr(w.view(np.float64))))
+    return E, w
+
+
+def must_site_charge(lmax: int, E, w, V, r_mt: float, tau00, n_of_E, N, stream=None):
+    """Site charge of the centre (device tensors): tau00 [n_out][nE][kap][kap] complex128,
+    E, w [nE] complex128, V [n_out] float64, n_of_E [n_out][nE] float64 or None, N [n_out] float64."""
+    n_out, nE = int(tau00.shape[0]), int(tau00.shape[1])
+    _check(load().must_site_charge(int(lmax), nE, _ptr(E), _ptr(w), n_out, _ptr(V), float(r_mt), _ptr(tau00),
+                                   _ptr(n_of_E), _ptr(N), _stream(stream)))

@@ -207,4 +207,69 @@ must_status must_tinv_square_well(int32_t nE, const double* E, int32_t n_pot, co
   return MUST_OK;
 }
 
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_n (three-term recurrence).
+static void gauss_legendre_host(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+must_status must_contour_weights(int32_t n_e, double e_bot, double e_f, double* E, double* w) {
+  if (n_e < 1 || !E || !w || !(e_f > e_bot)) { must_set_error("must_contour_weights: bad argument"); return MUST_EINVAL; }
+  std::vector<double> x, W;
+  gauss_legendre_host(n_e, x, W);
+  const double c = 0.5 * (e_bot + e_f), r = 0.5 * (e_f - e_bot);
+  for (int k = 0; k < n_e; ++k) {
+    const double th = 0.5 * M_PI * (1.0 - x[k]);     // from pi (e_bot) to 0 (e_f)
+    const double ct = std::cos(th), st = std::sin(th);
+    E[2 * k] = c + r * ct;
+    E[2 * k + 1] = r * st;
+    // w = W (dtheta/dx) (dE/dtheta) = W (-pi/2) (i r e^{i theta})
+    const double f = -0.5 * M_PI * W[k] * r;
+    w[2 * k] = -f * st;
+    w[2 * k + 1] = f * ct;
+  }
+  return MUST_OK;
+}
+
+must_status must_site_charge(int32_t lmax, int32_t nE, const double* E, const double* w, int32_t n_out,
+                             const double* V, double r_mt, const double* tau00, double* n_of_E, double* N,
+                             void* stream) {
+  if (nE < 1 || n_out < 1 || !E || !w || !V || !tau00 || !N) {
+    must_set_error("must_site_charge: bad argument");
+    return MUST_EINVAL;
+  }
+  if (lmax < 0 || lmax > MUST_MAX_LMAX || !(r_mt > 0.0)) { must_set_error("must_site_charge: lmax/r_mt"); return MUST_EINVAL; }
+  const void* ptrs[6] = {E, w, V, tau00, N, n_of_E};
+  for (int i = 0; i < 6; ++i)
+    if (ptrs[i] && !must_is_device_ptr(ptrs[i])) {
+      must_set_error("must_site_charge: every array must be device memory");
+      return MUST_EINVAL;
+    }
+  const int kap = (lmax + 1) * (lmax + 1);
+  launch_site_charge(lmax, nE, reinterpret_cast<const double2*>(E), reinterpret_cast<const double2*>(w), n_out, V,
+                     r_mt, reinterpret_cast<const double2*>(tau00), kap, n_of_E, N, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { must_set_error("must_site_charge: %s", cudaGetErrorString(e)); return MUST_ECUDA; }
+  return MUST_OK;
+}
+
 }  // extern "C"

@@ -171,6 +171,104 @@ __global__ void tinv_kernel(int nE, const double2* __restrict__ E, int n_pot, co
 }
 
 // ------------------------------------------------------------------------
+// Site charge inside the sphere (Eq. 2-3) for the square-well single-site
+// problem.  Per energy: int_sphere G(r,r;E) d^3r = sum_L tau_LL F_l - sum_l
+// (2l+1) I_l with F_l = int_0^a Z_l^2 r^2 dr, I_l = int_0^a Z_l J_l r^2 dr;
+// Z_l = c_l j_l(q r) inside, matched in value to j_l(kappa a)/t_l - i kappa
+// h_l(kappa a); J_l = alpha j_l(q r) + beta y_l(q r), matched in value and
+// slope to j_l(kappa r).  Radial integrals by the Lommel identity.
+namespace {
+
+// j_l, y_l for l = -1 .. lmax + 1 at z (index l + 1)
+__device__ void bessel_jy_ext(int lmax, cd z, cd* j, cd* y) {
+  cd jj[MUST_MAX_LMAX + 3], hh[MUST_MAX_LMAX + 3];
+  bessel_j(lmax + 1, z, jj);
+  hankel_up(lmax + 1, z, hh);
+  const cd iz = cinv(z);
+  const cd e = cexpi(z), emi = cinv(e);
+  j[0] = (0.5 * (e + emi)) * iz;                     // j_{-1} = cos z / z
+  y[0] = (mk(0.0, -0.5) * (e - emi)) * iz;           // y_{-1} = sin z / z
+  for (int l = 0; l <= lmax + 1; ++l) {
+    j[l + 1] = jj[l];
+    y[l + 1] = mk(0.0, -1.0) * (hh[l] - jj[l]);      // y = (h - j) / i
+  }
+}
+
+// (x^3/2)[u_l v_l - (u_{l-1} v_{l+1} + u_{l+1} v_{l-1})/2], u, v indexed l + 1
+__device__ __forceinline__ cd lommel(int l, cd x, const cd* u, const cd* v) {
+  const int k = l + 1;
+  return (0.5 * (x * x * x)) * (u[k] * v[k] - 0.5 * (u[k - 1] * v[k + 1] + u[k + 1] * v[k - 1]));
+}
+
+__device__ cd site_integrand(int lmax, cd E, double V, double a, const double2* tau, int kap) {
+  const cd kp = csqrt_p(E), q = csqrt_p(E - mk(V, 0.0));
+  const cd ka = a * kp, qa = a * q;
+  cd jk[MUST_MAX_LMAX + 3], yk[MUST_MAX_LMAX + 3], jq[MUST_MAX_LMAX + 3], yq[MUST_MAX_LMAX + 3];
+  bessel_jy_ext(lmax, ka, jk, yk);
+  bessel_jy_ext(lmax, qa, jq, yq);
+  const cd ika = cinv(ka), iqa = cinv(qa), iq3 = cinv(q * q * q);
+  cd g = mk(0.0, 0.0);
+  for (int l = 0; l <= lmax; ++l) {
+    const int k = l + 1;
+    const cd hk = jk[k] + mk(0.0, 1.0) * yk[k];
+    const cd hkm = jk[k - 1] + mk(0.0, 1.0) * yk[k - 1];
+    const cd djk = jk[k - 1] - (l + 1.0) * (ika * jk[k]);
+    const cd dhk = hkm - (l + 1.0) * (ika * hk);
+    const cd djq = jq[k - 1] - (l + 1.0) * (iqa * jq[k]);
+    const cd dyq = yq[k - 1] - (l + 1.0) * (iqa * yq[k]);
+    // t_l of the well (log-derivative matching), as in tinv_kernel but inverted
+    const cd num = mk(0.0, 1.0) * kp * (kp * dhk * jq[k] - q * djq * hk);
+    const cd den = kp * djk * jq[k] - q * djq * jk[k];
+    const cd tinv = cdiv(num, den);
+    const cd c = cdiv(jk[k] * tinv - mk(0.0, 1.0) * kp * hk, jq[k]);
+    const cd det = q * (jq[k] * dyq - yq[k] * djq);
+    const cd alpha = cdiv(q * (jk[k] * dyq) - kp * (djk * yq[k]), det);
+    const cd beta = cdiv(kp * (djk * jq[k]) - q * (jk[k] * djq), det);
+    const cd ljj = iq3 * lommel(l, qa, jq, jq);
+    const cd ljy = iq3 * (lommel(l, qa, jq, yq) - mk((2.0 * l + 1.0) / 4.0, 0.0));
+    const cd F = c * c * ljj;
+    const cd I = c * (alpha * ljj + beta * ljy);
+    cd dsum = mk(0.0, 0.0);
+    for (int m = -l; m <= l; ++m) {
+      const int L = l * l + l + m;
+      const double2 tv = tau[size_t(L) * kap + L];
+      dsum = dsum + mk(tv.x, tv.y);
+    }
+    g = g + dsum * F - (2.0 * l + 1.0) * I;
+  }
+  return g;
+}
+
+}  // namespace
+
+__global__ void site_charge_kernel(int lmax, int nE, const double2* __restrict__ E, const double2* __restrict__ w,
+                                   const double* __restrict__ V, double a, const double2* __restrict__ tau, int kap,
+                                   double* __restrict__ nE_out, double* __restrict__ N_out) {
+  __shared__ double red[32];
+  const int s = blockIdx.x;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nE; k += blockDim.x) {
+    const cd g = site_integrand(lmax, mk(E[k].x, E[k].y), V[s], a, tau + (size_t(s) * nE + k) * kap * kap, kap);
+    if (nE_out) nE_out[size_t(s) * nE + k] = -g.y / 3.14159265358979323846;
+    acc += (mk(w[k].x, w[k].y) * g).y;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) t += red[i];
+    N_out[s] = -t / 3.14159265358979323846;
+  }
+}
+
+void launch_site_charge(int lmax, int nE, const double2* E, const double2* w, int n_out, const double* V, double a,
+                        const double2* tau, int kap, double* nE_out, double* N_out, cudaStream_t st) {
+  site_charge_kernel<<<n_out, 128, 0, st>>>(lmax, nE, E, w, V, a, tau, kap, nE_out, N_out);
+  prof_launched(PH_OTHER, 1);
+}
+
+// ------------------------------------------------------------------------
 struct LizDev {
   int N, n_pairs, pad;
   const int* species;     // [N] permuted

@@ -48,3 +48,6 @@ struct ChunkIndex {
   int liz_global[MUST_CHUNK_LIZ];
 };
 void launch_chunk_index(int* out_index, int* status, int items, const ChunkIndex& ci, cudaStream_t st);
+
+void launch_site_charge(int lmax, int nE, const double2* E, const double2* w, int n_out, const double* V, double a,
+                        const double2* tau, int kap, double* nE_out, double* N_out, cudaStream_t st);
