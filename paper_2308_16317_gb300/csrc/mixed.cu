@@ -623,19 +623,27 @@ struct __align__(16) XQ {
   float sr, si, xr, xi;  // sigma and X~ (FP32)
 };
 
-__global__ void row_exp_kernel(const float4* __restrict__ M0, size_t stride, int ld, int n, int* __restrict__ ex0) {
+__global__ void __launch_bounds__(256) row_exp_kernel(const float4* __restrict__ M0, size_t stride, int ld, int n,
+                                                      int* __restrict__ ex0) {
+  // 32 rows per CTA (threadIdx.x), the columns split over 8 groups (threadIdx.y)
+  __shared__ float red[8][33];
   const int item = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float4* M = M0 + size_t(item) * stride + i;
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int ic = min(i, n - 1);
+  const float4* M = M0 + size_t(item) * stride + ic;
   float mx = 0.f;
-#pragma unroll 8
-  for (int k = 0; k < n; ++k) {
+#pragma unroll 4
+  for (int k = threadIdx.y; k < n; k += 8) {
     const float4 v = M[size_t(k) * ld];
-    if (k != i) mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    if (k != ic) mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
   }
-  const int e = (mx > 0.f && mx <= 3.0e38f) ? ilogbf(mx) + 2 : 0;
-  ex0[size_t(item) * n + i] = min(max(e, -90), 120);
+  red[threadIdx.y][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0 && i < n) {
+    for (int g = 1; g < 8; ++g) mx = fmaxf(mx, red[g][threadIdx.x]);
+    const int e = (mx > 0.f && mx <= 3.0e38f) ? ilogbf(mx) + 2 : 0;
+    ex0[size_t(item) * n + i] = min(max(e, -90), 120);
+  }
 }
 
 // One block per (column c, item): f_c, then X~ = X 2^(23 - f_c) split into
@@ -1342,7 +1350,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   };
   if (c.opts.residual == 2) {   // row exponents of M for the split-integer residual
     ProfScope ps(PH_RESIDUAL, st);
-    row_exp_kernel<<<dim3((n + 127) / 128, items), 128, 0, st>>>(reinterpret_cast<const float4*>(c.M64), stride, ld,
+    row_exp_kernel<<<dim3((n + 31) / 32, items), dim3(32, 8), 0, st>>>(reinterpret_cast<const float4*>(c.M64), stride, ld,
                                                                  n, rexp);
     prof_launched(PH_RESIDUAL, 1);
   }
