@@ -342,8 +342,9 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"bf16x3": "bf16x3+f32, f64 refinement", "tf32x3": "tf32x3+f32, f64 refinement",
-                                           "fp64": "f64"}[prec],
+            "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "%s+f32 factors, %s residual, f64 solution" % (
+                prec, {"fp64": "f64", "df": "double-float", "int": "split-integer"}[args.residual]),
             "data": "synthetic (seeded fcc 50/50 random alloy, square-well t-matrices)",
             "config": {"workload": "fcc135 LIZ, lmax=3, n=2160, 32 contour energies x 2 spins = 64 tau_00 solves/step",
                        "n": n, "n_liz": int(w.lizs[0].n_sites), "lmax": w.lmax, "solves_per_step": items,
