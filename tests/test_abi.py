@@ -56,3 +56,18 @@ def test_host_side_argument_errors_need_no_gpu(lib):
                                 None, None, ctypes.byref(out))
     assert r == 1 and b"lmax" in B.load().must_last_error()
     assert B.load().must_tau00_solve(None, 1, None, None, 1, 1, None, None, 0, None, None, None) == 1
+
+
+def test_bench_traffic_profile_matches_current_kernel_source():
+    """profiles/tc_update_kernel_fcc135.txt carries the sha256 of the kernel
+    source it was captured from; bench.py reports roofline.traffic only while
+    it matches (a stale capture reads as null)."""
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    t = bench.traffic_from_profiles("tc_update_kernel_fcc135", "paper_2308_16317_gb300/csrc/tc_gemm.cu")
+    assert t is not None and 5e8 < t < 1e9
+    assert bench.traffic_from_profiles("tc_update_kernel_fcc135", "paper_2308_16317_gb300/csrc/mixed.cu") is None
