@@ -255,7 +255,7 @@ size_t must_static_scratch_bytes(void);
  * tau_00 at the neighbouring contour energies E_{k-1}, E_{k+1}, the three
  * energies, the spin and the LIZ's species occupancy; the prediction can seed
  * the refinement of must_tau00_solve_seeded, whose plain solve is the
- * fallback and the judge of its error.
+ * fallback and the reference its error is measured against.
  *   must_mlp_create   n_in inputs, hidden width, n_out outputs, largest batch,
  *                     seed of the initial weights (device allocation).
  *   must_mlp_forward  y[batch][n_out] = net(x[batch][n_in]) (device FP32).
@@ -305,7 +305,7 @@ must_status must_mlp_targets(int32_t n, int32_t kap, const double* tau, const fl
  * The seed is accepted only if ||E0 - M X||_F <= 1e-3 ||E0||_F; otherwise (and
  * for unmasked items) the plain low-precision solve starts the refinement,
  * which then runs to the same tolerance either way, so the plain solve is the
- * fallback and the judge of the seed.  seed_used (optional) receives 1 where
+ * fallback and what the seed is checked against.  seed_used (optional) receives 1 where
  * the seed was accepted.  tau_seed, seed_mask, seed_used and tau00 must be
  * device memory.  Errors: as must_tau00_solve; MUST_EINVAL for MUST_FP64.
  */
