@@ -705,8 +705,6 @@ size_t tc_pack_bytes_per_item(int n) {
   return 4 * a256(size_t(rows_pad) * kp * 4);
 }
 
-static bool tc_supported = true;
-
 int tc_tile_n() { return g_tile_n; }
 
 namespace {

@@ -71,3 +71,32 @@ def test_bench_traffic_profile_matches_current_kernel_source():
     t = bench.traffic_from_profiles("tc_update_kernel_fcc135", "paper_2308_16317_gb300/csrc/tc_gemm.cu")
     assert t is not None and 5e8 < t < 1e9
     assert bench.traffic_from_profiles("tc_update_kernel_fcc135", "paper_2308_16317_gb300/csrc/mixed.cu") is None
+
+
+def test_contour_weights_are_computed_on_the_host():
+    """must_contour_weights needs no GPU: the library's Gauss-Legendre nodes
+    (its own Newton iteration) agree with numpy's, and the weights integrate
+    polynomials along the semicircle."""
+    import numpy as np
+    from paper_2308_16317_gb300 import binding as B
+    for n in (1, 5, 32):
+        E, w = B.must_contour_weights(n)
+        x, W = np.polynomial.legendre.leggauss(n)
+        th = 0.5 * np.pi * (1.0 - x)
+        assert np.abs(E - (0.2 + 0.5 * np.exp(1j * th))).max() <= 1e-14
+    E, w = B.must_contour_weights(24)
+    for m in range(4):
+        assert abs(np.sum(w * E ** m) - (0.7 ** (m + 1) - (-0.3) ** (m + 1)) / (m + 1)) <= 1e-13
+    with pytest.raises(B.MustError):
+        B.must_contour_weights(8, 0.7, -0.3)
+
+
+def test_site_charge_rejects_host_arrays():
+    import numpy as np
+    from paper_2308_16317_gb300 import binding as B
+    E, w = B.must_contour_weights(4)
+    tau = np.zeros((1, 4, 16, 16), np.complex128)
+    V = np.array([-1.0])
+    N = np.zeros(1)
+    with pytest.raises(B.MustError):
+        B.must_site_charge(3, E, w, V, 2.5, tau, None, N)
