@@ -31,6 +31,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "τ_00 solves/sec at N_LIZ=135,l_max=3 (n=2160) vs plain FP64; % tensor peak"
+
+TUNE = {}   # knob -> value set through --tune (library defaults otherwise)
+
+
+def emit(line):
+    """Print one JSON result line; non-default library knobs are recorded in it."""
+    if TUNE and isinstance(line, dict):
+        line = dict(line, tune={str(k): v for k, v in TUNE.items()})
+    print(json.dumps(line))
+
 UNIT = "solves/s"
 PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
 RES = {"fp64": 0, "df": 1, "int": 2}
@@ -354,7 +364,7 @@ def run_ours(args):
             "clocks": clocks, "plain_fp64": fp64, "max_rel_err_vs_fp64": max_err,
             "status_ok": bool((status == 0).all() and (st0 == 0).all()), "phases": phases,
         }
-        print(json.dumps(line))
+        emit(line)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -427,7 +437,7 @@ def run_supercell(args):
             "gpu_launches": int(launches), "clocks": clocks, "plain_fp64_batched": fp64,
             "max_rel_err_vs_fp64": err, "status_ok": bool((st.cpu().numpy() == 0).all())}
     if rank == 0:
-        print(json.dumps(line))
+        emit(line)
 
 
 def run_warmstart(args):
@@ -529,7 +539,7 @@ def run_warmstart(args):
                      "solves_per_s_cold": n_solves / (t_cold / 1e3),
                      "solves_per_s_seeded_schedule": n_solves / (t_seed / 1e3)},
             "precision": args.precision, "residual": args.residual}
-    print(json.dumps(line))
+    emit(line)
 
 
 def run_canted(args):
@@ -571,13 +581,13 @@ def run_canted(args):
     t64 = blocks_to_numpy(out64[0][0])
     err = np.linalg.norm(tau - t64, axis=(-2, -1)) / np.linalg.norm(t64, axis=(-2, -1))
     nE = len(w.energies)
-    print(json.dumps({"metric": "tau_00 solves/sec, spin-canted 135-site LIZ (order 2n = 4320)",
+    emit({"metric": "tau_00 solves/sec, spin-canted 135-site LIZ (order 2n = 4320)",
                       "value": nE / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
                       "precision": args.precision, "residual": args.residual,
                       "plain_fp64": {"value": nE / (ms64 / 1e3), "ms_per_step": ms64},
                       "status_ok": bool((st == 0).all()),
                       "per_energy_rel_err_vs_fp64": [float(x) for x in err.ravel()],
-                      "im_E": [float(e.imag) for e in w.energies]}))
+                      "im_E": [float(e.imag) for e in w.energies]})
 
 
 def run_paper_shapes(args):
@@ -628,9 +638,9 @@ def run_paper_shapes(args):
                      "max_rel_err_vs_fp64": float(err.max()), "status_ok": ok}
         del s, out, out64
         torch.cuda.empty_cache()
-    print(json.dumps({"metric": "tau_00 solves/sec at the paper's ranks (lmax = 4)", "unit": UNIT,
+    emit({"metric": "tau_00 solves/sec at the paper's ranks (lmax = 4)", "unit": UNIT,
                       "precision": args.precision, "residual": args.residual, "steps": args.steps,
-                      "results": res}))
+                      "results": res})
 
 
 def run_site_charge(args):
@@ -673,13 +683,13 @@ def run_site_charge(args):
         t_solve += e0.elapsed_time(e1)
         t_charge += e1.elapsed_time(e2)
     items = nE * s.nspin
-    print(json.dumps({"metric": "site charge inside the centre sphere from tau_00 (contour integral of Eq. 2-3)",
+    emit({"metric": "site charge inside the centre sphere from tau_00 (contour integral of Eq. 2-3)",
                       "N_per_spin": [float(x) for x in N.cpu().numpy()],
                       "n_of_E_per_spin": n_of_E.cpu().numpy().tolist(),
                       "solves_per_s": items * args.steps / (t_solve / 1e3),
                       "charge_kernel_ms": t_charge / args.steps, "solve_ms": t_solve / args.steps,
                       "precision": args.precision, "residual": args.residual,
-                      "status_ok": bool((out[1].cpu().numpy() == 0).all())}))
+                      "status_ok": bool((out[1].cpu().numpy() == 0).all())})
 
 
 def run_cusolver_context(args):
@@ -708,9 +718,9 @@ def run_cusolver_context(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"metric": "context: vendor complex128 LU + solve (torch.linalg.solve), n=2160, 16 RHS",
+    emit({"metric": "context: vendor complex128 LU + solve (torch.linalg.solve), n=2160, 16 RHS",
                       "value": batch / (ms / 1e3), "unit": UNIT, "ms_per_batch": ms, "batch": batch,
-                      "tflops_8_3_n3": batch * 8 / 3 * n ** 3 / (ms / 1e3) / 1e12}))
+                      "tflops_8_3_n3": batch * 8 / 3 * n ** 3 / (ms / 1e3) / 1e12})
 
 
 def cpu_baseline(w, sample: int):
@@ -758,7 +768,7 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d steps x %d solves of the n=2160 LIZ" % (args.steps, cores)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    emit(line)
 
 
 def main():
@@ -780,12 +790,21 @@ def main():
     ap.add_argument("--n-lizs", type=int, default=32, help="supercell / warmstart mode: evaluation LIZs")
     ap.add_argument("--chunk-lizs", type=int, default=2,
                     help="supercell: workspace for this many LIZs per launch (more LIZs share launches; "
-                         "2 measured 5% faster than 1, 4 no faster than 2)")
+                         "2 measured 5%% faster than 1, 4 no faster than 2)")
     ap.add_argument("--train-lizs", type=int, default=400,
                     help="warmstart mode: random 135-site training LIZs (x 2 spins x 15 predicted points)")
+    ap.add_argument("--tune", action="append", default=[], metavar="KNOB=VALUE",
+                    help="set a library knob (must_tune_set) before the run; recorded in the JSON line")
     ap.add_argument("--n-energies", type=int, default=32,
                     help="contour energies per step (32 = the benchmark workload; fewer for ncu captures)")
     args = ap.parse_args()
+    if args.tune and args.impl != "reference":
+        from paper_2308_16317_gb300 import binding as B
+        B.load()
+        for kv in args.tune:
+            k, v = (int(x) for x in kv.split("="))
+            B.must_tune_set(k, v)   # raises if the library rejects it
+            TUNE[k] = v
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -59,8 +59,7 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
   extern __shared__ cf Lf[];           // leaf, column-major [lw][mrows]
   __shared__ float sv[PPT / 32];
   __shared__ int si[PPT / 32];
-  __shared__ int s_p;
-  __shared__ cf Ub[LEAF][PANEL_W];     // leaf rows of the remaining panel columns
+  __shared__ cf Ub[LEAF][PANEL_W + 4]; // leaf rows of the remaining panel columns (+ padding)
   __shared__ cf Ll[LEAF][LEAF];        // leaf's unit-lower top block
   __shared__ int s_nr;                 // rows touched by the leaf's interchanges
   __shared__ int s_rows[2 * LEAF];     // ... their indices
@@ -78,15 +77,22 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
     const int le = c0 + lw;             // leaf columns [c0, le)
     const int mrows = n - c0;           // leaf rows [c0, n)
     const int pr = r - c0;              // pivot-eligible local rows [j, pr)
-    // (a) leaf into shared memory
-    for (int q = 0; q < lw; ++q)
-      for (int ii = tid; ii < mrows; ii += PPT) Lf[q * mrows + ii] = A[size_t(c0 + q) * ld + c0 + ii];
+    // (a) leaf into shared memory (later leaves were left there by step (c)
+    // of the leaf before)
+    if (lb == 0) {
+      for (int q = 0; q < lw; ++q)
+        for (int ii = tid; ii < mrows; ii += PPT) Lf[q * mrows + ii] = A[size_t(c0 + q) * ld + c0 + ii];
+    }
     __syncthreads();
+    // Two barriers per column: the candidates of column j (found while
+    // column j-1 was applied) are reduced and the pivot rows swapped by warp
+    // 0; then every thread scales its rows of column j, applies them to the
+    // leaf's later columns and already scans column j+1 for its pivot.
+    float best = -1.0f;
+    int bi = 0;
+    for (int ii = tid; ii < pr; ii += PPT) argmax_merge(best, bi, cnormf(Lf[ii]), ii);
     for (int j = 0; j < lw; ++j) {
       cf* colj = Lf + j * mrows;
-      float best = -1.0f;
-      int bi = j;
-      for (int ii = j + tid; ii < pr; ii += PPT) argmax_merge(best, bi, cnormf(colj[ii]), ii);
       for (int o = 16; o > 0; o >>= 1) {
         const float v2 = __shfl_down_sync(0xffffffffu, best, o);
         const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
@@ -100,35 +106,39 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
         float b = (lane < PPT / 32) ? sv[lane] : -1.0f;
         int p = (lane < PPT / 32) ? si[lane] : j;
         for (int o = 16; o > 0; o >>= 1) {
-          const float v2 = __shfl_down_sync(0xffffffffu, b, o);
-          const int i2 = __shfl_down_sync(0xffffffffu, p, o);
+          const float v2 = __shfl_xor_sync(0xffffffffu, b, o);
+          const int i2 = __shfl_xor_sync(0xffffffffu, p, o);
           argmax_merge(b, p, v2, i2);
         }
         if (lane == 0) {
           if (!(b > 0.0f)) status[item] = ST_SINGULAR;
           piv[c0 + j] = c0 + p;
-          s_p = p;
+        }
+        if (p != j && lane < lw) {
+          const cf t = Lf[lane * mrows + j];
+          Lf[lane * mrows + j] = Lf[lane * mrows + p];
+          Lf[lane * mrows + p] = t;
         }
       }
       __syncthreads();
-      const int p = s_p;
-      if (p != j && tid < lw) {
-        const cf t = Lf[tid * mrows + j];
-        Lf[tid * mrows + j] = Lf[tid * mrows + p];
-        Lf[tid * mrows + p] = t;
-      }
-      __syncthreads();
       const cf d = colj[j];
+      best = -1.0f;
+      bi = j + 1;
+      const bool scan = j + 1 < lw;
+      cf* coln = colj + mrows;
       if (cnormf(d) > 0.0f) {
         const cf inv = cinvf(d);
         for (int ii = j + 1 + tid; ii < mrows; ii += PPT) {
           const cf l = cmulf(colj[ii], inv);
           colj[ii] = l;
           for (int q = j + 1; q < lw; ++q) cfmsf(Lf[q * mrows + ii], l, Lf[q * mrows + j]);
+          if (scan && ii < pr) argmax_merge(best, bi, cnormf(coln[ii]), ii);
         }
+      } else if (scan) {
+        for (int ii = j + 1 + tid; ii < pr; ii += PPT) argmax_merge(best, bi, cnormf(coln[ii]), ii);
       }
-      __syncthreads();
     }
+    __syncthreads();
     for (int q = 0; q < lw; ++q)
       for (int ii = tid; ii < mrows; ii += PPT) A[size_t(c0 + q) * ld + c0 + ii] = Lf[q * mrows + ii];
     // (a') the leaf's interchanges on the other panel columns.  The sequence
@@ -202,41 +212,56 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
     }
     __syncthreads();
     // (c) rows below the leaf: A[i, rest] -= L[i, leaf] U[leaf, rest], two
-    // rows per pass so that twice the loads are in flight
-    for (int i0 = le + tid; i0 < n; i0 += 2 * PPT) {
-      const int i1 = i0 + PPT;
-      const bool has1 = i1 < n;
-      cf l0[LEAF], l1[LEAF];
+    // rows per pass so that twice the loads are in flight, the columns in
+    // groups of 4 (a ragged last group reads Ub past `rest`, into its padding,
+    // and drops those lanes' results).  The next leaf's columns go to the
+    // leaf buffer (free once the leaf is written back) instead of to memory.
+    {
+      const size_t cs = size_t(ld);
+      const int lwn = min(LW, rest), mn = n - le;
+#pragma unroll 1
+      for (int i0 = le + tid; i0 < n; i0 += 2 * PPT) {
+        const bool has1 = i0 + PPT < n;
+        const cf* Lp = A + size_t(c0) * cs + i0;
+        cf l0[LEAF], l1[LEAF];
 #pragma unroll
-      for (int jj = 0; jj < LEAF; ++jj)
-        if (jj < lw) {
-          l0[jj] = A[size_t(c0 + jj) * ld + i0];
-          l1[jj] = has1 ? A[size_t(c0 + jj) * ld + i1] : mkf(0.f, 0.f);
+        for (int jj = 0; jj < LEAF; ++jj) {
+          const bool on = jj < lw;
+          l0[jj] = on ? Lp[jj * cs] : mkf(0.f, 0.f);
+          l1[jj] = (on && has1) ? Lp[jj * cs + PPT] : mkf(0.f, 0.f);
         }
-      for (int q0 = 0; q0 < rest; q0 += 8) {
-        cf v0[8], v1[8];
+        cf* Vp = A + size_t(le) * cs + i0;
+#pragma unroll 1
+        for (int q0 = 0; q0 < rest; q0 += 4, Vp += 4 * cs) {
+          const int nq = min(4, rest - q0);
+          cf v0[4], v1[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (q0 + q < rest) {
-            v0[q] = A[size_t(le + q0 + q) * ld + i0];
-            v1[q] = has1 ? A[size_t(le + q0 + q) * ld + i1] : mkf(0.f, 0.f);
+          for (int q = 0; q < 4; ++q) {
+            v0[q] = (q < nq) ? Vp[q * cs] : mkf(0.f, 0.f);
+            v1[q] = (q < nq && has1) ? Vp[q * cs + PPT] : mkf(0.f, 0.f);
           }
 #pragma unroll
-        for (int jj = 0; jj < LEAF; ++jj)
-          if (jj < lw)
+          for (int jj = 0; jj < LEAF; ++jj)
+            if (jj < lw)
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-              if (q0 + q < rest) {
+              for (int q = 0; q < 4; ++q) {
                 const cf u = Ub[jj][q0 + q];
                 cfmsf(v0[q], l0[jj], u);
                 cfmsf(v1[q], l1[jj], u);
               }
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (q0 + q < rest) {
-            A[size_t(le + q0 + q) * ld + i0] = v0[q];
-            if (has1) A[size_t(le + q0 + q) * ld + i1] = v1[q];
-          }
+          for (int q = 0; q < 4; ++q)
+            if (q < nq) {
+              if (q0 + q < lwn) {
+                cf* Ln = Lf + (q0 + q) * mn + (i0 - le);
+                Ln[0] = v0[q];
+                if (has1) Ln[PPT] = v1[q];
+              } else {
+                Vp[q * cs] = v0[q];
+                if (has1) Vp[q * cs + PPT] = v1[q];
+              }
+            }
+        }
       }
     }
     __syncthreads();
