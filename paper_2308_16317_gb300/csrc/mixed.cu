@@ -714,7 +714,8 @@ __device__ __forceinline__ void ll_split(long long v, float& hi, float& lo) {
   lo = __ll2float_rn(v - __float2ll_rn(hi));
 }
 
-__global__ void __launch_bounds__(1024) residual_int_kernel(const float4* __restrict__ M0, size_t stride, int ld,
+template <int CPT>
+__global__ void __launch_bounds__(256) residual_int_kernel(const float4* __restrict__ M0, size_t stride, int ld,
                                                            int n, int kap, const XQ* __restrict__ Q0,
                                                            const double2* __restrict__ X0,
                                                            const int* __restrict__ rexp0,
@@ -729,17 +730,17 @@ __global__ void __launch_bounds__(1024) residual_int_kernel(const float4* __rest
   const XQ* Q = Q0 + size_t(item) * n * kap;
   const int tid = threadIdx.x;
   const int row = blockIdx.x * 64 + (tid & 63);
-  const int c0 = (tid >> 6) * 4;
+  const int c0 = (tid >> 6) * CPT;
   const int rowc = min(row, n - 1);      // clamped row for loads (results of row >= n are dropped)
   const int nkb = (n + 63) / 64, ks = gridDim.z, z = blockIdx.z;
   const int kb0 = int((long long)nkb * z / ks), kb1 = int((long long)nkb * (z + 1) / ks);
   const int e = rexp0[size_t(item) * n + rowc];
   const float s = __int_as_float((150 - e) << 23);   // 2^(23 - e), exact
   const float MAGIC = 12582912.0f;                   // 1.5 * 2^23: adding it rounds |t| < 2^22 to an integer
-  long long p1[4], p2[4], p3[4];
-  float cr[4], ci[4];
+  long long p1[CPT], p2[CPT], p3[CPT];
+  float cr[CPT], ci[CPT];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < CPT; ++q) {
     p1[q] = p2[q] = p3[q] = 0;
     cr[q] = ci[q] = 0.f;
   }
@@ -764,7 +765,7 @@ __global__ void __launch_bounds__(1024) residual_int_kernel(const float4* __rest
       const float fr = yr - MAGIC, fi = yi - MAGIC;                          // A as floats
       const float rr = fmaf(m.z, s, tr - fr), ri = fmaf(m.w, s, ti - fi);   // rho
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < CPT; ++q)
         if (c0 + q < kap) {
           const XQ x = Qs[k * kap + c0 + q];
           p1[q] += (long long)ar * x.br;
@@ -791,7 +792,7 @@ __global__ void __launch_bounds__(1024) residual_int_kernel(const float4* __rest
   float4* P = P0 + (size_t(z) * gridDim.y + item) * size_t(n) * kap;
   const double2* X = X0 + size_t(item) * n * kap;
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < CPT; ++q)
     if (c0 + q < kap) {
       const int c = c0 + q;
       const float sc = __int_as_float(min(max(81 + e + fexp0[size_t(item) * kap + c], 1), 254) << 23);
@@ -1192,6 +1193,7 @@ static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
 
 // ---------------------------------------------------------------- driver --
 constexpr int RES_SPLIT = 4;   // K splits of the double-float residual
+constexpr int RES_CPT = 8;     // right-hand sides per thread of the split-integer residual
 
 size_t mixed_item_bytes(int n, int ld, int kap) {
   return a256(size_t(ld) * n * 8)          // M32
@@ -1340,7 +1342,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       cudaFuncSetAttribute(correct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(residual64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 16);
       cudaFuncSetAttribute(residual_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 16);
-      cudaFuncSetAttribute(residual_int_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 32);
+      cudaFuncSetAttribute(residual_int_kernel<RES_CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 50 * 32);
       attr = true;
     }
   }
@@ -1354,7 +1356,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   auto launch_residual_df = [&](const int* mask, unsigned long long* work, int phase) {
     const dim3 g(gres.x, items, RES_SPLIT);
     if (c.opts.residual == 2)
-      residual_int_kernel<<<g, tres, size_t(64) * kap * sizeof(XQ), st>>>(
+      residual_int_kernel<RES_CPT><<<g, 64 * ((kap + RES_CPT - 1) / RES_CPT), size_t(64) * kap * sizeof(XQ), st>>>(
           reinterpret_cast<const float4*>(c.M64), stride, ld, n, kap, Xq, X, rexp, fexp, Rpart, mask, work);
     else
       residual_df_kernel<<<g, tres, size_t(64) * kap * 16, st>>>(reinterpret_cast<const float4*>(c.M64), stride, ld,
