@@ -12,6 +12,7 @@
 // the O(n^3) part moves to FP32/BF16 and FP64 is kept for the residual and the
 // solution update (the parts that decide the final accuracy).
 #include <algorithm>
+#include <cuda_bf16.h>
 
 #include "mixed.h"
 #include "tc_gemm.h"
@@ -318,10 +319,23 @@ constexpr int TRSM_COLS = 64;
 constexpr size_t TRSM_SMEM = size_t(64 * 64 + TRSM_COLS * 65) * sizeof(cf);
 
 // One CTA per (64-column tile, item): x = Linv a for every column of the tile.
-// Thread t takes rows i and 63 - i (i = t % 32, so every thread sums 65 terms)
-// of TRSM_COLS / 8 columns.
+// Thread t takes rows i0 = t % 32 and i1 = 63 - i0 of TRSM_COLS / 8 columns.
+// Linv is lower triangular with explicit zeros above its diagonal, so row i0
+// (< 32) takes the terms j < 32 only and row i1 all 64 (zero terms add
+// exactly nothing).  With bhi != nullptr the tile is also written as the
+// tensor-core B operand (BF16 hi/lo pairs; row p of column j at j * Kp + 2p).
+__device__ __forceinline__ unsigned bf16x2_split(float re, float im, unsigned& lo) {
+  const __nv_bfloat16 hr = __float2bfloat16_rn(re), hi_ = __float2bfloat16_rn(im);
+  const __nv_bfloat16 lr = __float2bfloat16_rn(re - __bfloat162float(hr));
+  const __nv_bfloat16 li = __float2bfloat16_rn(im - __bfloat162float(hi_));
+  lo = unsigned(__bfloat16_as_ushort(lr)) | (unsigned(__bfloat16_as_ushort(li)) << 16);
+  return unsigned(__bfloat16_as_ushort(hr)) | (unsigned(__bfloat16_as_ushort(hi_)) << 16);
+}
+
 __global__ void __launch_bounds__(256) trsm_inv_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int k0,
-                                                       int nbe, const float2* __restrict__ Linv0) {
+                                                       int nbe, const float2* __restrict__ Linv0,
+                                                       uint16_t* __restrict__ bhi0, uint16_t* __restrict__ blo0,
+                                                       int Kp, int bitem_rows) {
   extern __shared__ cf tsm[];
   cf (*Li)[64] = reinterpret_cast<cf (*)[64]>(tsm);                // [col j][row i]
   cf (*Xs)[65] = reinterpret_cast<cf (*)[65]>(tsm + 64 * 64);      // [column][row]
@@ -342,9 +356,9 @@ __global__ void __launch_bounds__(256) trsm_inv_kernel(float2* __restrict__ A0, 
   cf y0[CPT], y1[CPT];
 #pragma unroll
   for (int q = 0; q < CPT; ++q) y0[q] = y1[q] = mkf(0.f, 0.f);
-  for (int j = 0; j <= i1; ++j) {
+  for (int j = 0; j < 32; ++j) {
     const cf l1 = Li[j][i1];
-    const cf l0 = (j <= i0) ? Li[j][i0] : mkf(0.f, 0.f);
+    const cf l0 = Li[j][i0];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
       const cf a = Xs[cg * CPT + q][j];
@@ -352,13 +366,27 @@ __global__ void __launch_bounds__(256) trsm_inv_kernel(float2* __restrict__ A0, 
       cfmaf_acc(y0[q], l0, a);
     }
   }
-  __syncthreads();
+  for (int j = 32; j < 64; ++j) {
+    const cf l1 = Li[j][i1];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) cfmaf_acc(y1[q], l1, Xs[cg * CPT + q][j]);
+  }
 #pragma unroll
   for (int q = 0; q < CPT; ++q) {
     const int cc = cg * CPT + q;
     if (cc < ncol) {
       if (i0 < nbe) A[size_t(c_beg + cc) * ld + k0 + i0] = y0[q];
       if (i1 < nbe) A[size_t(c_beg + cc) * ld + k0 + i1] = y1[q];
+      if (bhi0) {
+        const size_t base = size_t(item) * bitem_rows * Kp + size_t(c_beg + cc) * Kp;
+        unsigned lo;
+        unsigned hi = bf16x2_split(y0[q].x, y0[q].y, lo);
+        *reinterpret_cast<unsigned*>(bhi0 + base + 2 * i0) = hi;
+        *reinterpret_cast<unsigned*>(blo0 + base + 2 * i0) = lo;
+        hi = bf16x2_split(y1[q].x, y1[q].y, lo);
+        *reinterpret_cast<unsigned*>(bhi0 + base + 2 * i1) = hi;
+        *reinterpret_cast<unsigned*>(blo0 + base + 2 * i1) = lo;
+      }
     }
   }
 }
@@ -1288,13 +1316,17 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     }
     const int rem = n - k0 - nbe;
     if (rem > 0) {
+      // the BF16 B operand is written by the U12 solve itself
+      PackB pb = {nullptr, nullptr, 0, 0};
+      const bool fuse_b = tc_pack_b_target(c.opts.precision, n, k0, nbe, items, packs, &pb);
       {
         ProfScope ps(PH_TRSM, st);
-        trsm_inv_kernel<<<dim3((rem + TRSM_COLS - 1) / TRSM_COLS, items), 256, TRSM_SMEM, st>>>(M32, stride, ld, n,
-                                                                                           k0, nbe, Linv);
+        trsm_inv_kernel<<<dim3((rem + TRSM_COLS - 1) / TRSM_COLS, items), 256, TRSM_SMEM, st>>>(
+            M32, stride, ld, n, k0, nbe, Linv, fuse_b ? pb.hi : nullptr, fuse_b ? pb.lo : nullptr, pb.Kp,
+            pb.item_rows);
         prof_launched(PH_TRSM, 1, items);
       }
-      if (!tc_pack(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, st)) return MUST_ECUDA;
+      if (!tc_pack(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, st, !fuse_b)) return MUST_ECUDA;
       const int k1 = k0 + nbe;
       if (lookahead && k1 < r && rem > bn) {
         if (!tc_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, 0, bn, st))

@@ -732,14 +732,36 @@ PackGeom pack_geom(int precision, int n, int k0, int nbe, int items, char* packs
 }
 }  // namespace
 
+bool tc_pack_b_target(int precision, int n, int k0, int nbe, int items, char* packs, PackB* out) {
+  const PackGeom g = pack_geom(precision, n, k0, nbe, items, packs);
+  if (g.tf32) return false;
+  out->hi = reinterpret_cast<uint16_t*>(g.pb_hi);
+  out->lo = reinterpret_cast<uint16_t*>(g.pb_lo);
+  out->Kp = g.Kp;
+  out->item_rows = g.item_rows;
+  return true;
+}
+
 bool tc_pack(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
-             cudaStream_t st) {
+             cudaStream_t st, bool with_b) {
   const PackGeom g = pack_geom(precision, n, k0, nbe, items, packs);
   if (g.m <= 0) return true;
   ProfScope ps(PH_PACK, st);
   const int half = g.Kp / 2;
   const int ta = g.m * half;
   dim3 grid((ta + 255) / 256, items);
+  if (!with_b) {
+    if (g.tf32)
+      pack_a_kernel<float><<<grid, 256, 0, st>>>(A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows,
+                                                 reinterpret_cast<float*>(g.pa_hi), reinterpret_cast<float*>(g.pa_lo),
+                                                 1);
+    else
+      pack_a_kernel<uint16_t><<<grid, 256, 0, st>>>(A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows,
+                                                    reinterpret_cast<uint16_t*>(g.pa_hi),
+                                                    reinterpret_cast<uint16_t*>(g.pa_lo), 0);
+    prof_launched(PH_PACK, 1, items);
+    return true;
+  }
   if (g.tf32) {
     pack_a_kernel<float><<<grid, 256, 0, st>>>(A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows,
                                                reinterpret_cast<float*>(g.pa_hi), reinterpret_cast<float*>(g.pa_lo), 1);

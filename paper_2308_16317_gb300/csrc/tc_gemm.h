@@ -10,8 +10,19 @@ size_t tc_pack_bytes_per_item(int n);
 // tc_update over the complex columns [base + col_lo, base + col_hi) of the
 // trailing block (col_hi < 0: to the end); col_lo/col_hi are rounded to the
 // tile width, which tc_tile_n() returns.
+// with_b = false: only the A operand (L21); the caller wrote the B operand
+// itself into the target tc_pack_b_target() describes.
 bool tc_pack(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
-             cudaStream_t st);
+             cudaStream_t st, bool with_b = true);
+// B-operand (U12) pack of panel step k0 in BF16 hi/lo pairs: matrix column j,
+// panel row p -> element j * Kp + 2p (re) and + 1 (im) of item `item_rows *
+// Kp` elements apart; rows p >= nbe are zero.  False for the TF32 splits
+// (those keep the separate pack kernel).
+struct PackB {
+  uint16_t *hi, *lo;
+  int Kp, item_rows;
+};
+bool tc_pack_b_target(int precision, int n, int k0, int nbe, int items, char* packs, PackB* out);
 bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
                int* err, int col_lo, int col_hi, cudaStream_t st);
 int tc_tile_n();
