@@ -318,6 +318,9 @@ constexpr int S_B_BYTES = 2 * S_KSTEPS * SB_BYTES;
 constexpr size_t S_SMEM = size_t(S_STAGES) * S_STAGE_BYTES + S_B_BYTES + size_t(S_CBUF) * C_TILE_BYTES + 1024;
 
 struct TcsParams {
+  float* C;      // C as floats (tmem-C kernel only): item `stride2` floats apart, columns ld2 floats apart
+  size_t stride2;
+  int ld2, n;
   int base;      // first trailing row/column (k0 + nbe)
   int abase;     // base rounded down to even: row origin of the tiles (16-byte TMA rule)
   int rt, ct;    // row tiles, column tiles of this launch
@@ -524,6 +527,180 @@ __global__ void __launch_bounds__(S_THREADS, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * SBN));
 }
 
+// ------------------------------------------ streamed, C through registers --
+// Same runs, operands and resident B block as the streamed kernel, but C never
+// passes through shared memory: the epilogue warps load a tile of C from
+// global memory into registers ahead of time, read the tile's accumulator
+// once its MMAs are done, and store C - A'B' straight to global memory.  The
+// products are still summed from zero in TMEM (adding them onto C there would
+// round each partial sum at the scale of C).  Shared memory then carries only
+// the MMA operands, which leaves room for a deeper A ring (or two CTAs per SM).
+template <int STAGES>
+struct RegcCfg {
+  static constexpr int THREADS = 320;   // producer, MMA, 8 epilogue warps
+  static constexpr size_t SMEM = size_t(STAGES) * S_STAGE_BYTES + S_B_BYTES + 1024;
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(RegcCfg<STAGES>::THREADS, RegcCfg<STAGES>::SMEM * 2 <= 227 * 1024 ? 2 : 1)
+    tc_update_regc(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+                    const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, TcsParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* bres = smem + STAGES * S_STAGE_BYTES;   // [hi k0, hi k1, lo k0, lo k1]
+  __shared__ __align__(8) uint64_t full[STAGES];
+  __shared__ __align__(8) uint64_t empty[STAGES];
+  __shared__ __align__(8) uint64_t bfull;        // resident B landed
+  __shared__ __align__(8) uint64_t aempty[2];    // accumulator read out (8 epilogue warps)
+  __shared__ __align__(8) uint64_t afull[2];     // accumulator ready
+  __shared__ __align__(8) uint64_t mdone;        // every MMA of this CTA retired
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail_raw;
+  volatile int* s_fail = &s_fail_raw;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int rt0, ntile, col0, item;
+  run_coords(P, blockIdx.x, rt0, ntile, col0, item);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&aempty[b], 8);
+      mbar_init(&afull[b], 1);
+    }
+    mbar_init(&bfull, 1);
+    mbar_init(&mdone, 1);
+    s_fail_raw = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(2 * SBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const int kstep_elems = KB / 2;
+
+  if (warp == 0 && lane == 0) {
+    // producer: the resident B block once, then two A stages per tile
+    mbar_expect_tx(&bfull, S_B_BYTES);
+    for (int kb = 0; kb < S_KSTEPS; ++kb) {
+      tma_load_3d(bres + kb * SB_BYTES, &tB_hi, kb * kstep_elems, P.base + col0, item, &bfull);
+      tma_load_3d(bres + (S_KSTEPS + kb) * SB_BYTES, &tB_lo, kb * kstep_elems, P.base + col0, item, &bfull);
+    }
+    int gs = 0;
+    for (int lt = 0; lt < ntile; ++lt) {
+      const int row0 = (rt0 + lt) * BM;
+      bool ok = true;
+      for (int kb = 0; kb < S_KSTEPS; ++kb, ++gs) {
+        const int s = gs % STAGES;
+        if (gs >= STAGES && !mbar_wait_f(&empty[s], ((gs / STAGES) - 1) & 1, s_fail)) { ok = false; break; }
+        uint8_t* sa = smem + s * S_STAGE_BYTES;
+        mbar_expect_tx(&full[s], S_STAGE_BYTES);
+        tma_load_3d(sa, &tA_hi, kb * kstep_elems, 2 * P.abase + row0, item, &full[s]);
+        tma_load_3d(sa + SA_BYTES, &tA_lo, kb * kstep_elems, 2 * P.abase + row0, item, &full[s]);
+      }
+      if (!ok) break;
+    }
+    if (*s_fail) {
+      volatile int dummy = 0;
+      mbar_wait_f(&bfull, 0, &dummy);
+      for (int s = 0; s < STAGES && s < gs; ++s) {
+        const int cnt = (gs - s + STAGES - 1) / STAGES;   // loads armed on full[s]
+        mbar_wait_f(&full[s], (cnt - 1) & 1, &dummy);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: per K step A_hi B_hi + A_hi B_lo + A_lo B_hi into accumulator lt & 1
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(SBN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+    bool ok = mbar_wait_f(&bfull, 0, s_fail);
+    const uint32_t bh = smem_u32(bres), bl = bh + S_KSTEPS * SB_BYTES;
+    int gs = 0;
+    for (int lt = 0; lt < ntile && ok; ++lt) {
+      const int ab = lt & 1;
+      if (lt >= 2 && !mbar_wait_f(&aempty[ab], ((lt >> 1) - 1) & 1, s_fail)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc = tmem + uint32_t(ab * SBN);
+      for (int kb = 0; kb < S_KSTEPS; ++kb, ++gs) {
+        const int s = gs % STAGES;
+        if (!mbar_wait_f(&full[s], (gs / STAGES) & 1, s_fail)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = smem_u32(smem + s * S_STAGE_BYTES), al = ah + SA_BYTES;
+        const uint32_t bhk = bh + kb * SB_BYTES, blk = bl + kb * SB_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < KB / 32; ++kk) {
+          mma_issue(acc, sdesc(ah + 32 * kk), sdesc(bhk + 32 * kk), idesc, (kb > 0 || kk > 0) ? 1u : 0u, 0);
+          mma_issue(acc, sdesc(ah + 32 * kk), sdesc(blk + 32 * kk), idesc, 1u, 0);
+          mma_issue(acc, sdesc(al + 32 * kk), sdesc(bhk + 32 * kk), idesc, 1u, 0);
+        }
+        mma_commit(&empty[s]);
+      }
+      if (ok) mma_commit(&afull[ab]);
+    }
+    mma_commit(&mdone);
+    volatile int dummy = 0;
+    mbar_wait_f(&mdone, 0, &dummy);
+  } else if (warp >= 2) {
+    // epilogue: warp w owns TMEM lane quarter w % 4 (float rows x of the
+    // tile) and column half (w - 2) / 4; the C of tile t + 1 is in registers
+    // (and that of t + 2 on its way) while tile t is finished
+    const int ew = warp - 2, quarter = warp & 3, half = ew >> 2;
+    const int x = quarter * 32 + lane;
+    const int colb = P.base + col0 + half * 32;
+    float* Cg = P.C + size_t(item) * P.stride2;
+    const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+    auto load_tile = [&](int lt, float* c) {
+      const int gr = 2 * P.abase + (rt0 + lt) * BM + x;
+      const bool ok = lt < ntile && gr < 2 * P.n;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        c[j] = (ok && colb + j < P.n) ? __ldcs(Cg + size_t(colb + j) * P.ld2 + gr) : 0.f;
+    };
+    // finish tile lt with its C in c: returns false when a wait gave up
+    auto finish = [&](int lt, const float* c) {
+      const int ab = lt & 1;
+      if (!mbar_wait_f(&afull[ab], (lt >> 1) & 1, s_fail)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t v[32];
+      tmem_ld32(tmem + lane_off + uint32_t(ab * SBN + half * 32), v);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&aempty[ab]);
+      const int gr = 2 * P.abase + (rt0 + lt) * BM + x;
+      if (gr >= 2 * P.base && gr < 2 * P.n) {   // rows above base stay as they are
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (colb + j < P.n) __stcs(Cg + size_t(colb + j) * P.ld2 + gr, c[j] - __uint_as_float(v[j]));
+      }
+      return true;
+    };
+    // two register sets used in turn (no copies between them, so a set's
+    // loads are first needed two tiles after they were issued)
+    float c0[32], c1[32];
+    load_tile(0, c0);
+    load_tile(1, c1);
+    for (int lt = 0; lt < ntile; lt += 2) {
+      if (!finish(lt, c0)) break;
+      load_tile(lt + 2, c0);
+      if (lt + 1 < ntile) {
+        if (!finish(lt + 1, c1)) break;
+        load_tile(lt + 3, c1);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && *s_fail) atomicExch(P.err, 1);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * SBN));
+}
+
 // ---------------------------------------------------------------- packing --
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16_raw& hi, __nv_bfloat16_raw& lo) {
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -639,7 +816,8 @@ bool make_c_map(CUtensorMap* m, float2* C, int ld, size_t stride, int n, int ite
 
 constexpr int TC_STAGES = 3;
 int g_tile_n = 128;   // 128 or 256 complex columns per tile (autotuned)
-int g_streamed = 1;   // 1: streamed kernel (BF16 splits); 0: per-tile kernel
+int g_streamed = 2;   // 1: streamed kernel (BF16 splits, C through shared memory); 2, 3: streamed with C
+                      // through registers (6- / 2-stage A ring); 0: per-tile kernel
 int g_run = 32;       // row tiles per CTA of the streamed kernel
 
 template <int BN>
@@ -667,6 +845,19 @@ void launch_tc_streamed(const CUtensorMap& mah, const CUtensorMap& mal, const CU
   tc_update_streamed<<<grid, S_THREADS, S_SMEM, st>>>(mah, mal, mbh, mbl, mc, P);
 }
 
+template <int STAGES>
+void launch_tc_regc(const CUtensorMap& mah, const CUtensorMap& mal, const CUtensorMap& mbh, const CUtensorMap& mbl,
+                     const TcsParams& P, int items, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_update_regc<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(RegcCfg<STAGES>::SMEM));
+    attr = true;
+  }
+  const int grid = P.rruns * P.ct * items;
+  tc_update_regc<STAGES><<<grid, RegcCfg<STAGES>::THREADS, RegcCfg<STAGES>::SMEM, st>>>(mah, mal, mbh, mbl, P);
+}
+
 int kp_of(bool tf32) {
   // K elements per pass padded to whole 128-byte stages
   const int per = tf32 ? KB / 4 : KB / 2;
@@ -686,7 +877,7 @@ bool tc_set_tile_n(int bn) {
 int tc_get_tile_n() { return g_tile_n; }
 
 bool tc_set_streamed(int on) {
-  if (on != 0 && on != 1) return false;
+  if (on < 0 || on > 3) return false;
   g_streamed = on;
   return true;
 }
@@ -818,17 +1009,41 @@ bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, i
       return false;
     }
     TcsParams S;
+    S.C = reinterpret_cast<float*>(A);
+    S.stride2 = 2 * stride;
+    S.ld2 = 2 * ld;
+    S.n = n;
     S.base = g.base;
     S.abase = abase;
     S.rt = (2 * (n - abase) + BM - 1) / BM;
     S.ct = t1 - t0;
     S.col_tile0 = t0;
-    S.run = std::min(g_run, S.rt);
-    S.rruns = (S.rt + S.run - 1) / S.run;
+    // runs of at most g_run row tiles, evenly split, and enough of them for
+    // two CTAs per SM when few column tiles are updated (the look-ahead's
+    // first-tile launch, the last panel steps)
+    {
+      static int sms = 0;
+      if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+      }
+      const int per_col = items * S.ct;
+      int rruns = (S.rt + g_run - 1) / g_run;
+      rruns = std::max(rruns, (2 * sms + per_col - 1) / per_col);
+      rruns = std::min(rruns, S.rt);
+      S.run = (S.rt + rruns - 1) / rruns;
+      S.rruns = (S.rt + S.run - 1) / S.run;
+    }
     S.err = err;
     S.tf32 = 0;
     ProfScope ps(PH_UPDATE, st);
-    launch_tc_streamed(mah, mal, mbh, mbl, mc, S, items, st);
+    if (g_streamed == 2)
+      launch_tc_regc<6>(mah, mal, mbh, mbl, S, items, st);
+    else if (g_streamed == 3)
+      launch_tc_regc<2>(mah, mal, mbh, mbl, S, items, st);
+    else
+      launch_tc_streamed(mah, mal, mbh, mbl, mc, S, items, st);
     prof_launched(PH_UPDATE, 1, items);
     return true;
   }

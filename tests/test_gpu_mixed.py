@@ -108,12 +108,14 @@ def test_mixed_canted_full_size_sampled(B, orc):
 
 @pytest.mark.parametrize("case", ["odd_base", "fcc135"])
 def test_streamed_update_matches_per_tile_kernel(B, orc, case):
-    """The streamed trailing-update kernel issues the same MMAs for every run
-    length, so tau_00 must agree bit for bit across run lengths; against the
-    one-CTA-per-tile kernel (which sums the three split products in another
-    order) it agrees to the refinement tolerance.  The 42-site l_max = 2 LIZ
-    has r = n - kap = 369, so the last panel step starts its trailing block at
-    an odd row (tiles then start one row above it)."""
+    """The streamed trailing-update kernels (C through shared memory, or
+    through registers with either A-ring depth) issue the same MMAs for every
+    run length and subtract the accumulator from C the same way, so tau_00
+    must agree bit for bit across all of them; against the one-CTA-per-tile
+    kernel (which sums the three split products in another order) it agrees
+    to the refinement tolerance.  The 42-site l_max = 2 LIZ has r = n - kap =
+    369, so the last panel step starts its trailing block at an odd row (tiles
+    then start one row above it)."""
     if case == "odd_base":
         pos, _ = wl.fcc_cluster(3)
         pos = pos[:42]
@@ -125,7 +127,7 @@ def test_streamed_update_matches_per_tile_kernel(B, orc, case):
     old = (B.must_tune_get(2), B.must_tune_get(3))
     taus = []
     try:
-        for streamed, run in ((1, 8), (1, 1), (1, 64), (1, 3), (0, 8)):
+        for streamed, run in ((1, 8), (1, 1), (1, 64), (1, 3), (0, 8), (2, 8), (2, 1), (2, 64), (3, 3)):
             B.must_tune_set(2, streamed)
             B.must_tune_set(3, run)
             tau, st = _gpu_tau(B, w, 1, residual=1)
@@ -134,7 +136,7 @@ def test_streamed_update_matches_per_tile_kernel(B, orc, case):
     finally:
         B.must_tune_set(2, old[0])
         B.must_tune_set(3, old[1])
-    for t in taus[1:4]:
+    for t in taus[1:4] + taus[5:9]:
         assert np.array_equal(t, taus[0])
     k = w.kappa()
     assert rel_fro(taus[4].reshape(-1, k, k), taus[0].reshape(-1, k, k)).max() <= TOLMIX
