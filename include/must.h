@@ -207,11 +207,16 @@ must_status must_site_charge(int32_t lmax, int32_t nE, const double* E, const do
  *           uneven size (1..64, default 4);
  *   knob 1: complex columns per tensor-core tile of the trailing update
  *           (128 or 256, default 128);
- *   knob 2: trailing-update kernel for 128-column tiles: 1 (default) the
- *           streamed kernel, whose CTAs each update a short run of tiles and
- *           move C through shared memory with TMA loads and stores, 0 one CTA
- *           per tile with C read and written from registers;
- *   knob 3: row tiles per CTA of the streamed kernel (1..64, default 32);
+ *   knob 2: trailing-update kernel for 128-column tiles (BF16 splits): the
+ *           streamed kernels give each CTA a run of 64-column tiles with the
+ *           U block resident and move C as follows: 3 (default) TMA loads
+ *           into shared memory, results stored from registers; 2 loads and
+ *           stores from registers; 1 TMA loads and stores through shared
+ *           memory; 0 selects the one-CTA-per-tile kernel.  All streamed
+ *           kernels give identical results;
+ *   knob 3: longest run of row tiles per CTA of the streamed kernels (1..64,
+ *           default 32; runs are split evenly, and shorter when few column
+ *           tiles would leave SMs idle);
  *   knob 4: panel look-ahead of the mixed path: 1 (default) factors panel
  *           k+1 on a high-priority side stream while the rest of step k's
  *           trailing update runs, 0 keeps every step on the caller's stream;

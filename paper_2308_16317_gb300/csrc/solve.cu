@@ -502,7 +502,7 @@ extern "C" must_status must_tune_set(int32_t knob, int32_t value) {
       if (!tc_set_tile_n(value)) { must_set_error("tile width must be 128 or 256"); return MUST_EINVAL; }
       return MUST_OK;
     case 2:   // streamed trailing-update kernel on/off
-      if (!tc_set_streamed(value)) { must_set_error("streamed-update switch must be 0 or 1"); return MUST_EINVAL; }
+      if (!tc_set_streamed(value)) { must_set_error("trailing-update kernel must be 0..3"); return MUST_EINVAL; }
       return MUST_OK;
     case 3:   // tiles per CTA of the streamed kernel
       if (!tc_set_run(value)) { must_set_error("tiles per CTA must be in [1, 64]"); return MUST_EINVAL; }

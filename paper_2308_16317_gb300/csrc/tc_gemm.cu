@@ -701,6 +701,178 @@ __global__ void __launch_bounds__(RegcCfg<STAGES>::THREADS, RegcCfg<STAGES>::SME
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * SBN));
 }
 
+// Variant of the register kernel whose C tiles come in by TMA (a loader warp
+// keeps up to 3 tiles in flight in shared memory); the epilogue reads them
+// from there and stores C - A'B' straight to global memory.
+constexpr int T_CBUF = 3;
+constexpr int T_STAGES = 3;
+constexpr int T_THREADS = 352;                 // producer, MMA, 8 epilogue warps, C loader
+constexpr size_t T_SMEM = size_t(T_STAGES) * S_STAGE_BYTES + S_B_BYTES + size_t(T_CBUF) * C_TILE_BYTES + 1024;
+
+__global__ void __launch_bounds__(T_THREADS, 1)
+    tc_update_tmac(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+                   const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
+                   const __grid_constant__ CUtensorMap tC, TcsParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* bres = smem + T_STAGES * S_STAGE_BYTES;
+  uint8_t* cbuf = bres + S_B_BYTES;
+  __shared__ __align__(8) uint64_t full[T_STAGES];
+  __shared__ __align__(8) uint64_t empty[T_STAGES];
+  __shared__ __align__(8) uint64_t bfull;
+  __shared__ __align__(8) uint64_t cfull[T_CBUF];   // C tile landed
+  __shared__ __align__(8) uint64_t cfree[T_CBUF];   // C tile read by the epilogue (8 warps)
+  __shared__ __align__(8) uint64_t aempty[2];
+  __shared__ __align__(8) uint64_t afull[2];
+  __shared__ __align__(8) uint64_t mdone;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail_raw;
+  volatile int* s_fail = &s_fail_raw;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int rt0, ntile, col0, item;
+  run_coords(P, blockIdx.x, rt0, ntile, col0, item);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < T_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < T_CBUF; ++b) {
+      mbar_init(&cfull[b], 1);
+      mbar_init(&cfree[b], 8);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&aempty[b], 8);
+      mbar_init(&afull[b], 1);
+    }
+    mbar_init(&bfull, 1);
+    mbar_init(&mdone, 1);
+    s_fail_raw = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(2 * SBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const int kstep_elems = KB / 2;
+
+  if (warp == 0 && lane == 0) {
+    mbar_expect_tx(&bfull, S_B_BYTES);
+    for (int kb = 0; kb < S_KSTEPS; ++kb) {
+      tma_load_3d(bres + kb * SB_BYTES, &tB_hi, kb * kstep_elems, P.base + col0, item, &bfull);
+      tma_load_3d(bres + (S_KSTEPS + kb) * SB_BYTES, &tB_lo, kb * kstep_elems, P.base + col0, item, &bfull);
+    }
+    int gs = 0;
+    for (int lt = 0; lt < ntile; ++lt) {
+      const int row0 = (rt0 + lt) * BM;
+      bool ok = true;
+      for (int kb = 0; kb < S_KSTEPS; ++kb, ++gs) {
+        const int s = gs % T_STAGES;
+        if (gs >= T_STAGES && !mbar_wait_f(&empty[s], ((gs / T_STAGES) - 1) & 1, s_fail)) { ok = false; break; }
+        uint8_t* sa = smem + s * S_STAGE_BYTES;
+        mbar_expect_tx(&full[s], S_STAGE_BYTES);
+        tma_load_3d(sa, &tA_hi, kb * kstep_elems, 2 * P.abase + row0, item, &full[s]);
+        tma_load_3d(sa + SA_BYTES, &tA_lo, kb * kstep_elems, 2 * P.abase + row0, item, &full[s]);
+      }
+      if (!ok) break;
+    }
+    if (*s_fail) {
+      volatile int dummy = 0;
+      mbar_wait_f(&bfull, 0, &dummy);
+      for (int s = 0; s < T_STAGES && s < gs; ++s) {
+        const int cnt = (gs - s + T_STAGES - 1) / T_STAGES;
+        mbar_wait_f(&full[s], (cnt - 1) & 1, &dummy);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(SBN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+    bool ok = mbar_wait_f(&bfull, 0, s_fail);
+    const uint32_t bh = smem_u32(bres), bl = bh + S_KSTEPS * SB_BYTES;
+    int gs = 0;
+    for (int lt = 0; lt < ntile && ok; ++lt) {
+      const int ab = lt & 1;
+      if (lt >= 2 && !mbar_wait_f(&aempty[ab], ((lt >> 1) - 1) & 1, s_fail)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc = tmem + uint32_t(ab * SBN);
+      for (int kb = 0; kb < S_KSTEPS; ++kb, ++gs) {
+        const int s = gs % T_STAGES;
+        if (!mbar_wait_f(&full[s], (gs / T_STAGES) & 1, s_fail)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = smem_u32(smem + s * S_STAGE_BYTES), al = ah + SA_BYTES;
+        const uint32_t bhk = bh + kb * SB_BYTES, blk = bl + kb * SB_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < KB / 32; ++kk) {
+          mma_issue(acc, sdesc(ah + 32 * kk), sdesc(bhk + 32 * kk), idesc, (kb > 0 || kk > 0) ? 1u : 0u, 0);
+          mma_issue(acc, sdesc(ah + 32 * kk), sdesc(blk + 32 * kk), idesc, 1u, 0);
+          mma_issue(acc, sdesc(al + 32 * kk), sdesc(bhk + 32 * kk), idesc, 1u, 0);
+        }
+        mma_commit(&empty[s]);
+      }
+      if (ok) mma_commit(&afull[ab]);
+    }
+    mma_commit(&mdone);
+    volatile int dummy = 0;
+    mbar_wait_f(&mdone, 0, &dummy);
+  } else if (warp >= 2 && warp < 10) {
+    // epilogue: C from the shared-memory tile, result stored to global memory
+    const int ew = warp - 2, quarter = warp & 3, half = ew >> 2;
+    const int x = quarter * 32 + lane;
+    const int colb = P.base + col0 + half * 32;
+    float* Cg = P.C + size_t(item) * P.stride2;
+    const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+    for (int lt = 0; lt < ntile; ++lt) {
+      const int ab = lt & 1, cb = lt % T_CBUF;
+      if (!mbar_wait_f(&afull[ab], (lt >> 1) & 1, s_fail)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t v[32];
+      tmem_ld32(tmem + lane_off + uint32_t(ab * SBN + half * 32), v);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&aempty[ab]);
+      if (!mbar_wait_f(&cfull[cb], (lt / T_CBUF) & 1, s_fail)) break;
+      const float* cs = reinterpret_cast<const float*>(cbuf + cb * C_TILE_BYTES);
+      float c[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) c[j] = cs[(half * 32 + j) * BM + x];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&cfree[cb]);
+      const int gr = 2 * P.abase + (rt0 + lt) * BM + x;
+      if (gr >= 2 * P.base && gr < 2 * P.n) {   // rows above base stay as they are
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (colb + j < P.n) __stcs(Cg + size_t(colb + j) * P.ld2 + gr, c[j] - __uint_as_float(v[j]));
+      }
+    }
+  } else if (warp == 10 && lane == 0) {
+    // C loader: tile lt into buffer lt % T_CBUF once the epilogue has read tile lt - T_CBUF from it
+    int issued = 0;
+    for (; issued < ntile; ++issued) {
+      const int cb = issued % T_CBUF;
+      if (issued >= T_CBUF && !mbar_wait_f(&cfree[cb], ((issued / T_CBUF) - 1) & 1, s_fail)) break;
+      mbar_expect_tx(&cfull[cb], C_TILE_BYTES);
+      tma_load_3d(cbuf + cb * C_TILE_BYTES, &tC, 2 * P.abase + (rt0 + issued) * BM, P.base + col0, item, &cfull[cb]);
+    }
+    if (*s_fail) {
+      volatile int dummy = 0;
+      for (int cb = 0; cb < T_CBUF && cb < issued; ++cb) {
+        const int cnt = (issued - cb + T_CBUF - 1) / T_CBUF;
+        mbar_wait_f(&cfull[cb], (cnt - 1) & 1, &dummy);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && *s_fail) atomicExch(P.err, 1);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * SBN));
+}
+
 // ---------------------------------------------------------------- packing --
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16_raw& hi, __nv_bfloat16_raw& lo) {
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -816,8 +988,8 @@ bool make_c_map(CUtensorMap* m, float2* C, int ld, size_t stride, int n, int ite
 
 constexpr int TC_STAGES = 3;
 int g_tile_n = 128;   // 128 or 256 complex columns per tile (autotuned)
-int g_streamed = 2;   // 1: streamed kernel (BF16 splits, C through shared memory); 2, 3: streamed with C
-                      // through registers (6- / 2-stage A ring); 0: per-tile kernel
+int g_streamed = 3;   // BF16 splits, streamed runs: 3: C loaded by TMA, stored from registers; 2: C loaded
+                      // and stored through registers; 1: C through shared memory both ways; 0: per-tile kernel
 int g_run = 32;       // row tiles per CTA of the streamed kernel
 
 template <int BN>
@@ -856,6 +1028,17 @@ void launch_tc_regc(const CUtensorMap& mah, const CUtensorMap& mal, const CUtens
   }
   const int grid = P.rruns * P.ct * items;
   tc_update_regc<STAGES><<<grid, RegcCfg<STAGES>::THREADS, RegcCfg<STAGES>::SMEM, st>>>(mah, mal, mbh, mbl, P);
+}
+
+void launch_tc_tmac(const CUtensorMap& mah, const CUtensorMap& mal, const CUtensorMap& mbh, const CUtensorMap& mbl,
+                    const CUtensorMap& mc, const TcsParams& P, int items, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_update_tmac, cudaFuncAttributeMaxDynamicSharedMemorySize, int(T_SMEM));
+    attr = true;
+  }
+  const int grid = P.rruns * P.ct * items;
+  tc_update_tmac<<<grid, T_THREADS, T_SMEM, st>>>(mah, mal, mbh, mbl, mc, P);
 }
 
 int kp_of(bool tf32) {
@@ -1041,7 +1224,7 @@ bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, i
     if (g_streamed == 2)
       launch_tc_regc<6>(mah, mal, mbh, mbl, S, items, st);
     else if (g_streamed == 3)
-      launch_tc_regc<2>(mah, mal, mbh, mbl, S, items, st);
+      launch_tc_tmac(mah, mal, mbh, mbl, mc, S, items, st);
     else
       launch_tc_streamed(mah, mal, mbh, mbl, mc, S, items, st);
     prof_launched(PH_UPDATE, 1, items);
