@@ -120,19 +120,31 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def code_sha256(path: str) -> str:
+    """sha256 of a C/CUDA source with its comments and blank lines removed, so
+    that a capture stays valid across comment-only edits of the kernel file."""
+    import re
+    text = open(path, encoding="utf-8").read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    lines = [ln.rstrip() for ln in text.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()
+
+
 def traffic_from_profiles(kernel_key: str, source: str):
-    """DRAM bytes per launch recorded in profiles/<kernel_key>.txt, if the kernel
-    source it was captured from is unchanged (sha256 line); else None."""
+    """DRAM bytes per launch recorded in profiles/<kernel_key>.txt, if the code
+    of the kernel source it was captured from is unchanged (code_sha256 line);
+    else None."""
     path = os.path.join(ROOT, "profiles", kernel_key + ".txt")
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+    sha = code_sha256(os.path.join(ROOT, source))
     vals = {}
     for ln in open(path):
         if ":" in ln:
             k, v = ln.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("source_sha256") != sha:
+    if vals.get("code_sha256") != sha:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])

@@ -13,13 +13,22 @@
 //   A'B'^T ~ A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
 // accumulated in one FP32 TMEM accumulator (the lo*lo term is dropped).
 //
-// Two kernels share this scheme.  The streamed kernel (default) gives each
-// CTA a short run of 128 x 128 tiles and moves C itself through shared memory
-// with TMA (tile load, in-place update, tile store), double-buffering both the
-// C tile and the TMEM accumulator so that the load of tile t+1, the MMAs of
-// tile t+1 and the store of tile t overlap; the update is HBM-bound, and this
-// keeps C streaming without registers holding it.  The per-tile kernel below
-// is kept for 256-column tiles.
+// Kernels sharing this scheme (knob 2 of must_tune_set picks one):
+//  - streamed kernels: each CTA takes a run of 128-row x 64-column tiles of
+//    one column block, with the U block (B_hi, B_lo) resident in shared
+//    memory, the A rows streaming through a TMA ring and two TMEM
+//    accumulators, so that the MMAs of tile t+1 overlap the epilogue of tile
+//    t.  The update is HBM-bound, so they differ in how C moves:
+//      tc_update_tmac (default): a loader warp brings C tiles into three
+//        shared-memory buffers by TMA; the epilogue forms C - A'B' and stores
+//        it from registers (coalesced 128-byte column segments);
+//      tc_update_regc: C loaded and stored from registers, two tiles ahead;
+//      tc_update_streamed: C loaded by TMA, updated in shared memory and
+//        stored by TMA.
+//    All three issue the same MMAs and subtract the same way, so their
+//    results are identical.
+//  - the per-tile kernel (one CTA per tile), used for 256-column tiles and
+//    the TF32 splits.
 //
 // Per-tile kernel: one CTA (256 threads) computes a 128 x BN tile of C' (64 complex rows x BN
 // complex columns): warp 0 lane 0 issues TMA loads into a STAGES-deep ring,

@@ -59,9 +59,10 @@ def test_host_side_argument_errors_need_no_gpu(lib):
 
 
 def test_bench_traffic_profile_matches_current_kernel_source():
-    """profiles/tc_update_kernel_fcc135.txt carries the sha256 of the kernel
-    source it was captured from; bench.py reports roofline.traffic only while
-    it matches (a stale capture reads as null)."""
+    """profiles/tc_update_kernel_fcc135.txt carries the sha256 of the code
+    (comments stripped) of the kernel source it was captured from; bench.py
+    reports roofline.traffic only while it matches (a stale capture reads as
+    null)."""
     import importlib.util
     import os
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -100,3 +101,17 @@ def test_site_charge_rejects_host_arrays():
     N = np.zeros(1)
     with pytest.raises(B.MustError):
         B.must_site_charge(3, E, w, V, 2.5, tau, None, N)
+
+
+def test_code_digest_ignores_comments_only(tmp_path):
+    import importlib.util
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    a, b, c = tmp_path / "a.cu", tmp_path / "b.cu", tmp_path / "c.cu"
+    a.write_text("// header\nint f(int x) {\n  return x + 1;  // add\n}\n")
+    b.write_text("/* another\n   header */\n\nint f(int x) {\n  return x + 1;\n}\n")
+    c.write_text("int f(int x) {\n  return x + 2;\n}\n")
+    assert bench.code_sha256(str(a)) == bench.code_sha256(str(b))
+    assert bench.code_sha256(str(a)) != bench.code_sha256(str(c))
