@@ -196,10 +196,26 @@ void must_plan_free(must_plan* plan);
  * (4 pi d)).  Every array must be device memory (MUST_EINVAL otherwise);
  * asynchronous on `stream`.
  */
+/*
+ * must_site_density: the spherically averaged charge density inside the
+ * centre sphere at n_r radii r[i] (0 < r[i] <= r_mt; other radii give NaN),
+ * for each output block s as in must_site_charge:
+ *   n_of_r[s][i] = -(1/pi) Im sum_k w_k (1/(4 pi)) [sum_L tau_LL(E_k) Z_l(r_i)^2
+ *                                               - sum_l (2l+1) Z_l(r_i) J_l(r_i)],
+ * the angular average of the site Green's function G(r, r; E) of Eq. 3
+ * integrated along the contour as in Eq. 2, so that 4 pi int_0^a n r^2 dr is
+ * must_site_charge's N.  Inside the well Z_l = c_l j_l(q r) and J_l =
+ * alpha_l j_l(q r) + beta_l y_l(q r), q = sqrt(E - V), matched at r_mt as
+ * above.  Every array (E, w, V, tau00, r, n_of_r) must be device memory
+ * (MUST_EINVAL otherwise); asynchronous on `stream`.
+ */
 must_status must_contour_weights(int32_t n_e, double e_bot, double e_f, double* E, double* w);
 must_status must_site_charge(int32_t lmax, int32_t nE, const double* E, const double* w, int32_t n_out,
                              const double* V, double r_mt, const double* tau00, double* n_of_E, double* N,
                              void* stream);
+must_status must_site_density(int32_t lmax, int32_t nE, const double* E, const double* w, int32_t n_out,
+                              const double* V, double r_mt, const double* tau00, int32_t n_r, const double* r,
+                              double* n_of_r, void* stream);
 
 /*
  * Tuning knobs (set by the project's autotuner, paper_2308_16317_gb300/autotune.py):

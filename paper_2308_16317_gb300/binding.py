@@ -78,6 +78,7 @@ def load():
         "must_tune_get": (I32, [I32]),
         "must_contour_weights": (I32, [I32, D, D, P, P]),
         "must_site_charge": (I32, [I32, I32, P, P, I32, P, D, P, P, P, P]),
+        "must_site_density": (I32, [I32, I32, P, P, I32, P, D, P, I32, P, P, P]),
         "must_static_scratch_bytes": (SZ, []),
         "must_profile_enable": (None, [ctypes.c_int]),
         "must_profile_read": (ctypes.c_int, [P, P, P, ctypes.c_int]),
@@ -104,7 +105,7 @@ def exported_symbols():
                         "must_mlp_create", "must_mlp_free", "must_mlp_param_count", "must_mlp_get_params",
                         "must_mlp_set_params", "must_mlp_forward", "must_mlp_gradients", "must_mlp_train_step",
                         "must_mlp_save", "must_mlp_load", "must_mlp_features", "must_mlp_apply", "must_mlp_targets",
-                        "must_tau00_solve_seeded", "must_contour_weights", "must_site_charge")]
+                        "must_tau00_solve_seeded", "must_contour_weights", "must_site_charge", "must_site_density")]
 
 
 def _ptr(a):
@@ -374,3 +375,12 @@ def must_site_charge(lmax: int, E, w, V, r_mt: float, tau00, n_of_E, N, stream=N
     n_out, nE = int(tau00.shape[0]), int(tau00.shape[1])
     _check(load().must_site_charge(int(lmax), nE, _ptr(E), _ptr(w), n_out, _ptr(V), float(r_mt), _ptr(tau00),
                                    _ptr(n_of_E), _ptr(N), _stream(stream)))
+
+
+def must_site_density(lmax: int, E, w, V, r_mt: float, tau00, r, n_of_r, stream=None):
+    """Radial density inside the centre sphere (device tensors): tau00 [n_out][nE][kap][kap]
+    complex128, E, w [nE] complex128, V [n_out] float64, r [n_r] float64, n_of_r [n_out][n_r]."""
+    n_out, nE = int(tau00.shape[0]), int(tau00.shape[1])
+    n_r = int(r.shape[0])
+    _check(load().must_site_density(int(lmax), nE, _ptr(E), _ptr(w), n_out, _ptr(V), float(r_mt), _ptr(tau00),
+                                    n_r, _ptr(r), _ptr(n_of_r), _stream(stream)))

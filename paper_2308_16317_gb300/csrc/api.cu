@@ -272,4 +272,27 @@ must_status must_site_charge(int32_t lmax, int32_t nE, const double* E, const do
   return MUST_OK;
 }
 
+must_status must_site_density(int32_t lmax, int32_t nE, const double* E, const double* w, int32_t n_out,
+                              const double* V, double r_mt, const double* tau00, int32_t n_r, const double* r,
+                              double* n_of_r, void* stream) {
+  if (nE < 1 || n_out < 1 || n_r < 1 || !E || !w || !V || !tau00 || !r || !n_of_r) {
+    must_set_error("must_site_density: bad argument");
+    return MUST_EINVAL;
+  }
+  if (lmax < 0 || lmax > MUST_MAX_LMAX || !(r_mt > 0.0)) { must_set_error("must_site_density: lmax/r_mt"); return MUST_EINVAL; }
+  const void* ptrs[6] = {E, w, V, tau00, r, n_of_r};
+  for (int i = 0; i < 6; ++i)
+    if (!must_is_device_ptr(ptrs[i])) {
+      must_set_error("must_site_density: every array must be device memory");
+      return MUST_EINVAL;
+    }
+  const int kap = (lmax + 1) * (lmax + 1);
+  launch_site_density(lmax, nE, reinterpret_cast<const double2*>(E), reinterpret_cast<const double2*>(w), n_out, V,
+                      r_mt, reinterpret_cast<const double2*>(tau00), kap, n_r, r, n_of_r,
+                      static_cast<cudaStream_t>(stream));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { must_set_error("must_site_density: %s", cudaGetErrorString(e)); return MUST_ECUDA; }
+  return MUST_OK;
+}
+
 }  // extern "C"

@@ -200,14 +200,18 @@ __device__ __forceinline__ cd lommel(int l, cd x, const cd* u, const cd* v) {
   return (0.5 * (x * x * x)) * (u[k] * v[k] - 0.5 * (u[k - 1] * v[k + 1] + u[k + 1] * v[k - 1]));
 }
 
-__device__ cd site_integrand(int lmax, cd E, double V, double a, const double2* tau, int kap) {
+// Inside the well (square well of depth V, radius a) at energy E, per l:
+// Z_l = c_l j_l(q r) (value matched to j_l/t_l - i kappa h_l at r = a) and
+// J_l = alpha_l j_l(q r) + beta_l y_l(q r) (value and slope matched to j_l).
+// Also returns j_l(qa), y_l(qa) (indexed l + 1, l = -1 .. lmax + 1) and q.
+__device__ void well_coefficients(int lmax, cd E, double V, double a, cd* c, cd* alpha, cd* beta, cd* jq, cd* yq,
+                                  cd& q_out) {
   const cd kp = csqrt_p(E), q = csqrt_p(E - mk(V, 0.0));
   const cd ka = a * kp, qa = a * q;
-  cd jk[MUST_MAX_LMAX + 3], yk[MUST_MAX_LMAX + 3], jq[MUST_MAX_LMAX + 3], yq[MUST_MAX_LMAX + 3];
+  cd jk[MUST_MAX_LMAX + 3], yk[MUST_MAX_LMAX + 3];
   bessel_jy_ext(lmax, ka, jk, yk);
   bessel_jy_ext(lmax, qa, jq, yq);
-  const cd ika = cinv(ka), iqa = cinv(qa), iq3 = cinv(q * q * q);
-  cd g = mk(0.0, 0.0);
+  const cd ika = cinv(ka), iqa = cinv(qa);
   for (int l = 0; l <= lmax; ++l) {
     const int k = l + 1;
     const cd hk = jk[k] + mk(0.0, 1.0) * yk[k];
@@ -220,21 +224,37 @@ __device__ cd site_integrand(int lmax, cd E, double V, double a, const double2* 
     const cd num = mk(0.0, 1.0) * kp * (kp * dhk * jq[k] - q * djq * hk);
     const cd den = kp * djk * jq[k] - q * djq * jk[k];
     const cd tinv = cdiv(num, den);
-    const cd c = cdiv(jk[k] * tinv - mk(0.0, 1.0) * kp * hk, jq[k]);
+    c[l] = cdiv(jk[k] * tinv - mk(0.0, 1.0) * kp * hk, jq[k]);
     const cd det = q * (jq[k] * dyq - yq[k] * djq);
-    const cd alpha = cdiv(q * (jk[k] * dyq) - kp * (djk * yq[k]), det);
-    const cd beta = cdiv(kp * (djk * jq[k]) - q * (jk[k] * djq), det);
+    alpha[l] = cdiv(q * (jk[k] * dyq) - kp * (djk * yq[k]), det);
+    beta[l] = cdiv(kp * (djk * jq[k]) - q * (jk[k] * djq), det);
+  }
+  q_out = q;
+}
+
+// sum over m of tau_LL for each l (tau column-major kap x kap)
+__device__ __forceinline__ cd tau_diag_l(const double2* tau, int kap, int l) {
+  cd dsum = mk(0.0, 0.0);
+  for (int m = -l; m <= l; ++m) {
+    const int L = l * l + l + m;
+    const double2 tv = tau[size_t(L) * kap + L];
+    dsum = dsum + mk(tv.x, tv.y);
+  }
+  return dsum;
+}
+
+__device__ cd site_integrand(int lmax, cd E, double V, double a, const double2* tau, int kap) {
+  cd c[MUST_MAX_LMAX + 1], al[MUST_MAX_LMAX + 1], be[MUST_MAX_LMAX + 1];
+  cd jq[MUST_MAX_LMAX + 3], yq[MUST_MAX_LMAX + 3], q;
+  well_coefficients(lmax, E, V, a, c, al, be, jq, yq, q);
+  const cd qa = a * q, iq3 = cinv(q * q * q);
+  cd g = mk(0.0, 0.0);
+  for (int l = 0; l <= lmax; ++l) {
     const cd ljj = iq3 * lommel(l, qa, jq, jq);
     const cd ljy = iq3 * (lommel(l, qa, jq, yq) - mk((2.0 * l + 1.0) / 4.0, 0.0));
-    const cd F = c * c * ljj;
-    const cd I = c * (alpha * ljj + beta * ljy);
-    cd dsum = mk(0.0, 0.0);
-    for (int m = -l; m <= l; ++m) {
-      const int L = l * l + l + m;
-      const double2 tv = tau[size_t(L) * kap + L];
-      dsum = dsum + mk(tv.x, tv.y);
-    }
-    g = g + dsum * F - (2.0 * l + 1.0) * I;
+    const cd F = c[l] * c[l] * ljj;
+    const cd I = c[l] * (al[l] * ljj + be[l] * ljy);
+    g = g + tau_diag_l(tau, kap, l) * F - (2.0 * l + 1.0) * I;
   }
   return g;
 }
@@ -265,6 +285,46 @@ __global__ void site_charge_kernel(int lmax, int nE, const double2* __restrict__
 void launch_site_charge(int lmax, int nE, const double2* E, const double2* w, int n_out, const double* V, double a,
                         const double2* tau, int kap, double* nE_out, double* N_out, cudaStream_t st) {
   site_charge_kernel<<<n_out, 128, 0, st>>>(lmax, nE, E, w, V, a, tau, kap, nE_out, N_out);
+  prof_launched(PH_OTHER, 1);
+}
+
+// Radial density inside the sphere: one thread per (radius, output block),
+// the contour sum over energies in order:
+//   n(r) = -(1/pi) Im sum_k w_k (1/4pi) [sum_L tau_LL Z_l(r)^2 - sum_l (2l+1) Z_l(r) J_l(r)].
+// Radii outside (0, a] give NaN.
+__global__ void site_density_kernel(int lmax, int nE, const double2* __restrict__ E, const double2* __restrict__ w,
+                                    const double* __restrict__ V, double a, const double2* __restrict__ tau, int kap,
+                                    int n_r, const double* __restrict__ r, double* __restrict__ out) {
+  const int s = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_r) return;
+  const double ri = r[i];
+  if (!(ri > 0.0 && ri <= a)) {
+    out[size_t(s) * n_r + i] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  double acc = 0.0;
+  for (int k = 0; k < nE; ++k) {
+    cd c[MUST_MAX_LMAX + 1], al[MUST_MAX_LMAX + 1], be[MUST_MAX_LMAX + 1];
+    cd jq[MUST_MAX_LMAX + 3], yq[MUST_MAX_LMAX + 3], q;
+    well_coefficients(lmax, mk(E[k].x, E[k].y), V[s], a, c, al, be, jq, yq, q);
+    cd jr[MUST_MAX_LMAX + 3], yr[MUST_MAX_LMAX + 3];
+    bessel_jy_ext(lmax, ri * q, jr, yr);
+    const double2* tk = tau + (size_t(s) * nE + k) * kap * kap;
+    cd g = mk(0.0, 0.0);
+    for (int l = 0; l <= lmax; ++l) {
+      const cd Z = c[l] * jr[l + 1];
+      const cd J = al[l] * jr[l + 1] + be[l] * yr[l + 1];
+      g = g + tau_diag_l(tk, kap, l) * (Z * Z) - (2.0 * l + 1.0) * (Z * J);
+    }
+    acc += (mk(w[k].x, w[k].y) * g).y;
+  }
+  out[size_t(s) * n_r + i] = -acc / (4.0 * 3.14159265358979323846 * 3.14159265358979323846);
+}
+
+void launch_site_density(int lmax, int nE, const double2* E, const double2* w, int n_out, const double* V, double a,
+                         const double2* tau, int kap, int n_r, const double* r, double* out, cudaStream_t st) {
+  site_density_kernel<<<dim3((n_r + 63) / 64, n_out), 64, 0, st>>>(lmax, nE, E, w, V, a, tau, kap, n_r, r, out);
   prof_launched(PH_OTHER, 1);
 }
 

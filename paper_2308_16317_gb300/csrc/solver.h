@@ -51,3 +51,5 @@ void launch_chunk_index(int* out_index, int* status, int items, const ChunkIndex
 
 void launch_site_charge(int lmax, int nE, const double2* E, const double2* w, int n_out, const double* V, double a,
                         const double2* tau, int kap, double* nE_out, double* N_out, cudaStream_t st);
+void launch_site_density(int lmax, int nE, const double2* E, const double2* w, int n_out, const double* V, double a,
+                         const double2* tau, int kap, int n_r, const double* r, double* out, cudaStream_t st);

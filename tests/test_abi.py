@@ -115,3 +115,15 @@ def test_code_digest_ignores_comments_only(tmp_path):
     c.write_text("int f(int x) {\n  return x + 2;\n}\n")
     assert bench.code_sha256(str(a)) == bench.code_sha256(str(b))
     assert bench.code_sha256(str(a)) != bench.code_sha256(str(c))
+
+
+def test_site_density_rejects_host_arrays():
+    import numpy as np
+    from paper_2308_16317_gb300 import binding as B
+    E, w = B.must_contour_weights(4)
+    tau = np.zeros((1, 4, 16, 16), np.complex128)
+    V = np.array([-1.0])
+    r = np.array([0.5, 1.0])
+    out = np.zeros((1, 2))
+    with pytest.raises(B.MustError):
+        B.must_site_density(3, E, w, V, 2.5, tau, r, out)

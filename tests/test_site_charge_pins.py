@@ -109,3 +109,52 @@ def test_bound_state_weight_inside_the_sphere():
     p_in = inside / (inside + outside)
     assert -0.3 < Eb < -0.25
     assert abs(dN - p_in) <= 1e-6
+
+
+def test_radial_density_integrates_to_the_site_charge():
+    """4 pi int_0^a n(r) r^2 dr (Gauss-Legendre in r) must equal the charge
+    that the Lommel integrals give, for the lone-site tau = t and for a tau
+    that is not t (each l channel scaled differently), both spins' depths."""
+    lmax = 3
+    E, w = sc.contour_weights(24)
+    x, W = np.polynomial.legendre.leggauss(48)
+    r, wr = 0.5 * A * (x + 1.0), 0.5 * A * W
+    lL = oracle.l_of_L(lmax)
+    for V in (-0.95, -1.45):
+        for scale in ([1.0, 1.0, 1.0, 1.0], [1.2 + 0.1j, 0.8, 1.0 - 0.2j, 1.5]):
+            taus = []
+            for e in E:
+                t, _ = oracle.square_well(lmax, e, V, A)
+                taus.append(np.diag((t * np.asarray(scale))[lL]))
+            _, N = sc.site_charge(lmax, E, w, V, A, taus)
+            n = sc.radial_density(lmax, E, w, V, A, taus, r)
+            assert np.isfinite(n).all()
+            assert abs(4.0 * np.pi * np.sum(wr * r * r * n) - N) <= 1e-11 * abs(N)
+
+
+def test_radial_density_of_a_lone_site_on_the_real_axis():
+    """tau = t at one real energy above the well bottom (unit weight): the
+    local density of states is kappa/(4 pi^2) sum_l (2l+1) R_l(r)^2 with the
+    real regular solution R_l = cos(d_l) j_l(kappa r) - sin(d_l) y_l(kappa r)
+    outside and its continuation d j_l(q r) inside, the phase shifts d_l from
+    the textbook log-derivative matching (no t-matrix or Green's function)."""
+    from scipy.special import spherical_jn, spherical_yn
+    lmax, V = 3, -1.0
+    for E in (0.15, 0.45):
+        kap, q = np.sqrt(E), np.sqrt(E - V)
+        t, _ = oracle.square_well(lmax, E + 0j, V, A)
+        tau = np.diag(t[oracle.l_of_L(lmax)])
+        r = np.linspace(0.1, 1.0, 10) * A
+        n = sc.radial_density(lmax, [E + 0j], [1.0 + 0j], V, A, [tau], r)
+        ref = np.zeros_like(r)
+        for l in range(lmax + 1):
+            jk, djk = spherical_jn(l, kap * A), spherical_jn(l, kap * A, derivative=True)
+            yk, dyk = spherical_yn(l, kap * A), spherical_yn(l, kap * A, derivative=True)
+            jq, djq = spherical_jn(l, q * A), spherical_jn(l, q * A, derivative=True)
+            # tan d = (kap j' j_q - q j_q' j) / (kap y' j_q - q j_q' y)
+            d = np.arctan2(kap * djk * jq - q * djq * jk, kap * dyk * jq - q * djq * yk)
+            Ra = np.cos(d) * jk - np.sin(d) * yk
+            R = Ra / jq * spherical_jn(l, q * r)
+            ref += (2 * l + 1) * R * R
+        ref *= kap / (4.0 * np.pi ** 2)
+        assert np.abs(n - ref).max() <= 1e-12 * np.abs(ref).max(), (E, n, ref)
