@@ -743,7 +743,7 @@ __device__ __forceinline__ void ll_split(long long v, float& hi, float& lo) {
 }
 
 template <int CPT>
-__global__ void __launch_bounds__(256) residual_int_kernel(const float4* __restrict__ M0, size_t stride, int ld,
+__global__ void __launch_bounds__(512) residual_int_kernel(const float4* __restrict__ M0, size_t stride, int ld,
                                                            int n, int kap, const XQ* __restrict__ Q0,
                                                            const double2* __restrict__ X0,
                                                            const int* __restrict__ rexp0,
@@ -1222,6 +1222,8 @@ static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
 // ---------------------------------------------------------------- driver --
 constexpr int RES_SPLIT = 4;   // K splits of the double-float residual
 constexpr int RES_CPT = 8;     // right-hand sides per thread of the split-integer residual
+// its CTA: 64 rows x ceil(kap / RES_CPT) column groups, at most 64 x 7 = 448 threads (kap <= 50)
+static_assert(64 * ((2 * MUST_MAX_NL + RES_CPT - 1) / RES_CPT) <= 512, "residual_int_kernel launch bound");
 
 size_t mixed_item_bytes(int n, int ld, int kap) {
   return a256(size_t(ld) * n * 8)          // M32

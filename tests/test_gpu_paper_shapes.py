@@ -41,11 +41,13 @@ def test_lmax4_small_vs_oracle(B, orc, canted):
                     wl.R_MT, canted=canted)
     k = w.kappa()
     ref, _ = oracle_tau(orc, w, nthreads=ncpu())
-    for precision, tol in ((0, 1e-11), (1, 1e-9)):
-        tau, st = _tau(B, w, precision, residual=1)
+    # FP64, and the mixed path with the double-float and the split-integer
+    # residual (kap = 50 canted: the widest residual CTA)
+    for precision, tol, residual in ((0, 1e-11, 1), (1, 1e-9, 1), (1, 1e-9, 2)):
+        tau, st = _tau(B, w, precision, residual=residual)
         assert (st == 0).all()
         err = rel_fro(tau.reshape(-1, k, k), ref)
-        assert err.max() <= tol, (precision, err)
+        assert err.max() <= tol, (precision, residual, err)
 
 
 @pytest.mark.parametrize("shape", ["niau249", "cocrfemnni135_canted"])
