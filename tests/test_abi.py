@@ -127,3 +127,27 @@ def test_site_density_rejects_host_arrays():
     out = np.zeros((1, 2))
     with pytest.raises(B.MustError):
         B.must_site_density(3, E, w, V, 2.5, tau, r, out)
+
+
+def test_bench_algorithmic_work_of_the_update():
+    """The roofline numerators of bench.py: the mixed path's trailing update
+    moves 16 B per trailing-block element per panel step (7.905e8 B per launch
+    of the 64-item n = 2160 workload, 65 launches per step); the FP64 path's
+    update does 8 flops per complex MAC, which for r = n - kap eliminated
+    columns approaches the unblocked 8/3 (n^3 - kap^3) minus the panels' share."""
+    import importlib.util
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    n, kap, nb, items = 2160, 16, 64, 64
+    byts = bench.phase_work("trailing_update", n, kap, nb, items, "bf16x3")[0]
+    steps = [(k0, min(nb, n - kap - k0)) for k0 in range(0, n - kap, nb)]
+    assert len(steps) == 34
+    ref = sum(16 * (n - k0 - w) ** 2 for k0, w in steps) * items
+    assert byts == ref
+    assert abs(byts / 65 - 7.905e8) < 0.001e8
+    flops = bench.phase_work("trailing_update", n, kap, nb, 1, "fp64")[0]
+    unblocked = 8.0 * sum((n - j - 1) ** 2 for j in range(n - kap))
+    # the blocked update leaves out the work inside each panel (about nb/2 columns of width m)
+    assert 0.9 * unblocked < flops < unblocked
