@@ -1237,7 +1237,8 @@ size_t mixed_item_bytes(int n, int ld, int kap) {
          + RES_SPLIT * a256(size_t(n) * kap * 16)   // split-K residual partials
          + a256(size_t(kap) * kap * 16)    // Sinv
          + a256(size_t(64) * 64 * 8)       // inverse of the panel's L11
-         + 1280                            // norms, previous norms, conv, error word, seed flags
+         + 1536                            // norms, previous norms, conv, error word, two seed flag
+                                           // arrays: six 256-byte-rounded carves per chunk
          + tc_pack_bytes_per_item(n);      // tensor-core operand packs
 }
 

@@ -28,7 +28,10 @@ struct Layout {
 
 size_t item_bytes(int n, int ld, int kap, int precision) {
   const size_t mat64 = a256(size_t(ld) * n * 16);
-  size_t b = mat64 + a256(size_t(n) * 4) /*piv*/ + a256(size_t(n) * 8) /*scale*/ + 256 /*status+index*/;
+  // status and output index are carved as two separate 256-byte-rounded
+  // arrays per chunk: 2 x 256 bytes per item covers their rounding for any
+  // item count >= 1
+  size_t b = mat64 + a256(size_t(n) * 4) /*piv*/ + a256(size_t(n) * 8) /*scale*/ + 512 /*status+index*/;
   if (precision != MUST_FP64) b += mixed_item_bytes(n, ld, kap);
   return b;
 }

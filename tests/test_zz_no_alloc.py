@@ -6,7 +6,8 @@ while they run; it solves in a scratch array compiled into the library.  The
 check: two calls in a row (the second finds the first call's data still in
 the shared scratch) give the same tau_00 as the ordinary FP64 solve, within
 the FP64 tolerance of the parity tests; an LIZ too large for the scratch is
-rejected with a clear error.  Collected last so that a failure here does not
+rejected with a clear error; the second call leaves the device's free memory
+unchanged (it allocates nothing).  Collected last so that a failure here does not
 hide the other GPU tests.
 """
 import numpy as np
@@ -45,12 +46,19 @@ def test_static_scratch_solve_matches_workspace_solve(B, make):
     torch.cuda.synchronize()
     ref = ref.cpu().numpy()
     assert (st_ref.cpu().numpy() == 0).all()
-    for _ in range(2):      # two calls in a row share the scratch
-        tau = torch.full((s.n_out, len(w.energies), s.kap, s.kap), float("nan"), dtype=torch.complex128,
-                         device="cuda")
-        st = torch.full((s.n_out, len(w.energies)), -1, dtype=torch.int32, device="cuda")
+    outs = [(torch.full((s.n_out, len(w.energies), s.kap, s.kap), float("nan"), dtype=torch.complex128,
+                        device="cuda"),
+             torch.full((s.n_out, len(w.energies)), -1, dtype=torch.int32, device="cuda")) for _ in range(2)]
+    torch.cuda.synchronize()
+    for call, (tau, st) in enumerate(outs):      # two calls in a row share the scratch
+        # the first call on the device looks up the scratch address and loads
+        # the kernels; the second must leave the device's free memory unchanged
+        free0 = torch.cuda.mem_get_info()[0]
         B.must_tau00_solve_static(s.lizs[0], s.E, s.tinv, s.n_species, s.nspin, tau, st)
         torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        if call == 1:
+            assert free1 == free0, "the allocation-free solve changed free device memory by %d bytes" % (free0 - free1)
         assert (st.cpu().numpy() == 0).all()
         assert _rel(tau.cpu().numpy(), ref) <= TOL64
 
