@@ -239,28 +239,37 @@ def run_ours(args):
     if rank == 0:
         sampler.start()
         time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize(dev)
-    B.must_profile_enable(True)
-    B.must_profile_read()
-    l0 = B.must_launch_count()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        s.solve(opts, out=out)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier()
-    l1 = B.must_launch_count()
-    prof = B.must_profile_read()
-    B.must_profile_enable(False)
+    def timed_region(profiled: bool):
+        # K steps between a barrier + synchronize on both sides, CUDA events on
+        # the launching stream; the headline region runs with the library's
+        # per-phase instrumentation off, a second region with it on gives the
+        # phase split and the dominant kernel's launch times
+        barrier()
+        torch.cuda.synchronize(dev)
+        B.must_profile_enable(profiled)
+        B.must_profile_read()
+        l0 = B.must_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            s.solve(opts, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        l1 = B.must_launch_count()
+        prof = B.must_profile_read() if profiled else None
+        B.must_profile_enable(False)
+        return max_over_ranks(e0.elapsed_time(e1)), l1 - l0, prof
+
+    ms_total, n_launches, _ = timed_region(False)
     clocks = sampler.stop() if rank == 0 else None
-    ms_total = max_over_ranks(e0.elapsed_time(e1))
     ms_step = ms_total / args.steps
     value = items * ws * args.steps / (ms_total / 1e3)
     tau_fast = blocks_to_numpy(out[0][0])
     status = out[1].cpu().numpy()
+    ms_prof_total, _, prof = timed_region(True)
+    status_prof = out[1].cpu().numpy()
 
     # roofline of the dominant phase (largest measured share of the step)
     peaks, peak_kind = load_peaks()
@@ -314,7 +323,9 @@ def run_ours(args):
                     else "nominal FP64/FP32 from unit counts and clocks",
                     "algorithmic_per_launch": total / max(launches_d, 1),
                     "avg_launch_ms": ms_d / max(launches_d, 1), "launches": launches_d,
-                    "share_of_step": ms_d / (ms_total if ws == 1 else ms_total), "tensor_view": tensor_view}
+                    "share_of_step": ms_d / ms_prof_total, "tensor_view": tensor_view,
+                    "timed_in": "a second %d-step region with per-phase CUDA events on (%.3f ms/step)"
+                                % (args.steps, ms_prof_total / args.steps)}
     phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
               for k, v in prof.items() if v[1] > 0}
 
@@ -357,8 +368,15 @@ def run_ours(args):
            "d2h_bytes_per_step": int(tau_h.numel() * 16 + sta_h.numel() * 4)}
 
     cpu = None
+    per_energy = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, args.cpu_sample)
+        cpu, o_items, o_tau = cpu_baseline(w, args.cpu_sample)
+        # the headline's tau_00 against the oracle on the sampled (spin, energy) items
+        errs = [float(np.linalg.norm(tau_fast[sp, e] - o_tau[q]) / np.linalg.norm(o_tau[q]))
+                for q, (sp, e) in enumerate(o_items)]
+        per_energy = {"max": max(errs), "items": [
+            {"spin": sp, "e": e, "E": [float(w.energies[e].real), float(w.energies[e].imag)], "rel_err": er}
+            for (sp, e), er in sorted(zip(o_items, errs), key=lambda t: (t[0][1], t[0][0]))]}
 
     if rank == 0:
         line = {
@@ -372,9 +390,11 @@ def run_ours(args):
                        "n": n, "n_liz": int(w.lizs[0].n_sites), "lmax": w.lmax, "solves_per_step": items,
                        "precision": prec, "residual": args.residual if prec != "fp64" else None, "l2": "inputs larger than L2 (%.1f GB of matrices per step)" % (
                            items * n * n * (24 if prec != "fp64" else 16) / 1e9)},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(l1 - l0),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(n_launches),
             "clocks": clocks, "plain_fp64": fp64, "max_rel_err_vs_fp64": max_err,
-            "status_ok": bool((status == 0).all() and (st0 == 0).all()), "phases": phases,
+            "rel_err_vs_oracle_per_energy": per_energy,
+            "status_ok": bool((status == 0).all() and (st0 == 0).all() and (status_prof == 0).all()),
+            "phases": phases, "profiled_ms_per_step": ms_prof_total / args.steps,
         }
         emit(line)
     if ws > 1:
@@ -735,6 +755,47 @@ def run_cusolver_context(args):
                       "tflops_8_3_n3": batch * 8 / 3 * n ** 3 / (ms / 1e3) / 1e12})
 
 
+def run_peaks(args):
+    """Measured arithmetic peaks of this GPU (the denominators of the FP64 and
+    FP32 roofline fractions): DFMA, DMMA (FP64 tensor, mma.sync m8n8k4) and
+    FFMA probes of the library (must_peak_probe), each launch sized to about
+    150 ms and timed with CUDA events, best of 5, clocks sampled meanwhile."""
+    import torch
+    from paper_2308_16317_gb300 import binding as B
+    from paper_2308_16317_gb300 import build as libbuild
+    libbuild.build()
+    B.load()
+    res = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    for kind, name in ((0, "dfma_f64"), (1, "dmma_f64_m8n8k4"), (2, "ffma_f32")):
+        res[name] = {}
+        for per_sm in (4, 8):
+            blocks = 152 * per_sm
+            sink = torch.zeros(blocks * 256, dtype=torch.float64, device="cuda")
+            iters = 256
+            best = 0.0
+            for trial in range(7):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                fl = B.must_peak_probe(kind, blocks, iters, sink)
+                b.record()
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b)
+                if trial < 2:   # calibrate the launch to ~150 ms
+                    iters = max(256, int(iters * 150.0 / max(ms, 1e-3)))
+                    continue
+                best = max(best, fl / (ms / 1e3))
+            res[name]["%d_ctas_per_sm" % per_sm] = {"tflops": best / 1e12, "iters": iters}
+        res[name]["tflops"] = max(v["tflops"] for v in res[name].values() if isinstance(v, dict))
+    clocks = sampler.stop()
+    emit({"metric": "measured arithmetic peaks (probe kernels, CUDA events, best of 5 launches of ~150 ms)",
+          "unit": "TFLOP/s", "dfma_f64": res["dfma_f64"]["tflops"], "dmma_f64": res["dmma_f64_m8n8k4"]["tflops"],
+          "ffma_f32": res["ffma_f32"]["tflops"], "detail": res, "clocks": clocks})
+
+
 def cpu_baseline(w, sample: int):
     """The oracle on the host cores: `sample` (energy, spin) solves of the same
     LIZ, one per thread, timed end to end."""
@@ -747,10 +808,11 @@ def cpu_baseline(w, sample: int):
     E = np.array([w.energies[e] for _, e in items])
     ti = np.array([oracle.site_tinv(w.lmax, w.energies[e], w.site_depths(liz, s), w.r_mt) for s, e in items])
     t0 = time.perf_counter()
-    _, _, used = oracle.tau00_batch(liz.pos, w.lmax, E, ti, nthreads=cores)
+    tau, _, used = oracle.tau00_batch(liz.pos, w.lmax, E, ti, nthreads=cores)
     dt = time.perf_counter() - t0
-    return {"value": len(items) / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
-            "sample": "%d of the 64 (energy, spin) solves of the n=2160 LIZ, one per thread, %.1f s" % (len(items), dt)}
+    return ({"value": len(items) / dt, "unit": UNIT, "cores": int(used), "kind": "oracle",
+             "sample": "%d of the 64 (energy, spin) solves of the n=2160 LIZ, one per thread, %.1f s"
+                       % (len(items), dt)}, items, tau)
 
 
 def run_reference(args):
@@ -765,7 +827,7 @@ def run_reference(args):
     times = []
     solves = 0
     for _ in range(args.steps):
-        c = cpu_baseline(w, cores)
+        c = cpu_baseline(w, cores)[0]
         solves += cores
         times.append(cores / c["value"])
     total = sum(times)
@@ -796,7 +858,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0)
     ap.add_argument("--workload", default="liz135",
-                    choices=["liz135", "supercell", "warmstart", "cusolver", "canted", "paper", "charge"],
+                    choices=["liz135", "supercell", "warmstart", "cusolver", "canted", "paper", "charge", "peaks"],
                     help="liz135: the benchmark workload; supercell: per-site LIZs of the 256-site supercell "
                          "with vacancies (uneven n), batched and replayed as a captured plan")
     ap.add_argument("--n-lizs", type=int, default=32, help="supercell / warmstart mode: evaluation LIZs")
@@ -833,6 +895,8 @@ def main():
         run_paper_shapes(args)
     elif args.workload == "charge":
         run_site_charge(args)
+    elif args.workload == "peaks":
+        run_peaks(args)
     else:
         run_ours(args)
 

@@ -347,6 +347,19 @@ must_status must_tau00_solve_seeded(const must_liz* liz, int32_t nE, const doubl
  * NULL), clears them and returns the number of phases.  must_launch_count
  * returns the number of kernels this library has launched in the process.
  */
+/*
+ * Arithmetic peak probe (instrumentation, not part of the paper's method):
+ * one launch of `blocks` CTAs of 256 threads keeping every lane busy with
+ * independent chains of one instruction kind for `iters` iterations: kind 0
+ * DFMA (a 4 x 4 register block, 16 chains per thread), 1 DMMA (mma.sync
+ * m8n8k4 f64, 8 accumulators per warp), 2 FFMA (8 chains per thread).  sink: device memory of
+ * blocks x 256 doubles (read for the chains' start values, overwritten with
+ * their results).  *flops (host) receives the flops the launch performs; the
+ * caller times the launch on `stream` and divides.  Errors: MUST_EINVAL
+ * (kind, sizes, NULL or host sink), MUST_ECUDA.
+ */
+must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double* sink, double* flops, void* stream);
+
 void must_profile_enable(int on);
 int must_profile_read(double* ms, long long* launches, long long* items, int n_phases);
 long long must_launch_count(void);

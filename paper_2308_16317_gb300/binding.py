@@ -83,6 +83,7 @@ def load():
         "must_profile_enable": (None, [ctypes.c_int]),
         "must_profile_read": (ctypes.c_int, [P, P, P, ctypes.c_int]),
         "must_launch_count": (ctypes.c_longlong, []),
+        "must_peak_probe": (I32, [I32, I32, ctypes.c_int64, P, ctypes.POINTER(D), P]),
         "must_phase_name": (ctypes.c_char_p, [ctypes.c_int]),
         "must_status_string": (ctypes.c_char_p, [I32]),
         "must_last_error": (ctypes.c_char_p, []),
@@ -105,7 +106,8 @@ def exported_symbols():
                         "must_mlp_create", "must_mlp_free", "must_mlp_param_count", "must_mlp_get_params",
                         "must_mlp_set_params", "must_mlp_forward", "must_mlp_gradients", "must_mlp_train_step",
                         "must_mlp_save", "must_mlp_load", "must_mlp_features", "must_mlp_apply", "must_mlp_targets",
-                        "must_tau00_solve_seeded", "must_contour_weights", "must_site_charge", "must_site_density")]
+                        "must_tau00_solve_seeded", "must_contour_weights", "must_site_charge", "must_site_density",
+                        "must_peak_probe")]
 
 
 def _ptr(a):
@@ -158,6 +160,13 @@ def must_profile_read():
 
 def must_launch_count() -> int:
     return int(load().must_launch_count())
+
+
+def must_peak_probe(kind: int, blocks: int, iters: int, sink, stream=None) -> float:
+    """Launch one arithmetic peak probe (0 DFMA, 1 DMMA, 2 FFMA); returns its flop count."""
+    fl = ctypes.c_double(0.0)
+    _check(load().must_peak_probe(kind, blocks, iters, _ptr(sink), ctypes.byref(fl), _stream(stream)))
+    return fl.value
 
 
 def must_default_opts(precision: int = MUST_FP64, **kw) -> must_solve_opts:
