@@ -43,7 +43,7 @@ def emit(line):
 
 UNIT = "solves/s"
 PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
-RES = {"fp64": 0, "df": 1, "int": 2}
+RES = {"fp64": 0, "df": 1, "int": 2, "tc": 3}
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (profiling recipe); DFMA/DMMA microbenchmark: 1.01-1.05
 FP32_PEAK_TFLOPS = 80.5      # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (measured FFMA: 75)
 FP32_INSTR_PEAK = 40.3       # T FP32 instructions/s: 152 SMs x 128 lanes x 2.07 GHz
@@ -174,6 +174,10 @@ def phase_work(phase: str, n: int, kap: int, nb: int, items: int, precision: str
             macs += m * m * nbe
         return macs * 8 * items, "flop", "alu", "paper_2308_16317_gb300/csrc/lu64.cu", "gemm64_kernel_fcc135"
     if phase == "residual":
+        if residual == "tc":
+            # tensor-core digit split: bound by one read of M's double-float copy (16 B per element)
+            return 16.0 * n * n * items, "byte", "hbm", "paper_2308_16317_gb300/csrc/tc_residual.cu", \
+                "residual_tc_kernel_fcc135"
         return 8.0 * n * n * kap * items, "flop", "alu", "paper_2308_16317_gb300/csrc/mixed.cu", \
             {"df": "residual_df_kernel_fcc135", "int": "residual_int_kernel_fcc135"}.get(residual,
                                                                                        "residual64_kernel_fcc135")
@@ -384,7 +388,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else "%s+f32 factors, %s residual, f64 solution" % (
-                prec, {"fp64": "f64", "df": "double-float", "int": "split-integer"}[args.residual]),
+                prec, {"fp64": "f64", "df": "double-float", "int": "split-integer",
+                       "tc": "tensor-core digit-split"}[args.residual]),
             "data": "synthetic (seeded fcc 50/50 random alloy, square-well t-matrices)",
             "config": {"workload": "fcc135 LIZ, lmax=3, n=2160, 32 contour energies x 2 spins = 64 tau_00 solves/step",
                        "n": n, "n_liz": int(w.lizs[0].n_sites), "lmax": w.lmax, "solves_per_step": items,
@@ -852,8 +857,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
-    ap.add_argument("--residual", default="int", choices=list(RES),
-                    help="refinement residual: FP64 (DFMA), double-float FP32 pairs, or split-integer")
+    ap.add_argument("--residual", default="tc", choices=list(RES),
+                    help="refinement residual: FP64 (DFMA), double-float FP32 pairs, split-integer, or the "
+                         "tensor-core digit split (default)")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0)

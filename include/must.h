@@ -71,9 +71,17 @@ typedef struct {
   int32_t warm_start;     /* reserved for the learned seed; 0 = cold solve           */
   int32_t deterministic;  /* 1 = static schedule in batched launches                 */
   int32_t equilibrate;    /* 1 = symmetric |diag M|^{-1/2} scaling before low-prec LU */
-  int32_t residual;       /* mixed paths: 0 = FP64 residual (DFMA); 1 = residual in
-                             double-float (unevaluated FP32 pairs, ~48-bit, on the
-                             FP32 pipes, ~6x the GB300 FP64 rate)                 */
+  int32_t residual;       /* mixed paths: how R = E0 - M X is formed (all ~2^-47 of
+                             the row scale or better):
+                             0 = FP64 (DFMA);
+                             1 = double-float (unevaluated FP32 pairs, FP32 pipes);
+                             2 = split-integer (leading 23 bits of M and X as
+                                 integers, exact 64-bit products, FP32 remainders);
+                             3 = tensor cores: M and X split into six fixed-point
+                                 BF16 digits, digit products on tcgen05 with FP32
+                                 accumulation that is exact over 128-element K
+                                 chunks, chunks combined in integers (Ozaki-style
+                                 error-free split); the diagonal entry in FP64.  */
 } must_solve_opts;
 
 typedef struct must_liz must_liz;   /* opaque, immutable after build */

@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 
 #include "mixed.h"
+#include "tc_residual.h"
 #include "tc_gemm.h"
 #include "prof.h"
 
@@ -1234,7 +1235,8 @@ size_t mixed_item_bytes(int n, int ld, int kap) {
          + a256(size_t(n) * kap * 32)      // X split for the residual (double-float pairs or XQ)
          + a256(size_t(n) * 4)             // row exponents (split-integer residual)
          + a256(size_t(kap) * 4)           // column exponents (split-integer residual)
-         + RES_SPLIT * a256(size_t(n) * kap * 16)   // split-K residual partials
+         + a256(std::max(RES_SPLIT * size_t(n) * kap * 16,   // split-K residual partials, or the
+                         tc_residual_b_bytes(n, kap)))        // digit tiles of the tensor-core residual
          + a256(size_t(kap) * kap * 16)    // Sinv
          + a256(size_t(64) * 64 * 8)       // inverse of the panel's L11
          + 1536                            // norms, previous norms, conv, error word, two seed flag
@@ -1257,7 +1259,8 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   XQ* Xq = reinterpret_cast<XQ*>(Xsplit);
   int* rexp = reinterpret_cast<int*>(take(size_t(items) * n * 4));
   int* fexp = reinterpret_cast<int*>(take(size_t(items) * kap * 4));
-  float4* Rpart = reinterpret_cast<float4*>(take(size_t(RES_SPLIT) * items * n * kap * 16));
+  float4* Rpart = reinterpret_cast<float4*>(
+      take(std::max(size_t(RES_SPLIT) * n * kap * 16, tc_residual_b_bytes(n, kap)) * items));
   double2* Sinv = reinterpret_cast<double2*>(take(size_t(items) * kap * kap * 16));
   float2* Linv = reinterpret_cast<float2*>(take(size_t(items) * 64 * 64 * 8));
   double* norms = reinterpret_cast<double*>(take(size_t(items) * 16));
@@ -1388,7 +1391,13 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   const int iters = std::max(c.opts.max_iter, 0);
   const bool seeded = c.seed && c.seed_mask;
   // double-float residual with RES_SPLIT K splits and the in-order reduction
+  bool res_ok = true;
   auto launch_residual_df = [&](const int* mask, unsigned long long* work, int phase) {
+    if (c.opts.residual == 3) {
+      res_ok = res_ok && tc_residual(reinterpret_cast<const float4*>(c.M64), stride, ld, n, kap, items, rexp, fexp, X,
+                                     R, Rpart, mask, err, work, st);
+      return;
+    }
     const dim3 g(gres.x, items, RES_SPLIT);
     if (c.opts.residual == 2)
       residual_int_kernel<RES_CPT><<<g, 64 * ((kap + RES_CPT - 1) / RES_CPT), size_t(64) * kap * sizeof(XQ), st>>>(
@@ -1403,6 +1412,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   };
   // X split for the residual: double-float pairs, or integer + FP32 remainder
   auto launch_split_x = [&](const int* mask) {
+    if (c.opts.residual == 3) return;   // the tensor-core residual splits X itself
     if (c.opts.residual == 2) {
       split_xq_kernel<<<dim3(kap, items), 256, 0, st>>>(X, n, kap, Xq, fexp, mask);
     } else {
@@ -1410,7 +1420,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       split_x_kernel<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(X, Xdf, cnt, mask, size_t(n) * kap);
     }
   };
-  if (c.opts.residual == 2) {   // row exponents of M for the split-integer residual
+  if (c.opts.residual >= 2) {   // row exponents of M for the split-integer and tensor-core residuals
     ProfScope ps(PH_RESIDUAL, st);
     row_exp_kernel<<<dim3((n + 31) / 32, items), dim3(32, 8), 0, st>>>(reinterpret_cast<const float4*>(c.M64), stride, ld,
                                                                  n, rexp);
@@ -1469,6 +1479,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       prof_launched(PH_OTHER, 1);
     }
   }
+  if (!res_ok) return MUST_ECUDA;
   if (iters == 0)   // no refinement allowed: the unrefined low-precision result is reported as not converged
     check_kernel<<<(items + 127) / 128, 128, 0, st>>>(norms, prevn, conv, c.status, items, 0.0, 2);
   output_kernel<<<items, 256, 0, st>>>(X, n, kap, c.tau, c.out_index, c.status, c.status_out, err);

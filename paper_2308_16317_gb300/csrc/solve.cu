@@ -59,7 +59,7 @@ Layout make_layout(const must_liz* z, int nE, int nspin, int n_species, int prec
 int check_opts(const must_solve_opts* o) {
   if (o->precision < MUST_FP64 || o->precision > MUST_MIXED_TF32X3) return 0;
   if (o->precision != MUST_FP64 && (o->max_iter < 0 || !(o->tol > 0.0))) return 0;
-  if (o->residual < 0 || o->residual > 2) return 0;
+  if (o->residual < 0 || o->residual > 3) return 0;
   return 1;
 }
 

@@ -43,7 +43,7 @@ def test_lmax4_small_vs_oracle(B, orc, canted):
     ref, _ = oracle_tau(orc, w, nthreads=ncpu())
     # FP64, and the mixed path with the double-float and the split-integer
     # residual (kap = 50 canted: the widest residual CTA)
-    for precision, tol, residual in ((0, 1e-11, 1), (1, 1e-9, 1), (1, 1e-9, 2)):
+    for precision, tol, residual in ((0, 1e-11, 1), (1, 1e-9, 1), (1, 1e-9, 2), (1, 1e-9, 3)):
         tau, st = _tau(B, w, precision, residual=residual)
         assert (st == 0).all()
         err = rel_fro(tau.reshape(-1, k, k), ref)
