@@ -223,3 +223,15 @@ def cocrfemnni135_canted(seed: int = SEED_BASE + 7, n_e: int = 8) -> Workload:
     dirs = random_unit_vectors(rng, pos.shape[0])
     return Workload("cocrfemnni135_lmax4_canted", 4, [Liz(pos, species, dirs)], semicircle_contour(n_e),
                     _depths(5, 2), R_MT, canted=True)
+
+
+def niau249_canted(seed: int = SEED_BASE + 8, n_e: int = 8) -> Workload:
+    """Ni30Au70-shaped LIZ with spin canting: 249 sites (fcc shells 1-12),
+    lmax = 4, random moment directions, canted rank 2n = 12450 (the paper's
+    largest rank, Sec. 4.1); contour nodes unclamped."""
+    rng = np.random.default_rng(seed)
+    pos, _ = fcc_cluster(12)
+    species = (rng.random(pos.shape[0]) >= 0.3).astype(np.int32)   # 0 = Ni, 1 = Au
+    dirs = random_unit_vectors(rng, pos.shape[0])
+    return Workload("niau249_lmax4_canted", 4, [Liz(pos, species, dirs)], semicircle_contour(n_e),
+                    _depths(2, 2), R_MT, canted=True)
