@@ -357,6 +357,8 @@ struct AsmArgs {
   int items_per_e;        // nspin (collinear) or 1 (canted)
   int scale64;            // 1: the FP64 copy is equilibrated too (D M D)
   int m64_df;             // 1: the M64 buffer holds M as FP32 pairs (hi.re, hi.im, lo.re, lo.im)
+  int* rowmax;            // NULL or [item][n]: atomic max of the float bits of max(|hi.re|, |hi.im|) over
+                          // the off-diagonal entries of each row (needs the double-float split)
 };
 
 // M_aa of item `it` at row a (for the equilibration scale); 1 on padding sites.
@@ -471,9 +473,12 @@ constexpr int PAIRS_PER_BLOCK = 64;
 
 __host__ __device__ inline int asm_pair_blocks(int n_pairs) { return (n_pairs + PAIRS_PER_BLOCK - 1) / PAIRS_PER_BLOCK; }
 
+__device__ __forceinline__ int absmax_bits(float4 f) { return __float_as_int(fmaxf(fabsf(f.x), fabsf(f.y))); }
+
 __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
   __shared__ cd wsh[8][MUST_MAX_NL2];
   __shared__ cd hsh[PAIRS_PER_BLOCK][2 * MUST_MAX_LMAX + 1];
+  __shared__ int rmx[8][MUST_MAX_NL];   // per warp: row maxima of the current pair block (float bits)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int el = blockIdx.y;
   const int lz = blockIdx.z;
@@ -514,6 +519,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
         const double y = Lz.pair_Y[size_t(unit) * A.nL2 + L2];
         wsh[warp][L2] = y * hsh[pi][l_of(L2)];
       }
+      if (lane < nL) rmx[warp][lane] = 0;
       __syncwarp();
       const int p = pq.x + off, q = pq.y + off;
       for (int ent = lane; ent < nL * nL; ent += 32) {
@@ -531,6 +537,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
         const cd vt = odd ? -v : v;
         const float4 f = need_df(A) ? split_cd(v) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 ft = odd ? make_float4(-f.x, -f.y, -f.z, -f.w) : f;
+        if (A.rowmax) atomicMax(&rmx[warp][L], absmax_bits(f));
         const cd z0 = mk(0.0, 0.0);
         const float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int ii = 0; ii < A.items_per_e; ++ii) {
@@ -547,6 +554,19 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
             }
           }
         }
+      }
+      __syncwarp();
+      if (A.rowmax && lane < nL) {
+        // row L of block (p, q) and row L of its transpose (q, p) have the same entries up to sign
+        const int m = rmx[warp][lane];
+        if (m > 0)
+          for (int ii = 0; ii < A.items_per_e; ++ii) {
+            int* rm = A.rowmax + size_t(item_of(ii)) * A.n;
+            for (int s = 0; s < (A.canted ? 2 : 1); ++s) {
+              atomicMax(rm + p * kap + s * nL + lane, m);
+              atomicMax(rm + q * kap + s * nL + lane, m);
+            }
+          }
       }
       __syncwarp();
     }
@@ -586,6 +606,10 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
             v = hd * sig;
             if (sa == sb) v = v + hs;
           }
+        }
+        if (A.rowmax && a != b && A.canted) {   // spin-coupling entries of the site block
+          const int m = absmax_bits(split_cd(v));
+          if (m > 0) atomicMax(A.rowmax + size_t(it) * A.n + p * kap + a, m);
         }
         store_elem(A, it, p * kap + a, p * kap + b, v);
       }
@@ -632,6 +656,13 @@ void launch_assemble(const AsmArgs& A, int max_units, cudaStream_t st) {
   }
   dim3 grid((max_units + 7) / 8, A.nEc, A.n_lz);
   const size_t smem = size_t(A.g_nnz) * 12 + size_t(A.nL * A.nL + 1) * 4;
+  // the Gaunt table of lmax = 4 (29 KB) plus the static buffers pass the
+  // 48 KB that a launch gets without opting in
+  static size_t smem_set = 0;
+  if (smem > smem_set) {
+    cudaFuncSetAttribute(assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    smem_set = smem;
+  }
   assemble_kernel<<<grid, 256, smem, st>>>(A);
   prof_launched(PH_ASSEMBLE, 1, n_items);
 }
@@ -659,6 +690,7 @@ void launch_assemble_chunk(const AsmChunk& c, cudaStream_t st) {
   A.items_per_e = z0->canted ? 1 : c.nspin;
   A.scale64 = c.scale64;
   A.m64_df = c.m64_df;
+  A.rowmax = (c.rowmax && (c.M32 || c.m64_df)) ? c.rowmax : nullptr;
   if (any_pad) {   // padding sites: zero their coupling blocks first
     const size_t items = size_t(A.items_per_e) * c.nEc * c.n_lz;
     if (c.M64) cudaMemsetAsync(c.M64, 0, items * c.stride * 16, st);

@@ -677,27 +677,15 @@ struct __align__(16) XQ {
   float sr, si, xr, xi;  // sigma and X~ (FP32)
 };
 
-__global__ void __launch_bounds__(256) row_exp_kernel(const float4* __restrict__ M0, size_t stride, int ld, int n,
-                                                      int* __restrict__ ex0) {
-  // 32 rows per CTA (threadIdx.x), the columns split over 8 groups (threadIdx.y)
-  __shared__ float red[8][33];
-  const int item = blockIdx.y;
-  const int i = blockIdx.x * 32 + threadIdx.x;
-  const int ic = min(i, n - 1);
-  const float4* M = M0 + size_t(item) * stride + ic;
-  float mx = 0.f;
-#pragma unroll 4
-  for (int k = threadIdx.y; k < n; k += 8) {
-    const float4 v = M[size_t(k) * ld];
-    if (k != ic) mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
-  }
-  red[threadIdx.y][threadIdx.x] = mx;
-  __syncthreads();
-  if (threadIdx.y == 0 && i < n) {
-    for (int g = 1; g < 8; ++g) mx = fmaxf(mx, red[g][threadIdx.x]);
-    const int e = (mx > 0.f && mx <= 3.0e38f) ? ilogbf(mx) + 2 : 0;
-    ex0[size_t(item) * n + i] = min(max(e, -90), 120);
-  }
+// Row exponents from the row maxima the assembly recorded (float bits of the
+// largest off-diagonal |hi| of the row): e_i = ilogb(max) + 2, so that
+// |M_ik| < 2^(e_i - 1); 0 for an empty row.  In place.
+__global__ void row_exp_from_max_kernel(int* __restrict__ ex, size_t count) {
+  const size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const float mx = __int_as_float(ex[t]);
+  const int e = (mx > 0.f && mx <= 3.0e38f) ? ilogbf(mx) + 2 : 0;
+  ex[t] = min(max(e, -90), 120);
 }
 
 // One block per (column c, item): f_c, then X~ = X 2^(23 - f_c) split into
@@ -1276,7 +1264,17 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   a.M32 = M32;
   a.scale = scale;
   a.scale32 = scale32;
+  // row scales of the split-integer and tensor-core residuals: the assembly
+  // records each row's largest off-diagonal |hi| (one pass over M saved)
+  a.rowmax = (c.opts.residual >= 2) ? rexp : nullptr;
+  if (a.rowmax) cudaMemsetAsync(rexp, 0, size_t(items) * n * 4, st);
   launch_assemble_chunk(a, st);
+  if (a.rowmax) {
+    ProfScope ps(PH_ASSEMBLE, st);
+    const size_t cnt = size_t(items) * n;
+    row_exp_from_max_kernel<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(rexp, cnt);
+    prof_launched(PH_ASSEMBLE, 1);
+  }
   cudaMemsetAsync(norms, 0, sizeof(double) * 2 * items, st);
   cudaMemsetAsync(prevn, 0, sizeof(double) * items, st);
   cudaMemsetAsync(conv, 0, sizeof(int) * items, st);
@@ -1420,12 +1418,6 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       split_x_kernel<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(X, Xdf, cnt, mask, size_t(n) * kap);
     }
   };
-  if (c.opts.residual >= 2) {   // row exponents of M for the split-integer and tensor-core residuals
-    ProfScope ps(PH_RESIDUAL, st);
-    row_exp_kernel<<<dim3((n + 31) / 32, items), dim3(32, 8), 0, st>>>(reinterpret_cast<const float4*>(c.M64), stride, ld,
-                                                                 n, rexp);
-    prof_launched(PH_RESIDUAL, 1);
-  }
   if (seeded) {
     // X = X^ from the predicted tau_00, R = E0 - M X^ for seeded items, gate
     ProfScope ps(PH_OTHER, st);

@@ -157,6 +157,7 @@ static must_status solve_group(const must_liz* const* lz, const int* liz_global,
     return MUST_ENOMEM;
   }
   AsmChunk c;
+  c.rowmax = nullptr;
   c.n = n; c.nE = nE; c.nspin = nspin; c.n_species = n_species; c.E = E_dev; c.tinv = tinv_dev;
   ChunkIndex ci;
   ci.ipe = ipe; ci.nE = nE; ci.n_out = n_out;

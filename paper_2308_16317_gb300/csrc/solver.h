@@ -33,6 +33,8 @@ struct AsmChunk {
   float* scale32;   // FP32 copy of scale (mixed path; NULL otherwise)
   int scale64;      // equilibrate the FP64 copy as well (FP64 path)
   int m64_df;       // store the unscaled matrix as FP32 pairs (double-float residual)
+  int* rowmax;      // NULL, or [item][n] zeroed ints that receive (atomic max) the bits of the largest
+                    // |hi.re|, |hi.im| of each row without its diagonal entry (row scales of the residual)
 };
 void launch_assemble_chunk(const AsmChunk& c, cudaStream_t st);
 

@@ -3,8 +3,9 @@ written by tests/golden/make_golden.py, which calls only the CPU oracle).
 
 Orders 4320 (spin-canted 135-site LIZ, Im E down to 0.00215), 6225 (NiAu-
 shaped, Sec. 4.1), 6750 and 12450 (CoCrFeMnNi- and NiAu-shaped canted,
-Sec. 4.1): the plain FP64 path and the mixed path in the benchmark's
-configuration (BF16x3 factors, split-integer residual) against the oracle,
+Sec. 4.1): the plain FP64 path and the mixed path (BF16x3 factors) with the
+split-integer and with the tensor-core residual (the benchmark's
+configuration) against the oracle,
 per item, by relative Frobenius error: <= 1e-11 (FP64), <= 1e-9 (mixed).
 The CPU test checks that the generator still produces the stored inputs.
 """
@@ -65,13 +66,14 @@ def B():
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("path", ["fp64", "mixed_int"])
+@pytest.mark.parametrize("path", ["fp64", "mixed_int", "mixed_tc"])
 def test_large_orders_vs_oracle_golden(B, case, path):
     import torch
     from paper_2308_16317_gb300.runner import Session, blocks_to_numpy
     g = _load(case)
     w, sub, e_idx = _workload(g)
-    opts = B.must_default_opts(0) if path == "fp64" else B.must_default_opts(1, residual=2)
+    opts = {"fp64": B.must_default_opts(0), "mixed_int": B.must_default_opts(1, residual=2),
+            "mixed_tc": B.must_default_opts(1, residual=3)}[path]
     s = Session(sub)
     tau, st = s.solve(opts)
     torch.cuda.synchronize()
