@@ -246,7 +246,11 @@ must_status must_site_density(int32_t lmax, int32_t nE, const double* E, const d
  *           trailing update runs, 0 keeps every step on the caller's stream;
  *   knob 5: right-hand sides per CTA of the mixed path's correction solve
  *           (2, 4 or 8; 0, the default, takes the most that fit: 8 up to
- *           order 3200, 4 up to 6400, 2 up to 12800).
+ *           order 3200, 4 up to 6400, 2 up to 12800) when knob 6 is 0;
+ *   knob 6: correction solve kernel: 1 thread-block clusters of 8 CTAs per
+ *           item and group of right-hand sides, the rows of L and U spread
+ *           over the cluster and each solved 32-row block shared through
+ *           distributed shared memory; 0 (default) one CTA per item and group.
  * Process-wide; set them between calls, not while solves are being enqueued.
  */
 must_status must_tune_set(int32_t knob, int32_t value);

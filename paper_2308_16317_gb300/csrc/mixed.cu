@@ -1185,6 +1185,7 @@ thread_local SideStream g_side;
 
 int g_lookahead = 1;   // tuning knob 4
 int g_corr_rhs = 0;    // tuning knob 5 (0: by matrix order)
+int g_corr_cluster = 0;   // tuning knob 6
 
 static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
   int dev = 0;
@@ -1382,7 +1383,8 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       attr = true;
     }
   }
-  if (smem_corr > 200 * 1024) {
+  const bool use_cluster = g_corr_cluster && correct_cluster_rhs(n, kap) > 0;
+  if (!use_cluster && smem_corr > 200 * 1024) {
     must_set_error("matrix order %d too large for the correction kernel", n);
     return MUST_EUNSUPPORTED;
   }
@@ -1451,7 +1453,10 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       ProfScope ps(PH_CORRECT, st);
       const int* ff = (first && seeded) ? first_flags : nullptr;
       unsigned long long* wc = prof_work_counter(PH_CORRECT);
-      if (G == 8)
+      if (use_cluster) {
+        if (!correct_cluster(M32, stride, ld, n, kap, items, perm, scale, Sinv, R, X, norms, conv, first, ff, wc, st))
+          return MUST_ECUDA;
+      } else if (G == 8)
         correct_kernel<8><<<gcorr, 512, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,
                                                          conv, first, ff, wc);
       else if (G == 4)

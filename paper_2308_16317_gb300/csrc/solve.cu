@@ -522,6 +522,10 @@ extern "C" must_status must_tune_set(int32_t knob, int32_t value) {
       }
       g_corr_rhs = value;
       return MUST_OK;
+    case 6:   // correction kernel: 1 = thread-block clusters, 0 = one CTA per item and RHS group
+      if (value != 0 && value != 1) { must_set_error("correction kernel must be 0 or 1"); return MUST_EINVAL; }
+      g_corr_cluster = value;
+      return MUST_OK;
   }
   must_set_error("unknown tuning knob %d", knob);
   return MUST_EINVAL;
@@ -535,6 +539,7 @@ extern "C" int32_t must_tune_get(int32_t knob) {
     case 3: return tc_get_run();
     case 4: return g_lookahead;
     case 5: return g_corr_rhs;
+    case 6: return g_corr_cluster;
   }
   return -1;
 }

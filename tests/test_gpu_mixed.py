@@ -146,3 +146,44 @@ def test_streamed_update_matches_per_tile_kernel(B, orc, case):
         ref, _ = oracle_tau(orc, w, nthreads=ncpu())
         for t in (taus[0], taus[4]):
             assert rel_fro(t.reshape(-1, k, k), ref).max() <= TOLMIX
+
+
+@pytest.mark.parametrize("case", ["fcc13", "ragged387", "canted19", "lmax4_13"])
+def test_cluster_correction_matches_one_cta_correction(B, orc, case):
+    """The correction on thread-block clusters (knob 6 = 1) and on one CTA
+    per item (knob 6 = 0, the default) apply the same substitutions in another
+    summation order: both reach the oracle within the mixed tolerance, and
+    they agree with each other to the refinement tolerance.  The cases cover
+    eliminated widths r = n - kap that are not multiples of the 32-row blocks
+    (117 - 9, 387 - 9, 342 - 18, 325 - 25) and several right-hand-side groups."""
+    rng = np.random.default_rng(3)
+    if case == "fcc13":
+        w = wl.first_shell_small()
+    elif case == "ragged387":
+        pos, _ = wl.fcc_cluster(3)
+        w = wl.Workload(case, 2, [wl.Liz(pos, rng.integers(0, 2, pos.shape[0]).astype(np.int32))],
+                        wl.semicircle_contour(4), wl.spin_depths(2), wl.R_MT)
+    elif case == "canted19":
+        pos, _ = wl.fcc_cluster(2)
+        w = wl.Workload(case, 2, [wl.Liz(pos, rng.integers(0, 2, pos.shape[0]).astype(np.int32),
+                                         wl.random_unit_vectors(rng, pos.shape[0]))],
+                        wl.semicircle_contour(4), wl.spin_depths(2), wl.R_MT, canted=True)
+    else:
+        pos, _ = wl.fcc_cluster(1)
+        w = wl.Workload(case, 4, [wl.Liz(pos, rng.integers(0, 2, pos.shape[0]).astype(np.int32))],
+                        wl.semicircle_contour(3), wl.spin_depths(2), wl.R_MT)
+    k = w.kappa()
+    old = B.must_tune_get(6)
+    try:
+        taus = []
+        for kern in (1, 0):
+            B.must_tune_set(6, kern)
+            tau, st = _gpu_tau(B, w, 1, residual=3)
+            assert (st == 0).all()
+            taus.append(tau.reshape(-1, k, k))
+    finally:
+        B.must_tune_set(6, old)
+    ref, _ = oracle_tau(orc, w, nthreads=ncpu())
+    for t in taus:
+        assert rel_fro(t, ref).max() <= TOLMIX
+    assert rel_fro(taus[0], taus[1]).max() <= TOLMIX
