@@ -629,9 +629,10 @@ def run_canted(args):
 
 def run_paper_shapes(args):
     """The paper's own ranks (Sec. 4.1, lmax = 4): a Ni30Au70-shaped 249-site LIZ
-    (n = 6225, two spins) and a CoCrFeMnNi-shaped canted 135-site LIZ
-    (n = 6750), 8 contour energies each; mixed-precision and plain FP64
-    throughput, and the mixed path's error against the FP64 path."""
+    (n = 6225, two spins), a CoCrFeMnNi-shaped canted 135-site LIZ (n = 6750)
+    and the NiAu-shaped canted 249-site LIZ (n = 12450), 8 contour energies
+    each; mixed-precision and plain FP64 throughput, and the mixed path's
+    error against the FP64 path."""
     import torch
     from paper_2308_16317_gb300 import binding as B
     from paper_2308_16317_gb300 import build as libbuild
@@ -640,7 +641,9 @@ def run_paper_shapes(args):
     libbuild.build()
     B.load()
     res = {}
-    for name, w in (("niau249_n6225", wl.niau249(n_e=8)), ("cocrfemnni135_canted_n6750", wl.cocrfemnni135_canted(n_e=8))):
+    shapes = [("niau249_n6225", wl.niau249(n_e=8)), ("cocrfemnni135_canted_n6750", wl.cocrfemnni135_canted(n_e=8)),
+              ("niau249_canted_n12450", wl.niau249_canted(n_e=8))]
+    for name, w in shapes:
         s = Session(w)
         items = len(w.energies) * (1 if w.canted else s.nspin)
         out = s.alloc_out(1)
