@@ -247,10 +247,13 @@ must_status must_site_density(int32_t lmax, int32_t nE, const double* E, const d
  *   knob 5: right-hand sides per CTA of the mixed path's correction solve
  *           (2, 4 or 8; 0, the default, takes the most that fit: 8 up to
  *           order 3200, 4 up to 6400, 2 up to 12800) when knob 6 is 0;
- *   knob 6: correction solve kernel: 1 thread-block clusters of 8 CTAs per
- *           item and group of right-hand sides, the rows of L and U spread
- *           over the cluster and each solved 32-row block shared through
- *           distributed shared memory; 0 (default) one CTA per item and group.
+ *   knob 6: correction solve kernel: 1 (default) thread-block clusters of
+ *           CTAs per item and group of right-hand sides, the rows of L and U
+ *           spread over the cluster and each solved 32-row block shared
+ *           through distributed shared memory; 0 one CTA per item and group;
+ *   knob 7: preferred CTAs per cluster of that kernel (2, 4 or 8, default 2;
+ *           a larger cluster is taken when the rows do not fit its shared
+ *           memory).
  * Process-wide; set them between calls, not while solves are being enqueued.
  */
 must_status must_tune_set(int32_t knob, int32_t value);

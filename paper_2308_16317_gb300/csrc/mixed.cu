@@ -1185,7 +1185,7 @@ thread_local SideStream g_side;
 
 int g_lookahead = 1;   // tuning knob 4
 int g_corr_rhs = 0;    // tuning knob 5 (0: by matrix order)
-int g_corr_cluster = 0;   // tuning knob 6
+int g_corr_cluster = 1;   // tuning knob 6
 
 static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
   int dev = 0;

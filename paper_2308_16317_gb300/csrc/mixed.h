@@ -31,15 +31,19 @@ extern int g_lookahead;
 // Tuning knob 5: right-hand sides per CTA of the correction solve (2, 4 or 8;
 // 0 = the most that fit: 8 up to order 3200, 4 up to 6400, else 2).
 extern int g_corr_rhs;
-// Tuning knob 6: 1 runs the correction solve on thread-block clusters
-// (correct_cluster.cu), 0 (default) on one CTA per item and RHS group.
+// Tuning knob 6: 1 (default) runs the correction solve on thread-block
+// clusters (correct_cluster.cu), 0 on one CTA per item and RHS group.
 extern int g_corr_cluster;
 
-// Correction delta = D U^{-1} L^{-1} P (D R), X += delta, on clusters of 8
-// CTAs per item and group of right-hand sides (correct_cluster.cu).  Same
+// Correction delta = D U^{-1} L^{-1} P (D R), X += delta, on clusters of
+// CTAs (knob 7) per item and group of right-hand sides (correct_cluster.cu).  Same
 // arguments as the one-CTA kernel; false (with must_set_error) if the order
 // is too large for its shared memory or the launch failed.
 int correct_cluster_rhs(int n, int kap);
+// Tuning knob 7: preferred CTAs per cluster of the cluster correction (2, 4
+// or 8; a larger one is taken when the rows do not fit).
+bool correct_cluster_set_ctas(int ctas);
+int correct_cluster_get_ctas();
 bool correct_cluster(const float2* A, size_t stride, int ld, int n, int kap, int items, const int* perm,
                      const double* scale, const double2* Sinv, const double2* R, double2* X, double* norms,
                      const int* conv, int first_all, const int* first_flags, unsigned long long* work,

@@ -526,6 +526,9 @@ extern "C" must_status must_tune_set(int32_t knob, int32_t value) {
       if (value != 0 && value != 1) { must_set_error("correction kernel must be 0 or 1"); return MUST_EINVAL; }
       g_corr_cluster = value;
       return MUST_OK;
+    case 7:   // CTAs per cluster of the cluster correction
+      if (!correct_cluster_set_ctas(value)) { must_set_error("cluster CTAs must be 2, 4 or 8"); return MUST_EINVAL; }
+      return MUST_OK;
   }
   must_set_error("unknown tuning knob %d", knob);
   return MUST_EINVAL;
@@ -540,6 +543,7 @@ extern "C" int32_t must_tune_get(int32_t knob) {
     case 4: return g_lookahead;
     case 5: return g_corr_rhs;
     case 6: return g_corr_cluster;
+    case 7: return correct_cluster_get_ctas();
   }
   return -1;
 }

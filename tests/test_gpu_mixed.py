@@ -150,8 +150,8 @@ def test_streamed_update_matches_per_tile_kernel(B, orc, case):
 
 @pytest.mark.parametrize("case", ["fcc13", "ragged387", "canted19", "lmax4_13"])
 def test_cluster_correction_matches_one_cta_correction(B, orc, case):
-    """The correction on thread-block clusters (knob 6 = 1) and on one CTA
-    per item (knob 6 = 0, the default) apply the same substitutions in another
+    """The correction on thread-block clusters of 2, 4 or 8 CTAs (knob 6 = 1,
+    the default, and knob 7) and on one CTA per item (knob 6 = 0) apply the same substitutions in another
     summation order: both reach the oracle within the mixed tolerance, and
     they agree with each other to the refinement tolerance.  The cases cover
     eliminated widths r = n - kap that are not multiples of the 32-row blocks
@@ -173,17 +173,20 @@ def test_cluster_correction_matches_one_cta_correction(B, orc, case):
         w = wl.Workload(case, 4, [wl.Liz(pos, rng.integers(0, 2, pos.shape[0]).astype(np.int32))],
                         wl.semicircle_contour(3), wl.spin_depths(2), wl.R_MT)
     k = w.kappa()
-    old = B.must_tune_get(6)
+    old = (B.must_tune_get(6), B.must_tune_get(7))
     try:
         taus = []
-        for kern in (1, 0):
+        for kern, ctas in ((0, 4), (1, 2), (1, 4), (1, 8)):
             B.must_tune_set(6, kern)
+            B.must_tune_set(7, ctas)
             tau, st = _gpu_tau(B, w, 1, residual=3)
             assert (st == 0).all()
             taus.append(tau.reshape(-1, k, k))
     finally:
-        B.must_tune_set(6, old)
+        B.must_tune_set(6, old[0])
+        B.must_tune_set(7, old[1])
     ref, _ = oracle_tau(orc, w, nthreads=ncpu())
     for t in taus:
         assert rel_fro(t, ref).max() <= TOLMIX
-    assert rel_fro(taus[0], taus[1]).max() <= TOLMIX
+    for t in taus[1:]:
+        assert rel_fro(t, taus[0]).max() <= TOLMIX
