@@ -874,8 +874,9 @@ def main():
     ap.add_argument("--chunk-lizs", type=int, default=2,
                     help="supercell: workspace for this many LIZs per launch (more LIZs share launches; "
                          "2 measured 5%% faster than 1, 4 no faster than 2)")
-    ap.add_argument("--train-lizs", type=int, default=400,
-                    help="warmstart mode: random 135-site training LIZs (x 2 spins x 15 predicted points)")
+    ap.add_argument("--train-lizs", type=int, default=1667,
+                    help="warmstart mode: random 135-site training LIZs (x 2 spins x 15 predicted points; "
+                         "1667 LIZs give the 50k training samples of the design)")
     ap.add_argument("--tune", action="append", default=[], metavar="KNOB=VALUE",
                     help="set a library knob (must_tune_set) before the run; recorded in the JSON line")
     ap.add_argument("--n-energies", type=int, default=32,

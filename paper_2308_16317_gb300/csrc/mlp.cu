@@ -3,9 +3,11 @@
 // tau_00 at the neighbouring contour energies and the LIZ's species
 // occupancy.  BF16 weights for the products, FP32 accumulation, FP32 master
 // weights and Adam moments; every pass is a hand-written kernel:
-//   gemm_kernel        C = op(A) op(B) with arbitrary strides (covers the
-//                      forward products, the data gradients and the weight
-//                      gradients), fused bias / SiLU / SiLU' epilogues
+//   mlp_tc_gemm_kernel C = op(A) op(B) on the tcgen05 tensor cores (3xTF32
+//                      splits packed K-major by tf32_pack_kernel from
+//                      arbitrary strides; covers the forward products, the
+//                      data gradients and the weight gradients), fused bias /
+//                      SiLU / SiLU' epilogues
 //   colsum_kernel      bias gradients
 //   mse_kernel         loss and dL/dy
 //   adam_kernel        Adam (Kingma & Ba) on the master weights, refreshes
@@ -14,6 +16,7 @@
 //   apply_kernel       tau^ = interpolation + scale * y
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <random>
@@ -21,6 +24,8 @@
 
 #include "common.cuh"
 #include "prof.h"
+#include "tc_gemm.h"
+#include "tc_ptx.cuh"
 
 struct must_mlp {
   int I, H, O, max_batch;
@@ -33,6 +38,9 @@ struct must_mlp {
   float* act;            // activations: z1 h1 z2 h2 y dy dh
   double* loss;          // device scalar
   long long step;
+  float* pk;             // tensor-core operand packs: A_hi A_lo [pa floats each], B_hi B_lo [pb floats each]
+  size_t pa, pb;
+  int* err;              // device word raised when a bounded wait of the product kernel runs out
 };
 
 namespace {
@@ -54,60 +62,167 @@ __device__ __forceinline__ float dsilu_f(float z) {
 
 enum { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_SILU = 2, EPI_DSILU = 3 };
 
-// C[m][n] = sum_k A(m,k) B(k,n), A(m,k) = A[m*ars + k*acs], B(k,n) = B[k*brs + n*bcs].
-// 64x64 tiles, 256 threads, 4x4 outputs per thread, K in chunks of 16.
-template <typename TA, typename TB>
-__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const TA* __restrict__ A, long ars, long acs,
-                                                   const TB* __restrict__ B, long brs, long bcs, float* __restrict__ C,
-                                                   long ldc, int epi, const float* __restrict__ bias,
-                                                   float* __restrict__ aux, long ldaux) {
-  __shared__ float As[16][65];
-  __shared__ float Bs[16][65];
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int t = tid; t < 16 * 64; t += 256) {
-      const int kk = t / 64, mm = t % 64;
-      const int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < M && k < K) ? ld_elem(A, size_t(m) * ars + size_t(k) * acs) : 0.f;
-      const int n = n0 + mm;
-      Bs[kk][mm] = (n < N && k < K) ? ld_elem(B, size_t(k) * brs + size_t(n) * bcs) : 0.f;
+// ---------------------------------------------------- tensor-core products --
+// C[m][n] = sum_k A(m,k) B(k,n) (+ epilogue) on tcgen05 with kind::tf32 and
+// FP32 accumulation in tensor memory.  Operands are first packed K-major
+// (row r, K contiguous, zero-padded to 128 x 32 / 64 x 32 tiles) as a TF32
+// pair x = hi + lo (hi = x rounded to TF32, lo = the rest rounded to TF32):
+//   A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi      (3xTF32, ~FP32 accuracy)
+// and the A_hi B_lo product is skipped when B holds the BF16 weights, which
+// TF32 represents exactly (B_lo = 0).
+constexpr int MG_BM = 128, MG_BN = 64, MG_KB = 32;   // tile rows, columns; K elements per stage (128 B)
+constexpr int MG_STAGES = 4;
+constexpr int MG_A_BYTES = MG_BM * 128, MG_B_BYTES = MG_BN * 128;
+constexpr int MG_STAGE_BYTES = 2 * MG_A_BYTES + 2 * MG_B_BYTES;
+constexpr size_t MG_SMEM = size_t(MG_STAGES) * MG_STAGE_BYTES + 1024;
+constexpr int MG_THREADS = 192;                       // producer, MMA issuer, 4 epilogue warps
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// dst_hi / dst_lo [Rp][Kp] (row-major) = TF32 split of src(r, k) = src[r rs + k cs]
+// for r < R, k < K; zero in the padding.
+template <typename T>
+__global__ void tf32_pack_kernel(int R, int K, int Rp, int Kp, const T* __restrict__ src, long rs, long cs,
+                                 float* __restrict__ hi, float* __restrict__ lo) {
+  const size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= size_t(Rp) * Kp) return;
+  const int r = int(t / Kp), k = int(t % Kp);
+  const float x = (r < R && k < K) ? ld_elem(src, size_t(r) * rs + size_t(k) * cs) : 0.f;
+  const float h = tf32_rn(x);
+  hi[t] = h;
+  lo[t] = tf32_rn(x - h);
+}
+
+__device__ __forceinline__ void mg_tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          tcptx::smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(tcptx::smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mg_mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+// One CTA per 128 x 64 tile of C.  Warp 0 streams the four operand tiles of
+// each 32-element K step by TMA (4 stages), warp 1 issues the MMAs (four
+// K = 8 instructions per stage and product), warps 2-5 read the accumulator
+// (one TMEM lane quarter each) and apply the epilogue.  Every wait is bounded;
+// on time-out the kernel raises *err, drains its copies and frees its TMEM.
+__global__ void __launch_bounds__(MG_THREADS, 1)
+    mlp_tc_gemm_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+                       const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, int M, int N,
+                       int nks, int three, float* __restrict__ C, long ldc, int epi, const float* __restrict__ bias,
+                       float* __restrict__ aux, long ldaux, int* __restrict__ err) {
+  using namespace tcptx;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[MG_STAGES], empty[MG_STAGES], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * MG_BM, n0 = blockIdx.x * MG_BN;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MG_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
     }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
+    mbar_init(&done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty * 4 + i;
-    if (m >= M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = n0 + tx * 4 + j;
-      if (n >= N) continue;
-      float v = acc[i][j];
-      if (epi == EPI_BIAS || epi == EPI_BIAS_SILU) v += bias[n];
-      if (epi == EPI_BIAS_SILU) {
-        aux[size_t(m) * ldaux + n] = v;
-        v = silu_f(v);
-      } else if (epi == EPI_DSILU) {
-        v *= dsilu_f(aux[size_t(m) * ldaux + n]);
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(MG_BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  volatile int* fail = &s_fail;
+  int issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int ks = 0; ks < nks; ++ks) {
+        const int s = ks % MG_STAGES;
+        if (ks >= MG_STAGES && !mbar_wait_f(&empty[s], ((ks / MG_STAGES) - 1) & 1, fail)) break;
+        uint8_t* st = smem + s * MG_STAGE_BYTES;
+        mbar_expect_tx(&full[s], MG_STAGE_BYTES);
+        mg_tma_load_2d(st, &tAh, ks * MG_KB, m0, &full[s]);
+        mg_tma_load_2d(st + MG_A_BYTES, &tAl, ks * MG_KB, m0, &full[s]);
+        mg_tma_load_2d(st + 2 * MG_A_BYTES, &tBh, ks * MG_KB, n0, &full[s]);
+        mg_tma_load_2d(st + 2 * MG_A_BYTES + MG_B_BYTES, &tBl, ks * MG_KB, n0, &full[s]);
+        ++issued;
       }
-      C[size_t(m) * ldc + n] = v;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // D FP32, A and B TF32, both K-major, N = 64, M = 128
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(MG_BN >> 3) << 17) |
+                             (uint32_t(MG_BM >> 4) << 24);
+      for (int ks = 0; ks < nks; ++ks) {
+        const int s = ks % MG_STAGES;
+        if (!mbar_wait_f(&full[s], (ks / MG_STAGES) & 1, fail)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = smem_u32(smem + s * MG_STAGE_BYTES), al = ah + MG_A_BYTES;
+        const uint32_t bh = ah + 2 * MG_A_BYTES, bl = bh + MG_B_BYTES;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {   // four K = 8 steps of 32 bytes per 128-byte row
+          mg_mma_tf32(tmem, sdesc(ah + 32 * k), sdesc(bh + 32 * k), idesc, (ks > 0 || k > 0) ? 1u : 0u);
+          if (three) mg_mma_tf32(tmem, sdesc(ah + 32 * k), sdesc(bl + 32 * k), idesc, 1u);
+          mg_mma_tf32(tmem, sdesc(al + 32 * k), sdesc(bh + 32 * k), idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&done);
+    }
+  } else {
+    const int quarter = warp & 3;
+    const int m = m0 + quarter * 32 + lane;
+    if (mbar_wait_f(&done, 0, fail)) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int h = 0; h < MG_BN; h += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(h), v);
+        if (m < M) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = n0 + h + j;
+            if (n >= N) continue;
+            float x = __uint_as_float(v[j]);
+            if (epi == EPI_BIAS || epi == EPI_BIAS_SILU) x += bias[n];
+            if (epi == EPI_BIAS_SILU) {
+              aux[size_t(m) * ldaux + n] = x;
+              x = silu_f(x);
+            } else if (epi == EPI_DSILU) {
+              x *= dsilu_f(aux[size_t(m) * ldaux + n]);
+            }
+            C[size_t(m) * ldc + n] = x;
+          }
+        }
+      }
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 32 && !mbar_wait(&done, 0)) s_fail = 1;   // the MMAs have drained
+  if (warp == 0 && lane == 0 && *fail)
+    for (int ks = (issued > MG_STAGES ? issued - MG_STAGES : 0); ks < issued; ++ks)
+      mbar_wait(&full[ks % MG_STAGES], (ks / MG_STAGES) & 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && *fail) atomicExch(err, 1);
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MG_BN));
 }
 
 // out[n] = sum_b d[b][n]
@@ -152,12 +267,38 @@ __global__ void to_bf16_kernel(size_t np, const float* __restrict__ p, __nv_bflo
   if (i < np) wb[i] = __float2bfloat16_rn(p[i]);
 }
 
+size_t rup(size_t x, size_t m) { return (x + m - 1) / m * m; }
+
+// C = A B (+ epilogue) on the tensor cores: A(m,k) = A[m ars + k acs], B(k,n) =
+// B[k brs + n bcs].  b_exact: B holds BF16 values (exact in TF32), so its low
+// TF32 part is zero and the A_hi B_lo product is skipped.
 template <typename TA, typename TB>
-void gemm(int M, int N, int K, const TA* A, long ars, long acs, const TB* B, long brs, long bcs, float* C, long ldc,
-          int epi, const float* bias, float* aux, long ldaux, cudaStream_t st) {
-  dim3 grid((N + 63) / 64, (M + 63) / 64);
-  gemm_kernel<TA, TB><<<grid, 256, 0, st>>>(M, N, K, A, ars, acs, B, brs, bcs, C, ldc, epi, bias, aux, ldaux);
-  prof_launched(PH_OTHER, 1);
+bool gemm(const must_mlp* net, int M, int N, int K, const TA* A, long ars, long acs, const TB* B, long brs, long bcs,
+          float* C, long ldc, int epi, const float* bias, float* aux, long ldaux, bool b_exact, cudaStream_t st) {
+  const int Mp = int(rup(M, MG_BM)), Np = int(rup(N, MG_BN)), Kp = int(rup(K, MG_KB));
+  if (size_t(Mp) * Kp > net->pa || size_t(Np) * Kp > net->pb) return false;
+  float* ah = net->pk;
+  float* al = ah + net->pa;
+  float* bh = al + net->pa;
+  float* bl = bh + net->pb;
+  const size_t na = size_t(Mp) * Kp, nb = size_t(Np) * Kp;
+  tf32_pack_kernel<TA><<<unsigned((na + 255) / 256), 256, 0, st>>>(M, K, Mp, Kp, A, ars, acs, ah, al);
+  tf32_pack_kernel<TB><<<unsigned((nb + 255) / 256), 256, 0, st>>>(N, K, Np, Kp, B, bcs, brs, bh, bl);
+  CUtensorMap mAh, mAl, mBh, mBl;
+  const uint64_t rb = uint64_t(Kp) * 4;
+  if (!tc_encode_2d_sw128(&mAh, 1, ah, Kp, Mp, rb, MG_KB, MG_BM) || !tc_encode_2d_sw128(&mAl, 1, al, Kp, Mp, rb, MG_KB, MG_BM) ||
+      !tc_encode_2d_sw128(&mBh, 1, bh, Kp, Np, rb, MG_KB, MG_BN) || !tc_encode_2d_sw128(&mBl, 1, bl, Kp, Np, rb, MG_KB, MG_BN))
+    return false;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(mlp_tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(MG_SMEM));
+    attr = true;
+  }
+  const dim3 grid(Np / MG_BN, Mp / MG_BM);
+  mlp_tc_gemm_kernel<<<grid, MG_THREADS, MG_SMEM, st>>>(mAh, mAl, mBh, mBl, M, N, Kp / MG_KB, b_exact ? 0 : 1, C, ldc,
+                                                        epi, bias, aux, ldaux, net->err);
+  prof_launched(PH_OTHER, 3);
+  return true;
 }
 
 // activations layout inside act: z1 h1 z2 h2 [B][H] each, y dy [B][O], dh [B][H]
@@ -177,34 +318,41 @@ Act acts(const must_mlp* n) {
   return a;
 }
 
-void forward(const must_mlp* n, int Bn, const float* x, float* y, cudaStream_t st) {
+bool forward(const must_mlp* n, int Bn, const float* x, float* y, cudaStream_t st) {
   const Act a = acts(n);
   const __nv_bfloat16* w = n->wb;
   const float* p = n->p;
   // z1 = x W1^T + b1 ; h1 = silu(z1)     (B(k=i, n=h) = W1[h][i])
-  gemm(Bn, n->H, n->I, x, n->I, 1, w + off_W1(n), 1, n->I, a.h1, n->H, EPI_BIAS_SILU, p + off_b1(n), a.z1, n->H, st);
-  gemm(Bn, n->H, n->H, a.h1, n->H, 1, w + off_W2(n), 1, n->H, a.h2, n->H, EPI_BIAS_SILU, p + off_b2(n), a.z2, n->H, st);
-  gemm(Bn, n->O, n->H, a.h2, n->H, 1, w + off_W3(n), 1, n->H, y, n->O, EPI_BIAS, p + off_b3(n), nullptr, 0, st);
+  return gemm(n, Bn, n->H, n->I, x, n->I, 1, w + off_W1(n), 1, n->I, a.h1, n->H, EPI_BIAS_SILU, p + off_b1(n), a.z1,
+              n->H, true, st) &&
+         gemm(n, Bn, n->H, n->H, a.h1, n->H, 1, w + off_W2(n), 1, n->H, a.h2, n->H, EPI_BIAS_SILU, p + off_b2(n),
+              a.z2, n->H, true, st) &&
+         gemm(n, Bn, n->O, n->H, a.h2, n->H, 1, w + off_W3(n), 1, n->H, y, n->O, EPI_BIAS, p + off_b3(n), nullptr, 0,
+              true, st);
 }
 
 // gradients of the mean-squared loss into n->g; dy must hold dL/dy
-void backward(must_mlp* n, int Bn, const float* x, cudaStream_t st) {
+bool backward(must_mlp* n, int Bn, const float* x, cudaStream_t st) {
   const Act a = acts(n);
   const __nv_bfloat16* w = n->wb;
   float* g = n->g;
   const int H = n->H, O = n->O, I = n->I;
   // dW3[o][h] = sum_b dy[b][o] h2[b][h]
-  gemm(O, H, Bn, a.dy, 1, O, a.h2, H, 1, g + off_W3(n), H, EPI_STORE, nullptr, nullptr, 0, st);
+  if (!gemm(n, O, H, Bn, a.dy, 1, O, a.h2, H, 1, g + off_W3(n), H, EPI_STORE, nullptr, nullptr, 0, false, st))
+    return false;
   colsum_kernel<<<(O + 255) / 256, 256, 0, st>>>(Bn, O, a.dy, g + off_b3(n));
   // dz2 = (dy W3) * silu'(z2)        (B(k=o, n=h) = W3[o][h])
-  gemm(Bn, H, O, a.dy, O, 1, w + off_W3(n), H, 1, a.dh, H, EPI_DSILU, nullptr, a.z2, H, st);
-  gemm(H, H, Bn, a.dh, 1, H, a.h1, H, 1, g + off_W2(n), H, EPI_STORE, nullptr, nullptr, 0, st);
+  if (!gemm(n, Bn, H, O, a.dy, O, 1, w + off_W3(n), H, 1, a.dh, H, EPI_DSILU, nullptr, a.z2, H, true, st) ||
+      !gemm(n, H, H, Bn, a.dh, 1, H, a.h1, H, 1, g + off_W2(n), H, EPI_STORE, nullptr, nullptr, 0, false, st))
+    return false;
   colsum_kernel<<<(H + 255) / 256, 256, 0, st>>>(Bn, H, a.dh, g + off_b2(n));
   // dz1 = (dz2 W2) * silu'(z1); reuse h2 as the buffer for dz1
-  gemm(Bn, H, H, a.dh, H, 1, w + off_W2(n), H, 1, a.h2, H, EPI_DSILU, nullptr, a.z1, H, st);
-  gemm(H, I, Bn, a.h2, 1, H, x, I, 1, g + off_W1(n), I, EPI_STORE, nullptr, nullptr, 0, st);
+  if (!gemm(n, Bn, H, H, a.dh, H, 1, w + off_W2(n), H, 1, a.h2, H, EPI_DSILU, nullptr, a.z1, H, true, st) ||
+      !gemm(n, H, I, Bn, a.h2, 1, H, x, I, 1, g + off_W1(n), I, EPI_STORE, nullptr, nullptr, 0, false, st))
+    return false;
   colsum_kernel<<<(H + 255) / 256, 256, 0, st>>>(Bn, H, a.h2, g + off_b1(n));
   prof_launched(PH_OTHER, 3);
+  return true;
 }
 
 }  // namespace
@@ -224,17 +372,28 @@ must_status must_mlp_create(int32_t n_in, int32_t hidden, int32_t n_out, int32_t
   n->nparam = size_t(hidden) * n_in + hidden + size_t(hidden) * hidden + hidden + size_t(n_out) * hidden + n_out;
   const size_t np = n->nparam;
   const size_t nact = size_t(max_batch) * (5 * size_t(hidden) + 2 * size_t(n_out));
+  // operand packs of the tensor-core products: every product's rows, columns
+  // and K are among the batch, the input, hidden and output widths
+  const size_t mmax = std::max({size_t(max_batch), size_t(hidden), size_t(n_out)});
+  const size_t nmax = std::max({size_t(hidden), size_t(n_out), size_t(n_in)});
+  const size_t kmax = std::max({size_t(n_in), size_t(hidden), size_t(max_batch), size_t(n_out)});
+  n->pa = rup(mmax, MG_BM) * rup(kmax, MG_KB);
+  n->pb = rup(nmax, MG_BN) * rup(kmax, MG_KB);
+  n->pk = nullptr;
+  n->err = nullptr;
   bool ok = cudaMalloc(&n->p, np * 4) == cudaSuccess && cudaMalloc(&n->g, np * 4) == cudaSuccess &&
             cudaMalloc(&n->m, np * 4) == cudaSuccess && cudaMalloc(&n->v, np * 4) == cudaSuccess &&
             cudaMalloc(&n->wb, np * 2) == cudaSuccess && cudaMalloc(&n->act, nact * 4) == cudaSuccess &&
-            cudaMalloc(&n->loss, 8) == cudaSuccess;
+            cudaMalloc(&n->loss, 8) == cudaSuccess && cudaMalloc(&n->pk, 2 * (n->pa + n->pb) * 4) == cudaSuccess &&
+            cudaMalloc(&n->err, 4) == cudaSuccess;
   if (!ok) {
     must_set_error("must_mlp_create: device allocation failed");
     cudaFree(n->p); cudaFree(n->g); cudaFree(n->m); cudaFree(n->v); cudaFree(n->wb); cudaFree(n->act);
-    cudaFree(n->loss);
+    cudaFree(n->loss); cudaFree(n->pk); cudaFree(n->err);
     delete n;
     return MUST_ENOMEM;
   }
+  cudaMemset(n->err, 0, 4);
   // He-style uniform initialisation from the seed (host), zero biases
   std::vector<float> h(np, 0.f);
   std::mt19937_64 rng(seed);
@@ -262,7 +421,7 @@ must_status must_mlp_create(int32_t n_in, int32_t hidden, int32_t n_out, int32_t
 void must_mlp_free(must_mlp* n) {
   if (!n) return;
   cudaFree(n->p); cudaFree(n->g); cudaFree(n->m); cudaFree(n->v); cudaFree(n->wb); cudaFree(n->act);
-  cudaFree(n->loss);
+  cudaFree(n->loss); cudaFree(n->pk); cudaFree(n->err);
   delete n;
 }
 
@@ -298,7 +457,10 @@ must_status must_mlp_forward(const must_mlp* n, int32_t batch, const float* x, f
     must_set_error("must_mlp_forward: bad argument (batch must be in [1, max_batch])");
     return MUST_EINVAL;
   }
-  forward(n, batch, x, y, static_cast<cudaStream_t>(stream));
+  if (!forward(n, batch, x, y, static_cast<cudaStream_t>(stream))) {
+    must_set_error("must_mlp_forward: tensor-core product could not be launched");
+    return MUST_ECUDA;
+  }
   return cudaGetLastError() == cudaSuccess ? MUST_OK : MUST_ECUDA;
 }
 
@@ -312,11 +474,17 @@ must_status must_mlp_gradients(must_mlp* n, int32_t batch, const float* x, const
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Act a = acts(n);
-  forward(n, batch, x, a.y, st);
+  if (!forward(n, batch, x, a.y, st)) {
+    must_set_error("must_mlp_gradients: tensor-core product could not be launched");
+    return MUST_ECUDA;
+  }
   cudaMemsetAsync(n->loss, 0, 8, st);
   const size_t cnt = size_t(batch) * n->O;
   mse_kernel<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(batch, n->O, a.y, target, a.dy, n->loss);
-  backward(n, batch, x, st);
+  if (!backward(n, batch, x, st)) {
+    must_set_error("must_mlp_gradients: tensor-core product could not be launched");
+    return MUST_ECUDA;
+  }
   if (grads) cudaMemcpyAsync(grads, n->g, n->nparam * 4, cudaMemcpyDefault, st);
   if (loss) cudaMemcpyAsync(loss, n->loss, 8, cudaMemcpyDefault, st);
   return cudaGetLastError() == cudaSuccess ? MUST_OK : MUST_ECUDA;

@@ -1,6 +1,6 @@
-"""The warm-start MLP's hand-written GPU kernels against the CPU reference
-(oracle/mlp.py): gradients on the same BF16-rounded weights within 1e-3
-relative per tensor, training reduces the loss, checkpoints round-trip, and
+"""The warm-start MLP's hand-written GPU kernels (products on the tcgen05
+tensor cores in 3xTF32) against the CPU reference (oracle/mlp.py): gradients
+on the same BF16-rounded weights within 1e-3 relative per tensor, training reduces the loss, checkpoints round-trip, and
 the feature / target / apply kernels invert each other."""
 import numpy as np
 import pytest
@@ -28,13 +28,16 @@ def _split(p, I, H, O):
     return out
 
 
-def test_gradients_match_cpu_reference(B):
+@pytest.mark.parametrize("I,H,O,Bn", [(37, 24, 10, 16), (1302, 256, 512, 200)])
+def test_gradients_match_cpu_reference(B, I, H, O, Bn):
+    """Small widths (every product a single padded tile) and the warm start's
+    own widths (1302 -> 256 -> 256 -> 512, a ragged batch of 200: several
+    row, column and K tiles of the tensor-core products)."""
     import torch
     from oracle import mlp
-    I, H, O, Bn = 37, 24, 10, 16
-    net = B.Mlp(I, H, O, 64, seed=3)
+    net = B.Mlp(I, H, O, max(64, Bn), seed=3)
     rng = np.random.default_rng(0)
-    p = (rng.standard_normal(net.param_count()) * 0.3).astype(np.float32)
+    p = (rng.standard_normal(net.param_count()) * 0.3 / np.sqrt(I / 37.0)).astype(np.float32)
     B.must_mlp_set_params(net, torch.tensor(p, device="cuda"))
     x = rng.standard_normal((Bn, I)).astype(np.float32)
     t = rng.standard_normal((Bn, O)).astype(np.float32)
