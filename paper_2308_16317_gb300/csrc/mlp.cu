@@ -24,8 +24,8 @@
 
 #include "common.cuh"
 #include "prof.h"
-#include "tc_gemm.h"
 #include "tc_ptx.cuh"
+#include "tmap.h"
 
 struct must_mlp {
   int I, H, O, max_batch;
@@ -286,8 +286,8 @@ bool gemm(const must_mlp* net, int M, int N, int K, const TA* A, long ars, long 
   tf32_pack_kernel<TB><<<unsigned((nb + 255) / 256), 256, 0, st>>>(N, K, Np, Kp, B, bcs, brs, bh, bl);
   CUtensorMap mAh, mAl, mBh, mBl;
   const uint64_t rb = uint64_t(Kp) * 4;
-  if (!tc_encode_2d_sw128(&mAh, 1, ah, Kp, Mp, rb, MG_KB, MG_BM) || !tc_encode_2d_sw128(&mAl, 1, al, Kp, Mp, rb, MG_KB, MG_BM) ||
-      !tc_encode_2d_sw128(&mBh, 1, bh, Kp, Np, rb, MG_KB, MG_BN) || !tc_encode_2d_sw128(&mBl, 1, bl, Kp, Np, rb, MG_KB, MG_BN))
+  if (!encode_2d_sw128(&mAh, 1, ah, Kp, Mp, rb, MG_KB, MG_BM) || !encode_2d_sw128(&mAl, 1, al, Kp, Mp, rb, MG_KB, MG_BM) ||
+      !encode_2d_sw128(&mBh, 1, bh, Kp, Np, rb, MG_KB, MG_BN) || !encode_2d_sw128(&mBl, 1, bl, Kp, Np, rb, MG_KB, MG_BN))
     return false;
   static bool attr = false;
   if (!attr) {
