@@ -449,6 +449,13 @@ def run_supercell(args):
 
     prec = args.precision
     opts = B.must_default_opts(PREC[prec], residual=RES[args.residual])
+    tuned = None
+    if args.autotune:
+        # grid search of the library's knobs on this batch (timed apart from the steps below)
+        from paper_2308_16317_gb300 import autotune
+        t0 = time.perf_counter()
+        best, results = autotune.tune_session(s, opts, reps=1)
+        tuned = {"best": best, "points": len(results or []), "seconds": time.perf_counter() - t0}
     sampler = ClockSampler(local)
     sampler.start()
     ms, launches, tau, st = timed_plan(opts, args.steps, args.warmup)
@@ -472,7 +479,7 @@ def run_supercell(args):
                        "launch": "captured CUDA graph (must_plan_batch), replayed per step",
                        "bucket_sites": B.must_tune_get(0), "tile_n": B.must_tune_get(1)},
             "gpu_launches": int(launches), "clocks": clocks, "plain_fp64_batched": fp64,
-            "max_rel_err_vs_fp64": err, "status_ok": bool((st.cpu().numpy() == 0).all())}
+            "max_rel_err_vs_fp64": err, "status_ok": bool((st.cpu().numpy() == 0).all()), "autotune": tuned}
     if rank == 0:
         emit(line)
 
@@ -877,6 +884,8 @@ def main():
     ap.add_argument("--train-lizs", type=int, default=1667,
                     help="warmstart mode: random 135-site training LIZs (x 2 spins x 15 predicted points; "
                          "1667 LIZs give the 50k training samples of the design)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="supercell mode: grid-search the library's knobs on the batch first (autotune.py)")
     ap.add_argument("--tune", action="append", default=[], metavar="KNOB=VALUE",
                     help="set a library knob (must_tune_set) before the run; recorded in the JSON line")
     ap.add_argument("--n-energies", type=int, default=32,

@@ -7,7 +7,9 @@ re-measuring.  Knobs:
   bucket_sites  sites per padding quantum when LIZs of uneven size are
                 grouped into shared launches (padding costs flops, finer
                 quanta cost launches);
-  tile_n        complex columns per tensor-core tile of the trailing update.
+  tile_n        complex columns per tensor-core tile of the trailing update;
+  run_tiles     longest run of row tiles per CTA of the streamed update;
+  cluster_ctas  CTAs per cluster of the correction solve.
 """
 from __future__ import annotations
 
@@ -15,8 +17,8 @@ import itertools
 import json
 import os
 
-KNOBS = {"bucket_sites": 0, "tile_n": 1}
-CANDIDATES = {"bucket_sites": [1, 2, 4, 8], "tile_n": [128, 256]}
+KNOBS = {"bucket_sites": 0, "tile_n": 1, "run_tiles": 3, "cluster_ctas": 7}
+CANDIDATES = {"bucket_sites": [1, 2, 4, 8], "tile_n": [128, 256], "run_tiles": [16, 32, 64], "cluster_ctas": [2, 4]}
 
 
 def search(run, set_knob, candidates=None, reps: int = 2):

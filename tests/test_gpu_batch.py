@@ -163,12 +163,14 @@ def test_autotuner_on_uneven_batch(B, tmp_path):
     ref, _ = s.solve_batch(opts)
     torch.cuda.synchronize()
     ref = ref.cpu().numpy()
-    old = (B.must_tune_get(0), B.must_tune_get(1))
+    knobs = (0, 1, 3, 7)
+    old = {k: B.must_tune_get(k) for k in knobs}
     try:
         path = os.path.join(tmp_path, "tune.json")
         best, results = autotune.tune_session(s, opts, cache_path=path, reps=1)
-        assert len(results) == 8 and all(ms > 0 for _, ms in results)
-        assert B.must_tune_get(0) == best["bucket_sites"] and B.must_tune_get(1) == best["tile_n"]
+        assert len(results) == 4 * 2 * 3 * 2 and all(ms > 0 for _, ms in results)
+        for name, k in autotune.KNOBS.items():
+            assert B.must_tune_get(k) == best[name]
         again, none = autotune.tune_session(s, opts, cache_path=path)
         assert again == best and none is None
         tau, st = s.solve_batch(opts)
@@ -176,5 +178,5 @@ def test_autotuner_on_uneven_batch(B, tmp_path):
         assert (st.cpu().numpy() == 0).all()
         assert rel_fro(tau.cpu().numpy(), ref).max() <= 1e-9
     finally:
-        B.must_tune_set(0, old[0])
-        B.must_tune_set(1, old[1])
+        for k, v in old.items():
+            B.must_tune_set(k, v)
