@@ -41,20 +41,22 @@ namespace {
 using namespace tcptx;
 
 constexpr int RT_ROWS = 128;                    // complex rows of M per CTA (TMEM lanes)
-constexpr int RT_KC = 32;                       // complex columns of M per K block (64 real K, 128 B rows)
+constexpr int RT_KC = 16;                       // complex columns of M per K block (32 real K, 64-byte rows)
 constexpr int RT_RHS = 16;                      // right-hand sides per group
 constexpr int RT_SLICES = 6;                    // digits per number
 constexpr int RT_N = 2 * RT_RHS;                // real accumulator columns per level
-constexpr int RT_A_SLICE = RT_ROWS * 128;       // bytes of one A digit slice of a K block (16 KB)
-constexpr int RT_A_BYTES = RT_SLICES * RT_A_SLICE;           // 96 KB
-constexpr int RT_B_BYTES = RT_SLICES * RT_N * 128;           // 24 KB: B tile of a K block
-constexpr int RT_B_STAGES = 2;
-constexpr int RT_CHUNK_KB = 2;                  // K blocks per exact accumulation chunk (128 real K)
+constexpr int RT_ROWB = 64;                     // bytes per operand row of a K block (64-byte swizzle)
+constexpr int RT_A_SLICE = RT_ROWS * RT_ROWB;   // bytes of one A digit slice of a K block (8 KB)
+constexpr int RT_A_BYTES = RT_SLICES * RT_A_SLICE;           // 48 KB
+constexpr int RT_A_STAGES = 3;
+constexpr int RT_B_BYTES = RT_SLICES * RT_N * RT_ROWB;       // 12 KB: B tile of a K block
+constexpr int RT_B_STAGES = 3;
+constexpr int RT_CHUNK_KB = 4;                  // K blocks per exact accumulation chunk (128 real K)
 constexpr int RT_ACC_COLS = 256;                // tensor-memory columns per accumulator buffer
 constexpr int RT_CONV_WARPS = 8;
 constexpr int RT_EPI_WARPS = 8;
 constexpr int RT_THREADS = 32 * (2 + RT_CONV_WARPS + RT_EPI_WARPS);
-constexpr size_t RT_SMEM = size_t(RT_A_BYTES) + RT_B_STAGES * RT_B_BYTES + 1024;
+constexpr size_t RT_SMEM = size_t(RT_A_STAGES) * RT_A_BYTES + RT_B_STAGES * RT_B_BYTES + 1024;
 
 // Six fixed-point digits of H + L (|H| < 128, L the low word scaled alike).
 __device__ __forceinline__ void digits6(float H, float L, float d[RT_SLICES]) {
@@ -78,9 +80,17 @@ __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
 }
 
 // Byte offset of the 4-byte pair (real K elements 2k, 2k+1) of row r in a
-// 128-byte-swizzled K-major tile (16-byte chunk index XOR row mod 8).
+// 64-byte-swizzled K-major tile: rows 64 bytes apart, the 16-byte chunk
+// index XOR (row / 2) mod 4 (the pattern repeats every 8 rows, 512 bytes).
 __device__ __forceinline__ uint32_t swz(int r, int k) {
-  return uint32_t(r) * 128u + uint32_t(((k >> 2) ^ (r & 7)) << 4) + uint32_t(k & 3) * 4u;
+  return uint32_t(r) * RT_ROWB + uint32_t(((k >> 2) ^ ((r >> 1) & 3)) << 4) + uint32_t(k & 3) * 4u;
+}
+
+// Shared-memory matrix descriptor of such a tile: K-major, 64-byte swizzle,
+// 8-row groups 512 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc64(uint32_t addr) {
+  return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t(1) << 16) | (uint64_t(512 >> 4) << 32) | (uint64_t(1) << 46) |
+         (uint64_t(4) << 61);
 }
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -127,16 +137,19 @@ struct RtParams {
 };
 
 // One CTA per (128-row tile, item, group of 16 right-hand sides).  Warp 0
-// streams the B tiles (bulk copies, two stages), warp 1 allocates tensor
+// streams the B tiles (bulk copies, three stages), warp 1 allocates tensor
 // memory and issues the MMAs, warps 2-9 convert the M tile of each K block
-// into six swizzled digit slices in shared memory, warps 10-17 drain the two
-// accumulator buffers (one per chunk of two K blocks) and write R.
+// into six swizzled digit slices in shared memory (three stages, so the
+// conversion of the next blocks overlaps the MMAs of this one; each
+// converter loads the next block's M entries before converting this one's),
+// warps 10-17 drain the two accumulator buffers (one per chunk of four K
+// blocks) and write R.
 __global__ void __launch_bounds__(RT_THREADS, 1) residual_tc_kernel(RtParams P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
-  uint8_t* sB = smem + RT_A_BYTES;
-  __shared__ __align__(8) uint64_t a_full, a_empty, mma_done;
+  uint8_t* sB = smem + RT_A_STAGES * RT_A_BYTES;
+  __shared__ __align__(8) uint64_t a_full[RT_A_STAGES], a_empty[RT_A_STAGES], mma_done;
   __shared__ __align__(8) uint64_t b_full[RT_B_STAGES], b_empty[RT_B_STAGES];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
@@ -149,8 +162,10 @@ __global__ void __launch_bounds__(RT_THREADS, 1) residual_tc_kernel(RtParams P) 
   const int n = P.n, nkb = P.nkb, nchunks = (nkb + RT_CHUNK_KB - 1) / RT_CHUNK_KB;
 
   if (threadIdx.x == 0) {
-    mbar_init(&a_full, RT_CONV_WARPS);
-    mbar_init(&a_empty, 1);
+    for (int s = 0; s < RT_A_STAGES; ++s) {
+      mbar_init(&a_full[s], RT_CONV_WARPS);
+      mbar_init(&a_empty[s], 1);
+    }
     mbar_init(&mma_done, 1);
     for (int s = 0; s < RT_B_STAGES; ++s) {
       mbar_init(&b_full[s], 1);
@@ -200,18 +215,19 @@ __global__ void __launch_bounds__(RT_THREADS, 1) residual_tc_kernel(RtParams P) 
         const bool cfirst = (kb % RT_CHUNK_KB) == 0;
         const bool clast = (kb % RT_CHUNK_KB) == RT_CHUNK_KB - 1 || kb == nkb - 1;
         if (cfirst && c >= 2 && !mbar_wait_f(&acc_empty[buf], ((c >> 1) - 1) & 1, fail)) break;
-        if (!mbar_wait_f(&a_full, kb & 1, fail)) break;
+        const int sa = kb % RT_A_STAGES;
+        if (!mbar_wait_f(&a_full[sa], (kb / RT_A_STAGES) & 1, fail)) break;
         if (!mbar_wait_f(&b_full[kb % RT_B_STAGES], (kb / RT_B_STAGES) & 1, fail)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + (kb % RT_B_STAGES) * RT_B_BYTES);
+        const uint32_t a0 = smem_u32(sA + sa * RT_A_BYTES), b0 = smem_u32(sB + (kb % RT_B_STAGES) * RT_B_BYTES);
         const uint32_t d0 = tmem + uint32_t(buf * RT_ACC_COLS);
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks)
+        for (int ks = 0; ks < RT_ROWB / 32; ++ks)   // K = 16 BF16 (32 bytes) per MMA
 #pragma unroll
           for (int s = 0; s < RT_SLICES; ++s)
-            mma_bf16(d0 + uint32_t(RT_N * s), sdesc(a0 + s * RT_A_SLICE + 32 * ks), sdesc(b0 + 32 * ks), idesc[s],
-                     (cfirst && ks == 0 && s == 0) ? 0u : 1u);
-        mma_commit(&a_empty);
+            mma_bf16(d0 + uint32_t(RT_N * s), sdesc64(a0 + s * RT_A_SLICE + 32 * ks), sdesc64(b0 + 32 * ks),
+                     idesc[s], (cfirst && ks == 0 && s == 0) ? 0u : 1u);
+        mma_commit(&a_empty[sa]);
         mma_commit(&b_empty[kb % RT_B_STAGES]);
         if (clast) mma_commit(&acc_full[buf]);
       }
@@ -220,7 +236,8 @@ __global__ void __launch_bounds__(RT_THREADS, 1) residual_tc_kernel(RtParams P) 
   } else if (warp < 2 + RT_CONV_WARPS) {
     // Converter warp cw owns row octets 2cw, 2cw + 1 of the tile; lane l takes
     // row 8 octet + (l & 7) and complex column 4 kq + (l >> 3) of each K-quad
-    // kq, so that a warp's 4-byte digit stores hit 32 distinct banks.
+    // kq, so that a warp's global loads read 128 contiguous bytes per column
+    // and its 4-byte digit stores hit 32 distinct banks.
     const int cw = warp - 2;
     const float4* M = P.M + size_t(item) * P.stride;
     int grow[2];
@@ -231,31 +248,44 @@ __global__ void __launch_bounds__(RT_THREADS, 1) residual_tc_kernel(RtParams P) 
       const int e = (grow[h] < n) ? P.rexp[size_t(item) * n + grow[h]] : 0;
       sc[h] = __int_as_float((127 + 8 - e) << 23);   // 2^(8 - e), exact
     }
-    for (int kb = 0; kb < nkb; ++kb) {
-      float4 v[16];
+    auto load_block = [&](int kb, float4* v) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int h = j >> 3, kq = j & 7;
+      for (int j = 0; j < 8; ++j) {
+        const int h = j >> 2, kq = j & 3;
         const int gk = kb * RT_KC + 4 * kq + (lane >> 3);
-        const bool ok = grow[h] < n && gk < n && gk != grow[h];
+        const bool ok = kb < nkb && grow[h] < n && gk < n && gk != grow[h];
         v[j] = ok ? M[size_t(gk) * P.ld + grow[h]] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      if (kb >= 1 && !mbar_wait_f(&a_empty, (kb - 1) & 1, fail)) break;
+    };
+    float4 va[8], vb[8];
+    load_block(0, va);
+    for (int kb = 0; kb < nkb; kb += 2) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int h = j >> 3, kq = j & 7;
-        const int r = 8 * (2 * cw + h) + (lane & 7), k = 4 * kq + (lane >> 3);
-        float dr[RT_SLICES], di[RT_SLICES];
-        digits6(v[j].x * sc[h], v[j].z * sc[h], dr);
-        digits6(v[j].y * sc[h], v[j].w * sc[h], di);
-        const uint32_t off = swz(r, k);
+      for (int half = 0; half < 2; ++half) {   // blocks kb (registers va) and kb + 1 (vb)
+        const int b = kb + half;
+        if (b >= nkb) break;
+        float4* cur = half ? vb : va;
+        float4* nxt = half ? va : vb;
+        load_block(b + 1, nxt);   // in flight while this block is converted
+        const int sa = b % RT_A_STAGES;
+        if (b >= RT_A_STAGES && !mbar_wait_f(&a_empty[sa], ((b / RT_A_STAGES) - 1) & 1, fail)) { kb = nkb; break; }
+        uint8_t* dst = sA + sa * RT_A_BYTES;
 #pragma unroll
-        for (int s = 0; s < RT_SLICES; ++s)
-          *reinterpret_cast<uint32_t*>(sA + s * RT_A_SLICE + off) = bf16x2(dr[s], di[s]);
+        for (int j = 0; j < 8; ++j) {
+          const int h = j >> 2, kq = j & 3;
+          const int r = 8 * (2 * cw + h) + (lane & 7), k = 4 * kq + (lane >> 3);
+          float dr[RT_SLICES], di[RT_SLICES];
+          digits6(cur[j].x * sc[h], cur[j].z * sc[h], dr);
+          digits6(cur[j].y * sc[h], cur[j].w * sc[h], di);
+          const uint32_t off = swz(r, k);
+#pragma unroll
+          for (int s = 0; s < RT_SLICES; ++s)
+            *reinterpret_cast<uint32_t*>(dst + s * RT_A_SLICE + off) = bf16x2(dr[s], di[s]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor-core reads
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a_full[sa]);
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor-core reads
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&a_full);
     }
   } else {
     // Epilogue warp: TMEM lane quarter (warp % 4), accumulator half (16 real
