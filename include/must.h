@@ -253,7 +253,9 @@ must_status must_site_density(int32_t lmax, int32_t nE, const double* E, const d
  *           through distributed shared memory; 0 one CTA per item and group;
  *   knob 7: preferred CTAs per cluster of that kernel (2, 4 or 8, default 2;
  *           a larger cluster is taken when the rows do not fit its shared
- *           memory).
+ *           memory);
+ *   knob 8: right-hand sides per cluster of that kernel (4, 8 or 16; 0, the
+ *           default, takes the most whose rows fit 72 KB of shared memory).
  * Process-wide; set them between calls, not while solves are being enqueued.
  */
 must_status must_tune_set(int32_t knob, int32_t value);

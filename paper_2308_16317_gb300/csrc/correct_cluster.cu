@@ -36,6 +36,7 @@ namespace {
 constexpr int CT = 256;        // threads per CTA
 constexpr int W_BUDGET = 72 * 1024;   // shared memory for the owned rows' right-hand sides
 int g_cluster_ctas = 2;        // preferred CTAs per cluster (tuning knob 7)
+int g_cluster_rhs = 0;         // right-hand sides per cluster (tuning knob 8; 0: the most within W_BUDGET)
 
 // One warp's unit of a substitution step: the 32 rows of one owned block
 // (lane = row) against the G / 2 right-hand sides of one half, for the
@@ -364,6 +365,14 @@ bool correct_cluster_set_ctas(int ctas) {
 
 int correct_cluster_get_ctas() { return g_cluster_ctas; }
 
+bool correct_cluster_set_rhs(int rhs) {
+  if (rhs != 0 && rhs != 4 && rhs != 8 && rhs != 16) return false;
+  g_cluster_rhs = rhs;
+  return true;
+}
+
+int correct_cluster_get_rhs() { return g_cluster_rhs; }
+
 // Right-hand sides per cluster and CTAs per cluster for order n: the
 // preferred cluster size (knob 7) or, when the owned rows' right-hand sides
 // do not fit its shared memory even for 4 right-hand sides, the next larger.
@@ -373,7 +382,8 @@ static void cc_shape(int n, int kap, int* G_out, int* CL_out) {
   for (int CL = g_cluster_ctas; CL <= 8; CL *= 2) {
     const int nb = (n + 31) / 32, nlb = (nb + CL - 1) / CL;
     for (int G : {16, 8, 4})
-      if (size_t(nlb) * G * 32 * 8 <= size_t(W_BUDGET) && cc_smem_bytes(n, kap, G, CL) <= 100 * 1024) {
+      if (g_cluster_rhs ? (G == g_cluster_rhs && cc_smem_bytes(n, kap, G, CL) <= 200 * 1024)
+                        : (size_t(nlb) * G * 32 * 8 <= size_t(W_BUDGET) && cc_smem_bytes(n, kap, G, CL) <= 100 * 1024)) {
         *G_out = G;
         *CL_out = CL;
         return;

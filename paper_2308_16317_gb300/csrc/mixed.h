@@ -44,6 +44,11 @@ int correct_cluster_rhs(int n, int kap);
 // or 8; a larger one is taken when the rows do not fit).
 bool correct_cluster_set_ctas(int ctas);
 int correct_cluster_get_ctas();
+// Tuning knob 8: right-hand sides per cluster of the cluster correction (4, 8
+// or 16; 0, the default: the most whose rows fit a 72 KB share of shared
+// memory, so that two CTAs fit an SM).
+bool correct_cluster_set_rhs(int rhs);
+int correct_cluster_get_rhs();
 bool correct_cluster(const float2* A, size_t stride, int ld, int n, int kap, int items, const int* perm,
                      const double* scale, const double2* Sinv, const double2* R, double2* X, double* norms,
                      const int* conv, int first_all, const int* first_flags, unsigned long long* work,

@@ -151,3 +151,26 @@ def test_bench_algorithmic_work_of_the_update():
     unblocked = 8.0 * sum((n - j - 1) ** 2 for j in range(n - kap))
     # the blocked update leaves out the work inside each panel (about nb/2 columns of width m)
     assert 0.9 * unblocked < flops < unblocked
+
+
+def test_tuning_knobs_validate_and_round_trip():
+    """Tuning knobs are process-wide host settings: valid values round-trip,
+    invalid ones are rejected with MUST_EINVAL and leave the setting as it was
+    (no GPU needed)."""
+    from paper_2308_16317_gb300 import binding as B
+    cases = {6: ([0, 1], [2, -1]), 7: ([2, 4, 8], [3, 16]), 8: ([0, 4, 8, 16], [2, 32]), 5: ([0, 2, 4, 8], [3])}
+    for knob, (good, bad) in cases.items():
+        old = B.must_tune_get(knob)
+        try:
+            for v in good:
+                B.must_tune_set(knob, v)
+                assert B.must_tune_get(knob) == v
+            for v in bad:
+                with pytest.raises(B.MustError) as ei:
+                    B.must_tune_set(knob, v)
+                assert ei.value.code == 1
+                assert B.must_tune_get(knob) == good[-1]
+        finally:
+            B.must_tune_set(knob, old)
+    with pytest.raises(B.MustError):
+        B.must_tune_set(99, 1)
