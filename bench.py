@@ -414,18 +414,42 @@ def run_supercell(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
     from paper_2308_16317_gb300 import binding as B
     from paper_2308_16317_gb300 import build as libbuild
+    from paper_2308_16317_gb300 import shard
     from paper_2308_16317_gb300 import workload as wl
     from paper_2308_16317_gb300.runner import Session, blocks_to_numpy
     libbuild.build()
     B.load()
     full = wl.batched_supercell()
-    lizs = full.lizs[rank * args.n_lizs:(rank + 1) * args.n_lizs]
+    if args.shard == "balanced":
+        # strong scaling: the first n_lizs LIZs split over the ranks by cost (sum of n^3)
+        pool = full.lizs[:args.n_lizs]
+        orders = [full.n_of(z) for z in pool]
+        lizs = [pool[i] for i in shard.balanced_shards(orders, ws)[rank]]
+    else:
+        # weak scaling: every rank its own n_lizs LIZs
+        lizs = full.lizs[rank * args.n_lizs:(rank + 1) * args.n_lizs]
     w = wl.Workload(full.name, full.lmax, lizs, wl.semicircle_contour(args.n_energies, im_min=0.005), full.v_species,
                     full.r_mt)
     s = Session(w, device="cuda:%d" % local)
     items = len(w.energies) * s.nspin * len(lizs)
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
 
     def timed_plan(opts, steps, warm):
         # the minimum holds one LIZ's items at the largest order; a multiple lets
@@ -436,6 +460,7 @@ def run_supercell(args):
         plan = B.must_plan_batch(s.lizs, s.E, s.tinv, s.n_species, s.nspin, opts, wsp, nbytes, tau, st)
         for _ in range(warm):
             B.must_plan_launch(plan)
+        barrier()
         torch.cuda.synchronize(dev)
         l0 = B.must_launch_count()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -445,7 +470,8 @@ def run_supercell(args):
             B.must_plan_launch(plan)
         e1.record()
         torch.cuda.synchronize(dev)
-        return e0.elapsed_time(e1), B.must_launch_count() - l0, tau, st
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1)), B.must_launch_count() - l0, tau, st
 
     prec = args.precision
     opts = B.must_default_opts(PREC[prec], residual=RES[args.residual])
@@ -454,25 +480,34 @@ def run_supercell(args):
         # grid search of the library's knobs on this batch (timed apart from the steps below)
         from paper_2308_16317_gb300 import autotune
         t0 = time.perf_counter()
-        best, results = autotune.tune_session(s, opts, reps=1)
+        best, results = autotune.tune_session(s, opts, reps=2, workspace_lizs=max(1, args.chunk_lizs))
         tuned = {"best": best, "points": len(results or []), "seconds": time.perf_counter() - t0}
     sampler = ClockSampler(local)
-    sampler.start()
+    if rank == 0:
+        sampler.start()
     ms, launches, tau, st = timed_plan(opts, args.steps, args.warmup)
-    clocks = sampler.stop()
+    clocks = sampler.stop() if rank == 0 else None
+    total_items = items
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([items], dtype=torch.float64, device=dev)
+        dist.all_reduce(t)
+        total_items = int(t.item())
     fp64 = None
     err = None
     if prec != "fp64" and args.fp64_steps > 0:
         ms64, _, tau64, _ = timed_plan(B.must_default_opts(0), args.fp64_steps, 1)
-        fp64 = {"value": items * args.fp64_steps / (ms64 / 1e3), "ms_per_step": ms64 / args.fp64_steps}
+        fp64 = {"value": total_items * args.fp64_steps / (ms64 / 1e3), "ms_per_step": ms64 / args.fp64_steps}
         a, b = blocks_to_numpy(tau), blocks_to_numpy(tau64)
         err = float((np.linalg.norm(a - b, axis=(-2, -1)) / np.linalg.norm(b, axis=(-2, -1))).max())
     sizes = [z.n for z in s.lizs]
     line = {"metric": "tau_00 solves/sec, batched uneven LIZs (supercell, n %d..%d)" % (min(sizes), max(sizes)),
-            "value": items * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "value": total_items * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if args.shard == "balanced" else "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
-            "config": {"workload": "supercell256 per-site LIZs with vacancies, lmax=3", "lizs": len(lizs),
+            "config": {"workload": "supercell256 per-site LIZs with vacancies, lmax=3", "lizs_per_rank": len(lizs),
+                       "shard": args.shard,
                        "workspace_lizs": max(1, args.chunk_lizs),
                        "energies": len(w.energies), "spins": s.nspin, "solves_per_step": items,
                        "n_min": min(sizes), "n_max": max(sizes), "precision": prec, "residual": args.residual,
@@ -482,6 +517,9 @@ def run_supercell(args):
             "max_rel_err_vs_fp64": err, "status_ok": bool((st.cpu().numpy() == 0).all()), "autotune": tuned}
     if rank == 0:
         emit(line)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def run_warmstart(args):
@@ -884,6 +922,9 @@ def main():
     ap.add_argument("--train-lizs", type=int, default=1667,
                     help="warmstart mode: random 135-site training LIZs (x 2 spins x 15 predicted points; "
                          "1667 LIZs give the 50k training samples of the design)")
+    ap.add_argument("--shard", default="slices", choices=["slices", "balanced"],
+                    help="supercell mode under torchrun: every rank its own n-lizs LIZs (weak scaling), or the "
+                         "first n-lizs LIZs split over the ranks by the cost sum n^3 (shard.py, strong scaling)")
     ap.add_argument("--autotune", action="store_true",
                     help="supercell mode: grid-search the library's knobs on the batch first (autotune.py)")
     ap.add_argument("--tune", action="append", default=[], metavar="KNOB=VALUE",

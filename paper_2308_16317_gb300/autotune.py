@@ -70,9 +70,12 @@ def apply(path: str, key: str, set_knob) -> bool:
     return True
 
 
-def tune_session(session, opts, cache_path: str | None = None, reps: int = 2, candidates=None):
-    """Tune the knobs for must_tau00_batch on `session`'s LIZs (device timing
-    with CUDA events); reuse a cached choice for the same key if present."""
+def tune_session(session, opts, cache_path: str | None = None, reps: int = 2, candidates=None,
+                 workspace_lizs: int = 2):
+    """Tune the knobs for the batched call on `session`'s LIZs: each setting
+    is captured into a plan (must_plan_batch, the way a batch is run) and its
+    replays are timed with CUDA events on the device, so host launch cost does
+    not bias the choice; reuses a cached choice for the same key if present."""
     import torch
 
     from . import binding as B
@@ -82,18 +85,30 @@ def tune_session(session, opts, cache_path: str | None = None, reps: int = 2, ca
                     items * len(session.lizs))
     if cache_path and apply(cache_path, key, B.must_tune_set):
         return load(cache_path)[key]["best"], None
-    out = session.alloc_out(len(session.lizs))
+    tau, st = session.alloc_out(len(session.lizs))
+    nbytes = B.must_batch_workspace_bytes(session.lizs, items, opts) * max(1, workspace_lizs)
+    ws = session.workspace(nbytes)
+
+    state = {"plan": None}
+
+    def set_knob(k, v):
+        B.must_tune_set(k, v)
+        state["plan"] = None       # the next run captures a plan with the new setting
 
     def run():
+        if state["plan"] is None:
+            state["plan"] = B.must_plan_batch(session.lizs, session.E, session.tinv, session.n_species,
+                                              session.nspin, opts, ws, nbytes, tau, st)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        session.solve_batch(opts, out=out)
+        B.must_plan_launch(state["plan"])
         e1.record()
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    best, results = search(run, B.must_tune_set, candidates, reps)
+    best, results = search(run, set_knob, candidates, reps)
+    state["plan"] = None
     if cache_path:
         save(cache_path, key, best, results)
     return best, results
