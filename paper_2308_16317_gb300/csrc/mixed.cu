@@ -48,6 +48,7 @@ __device__ __forceinline__ float cnormf(cf a) { return a.x * a.x + a.y * a.y; }
 constexpr int PANEL_W = 64;
 constexpr int LEAF = 8;
 constexpr int PPT = 512;                       // threads of the panel kernel
+constexpr int PANEL_QG = 8;                    // columns per group of the panel update (c)
 constexpr size_t PANEL_SMEM = 200 * 1024;      // leaf buffer budget (bytes)
 
 __host__ __device__ inline int leaf_width(int n) {
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
   extern __shared__ cf Lf[];           // leaf, column-major [lw][mrows]
   __shared__ float sv[PPT / 32];
   __shared__ int si[PPT / 32];
-  __shared__ cf Ub[LEAF][PANEL_W + 4]; // leaf rows of the remaining panel columns (+ padding)
+  __shared__ cf Ub[LEAF][PANEL_W + PANEL_QG]; // leaf rows of the remaining panel columns (+ padding)
   __shared__ cf Ll[LEAF][LEAF];        // leaf's unit-lower top block
   __shared__ int s_nr;                 // rows touched by the leaf's interchanges
   __shared__ int s_rows[2 * LEAF];     // ... their indices
@@ -215,8 +216,8 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
     __syncthreads();
     // (c) rows below the leaf: A[i, rest] -= L[i, leaf] U[leaf, rest], two
     // rows per pass so that twice the loads are in flight, the columns in
-    // groups of 4 (a ragged last group reads Ub past `rest`, into its padding,
-    // and drops those lanes' results).  The next leaf's columns go to the
+    // groups of PANEL_QG (a ragged last group reads Ub past `rest`, into its
+    // padding, and drops those lanes' results).  The next leaf's columns go to the
     // leaf buffer (free once the leaf is written back) instead of to memory.
     {
       const size_t cs = size_t(ld);
@@ -234,11 +235,11 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
         }
         cf* Vp = A + size_t(le) * cs + i0;
 #pragma unroll 1
-        for (int q0 = 0; q0 < rest; q0 += 4, Vp += 4 * cs) {
-          const int nq = min(4, rest - q0);
-          cf v0[4], v1[4];
+        for (int q0 = 0; q0 < rest; q0 += PANEL_QG, Vp += PANEL_QG * cs) {
+          const int nq = min(PANEL_QG, rest - q0);
+          cf v0[PANEL_QG], v1[PANEL_QG];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < PANEL_QG; ++q) {
             v0[q] = (q < nq) ? Vp[q * cs] : mkf(0.f, 0.f);
             v1[q] = (q < nq && has1) ? Vp[q * cs + PPT] : mkf(0.f, 0.f);
           }
@@ -246,13 +247,13 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
           for (int jj = 0; jj < LEAF; ++jj)
             if (jj < lw)
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
+              for (int q = 0; q < PANEL_QG; ++q) {
                 const cf u = Ub[jj][q0 + q];
                 cfmsf(v0[q], l0[jj], u);
                 cfmsf(v1[q], l1[jj], u);
               }
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
+          for (int q = 0; q < PANEL_QG; ++q)
             if (q < nq) {
               if (q0 + q < lwn) {
                 cf* Ln = Lf + (q0 + q) * mn + (i0 - le);
