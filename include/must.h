@@ -255,7 +255,10 @@ must_status must_site_density(int32_t lmax, int32_t nE, const double* E, const d
  *           a larger cluster is taken when the rows do not fit its shared
  *           memory);
  *   knob 8: right-hand sides per cluster of that kernel (4, 8 or 16; 0, the
- *           default, takes the most whose rows fit 72 KB of shared memory).
+ *           default, takes the most whose rows fit 72 KB of shared memory);
+ *   knob 9: U12 = L11^-1 A12 of the mixed path: 1 (default) persistent CTAs
+ *           (contiguous runs of 64-column tiles, the next tile copied while
+ *           the current one is multiplied), 0 one CTA per tile.
  * Process-wide; set them between calls, not while solves are being enqueued.
  */
 must_status must_tune_set(int32_t knob, int32_t value);

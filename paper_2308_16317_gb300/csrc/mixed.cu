@@ -393,6 +393,112 @@ __global__ void __launch_bounds__(256) trsm_inv_kernel(float2* __restrict__ A0, 
   }
 }
 
+// Persistent form of the same product: P CTAs, CTA b takes a contiguous run
+// of the (item, 64-column tile) pairs, keeps L11^{-1} of the current item in
+// shared memory (reloaded when the run crosses to the next item) and copies
+// the next tile of A12 into a second buffer with cp.async while it computes
+// the current one, so that the loads' latency is hidden behind the products.
+constexpr size_t TRSMP_SMEM = size_t(64 * 64 + 2 * TRSM_COLS * 65) * sizeof(cf);
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(256) trsm_inv_persist_kernel(float2* __restrict__ A0, size_t stride, int ld, int n,
+                                                               int k0, int nbe, int items,
+                                                               const float2* __restrict__ Linv0,
+                                                               uint16_t* __restrict__ bhi0,
+                                                               uint16_t* __restrict__ blo0, int Kp, int bitem_rows) {
+  extern __shared__ cf tsm[];
+  cf (*Li)[64] = reinterpret_cast<cf (*)[64]>(tsm);                          // [col j][row i]
+  cf (*Xb)[TRSM_COLS][65] = reinterpret_cast<cf (*)[TRSM_COLS][65]>(tsm + 64 * 64);   // 2 x [column][row]
+  const int rem = n - k0 - nbe;
+  const int ntile = (rem + TRSM_COLS - 1) / TRSM_COLS;
+  const long long total = (long long)ntile * items;
+  const long long t_beg = total * blockIdx.x / gridDim.x, t_end = total * (blockIdx.x + 1) / gridDim.x;
+  if (t_beg >= t_end) return;
+  // copy the A12 tile of pair t into buffer b (columns past n and rows past nbe zero-filled)
+  auto issue_tile = [&](long long t, int b) {
+    const int item = int(t / ntile), tile = int(t % ntile);
+    const cf* A = reinterpret_cast<const cf*>(A0 + size_t(item) * stride);
+    const int c_beg = k0 + nbe + tile * TRSM_COLS;
+    const int ncol = min(TRSM_COLS, n - c_beg);
+    for (int q = threadIdx.x; q < TRSM_COLS * 64; q += blockDim.x) {
+      const int i = q & 63, cc = q >> 6;
+      if (i < nbe && cc < ncol)
+        cp_async8(&Xb[b][cc][i], A + size_t(c_beg + cc) * ld + k0 + i);
+      else
+        Xb[b][cc][i] = mkf(0.f, 0.f);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  int cur_item = -1;
+  issue_tile(t_beg, 0);
+  for (long long t = t_beg; t < t_end; ++t) {
+    const int b = int(t - t_beg) & 1;
+    const int item = int(t / ntile), tile = int(t % ntile);
+    if (item != cur_item) {   // L11^{-1} of this item (all threads wait for the current tile's copy first)
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncthreads();
+      const cf* Lg = reinterpret_cast<const cf*>(Linv0 + size_t(item) * 64 * 64);
+      for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) tsm[q] = Lg[q];
+      cur_item = item;
+    }
+    if (t + 1 < t_end) {
+      issue_tile(t + 1, b ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's copy has landed
+    } else {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    __syncthreads();
+    const int i0 = threadIdx.x & 31, i1 = 63 - i0;
+    const int cgp = threadIdx.x >> 5;     // 8 column groups
+    constexpr int CPT = TRSM_COLS / 8;
+    cf y0[CPT], y1[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) y0[q] = y1[q] = mkf(0.f, 0.f);
+    for (int j = 0; j < 32; ++j) {
+      const cf l1 = Li[j][i1];
+      const cf l0 = Li[j][i0];
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) {
+        const cf a = Xb[b][cgp * CPT + q][j];
+        cfmaf_acc(y1[q], l1, a);
+        cfmaf_acc(y0[q], l0, a);
+      }
+    }
+    for (int j = 32; j < 64; ++j) {
+      const cf l1 = Li[j][i1];
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) cfmaf_acc(y1[q], l1, Xb[b][cgp * CPT + q][j]);
+    }
+    cf* A = reinterpret_cast<cf*>(A0 + size_t(item) * stride);
+    const int c_beg = k0 + nbe + tile * TRSM_COLS;
+    const int ncol = min(TRSM_COLS, n - c_beg);
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int cc = cgp * CPT + q;
+      if (cc < ncol) {
+        if (i0 < nbe) A[size_t(c_beg + cc) * ld + k0 + i0] = y0[q];
+        if (i1 < nbe) A[size_t(c_beg + cc) * ld + k0 + i1] = y1[q];
+        if (bhi0) {
+          const size_t base = size_t(item) * bitem_rows * Kp + size_t(c_beg + cc) * Kp;
+          unsigned lo;
+          unsigned hi = bf16x2_split(y0[q].x, y0[q].y, lo);
+          *reinterpret_cast<unsigned*>(bhi0 + base + 2 * i0) = hi;
+          *reinterpret_cast<unsigned*>(blo0 + base + 2 * i0) = lo;
+          hi = bf16x2_split(y1[q].x, y1[q].y, lo);
+          *reinterpret_cast<unsigned*>(bhi0 + base + 2 * i1) = hi;
+          *reinterpret_cast<unsigned*>(blo0 + base + 2 * i1) = lo;
+        }
+      }
+    }
+    __syncthreads();   // buffer b and Li are reused by the next tiles
+  }
+}
+
 // ------------------------------------------------ permutation, Schur block --
 // perm[i] = row of the original matrix that the swap sequence moves to row i.
 // One CTA per item: the swaps are applied in order by one thread on a copy in
@@ -1187,6 +1293,8 @@ thread_local SideStream g_side;
 int g_lookahead = 1;   // tuning knob 4
 int g_corr_rhs = 0;    // tuning knob 5 (0: by matrix order)
 int g_corr_cluster = 1;   // tuning knob 6
+int g_trsm_persist = 1;   // tuning knob 9
+static int g_num_sms = 152;
 
 static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
   int dev = 0;
@@ -1288,6 +1396,10 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     if (!attr) {
       cudaFuncSetAttribute(panel32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(PANEL_SMEM));
       cudaFuncSetAttribute(trsm_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TRSM_SMEM));
+      cudaFuncSetAttribute(trsm_inv_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TRSMP_SMEM));
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
       cudaFuncSetAttribute(perm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       attr = true;
     }
@@ -1327,9 +1439,17 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       const bool fuse_b = tc_pack_b_target(c.opts.precision, n, k0, nbe, items, packs, &pb);
       {
         ProfScope ps(PH_TRSM, st);
-        trsm_inv_kernel<<<dim3((rem + TRSM_COLS - 1) / TRSM_COLS, items), 256, TRSM_SMEM, st>>>(
-            M32, stride, ld, n, k0, nbe, Linv, fuse_b ? pb.hi : nullptr, fuse_b ? pb.lo : nullptr, pb.Kp,
-            pb.item_rows);
+        const long long tiles = (long long)((rem + TRSM_COLS - 1) / TRSM_COLS) * items;
+        if (g_trsm_persist) {
+          const int grid = int(std::min<long long>(tiles, 2LL * g_num_sms));
+          trsm_inv_persist_kernel<<<grid, 256, TRSMP_SMEM, st>>>(M32, stride, ld, n, k0, nbe, items, Linv,
+                                                                 fuse_b ? pb.hi : nullptr, fuse_b ? pb.lo : nullptr,
+                                                                 pb.Kp, pb.item_rows);
+        } else {
+          trsm_inv_kernel<<<dim3((rem + TRSM_COLS - 1) / TRSM_COLS, items), 256, TRSM_SMEM, st>>>(
+              M32, stride, ld, n, k0, nbe, Linv, fuse_b ? pb.hi : nullptr, fuse_b ? pb.lo : nullptr, pb.Kp,
+              pb.item_rows);
+        }
         prof_launched(PH_TRSM, 1, items);
       }
       if (!tc_pack(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, st, !fuse_b)) return MUST_ECUDA;

@@ -53,3 +53,8 @@ bool correct_cluster(const float2* A, size_t stride, int ld, int n, int kap, int
                      const double* scale, const double2* Sinv, const double2* R, double2* X, double* norms,
                      const int* conv, int first_all, const int* first_flags, unsigned long long* work,
                      cudaStream_t st);
+
+// Tuning knob 9: 1 (default) runs U12 = L11^{-1} A12 with persistent CTAs
+// (contiguous runs of column tiles, the next tile copied by cp.async while
+// the current one is multiplied), 0 with one CTA per column tile.
+extern int g_trsm_persist;

@@ -529,6 +529,10 @@ extern "C" must_status must_tune_set(int32_t knob, int32_t value) {
     case 7:   // CTAs per cluster of the cluster correction
       if (!correct_cluster_set_ctas(value)) { must_set_error("cluster CTAs must be 2, 4 or 8"); return MUST_EINVAL; }
       return MUST_OK;
+    case 9:   // U12 solve: persistent CTAs with copies overlapped (1) or one CTA per tile (0)
+      if (value != 0 && value != 1) { must_set_error("U12 solve kernel must be 0 or 1"); return MUST_EINVAL; }
+      g_trsm_persist = value;
+      return MUST_OK;
     case 8:   // right-hand sides per cluster of the cluster correction
       if (!correct_cluster_set_rhs(value)) { must_set_error("cluster right-hand sides must be 0, 4, 8 or 16"); return MUST_EINVAL; }
       return MUST_OK;
@@ -548,6 +552,7 @@ extern "C" int32_t must_tune_get(int32_t knob) {
     case 6: return g_corr_cluster;
     case 7: return correct_cluster_get_ctas();
     case 8: return correct_cluster_get_rhs();
+    case 9: return g_trsm_persist;
   }
   return -1;
 }

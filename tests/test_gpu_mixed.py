@@ -190,3 +190,26 @@ def test_cluster_correction_matches_one_cta_correction(B, orc, case):
         assert rel_fro(t, ref).max() <= TOLMIX
     for t in taus[1:]:
         assert rel_fro(t, taus[0]).max() <= TOLMIX
+
+
+def test_persistent_u12_solve_matches_per_tile_kernel(B):
+    """The persistent U12 solve (knob 9 = 1, the default) runs the same
+    products in the same order as the one-CTA-per-tile kernel (knob 9 = 0):
+    tau_00 is identical bit for bit, on a ragged order (n = 387) and on the
+    135-site LIZ (several items per run and runs crossing items)."""
+    rng = np.random.default_rng(12)
+    pos, _ = wl.fcc_cluster(3)
+    ws = [wl.Workload("ragged387", 2, [wl.Liz(pos, rng.integers(0, 2, pos.shape[0]).astype(np.int32))],
+                      wl.semicircle_contour(5), wl.spin_depths(2), wl.R_MT), wl.liz135(n_e=4)]
+    old = B.must_tune_get(9)
+    try:
+        for w in ws:
+            taus = []
+            for v in (1, 0):
+                B.must_tune_set(9, v)
+                tau, st = _gpu_tau(B, w, 1, residual=3)
+                assert (st == 0).all()
+                taus.append(tau)
+            assert np.array_equal(taus[0], taus[1])
+    finally:
+        B.must_tune_set(9, old)
