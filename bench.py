@@ -921,7 +921,7 @@ def main():
                          "2 measured 5%% faster than 1, 4 no faster than 2)")
     ap.add_argument("--train-lizs", type=int, default=1667,
                     help="warmstart mode: random 135-site training LIZs (x 2 spins x 15 predicted points; "
-                         "1667 LIZs give the 50k training samples of the design)")
+                         "1667 LIZs give 50k training samples)")
     ap.add_argument("--shard", default="slices", choices=["slices", "balanced"],
                     help="supercell mode under torchrun: every rank its own n-lizs LIZs (weak scaling), or the "
                          "first n-lizs LIZs split over the ranks by the cost sum n^3 (shard.py, strong scaling)")

@@ -165,7 +165,7 @@ size_t must_batch_workspace_bytes(int32_t n_liz, const must_liz* const* lizs, in
                                   const must_solve_opts* opts);
 
 /*
- * Batched plan (the batched launch of the design, captured in a CUDA graph):
+ * Batched plan (the batched launch captured in a CUDA graph):
  * the complete launch sequence of one must_tau00_batch call with these
  * arguments is captured once into a CUDA graph; must_plan_launch replays it
  * on `stream`, so repeated solves with new contents in the same E / tinv
@@ -289,7 +289,7 @@ must_status must_tau00_solve_static(const must_liz* liz, int32_t nE, const doubl
 size_t must_static_scratch_bytes(void);
 
 /*
- * Learned warm start (design growth item 4; the paper has no learned part).
+ * Learned warm start (an extension; the paper has no learned part).
  * A small MLP, three linear layers with SiLU between them, BF16 weights with
  * FP32 accumulation and FP32 master weights / Adam moments, trained and
  * evaluated by the library's own kernels.  It predicts tau_00(E_k) from

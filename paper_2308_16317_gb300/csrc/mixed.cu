@@ -1,4 +1,4 @@
-// Mixed-precision path (growth item 1 of the design: low-precision
+// Mixed-precision path (an extension beyond the paper's FP64 method: low-precision
 // factorisation on the tensor cores + FP64 iterative refinement).
 //
 //   M_s = D M D, D = diag(|M_aa|^{-1/2})        (symmetric equilibration)

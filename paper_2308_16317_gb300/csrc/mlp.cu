@@ -1,4 +1,4 @@
-// Learned warm start for the refinement (design growth item 4): a small MLP
+// Learned warm start for the refinement (an extension; the paper has no learned part): a small MLP
 // (three linear layers with SiLU between them) that predicts tau_00(E_k) from
 // tau_00 at the neighbouring contour energies and the LIZ's species
 // occupancy.  BF16 weights for the products, FP32 accumulation, FP32 master
