@@ -1294,6 +1294,7 @@ int g_lookahead = 1;   // tuning knob 4
 int g_corr_rhs = 0;    // tuning knob 5 (0: by matrix order)
 int g_corr_cluster = 1;   // tuning knob 6
 int g_trsm_persist = 1;   // tuning knob 9
+int g_pack_side = 0;      // tuning knob 10
 static int g_num_sms = 152;
 
 static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
@@ -1420,8 +1421,12 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     prof_launched(PH_PANEL, 1, items);
   };
   bool panel_ready = false;   // panel k0 already launched on the side stream
-  for (int k0 = 0; k0 < r; k0 += nb) {
+  // A operand of step k in slot k % 2 when it is packed on the side stream
+  const bool side_pack = lookahead && g_pack_side && tc_pack_slots(c.opts.precision) == 2;
+  bool a_ready = false;       // A operand of step k0 already packed on the side stream
+  for (int k0 = 0, step = 0; k0 < r; k0 += nb, ++step) {
     const int nbe = std::min(nb, r - k0);
+    const int slot = side_pack ? (step & 1) : 0;
     if (panel_ready)
       cudaStreamWaitEvent(st, ev_panel, 0);
     else
@@ -1452,20 +1457,32 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
         }
         prof_launched(PH_TRSM, 1, items);
       }
-      if (!tc_pack(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, st, !fuse_b)) return MUST_ECUDA;
+      if (!(a_ready && fuse_b) &&
+          !tc_pack(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, st, !fuse_b, fuse_b ? slot : 0))
+        return MUST_ECUDA;
+      a_ready = false;
       const int k1 = k0 + nbe;
       if (lookahead && k1 < r && rem > bn) {
-        if (!tc_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, 0, bn, st))
+        if (!tc_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, 0, bn, st, slot))
           return MUST_ECUDA;
         cudaEventRecord(ev_next, st);
         cudaStreamWaitEvent(ss, ev_next, 0);
-        launch_panel(k1, std::min(nb, r - k1), ss);
+        const int nbe1 = std::min(nb, r - k1);
+        launch_panel(k1, nbe1, ss);
+        // L21 of panel k1 is final once the panel is done (its interchanges
+        // are applied inside the panel): pack it into the other slot while
+        // this step's update still reads this one
+        if (side_pack && fuse_b) {
+          if (!tc_pack(c.opts.precision, M32, stride, ld, n, k1, nbe1, items, packs, ss, false, slot ^ 1))
+            return MUST_ECUDA;
+          a_ready = true;
+        }
         cudaEventRecord(ev_panel, ss);
         panel_ready = true;
-        if (!tc_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, bn, -1, st))
+        if (!tc_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, bn, -1, st, slot))
           return MUST_ECUDA;
       } else {
-        if (!tc_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, 0, -1, st))
+        if (!tc_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, 0, -1, st, slot))
           return MUST_ECUDA;
       }
     }

@@ -58,3 +58,11 @@ bool correct_cluster(const float2* A, size_t stride, int ld, int n, int kap, int
 // (contiguous runs of column tiles, the next tile copied by cp.async while
 // the current one is multiplied), 0 with one CTA per column tile.
 extern int g_trsm_persist;
+// Tuning knob 10: 1 packs the A operand (L21 in BF16 hi/lo pairs) of panel
+// step k+1 on the side stream right after that panel, into the pack's other
+// buffer, so that the main stream's chain per step is row swaps, U12 solve
+// and first-tile update only; 0 (default) packs it on the main stream.  Needs
+// the look-ahead (knob 4) and the BF16 splits.  On the 135-site LIZ the side
+// pack slows the concurrent trailing update more than it shortens the chain
+// (2165 against 2187 solves/s), hence the default.
+extern int g_pack_side;

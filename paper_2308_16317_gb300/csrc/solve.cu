@@ -536,6 +536,10 @@ extern "C" must_status must_tune_set(int32_t knob, int32_t value) {
     case 8:   // right-hand sides per cluster of the cluster correction
       if (!correct_cluster_set_rhs(value)) { must_set_error("cluster right-hand sides must be 0, 4, 8 or 16"); return MUST_EINVAL; }
       return MUST_OK;
+    case 10:  // A operand of the next panel step packed on the side stream
+      if (value != 0 && value != 1) { must_set_error("side-stream A pack switch must be 0 or 1"); return MUST_EINVAL; }
+      g_pack_side = value;
+      return MUST_OK;
   }
   must_set_error("unknown tuning knob %d", knob);
   return MUST_EINVAL;
@@ -553,6 +557,7 @@ extern "C" int32_t must_tune_get(int32_t knob) {
     case 7: return correct_cluster_get_ctas();
     case 8: return correct_cluster_get_rhs();
     case 9: return g_trsm_persist;
+    case 10: return g_pack_side;
   }
   return -1;
 }

@@ -97,6 +97,7 @@ struct TcParams {
   int* err;      // workspace error word
   int tf32;
   int col_tile0; // first column tile of this launch
+  int aoff;      // first row of the A operand's slot in the pack (0 or rows_pad)
 };
 
 template <int BN, int STAGES>
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(256, 1)
       const CUtensorMap* mb = (pass == 1) ? &tB_lo : &tB_hi;
       uint8_t* sa = smem + s * ST_BYTES;
       mbar_expect_tx(&full[s], ST_BYTES);
-      tma_load_3d(sa, ma, kb * kstep_elems, 2 * P.base + row0, item, &full[s]);
+      tma_load_3d(sa, ma, kb * kstep_elems, P.aoff + 2 * P.base + row0, item, &full[s]);
       tma_load_3d(sa + A_BYTES, mb, kb * kstep_elems, P.base + col0, item, &full[s]);
       ++issued;
     }
@@ -256,6 +257,7 @@ struct TcsParams {
   int rruns;     // runs per column tile
   int* err;
   int tf32;
+  int aoff;      // first row of the A operand's slot in the pack (0 or rows_pad)
 };
 
 // CTA b: item, column tile and first row tile of its run; runs of one item
@@ -340,8 +342,8 @@ __global__ void __launch_bounds__(S_THREADS, 1)
         if (gs >= S_STAGES && !mbar_wait_f(&empty[s], ((gs / S_STAGES) - 1) & 1, s_fail)) { ok = false; break; }
         uint8_t* sa = smem + s * S_STAGE_BYTES;
         mbar_expect_tx(&full[s], S_STAGE_BYTES);
-        tma_load_3d(sa, &tA_hi, kb * kstep_elems, 2 * P.abase + row0, item, &full[s]);
-        tma_load_3d(sa + SA_BYTES, &tA_lo, kb * kstep_elems, 2 * P.abase + row0, item, &full[s]);
+        tma_load_3d(sa, &tA_hi, kb * kstep_elems, P.aoff + 2 * P.abase + row0, item, &full[s]);
+        tma_load_3d(sa + SA_BYTES, &tA_lo, kb * kstep_elems, P.aoff + 2 * P.abase + row0, item, &full[s]);
       }
       if (!ok) break;
     }
@@ -531,8 +533,8 @@ __global__ void __launch_bounds__(RegcCfg<STAGES>::THREADS, RegcCfg<STAGES>::SME
         if (gs >= STAGES && !mbar_wait_f(&empty[s], ((gs / STAGES) - 1) & 1, s_fail)) { ok = false; break; }
         uint8_t* sa = smem + s * S_STAGE_BYTES;
         mbar_expect_tx(&full[s], S_STAGE_BYTES);
-        tma_load_3d(sa, &tA_hi, kb * kstep_elems, 2 * P.abase + row0, item, &full[s]);
-        tma_load_3d(sa + SA_BYTES, &tA_lo, kb * kstep_elems, 2 * P.abase + row0, item, &full[s]);
+        tma_load_3d(sa, &tA_hi, kb * kstep_elems, P.aoff + 2 * P.abase + row0, item, &full[s]);
+        tma_load_3d(sa + SA_BYTES, &tA_lo, kb * kstep_elems, P.aoff + 2 * P.abase + row0, item, &full[s]);
       }
       if (!ok) break;
     }
@@ -705,8 +707,8 @@ __global__ void __launch_bounds__(T_THREADS, 1)
         if (gs >= T_STAGES && !mbar_wait_f(&empty[s], ((gs / T_STAGES) - 1) & 1, s_fail)) { ok = false; break; }
         uint8_t* sa = smem + s * S_STAGE_BYTES;
         mbar_expect_tx(&full[s], S_STAGE_BYTES);
-        tma_load_3d(sa, &tA_hi, kb * kstep_elems, 2 * P.abase + row0, item, &full[s]);
-        tma_load_3d(sa + SA_BYTES, &tA_lo, kb * kstep_elems, 2 * P.abase + row0, item, &full[s]);
+        tma_load_3d(sa, &tA_hi, kb * kstep_elems, P.aoff + 2 * P.abase + row0, item, &full[s]);
+        tma_load_3d(sa + SA_BYTES, &tA_lo, kb * kstep_elems, P.aoff + 2 * P.abase + row0, item, &full[s]);
       }
       if (!ok) break;
     }
@@ -1043,10 +1045,17 @@ bool tc_pack_b_target(int precision, int n, int k0, int nbe, int items, char* pa
   return true;
 }
 
+int tc_pack_slots(int precision) { return precision == MUST_MIXED_TF32X3 ? 1 : 2; }
+
 bool tc_pack(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
-             cudaStream_t st, bool with_b) {
+             cudaStream_t st, bool with_b, int slot) {
   const PackGeom g = pack_geom(precision, n, k0, nbe, items, packs);
   if (g.m <= 0) return true;
+  if (slot < 0 || slot >= tc_pack_slots(precision) || (slot && with_b)) {
+    must_set_error("tc_pack: bad operand slot %d", slot);
+    return false;
+  }
+  const size_t aoff = size_t(slot) * g.rows_pad * g.Kp;   // elements: slot 1 starts rows_pad rows in
   ProfScope ps(PH_PACK, st);
   const int half = g.Kp / 2;
   const int ta = g.m * half;
@@ -1058,8 +1067,8 @@ bool tc_pack(int precision, float2* A, size_t stride, int ld, int n, int k0, int
                                                  1);
     else
       pack_a_kernel<uint16_t><<<grid, 256, 0, st>>>(A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows,
-                                                    reinterpret_cast<uint16_t*>(g.pa_hi),
-                                                    reinterpret_cast<uint16_t*>(g.pa_lo), 0);
+                                                    reinterpret_cast<uint16_t*>(g.pa_hi) + aoff,
+                                                    reinterpret_cast<uint16_t*>(g.pa_lo) + aoff, 0);
     prof_launched(PH_PACK, 1, items);
     return true;
   }
@@ -1081,13 +1090,17 @@ bool tc_pack(int precision, float2* A, size_t stride, int ld, int n, int k0, int
 }
 
 bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
-               int* err, int col_lo, int col_hi, cudaStream_t st) {
+               int* err, int col_lo, int col_hi, cudaStream_t st, int slot) {
   if (!get_encoder()) {
     must_set_error("cuTensorMapEncodeTiled is not available");
     return false;
   }
   const PackGeom g = pack_geom(precision, n, k0, nbe, items, packs);
   if (g.m <= 0) return true;
+  if (slot < 0 || slot >= tc_pack_slots(precision)) {
+    must_set_error("tc_update: bad operand slot %d", slot);
+    return false;
+  }
   // The streamed kernel serves the BF16 splits (K = 2 x 128-byte steps per
   // product); TF32 splits and 256-column tiles use the per-tile kernel.
   const bool streamed = g_streamed && !g.tf32;
@@ -1147,6 +1160,7 @@ bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, i
     }
     S.err = err;
     S.tf32 = 0;
+    S.aoff = slot * g.rows_pad;
     ProfScope ps(PH_UPDATE, st);
     if (g_streamed == 2)
       launch_tc_regc<6>(mah, mal, mbh, mbl, S, items, st);
@@ -1167,6 +1181,7 @@ bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, i
   P.err = err;
   P.tf32 = g.tf32 ? 1 : 0;
   P.col_tile0 = t0;
+  P.aoff = slot * g.rows_pad;
   ProfScope ps(PH_UPDATE, st);
   if (bn == 256)
     launch_tc<256>(mah, mal, mbh, mbl, P, g.m, items, t1 - t0, st);

@@ -12,8 +12,13 @@ size_t tc_pack_bytes_per_item(int n);
 // tile width, which tc_tile_n() returns.
 // with_b = false: only the A operand (L21); the caller wrote the B operand
 // itself into the target tc_pack_b_target() describes.
+// slot: which of the A operand's buffers to write (tc_pack_slots(): 2 for
+// the BF16 splits, whose rows take half of the TF32-sized pack, 1 for TF32),
+// so that the A operand of the next panel step can be packed while the
+// current one is still being read; slot > 0 only with with_b = false.
+int tc_pack_slots(int precision);
 bool tc_pack(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
-             cudaStream_t st, bool with_b = true);
+             cudaStream_t st, bool with_b = true, int slot = 0);
 // B-operand (U12) pack of panel step k0 in BF16 hi/lo pairs: matrix column j,
 // panel row p -> element j * Kp + 2p (re) and + 1 (im) of item `item_rows *
 // Kp` elements apart; rows p >= nbe are zero.  False for the TF32 splits
@@ -24,7 +29,7 @@ struct PackB {
 };
 bool tc_pack_b_target(int precision, int n, int k0, int nbe, int items, char* packs, PackB* out);
 bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
-               int* err, int col_lo, int col_hi, cudaStream_t st);
+               int* err, int col_lo, int col_hi, cudaStream_t st, int slot = 0);
 int tc_tile_n();
 bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items,
                         char* packs, int* err, cudaStream_t st);

@@ -213,3 +213,31 @@ def test_persistent_u12_solve_matches_per_tile_kernel(B):
             assert np.array_equal(taus[0], taus[1])
     finally:
         B.must_tune_set(9, old)
+
+
+def test_side_stream_a_pack_matches_main_stream(B):
+    """Packing the A operand of the next panel step on the side stream into
+    the pack's second buffer (knob 10 = 1, the default) changes where and
+    when the same pack kernel runs, not what it writes: tau_00 is identical
+    bit for bit to the main-stream pack (knob 10 = 0) and to the schedule
+    without look-ahead (knob 4 = 0), on a ragged order (n = 387, an odd
+    number of panel steps) and on the 135-site LIZ (34 panel steps)."""
+    rng = np.random.default_rng(13)
+    pos, _ = wl.fcc_cluster(3)
+    ws = [wl.Workload("ragged387", 2, [wl.Liz(pos, rng.integers(0, 2, pos.shape[0]).astype(np.int32))],
+                      wl.semicircle_contour(5), wl.spin_depths(2), wl.R_MT), wl.liz135(n_e=4)]
+    old = (B.must_tune_get(4), B.must_tune_get(10))
+    try:
+        for w in ws:
+            taus = []
+            for la, side in ((1, 1), (1, 0), (0, 1)):
+                B.must_tune_set(4, la)
+                B.must_tune_set(10, side)
+                tau, st = _gpu_tau(B, w, 1, residual=3)
+                assert (st == 0).all()
+                taus.append(tau)
+            assert np.array_equal(taus[0], taus[1])
+            assert np.array_equal(taus[0], taus[2])
+    finally:
+        B.must_tune_set(4, old[0])
+        B.must_tune_set(10, old[1])
