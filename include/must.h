@@ -259,11 +259,11 @@ must_status must_site_density(int32_t lmax, int32_t nE, const double* E, const d
  *   knob 9: U12 = L11^-1 A12 of the mixed path: 1 (default) persistent CTAs
  *           (contiguous runs of 64-column tiles, the next tile copied while
  *           the current one is multiplied), 0 one CTA per tile;
- *   knob 10: with the look-ahead and the BF16 splits, 1 packs the A operand
- *           (L21 as BF16 hi/lo pairs) of panel step k+1 on the side stream
- *           right after that panel, into the second of two buffers, so the
- *           caller's stream does not wait for it; 0 (default) packs it on the
- *           caller's stream.  Both give identical results.
+ *   knob 10: where the mixed path packs the A operand (L21 as BF16 hi/lo
+ *           pairs) of each panel step: 0 a pack kernel on the caller's
+ *           stream, 1 a pack kernel on the look-ahead's side stream, 2 the
+ *           panel kernel itself; all three write the same values
+ *           (default 0, the fastest on the 135-site LIZ).
  * Process-wide; set them between calls, not while solves are being enqueued.
  */
 must_status must_tune_set(int32_t knob, int32_t value);

@@ -31,6 +31,17 @@ __device__ __forceinline__ void argmax_merge(float& v, int& i, float v2, int i2)
 
 __device__ __forceinline__ float cnormf(cf a) { return a.x * a.x + a.y * a.y; }
 
+// BF16 hi/lo split of a complex FP32 pair: hi = rn(x), lo = rn(x - hi), the
+// real part in the low half of each 32-bit word (element 2p of a pack row).
+__device__ __forceinline__ unsigned bf16x2_split(float re, float im, unsigned& lo) {
+  const __nv_bfloat16 hr = __float2bfloat16_rn(re), hi_ = __float2bfloat16_rn(im);
+  const __nv_bfloat16 lr = __float2bfloat16_rn(re - __bfloat162float(hr));
+  const __nv_bfloat16 li = __float2bfloat16_rn(im - __bfloat162float(hi_));
+  lo = unsigned(__bfloat16_as_ushort(lr)) | (unsigned(__bfloat16_as_ushort(li)) << 16);
+  return unsigned(__bfloat16_as_ushort(hr)) | (unsigned(__bfloat16_as_ushort(hi_)) << 16);
+}
+
+
 }  // namespace
 
 // ------------------------------------------------------------ FP32 panel --
@@ -58,7 +69,9 @@ __host__ __device__ inline int leaf_width(int n) {
 
 __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int r,
                                                       int k0, int nbe, int* __restrict__ piv0, int* __restrict__ status,
-                                                      const int* __restrict__ conv, float2* __restrict__ Linv0) {
+                                                      const int* __restrict__ conv, float2* __restrict__ Linv0,
+                                                      uint16_t* __restrict__ pa_hi, uint16_t* __restrict__ pa_lo,
+                                                      int Kp, int pa_rows) {
   extern __shared__ cf Lf[];           // leaf, column-major [lw][mrows]
   __shared__ float sv[PPT / 32];
   __shared__ int si[PPT / 32];
@@ -292,6 +305,41 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
     Li[col * 64 + lane] = v0;
     Li[col * 64 + lane + 32] = v1;
   }
+  if (!pa_hi) return;
+  // The A operand of this step's trailing update (L21 in BF16 hi/lo pairs,
+  // the layout of the separate pack kernel: rows 2i = (Lr, -Li), 2i+1 =
+  // (Li, Lr) for matrix rows i >= k0 + nbe, word p per panel column p, zero
+  // for p >= nbe), staged through shared memory 64 rows at a time so that
+  // the loads (a column segment per warp) and the stores (a pack row per
+  // warp) are both coalesced.  The final row order of L21 is known only now.
+  __syncthreads();
+  cf (*T)[65] = reinterpret_cast<cf (*)[65]>(Lf);   // [64 rows][64 columns + pad]
+  const int KW = Kp / 2;                              // 32-bit words per pack row
+  unsigned* phi = reinterpret_cast<unsigned*>(pa_hi + size_t(item) * pa_rows * Kp);
+  unsigned* plo = reinterpret_cast<unsigned*>(pa_lo + size_t(item) * pa_rows * Kp);
+  for (int i0 = k0 + nbe; i0 < n; i0 += 64) {
+    for (int q = warp; q < 64; q += PPT / 32)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rr = lane + 32 * h, i = i0 + rr;
+        T[rr][q] = (q < nbe && i < n) ? A[size_t(k0 + q) * ld + i] : mkf(0.f, 0.f);
+      }
+    __syncthreads();
+    for (int t = tid; t < 64 * KW; t += PPT) {
+      const int rr = t / KW, p = t % KW, i = i0 + rr;
+      if (i < n) {
+        const cf v = T[rr][p];
+        unsigned l0, l1;
+        const unsigned h0 = bf16x2_split(v.x, -v.y, l0);
+        const unsigned h1 = bf16x2_split(v.y, v.x, l1);
+        phi[size_t(2 * i) * KW + p] = h0;
+        plo[size_t(2 * i) * KW + p] = l0;
+        phi[size_t(2 * i + 1) * KW + p] = h1;
+        plo[size_t(2 * i + 1) * KW + p] = l1;
+      }
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void laswp32_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int r, int k0, int nbe,
@@ -326,14 +374,6 @@ constexpr size_t TRSM_SMEM = size_t(64 * 64 + TRSM_COLS * 65) * sizeof(cf);
 // (< 32) takes the terms j < 32 only and row i1 all 64 (zero terms add
 // exactly nothing).  With bhi != nullptr the tile is also written as the
 // tensor-core B operand (BF16 hi/lo pairs; row p of column j at j * Kp + 2p).
-__device__ __forceinline__ unsigned bf16x2_split(float re, float im, unsigned& lo) {
-  const __nv_bfloat16 hr = __float2bfloat16_rn(re), hi_ = __float2bfloat16_rn(im);
-  const __nv_bfloat16 lr = __float2bfloat16_rn(re - __bfloat162float(hr));
-  const __nv_bfloat16 li = __float2bfloat16_rn(im - __bfloat162float(hi_));
-  lo = unsigned(__bfloat16_as_ushort(lr)) | (unsigned(__bfloat16_as_ushort(li)) << 16);
-  return unsigned(__bfloat16_as_ushort(hr)) | (unsigned(__bfloat16_as_ushort(hi_)) << 16);
-}
-
 __global__ void __launch_bounds__(256) trsm_inv_kernel(float2* __restrict__ A0, size_t stride, int ld, int n, int k0,
                                                        int nbe, const float2* __restrict__ Linv0,
                                                        uint16_t* __restrict__ bhi0, uint16_t* __restrict__ blo0,
@@ -1300,7 +1340,8 @@ static int g_num_sms = 152;
 static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  if (g_side.s == nullptr || g_side.dev != dev) {
+  SideStream& g = g_side;
+  if (g.s == nullptr || g.dev != dev) {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
     SideStream n;
@@ -1311,11 +1352,11 @@ static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
       cudaGetLastError();
       return false;
     }
-    g_side = n;
+    g = n;
   }
-  *s = g_side.s;
-  *e1 = g_side.e1;
-  *e2 = g_side.e2;
+  *s = g.s;
+  *e1 = g.e1;
+  *e2 = g.e2;
   return true;
 }
 
@@ -1414,23 +1455,36 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   cudaEvent_t ev_next = nullptr, ev_panel = nullptr;
   const bool lookahead = g_lookahead && side_stream(&ss, &ev_next, &ev_panel);
   const size_t panel_smem = std::max(size_t(leaf_width(n)) * n, size_t(64 * 65)) * sizeof(float2);
-  const int bn = tc_tile_n();
-  auto launch_panel = [&](int k, int w, cudaStream_t s) {
+  // columns of the look-ahead's first update launch: the next panel alone
+  // when the update's tiles are one panel wide (the streamed kernels of the
+  // BF16 splits), else one tile
+  const int bn = (tc_get_streamed() && c.opts.precision != MUST_MIXED_TF32X3) ? nb : tc_tile_n();
+  // where the A operand (L21 as BF16 pairs) of each step is packed (knob 10):
+  // 0 a pack kernel on the main stream, 1 a pack kernel on the side stream
+  // after the next panel, 2 by the panel kernel itself; 1 and 2 alternate the
+  // pack's two slots so that step k+1's operand is written while step k's
+  // update still reads the other
+  const int two = tc_pack_slots(c.opts.precision) == 2;
+  const int apack = !two ? 0 : (g_pack_side == 1 && !lookahead) ? 0 : g_pack_side;
+  auto launch_panel = [&](int k, int w, int slot, cudaStream_t s) {
+    PackB pa = {nullptr, nullptr, 0, 0};
+    if (apack == 2 && !(tc_pack_a_target(c.opts.precision, n, k, w, items, packs, slot, &pa) && pa.Kp == 128))
+      pa.hi = pa.lo = nullptr;
     ProfScope ps(PH_PANEL, s);
-    panel32_kernel<<<items, PPT, panel_smem, s>>>(M32, stride, ld, n, r, k, w, c.piv, c.status, conv, Linv);
+    panel32_kernel<<<items, PPT, panel_smem, s>>>(M32, stride, ld, n, r, k, w, c.piv, c.status, conv, Linv, pa.hi,
+                                                  pa.lo, pa.Kp, pa.item_rows);
     prof_launched(PH_PANEL, 1, items);
+    return pa.hi != nullptr;
   };
   bool panel_ready = false;   // panel k0 already launched on the side stream
-  // A operand of step k in slot k % 2 when it is packed on the side stream
-  const bool side_pack = lookahead && g_pack_side && tc_pack_slots(c.opts.precision) == 2;
-  bool a_ready = false;       // A operand of step k0 already packed on the side stream
+  bool a_ready = false;       // A operand of step k0 already packed (side stream or panel)
   for (int k0 = 0, step = 0; k0 < r; k0 += nb, ++step) {
     const int nbe = std::min(nb, r - k0);
-    const int slot = side_pack ? (step & 1) : 0;
+    const int slot = apack ? (step & 1) : 0;
     if (panel_ready)
       cudaStreamWaitEvent(st, ev_panel, 0);
     else
-      launch_panel(k0, nbe, st);
+      a_ready = launch_panel(k0, nbe, slot, st);
     panel_ready = false;
     {
       ProfScope ps(PH_SWAP, st);
@@ -1468,11 +1522,11 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
         cudaEventRecord(ev_next, st);
         cudaStreamWaitEvent(ss, ev_next, 0);
         const int nbe1 = std::min(nb, r - k1);
-        launch_panel(k1, nbe1, ss);
+        a_ready = launch_panel(k1, nbe1, slot ^ 1, ss);
         // L21 of panel k1 is final once the panel is done (its interchanges
         // are applied inside the panel): pack it into the other slot while
         // this step's update still reads this one
-        if (side_pack && fuse_b) {
+        if (apack == 1 && fuse_b) {
           if (!tc_pack(c.opts.precision, M32, stride, ld, n, k1, nbe1, items, packs, ss, false, slot ^ 1))
             return MUST_ECUDA;
           a_ready = true;

@@ -58,11 +58,13 @@ bool correct_cluster(const float2* A, size_t stride, int ld, int n, int kap, int
 // (contiguous runs of column tiles, the next tile copied by cp.async while
 // the current one is multiplied), 0 with one CTA per column tile.
 extern int g_trsm_persist;
-// Tuning knob 10: 1 packs the A operand (L21 in BF16 hi/lo pairs) of panel
-// step k+1 on the side stream right after that panel, into the pack's other
-// buffer, so that the main stream's chain per step is row swaps, U12 solve
-// and first-tile update only; 0 (default) packs it on the main stream.  Needs
-// the look-ahead (knob 4) and the BF16 splits.  On the 135-site LIZ the side
-// pack slows the concurrent trailing update more than it shortens the chain
-// (2165 against 2187 solves/s), hence the default.
+// Tuning knob 10: where the A operand (L21 as BF16 hi/lo pairs) of each
+// panel step is packed: 0 a pack kernel on the main stream; 1 a pack kernel
+// on the side stream right after the next panel (needs the look-ahead, knob
+// 4); 2 the panel kernel itself, at its end.  1 and 2 alternate the pack's
+// two A buffers so that step k+1's operand is written while step k's update
+// still reads the other.  All three write the same values.  Default 0: on
+// the 135-site LIZ 1 measured 1 % slower (the concurrent pack kernel slows
+// the bandwidth-bound trailing update) and 2 measured 2.4 % slower (the pack
+// adds ~90 us to each panel on its single SM per item).
 extern int g_pack_side;

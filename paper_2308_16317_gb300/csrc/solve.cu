@@ -536,8 +536,8 @@ extern "C" must_status must_tune_set(int32_t knob, int32_t value) {
     case 8:   // right-hand sides per cluster of the cluster correction
       if (!correct_cluster_set_rhs(value)) { must_set_error("cluster right-hand sides must be 0, 4, 8 or 16"); return MUST_EINVAL; }
       return MUST_OK;
-    case 10:  // A operand of the next panel step packed on the side stream
-      if (value != 0 && value != 1) { must_set_error("side-stream A pack switch must be 0 or 1"); return MUST_EINVAL; }
+    case 10:  // where the A operand is packed: main stream, side stream, inside the panel kernel
+      if (value < 0 || value > 2) { must_set_error("A pack placement must be 0, 1 or 2"); return MUST_EINVAL; }
       g_pack_side = value;
       return MUST_OK;
   }

@@ -767,16 +767,22 @@ __global__ void __launch_bounds__(T_THREADS, 1)
       if (lane == 0) mbar_arrive(&aempty[ab]);
       if (!mbar_wait_f(&cfull[cb], (lt / T_CBUF) & 1, s_fail)) break;
       const float* cs = reinterpret_cast<const float*>(cbuf + cb * C_TILE_BYTES);
+      // C - A'B' is formed before the buffer is handed back: the loader's
+      // next TMA write into it (async proxy) must not overtake these reads
+      // (generic proxy), so the values are consumed and the reads fenced
+      // against the async proxy before the release.  (Without this, tiles
+      // came out stale when other kernels ran concurrently on the GPU.)
       float c[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) c[j] = cs[(half * 32 + j) * BM + x];
+      for (int j = 0; j < 32; ++j) c[j] = cs[(half * 32 + j) * BM + x] - __uint_as_float(v[j]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&cfree[cb]);
       const int gr = 2 * P.abase + (rt0 + lt) * BM + x;
       if (gr >= 2 * P.base && gr < 2 * P.n) {   // rows above base stay as they are
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (colb + j < P.n) __stcs(Cg + size_t(colb + j) * P.ld2 + gr, c[j] - __uint_as_float(v[j]));
+          if (colb + j < P.n) __stcs(Cg + size_t(colb + j) * P.ld2 + gr, c[j]);
       }
     }
   } else if (warp == 10 && lane == 0) {
@@ -1046,6 +1052,17 @@ bool tc_pack_b_target(int precision, int n, int k0, int nbe, int items, char* pa
 }
 
 int tc_pack_slots(int precision) { return precision == MUST_MIXED_TF32X3 ? 1 : 2; }
+
+bool tc_pack_a_target(int precision, int n, int k0, int nbe, int items, char* packs, int slot, PackB* out) {
+  const PackGeom g = pack_geom(precision, n, k0, nbe, items, packs);
+  if (g.tf32 || slot < 0 || slot >= tc_pack_slots(precision)) return false;
+  const size_t aoff = size_t(slot) * g.rows_pad * g.Kp;
+  out->hi = reinterpret_cast<uint16_t*>(g.pa_hi) + aoff;
+  out->lo = reinterpret_cast<uint16_t*>(g.pa_lo) + aoff;
+  out->Kp = g.Kp;
+  out->item_rows = g.item_rows;
+  return true;
+}
 
 bool tc_pack(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
              cudaStream_t st, bool with_b, int slot) {

@@ -28,6 +28,11 @@ struct PackB {
   int Kp, item_rows;
 };
 bool tc_pack_b_target(int precision, int n, int k0, int nbe, int items, char* packs, PackB* out);
+// A-operand (L21) pack target of panel step k0 in the given slot, same
+// layout as tc_pack writes (rows 2i, 2i+1 for matrix rows i >= k0 + nbe;
+// item `item_rows * Kp` elements apart; hi/lo already offset to the slot).
+// False for the TF32 splits.
+bool tc_pack_a_target(int precision, int n, int k0, int nbe, int items, char* packs, int slot, PackB* out);
 bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
                int* err, int col_lo, int col_hi, cudaStream_t st, int slot = 0);
 int tc_tile_n();

@@ -180,3 +180,4 @@ def test_autotuner_on_uneven_batch(B, tmp_path):
     finally:
         for k, v in old.items():
             B.must_tune_set(k, v)
+
