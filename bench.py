@@ -152,21 +152,35 @@ def traffic_from_profiles(kernel_key: str, source: str):
         return None
 
 
-def phase_work(phase: str, n: int, kap: int, nb: int, items: int, precision: str, residual: str = "df"):
+def update_bytes(n: int, r: int, nb: int, pair_rows: int = 0) -> int:
+    """C bytes the mixed path's trailing update reads and writes per matrix
+    (16 B per complex-FP32 element per pass): one pass over the m x m
+    trailing block per panel step, or, for paired steps (knob 11), step k's
+    update of panel k+1's columns and rows plus one pass for both steps."""
+    byts, k0 = 0, 0
+    while k0 < r:
+        nbe = min(nb, r - k0)
+        k1 = k0 + nbe
+        if pair_rows > 0 and nbe == nb and k1 + nb <= r and n - (k1 + nb) >= pair_rows:
+            k2 = k1 + nb
+            byts += 16 * (n - k1) * nb + 16 * nb * (n - k2) + 16 * (n - k2) ** 2
+            k0 = k2
+        else:
+            byts += 16 * (n - k1) ** 2
+            k0 = k1
+    return byts
+
+
+def phase_work(phase: str, n: int, kap: int, nb: int, items: int, precision: str, residual: str = "df",
+               pair_rows: int = 0):
     """Algorithmic work of `items` matrices in one phase of one step:
     (amount, unit, bound, kernel source, profile key)."""
     r = n - kap
     if phase == "trailing_update":
         if precision != "fp64":
-            # HBM-bound on the mixed path: every panel step reads and writes the
-            # m x m complex-FP32 trailing block once (16 B per element)
-            byts = 0
-            for k0 in range(0, r, nb):
-                nbe = min(nb, r - k0)
-                m = n - k0 - nbe
-                byts += 16 * m * m
-            return float(byts) * items, "byte", "hbm", "paper_2308_16317_gb300/csrc/tc_gemm.cu", \
-                "tc_update_kernel_fcc135"
+            # HBM-bound on the mixed path: the trailing block read and written once per pass
+            return float(update_bytes(n, r, nb, pair_rows)) * items, "byte", "hbm", \
+                "paper_2308_16317_gb300/csrc/tc_gemm.cu", "tc_update_kernel_fcc135"
         macs = 0
         for k0 in range(0, r, nb):
             nbe = min(nb, r - k0)
@@ -279,7 +293,7 @@ def run_ours(args):
     peaks, peak_kind = load_peaks()
     dom = max((k for k in prof if k not in ("other",)), key=lambda k: prof[k][0])
     roofline = None
-    pw = phase_work(dom, n, kap, nb, 1, prec, args.residual)
+    pw = phase_work(dom, n, kap, nb, 1, prec, args.residual, B.must_tune_get(11))
     if pw is not None:
         per_item, unit, bound, src, key = pw
         ms_d, launches_d, items_d = prof[dom]

@@ -263,7 +263,17 @@ must_status must_site_density(int32_t lmax, int32_t nE, const double* E, const d
  *           pairs) of each panel step: 0 a pack kernel on the caller's
  *           stream, 1 a pack kernel on the look-ahead's side stream, 2 the
  *           panel kernel itself; all three write the same values
- *           (default 0, the fastest on the 135-site LIZ).
+ *           (default 0, the fastest on the 135-site LIZ);
+ *   knob 11: paired panel steps of the mixed path: while the trailing block
+ *           left after two panels has at least this many rows, the two
+ *           steps' trailing updates are applied in one K = 128 pass (half
+ *           the C traffic; the second panel then runs with nothing to
+ *           overlap it).  0 (default) pairs nothing.  BF16 splits with knob
+ *           2 = 3 only;
+ *   knob 12: shape of the cluster correction from the third correction on
+ *           (CTAs per cluster * 100 + right-hand sides per cluster: 204, 404,
+ *           408, 416, 804, 808, 816, ...; 0: the shape of the first two).
+ *           Default 408.
  * Process-wide; set them between calls, not while solves are being enqueued.
  */
 must_status must_tune_set(int32_t knob, int32_t value);

@@ -400,9 +400,16 @@ int correct_cluster_rhs(int n, int kap) {
 bool correct_cluster(const float2* A, size_t stride, int ld, int n, int kap, int items, const int* perm,
                      const double* scale, const double2* Sinv, const double2* R, double2* X, double* norms,
                      const int* conv, int first_all, const int* first_flags, unsigned long long* work,
-                     cudaStream_t st) {
+                     cudaStream_t st, int shape) {
   int G, CL;
   cc_shape(n, kap, &G, &CL);
+  if (shape > 0) {   // CL * 100 + G, if its rows fit the shared memory
+    const int CLs = shape / 100, Gs = shape % 100;
+    if (cc_smem_bytes(n, kap, Gs, CLs) <= 200 * 1024) {
+      G = Gs;
+      CL = CLs;
+    }
+  }
   if (!G) {
     must_set_error("matrix order %d too large for the cluster correction", n);
     return false;

@@ -1335,6 +1335,8 @@ int g_corr_rhs = 0;    // tuning knob 5 (0: by matrix order)
 int g_corr_cluster = 1;   // tuning knob 6
 int g_trsm_persist = 1;   // tuning knob 9
 int g_pack_side = 0;      // tuning knob 10
+int g_pair_rows = 0;      // tuning knob 11
+int g_corr_late = 408;    // tuning knob 12
 static int g_num_sms = 152;
 
 static bool side_stream(cudaStream_t* s, cudaEvent_t* e1, cudaEvent_t* e2) {
@@ -1465,7 +1467,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   // pack's two slots so that step k+1's operand is written while step k's
   // update still reads the other
   const int two = tc_pack_slots(c.opts.precision) == 2;
-  const int apack = !two ? 0 : (g_pack_side == 1 && !lookahead) ? 0 : g_pack_side;
+  const int apack = (!two || g_pair_rows > 0) ? 0 : (g_pack_side == 1 && !lookahead) ? 0 : g_pack_side;
   auto launch_panel = [&](int k, int w, int slot, cudaStream_t s) {
     PackB pa = {nullptr, nullptr, 0, 0};
     if (apack == 2 && !(tc_pack_a_target(c.opts.precision, n, k, w, items, packs, slot, &pa) && pa.Kp == 128))
@@ -1476,46 +1478,94 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     prof_launched(PH_PANEL, 1, items);
     return pa.hi != nullptr;
   };
+  auto do_swap = [&](int k, int w) {
+    ProfScope ps(PH_SWAP, st);
+    laswp32_kernel<<<dim3((n - w + 255) / 256, items), 256, 0, st>>>(M32, stride, ld, n, r, k, w, c.piv);
+    prof_launched(PH_SWAP, 1, items);
+  };
+  // U12 = L11^{-1} A12 of step (k, w) for every column right of its panel;
+  // the BF16 B operand is written by the solve itself, into buffer bslot
+  auto do_trsm = [&](int k, int w, int bslot) {
+    const int rem = n - k - w;
+    PackB pb = {nullptr, nullptr, 0, 0};
+    const bool fuse_b = tc_pack_b_target(c.opts.precision, n, k, w, items, packs, &pb, bslot);
+    ProfScope ps(PH_TRSM, st);
+    const long long tiles = (long long)((rem + TRSM_COLS - 1) / TRSM_COLS) * items;
+    if (g_trsm_persist) {
+      const int grid = int(std::min<long long>(tiles, 2LL * g_num_sms));
+      trsm_inv_persist_kernel<<<grid, 256, TRSMP_SMEM, st>>>(M32, stride, ld, n, k, w, items, Linv,
+                                                             fuse_b ? pb.hi : nullptr, fuse_b ? pb.lo : nullptr,
+                                                             pb.Kp, pb.item_rows);
+    } else {
+      trsm_inv_kernel<<<dim3((rem + TRSM_COLS - 1) / TRSM_COLS, items), 256, TRSM_SMEM, st>>>(
+          M32, stride, ld, n, k, w, Linv, fuse_b ? pb.hi : nullptr, fuse_b ? pb.lo : nullptr, pb.Kp, pb.item_rows);
+    }
+    prof_launched(PH_TRSM, 1, items);
+    return fuse_b;
+  };
+  // Paired steps (knob 11): while the trailing block after two panels has at
+  // least g_pair_rows rows, steps k and k+1 share one pass of the trailing
+  // update with K = 128, which halves its C traffic:
+  //   panel k, swaps, U12_k, A_k; step k's update of panel k+1's columns;
+  //   panel k+1 (on the main stream: no update is left to overlap it);
+  //   its swaps, also applied to the rows of A_k's pack; step k's update of
+  //   the rows of panel k+1 (one row tile); U12_{k+1}, A_{k+1};
+  //   [A_k A_{k+1}] [U12_k; U12_{k+1}] subtracted from the trailing block in
+  //   one pass, its first 64 columns first so that panel k+2 overlaps the rest.
+  // Operands of the first step of a pair in buffers 0, of the second in 1.
+  const bool pairing = g_pair_rows > 0 && two && tc_get_streamed() == 3 && nb == 64;
   bool panel_ready = false;   // panel k0 already launched on the side stream
   bool a_ready = false;       // A operand of step k0 already packed (side stream or panel)
-  for (int k0 = 0, step = 0; k0 < r; k0 += nb, ++step) {
+  for (int k0 = 0, step = 0; k0 < r;) {
     const int nbe = std::min(nb, r - k0);
-    const int slot = apack ? (step & 1) : 0;
+    const int k1 = k0 + nbe;
+    const bool pair = pairing && nbe == nb && k1 + nb <= r && n - (k1 + nb) >= g_pair_rows;
+    const int slot = (apack && !pairing) ? (step & 1) : 0;
     if (panel_ready)
       cudaStreamWaitEvent(st, ev_panel, 0);
     else
       a_ready = launch_panel(k0, nbe, slot, st);
     panel_ready = false;
-    {
-      ProfScope ps(PH_SWAP, st);
-      laswp32_kernel<<<dim3((n - nbe + 255) / 256, items), 256, 0, st>>>(M32, stride, ld, n, r, k0, nbe, c.piv);
-      prof_launched(PH_SWAP, 1, items);
+    do_swap(k0, nbe);
+    if (pair) {
+      const int k2 = k1 + nb;
+      const TcStep sa = {k0, nb, 0, 0}, sb = {k1, nb, 1, 1};
+      do_trsm(k0, nb, 0);
+      if (!tc_pack(c.opts.precision, M32, stride, ld, n, k0, nb, items, packs, st, false, 0)) return MUST_ECUDA;
+      if (!tc_update_steps(c.opts.precision, M32, stride, ld, n, sa, nullptr, items, packs, err, 0, nb, -1, st))
+        return MUST_ECUDA;
+      launch_panel(k1, nb, 1, st);
+      do_swap(k1, nb);
+      if (!tc_pack_swap_rows(c.opts.precision, n, k0, nb, 0, items, packs, c.piv, r, k1, nb, st) ||
+          !tc_update_steps(c.opts.precision, M32, stride, ld, n, sa, nullptr, items, packs, err, nb, -1, 1, st))
+        return MUST_ECUDA;
+      do_trsm(k1, nb, 1);
+      if (!tc_pack(c.opts.precision, M32, stride, ld, n, k1, nb, items, packs, st, false, 1)) return MUST_ECUDA;
+      if (lookahead && k2 < r && n - k2 > bn) {
+        if (!tc_update_steps(c.opts.precision, M32, stride, ld, n, sa, &sb, items, packs, err, 0, bn, -1, st))
+          return MUST_ECUDA;
+        cudaEventRecord(ev_next, st);
+        cudaStreamWaitEvent(ss, ev_next, 0);
+        launch_panel(k2, std::min(nb, r - k2), 0, ss);
+        cudaEventRecord(ev_panel, ss);
+        panel_ready = true;
+        if (!tc_update_steps(c.opts.precision, M32, stride, ld, n, sa, &sb, items, packs, err, bn, -1, -1, st))
+          return MUST_ECUDA;
+      } else if (!tc_update_steps(c.opts.precision, M32, stride, ld, n, sa, &sb, items, packs, err, 0, -1, -1, st)) {
+        return MUST_ECUDA;
+      }
+      a_ready = false;
+      k0 = k2;
+      step += 2;
+      continue;
     }
     const int rem = n - k0 - nbe;
     if (rem > 0) {
-      // the BF16 B operand is written by the U12 solve itself
-      PackB pb = {nullptr, nullptr, 0, 0};
-      const bool fuse_b = tc_pack_b_target(c.opts.precision, n, k0, nbe, items, packs, &pb);
-      {
-        ProfScope ps(PH_TRSM, st);
-        const long long tiles = (long long)((rem + TRSM_COLS - 1) / TRSM_COLS) * items;
-        if (g_trsm_persist) {
-          const int grid = int(std::min<long long>(tiles, 2LL * g_num_sms));
-          trsm_inv_persist_kernel<<<grid, 256, TRSMP_SMEM, st>>>(M32, stride, ld, n, k0, nbe, items, Linv,
-                                                                 fuse_b ? pb.hi : nullptr, fuse_b ? pb.lo : nullptr,
-                                                                 pb.Kp, pb.item_rows);
-        } else {
-          trsm_inv_kernel<<<dim3((rem + TRSM_COLS - 1) / TRSM_COLS, items), 256, TRSM_SMEM, st>>>(
-              M32, stride, ld, n, k0, nbe, Linv, fuse_b ? pb.hi : nullptr, fuse_b ? pb.lo : nullptr, pb.Kp,
-              pb.item_rows);
-        }
-        prof_launched(PH_TRSM, 1, items);
-      }
+      const bool fuse_b = do_trsm(k0, nbe, 0);
       if (!(a_ready && fuse_b) &&
           !tc_pack(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, st, !fuse_b, fuse_b ? slot : 0))
         return MUST_ECUDA;
       a_ready = false;
-      const int k1 = k0 + nbe;
       if (lookahead && k1 < r && rem > bn) {
         if (!tc_update(c.opts.precision, M32, stride, ld, n, k0, nbe, items, packs, err, 0, bn, st, slot))
           return MUST_ECUDA;
@@ -1540,6 +1590,8 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
           return MUST_ECUDA;
       }
     }
+    k0 = k1;
+    ++step;
   }
   {
     ProfScope ps_schur(PH_SCHUR, st);
@@ -1646,7 +1698,8 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
       const int* ff = (first && seeded) ? first_flags : nullptr;
       unsigned long long* wc = prof_work_counter(PH_CORRECT);
       if (use_cluster) {
-        if (!correct_cluster(M32, stride, ld, n, kap, items, perm, scale, Sinv, R, X, norms, conv, first, ff, wc, st))
+        if (!correct_cluster(M32, stride, ld, n, kap, items, perm, scale, Sinv, R, X, norms, conv, first, ff, wc, st,
+                             it >= 2 ? g_corr_late : 0))
           return MUST_ECUDA;
       } else if (G == 8)
         correct_kernel<8><<<gcorr, 512, smem_corr, st>>>(M32, stride, ld, n, kap, perm, scale, Sinv, R, X, norms,

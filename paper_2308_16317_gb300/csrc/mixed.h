@@ -52,7 +52,15 @@ int correct_cluster_get_rhs();
 bool correct_cluster(const float2* A, size_t stride, int ld, int n, int kap, int items, const int* perm,
                      const double* scale, const double2* Sinv, const double2* R, double2* X, double* norms,
                      const int* conv, int first_all, const int* first_flags, unsigned long long* work,
-                     cudaStream_t st);
+                     cudaStream_t st, int shape = 0);
+// Tuning knob 12: shape of the cluster correction from the third
+// correction on, when few items are still iterating and each item's chain
+// of substitution steps, not the batch, sets the time: CTAs per cluster *
+// 100 + right-hand sides per cluster (204, 404, 408, 804, 808, ...), or 0 for
+// the shape of the first corrections.  Default 408: on the 135-site LIZ the
+// correction phase drops from 4.89 to 4.65 ms per step (404: 5.06, 804: 5.21,
+// 808: 4.95, 204: 4.93).
+extern int g_corr_late;
 
 // Tuning knob 9: 1 (default) runs U12 = L11^{-1} A12 with persistent CTAs
 // (contiguous runs of column tiles, the next tile copied by cp.async while
@@ -68,3 +76,14 @@ extern int g_trsm_persist;
 // the bandwidth-bound trailing update) and 2 measured 2.4 % slower (the pack
 // adds ~90 us to each panel on its single SM per item).
 extern int g_pack_side;
+// Tuning knob 11: paired panel steps.  While the trailing block left after
+// two panels has at least this many rows, steps k and k+1 are applied to it
+// in one pass of the tensor-core update (K = 128 instead of two passes with
+// K = 64), at the price of factoring panel k+1 with nothing to overlap it;
+// 0 pairs no steps.  Needs the BF16 splits and the TMA-C streamed update
+// kernel (knob 2 = 3); the A pack placement (knob 10) is then 0.  Default 0:
+// on the 135-site LIZ pairing cuts the trailing update from 13.6 to 10.5 ms
+// per step, but the exposed panels cost as much (2186-2217 against 2199
+// solves/s for thresholds 1-1536 rows): the elimination is bound by the
+// chain of panels, not by the update's bandwidth.
+extern int g_pair_rows;

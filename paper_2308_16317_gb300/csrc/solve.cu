@@ -536,6 +536,19 @@ extern "C" must_status must_tune_set(int32_t knob, int32_t value) {
     case 8:   // right-hand sides per cluster of the cluster correction
       if (!correct_cluster_set_rhs(value)) { must_set_error("cluster right-hand sides must be 0, 4, 8 or 16"); return MUST_EINVAL; }
       return MUST_OK;
+    case 11:  // paired panel steps while the trailing block has at least this many rows (0: never)
+      if (value < 0 || value > (1 << 20)) { must_set_error("pairing rows must be in [0, 2^20]"); return MUST_EINVAL; }
+      g_pair_rows = value;
+      return MUST_OK;
+    case 12: {  // cluster correction shape from the third correction on: CL * 100 + G, or 0
+      const int CLs = value / 100, Gs = value % 100;
+      if (value != 0 && !((CLs == 2 || CLs == 4 || CLs == 8) && (Gs == 4 || Gs == 8 || Gs == 16))) {
+        must_set_error("late correction shape must be 0 or CTAs * 100 + right-hand sides (CTAs 2, 4, 8; RHS 4, 8, 16)");
+        return MUST_EINVAL;
+      }
+      g_corr_late = value;
+      return MUST_OK;
+    }
     case 10:  // where the A operand is packed: main stream, side stream, inside the panel kernel
       if (value < 0 || value > 2) { must_set_error("A pack placement must be 0, 1 or 2"); return MUST_EINVAL; }
       g_pack_side = value;
@@ -558,6 +571,8 @@ extern "C" int32_t must_tune_get(int32_t knob) {
     case 8: return correct_cluster_get_rhs();
     case 9: return g_trsm_persist;
     case 10: return g_pack_side;
+    case 11: return g_pair_rows;
+    case 12: return g_corr_late;
   }
   return -1;
 }

@@ -258,6 +258,8 @@ struct TcsParams {
   int* err;
   int tf32;
   int aoff;      // first row of the A operand's slot in the pack (0 or rows_pad)
+  int boff;      // ... of the B operand's slot
+  int aoff2, boff2;   // the second step's slots (tmac kernel with K = 128 only)
 };
 
 // CTA b: item, column tile and first row tile of its run; runs of one item
@@ -631,21 +633,34 @@ __global__ void __launch_bounds__(RegcCfg<STAGES>::THREADS, RegcCfg<STAGES>::SME
 }
 
 // Variant of the register kernel whose C tiles come in by TMA (a loader warp
-// keeps up to 3 tiles in flight in shared memory); the epilogue reads them
-// from there and stores C - A'B' straight to global memory.
-constexpr int T_CBUF = 3;
-constexpr int T_STAGES = 3;
+// keeps up to T_CBUF tiles in flight in shared memory); the epilogue reads
+// them from there and stores C - A'B' straight to global memory.
+// KS = 2: one panel step (K = 64 complex, two 128-byte K steps); KS = 4: two
+// panel steps applied in one pass (K = 128 complex: K steps 0-1 from the
+// first step's operands, 2-3 from the second's, at the row offsets
+// aoff/boff and aoff2/boff2 of their pack slots), which halves the C traffic
+// of the pair; its larger resident B block leaves room for two C buffers.
+template <int KS>
+struct TmacCfg {
+  static constexpr int CBUF = KS == 2 ? 3 : 2;
+  static constexpr int STAGES = 3;
+  static constexpr int B_BYTES = 2 * KS * SB_BYTES;
+  static constexpr size_t SMEM =
+      size_t(STAGES) * S_STAGE_BYTES + B_BYTES + size_t(CBUF) * C_TILE_BYTES + 1024;
+};
 constexpr int T_THREADS = 352;                 // producer, MMA, 8 epilogue warps, C loader
-constexpr size_t T_SMEM = size_t(T_STAGES) * S_STAGE_BYTES + S_B_BYTES + size_t(T_CBUF) * C_TILE_BYTES + 1024;
+static_assert(TmacCfg<2>::SMEM <= 227 * 1024 && TmacCfg<4>::SMEM <= 227 * 1024, "tmac shared memory");
 
+template <int KS>
 __global__ void __launch_bounds__(T_THREADS, 1)
     tc_update_tmac(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                    const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
                    const __grid_constant__ CUtensorMap tC, TcsParams P) {
+  constexpr int T_CBUF = TmacCfg<KS>::CBUF, T_STAGES = TmacCfg<KS>::STAGES, T_B_BYTES = TmacCfg<KS>::B_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* bres = smem + T_STAGES * S_STAGE_BYTES;
-  uint8_t* cbuf = bres + S_B_BYTES;
+  uint8_t* bres = smem + T_STAGES * S_STAGE_BYTES;   // [hi k0 .. k(KS-1), lo k0 .. k(KS-1)]
+  uint8_t* cbuf = bres + T_B_BYTES;
   __shared__ __align__(8) uint64_t full[T_STAGES];
   __shared__ __align__(8) uint64_t empty[T_STAGES];
   __shared__ __align__(8) uint64_t bfull;
@@ -693,22 +708,24 @@ __global__ void __launch_bounds__(T_THREADS, 1)
   const int kstep_elems = KB / 2;
 
   if (warp == 0 && lane == 0) {
-    mbar_expect_tx(&bfull, S_B_BYTES);
-    for (int kb = 0; kb < S_KSTEPS; ++kb) {
-      tma_load_3d(bres + kb * SB_BYTES, &tB_hi, kb * kstep_elems, P.base + col0, item, &bfull);
-      tma_load_3d(bres + (S_KSTEPS + kb) * SB_BYTES, &tB_lo, kb * kstep_elems, P.base + col0, item, &bfull);
+    mbar_expect_tx(&bfull, T_B_BYTES);
+    for (int kb = 0; kb < KS; ++kb) {
+      const int brow = (kb < 2 ? P.boff : P.boff2) + P.base + col0, kc = (kb & 1) * kstep_elems;
+      tma_load_3d(bres + kb * SB_BYTES, &tB_hi, kc, brow, item, &bfull);
+      tma_load_3d(bres + (KS + kb) * SB_BYTES, &tB_lo, kc, brow, item, &bfull);
     }
     int gs = 0;
     for (int lt = 0; lt < ntile; ++lt) {
       const int row0 = (rt0 + lt) * BM;
       bool ok = true;
-      for (int kb = 0; kb < S_KSTEPS; ++kb, ++gs) {
+      for (int kb = 0; kb < KS; ++kb, ++gs) {
         const int s = gs % T_STAGES;
         if (gs >= T_STAGES && !mbar_wait_f(&empty[s], ((gs / T_STAGES) - 1) & 1, s_fail)) { ok = false; break; }
         uint8_t* sa = smem + s * S_STAGE_BYTES;
+        const int arow = (kb < 2 ? P.aoff : P.aoff2) + 2 * P.abase + row0, kc = (kb & 1) * kstep_elems;
         mbar_expect_tx(&full[s], S_STAGE_BYTES);
-        tma_load_3d(sa, &tA_hi, kb * kstep_elems, P.aoff + 2 * P.abase + row0, item, &full[s]);
-        tma_load_3d(sa + SA_BYTES, &tA_lo, kb * kstep_elems, P.aoff + 2 * P.abase + row0, item, &full[s]);
+        tma_load_3d(sa, &tA_hi, kc, arow, item, &full[s]);
+        tma_load_3d(sa + SA_BYTES, &tA_lo, kc, arow, item, &full[s]);
       }
       if (!ok) break;
     }
@@ -723,14 +740,14 @@ __global__ void __launch_bounds__(T_THREADS, 1)
   } else if (warp == 1 && lane == 0) {
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(SBN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
     bool ok = mbar_wait_f(&bfull, 0, s_fail);
-    const uint32_t bh = smem_u32(bres), bl = bh + S_KSTEPS * SB_BYTES;
+    const uint32_t bh = smem_u32(bres), bl = bh + KS * SB_BYTES;
     int gs = 0;
     for (int lt = 0; lt < ntile && ok; ++lt) {
       const int ab = lt & 1;
       if (lt >= 2 && !mbar_wait_f(&aempty[ab], ((lt >> 1) - 1) & 1, s_fail)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t acc = tmem + uint32_t(ab * SBN);
-      for (int kb = 0; kb < S_KSTEPS; ++kb, ++gs) {
+      for (int kb = 0; kb < KS; ++kb, ++gs) {
         const int s = gs % T_STAGES;
         if (!mbar_wait_f(&full[s], (gs / T_STAGES) & 1, s_fail)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -883,6 +900,29 @@ __global__ void pack_b_kernel(const float2* __restrict__ C0, size_t stride, int 
   }
 }
 
+// Row interchanges of a later panel step applied to the A operand of an
+// earlier one: pack rows (2c, 2c+1) <-> (2p, 2p+1) for c in [c0, c0 + nsw),
+// p = piv[c], in order (as the interchanges were applied to the matrix).
+// One CTA per item, one thread per 32-bit word column of the hi and lo rows.
+__global__ void pack_swap_kernel(uint32_t* __restrict__ hi0, uint32_t* __restrict__ lo0, size_t item_words, int KW,
+                                 const int* __restrict__ piv0, int r, int c0, int nsw) {
+  const int item = blockIdx.x, t = threadIdx.x;
+  if (t >= 4 * KW) return;
+  const int arr = t / (2 * KW), sub = (t / KW) & 1, w = t % KW;
+  uint32_t* P = (arr ? lo0 : hi0) + size_t(item) * item_words;
+  const int* piv = piv0 + size_t(item) * r;
+  for (int j = 0; j < nsw; ++j) {
+    const int c = c0 + j, p = piv[c];
+    if (p != c) {
+      uint32_t* x = P + size_t(2 * c + sub) * KW + w;
+      uint32_t* y = P + size_t(2 * p + sub) * KW + w;
+      const uint32_t v = *x;
+      *x = *y;
+      *y = v;
+    }
+  }
+}
+
 // ------------------------------------------------------------- host side --
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -965,15 +1005,17 @@ void launch_tc_regc(const CUtensorMap& mah, const CUtensorMap& mal, const CUtens
   tc_update_regc<STAGES><<<grid, RegcCfg<STAGES>::THREADS, RegcCfg<STAGES>::SMEM, st>>>(mah, mal, mbh, mbl, P);
 }
 
+template <int KS>
 void launch_tc_tmac(const CUtensorMap& mah, const CUtensorMap& mal, const CUtensorMap& mbh, const CUtensorMap& mbl,
                     const CUtensorMap& mc, const TcsParams& P, int items, cudaStream_t st) {
+  constexpr size_t smem = TmacCfg<KS>::SMEM;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(tc_update_tmac, cudaFuncAttributeMaxDynamicSharedMemorySize, int(T_SMEM));
+    cudaFuncSetAttribute(tc_update_tmac<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     attr = true;
   }
   const int grid = P.rruns * P.ct * items;
-  tc_update_tmac<<<grid, T_THREADS, T_SMEM, st>>>(mah, mal, mbh, mbl, mc, P);
+  tc_update_tmac<KS><<<grid, T_THREADS, smem, st>>>(mah, mal, mbh, mbl, mc, P);
 }
 
 int kp_of(bool tf32) {
@@ -1041,17 +1083,36 @@ PackGeom pack_geom(int precision, int n, int k0, int nbe, int items, char* packs
 }
 }  // namespace
 
-bool tc_pack_b_target(int precision, int n, int k0, int nbe, int items, char* packs, PackB* out) {
+bool tc_pack_b_target(int precision, int n, int k0, int nbe, int items, char* packs, PackB* out, int slot) {
   const PackGeom g = pack_geom(precision, n, k0, nbe, items, packs);
-  if (g.tf32) return false;
-  out->hi = reinterpret_cast<uint16_t*>(g.pb_hi);
-  out->lo = reinterpret_cast<uint16_t*>(g.pb_lo);
+  if (g.tf32 || slot < 0 || slot > 1) return false;
+  const size_t boff = size_t(slot) * g.rows_pad * g.Kp;
+  out->hi = reinterpret_cast<uint16_t*>(g.pb_hi) + boff;
+  out->lo = reinterpret_cast<uint16_t*>(g.pb_lo) + boff;
   out->Kp = g.Kp;
   out->item_rows = g.item_rows;
   return true;
 }
 
 int tc_pack_slots(int precision) { return precision == MUST_MIXED_TF32X3 ? 1 : 2; }
+
+bool tc_pack_swap_rows(int precision, int n, int k0, int nbe, int slot, int items, char* packs, const int* piv, int r,
+                       int c0, int nsw, cudaStream_t st) {
+  const PackGeom g = pack_geom(precision, n, k0, nbe, items, packs);
+  if (g.tf32 || slot < 0 || slot > 1 || c0 < g.base || nsw < 0) {
+    must_set_error("tc_pack_swap_rows: bad arguments");
+    return false;
+  }
+  if (nsw == 0 || g.m <= 0) return true;
+  const size_t aoff = size_t(slot) * g.rows_pad * g.Kp;   // BF16 elements
+  const int KW = g.Kp / 2;
+  ProfScope ps(PH_SWAP, st);
+  pack_swap_kernel<<<items, 4 * KW, 0, st>>>(reinterpret_cast<uint32_t*>(reinterpret_cast<uint16_t*>(g.pa_hi) + aoff),
+                                             reinterpret_cast<uint32_t*>(reinterpret_cast<uint16_t*>(g.pa_lo) + aoff),
+                                             size_t(g.item_rows) * KW, KW, piv, r, c0, nsw);
+  prof_launched(PH_SWAP, 1, items);
+  return true;
+}
 
 bool tc_pack_a_target(int precision, int n, int k0, int nbe, int items, char* packs, int slot, PackB* out) {
   const PackGeom g = pack_geom(precision, n, k0, nbe, items, packs);
@@ -1108,14 +1169,29 @@ bool tc_pack(int precision, float2* A, size_t stride, int ld, int n, int k0, int
 
 bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
                int* err, int col_lo, int col_hi, cudaStream_t st, int slot) {
+  return tc_update_steps(precision, A, stride, ld, n, TcStep{k0, nbe, slot, 0}, nullptr, items, packs, err, col_lo,
+                         col_hi, -1, st);
+}
+
+bool tc_update_steps(int precision, float2* A, size_t stride, int ld, int n, TcStep s1, const TcStep* s2, int items,
+                     char* packs, int* err, int col_lo, int col_hi, int row_tiles, cudaStream_t st) {
   if (!get_encoder()) {
     must_set_error("cuTensorMapEncodeTiled is not available");
     return false;
   }
-  const PackGeom g = pack_geom(precision, n, k0, nbe, items, packs);
+  // the trailing block starts after the last step's panel
+  const TcStep& last = s2 ? *s2 : s1;
+  const PackGeom g = pack_geom(precision, n, last.k0, last.nbe, items, packs);
   if (g.m <= 0) return true;
-  if (slot < 0 || slot >= tc_pack_slots(precision)) {
-    must_set_error("tc_update: bad operand slot %d", slot);
+  const int nslots = tc_pack_slots(precision);
+  if (s1.slot < 0 || s1.slot >= nslots || s1.bslot < 0 || s1.bslot >= nslots ||
+      (s2 && (s2->slot < 0 || s2->slot >= nslots || s2->bslot < 0 || s2->bslot >= nslots ||
+              s2->k0 != s1.k0 + s1.nbe || s1.nbe != PANEL_NB))) {
+    must_set_error("tc_update: bad operand slots or steps");
+    return false;
+  }
+  if ((s2 || s1.bslot || row_tiles >= 0) && !(g_streamed == 3 && !g.tf32)) {
+    must_set_error("tc_update: paired steps, B slots and row limits need the TMA-C streamed kernel (knob 2 = 3)");
     return false;
   }
   // The streamed kernel serves the BF16 splits (K = 2 x 128-byte steps per
@@ -1156,6 +1232,8 @@ bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, i
     S.base = g.base;
     S.abase = abase;
     S.rt = (2 * (n - abase) + BM - 1) / BM;
+    if (row_tiles >= 0) S.rt = std::min(S.rt, row_tiles);
+    if (S.rt <= 0) return true;
     S.ct = t1 - t0;
     S.col_tile0 = t0;
     // runs of at most g_run row tiles, evenly split, and enough of them for
@@ -1177,12 +1255,17 @@ bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, i
     }
     S.err = err;
     S.tf32 = 0;
-    S.aoff = slot * g.rows_pad;
+    S.aoff = s1.slot * g.rows_pad;
+    S.boff = s1.bslot * g.rows_pad;
+    S.aoff2 = s2 ? s2->slot * g.rows_pad : 0;
+    S.boff2 = s2 ? s2->bslot * g.rows_pad : 0;
     ProfScope ps(PH_UPDATE, st);
     if (g_streamed == 2)
       launch_tc_regc<6>(mah, mal, mbh, mbl, S, items, st);
+    else if (g_streamed == 3 && s2)
+      launch_tc_tmac<4>(mah, mal, mbh, mbl, mc, S, items, st);
     else if (g_streamed == 3)
-      launch_tc_tmac(mah, mal, mbh, mbl, mc, S, items, st);
+      launch_tc_tmac<2>(mah, mal, mbh, mbl, mc, S, items, st);
     else
       launch_tc_streamed(mah, mal, mbh, mbl, mc, S, items, st);
     prof_launched(PH_UPDATE, 1, items);
@@ -1198,7 +1281,7 @@ bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, i
   P.err = err;
   P.tf32 = g.tf32 ? 1 : 0;
   P.col_tile0 = t0;
-  P.aoff = slot * g.rows_pad;
+  P.aoff = s1.slot * g.rows_pad;
   ProfScope ps(PH_UPDATE, st);
   if (bn == 256)
     launch_tc<256>(mah, mal, mbh, mbl, P, g.m, items, t1 - t0, st);

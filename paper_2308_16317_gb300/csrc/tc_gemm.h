@@ -27,7 +27,8 @@ struct PackB {
   uint16_t *hi, *lo;
   int Kp, item_rows;
 };
-bool tc_pack_b_target(int precision, int n, int k0, int nbe, int items, char* packs, PackB* out);
+// slot: which of the B operand's two buffers (BF16 splits) to target.
+bool tc_pack_b_target(int precision, int n, int k0, int nbe, int items, char* packs, PackB* out, int slot = 0);
 // A-operand (L21) pack target of panel step k0 in the given slot, same
 // layout as tc_pack writes (rows 2i, 2i+1 for matrix rows i >= k0 + nbe;
 // item `item_rows * Kp` elements apart; hi/lo already offset to the slot).
@@ -35,6 +36,25 @@ bool tc_pack_b_target(int precision, int n, int k0, int nbe, int items, char* pa
 bool tc_pack_a_target(int precision, int n, int k0, int nbe, int items, char* packs, int slot, PackB* out);
 bool tc_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items, char* packs,
                int* err, int col_lo, int col_hi, cudaStream_t st, int slot = 0);
+// A panel step's operands in the pack: the step (k0, nbe), and the buffers
+// (slots) holding its A and B operands.
+struct TcStep {
+  int k0, nbe, slot, bslot;
+};
+// Trailing update by one panel step (s2 == nullptr), or by two consecutive
+// steps s1, s2 in one pass (K = 128; s1.nbe must be the panel width): the
+// trailing block starts after the last step's panel.  row_tiles >= 0 limits
+// the update to the first row_tiles tiles of 64 rows of that block (-1: all).
+// Pairs, B slots and row limits need the BF16 splits and the TMA-C streamed
+// kernel (knob 2 = 3).
+bool tc_update_steps(int precision, float2* A, size_t stride, int ld, int n, TcStep s1, const TcStep* s2, int items,
+                     char* packs, int* err, int col_lo, int col_hi, int row_tiles, cudaStream_t st);
+// Applies the row interchanges piv[c] <-> c, c in [c0, c0 + nsw) (in order,
+// piv indexed per item with stride r) to the A operand of step (k0, nbe)
+// held in `slot`: the operand of an earlier step whose rows a later panel
+// has permuted.  BF16 splits only.
+bool tc_pack_swap_rows(int precision, int n, int k0, int nbe, int slot, int items, char* packs, const int* piv, int r,
+                       int c0, int nsw, cudaStream_t st);
 int tc_tile_n();
 bool tc_trailing_update(int precision, float2* A, size_t stride, int ld, int n, int k0, int nbe, int items,
                         char* packs, int* err, cudaStream_t st);

@@ -147,6 +147,20 @@ def test_bench_algorithmic_work_of_the_update():
     ref = sum(16 * (n - k0 - w) ** 2 for k0, w in steps) * items
     assert byts == ref
     assert abs(byts / 65 - 7.905e8) < 0.001e8
+    # paired steps: step k's update of panel k+1's 64 columns and 64 rows, then
+    # one pass for both; pairing every step roughly halves the C traffic
+    b1 = bench.update_bytes(n, n - kap, nb, 1)
+    k0, ref1 = 0, 0
+    while k0 < n - kap:
+        if k0 + 2 * nb <= n - kap and n - (k0 + 2 * nb) >= 1:
+            m1, m2 = n - k0 - nb, n - k0 - 2 * nb
+            ref1 += 16 * (m1 * nb + nb * m2 + m2 * m2)
+            k0 += 2 * nb
+        else:
+            ref1 += 16 * (n - k0 - min(nb, n - kap - k0)) ** 2
+            k0 += nb
+    assert b1 == ref1 and 0.5 < b1 / (byts / items) < 0.6
+    assert bench.update_bytes(n, n - kap, nb, 10 ** 6) * items == byts
     flops = bench.phase_work("trailing_update", n, kap, nb, 1, "fp64")[0]
     unblocked = 8.0 * sum((n - j - 1) ** 2 for j in range(n - kap))
     # the blocked update leaves out the work inside each panel (about nb/2 columns of width m)
@@ -159,7 +173,7 @@ def test_tuning_knobs_validate_and_round_trip():
     (no GPU needed)."""
     from paper_2308_16317_gb300 import binding as B
     cases = {6: ([0, 1], [2, -1]), 7: ([2, 4, 8], [3, 16]), 8: ([0, 4, 8, 16], [2, 32]), 5: ([0, 2, 4, 8], [3]),
-             9: ([0, 1], [2]), 10: ([0, 1, 2], [3, -1])}
+             9: ([0, 1], [2]), 10: ([0, 1, 2], [3, -1]), 11: ([0, 1, 1024], [-1]), 12: ([0, 204, 404, 816], [1, 304, 405])}
     for knob, (good, bad) in cases.items():
         old = B.must_tune_get(knob)
         try:

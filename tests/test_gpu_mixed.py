@@ -274,3 +274,63 @@ def test_concurrent_solves_on_two_streams_are_bit_identical(B):
                     assert np.array_equal(blocks_to_numpy(o[0][0]), ref), kern
     finally:
         B.must_tune_set(2, old)
+
+
+@pytest.mark.parametrize("pair_rows", [1, 200])
+def test_paired_steps_match_oracle_and_single_steps(B, orc, pair_rows):
+    """Paired panel steps (knob 11): two steps' trailing updates in one K = 128
+    pass, with the second panel's interchanges applied to the first step's
+    packed A operand and the first step's update of the second panel's rows
+    done separately.  The result follows the oracle within the mixed
+    tolerance and the single-step schedule within it too, on a ragged order
+    (n = 387: pairs, then single steps where no full pair is left, and with
+    pair_rows = 200 a switch from pairs to single steps) and on the 135-site
+    LIZ (with and without look-ahead)."""
+    rng = np.random.default_rng(14)
+    pos, _ = wl.fcc_cluster(3)
+    w = wl.Workload("ragged387", 2, [wl.Liz(pos, rng.integers(0, 2, pos.shape[0]).astype(np.int32))],
+                    wl.semicircle_contour(5), wl.spin_depths(2), wl.R_MT)
+    big = wl.liz135(n_e=4)
+    old = (B.must_tune_get(11), B.must_tune_get(4))
+    try:
+        B.must_tune_set(11, 0)
+        single, st = _gpu_tau(B, w, 1, residual=3)
+        single_big, _ = _gpu_tau(B, big, 1, residual=3)
+        B.must_tune_set(11, pair_rows)
+        paired, st = _gpu_tau(B, w, 1, residual=3)
+        assert (st == 0).all()
+        k = w.kappa()
+        ref, _ = oracle_tau(orc, w, nthreads=ncpu())
+        assert rel_fro(paired.reshape(-1, k, k), ref).max() <= TOLMIX
+        assert rel_fro(paired.reshape(-1, k, k), single.reshape(-1, k, k)).max() <= TOLMIX
+        kb = big.kappa()
+        for la in (1, 0):
+            B.must_tune_set(4, la)
+            pb, stb = _gpu_tau(B, big, 1, residual=3)
+            assert (stb == 0).all()
+            assert rel_fro(pb.reshape(-1, kb, kb), single_big.reshape(-1, kb, kb)).max() <= TOLMIX
+    finally:
+        B.must_tune_set(11, old[0])
+        B.must_tune_set(4, old[1])
+
+
+@pytest.mark.parametrize("late", [404, 808, 204])
+def test_late_correction_shape(B, orc, late):
+    """From the third correction on, few items are still iterating; knob 12
+    gives those launches another cluster shape (more, smaller CTAs per item).
+    The substitutions are the same in another summation order: the result
+    follows the oracle and the default shape within the mixed tolerance, and
+    the same items converge."""
+    w = wl.first_shell_small()
+    old = B.must_tune_get(12)
+    try:
+        B.must_tune_set(12, 0)
+        ref_dev, st0 = _gpu_tau(B, w, 1, residual=3)
+        B.must_tune_set(12, late)
+        tau, st = _gpu_tau(B, w, 1, residual=3)
+    finally:
+        B.must_tune_set(12, old)
+    assert (st == 0).all() and (st0 == 0).all()
+    ref, _ = oracle_tau(orc, w)
+    assert rel_fro(tau.reshape(-1, 9, 9), ref).max() <= TOLMIX
+    assert rel_fro(tau.reshape(-1, 9, 9), ref_dev.reshape(-1, 9, 9)).max() <= TOLMIX
