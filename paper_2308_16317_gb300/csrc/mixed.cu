@@ -31,6 +31,18 @@ __device__ __forceinline__ void argmax_merge(float& v, int& i, float v2, int i2)
 
 __device__ __forceinline__ float cnormf(cf a) { return a.x * a.x + a.y * a.y; }
 
+// (max |z|^2, lowest row index) over the warp, in every lane: two warp
+// reductions instead of five shuffle rounds.  The keys order like the
+// non-negative values (no candidate, value -1: key 0); the index is the
+// lowest among the lanes holding the maximum, as the pairwise merge picks.
+__device__ __forceinline__ void warp_argmax(float& v, int& i) {
+  const unsigned key = v < 0.0f ? 0u : __float_as_uint(v) + 1u;
+  const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+  const unsigned imin = __reduce_min_sync(0xffffffffu, key == kmax ? unsigned(i) : 0xffffffffu);
+  v = kmax == 0u ? -1.0f : __uint_as_float(kmax - 1u);
+  i = int(imin);
+}
+
 // BF16 hi/lo split of a complex FP32 pair: hi = rn(x), lo = rn(x - hi), the
 // real part in the low half of each 32-bit word (element 2p of a pack row).
 __device__ __forceinline__ unsigned bf16x2_split(float re, float im, unsigned& lo) {
@@ -109,11 +121,7 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
     for (int ii = tid; ii < pr; ii += PPT) argmax_merge(best, bi, cnormf(Lf[ii]), ii);
     for (int j = 0; j < lw; ++j) {
       cf* colj = Lf + j * mrows;
-      for (int o = 16; o > 0; o >>= 1) {
-        const float v2 = __shfl_down_sync(0xffffffffu, best, o);
-        const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
-        argmax_merge(best, bi, v2, i2);
-      }
+      warp_argmax(best, bi);
       if (lane == 0) { sv[warp] = best; si[warp] = bi; }
       __syncthreads();
       if (warp == 0) {
@@ -121,11 +129,8 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
         // the merges does not change the winner
         float b = (lane < PPT / 32) ? sv[lane] : -1.0f;
         int p = (lane < PPT / 32) ? si[lane] : j;
-        for (int o = 16; o > 0; o >>= 1) {
-          const float v2 = __shfl_xor_sync(0xffffffffu, b, o);
-          const int i2 = __shfl_xor_sync(0xffffffffu, p, o);
-          argmax_merge(b, p, v2, i2);
-        }
+        warp_argmax(b, p);
+        if (!(b >= 0.0f)) p = j;
         if (lane == 0) {
           if (!(b > 0.0f)) status[item] = ST_SINGULAR;
           piv[c0 + j] = c0 + p;
@@ -143,7 +148,10 @@ __global__ void __launch_bounds__(PPT) panel32_kernel(float2* __restrict__ A0, s
       const bool scan = j + 1 < lw;
       cf* coln = colj + mrows;
       if (cnormf(d) > 0.0f) {
-        const cf inv = cinvf(d);
+        // 1/d = conj(d) / |d|^2 with one correctly rounded reciprocal (the
+        // equilibrated entries are O(1): |d|^2 neither overflows nor underflows)
+        const float rn = __frcp_rn(d.x * d.x + d.y * d.y);
+        const cf inv = mkf(d.x * rn, -d.y * rn);
         for (int ii = j + 1 + tid; ii < mrows; ii += PPT) {
           const cf l = cmulf(colj[ii], inv);
           colj[ii] = l;
