@@ -131,10 +131,12 @@ def code_sha256(path: str) -> str:
     return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()
 
 
-def traffic_from_profiles(kernel_key: str, source: str):
-    """DRAM bytes per launch recorded in profiles/<kernel_key>.txt, if the code
-    of the kernel source it was captured from is unchanged (code_sha256 line);
-    else None."""
+def traffic_from_profiles(kernel_key: str, source: str, algorithmic_per_launch: float | None = None):
+    """DRAM bytes per launch from profiles/<kernel_key>.txt, if the code of the
+    kernel source it was captured from is unchanged (code_sha256 line); else
+    None.  The file gives either the bytes per launch or the ratio of DRAM
+    bytes to algorithmic bytes over a captured step, which is applied to
+    algorithmic_per_launch."""
     path = os.path.join(ROOT, "profiles", kernel_key + ".txt")
     if not os.path.exists(path):
         return None
@@ -147,6 +149,8 @@ def traffic_from_profiles(kernel_key: str, source: str):
     if vals.get("code_sha256") != sha:
         return None
     try:
+        if "dram_to_algorithmic" in vals:
+            return None if algorithmic_per_launch is None else float(vals["dram_to_algorithmic"]) * algorithmic_per_launch
         return float(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
@@ -252,16 +256,30 @@ def run_ours(args):
         s.solve(opts, out=out)
     torch.cuda.synchronize(dev)
     st0 = out[1].cpu().numpy()
+    # the step as a captured plan (must_plan_batch / must_plan_launch): the
+    # whole launch sequence of the call replayed as one CUDA graph, recomputing
+    # everything from E and t^-1 every time
+    plan_nb = B.must_batch_workspace_bytes(s.lizs, items, opts)
+    plan_ws = torch.empty(plan_nb, dtype=torch.uint8, device=dev)
+    plan_out = s.alloc_out(1)
+    plan = None
+    if not args.no_plan:
+        plan = B.must_plan_batch(s.lizs, s.E, s.tinv, s.n_species, s.nspin, opts, plan_ws, plan_nb, plan_out[0],
+                                 plan_out[1])
+        for _ in range(args.warmup):
+            B.must_plan_launch(plan, stream=stream)
+        torch.cuda.synchronize(dev)
 
     sampler = ClockSampler(local)
     if rank == 0:
         sampler.start()
         time.sleep(0.3)
-    def timed_region(profiled: bool):
+    def timed_region(profiled: bool, use_plan: bool = False):
         # K steps between a barrier + synchronize on both sides, CUDA events on
-        # the launching stream; the headline region runs with the library's
-        # per-phase instrumentation off, a second region with it on gives the
-        # phase split and the dominant kernel's launch times
+        # the launching stream; the headline region replays the plan with the
+        # library's per-phase instrumentation off, a second region of direct
+        # calls with it on gives the phase split and the dominant kernel's
+        # launch times
         barrier()
         torch.cuda.synchronize(dev)
         B.must_profile_enable(profiled)
@@ -271,7 +289,10 @@ def run_ours(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            s.solve(opts, out=out)
+            if use_plan:
+                B.must_plan_launch(plan, stream=stream)
+            else:
+                s.solve(opts, out=out)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
@@ -280,12 +301,18 @@ def run_ours(args):
         B.must_profile_enable(False)
         return max_over_ranks(e0.elapsed_time(e1)), l1 - l0, prof
 
-    ms_total, n_launches, _ = timed_region(False)
+    ms_total, n_launches, _ = timed_region(False, use_plan=plan is not None)
     clocks = sampler.stop() if rank == 0 else None
     ms_step = ms_total / args.steps
     value = items * ws * args.steps / (ms_total / 1e3)
-    tau_fast = blocks_to_numpy(out[0][0])
-    status = out[1].cpu().numpy()
+    hout = plan_out if plan is not None else out
+    tau_fast = blocks_to_numpy(hout[0][0])
+    status = hout[1].cpu().numpy()
+    direct = None
+    if plan is not None:
+        ms_direct, _, _ = timed_region(False)
+        direct = {"value": items * ws * args.steps / (ms_direct / 1e3), "ms_per_step": ms_direct / args.steps,
+                  "identical_to_plan": bool(np.array_equal(blocks_to_numpy(out[0][0]), tau_fast))}
     ms_prof_total, _, prof = timed_region(True)
     status_prof = out[1].cpu().numpy()
 
@@ -322,7 +349,7 @@ def run_ours(args):
         else:
             peak = (FP64_PEAK_TFLOPS if dom == "residual" or prec == "fp64" else FP32_PEAK_TFLOPS) * 1e12
             punit, scale = "TFLOP/s", 1e12
-        traffic = traffic_from_profiles(key, src)
+        traffic = traffic_from_profiles(key, src, total / max(launches_d, 1))
         tensor_view = None
         if dom == "trailing_update" and prec != "fp64":
             # the same launches seen as tensor-core work: 24 tensor flops per complex MAC
@@ -383,7 +410,33 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": items * ws * e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(E_h.numel() * 16 + T_h.numel() * 16),
-           "d2h_bytes_per_step": int(tau_h.numel() * 16 + sta_h.numel() * 4)}
+           "d2h_bytes_per_step": int(tau_h.numel() * 16 + sta_h.numel() * 4),
+           "path": "must_tau00_solve with pinned host buffers (staged by the library)"}
+    if plan is not None:
+        # the same through the plan: every step copies E and t^-1 from pinned host
+        # memory into the plan's input buffers, replays it and reads tau_00 and
+        # the status back
+        tau_d, sta_d = plan_out[0][0], plan_out[1][0]
+
+        def e2e_step():
+            s.E.copy_(E_h, non_blocking=True)
+            s.tinv.copy_(T_h, non_blocking=True)
+            B.must_plan_launch(plan, stream=stream)
+            tau_h.copy_(tau_d, non_blocking=True)
+            sta_h.copy_(sta_d, non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            e2e_step()
+        e2e_p = max_over_ranks(time.perf_counter() - t0)
+        e2e_direct = e2e
+        e2e = {"value": items * ws * e_steps / e2e_p, "unit": UNIT,
+               "h2d_bytes_per_step": int(E_h.numel() * 16 + T_h.numel() * 16),
+               "d2h_bytes_per_step": int(tau_h.numel() * 16 + sta_h.numel() * 4),
+               "path": "plan replay (must_plan_launch) with the inputs copied from and tau_00 read back to "
+                       "pinned host memory every step", "direct_call": e2e_direct}
 
     cpu = None
     per_energy = None
@@ -414,6 +467,9 @@ def run_ours(args):
             "rel_err_vs_oracle_per_energy": per_energy,
             "status_ok": bool((status == 0).all() and (st0 == 0).all() and (status_prof == 0).all()),
             "phases": phases, "profiled_ms_per_step": ms_prof_total / args.steps,
+            "timed": "plan replay (the call captured once by must_plan_batch, replayed by must_plan_launch)"
+                     if plan is not None else "direct must_tau00_solve calls",
+            "direct_calls": direct,
         }
         emit(line)
     if ws > 1:
@@ -924,6 +980,8 @@ def main():
                          "tensor-core digit split (default)")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plan", action="store_true",
+                    help="time direct must_tau00_solve calls instead of replays of the captured plan")
     ap.add_argument("--cpu-sample", type=int, default=0)
     ap.add_argument("--workload", default="liz135",
                     choices=["liz135", "supercell", "warmstart", "cusolver", "canted", "paper", "charge", "peaks"],

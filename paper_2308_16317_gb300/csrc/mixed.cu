@@ -1343,7 +1343,7 @@ int g_corr_rhs = 0;    // tuning knob 5 (0: by matrix order)
 int g_corr_cluster = 1;   // tuning knob 6
 int g_trsm_persist = 1;   // tuning knob 9
 int g_pack_side = 0;      // tuning knob 10
-int g_pair_rows = 0;      // tuning knob 11
+int g_pair_rows = 1536;   // tuning knob 11
 int g_corr_late = 408;    // tuning knob 12
 static int g_num_sms = 152;
 

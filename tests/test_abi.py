@@ -60,18 +60,19 @@ def test_host_side_argument_errors_need_no_gpu(lib):
 
 def test_bench_traffic_profile_matches_current_kernel_source():
     """profiles/tc_update_kernel_fcc135.txt carries the sha256 of the code
-    (comments stripped) of the kernel source it was captured from; bench.py
-    reports roofline.traffic only while it matches (a stale capture reads as
-    null)."""
+    (comments stripped) of the kernel source it was captured from and the
+    ratio of DRAM bytes to algorithmic bytes over a captured step; bench.py
+    reports roofline.traffic (that ratio times the algorithmic bytes per
+    launch) only while the sha matches (a stale capture reads as null)."""
     import importlib.util
     import os
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     spec = importlib.util.spec_from_file_location("bench", os.path.join(root, "bench.py"))
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
-    t = bench.traffic_from_profiles("tc_update_kernel_fcc135", "paper_2308_16317_gb300/csrc/tc_gemm.cu")
-    assert t is not None and 5e8 < t < 1e9
-    assert bench.traffic_from_profiles("tc_update_kernel_fcc135", "paper_2308_16317_gb300/csrc/mixed.cu") is None
+    t = bench.traffic_from_profiles("tc_update_kernel_fcc135", "paper_2308_16317_gb300/csrc/tc_gemm.cu", 7e8)
+    assert t is not None and 0.95 * 7e8 < t < 1.1 * 7e8
+    assert bench.traffic_from_profiles("tc_update_kernel_fcc135", "paper_2308_16317_gb300/csrc/mixed.cu", 7e8) is None
 
 
 def test_contour_weights_are_computed_on_the_host():

@@ -126,9 +126,10 @@ def test_streamed_update_matches_per_tile_kernel(B, orc, case):
                         wl.semicircle_contour(4), wl.spin_depths(2), wl.R_MT)
     else:
         w = wl.liz135(n_e=4)
-    old = (B.must_tune_get(2), B.must_tune_get(3))
+    old = (B.must_tune_get(2), B.must_tune_get(3), B.must_tune_get(11))
     taus = []
     try:
+        B.must_tune_set(11, 0)   # one panel step per pass: paired steps use the TMA-C kernel only
         for streamed, run in ((1, 8), (1, 1), (1, 64), (1, 3), (0, 8), (2, 8), (2, 1), (2, 64), (3, 3)):
             B.must_tune_set(2, streamed)
             B.must_tune_set(3, run)
@@ -138,6 +139,7 @@ def test_streamed_update_matches_per_tile_kernel(B, orc, case):
     finally:
         B.must_tune_set(2, old[0])
         B.must_tune_set(3, old[1])
+        B.must_tune_set(11, old[2])
     for t in taus[1:4] + taus[5:9]:
         assert np.array_equal(t, taus[0])
     k = w.kappa()
@@ -227,8 +229,9 @@ def test_a_pack_placements_match(B):
     pos, _ = wl.fcc_cluster(3)
     ws = [wl.Workload("ragged387", 2, [wl.Liz(pos, rng.integers(0, 2, pos.shape[0]).astype(np.int32))],
                       wl.semicircle_contour(5), wl.spin_depths(2), wl.R_MT), wl.liz135(n_e=4)]
-    old = (B.must_tune_get(4), B.must_tune_get(10))
+    old = (B.must_tune_get(4), B.must_tune_get(10), B.must_tune_get(11))
     try:
+        B.must_tune_set(11, 0)   # paired steps keep the pack on the main stream
         for w in ws:
             taus = []
             for la, where in ((1, 0), (1, 1), (1, 2), (0, 2), (0, 1)):
@@ -242,6 +245,7 @@ def test_a_pack_placements_match(B):
     finally:
         B.must_tune_set(4, old[0])
         B.must_tune_set(10, old[1])
+        B.must_tune_set(11, old[2])
 
 
 def test_concurrent_solves_on_two_streams_are_bit_identical(B):
