@@ -268,8 +268,8 @@ must_status must_site_density(int32_t lmax, int32_t nE, const double* E, const d
  *           left after two panels has at least this many rows, the two
  *           steps' trailing updates are applied in one K = 128 pass (half
  *           the C traffic; the second panel then runs with nothing to
- *           overlap it).  0 (default) pairs nothing.  BF16 splits with knob
- *           2 = 3 only;
+ *           overlap it).  0 pairs nothing; default 1536.  BF16 splits with
+ *           knob 2 = 3 only;
  *   knob 12: shape of the cluster correction from the third correction on
  *           (CTAs per cluster * 100 + right-hand sides per cluster: 204, 404,
  *           408, 416, 804, 808, 816, ...; 0: the shape of the first two).

@@ -81,9 +81,10 @@ extern int g_pack_side;
 // in one pass of the tensor-core update (K = 128 instead of two passes with
 // K = 64), at the price of factoring panel k+1 with nothing to overlap it;
 // 0 pairs no steps.  Needs the BF16 splits and the TMA-C streamed update
-// kernel (knob 2 = 3); the A pack placement (knob 10) is then 0.  Default 0:
-// on the 135-site LIZ pairing cuts the trailing update from 13.6 to 10.5 ms
-// per step, but the exposed panels cost as much (2186-2217 against 2199
-// solves/s for thresholds 1-1536 rows): the elimination is bound by the
-// chain of panels, not by the update's bandwidth.
+// kernel (knob 2 = 3); the A pack placement (knob 10) is then 0.  Default
+// 1536: on the 135-site LIZ (with the faster panel) thresholds 1024 / 1536 /
+// 1792 / 1900 give 2252 / 2262 / 2256 / 2257 against 2239 solves/s unpaired:
+// pairing cuts the trailing update from 13.6 to 10.9-12.7 ms per step, but
+// each pair's second panel runs with nothing to overlap it, so only the
+// earliest steps, where the update dominates, gain.
 extern int g_pair_rows;
