@@ -273,7 +273,10 @@ must_status must_site_density(int32_t lmax, int32_t nE, const double* E, const d
  *   knob 12: shape of the cluster correction from the third correction on
  *           (CTAs per cluster * 100 + right-hand sides per cluster: 204, 404,
  *           408, 416, 804, 808, 816, ...; 0: the shape of the first two).
- *           Default 408.
+ *           Default 408;
+ *   knob 13: kernel of the paired (K = 128) pass: 3 (default) C tiles
+ *           loaded by TMA, 2 C through registers with a deeper A ring; both
+ *           give identical results.
  * Process-wide; set them between calls, not while solves are being enqueued.
  */
 must_status must_tune_set(int32_t knob, int32_t value);

@@ -549,6 +549,9 @@ extern "C" must_status must_tune_set(int32_t knob, int32_t value) {
       g_corr_late = value;
       return MUST_OK;
     }
+    case 13:  // kernel of the paired pass
+      if (!tc_set_pair_kernel(value)) { must_set_error("paired-pass kernel must be 2 or 3"); return MUST_EINVAL; }
+      return MUST_OK;
     case 10:  // where the A operand is packed: main stream, side stream, inside the panel kernel
       if (value < 0 || value > 2) { must_set_error("A pack placement must be 0, 1 or 2"); return MUST_EINVAL; }
       g_pack_side = value;
@@ -573,6 +576,7 @@ extern "C" int32_t must_tune_get(int32_t knob) {
     case 10: return g_pack_side;
     case 11: return g_pair_rows;
     case 12: return g_corr_late;
+    case 13: return tc_get_pair_kernel();
   }
   return -1;
 }

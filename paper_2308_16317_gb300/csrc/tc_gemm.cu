@@ -466,19 +466,24 @@ __global__ void __launch_bounds__(S_THREADS, 1)
 // products are still summed from zero in TMEM (adding them onto C there would
 // round each partial sum at the scale of C).  Shared memory then carries only
 // the MMA operands, which leaves room for a deeper A ring (or two CTAs per SM).
-template <int STAGES>
+// KS = 4: two paired panel steps per pass (as in the TMA-C kernel below), with
+// the deeper A ring that the K = 128 pass needs to keep its A loads in flight.
+template <int STAGES, int KS = 2>
 struct RegcCfg {
   static constexpr int THREADS = 320;   // producer, MMA, 8 epilogue warps
-  static constexpr size_t SMEM = size_t(STAGES) * S_STAGE_BYTES + S_B_BYTES + 1024;
+  static constexpr int B_BYTES = 2 * KS * SB_BYTES;
+  static constexpr size_t SMEM = size_t(STAGES) * S_STAGE_BYTES + B_BYTES + 1024;
 };
+static_assert(RegcCfg<5, 4>::SMEM <= 227 * 1024, "regc shared memory");
 
-template <int STAGES>
-__global__ void __launch_bounds__(RegcCfg<STAGES>::THREADS, RegcCfg<STAGES>::SMEM * 2 <= 227 * 1024 ? 2 : 1)
+template <int STAGES, int KS = 2>
+__global__ void __launch_bounds__(RegcCfg<STAGES, KS>::THREADS, RegcCfg<STAGES, KS>::SMEM * 2 <= 227 * 1024 ? 2 : 1)
     tc_update_regc(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                     const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, TcsParams P) {
+  constexpr int R_B_BYTES = RegcCfg<STAGES, KS>::B_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* bres = smem + STAGES * S_STAGE_BYTES;   // [hi k0, hi k1, lo k0, lo k1]
+  uint8_t* bres = smem + STAGES * S_STAGE_BYTES;   // [hi k0 .. k(KS-1), lo k0 .. k(KS-1)]
   __shared__ __align__(8) uint64_t full[STAGES];
   __shared__ __align__(8) uint64_t empty[STAGES];
   __shared__ __align__(8) uint64_t bfull;        // resident B landed
@@ -520,23 +525,26 @@ __global__ void __launch_bounds__(RegcCfg<STAGES>::THREADS, RegcCfg<STAGES>::SME
   const int kstep_elems = KB / 2;
 
   if (warp == 0 && lane == 0) {
-    // producer: the resident B block once, then two A stages per tile
-    mbar_expect_tx(&bfull, S_B_BYTES);
-    for (int kb = 0; kb < S_KSTEPS; ++kb) {
-      tma_load_3d(bres + kb * SB_BYTES, &tB_hi, kb * kstep_elems, P.base + col0, item, &bfull);
-      tma_load_3d(bres + (S_KSTEPS + kb) * SB_BYTES, &tB_lo, kb * kstep_elems, P.base + col0, item, &bfull);
+    // producer: the resident B block once, then KS A stages per tile (K
+    // steps 2-3 of a paired pass from the second step's operand slots)
+    mbar_expect_tx(&bfull, R_B_BYTES);
+    for (int kb = 0; kb < KS; ++kb) {
+      const int brow = (kb < 2 ? P.boff : P.boff2) + P.base + col0, kc = (kb & 1) * kstep_elems;
+      tma_load_3d(bres + kb * SB_BYTES, &tB_hi, kc, brow, item, &bfull);
+      tma_load_3d(bres + (KS + kb) * SB_BYTES, &tB_lo, kc, brow, item, &bfull);
     }
     int gs = 0;
     for (int lt = 0; lt < ntile; ++lt) {
       const int row0 = (rt0 + lt) * BM;
       bool ok = true;
-      for (int kb = 0; kb < S_KSTEPS; ++kb, ++gs) {
+      for (int kb = 0; kb < KS; ++kb, ++gs) {
         const int s = gs % STAGES;
         if (gs >= STAGES && !mbar_wait_f(&empty[s], ((gs / STAGES) - 1) & 1, s_fail)) { ok = false; break; }
         uint8_t* sa = smem + s * S_STAGE_BYTES;
+        const int arow = (kb < 2 ? P.aoff : P.aoff2) + 2 * P.abase + row0, kc = (kb & 1) * kstep_elems;
         mbar_expect_tx(&full[s], S_STAGE_BYTES);
-        tma_load_3d(sa, &tA_hi, kb * kstep_elems, P.aoff + 2 * P.abase + row0, item, &full[s]);
-        tma_load_3d(sa + SA_BYTES, &tA_lo, kb * kstep_elems, P.aoff + 2 * P.abase + row0, item, &full[s]);
+        tma_load_3d(sa, &tA_hi, kc, arow, item, &full[s]);
+        tma_load_3d(sa + SA_BYTES, &tA_lo, kc, arow, item, &full[s]);
       }
       if (!ok) break;
     }
@@ -552,14 +560,14 @@ __global__ void __launch_bounds__(RegcCfg<STAGES>::THREADS, RegcCfg<STAGES>::SME
     // MMA issuer: per K step A_hi B_hi + A_hi B_lo + A_lo B_hi into accumulator lt & 1
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(SBN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
     bool ok = mbar_wait_f(&bfull, 0, s_fail);
-    const uint32_t bh = smem_u32(bres), bl = bh + S_KSTEPS * SB_BYTES;
+    const uint32_t bh = smem_u32(bres), bl = bh + KS * SB_BYTES;
     int gs = 0;
     for (int lt = 0; lt < ntile && ok; ++lt) {
       const int ab = lt & 1;
       if (lt >= 2 && !mbar_wait_f(&aempty[ab], ((lt >> 1) - 1) & 1, s_fail)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t acc = tmem + uint32_t(ab * SBN);
-      for (int kb = 0; kb < S_KSTEPS; ++kb, ++gs) {
+      for (int kb = 0; kb < KS; ++kb, ++gs) {
         const int s = gs % STAGES;
         if (!mbar_wait_f(&full[s], (gs / STAGES) & 1, s_fail)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -966,6 +974,7 @@ int g_tile_n = 128;   // 128 or 256 complex columns per tile (autotuned)
 int g_streamed = 3;   // BF16 splits, streamed runs: 3: C loaded by TMA, stored from registers; 2: C loaded
                       // and stored through registers; 1: C through shared memory both ways; 0: per-tile kernel
 int g_run = 32;       // row tiles per CTA of the streamed kernel
+int g_pair_kernel = 3;   // kernel of the paired (K = 128) pass: 3 TMA-C, 2 register-C with a 5-stage A ring
 
 template <int BN>
 void launch_tc(const CUtensorMap& mah, const CUtensorMap& mal, const CUtensorMap& mbh, const CUtensorMap& mbl,
@@ -992,17 +1001,17 @@ void launch_tc_streamed(const CUtensorMap& mah, const CUtensorMap& mal, const CU
   tc_update_streamed<<<grid, S_THREADS, S_SMEM, st>>>(mah, mal, mbh, mbl, mc, P);
 }
 
-template <int STAGES>
+template <int STAGES, int KS = 2>
 void launch_tc_regc(const CUtensorMap& mah, const CUtensorMap& mal, const CUtensorMap& mbh, const CUtensorMap& mbl,
                      const TcsParams& P, int items, cudaStream_t st) {
+  using Cfg = RegcCfg<STAGES, KS>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(tc_update_regc<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(RegcCfg<STAGES>::SMEM));
+    cudaFuncSetAttribute(tc_update_regc<STAGES, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::SMEM));
     attr = true;
   }
   const int grid = P.rruns * P.ct * items;
-  tc_update_regc<STAGES><<<grid, RegcCfg<STAGES>::THREADS, RegcCfg<STAGES>::SMEM, st>>>(mah, mal, mbh, mbl, P);
+  tc_update_regc<STAGES, KS><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(mah, mal, mbh, mbl, P);
 }
 
 template <int KS>
@@ -1049,6 +1058,13 @@ bool tc_set_run(int run) {
   return true;
 }
 int tc_get_run() { return g_run; }
+
+bool tc_set_pair_kernel(int k) {
+  if (k != 2 && k != 3) return false;
+  g_pair_kernel = k;
+  return true;
+}
+int tc_get_pair_kernel() { return g_pair_kernel; }
 
 size_t tc_pack_bytes_per_item(int n) {
   const int rows_pad = 2 * ((n + 127) / 128) * 128;
@@ -1262,6 +1278,8 @@ bool tc_update_steps(int precision, float2* A, size_t stride, int ld, int n, TcS
     ProfScope ps(PH_UPDATE, st);
     if (g_streamed == 2)
       launch_tc_regc<6>(mah, mal, mbh, mbl, S, items, st);
+    else if (s2 && g_pair_kernel == 2)
+      launch_tc_regc<5, 4>(mah, mal, mbh, mbl, S, items, st);
     else if (g_streamed == 3 && s2)
       launch_tc_tmac<4>(mah, mal, mbh, mbl, mc, S, items, st);
     else if (g_streamed == 3)

@@ -70,3 +70,8 @@ int tc_get_streamed();
 // Tiles per CTA of the streamed kernel (1..64).
 bool tc_set_run(int run);
 int tc_get_run();
+// Kernel of the paired (K = 128) pass: 3 (default) the TMA-C kernel (two C
+// buffers, three A stages), 2 the register-C kernel (five A stages; measured
+// slower on the 135-site LIZ: 2249 against 2273 solves/s).
+bool tc_set_pair_kernel(int k);
+int tc_get_pair_kernel();

@@ -174,7 +174,7 @@ def test_tuning_knobs_validate_and_round_trip():
     (no GPU needed)."""
     from paper_2308_16317_gb300 import binding as B
     cases = {6: ([0, 1], [2, -1]), 7: ([2, 4, 8], [3, 16]), 8: ([0, 4, 8, 16], [2, 32]), 5: ([0, 2, 4, 8], [3]),
-             9: ([0, 1], [2]), 10: ([0, 1, 2], [3, -1]), 11: ([0, 1, 1024], [-1]), 12: ([0, 204, 404, 816], [1, 304, 405])}
+             9: ([0, 1], [2]), 10: ([0, 1, 2], [3, -1]), 11: ([0, 1, 1024], [-1]), 12: ([0, 204, 404, 816], [1, 304, 405]), 13: ([2, 3], [0, 1, 4])}
     for knob, (good, bad) in cases.items():
         old = B.must_tune_get(knob)
         try:

@@ -338,3 +338,24 @@ def test_late_correction_shape(B, orc, late):
     ref, _ = oracle_tau(orc, w)
     assert rel_fro(tau.reshape(-1, 9, 9), ref).max() <= TOLMIX
     assert rel_fro(tau.reshape(-1, 9, 9), ref_dev.reshape(-1, 9, 9)).max() <= TOLMIX
+
+
+def test_paired_pass_kernels_identical(B):
+    """The paired (K = 128) pass on the TMA-C kernel (knob 13 = 3) and on the
+    register-C kernel with the deeper A ring (13 = 2) issue the same MMAs and
+    subtract the same way: tau_00 is identical bit for bit (135-site LIZ,
+    every possible step paired)."""
+    w = wl.liz135(n_e=4)
+    old = (B.must_tune_get(11), B.must_tune_get(13))
+    try:
+        B.must_tune_set(11, 1)
+        taus = []
+        for kern in (3, 2):
+            B.must_tune_set(13, kern)
+            tau, st = _gpu_tau(B, w, 1, residual=3)
+            assert (st == 0).all()
+            taus.append(tau)
+        assert np.array_equal(taus[0], taus[1])
+    finally:
+        B.must_tune_set(11, old[0])
+        B.must_tune_set(13, old[1])
