@@ -435,6 +435,23 @@ __device__ __forceinline__ float4 split_cd(cd v) {
 
 __device__ __forceinline__ bool need_df(const AsmArgs& A) { return A.M32 || (A.M64 && A.m64_df); }
 
+// Double-float arithmetic (value = hi + lo, |lo| <= ulp(hi) / 2) for the
+// Gaunt contraction of the mixed path, whose M is kept as a double-float copy
+// and whose residual resolves M to ~2^-48 of each row scale anyway: the FP32
+// pipes carry it at several times the rate of the FP64 pipe.
+// acc += c * w with c, w double-floats: the product by Dekker's method with
+// FMA (Dekker, Numer. Math. 18, 1971), the sum by Knuth's two-sum, then the
+// result renormalised.
+__device__ __forceinline__ void df_mac(float& ah, float& al, float ch, float cl, float wh, float wl) {
+  const float ph = ch * wh;
+  const float pl = fmaf(ch, wl, fmaf(cl, wh, fmaf(ch, wh, -ph)));
+  const float sh = ah + ph;
+  const float v = sh - ah;
+  const float e = ((ah - (sh - v)) + (ph - v)) + (al + pl);
+  ah = sh + e;
+  al = e - (ah - sh);
+}
+
 // Store entry (row, col) of item it: v in FP64 and, when a FP32 copy or the
 // double-float M is kept, its split f = split_cd(v).
 __device__ __forceinline__ void store_elem(const AsmArgs& A, int it, int row, int col, cd v, float4 f) {
@@ -471,6 +488,13 @@ __device__ __forceinline__ void store_elem(const AsmArgs& A, int it, int row, in
 // launch).
 constexpr int PAIRS_PER_BLOCK = 64;
 
+// Byte offset of the float-pair copy of the Gaunt coefficients in the pair
+// blocks' dynamic shared memory (after the FP64 coefficients, the L''
+// indices and the row starts), rounded up to 8 bytes.
+__host__ __device__ inline size_t gaunt_cf_offset(int g_nnz, int nL) {
+  return (size_t(g_nnz) * 12 + size_t(nL * nL + 1) * 4 + 7) & ~size_t(7);
+}
+
 __host__ __device__ inline int asm_pair_blocks(int n_pairs) { return (n_pairs + PAIRS_PER_BLOCK - 1) / PAIRS_PER_BLOCK; }
 
 __device__ __forceinline__ int absmax_bits(float4 f) { return __float_as_int(fmaxf(fabsf(f.x), fabsf(f.y))); }
@@ -492,14 +516,21 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
     const int u0 = blockIdx.x * PAIRS_PER_BLOCK;
     const int np = min(PAIRS_PER_BLOCK, Lz.n_pairs - u0);
     const int l2max = 2 * A.lmax;
-    // the Gaunt table in shared memory: [g_nnz] coefficients, [g_nnz] L'', [nL^2 + 1] row starts
+    // the Gaunt table in shared memory: [g_nnz] coefficients, [g_nnz] L'', [nL^2 + 1] row starts, and
+    // (double-float contraction) the coefficients as (hi, lo) float pairs
     extern __shared__ double gsm[];
     double* gs_c = gsm;
     int* gs_L2 = reinterpret_cast<int*>(gs_c + A.g_nnz);
     int* gs_start = gs_L2 + A.g_nnz;
+    float2* gs_cf = reinterpret_cast<float2*>(reinterpret_cast<char*>(gsm) + gaunt_cf_offset(A.g_nnz, nL));
+    const bool dfc = A.M32 && A.M64 && A.m64_df;   // mixed path with the double-float M
     for (int i = threadIdx.x; i < A.g_nnz; i += blockDim.x) {
       gs_c[i] = A.g_c[i];
       gs_L2[i] = A.g_L2[i];
+      if (dfc) {
+        const float h = float(A.g_c[i]);
+        gs_cf[i] = make_float2(h, float(A.g_c[i] - double(h)));
+      }
     }
     for (int i = threadIdx.x; i <= nL * nL; i += blockDim.x) gs_start[i] = A.g_start[i];
     if (int(threadIdx.x) < np) {
@@ -517,7 +548,11 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
       const int2 pq = Lz.pair_pq[unit];
       for (int L2 = lane; L2 < A.nL2; L2 += 32) {
         const double y = Lz.pair_Y[size_t(unit) * A.nL2 + L2];
-        wsh[warp][L2] = y * hsh[pi][l_of(L2)];
+        const cd w = y * hsh[pi][l_of(L2)];
+        if (dfc)   // (re hi, im hi, re lo, im lo) in the same 16 bytes
+          reinterpret_cast<float4*>(&wsh[warp][0])[L2] = split_cd(w);
+        else
+          wsh[warp][L2] = w;
       }
       if (lane < nL) rmx[warp][lane] = 0;
       __syncwarp();
@@ -526,16 +561,28 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs A) {
         const int L = ent % nL, Lp = ent / nL;
         cd v = mk(0.0, 0.0);
         const int b = gs_start[L * nL + Lp], t = gs_start[L * nL + Lp + 1];
-        for (int i = b; i < t; ++i) {
-          const double c = gs_c[i];
-          const cd w = wsh[warp][gs_L2[i]];
-          v.x = fma(c, w.x, v.x);
-          v.y = fma(c, w.y, v.y);
+        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (dfc) {
+          const float4* wf = reinterpret_cast<const float4*>(&wsh[warp][0]);
+          for (int i = b; i < t; ++i) {
+            const float2 c = gs_cf[i];
+            const float4 w = wf[gs_L2[i]];
+            df_mac(f.x, f.z, c.x, c.y, w.x, w.z);
+            df_mac(f.y, f.w, c.x, c.y, w.y, w.w);
+          }
+          // (v, the FP64 value, is stored only without the double-float copy)
+        } else {
+          for (int i = b; i < t; ++i) {
+            const double c = gs_c[i];
+            const cd w = wsh[warp][gs_L2[i]];
+            v.x = fma(c, w.x, v.x);
+            v.y = fma(c, w.y, v.y);
+          }
+          if (need_df(A)) f = split_cd(v);
         }
         // the transposed block by parity: G^{qp}_{LL'} = (-1)^{l+l'} G^{pq}_{LL'} (exact sign flips)
         const bool odd = (l_of(L) + l_of(Lp)) & 1;
         const cd vt = odd ? -v : v;
-        const float4 f = need_df(A) ? split_cd(v) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 ft = odd ? make_float4(-f.x, -f.y, -f.z, -f.w) : f;
         if (A.rowmax) atomicMax(&rmx[warp][L], absmax_bits(f));
         const cd z0 = mk(0.0, 0.0);
@@ -655,7 +702,7 @@ void launch_assemble(const AsmArgs& A, int max_units, cudaStream_t st) {
     prof_launched(PH_ASSEMBLE, 1);
   }
   dim3 grid((max_units + 7) / 8, A.nEc, A.n_lz);
-  const size_t smem = size_t(A.g_nnz) * 12 + size_t(A.nL * A.nL + 1) * 4;
+  const size_t smem = gaunt_cf_offset(A.g_nnz, A.nL) + size_t(A.g_nnz) * 8;
   // the Gaunt table of lmax = 4 (29 KB) plus the static buffers pass the
   // 48 KB that a launch gets without opting in
   static size_t smem_set = 0;
