@@ -215,6 +215,60 @@ def phase_work(phase: str, n: int, kap: int, nb: int, items: int, precision: str
     return None
 
 
+class InflightPlans:
+    """depth captured plans of the same solve, each with its own workspace,
+    input copies (E, t^-1) and outputs; step i runs plan i % depth on stream
+    i % depth, all streams forked from and joined back into the caller's."""
+
+    def __init__(self, B, s, opts, items, depth, dev):
+        import torch
+        self.B, self.depth = B, depth
+        nb = B.must_batch_workspace_bytes(s.lizs, items, opts)
+        self.plans, self.outs, self.inputs, self.ws = [], [], [], []
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(depth)]
+        for _ in range(depth):
+            E, T = s.E.clone(), s.tinv.clone()
+            w = torch.empty(nb, dtype=torch.uint8, device=dev)
+            o = s.alloc_out(1)
+            self.plans.append(B.must_plan_batch(s.lizs, E, T, s.n_species, s.nspin, opts, w, nb, o[0], o[1]))
+            self.outs.append(o)
+            self.inputs.append((E, T))
+            self.ws.append(w)
+        self.host_out = None
+
+    def _fork(self, stream):
+        for x in self.streams:
+            x.wait_stream(stream)
+
+    def _join(self, stream):
+        for x in self.streams:
+            stream.wait_stream(x)
+
+    def launch(self, steps, stream):
+        self._fork(stream)
+        for i in range(steps):
+            j = i % self.depth
+            self.B.must_plan_launch(self.plans[j], stream=self.streams[j])
+        self._join(stream)
+
+    def e2e(self, steps, E_h, T_h, stream):
+        import torch
+        if self.host_out is None:
+            self.host_out = [(torch.empty(o[0][0].shape, dtype=o[0].dtype).pin_memory(),
+                              torch.empty(o[1][0].shape, dtype=o[1].dtype).pin_memory()) for o in self.outs]
+        self._fork(stream)
+        for i in range(steps):
+            j = i % self.depth
+            with torch.cuda.stream(self.streams[j]):
+                E, T = self.inputs[j]
+                E.copy_(E_h, non_blocking=True)
+                T.copy_(T_h, non_blocking=True)
+                self.B.must_plan_launch(self.plans[j], stream=self.streams[j])
+                self.host_out[j][0].copy_(self.outs[j][0][0], non_blocking=True)
+                self.host_out[j][1].copy_(self.outs[j][1][0], non_blocking=True)
+        self._join(stream)
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -258,17 +312,18 @@ def run_ours(args):
     st0 = out[1].cpu().numpy()
     # the step as a captured plan (must_plan_batch / must_plan_launch): the
     # whole launch sequence of the call replayed as one CUDA graph, recomputing
-    # everything from E and t^-1 every time
-    plan_nb = B.must_batch_workspace_bytes(s.lizs, items, opts)
-    plan_ws = torch.empty(plan_nb, dtype=torch.uint8, device=dev)
-    plan_out = s.alloc_out(1)
+    # everything from E and t^-1 every time.  With --inflight D, D plans (own
+    # workspace, inputs and outputs each) take the steps in turn on D streams,
+    # so that D independent solves are in flight: one solve's latency-bound
+    # panel chain and refinement leave the GPU room for the next one's work.
     plan = None
+    pset = None
     if not args.no_plan:
-        plan = B.must_plan_batch(s.lizs, s.E, s.tinv, s.n_species, s.nspin, opts, plan_ws, plan_nb, plan_out[0],
-                                 plan_out[1])
-        for _ in range(args.warmup):
-            B.must_plan_launch(plan, stream=stream)
+        pset = InflightPlans(B, s, opts, items, max(1, args.inflight), dev)
+        plan = pset.plans[0]
+        pset.launch(args.warmup * pset.depth, stream)
         torch.cuda.synchronize(dev)
+    plan_out = pset.outs[0] if pset else None
 
     sampler = ClockSampler(local)
     if rank == 0:
@@ -288,10 +343,10 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
-            if use_plan:
-                B.must_plan_launch(plan, stream=stream)
-            else:
+        if use_plan:
+            pset.launch(args.steps, stream)
+        else:
+            for _ in range(args.steps):
                 s.solve(opts, out=out)
         e1.record(stream)
         torch.cuda.synchronize(dev)
@@ -309,10 +364,24 @@ def run_ours(args):
     tau_fast = blocks_to_numpy(hout[0][0])
     status = hout[1].cpu().numpy()
     direct = None
+    one_in_flight = None
     if plan is not None:
         ms_direct, _, _ = timed_region(False)
         direct = {"value": items * ws * args.steps / (ms_direct / 1e3), "ms_per_step": ms_direct / args.steps,
                   "identical_to_plan": bool(np.array_equal(blocks_to_numpy(out[0][0]), tau_fast))}
+        if pset.depth > 1:
+            # the same plan replays, one solve at a time on the caller's stream
+            barrier()
+            torch.cuda.synchronize(dev)
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(args.steps):
+                B.must_plan_launch(plan, stream=stream)
+            g1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms1 = max_over_ranks(g0.elapsed_time(g1))
+            one_in_flight = {"value": items * ws * args.steps / (ms1 / 1e3), "ms_per_step": ms1 / args.steps}
     ms_prof_total, _, prof = timed_region(True)
     status_prof = out[1].cpu().numpy()
 
@@ -413,30 +482,23 @@ def run_ours(args):
            "d2h_bytes_per_step": int(tau_h.numel() * 16 + sta_h.numel() * 4),
            "path": "must_tau00_solve with pinned host buffers (staged by the library)"}
     if plan is not None:
-        # the same through the plan: every step copies E and t^-1 from pinned host
-        # memory into the plan's input buffers, replays it and reads tau_00 and
-        # the status back
-        tau_d, sta_d = plan_out[0][0], plan_out[1][0]
-
-        def e2e_step():
-            s.E.copy_(E_h, non_blocking=True)
-            s.tinv.copy_(T_h, non_blocking=True)
-            B.must_plan_launch(plan, stream=stream)
-            tau_h.copy_(tau_d, non_blocking=True)
-            sta_h.copy_(sta_d, non_blocking=True)
-            torch.cuda.current_stream(dev).synchronize()
-        e2e_step()
+        # the same through the plans: every step copies E and t^-1 from pinned
+        # host memory into its plan's input buffers, replays the plan and reads
+        # tau_00 and the status back into pinned host memory; the region ends
+        # when every stream is done
+        pset.e2e(pset.depth, E_h, T_h, stream)
+        torch.cuda.synchronize(dev)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(e_steps):
-            e2e_step()
+        pset.e2e(e_steps, E_h, T_h, stream)
+        torch.cuda.synchronize(dev)
         e2e_p = max_over_ranks(time.perf_counter() - t0)
         e2e_direct = e2e
         e2e = {"value": items * ws * e_steps / e2e_p, "unit": UNIT,
                "h2d_bytes_per_step": int(E_h.numel() * 16 + T_h.numel() * 16),
                "d2h_bytes_per_step": int(tau_h.numel() * 16 + sta_h.numel() * 4),
-               "path": "plan replay (must_plan_launch) with the inputs copied from and tau_00 read back to "
-                       "pinned host memory every step", "direct_call": e2e_direct}
+               "path": "plan replays (must_plan_launch, %d solves in flight) with the inputs copied from and "
+                       "tau_00 read back to pinned host memory every step" % pset.depth, "direct_call": e2e_direct}
 
     cpu = None
     per_energy = None
@@ -467,9 +529,10 @@ def run_ours(args):
             "rel_err_vs_oracle_per_energy": per_energy,
             "status_ok": bool((status == 0).all() and (st0 == 0).all() and (status_prof == 0).all()),
             "phases": phases, "profiled_ms_per_step": ms_prof_total / args.steps,
-            "timed": "plan replay (the call captured once by must_plan_batch, replayed by must_plan_launch)"
+            "timed": ("plan replays (the call captured once by must_plan_batch, replayed by must_plan_launch), "
+                      "%d independent solves in flight on %d streams" % (pset.depth, pset.depth))
                      if plan is not None else "direct must_tau00_solve calls",
-            "direct_calls": direct,
+            "direct_calls": direct, "one_solve_in_flight": one_in_flight,
         }
         emit(line)
     if ws > 1:
@@ -982,6 +1045,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plan", action="store_true",
                     help="time direct must_tau00_solve calls instead of replays of the captured plan")
+    ap.add_argument("--inflight", type=int, default=3,
+                    help="independent solves in flight: captured plans taking the steps in turn on their own "
+                         "streams (1: one plan, one stream)")
     ap.add_argument("--cpu-sample", type=int, default=0)
     ap.add_argument("--workload", default="liz135",
                     choices=["liz135", "supercell", "warmstart", "cusolver", "canted", "paper", "charge", "peaks"],

@@ -171,6 +171,11 @@ size_t must_batch_workspace_bytes(int32_t n_liz, const must_liz* const* lizs, in
  * on `stream`, so repeated solves with new contents in the same E / tinv
  * buffers (an SCF loop, a benchmark) pay no per-kernel launch cost.  All
  * pointers must be device memory and stay valid while the plan exists.
+ * Plans with their own workspace, inputs and outputs are independent: two or
+ * more may run at the same time on different streams (independent solves in
+ * flight; the results equal those of one plan at a time bit for bit), which
+ * keeps the GPU busy while one solve waits on its chain of panels.  One plan
+ * must not be replayed on two streams at once (its buffers are shared).
  * Errors: MUST_EINVAL (host pointers, as for must_tau00_batch), MUST_ECUDA
  * (capture or instantiation failed).
  */

@@ -181,3 +181,39 @@ def test_autotuner_on_uneven_batch(B, tmp_path):
         for k, v in old.items():
             B.must_tune_set(k, v)
 
+
+
+def test_plans_in_flight_on_two_streams(B):
+    """Two plans of the same batch (own workspace, inputs and outputs each)
+    replayed at the same time on two streams, several times each, give the
+    result of a plain batch call (to the tolerance the single-plan replay test
+    uses: the norms of the refinement are summed with atomics): nothing is
+    shared between plans in flight."""
+    import torch
+    from paper_2308_16317_gb300.runner import Session
+    w = _uneven_workload()
+    s = Session(w)
+    opts = B.must_default_opts(1, residual=3)
+    ref, st = s.solve_batch(opts)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    ref = ref.cpu().numpy()
+    items = len(w.energies) * s.nspin
+    nb = B.must_batch_workspace_bytes(s.lizs, items, opts)
+    plans, outs, keep = [], [], []
+    for _ in range(2):
+        E, T = s.E.clone(), s.tinv.clone()
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        tau, sta = s.alloc_out(len(s.lizs))
+        plans.append(B.must_plan_batch(s.lizs, E, T, s.n_species, s.nspin, opts, ws, nb, tau, sta))
+        outs.append((tau, sta))
+        keep.append((E, T, ws))
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    for _ in range(3):
+        for p, x in zip(plans, streams):
+            B.must_plan_launch(p, stream=x)
+    torch.cuda.synchronize()
+    for tau, sta in outs:
+        assert (sta.cpu().numpy() == 0).all()
+        assert np.abs(tau.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
