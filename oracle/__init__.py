@@ -67,6 +67,9 @@ def _load():
                 "orc_first_block": (c_dbl, [c_int, D, c_int, D, I]),
                 "orc_inverse": (c_int, [c_int, D, D]),
                 "orc_tau00_batch": (c_int, [c_int, D, c_int, c_int, D, D, D, D, c_int, D, D, I]),
+                "orc_kkr_lattice_sum": (None, [c_int, c_dbl, c_dbl, D, D, D, c_dbl, c_dbl, D]),
+                "orc_kkr_struct_const": (None, [c_int, c_dbl, c_dbl, D, c_int, D, D, c_dbl, c_dbl, D]),
+                "orc_kkr_tau": (c_int, [c_int, D, c_int, D, c_int, D, D, c_int, c_dbl, c_dbl, c_int, D]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -235,3 +238,58 @@ def tau00_batch(pos, lmax: int, E, tinv_a, tinv_b=None, dirs=None, nthreads: int
     if st.any():
         raise ZeroDivisionError("oracle met a zero pivot")
     return tau, err, used
+
+
+# -- full KKR (periodic crystal; Sec. 5) -----------------------------------
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def kkr_lattice_sum(l2max: int, E: complex, lattice, x, k, eta: float, cut: float = 50.0) -> np.ndarray:
+    """Ewald lattice sum D_L(k) = sum_{R: x-R != 0} e^{ik.R} h_l(kappa|x-R|) Y_L((x-R)^), L < (l2max+1)^2.
+
+    lattice: rows a1, a2, a3 (bohr); x = b_s - b_t; cut: truncation exponent of both sums.
+    """
+    D = np.zeros((l2max + 1) ** 2, np.complex128)
+    lat, xx, kk = _f64(lattice, (3, 3)), _f64(x, (3,)), _f64(k, (3,))
+    _load().orc_kkr_lattice_sum(l2max, float(np.real(E)), float(np.imag(E)), _dp(lat), _dp(xx), _dp(kk),
+                                float(eta), float(cut), _dp(D.view(np.float64)))
+    return D
+
+
+def kkr_struct_const(lmax: int, E: complex, lattice, basis, k, eta: float, cut: float = 50.0) -> np.ndarray:
+    """Bloch-summed structure constants G(k), n x n with n = N_b (lmax+1)^2, index (site, L)."""
+    basis = _f64(basis).reshape(-1, 3)
+    nb = basis.shape[0]
+    n = nb * nL(lmax)
+    G = np.zeros((n, n), np.complex128)
+    lat, kk = _f64(lattice, (3, 3)), _f64(k, (3,))
+    _load().orc_kkr_struct_const(lmax, float(np.real(E)), float(np.imag(E)), _dp(lat), nb, _dp(basis), _dp(kk),
+                                 float(eta), float(cut), _dp(G.view(np.float64)))
+    return G
+
+
+def kkr_tau(lmax: int, lattice, basis, E, tinv, nk: int, eta: float, cut: float = 50.0, nthreads: int = 0):
+    """Site-diagonal scattering-path blocks of the crystal, tau^{ss}(E) = <[t^{-1} - G(k)]^{-1}>_BZ.
+
+    E: [n_items] complex; tinv: [n_items][N_b][lmax+1]; Gamma-centred uniform mesh of nk^3 points.
+    Returns (tau [n_items][N_b][kap][kap], threads_used).
+    """
+    basis = _f64(basis).reshape(-1, 3)
+    nb = basis.shape[0]
+    E = _c128(E).reshape(-1)
+    n_items = E.shape[0]
+    ti = _c128(tinv).reshape(n_items, nb, lmax + 1)
+    kap = nL(lmax)
+    tau = np.zeros((n_items, nb, kap, kap), np.complex128)
+    lat = _f64(lattice, (3, 3))
+    used = _load().orc_kkr_tau(lmax, _dp(lat), nb, _dp(basis), n_items, _dp(E.view(np.float64)),
+                               _dp(ti.view(np.float64)), int(nk), float(eta), float(cut), int(nthreads),
+                               _dp(tau.view(np.float64)))
+    if used < 0:
+        raise ZeroDivisionError("oracle met a singular M(k)")
+    return tau, used

@@ -494,6 +494,274 @@ static int gauss_jordan(size_t n, const cplx* A, cplx* Ainv) {
 }
 
 // ==========================================================================
+// Full KKR (Sec. 5: the same matrix inverse for a periodic crystal instead of
+// a LIZ).  With N_b sites b_s per cell of the lattice {R} and the real-space
+// blocks G(rho) above, the Bloch-summed structure constants are
+//   G^{st}_{LL'}(k) = sum_{R : rho != 0} e^{i k.R} G_{LL'}(rho),  rho = b_s - b_t - R,
+// the KKR matrix of Eq. (4) becomes M(k) = t^{-1} - G(k) (order N_b (lmax+1)^2,
+// Sec. 2.1), and the site-diagonal scattering-path block is the Brillouin-zone
+// average  tau^{ss} = (1/N_k) sum_k [M(k)^{-1}]^{ss}  on a uniform k mesh.
+//
+// The lattice sum converges only for Im kappa > 0 and slowly near the real
+// axis, so it is split (Ewald).  With D^{st}_L(k) = sum_R e^{ik.R}
+// h_l(kappa|rho|) Y_L(rho^), and since h_l(kappa r) Y_L(r^) = (-kappa)^{-l}
+// Y_L(grad) h_0(kappa r) (Hobson's theorem with the Rayleigh formula for h_l),
+// h_0(kappa r) = -i e^{i kappa r}/(kappa r), and
+//   e^{i kappa r}/r = (2/sqrt(pi)) int_0^inf exp(-r^2 xi^2 + E/(4 xi^2)) d xi,
+// cut at xi0 = sqrt(eta)/2: the part below xi0 is summed in reciprocal space
+// (Poisson; its Fourier transform is 4 pi e^{(E - q^2)/eta}/(q^2 - E)), the part
+// above xi0 in real space, and the R = 0 term of the reciprocal sum is removed
+// when s = t:
+//   D_L = (-kappa)^{-l} (-i/kappa) [A_L + B_L + C_L]
+//   A_L = (4 pi/Omega) i^l sum_K e^{i q.x} |q|^l Y_L(q^) e^{(E-q^2)/eta}/(q^2-E),
+//         q = k + K, x = b_s - b_t
+//   B_L = (2/sqrt(pi)) (-2)^l sum_{R: rho != 0} e^{ik.R} |rho|^l Y_L(rho^)
+//         int_{xi0}^inf xi^{2l} exp(-rho^2 xi^2 + E/(4 xi^2)) d xi
+//   C_0 = -(1/sqrt(4 pi)) [i kappa - sqrt(eta/pi) sum_{n>=0} (E/eta)^n/(n! (2n-1))]
+//         for s = t (C_L = 0 otherwise)
+// and G^{st}_{LL'}(k) = -4 pi i kappa sum_L'' i^{l-l'+l''} C(L,L',L'') D^{st}_L''.
+// Both sums are truncated where their Gaussian factor falls below e^{-cut}.
+// ==========================================================================
+
+struct Lattice {
+  double a[3][3];  // primitive vectors (rows), bohr
+  double b[3][3];  // reciprocal vectors, a_i . b_j = 2 pi delta_ij
+  double omega;    // cell volume
+};
+
+static Lattice make_lattice(const double* A) {
+  Lattice L;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) L.a[i][j] = A[3 * i + j];
+  auto cross = [](const double* u, const double* v, double* w) {
+    w[0] = u[1] * v[2] - u[2] * v[1];
+    w[1] = u[2] * v[0] - u[0] * v[2];
+    w[2] = u[0] * v[1] - u[1] * v[0];
+  };
+  double c[3][3];
+  cross(L.a[1], L.a[2], c[0]);
+  cross(L.a[2], L.a[0], c[1]);
+  cross(L.a[0], L.a[1], c[2]);
+  const double vol = L.a[0][0] * c[0][0] + L.a[0][1] * c[0][1] + L.a[0][2] * c[0][2];
+  L.omega = std::fabs(vol);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) L.b[i][j] = 2.0 * kPi * c[i][j] / vol;
+  return L;
+}
+
+static double norm3(const double* v) { return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+
+// All integer combinations n1 v1 + n2 v2 + n3 v3 (v = rows of V) within
+// distance rmax of the point -c, i.e. |c + n.V| <= rmax.  dual = the rows of
+// the dual basis divided by 2 pi, used to bound each |n_i|.
+static void lattice_points(const double V[3][3], const double W[3][3], const double* c, double rmax,
+                           std::vector<double>& out) {
+  int nmax[3];
+  const double cn = norm3(c);
+  for (int i = 0; i < 3; ++i) nmax[i] = int(std::ceil((rmax + cn) * norm3(W[i]) / (2.0 * kPi))) + 1;
+  out.clear();
+  for (int n1 = -nmax[0]; n1 <= nmax[0]; ++n1)
+    for (int n2 = -nmax[1]; n2 <= nmax[1]; ++n2)
+      for (int n3 = -nmax[2]; n3 <= nmax[2]; ++n3) {
+        double v[3];
+        for (int d = 0; d < 3; ++d) v[d] = n1 * V[0][d] + n2 * V[1][d] + n3 * V[2][d];
+        const double w[3] = {c[0] + v[0], c[1] + v[1], c[2] + v[2]};
+        if (norm3(w) <= rmax) out.insert(out.end(), v, v + 3);
+      }
+}
+
+// int_{xi0}^{inf} xi^{2l} exp(-rho^2 xi^2 + E/(4 xi^2)) d xi for l = 0..lmax,
+// by composite 16-point Gauss-Legendre over [xi0, xi_hi], where
+// rho^2 (xi_hi^2 - xi0^2) = 90 (the rest is below e^{-90} of the first node).
+static void ewald_real_integrals(int lmax, double rho, double xi0, cplx E, cplx* I) {
+  static thread_local std::vector<double> gx, gw;
+  if (gx.empty()) { gx.resize(16); gw.resize(16); gauss_legendre(16, gx.data(), gw.data()); }
+  const double xhi = std::sqrt(xi0 * xi0 + 90.0 / (rho * rho));
+  const int panels = 48;
+  const double h = (xhi - xi0) / panels;
+  for (int l = 0; l <= lmax; ++l) I[l] = 0.0;
+  for (int p = 0; p < panels; ++p) {
+    const double lo = xi0 + p * h;
+    for (int q = 0; q < 16; ++q) {
+      const double xi = lo + 0.5 * h * (gx[q] + 1.0);
+      const cplx f = std::exp(-rho * rho * xi * xi + E / (4.0 * xi * xi)) * (0.5 * h * gw[q]);
+      double pw = 1.0;
+      for (int l = 0; l <= lmax; ++l) { I[l] += pw * f; pw *= xi * xi; }
+    }
+  }
+}
+
+// Real-space terms of the Ewald sum for one displacement x = b_s - b_t:
+// every lattice vector R with 0 < |x - R| <= sqrt(4 cut / eta), and for each
+// the k-independent factor (2/sqrt(pi)) (-2)^l |rho|^l Y_L(rho^) I_l(|rho|).
+struct EwaldRealTerms {
+  std::vector<double> R;  // 3 per point
+  std::vector<cplx> T;    // (l2max+1)^2 per point
+};
+
+static void ewald_real_terms(int l2max, cplx E, const Lattice& Lt, const double* x, double eta, double cut,
+                             EwaldRealTerms& out) {
+  const int nL2 = (l2max + 1) * (l2max + 1);
+  const double xi0 = 0.5 * std::sqrt(eta);
+  const double rmax = std::sqrt(4.0 * cut / eta);
+  const double mx[3] = {-x[0], -x[1], -x[2]};
+  std::vector<double> pts;
+  lattice_points(Lt.a, Lt.b, mx, rmax, pts);
+  std::vector<cplx> I(l2max + 1);
+  std::vector<double> Y(nL2);
+  out.R.clear();
+  out.T.clear();
+  for (size_t p = 0; p < pts.size(); p += 3) {
+    const double rho[3] = {x[0] - pts[p], x[1] - pts[p + 1], x[2] - pts[p + 2]};
+    const double rn = norm3(rho);
+    if (rn < 1e-10) continue;  // the site itself
+    ewald_real_integrals(l2max, rn, xi0, E, I.data());
+    real_ylm(l2max, rho[0], rho[1], rho[2], Y.data());
+    out.R.insert(out.R.end(), pts.begin() + p, pts.begin() + p + 3);
+    for (int l = 0; l <= l2max; ++l) {
+      const cplx f = (2.0 / std::sqrt(kPi)) * std::pow(-2.0, l) * std::pow(rn, l) * I[l];
+      for (int m = -l; m <= l; ++m) out.T.push_back(f * Y[l * l + l + m]);
+    }
+  }
+}
+
+// Lattice sums D_L(k), L < (l2max+1)^2, for the displacement x = b_s - b_t
+// whose real-space terms are `real` (self term included when x = 0).
+// cut: truncation exponent of the reciprocal sum.
+static void kkr_lattice_sum(int l2max, cplx E, const Lattice& Lt, const double* x, const double* k, double eta,
+                            double cut, const EwaldRealTerms& real, cplx* D) {
+  const int nL2 = (l2max + 1) * (l2max + 1);
+  const cplx kap = kappa_of(E);
+  std::vector<cplx> acc(nL2, cplx(0.0));
+  std::vector<double> Y(nL2);
+  // reciprocal space: all K with |k + K|^2 <= eta * cut + max(Re E, 0)
+  std::vector<double> pts;
+  const double qmax = std::sqrt(eta * cut + std::max(E.real(), 0.0));
+  lattice_points(Lt.b, Lt.a, k, qmax, pts);
+  for (size_t p = 0; p < pts.size(); p += 3) {
+    const double q[3] = {k[0] + pts[p], k[1] + pts[p + 1], k[2] + pts[p + 2]};
+    const double q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    const double qn = std::sqrt(q2);
+    const cplx w = (4.0 * kPi / Lt.omega) * std::exp((E - q2) / eta) / (q2 - E) *
+                   std::exp(cplx(0.0, q[0] * x[0] + q[1] * x[1] + q[2] * x[2]));
+    if (qn > 0.0) {
+      real_ylm(l2max, q[0], q[1], q[2], Y.data());
+    } else {
+      std::fill(Y.begin(), Y.end(), 0.0);
+      Y[0] = 1.0 / std::sqrt(4.0 * kPi);
+    }
+    for (int l = 0; l <= l2max; ++l) {
+      const cplx f = ipow(l) * std::pow(qn, l) * w;
+      for (int m = -l; m <= l; ++m) acc[l * l + l + m] += f * Y[l * l + l + m];
+    }
+  }
+  // real space
+  const size_t npt = real.R.size() / 3;
+  for (size_t p = 0; p < npt; ++p) {
+    const double* R = &real.R[3 * p];
+    const cplx ph = std::exp(cplx(0.0, k[0] * R[0] + k[1] * R[1] + k[2] * R[2]));
+    for (int L = 0; L < nL2; ++L) acc[L] += ph * real.T[p * nL2 + L];
+  }
+  // the removed R = 0 term of the reciprocal sum
+  if (norm3(x) < 1e-10) {
+    cplx s = 0.0, term = 1.0;  // term = (E/eta)^n / n!
+    for (int n = 0; n < 200; ++n) {
+      const cplx add = term / double(2 * n - 1);
+      s += add;
+      if (n > 4 && std::abs(add) < 1e-18 * std::abs(s)) break;
+      term *= (E / eta) / double(n + 1);
+    }
+    acc[0] -= (cplx(0.0, 1.0) * kap - std::sqrt(eta / kPi) * s) / std::sqrt(4.0 * kPi);
+  }
+  for (int l = 0; l <= l2max; ++l) {
+    const cplx f = std::pow(-kap, -l) * (cplx(0.0, -1.0) / kap);
+    for (int m = -l; m <= l; ++m) D[l * l + l + m] = f * acc[l * l + l + m];
+  }
+}
+
+// The real-space terms of every site pair (s, t), index s * nb + t.
+static std::vector<EwaldRealTerms> kkr_real_tables(int lmax, cplx E, const Lattice& Lt, int nb, const double* basis,
+                                                   double eta, double cut) {
+  std::vector<EwaldRealTerms> real(size_t(nb) * nb);
+  for (int s = 0; s < nb; ++s)
+    for (int t = 0; t < nb; ++t) {
+      const double x[3] = {basis[3 * s] - basis[3 * t], basis[3 * s + 1] - basis[3 * t + 1],
+                           basis[3 * s + 2] - basis[3 * t + 2]};
+      ewald_real_terms(2 * lmax, E, Lt, x, eta, cut, real[size_t(s) * nb + t]);
+    }
+  return real;
+}
+
+// G^{st}(k) of every site pair, row-major n x n with n = N_b (lmax+1)^2,
+// index (site, L).  gaunt: dense table for (lmax, lmax, 2 lmax).
+static void kkr_struct_const_k(int lmax, cplx E, const Lattice& Lt, int nb, const double* basis, const double* k,
+                               double eta, double cut, const std::vector<EwaldRealTerms>& real, const double* gaunt,
+                               cplx* G) {
+  const int nL = (lmax + 1) * (lmax + 1);
+  const int l2max = 2 * lmax, nL2 = (l2max + 1) * (l2max + 1);
+  const int n = nb * nL;
+  const cplx kap = kappa_of(E);
+  std::vector<cplx> D(nL2);
+  for (int s = 0; s < nb; ++s)
+    for (int t = 0; t < nb; ++t) {
+      const double x[3] = {basis[3 * s] - basis[3 * t], basis[3 * s + 1] - basis[3 * t + 1],
+                           basis[3 * s + 2] - basis[3 * t + 2]};
+      kkr_lattice_sum(l2max, E, Lt, x, k, eta, cut, real[size_t(s) * nb + t], D.data());
+      for (int L = 0; L < nL; ++L) {
+        const int l = int(std::sqrt(double(L)) + 1e-9);
+        for (int Lp = 0; Lp < nL; ++Lp) {
+          const int lp = int(std::sqrt(double(Lp)) + 1e-9);
+          cplx acc = 0.0;
+          for (int L2 = 0; L2 < nL2; ++L2) {
+            const double c = gaunt[(size_t(L) * nL + Lp) * nL2 + L2];
+            if (c == 0.0) continue;
+            const int l2 = int(std::sqrt(double(L2)) + 1e-9);
+            acc += ipow(l - lp + l2) * c * D[L2];
+          }
+          G[size_t(s * nL + L) * n + t * nL + Lp] = -4.0 * kPi * cplx(0.0, 1.0) * kap * acc;
+        }
+      }
+    }
+}
+
+// tau^{ss}(E) = (1/N_k) sum_k [M(k)^{-1}]^{ss}, M(k) = t^{-1} - G(k), on the
+// Gamma-centred mesh k = sum_i (m_i / n_k) b_i, m_i = 0..n_k-1.
+// tinv: [N_b][lmax+1]; tau: [N_b][kap][kap] row-major.  Returns 0, or 1 on a
+// singular M(k).
+static int kkr_tau(int lmax, cplx E, const Lattice& Lt, int nb, const double* basis, const cplx* tinv, int nk,
+                   double eta, double cut, cplx* tau) {
+  const int nL = (lmax + 1) * (lmax + 1);
+  const int n = nb * nL;
+  std::vector<double> C(size_t(nL) * nL * (2 * lmax + 1) * (2 * lmax + 1));
+  gaunt_table(lmax, lmax, 2 * lmax, C.data());
+  std::vector<cplx> G(size_t(n) * n), M(size_t(n) * n), Minv(size_t(n) * n);
+  std::vector<cplx> sum(size_t(nb) * nL * nL, cplx(0.0));
+  const std::vector<EwaldRealTerms> real = kkr_real_tables(lmax, E, Lt, nb, basis, eta, cut);
+  for (int m1 = 0; m1 < nk; ++m1)
+    for (int m2 = 0; m2 < nk; ++m2)
+      for (int m3 = 0; m3 < nk; ++m3) {
+        double k[3];
+        for (int d = 0; d < 3; ++d) k[d] = (m1 * Lt.b[0][d] + m2 * Lt.b[1][d] + m3 * Lt.b[2][d]) / nk;
+        kkr_struct_const_k(lmax, E, Lt, nb, basis, k, eta, cut, real, C.data(), G.data());
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j < n; ++j) M[size_t(i) * n + j] = -G[size_t(i) * n + j];
+        for (int s = 0; s < nb; ++s)
+          for (int L = 0; L < nL; ++L) {
+            const int l = int(std::sqrt(double(L)) + 1e-9);
+            M[size_t(s * nL + L) * n + s * nL + L] += tinv[s * (lmax + 1) + l];
+          }
+        if (gauss_jordan(n, M.data(), Minv.data())) return 1;
+        for (int s = 0; s < nb; ++s)
+          for (int L = 0; L < nL; ++L)
+            for (int Lp = 0; Lp < nL; ++Lp)
+              sum[(size_t(s) * nL + L) * nL + Lp] += Minv[size_t(s * nL + L) * n + s * nL + Lp];
+      }
+  const double w = 1.0 / (double(nk) * nk * nk);
+  for (size_t q = 0; q < sum.size(); ++q) tau[q] = sum[q] * w;
+  return 0;
+}
+
+// ==========================================================================
 // C entry points (ctypes).  Complex arrays are interleaved (re, im) doubles.
 // ==========================================================================
 extern "C" {
@@ -592,6 +860,50 @@ int orc_tau00_batch(int N, const double* pos, int lmax, int n_items, const doubl
                                 status + it);
   }
   return used;
+}
+
+// Lattice sums D_L(k), L < (l2max+1)^2 (Ewald; see the full-KKR section).
+void orc_kkr_lattice_sum(int l2max, double er, double ei, const double* lattice, const double* x, const double* k,
+                         double eta, double cut, double* D) {
+  const Lattice Lt = make_lattice(lattice);
+  EwaldRealTerms real;
+  ewald_real_terms(l2max, cplx(er, ei), Lt, x, eta, cut, real);
+  kkr_lattice_sum(l2max, cplx(er, ei), Lt, x, k, eta, cut, real, reinterpret_cast<cplx*>(D));
+}
+
+// G(k), row-major n x n, n = nb (lmax+1)^2.
+void orc_kkr_struct_const(int lmax, double er, double ei, const double* lattice, int nb, const double* basis,
+                          const double* k, double eta, double cut, double* G) {
+  const int nL = (lmax + 1) * (lmax + 1);
+  std::vector<double> C(size_t(nL) * nL * (2 * lmax + 1) * (2 * lmax + 1));
+  gaunt_table(lmax, lmax, 2 * lmax, C.data());
+  const Lattice Lt = make_lattice(lattice);
+  const std::vector<EwaldRealTerms> real = kkr_real_tables(lmax, cplx(er, ei), Lt, nb, basis, eta, cut);
+  kkr_struct_const_k(lmax, cplx(er, ei), Lt, nb, basis, k, eta, cut, real, C.data(), reinterpret_cast<cplx*>(G));
+}
+
+// Site-diagonal tau blocks of the crystal for many independent items (OpenMP
+// across items).  E [n_items], tinv [n_items][nb][lmax+1], tau
+// [n_items][nb][kap][kap] row-major.  Returns the threads used, or -1 if some
+// M(k) was singular.
+int orc_kkr_tau(int lmax, const double* lattice, int nb, const double* basis, int n_items, const double* E,
+                const double* tinv, int nk, double eta, double cut, int nthreads, double* tau) {
+  const Lattice Lt = make_lattice(lattice);
+  const int nL = (lmax + 1) * (lmax + 1);
+  int used = 1, bad = 0;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(| : bad)
+#endif
+  for (int it = 0; it < n_items; ++it) {
+#ifdef _OPENMP
+    if (omp_get_thread_num() == 0) used = omp_get_num_threads();
+#endif
+    const cplx e(E[2 * it], E[2 * it + 1]);
+    bad |= kkr_tau(lmax, e, Lt, nb, basis, reinterpret_cast<const cplx*>(tinv) + size_t(it) * nb * (lmax + 1), nk,
+                   eta, cut, reinterpret_cast<cplx*>(tau) + size_t(it) * nb * nL * nL);
+  }
+  return bad ? -1 : used;
 }
 
 }  // extern "C"

@@ -235,3 +235,53 @@ def niau249_canted(seed: int = SEED_BASE + 8, n_e: int = 8) -> Workload:
     dirs = random_unit_vectors(rng, pos.shape[0])
     return Workload("niau249_lmax4_canted", 4, [Liz(pos, species, dirs)], semicircle_contour(n_e),
                     _depths(2, 2), R_MT, canted=True)
+
+
+# ---------------------------------------------------------------------------
+# Periodic crystals for the full-KKR path (the paper's Sec. 5 target): the
+# same square wells on a lattice with a basis instead of a finite LIZ.
+
+@dataclasses.dataclass
+class Crystal:
+    """One periodic crystal: primitive vectors (rows), basis sites, species."""
+    name: str
+    lattice: np.ndarray              # [3,3] rows a1, a2, a3 (bohr)
+    basis: np.ndarray                # [N_b,3] (bohr)
+    species: np.ndarray              # [N_b] int32
+    lmax: int
+    n_k: int                         # mesh points per reciprocal axis
+    energies: np.ndarray             # [nE] complex128
+    v_species: np.ndarray            # [nspin][n_species]
+    r_mt: float
+
+    @property
+    def nspin(self) -> int:
+        return int(self.v_species.shape[0])
+
+    @property
+    def n_basis(self) -> int:
+        return int(self.basis.shape[0])
+
+    def site_depths(self, spin: int) -> np.ndarray:
+        return self.v_species[spin][self.species]
+
+
+FCC_PRIMITIVE = 0.5 * A_LAT * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+FCC_CUBIC_BASIS = A_LAT * np.array([[0.0, 0.0, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]])
+
+
+def fcc_crystal(species: int = 0, lmax: int = 3, n_e: int = 32, n_k: int = 16) -> Crystal:
+    """Pure fcc element on the primitive cell (one site), lmax = 3 (M(k) of
+    order 16), 32 contour energies (Im E >= 0.005), two spins."""
+    return Crystal("fcc1_lmax%d_nk%d" % (lmax, n_k), FCC_PRIMITIVE.copy(), np.zeros((1, 3)),
+                   np.array([species], np.int32), lmax, n_k, semicircle_contour(n_e, im_min=0.005),
+                   spin_depths(2), R_MT)
+
+
+def l12_crystal(lmax: int = 3, n_e: int = 32, n_k: int = 8) -> Crystal:
+    """Ordered Ni3Au-like L1_2 alloy on the 4-site simple-cubic cell of the fcc
+    lattice (species B at the cube corner, A on the face centres), lmax = 3
+    (M(k) of order 64), 32 contour energies (Im E >= 0.005), two spins."""
+    return Crystal("l12_cell4_lmax%d_nk%d" % (lmax, n_k), A_LAT * np.eye(3), FCC_CUBIC_BASIS.copy(),
+                   np.array([1, 0, 0, 0], np.int32), lmax, n_k, semicircle_contour(n_e, im_min=0.005),
+                   spin_depths(2), R_MT)
