@@ -982,6 +982,144 @@ def run_peaks(args):
           "ffma_f32": res["ffma_f32"]["tflops"], "detail": res, "clocks": clocks})
 
 
+FP64_DFMA_MEASURED = 1.058   # TFLOP/s, the library's DFMA probe on this GPU (profiles/fp64_peak.md)
+
+
+def kkr_work(h, c, items):
+    """Algorithmic FP64 flops of one must_kkr_tau call, per kernel: complex
+    multiply-adds (8 real flops) of the reciprocal sums (every (k, K) term for
+    every displacement and L''), of the real-space sums (every (k, point) term
+    for every L''), and n^3 of the in-place Gauss-Jordan inversion of each M(k)."""
+    nL2 = (2 * c.lmax + 1) ** 2
+    return {"kkr_recip": 8.0 * items * h.n_kK * h.n_disp * nL2,
+            "kkr_realsum": 8.0 * items * h.n_kpts * h.n_pts * nL2,
+            "kkr_invert": 8.0 * items * h.n_kpts * h.n ** 3}
+
+
+def run_kkr(args):
+    """Full KKR of a periodic crystal (the paper's Sec. 5 target): the
+    site-diagonal tau of every site for 32 contour energies x 2 spins per step,
+    by must_kkr_tau (Ewald structure constants, M(k) = t^-1 - G(k) inverted
+    per k point, Brillouin-zone average), on the 4-site L1_2 cell (M(k) of
+    order 64, 8^3 k points) and the primitive fcc cell (order 16, 16^3 k
+    points).  Reports tau solves/s (one (energy, spin) item = all sites of the
+    cell), M(k) inversions/s, the per-kernel split with the FP64 roofline of
+    the dominant kernel, an end-to-end figure from pinned host buffers, and the
+    oracle on the host cores on a bounded sample (errors of the sampled items
+    against it)."""
+    import torch
+    import oracle
+    from paper_2308_16317_gb300 import binding as B
+    from paper_2308_16317_gb300 import build as libbuild
+    from paper_2308_16317_gb300 import workload as wl
+    libbuild.build()
+    B.load()
+    oracle.build()
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    cores = min(16, os.cpu_count() or 1)
+    crystals = [wl.l12_crystal(n_k=8, n_e=args.n_energies), wl.fcc_crystal(n_k=16, n_e=args.n_energies)]
+    results = {}
+    for c in crystals:
+        h = B.must_kkr_build(c.lattice, c.basis, c.lmax, c.n_k)
+        nE = len(c.energies)
+        picks = [(sp, e) for sp in range(c.nspin) for e in range(nE)]
+        items = len(picks)
+        # t^-1 of every (spin, species) well from the library's fixture kernel, gathered per (item, site)
+        Vs = np.array([c.v_species[sp][k] for sp in range(c.nspin) for k in range(c.v_species.shape[1])])
+        Ed_all = torch.tensor(c.energies, dtype=torch.complex128, device=dev)
+        Vd = torch.tensor(Vs, dtype=torch.float64, device=dev)
+        tab = torch.zeros((len(Vs), nE, c.lmax + 1), dtype=torch.complex128, device=dev)
+        B.must_tinv_square_well(Ed_all, Vd, c.r_mt, c.lmax, tab)
+        n_sp = c.v_species.shape[1]
+        pot = torch.tensor([[sp * n_sp + int(c.species[b]) for b in range(c.n_basis)] for sp, _ in picks],
+                           device=dev)
+        eidx = torch.tensor([e for _, e in picks], device=dev)
+        tinv = tab[pot, eidx[:, None]].contiguous()                    # [items][N_b][lmax+1]
+        E = Ed_all[eidx].contiguous()
+        ws = torch.empty(B.must_kkr_workspace_bytes(h, items), dtype=torch.uint8, device=dev)
+        tau = torch.zeros((items, c.n_basis, h.kap, h.kap), dtype=torch.complex128, device=dev)
+        st = torch.zeros(items, dtype=torch.int32, device=dev)
+        for _ in range(args.warmup):
+            B.must_kkr_tau(h, E, tinv, ws, tau, st)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(0)
+        sampler.start()
+        time.sleep(0.2)
+        l0 = B.must_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            B.must_kkr_tau(h, E, tinv, ws, tau, st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        launches = B.must_launch_count() - l0
+        ms = e0.elapsed_time(e1) / args.steps
+        # per-kernel split from a second region with the phase events on
+        B.must_profile_enable(True)
+        B.must_profile_read()
+        for _ in range(args.steps):
+            B.must_kkr_tau(h, E, tinv, ws, tau, st)
+        torch.cuda.synchronize()
+        prof = B.must_profile_read()
+        B.must_profile_enable(False)
+        kern = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                for k, v in prof.items() if k.startswith("kkr_") and v[1] > 0}
+        work = kkr_work(h, c, items)
+        for k, f in work.items():
+            if k in kern and kern[k]["ms_per_step"] > 0:
+                kern[k]["tflops"] = f / (kern[k]["ms_per_step"] / 1e3) / 1e12
+                kern[k]["frac_of_measured_dfma"] = kern[k]["tflops"] / FP64_DFMA_MEASURED
+        dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+        # end to end: inputs from pinned host memory, tau and status back, every step
+        E_h = E.cpu().pin_memory()
+        T_h = tinv.cpu().pin_memory()
+        tau_h = torch.empty(tau.shape, dtype=tau.dtype).pin_memory()
+        st_h = torch.empty(st.shape, dtype=st.dtype).pin_memory()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            E.copy_(E_h, non_blocking=True)
+            tinv.copy_(T_h, non_blocking=True)
+            B.must_kkr_tau(h, E, tinv, ws, tau, st)
+            tau_h.copy_(tau, non_blocking=True)
+            st_h.copy_(st, non_blocking=True)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = g0.elapsed_time(g1) / args.steps
+        # the oracle on the host cores, on a bounded sample of the same items
+        sample = [picks[(k * 11) % items] for k in range(cores if c.n_basis == 1 else max(2, cores // 4))]
+        si = [picks.index(p) for p in sample]
+        Es = np.array([c.energies[e] for _, e in sample])
+        Ts = tinv.cpu().numpy()[si]
+        t0 = time.perf_counter()
+        ref, used = oracle.kkr_tau(c.lmax, c.lattice, c.basis, Es, Ts, c.n_k, h.eta, nthreads=cores)
+        dt = time.perf_counter() - t0
+        got = np.swapaxes(tau.cpu().numpy()[si], -1, -2)
+        err = np.linalg.norm(got - ref, axis=(-2, -1)) / np.linalg.norm(ref, axis=(-2, -1))
+        results[c.name] = {
+            "value": items / (ms / 1e3), "unit": "tau solves/s (all sites of the cell per (E, spin))",
+            "ms_per_step": ms, "items_per_step": items, "n": h.n, "k_points": h.n_kpts,
+            "inversions_per_s": items * h.n_kpts / (ms / 1e3),
+            "gpu_launches": launches, "kernels": kern,
+            "roofline": {"kernel_phase": dom, "bound": "alu", "unit": "TFLOP/s",
+                         "achieved": kern[dom].get("tflops"), "peak": FP64_DFMA_MEASURED,
+                         "peak_source": "measured DFMA probe (profiles/fp64_peak.md)",
+                         "frac": kern[dom].get("frac_of_measured_dfma")},
+            "e2e": {"value": items / (ms_e2e / 1e3), "unit": "tau solves/s",
+                    "h2d_bytes_per_step": int(E.numel() * 16 + tinv.numel() * 16),
+                    "d2h_bytes_per_step": int(tau.numel() * 16 + st.numel() * 4)},
+            "cpu_baseline": {"value": len(sample) / dt, "unit": "tau solves/s", "cores": int(used), "kind": "oracle",
+                             "sample": "%d of the %d items, one per thread, %.1f s" % (len(sample), items, dt)},
+            "max_rel_err_vs_oracle": float(err.max()),
+            "status_ok": bool((st.cpu().numpy() == 0).all()), "clocks": clocks, "eta": h.eta}
+    emit({"metric": "full KKR (periodic crystal): site-diagonal tau solves/s, FP64", "data": "synthetic "
+          "(square wells on the fcc lattice: L1_2 Ni3Au-like 4-site cell and a pure element's primitive cell)",
+          "dtype": "f64", "steps": args.steps, "warmup": args.warmup, "crystals": results})
+
+
 def cpu_baseline(w, sample: int):
     """The oracle on the host cores: `sample` (energy, spin) solves of the same
     LIZ, one per thread, timed end to end."""
@@ -1050,7 +1188,8 @@ def main():
                          "streams (1: one plan, one stream)")
     ap.add_argument("--cpu-sample", type=int, default=0)
     ap.add_argument("--workload", default="liz135",
-                    choices=["liz135", "supercell", "warmstart", "cusolver", "canted", "paper", "charge", "peaks"],
+                    choices=["liz135", "supercell", "warmstart", "cusolver", "canted", "paper", "charge", "peaks",
+                             "kkr"],
                     help="liz135: the benchmark workload; supercell: per-site LIZs of the 256-site supercell "
                          "with vacancies (uneven n), batched and replayed as a captured plan")
     ap.add_argument("--n-lizs", type=int, default=32, help="supercell / warmstart mode: evaluation LIZs")
@@ -1095,6 +1234,8 @@ def main():
         run_site_charge(args)
     elif args.workload == "peaks":
         run_peaks(args)
+    elif args.workload == "kkr":
+        run_kkr(args)
     else:
         run_ours(args)
 

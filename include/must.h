@@ -403,6 +403,56 @@ must_status must_tau00_solve_seeded(const must_liz* liz, int32_t nE, const doubl
  */
 must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double* sink, double* flops, void* stream);
 
+/*
+ * Full KKR of a periodic crystal (Sec. 5: the paper's next target is the
+ * same matrix inverse in the original KKR method, with the KKR matrix built on
+ * the GPU).  With N_b sites b_s in a cell of the lattice {R}, the structure
+ * constants of Eq. (4) summed over the lattice with Bloch phases,
+ *   G^{st}_{LL'}(k) = sum_{R: rho != 0} e^{ik.R} g0_{LL'}(rho),  rho = b_s - b_t - R,
+ * give M(k) = t^{-1} - G(k) of rank N_b (lmax+1)^2 (Sec. 2.1), and the
+ * site-diagonal block of tau in Eq. (4) is the Brillouin-zone average
+ *   tau^{ss}(E) = (1/n_k^3) sum_k [M(k)^{-1}]^{ss}
+ * over the Gamma-centred mesh k = sum_i (m_i / n_k) b*_i (b*_i the reciprocal
+ * vectors, a_i . b*_j = 2 pi delta_ij).  The lattice sums are evaluated by
+ * Ewald's split into a reciprocal-space and a real-space sum, both cut where
+ * their Gaussian factor falls below e^{-40}; that cut holds for Re E <= 1.5 Ry
+ * (items above it get MUST_EUNSUPPORTED in their status).  Everything is FP64.
+ *
+ * must_kkr_build: lattice: 3 x 3 row-major, rows a_1, a_2, a_3 (bohr); basis:
+ * n_basis x 3 site positions (bohr), distinct modulo the lattice; lmax in
+ * [0, 4] with n_basis (lmax+1)^2 <= 64 (one M(k) is inverted in one CTA's
+ * shared memory) and at most 32 distinct site displacements b_s - b_t; n_k in
+ * [1, 64]; eta: Ewald splitting parameter (bohr^-2), 0 = 4 pi / Omega^(2/3)
+ * (balances the two sums; the result does not depend on it).  Host arrays,
+ * read during the call.  Builds the k mesh, the reciprocal and real-space
+ * vector lists and the Gaunt table on the device (synchronises `stream`).
+ * Errors: MUST_EINVAL, MUST_ENOMEM, MUST_ECUDA.
+ *
+ * must_kkr_tau: n_items independent (energy, potential) items.  E: n_items
+ * complex; tinv: [n_items][n_basis][lmax+1] complex t^{-1}_l of each site;
+ * tau: [n_items][n_basis][kap][kap] complex, column-major blocks, kap =
+ * (lmax+1)^2; status: optional int32 per item (MUST_OK, MUST_ESINGULAR for an
+ * exactly zero pivot in some M(k), MUST_ENONFINITE, MUST_EUNSUPPORTED) or NULL.
+ * Pointers may be host or device memory (host buffers are staged through the
+ * workspace); workspace: caller-owned device memory of at least
+ * must_kkr_workspace_bytes(kkr, n_items) bytes (MUST_ENOMEM otherwise).
+ * Asynchronous on `stream` for device outputs; returns after the final copy
+ * for host outputs.  Errors: MUST_EINVAL, MUST_ENOMEM, MUST_ECUDA.
+ *
+ * must_kkr_info: info[6] = {M(k) order, k points, distinct displacements,
+ * real-space points, (k, K) reciprocal terms, k groups}; must_kkr_eta: the
+ * splitting parameter in use.
+ */
+typedef struct must_kkr must_kkr;
+must_status must_kkr_build(const double* lattice, const double* basis, int32_t n_basis, int32_t lmax, int32_t n_k,
+                           double eta, void* stream, must_kkr** out);
+void must_kkr_free(must_kkr* kkr);
+size_t must_kkr_workspace_bytes(const must_kkr* kkr, int32_t n_items);
+must_status must_kkr_tau(const must_kkr* kkr, int32_t n_items, const double* E, const double* tinv,
+                         void* workspace, size_t ws_bytes, double* tau, int32_t* status, void* stream);
+must_status must_kkr_info(const must_kkr* kkr, int32_t* info);
+double must_kkr_eta(const must_kkr* kkr);
+
 void must_profile_enable(int on);
 int must_profile_read(double* ms, long long* launches, long long* items, int n_phases);
 long long must_launch_count(void);

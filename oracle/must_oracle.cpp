@@ -893,16 +893,21 @@ int orc_kkr_tau(int lmax, const double* lattice, int nb, const double* basis, in
   int used = 1, bad = 0;
 #ifdef _OPENMP
   if (nthreads <= 0) nthreads = omp_get_max_threads();
-#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(| : bad)
+  if (nthreads > n_items) nthreads = n_items > 0 ? n_items : 1;
+#pragma omp parallel num_threads(nthreads) reduction(| : bad)
+  {
+#pragma omp single
+    used = omp_get_num_threads();
+#pragma omp for schedule(dynamic, 1)
 #endif
-  for (int it = 0; it < n_items; ++it) {
+    for (int it = 0; it < n_items; ++it) {
+      const cplx e(E[2 * it], E[2 * it + 1]);
+      bad |= kkr_tau(lmax, e, Lt, nb, basis, reinterpret_cast<const cplx*>(tinv) + size_t(it) * nb * (lmax + 1),
+                     nk, eta, cut, reinterpret_cast<cplx*>(tau) + size_t(it) * nb * nL * nL);
+    }
 #ifdef _OPENMP
-    if (omp_get_thread_num() == 0) used = omp_get_num_threads();
-#endif
-    const cplx e(E[2 * it], E[2 * it + 1]);
-    bad |= kkr_tau(lmax, e, Lt, nb, basis, reinterpret_cast<const cplx*>(tinv) + size_t(it) * nb * (lmax + 1), nk,
-                   eta, cut, reinterpret_cast<cplx*>(tau) + size_t(it) * nb * nL * nL);
   }
+#endif
   return bad ? -1 : used;
 }
 

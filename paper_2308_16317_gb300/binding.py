@@ -80,6 +80,12 @@ def load():
         "must_site_charge": (I32, [I32, I32, P, P, I32, P, D, P, P, P, P]),
         "must_site_density": (I32, [I32, I32, P, P, I32, P, D, P, I32, P, P, P]),
         "must_static_scratch_bytes": (SZ, []),
+        "must_kkr_build": (I32, [P, P, I32, I32, I32, D, P, ctypes.POINTER(P)]),
+        "must_kkr_free": (None, [P]),
+        "must_kkr_workspace_bytes": (SZ, [P, I32]),
+        "must_kkr_tau": (I32, [P, I32, P, P, P, SZ, P, P, P]),
+        "must_kkr_info": (I32, [P, P]),
+        "must_kkr_eta": (D, [P]),
         "must_profile_enable": (None, [ctypes.c_int]),
         "must_profile_read": (ctypes.c_int, [P, P, P, ctypes.c_int]),
         "must_launch_count": (ctypes.c_longlong, []),
@@ -107,7 +113,8 @@ def exported_symbols():
                         "must_mlp_set_params", "must_mlp_forward", "must_mlp_gradients", "must_mlp_train_step",
                         "must_mlp_save", "must_mlp_load", "must_mlp_features", "must_mlp_apply", "must_mlp_targets",
                         "must_tau00_solve_seeded", "must_contour_weights", "must_site_charge", "must_site_density",
-                        "must_peak_probe")]
+                        "must_peak_probe", "must_kkr_build", "must_kkr_free", "must_kkr_workspace_bytes",
+                        "must_kkr_tau", "must_kkr_info", "must_kkr_eta")]
 
 
 def _ptr(a):
@@ -393,3 +400,44 @@ def must_site_density(lmax: int, E, w, V, r_mt: float, tau00, r, n_of_r, stream=
     n_r = int(r.shape[0])
     _check(load().must_site_density(int(lmax), nE, _ptr(E), _ptr(w), n_out, _ptr(V), float(r_mt), _ptr(tau00),
                                     n_r, _ptr(r), _ptr(n_of_r), _stream(stream)))
+
+
+class Kkr:
+    """Owning wrapper of a must_kkr handle (full KKR of a periodic crystal)."""
+
+    def __init__(self, handle, n_basis, lmax):
+        self.handle = handle
+        self.n_basis, self.lmax = n_basis, lmax
+        self.kap = (lmax + 1) ** 2
+        info = np.zeros(6, np.int32)
+        _check(load().must_kkr_info(handle, _ptr(info)))
+        self.n, self.n_kpts, self.n_disp, self.n_pts, self.n_kK, self.n_kg = (int(v) for v in info)
+        self.eta = float(load().must_kkr_eta(handle))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.must_kkr_free(self.handle)
+            self.handle = None
+
+
+def must_kkr_build(lattice, basis, lmax: int, n_k: int, eta: float = 0.0, stream=None) -> Kkr:
+    lat = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(3, 3))
+    bas = np.ascontiguousarray(np.asarray(basis, dtype=np.float64).reshape(-1, 3))
+    out = ctypes.c_void_p()
+    _check(load().must_kkr_build(_ptr(lat), _ptr(bas), int(bas.shape[0]), int(lmax), int(n_k), float(eta),
+                                 _stream(stream), ctypes.byref(out)))
+    return Kkr(out, int(bas.shape[0]), int(lmax))
+
+
+def must_kkr_workspace_bytes(kkr: Kkr, n_items: int) -> int:
+    return int(load().must_kkr_workspace_bytes(kkr.handle, int(n_items)))
+
+
+def must_kkr_tau(kkr: Kkr, E, tinv, workspace, tau, status=None, stream=None):
+    """E [n_items] complex128; tinv [n_items][n_basis][lmax+1] complex128;
+    tau [n_items][n_basis][kap][kap] complex128 (column-major blocks); status [n_items] int32 or None."""
+    n_items = _numel_complex(E)
+    ws_bytes = int(workspace.numel() * workspace.element_size()) if hasattr(workspace, "numel") else workspace.nbytes
+    _check(load().must_kkr_tau(kkr.handle, n_items, _ptr(E), _ptr(tinv), _ptr(workspace), ws_bytes, _ptr(tau),
+                               _ptr(status), _stream(stream)))
+    return tau

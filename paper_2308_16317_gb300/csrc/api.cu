@@ -296,3 +296,6 @@ must_status must_site_density(int32_t lmax, int32_t nE, const double* E, const d
 }
 
 }  // extern "C"
+
+// Gauss-Legendre rule for other translation units (C++ linkage).
+void must_gauss_legendre_nodes(int n, std::vector<double>& x, std::vector<double>& w) { gauss_legendre_host(n, x, w); }

@@ -1,0 +1,965 @@
+// Full KKR for a periodic crystal (the paper's Sec. 5: the KKR matrix inverse
+// of the original method, built and inverted on the GPU).
+//
+// N_b sites b_s per cell of the lattice {R}.  The structure constants of
+// Eq. (4) summed over the lattice with Bloch phases,
+//   G^{st}_{LL'}(k) = sum_{R: rho != 0} e^{ik.R} g0_{LL'}(rho),  rho = b_s - b_t - R,
+// give the KKR matrix M(k) = t^{-1} - G(k) of order N_b (lmax+1)^2 (Sec. 2.1),
+// and the site-diagonal scattering-path block is its Brillouin-zone average
+//   tau^{ss}(E) = (1/N_k) sum_k [M(k)^{-1}]^{ss}
+// over a Gamma-centred uniform mesh of n_k^3 points.
+//
+// Lattice sums by Ewald's split.  With D^{st}_L(k) = sum_R e^{ik.R}
+// h_l(kappa|rho|) Y_L(rho^), so that G^{st}_{LL'} = -4 pi i kappa
+// sum_L'' i^{l-l'+l''} C(L,L',L'') D^{st}_L'':
+//   D_L = (-kappa)^{-l} (-i/kappa) [A_L + B_L + C_L]
+//   A_L = (4 pi/Omega) i^l sum_K e^{iq.x} YS_L(q) e^{(E-q^2)/eta} / (q^2 - E),   q = k + K
+//   B_L = (2/sqrt pi) (-2)^l sum_{R: rho != 0} e^{ik.R} YS_L(rho) I_l(|rho|)
+//   C_0 = -(1/sqrt(4 pi)) [i kappa - sqrt(eta/pi) sum_n (E/eta)^n / (n! (2n-1))]   (s = t only)
+// with x = b_s - b_t, YS_L(v) = |v|^l Y_L(v^) the real solid harmonics and
+//   I_l(rho) = int_{sqrt(eta)/2}^inf xi^{2l} exp(-rho^2 xi^2 + E/(4 xi^2)) d xi.
+// This follows from h_l(kappa r) Y_L(r^) = (-kappa)^{-l} YS_L(grad) h_0(kappa r),
+// h_0(z) = -i e^{iz}/z and e^{i kappa r}/r = (2/sqrt pi) int_0^inf
+// exp(-r^2 xi^2 + E/(4 xi^2)) d xi, split at xi0 = sqrt(eta)/2: the part below
+// xi0 is summed over the reciprocal lattice (Poisson), the part above in real
+// space.  I_l is evaluated after the substitution u = rho^2 (xi^2 - xi0^2),
+//   I_l = e^{-rho^2 xi0^2} / (2 rho^2) int_0^inf e^{-u} xi^{2l-1} e^{E/(4 xi^2)} du,
+// by 16-point Gauss-Legendre rules on the graded panels [0,1], [1,2], [2,4], ...,
+// [32,60] of u (the integrand's singularity at u = -rho^2 xi0^2 can lie close to
+// u = 0 for near-neighbour rho and small eta, which a Gauss-Laguerre rule
+// resolves only to ~1e-11; the graded panels reach ~1e-15).
+//
+// Kernels (all FP64):
+//   kkr_real_terms_kernel  per (item, real-space point): the k-independent factor of B_L
+//   kkr_recip_kernel       per (item, k): A_L + C_L for every distinct displacement x
+//   kkr_realsum_kernel     per (item, displacement, 32 k points): adds B_L
+//   kkr_invert_kernel      per (item, group of k points): M(k) by the Gaunt contraction in
+//                          shared memory, equilibrated, Gauss-Jordan with partial pivoting,
+//                          diagonal blocks of M(k)^{-1} summed over the group in a fixed order
+//   kkr_bz_sum_kernel      per output element: the groups summed in a fixed order, / N_k
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "solver.h"
+#include "prof.h"
+
+void must_gaunt_csr(int lmax, std::vector<int>& start, std::vector<int>& L2s, std::vector<double>& coef);
+void must_gauss_legendre_nodes(int n, std::vector<double>& x, std::vector<double>& w);
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int KKR_MAX_N = 64;          // largest M(k) order (one CTA's shared memory)
+constexpr int KKR_MAX_L2 = 8;          // l'' <= 2 lmax
+constexpr int KKR_MAX_NL2 = (KKR_MAX_L2 + 1) * (KKR_MAX_L2 + 1);
+constexpr int KKR_MAX_DISP = 32;       // distinct displacements b_s - b_t
+constexpr int KKR_QUAD = 112;          // quadrature nodes for I_l (7 panels x 16)
+constexpr int KKR_KCHUNK = 64;         // reciprocal vectors per shared-memory chunk
+constexpr int KKR_KB = 32;             // k points per real-space block
+constexpr int KKR_RCHUNK = 32;         // real-space points per chunk
+constexpr int KKR_KG = 8;              // k points per inversion CTA
+constexpr double KKR_CUT = 40.0;       // both sums cut where their Gaussian factor < e^{-cut}
+constexpr double KKR_ECAP = 1.5;       // sums are cut for Re E <= KKR_ECAP (Ry)
+
+__device__ __forceinline__ int l_of_L(int L) {
+  int l = 0;
+  while ((l + 1) * (l + 1) <= L) ++l;
+  return l;
+}
+
+// Real solid harmonics YS_L(v) = |v|^l Y_L(v^), L < (lmax+1)^2, same basis as
+// the library's Y_L (no Condon-Shortley phase), evaluated as polynomials so
+// that v = 0 needs no special case:
+//   YS_lm = N_lm {sqrt2 Re (x+iy)^m | 1 | sqrt2 Im (x+iy)^|m|} q_l^|m|(z, r^2),
+//   q_m^m = (2m-1)!!, q_{m+1}^m = (2m+1) z q_m^m,
+//   q_l^m = [(2l-1) z q_{l-1}^m - (l+m-1) r^2 q_{l-2}^m] / (l-m).
+__device__ void solid_harmonics(int lmax, double x, double y, double z, double* out) {
+  const double r2 = x * x + y * y + z * z;
+  double cr = 1.0, ci = 0.0;     // (x + i y)^m
+  double dfact = 1.0;            // (2m-1)!!
+  for (int m = 0; m <= lmax; ++m) {
+    if (m > 0) {
+      const double nr = cr * x - ci * y, ni = cr * y + ci * x;
+      cr = nr; ci = ni;
+      dfact *= (2.0 * m - 1.0);
+    }
+    double qm2 = 0.0, qm1 = 0.0;
+    for (int l = m; l <= lmax; ++l) {
+      double q;
+      if (l == m) q = dfact;
+      else if (l == m + 1) q = (2.0 * m + 1.0) * z * dfact;
+      else q = ((2.0 * l - 1.0) * z * qm1 - (l + m - 1.0) * r2 * qm2) / double(l - m);
+      qm2 = qm1;
+      qm1 = q;
+      double ratio = 1.0;
+      for (int k = l - m + 1; k <= l + m; ++k) ratio /= double(k);
+      const double N = sqrt((2.0 * l + 1.0) / (4.0 * kPi) * ratio);
+      if (m == 0) {
+        out[l * l + l] = N * q;
+      } else {
+        out[l * l + l + m] = 1.41421356237309504880 * N * q * cr;
+        out[l * l + l - m] = 1.41421356237309504880 * N * q * ci;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ cd cexp_d(cd z) {
+  double s, c;
+  sincos(z.y, &s, &c);
+  const double m = exp(z.x);
+  return mk(m * c, m * s);
+}
+
+// i^l
+__device__ __forceinline__ cd ipow_d(int l) {
+  switch (l & 3) {
+    case 0: return mk(1.0, 0.0);
+    case 1: return mk(0.0, 1.0);
+    case 2: return mk(-1.0, 0.0);
+    default: return mk(0.0, -1.0);
+  }
+}
+
+struct KkrDev {
+  int nb, lmax, nL, l2max, nL2, n, n_kpts, n_disp, n_pts, n_kg;
+  double eta, omega;
+  const double* kpts;     // [n_kpts][3]
+  const double* Kvec;     // [nK][3]
+  const int* kK_start;    // [n_kpts + 1]
+  const int* kK_idx;      // reciprocal vectors of each k with |k + K|^2 <= qmax^2
+  const double* disp;     // [n_disp][3], disp 0 = 0
+  const int* pair_disp;   // [nb * nb]
+  const int* pt_start;    // [n_disp + 1]
+  const double* pt_R;     // [n_pts][3] lattice vector R
+  const double* pt_rho;   // [n_pts][4] rho = x - R and |rho|
+  const double* quad_u;   // [KKR_QUAD] nodes in u
+  const double* quad_w;   // weights times e^{-u}
+  const int* g_start;     // Gaunt CSR, rows (L, L')
+  const int* g_L2;
+  const double* g_c;
+};
+
+// -------------------------------------------------------------------------
+// B_L's k-independent factor of every (item, real-space point):
+//   T[item][pt][L] = (2/sqrt pi) (-2)^l YS_L(rho) I_l(|rho|)
+__global__ void kkr_real_terms_kernel(KkrDev K, int items, const double2* __restrict__ E,
+                                      double2* __restrict__ T, int* __restrict__ status) {
+  const int pt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int it = blockIdx.y;
+  if (pt >= K.n_pts || it >= items) return;
+  const cd e = mk(E[it].x, E[it].y);
+  if (!(e.x <= KKR_ECAP) || !isfinite(e.y)) {
+    if (pt == 0) atomicMax(status + it, int(MUST_EUNSUPPORTED));
+  }
+  const double* pr = K.pt_rho + size_t(pt) * 4;
+  const double r = pr[3], r2 = r * r;
+  const double xi02 = 0.25 * K.eta;
+  cd I[KKR_MAX_L2 + 1];
+  for (int l = 0; l <= K.l2max; ++l) I[l] = mk(0.0, 0.0);
+  for (int j = 0; j < KKR_QUAD; ++j) {
+    const double xi2 = xi02 + K.quad_u[j] / r2;
+    const double inv_xi2 = 1.0 / xi2;
+    const cd g = K.quad_w[j] * cexp_d(mk(0.25 * e.x * inv_xi2, 0.25 * e.y * inv_xi2));
+    double p = rsqrt(xi2);               // xi^{2l-1}, l = 0
+    for (int l = 0; l <= K.l2max; ++l) {
+      I[l] = I[l] + p * g;
+      p *= xi2;
+    }
+  }
+  const double pref = exp(-r2 * xi02) / (2.0 * r2) * (2.0 / sqrt(kPi));
+  double Y[KKR_MAX_NL2];
+  solid_harmonics(K.l2max, pr[0], pr[1], pr[2], Y);
+  double2* out = T + (size_t(it) * K.n_pts + pt) * K.nL2;
+  double m2l = 1.0;                      // (-2)^l
+  for (int l = 0; l <= K.l2max; ++l) {
+    const cd f = (pref * m2l) * I[l];
+    for (int m = -l; m <= l; ++m) {
+      const int L = l * l + l + m;
+      out[L] = make_double2(f.x * Y[L], f.y * Y[L]);
+    }
+    m2l *= -2.0;
+  }
+}
+
+// -------------------------------------------------------------------------
+// A_L + C_L for every displacement, one CTA per (k, item):
+//   Dk[item][k][d][L] = (4 pi/Omega) i^l sum_K e^{iq.x_d} YS_L(q) e^{(E-q^2)/eta}/(q^2-E) + C_L
+constexpr int RECIP_THREADS = 256;
+constexpr int RECIP_OUT = (KKR_MAX_DISP * KKR_MAX_NL2 + RECIP_THREADS - 1) / RECIP_THREADS;
+
+__global__ void __launch_bounds__(RECIP_THREADS) kkr_recip_kernel(KkrDev K, int items, const double2* __restrict__ E,
+                                                                  double2* __restrict__ Dk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* F = reinterpret_cast<double2*>(smem_raw);                 // [KCHUNK][nL2]
+  double2* P = F + KKR_KCHUNK * K.nL2;                                 // [n_disp][KCHUNK]
+  double* qv = reinterpret_cast<double*>(P + K.n_disp * KKR_KCHUNK);  // [KCHUNK][3]
+  const int ik = blockIdx.x, it = blockIdx.y, tid = threadIdx.x;
+  const cd e = mk(E[it].x, E[it].y);
+  const double* kp = K.kpts + size_t(ik) * 3;
+  const int k0 = K.kK_start[ik], k1 = K.kK_start[ik + 1];
+  const int n_out = K.n_disp * K.nL2;
+  cd acc[RECIP_OUT];
+#pragma unroll
+  for (int j = 0; j < RECIP_OUT; ++j) acc[j] = mk(0.0, 0.0);
+  const double wpre = 4.0 * kPi / K.omega;
+  for (int c0 = k0; c0 < k1; c0 += KKR_KCHUNK) {
+    const int cn = min(KKR_KCHUNK, k1 - c0);
+    if (tid < KKR_KCHUNK) {
+      double2* f = F + tid * K.nL2;
+      if (tid < cn) {
+        const double* Kv = K.Kvec + size_t(K.kK_idx[c0 + tid]) * 3;
+        const double q0 = kp[0] + Kv[0], q1 = kp[1] + Kv[1], q2v = kp[2] + Kv[2];
+        const double qq = q0 * q0 + q1 * q1 + q2v * q2v;
+        qv[tid * 3] = q0; qv[tid * 3 + 1] = q1; qv[tid * 3 + 2] = q2v;
+        // w = wpre e^{(E - q^2)/eta} / (q^2 - E)
+        const cd ex = cexp_d(mk((e.x - qq) / K.eta, e.y / K.eta));
+        const cd w = wpre * (ex * cinv(mk(qq - e.x, -e.y)));
+        double Y[KKR_MAX_NL2];
+        solid_harmonics(K.l2max, q0, q1, q2v, Y);
+        for (int l = 0; l <= K.l2max; ++l) {
+          const cd wl = ipow_d(l) * w;
+          for (int m = -l; m <= l; ++m) {
+            const int L = l * l + l + m;
+            f[L] = make_double2(wl.x * Y[L], wl.y * Y[L]);
+          }
+        }
+      } else {
+        for (int L = 0; L < K.nL2; ++L) f[L] = make_double2(0.0, 0.0);
+        qv[tid * 3] = 0.0; qv[tid * 3 + 1] = 0.0; qv[tid * 3 + 2] = 0.0;
+      }
+    }
+    __syncthreads();
+    for (int p = tid; p < K.n_disp * KKR_KCHUNK; p += RECIP_THREADS) {
+      const int d = p / KKR_KCHUNK, j = p % KKR_KCHUNK;
+      const double* x = K.disp + d * 3;
+      double s, c;
+      sincos(qv[j * 3] * x[0] + qv[j * 3 + 1] * x[1] + qv[j * 3 + 2] * x[2], &s, &c);
+      P[d * KKR_KCHUNK + j] = make_double2(c, s);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < RECIP_OUT; ++jj) {
+      const int o = tid + jj * RECIP_THREADS;
+      if (o < n_out) {
+        const int d = o / K.nL2, L = o % K.nL2;
+        cd a = acc[jj];
+        for (int j = 0; j < cn; ++j) {
+          const double2 pp = P[d * KKR_KCHUNK + j], ff = F[j * K.nL2 + L];
+          a.x = fma(pp.x, ff.x, fma(-pp.y, ff.y, a.x));
+          a.y = fma(pp.x, ff.y, fma(pp.y, ff.x, a.y));
+        }
+        acc[jj] = a;
+      }
+    }
+    __syncthreads();
+  }
+  double2* out = Dk + (size_t(it) * K.n_kpts + ik) * n_out;
+#pragma unroll
+  for (int jj = 0; jj < RECIP_OUT; ++jj) {
+    const int o = tid + jj * RECIP_THREADS;
+    if (o < n_out) {
+      cd a = acc[jj];
+      if (o == 0) {
+        // C_0 of displacement 0 (x = 0): the R = 0 term of the reciprocal sum removed
+        const cd kap = csqrt_p(e);
+        const cd z = mk(e.x / K.eta, e.y / K.eta);
+        cd s = mk(0.0, 0.0), term = mk(1.0, 0.0);   // (E/eta)^n / n!
+        for (int n = 0; n < 400; ++n) {
+          const cd add = (1.0 / double(2 * n - 1)) * term;
+          s = s + add;
+          if (n > 4 && cnorm(add) < 1e-36 * cnorm(s)) break;
+          term = (1.0 / double(n + 1)) * (term * z);
+        }
+        const cd f1 = mk(-kap.y, kap.x) - sqrt(K.eta / kPi) * s;
+        a = a - (1.0 / sqrt(4.0 * kPi)) * f1;
+      }
+      out[o] = make_double2(a.x, a.y);
+    }
+  }
+}
+
+// -------------------------------------------------------------------------
+// Adds B_L: Dk[item][k][d][L] += sum_{pt of d} e^{ik.R_pt} T[item][pt][L], one CTA
+// per (block of KKR_KB k points, displacement, item).
+constexpr int RSUM_THREADS = 256;
+constexpr int RSUM_OUT = (KKR_KB * KKR_MAX_NL2 + RSUM_THREADS - 1) / RSUM_THREADS;
+
+__global__ void __launch_bounds__(RSUM_THREADS) kkr_realsum_kernel(KkrDev K, int items,
+                                                                   const double2* __restrict__ T,
+                                                                   double2* __restrict__ Dk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* Ts = reinterpret_cast<double2*>(smem_raw);   // [RCHUNK][nL2]
+  double2* ph = Ts + KKR_RCHUNK * K.nL2;                 // [KB][RCHUNK]
+  const int kb = blockIdx.x, d = blockIdx.y, it = blockIdx.z, tid = threadIdx.x;
+  const int kbase = kb * KKR_KB;
+  const int nkb = min(KKR_KB, K.n_kpts - kbase);
+  const int p0 = K.pt_start[d], p1 = K.pt_start[d + 1];
+  const int n_out = nkb * K.nL2;
+  cd acc[RSUM_OUT];
+#pragma unroll
+  for (int j = 0; j < RSUM_OUT; ++j) acc[j] = mk(0.0, 0.0);
+  const double2* Tit = T + size_t(it) * K.n_pts * K.nL2;
+  for (int c0 = p0; c0 < p1; c0 += KKR_RCHUNK) {
+    const int cn = min(KKR_RCHUNK, p1 - c0);
+    for (int q = tid; q < cn * K.nL2; q += RSUM_THREADS) Ts[q] = Tit[size_t(c0) * K.nL2 + q];
+    for (int q = tid; q < KKR_KB * KKR_RCHUNK; q += RSUM_THREADS) {
+      const int kk = q / KKR_RCHUNK, j = q % KKR_RCHUNK;
+      if (kk < nkb && j < cn) {
+        const double* kp = K.kpts + size_t(kbase + kk) * 3;
+        const double* R = K.pt_R + size_t(c0 + j) * 3;
+        double s, c;
+        sincos(kp[0] * R[0] + kp[1] * R[1] + kp[2] * R[2], &s, &c);
+        ph[q] = make_double2(c, s);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < RSUM_OUT; ++jj) {
+      const int o = tid + jj * RSUM_THREADS;
+      if (o < n_out) {
+        const int kk = o / K.nL2, L = o % K.nL2;
+        cd a = acc[jj];
+        for (int j = 0; j < cn; ++j) {
+          const double2 pp = ph[kk * KKR_RCHUNK + j], tt = Ts[j * K.nL2 + L];
+          a.x = fma(pp.x, tt.x, fma(-pp.y, tt.y, a.x));
+          a.y = fma(pp.x, tt.y, fma(pp.y, tt.x, a.y));
+        }
+        acc[jj] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int jj = 0; jj < RSUM_OUT; ++jj) {
+    const int o = tid + jj * RSUM_THREADS;
+    if (o < n_out) {
+      const int kk = o / K.nL2, L = o % K.nL2;
+      double2* dst = Dk + ((size_t(it) * K.n_kpts + kbase + kk) * K.n_disp + d) * K.nL2 + L;
+      const double2 v = *dst;
+      *dst = make_double2(v.x + acc[jj].x, v.y + acc[jj].y);
+    }
+  }
+}
+
+// -------------------------------------------------------------------------
+// M(k) = t^{-1} - G(k) in shared memory, inverted in place; the diagonal
+// blocks of M(k)^{-1} of KKR_KG k points summed in order into
+//   part[item][group][s][L][L'].
+constexpr int INV_THREADS = 256;
+
+__global__ void __launch_bounds__(INV_THREADS) kkr_invert_kernel(KkrDev K, int items, const double2* __restrict__ E,
+                                                                 const double2* __restrict__ tinv,
+                                                                 const double2* __restrict__ Dk,
+                                                                 double2* __restrict__ part, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = K.n, ldA = n + 1;
+  double2* A = reinterpret_cast<double2*>(smem_raw);        // [n][n+1] row-major
+  double2* Ds = A + n * ldA;                                 // [n_disp][nL2]
+  double2* acc = Ds + K.n_disp * K.nL2;                      // [nb][nL][nL]
+  double2* colk = acc + K.nb * K.nL * K.nL;                  // [n]
+  double* sc = reinterpret_cast<double*>(colk + n);          // [n]
+  int* perm = reinterpret_cast<int*>(sc + n);                // [n]
+  int* sigma = perm + n;                                     // [n]
+  __shared__ double2 fl[KKR_MAX_L2 + 1];
+  __shared__ double2 ti_s[KKR_MAX_N];
+  __shared__ int piv_s;
+  __shared__ int singular;
+  const int g = blockIdx.x, it = blockIdx.y, tid = threadIdx.x;
+  const int nL = K.nL, nb = K.nb;
+  const cd e = mk(E[it].x, E[it].y);
+  const cd kap = csqrt_p(e);
+  if (tid <= K.l2max) {
+    // f_l = (-kappa)^{-l} (-i/kappa), times the -4 pi i kappa of G: -4 pi (-kappa)^{-l}
+    cd p = mk(-4.0 * kPi, 0.0);
+    const cd mik = cinv(mk(-kap.x, -kap.y));
+    for (int l = 0; l < tid; ++l) p = p * mik;
+    fl[tid] = make_double2(p.x, p.y);
+  }
+  if (tid < n) {
+    const int s = tid / nL, L = tid % nL, l = l_of_L(L);
+    ti_s[tid] = tinv[(size_t(it) * nb + s) * (K.lmax + 1) + l];
+  }
+  for (int q = tid; q < nb * nL * nL; q += INV_THREADS) acc[q] = make_double2(0.0, 0.0);
+  if (tid == 0) singular = 0;
+  __syncthreads();
+  const int kbeg = g * KKR_KG, kend = min(K.n_kpts, kbeg + KKR_KG);
+  for (int ik = kbeg; ik < kend; ++ik) {
+    const double2* src = Dk + (size_t(it) * K.n_kpts + ik) * K.n_disp * K.nL2;
+    for (int q = tid; q < K.n_disp * K.nL2; q += INV_THREADS) {
+      const int L = q % K.nL2;
+      const cd v = mk(src[q].x, src[q].y) * mk(fl[l_of_L(L)].x, fl[l_of_L(L)].y);
+      Ds[q] = make_double2(v.x, v.y);
+    }
+    __syncthreads();
+    // A = t^{-1} - G, G_{LL'} = sum_{L''} c D_{L''} (prefactors folded into Ds)
+    for (int q = tid; q < n * n; q += INV_THREADS) {
+      const int i = q / n, j = q % n;
+      const int s = i / nL, L = i % nL, t = j / nL, Lp = j % nL;
+      const double2* Dd = Ds + K.pair_disp[s * nb + t] * K.nL2;
+      cd gsum = mk(0.0, 0.0);
+      for (int p = K.g_start[L * nL + Lp]; p < K.g_start[L * nL + Lp + 1]; ++p) {
+        const double c = K.g_c[p];
+        const double2 dv = Dd[K.g_L2[p]];
+        gsum.x = fma(c, dv.x, gsum.x);
+        gsum.y = fma(c, dv.y, gsum.y);
+      }
+      cd a = mk(-gsum.x, -gsum.y);
+      if (i == j) a = a + mk(ti_s[i].x, ti_s[i].y);
+      A[i * ldA + j] = make_double2(a.x, a.y);
+    }
+    __syncthreads();
+    // symmetric equilibration D A D, D = |diag A|^{-1/2}
+    if (tid < n) {
+      const double2 d = A[tid * ldA + tid];
+      const double m = sqrt(d.x * d.x + d.y * d.y);
+      sc[tid] = (m > 0.0 && isfinite(m)) ? 1.0 / sqrt(m) : 1.0;
+    }
+    __syncthreads();
+    for (int q = tid; q < n * n; q += INV_THREADS) {
+      const int i = q / n, j = q % n;
+      const double f = sc[i] * sc[j];
+      double2 v = A[i * ldA + j];
+      A[i * ldA + j] = make_double2(v.x * f, v.y * f);
+    }
+    __syncthreads();
+    // Gauss-Jordan in place with partial (row) pivoting
+    for (int k = 0; k < n; ++k) {
+      if (tid < 32) {
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + tid; i < n; i += 32) {
+          const double2 v = A[i * ldA + k];
+          const double m = fabs(v.x) + fabs(v.y);
+          if (m > best) { best = m; bi = i; }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          const double ob = __shfl_down_sync(0xffffffffu, best, off);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (tid == 0) {
+          piv_s = bi;
+          perm[k] = bi;
+          if (!(best > 0.0)) singular = 1;
+        }
+      }
+      __syncthreads();
+      const int p = piv_s;
+      if (p != k)
+        for (int j = tid; j < n; j += INV_THREADS) {
+          const double2 t0 = A[k * ldA + j];
+          A[k * ldA + j] = A[p * ldA + j];
+          A[p * ldA + j] = t0;
+        }
+      __syncthreads();
+      const double2 pv = A[k * ldA + k];
+      const cd pinv = (pv.x == 0.0 && pv.y == 0.0) ? mk(0.0, 0.0) : cinv(mk(pv.x, pv.y));
+      for (int j = tid; j < n; j += INV_THREADS) {
+        if (j == k) continue;
+        const cd v = mk(A[k * ldA + j].x, A[k * ldA + j].y) * pinv;
+        A[k * ldA + j] = make_double2(v.x, v.y);
+      }
+      if (tid < n) colk[tid] = A[tid * ldA + k];
+      __syncthreads();
+      for (int q = tid; q < n * n; q += INV_THREADS) {
+        const int i = q / n, j = q % n;
+        if (i == k) {
+          if (j == k) A[k * ldA + k] = make_double2(pinv.x, pinv.y);
+          continue;
+        }
+        const cd f = mk(colk[i].x, colk[i].y);
+        if (j == k) {
+          const cd v = f * pinv;
+          A[i * ldA + k] = make_double2(-v.x, -v.y);
+        } else {
+          cd a = mk(A[i * ldA + j].x, A[i * ldA + j].y);
+          const double2 rk = A[k * ldA + j];
+          cfms(a, f, mk(rk.x, rk.y));
+          A[i * ldA + j] = make_double2(a.x, a.y);
+        }
+      }
+      __syncthreads();
+    }
+    // column j of the inverse is column sigma(j) of the in-place result
+    if (tid < n) {
+      int v = tid;
+      for (int k = 0; k < n; ++k) {
+        const int pk = perm[k];
+        if (v == k) v = pk;
+        else if (v == pk) v = k;
+      }
+      sigma[tid] = v;
+    }
+    __syncthreads();
+    for (int q = tid; q < nb * nL * nL; q += INV_THREADS) {
+      const int s = q / (nL * nL), L = (q / nL) % nL, Lp = q % nL;
+      const int i = s * nL + L, j = s * nL + Lp;
+      const double2 x = A[i * ldA + sigma[j]];
+      const double f = sc[i] * sc[j];
+      acc[q] = make_double2(acc[q].x + f * x.x, acc[q].y + f * x.y);
+    }
+    __syncthreads();
+  }
+  double2* dst = part + (size_t(it) * K.n_kg + g) * nb * nL * nL;
+  for (int q = tid; q < nb * nL * nL; q += INV_THREADS) dst[q] = acc[q];
+  if (tid == 0 && singular) atomicMax(status + it, int(MUST_ESINGULAR));
+}
+
+// tau[item][s] (column-major kap x kap) = (1/N_k) sum over groups, in order.
+__global__ void kkr_bz_sum_kernel(KkrDev K, int items, const double2* __restrict__ part, double2* __restrict__ tau,
+                                  int* __restrict__ status) {
+  const int nLL = K.nL * K.nL;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= items * K.nb * nLL) return;
+  const int it = q / (K.nb * nLL), r = q % (K.nb * nLL);
+  const int s = r / nLL, L = (r / K.nL) % K.nL, Lp = r % K.nL;
+  double sx = 0.0, sy = 0.0;
+  for (int g = 0; g < K.n_kg; ++g) {
+    const double2 v = part[(size_t(it) * K.n_kg + g) * K.nb * nLL + r];
+    sx += v.x;
+    sy += v.y;
+  }
+  const double w = 1.0 / double(K.n_kpts);
+  sx *= w;
+  sy *= w;
+  if (!isfinite(sx) || !isfinite(sy)) atomicMax(status + it, int(MUST_ENONFINITE));
+  tau[(size_t(it) * K.nb + s) * nLL + L + Lp * K.nL] = make_double2(sx, sy);
+}
+
+__global__ void kkr_status_init_kernel(int items, int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < items) status[i] = 0;
+}
+
+__global__ void kkr_status_out_kernel(int items, const int* status, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < items) out[i] = status[i];
+}
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Nodes and weights (times e^{-u}) of 16-point Gauss-Legendre rules on the
+// graded panels [0,1], [1,2], [2,4], [4,8], [8,16], [16,32], [32,60] of u.
+void quadrature_u(std::vector<double>& u, std::vector<double>& w) {
+  std::vector<double> x, wx;
+  must_gauss_legendre_nodes(16, x, wx);
+  const double edges[8] = {0.0, 1.0, 2.0, 4.0, 8.0, 16.0, 32.0, 60.0};
+  u.clear();
+  w.clear();
+  for (int p = 0; p < 7; ++p) {
+    const double lo = edges[p], hi = edges[p + 1], h = 0.5 * (hi - lo);
+    for (int j = 0; j < 16; ++j) {
+      const double uj = lo + h * (x[j] + 1.0);
+      u.push_back(uj);
+      w.push_back(h * wx[j] * std::exp(-uj));
+    }
+  }
+}
+
+double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+double norm3(const double* a) { return std::sqrt(dot3(a, a)); }
+
+// All n1 V0 + n2 V1 + n3 V2 with |c + v| <= rmax; W: dual rows (a_i . b_j = 2 pi delta).
+void points_within(const double V[3][3], const double W[3][3], const double* c, double rmax,
+                   std::vector<double>& out) {
+  int nmax[3];
+  const double cn = norm3(c);
+  for (int i = 0; i < 3; ++i) nmax[i] = int(std::ceil((rmax + cn) * norm3(W[i]) / (2.0 * kPi))) + 1;
+  out.clear();
+  for (int n1 = -nmax[0]; n1 <= nmax[0]; ++n1)
+    for (int n2 = -nmax[1]; n2 <= nmax[1]; ++n2)
+      for (int n3 = -nmax[2]; n3 <= nmax[2]; ++n3) {
+        double v[3], w[3];
+        for (int d = 0; d < 3; ++d) {
+          v[d] = n1 * V[0][d] + n2 * V[1][d] + n3 * V[2][d];
+          w[d] = c[d] + v[d];
+        }
+        if (norm3(w) <= rmax) out.insert(out.end(), v, v + 3);
+      }
+}
+
+}  // namespace
+
+struct must_kkr {
+  int nb, lmax, nL, l2max, nL2, n, n_k, n_kpts, n_disp, n_pts, n_K, n_kK, n_kg, device;
+  double eta, omega;
+  double* d_kpts;
+  double* d_K;
+  int* d_kK_start;
+  int* d_kK_idx;
+  double* d_disp;
+  int* d_pair_disp;
+  int* d_pt_start;
+  double* d_pt_R;
+  double* d_pt_rho;
+  double* d_quad_u;
+  double* d_quad_w;
+  int* d_g_start;
+  int* d_g_L2;
+  double* d_g_c;
+};
+
+namespace {
+
+KkrDev dev_view(const must_kkr* h) {
+  KkrDev K;
+  K.nb = h->nb; K.lmax = h->lmax; K.nL = h->nL; K.l2max = h->l2max; K.nL2 = h->nL2; K.n = h->n;
+  K.n_kpts = h->n_kpts; K.n_disp = h->n_disp; K.n_pts = h->n_pts; K.n_kg = h->n_kg;
+  K.eta = h->eta; K.omega = h->omega;
+  K.kpts = h->d_kpts; K.Kvec = h->d_K; K.kK_start = h->d_kK_start; K.kK_idx = h->d_kK_idx;
+  K.disp = h->d_disp; K.pair_disp = h->d_pair_disp; K.pt_start = h->d_pt_start; K.pt_R = h->d_pt_R;
+  K.pt_rho = h->d_pt_rho; K.quad_u = h->d_quad_u; K.quad_w = h->d_quad_w;
+  K.g_start = h->d_g_start; K.g_L2 = h->d_g_L2; K.g_c = h->d_g_c;
+  return K;
+}
+
+size_t recip_smem(const must_kkr* h) {
+  return sizeof(double2) * (size_t(KKR_KCHUNK) * h->nL2 + size_t(h->n_disp) * KKR_KCHUNK) +
+         sizeof(double) * 3 * KKR_KCHUNK;
+}
+
+size_t realsum_smem(const must_kkr* h) {
+  return sizeof(double2) * (size_t(KKR_RCHUNK) * h->nL2 + size_t(KKR_KB) * KKR_RCHUNK);
+}
+
+size_t invert_smem(const must_kkr* h) {
+  return sizeof(double2) * (size_t(h->n) * (h->n + 1) + size_t(h->n_disp) * h->nL2 + size_t(h->nb) * h->nL * h->nL +
+                            h->n) +
+         sizeof(double) * h->n + sizeof(int) * 2 * h->n;
+}
+
+struct KkrWs {
+  double2* T;
+  double2* Dk;
+  double2* part;
+  int* status;
+  size_t bytes;
+};
+
+KkrWs carve(const must_kkr* h, int items, char* base) {
+  KkrWs w;
+  size_t off = 0;
+  auto take = [&](size_t b) { char* p = base ? base + off : nullptr; off += a256(b); return p; };
+  w.T = reinterpret_cast<double2*>(take(sizeof(double2) * size_t(items) * h->n_pts * h->nL2));
+  w.Dk = reinterpret_cast<double2*>(take(sizeof(double2) * size_t(items) * h->n_kpts * h->n_disp * h->nL2));
+  w.part = reinterpret_cast<double2*>(take(sizeof(double2) * size_t(items) * h->n_kg * h->nb * h->nL * h->nL));
+  w.status = reinterpret_cast<int*>(take(sizeof(int) * size_t(items)));
+  w.bytes = off;
+  return w;
+}
+
+size_t staging_bytes(const must_kkr* h, int items) {
+  return a256(sizeof(double2) * size_t(items)) + a256(sizeof(double2) * size_t(items) * h->nb * (h->lmax + 1)) +
+         a256(sizeof(double2) * size_t(items) * h->nb * h->nL * h->nL) + a256(sizeof(int) * size_t(items));
+}
+
+}  // namespace
+
+extern "C" must_status must_kkr_build(const double* lattice, const double* basis, int32_t n_basis, int32_t lmax,
+                                      int32_t n_k, double eta, void* stream, must_kkr** out) {
+  if (!out) { must_set_error("must_kkr_build: out is NULL"); return MUST_EINVAL; }
+  *out = nullptr;
+  if (!lattice || !basis || n_basis < 1 || lmax < 0 || lmax > 4 || n_k < 1 || n_k > 64 || !(eta >= 0.0)) {
+    must_set_error("must_kkr_build: bad argument (lattice/basis NULL, n_basis < 1, lmax outside 0..4, n_k outside "
+                   "1..64 or eta < 0)");
+    return MUST_EINVAL;
+  }
+  const int nL = (lmax + 1) * (lmax + 1);
+  if (n_basis * nL > KKR_MAX_N) {
+    must_set_error("must_kkr_build: order n_basis (lmax+1)^2 = %d exceeds %d", n_basis * nL, KKR_MAX_N);
+    return MUST_EINVAL;
+  }
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(lattice[i])) { must_set_error("must_kkr_build: non-finite lattice"); return MUST_EINVAL; }
+  for (int i = 0; i < 3 * n_basis; ++i)
+    if (!std::isfinite(basis[i])) { must_set_error("must_kkr_build: non-finite basis"); return MUST_EINVAL; }
+  double A[3][3], B[3][3], C[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) A[i][j] = lattice[3 * i + j];
+  auto cross = [](const double* u, const double* v, double* w) {
+    w[0] = u[1] * v[2] - u[2] * v[1];
+    w[1] = u[2] * v[0] - u[0] * v[2];
+    w[2] = u[0] * v[1] - u[1] * v[0];
+  };
+  cross(A[1], A[2], C[0]);
+  cross(A[2], A[0], C[1]);
+  cross(A[0], A[1], C[2]);
+  const double vol = dot3(A[0], C[0]);
+  const double scale = norm3(A[0]) * norm3(A[1]) * norm3(A[2]);
+  if (!(std::fabs(vol) > 1e-8 * scale)) { must_set_error("must_kkr_build: degenerate lattice"); return MUST_EINVAL; }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) B[i][j] = 2.0 * kPi * C[i][j] / vol;
+  const double omega = std::fabs(vol);
+  // distinct basis sites modulo the lattice
+  for (int s = 0; s < n_basis; ++s)
+    for (int t = s + 1; t < n_basis; ++t) {
+      double f[3];
+      for (int i = 0; i < 3; ++i) {
+        const double x[3] = {basis[3 * s] - basis[3 * t], basis[3 * s + 1] - basis[3 * t + 1],
+                             basis[3 * s + 2] - basis[3 * t + 2]};
+        f[i] = dot3(x, B[i]) / (2.0 * kPi);
+      }
+      if (std::fabs(f[0] - std::round(f[0])) < 1e-9 && std::fabs(f[1] - std::round(f[1])) < 1e-9 &&
+          std::fabs(f[2] - std::round(f[2])) < 1e-9) {
+        must_set_error("must_kkr_build: basis sites %d and %d coincide modulo the lattice", s, t);
+        return MUST_EINVAL;
+      }
+    }
+  if (eta == 0.0) eta = 4.0 * kPi / std::pow(omega, 2.0 / 3.0);   // balances the two sums
+  const int l2max = 2 * lmax, nL2 = (l2max + 1) * (l2max + 1);
+  // distinct displacements, 0 first
+  std::vector<double> disp = {0.0, 0.0, 0.0};
+  std::vector<int> pair_disp(size_t(n_basis) * n_basis);
+  for (int s = 0; s < n_basis; ++s)
+    for (int t = 0; t < n_basis; ++t) {
+      const double x[3] = {basis[3 * s] - basis[3 * t], basis[3 * s + 1] - basis[3 * t + 1],
+                           basis[3 * s + 2] - basis[3 * t + 2]};
+      int found = -1;
+      for (size_t d = 0; d < disp.size() / 3; ++d)
+        if (disp[3 * d] == x[0] && disp[3 * d + 1] == x[1] && disp[3 * d + 2] == x[2]) { found = int(d); break; }
+      if (found < 0) {
+        found = int(disp.size() / 3);
+        disp.insert(disp.end(), x, x + 3);
+      }
+      pair_disp[size_t(s) * n_basis + t] = found;
+    }
+  const int n_disp = int(disp.size() / 3);
+  if (n_disp > KKR_MAX_DISP) {
+    must_set_error("must_kkr_build: %d distinct site displacements exceed %d", n_disp, KKR_MAX_DISP);
+    return MUST_EINVAL;
+  }
+  // Gamma-centred mesh, folded to m_i in (-n_k/2, n_k/2]
+  std::vector<double> kpts;
+  double kmax = 0.0;
+  for (int m1 = 0; m1 < n_k; ++m1)
+    for (int m2 = 0; m2 < n_k; ++m2)
+      for (int m3 = 0; m3 < n_k; ++m3) {
+        const int f1 = (2 * m1 > n_k) ? m1 - n_k : m1, f2 = (2 * m2 > n_k) ? m2 - n_k : m2,
+                  f3 = (2 * m3 > n_k) ? m3 - n_k : m3;
+        double k[3];
+        for (int d = 0; d < 3; ++d) k[d] = (f1 * B[0][d] + f2 * B[1][d] + f3 * B[2][d]) / n_k;
+        kmax = std::max(kmax, norm3(k));
+        kpts.insert(kpts.end(), k, k + 3);
+      }
+  const int n_kpts = n_k * n_k * n_k;
+  // reciprocal vectors: |k + K|^2 <= eta cut + E_cap for each k
+  const double qmax = std::sqrt(eta * KKR_CUT + KKR_ECAP);
+  std::vector<double> Kv;
+  const double zero[3] = {0.0, 0.0, 0.0};
+  points_within(B, A, zero, qmax + kmax, Kv);
+  const int n_K = int(Kv.size() / 3);
+  std::vector<int> kK_start(n_kpts + 1, 0), kK_idx;
+  for (int ik = 0; ik < n_kpts; ++ik) {
+    kK_start[ik] = int(kK_idx.size());
+    const double* k = &kpts[3 * ik];
+    for (int j = 0; j < n_K; ++j) {
+      const double q[3] = {k[0] + Kv[3 * j], k[1] + Kv[3 * j + 1], k[2] + Kv[3 * j + 2]};
+      if (dot3(q, q) <= qmax * qmax) kK_idx.push_back(j);
+    }
+  }
+  kK_start[n_kpts] = int(kK_idx.size());
+  // real-space points of each displacement: 0 < |x - R| <= rho_max
+  const double rho_max = std::sqrt(4.0 * (KKR_CUT + KKR_ECAP / eta) / eta);
+  std::vector<int> pt_start(n_disp + 1, 0);
+  std::vector<double> pt_R, pt_rho, pts;
+  for (int d = 0; d < n_disp; ++d) {
+    pt_start[d] = int(pt_R.size() / 3);
+    const double* x = &disp[3 * d];
+    const double mx[3] = {-x[0], -x[1], -x[2]};
+    points_within(A, B, mx, rho_max, pts);
+    for (size_t p = 0; p < pts.size(); p += 3) {
+      const double rho[3] = {x[0] - pts[p], x[1] - pts[p + 1], x[2] - pts[p + 2]};
+      const double r = norm3(rho);
+      if (r < 1e-10) continue;
+      pt_R.insert(pt_R.end(), pts.begin() + p, pts.begin() + p + 3);
+      pt_rho.push_back(rho[0]);
+      pt_rho.push_back(rho[1]);
+      pt_rho.push_back(rho[2]);
+      pt_rho.push_back(r);
+    }
+  }
+  const int n_pts = int(pt_R.size() / 3);
+  pt_start[n_disp] = n_pts;
+  std::vector<double> lu, lw;
+  quadrature_u(lu, lw);
+  if (int(lu.size()) != KKR_QUAD) { must_set_error("must_kkr_build: quadrature size"); return MUST_ECUDA; }
+  std::vector<int> gs, gl;
+  std::vector<double> gc;
+  must_gaunt_csr(lmax, gs, gl, gc);
+
+  must_kkr* h = new must_kkr();
+  std::memset(h, 0, sizeof(*h));
+  h->nb = n_basis; h->lmax = lmax; h->nL = nL; h->l2max = l2max; h->nL2 = nL2; h->n = n_basis * nL;
+  h->n_k = n_k; h->n_kpts = n_kpts; h->n_disp = n_disp; h->n_pts = n_pts; h->n_K = n_K;
+  h->n_kK = int(kK_idx.size()); h->n_kg = (n_kpts + KKR_KG - 1) / KKR_KG;
+  h->eta = eta; h->omega = omega;
+  cudaGetDevice(&h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void** dst, const void* src, size_t bytes) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  up(reinterpret_cast<void**>(&h->d_kpts), kpts.data(), sizeof(double) * kpts.size());
+  up(reinterpret_cast<void**>(&h->d_K), Kv.data(), sizeof(double) * Kv.size());
+  up(reinterpret_cast<void**>(&h->d_kK_start), kK_start.data(), sizeof(int) * kK_start.size());
+  up(reinterpret_cast<void**>(&h->d_kK_idx), kK_idx.data(), sizeof(int) * kK_idx.size());
+  up(reinterpret_cast<void**>(&h->d_disp), disp.data(), sizeof(double) * disp.size());
+  up(reinterpret_cast<void**>(&h->d_pair_disp), pair_disp.data(), sizeof(int) * pair_disp.size());
+  up(reinterpret_cast<void**>(&h->d_pt_start), pt_start.data(), sizeof(int) * pt_start.size());
+  up(reinterpret_cast<void**>(&h->d_pt_R), pt_R.data(), sizeof(double) * pt_R.size());
+  up(reinterpret_cast<void**>(&h->d_pt_rho), pt_rho.data(), sizeof(double) * pt_rho.size());
+  up(reinterpret_cast<void**>(&h->d_quad_u), lu.data(), sizeof(double) * lu.size());
+  up(reinterpret_cast<void**>(&h->d_quad_w), lw.data(), sizeof(double) * lw.size());
+  up(reinterpret_cast<void**>(&h->d_g_start), gs.data(), sizeof(int) * gs.size());
+  up(reinterpret_cast<void**>(&h->d_g_L2), gl.data(), sizeof(int) * gl.size());
+  up(reinterpret_cast<void**>(&h->d_g_c), gc.data(), sizeof(double) * gc.size());
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    // the largest dynamic shared memory any handle can need (a handle built
+    // later must not lower the limit an earlier one relies on)
+    const size_t rs = sizeof(double2) * (size_t(KKR_KCHUNK) * KKR_MAX_NL2 + size_t(KKR_MAX_DISP) * KKR_KCHUNK) +
+                      sizeof(double) * 3 * KKR_KCHUNK;
+    const size_t is = sizeof(double2) * (size_t(KKR_MAX_N) * (KKR_MAX_N + 1) + size_t(KKR_MAX_DISP) * KKR_MAX_NL2 +
+                                         size_t(KKR_MAX_N) * 25 + KKR_MAX_N) +
+                      sizeof(double) * KKR_MAX_N + sizeof(int) * 2 * KKR_MAX_N;
+    const size_t ss = sizeof(double2) * (size_t(KKR_RCHUNK) * KKR_MAX_NL2 + size_t(KKR_KB) * KKR_RCHUNK);
+    if (recip_smem(h) > rs || invert_smem(h) > is || realsum_smem(h) > ss) {
+      must_set_error("must_kkr_build: shared-memory bound violated");
+      must_kkr_free(h);
+      return MUST_EINVAL;
+    }
+    e = cudaFuncSetAttribute(kkr_recip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rs));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kkr_invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(is));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kkr_realsum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ss));
+  }
+  if (e != cudaSuccess) {
+    must_set_error("must_kkr_build: %s", cudaGetErrorString(e));
+    const must_status s = (e == cudaErrorMemoryAllocation) ? MUST_ENOMEM : MUST_ECUDA;
+    must_kkr_free(h);
+    return s;
+  }
+  *out = h;
+  return MUST_OK;
+}
+
+extern "C" void must_kkr_free(must_kkr* h) {
+  if (!h) return;
+  void* ptrs[] = {h->d_kpts, h->d_K, h->d_kK_start, h->d_kK_idx, h->d_disp, h->d_pair_disp, h->d_pt_start,
+                  h->d_pt_R, h->d_pt_rho, h->d_quad_u, h->d_quad_w, h->d_g_start, h->d_g_L2, h->d_g_c};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete h;
+}
+
+extern "C" must_status must_kkr_info(const must_kkr* h, int32_t* info) {
+  if (!h || !info) { must_set_error("must_kkr_info: NULL argument"); return MUST_EINVAL; }
+  info[0] = h->n;
+  info[1] = h->n_kpts;
+  info[2] = h->n_disp;
+  info[3] = h->n_pts;
+  info[4] = h->n_kK;
+  info[5] = h->n_kg;
+  return MUST_OK;
+}
+
+extern "C" double must_kkr_eta(const must_kkr* h) { return h ? h->eta : 0.0; }
+
+extern "C" size_t must_kkr_workspace_bytes(const must_kkr* h, int32_t n_items) {
+  if (!h || n_items < 1) return 0;
+  return carve(h, n_items, nullptr).bytes + staging_bytes(h, n_items) + 256;
+}
+
+extern "C" must_status must_kkr_tau(const must_kkr* h, int32_t n_items, const double* E, const double* tinv,
+                                    void* workspace, size_t workspace_bytes, double* tau, int32_t* status,
+                                    void* stream) {
+  if (!h || n_items < 0 || (n_items > 0 && (!E || !tinv || !tau || !workspace))) {
+    must_set_error("must_kkr_tau: bad argument");
+    return MUST_EINVAL;
+  }
+  if (n_items == 0) return MUST_OK;
+  if (workspace_bytes < must_kkr_workspace_bytes(h, n_items)) {
+    must_set_error("must_kkr_tau: workspace too small: need %zu bytes", must_kkr_workspace_bytes(h, n_items));
+    return MUST_ENOMEM;
+  }
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) {
+    must_set_error("must_kkr_tau: handle built on device %d, current device is %d", h->device, dev);
+    return MUST_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~uintptr_t(255));
+  KkrWs w = carve(h, n_items, base);
+  char* stage = base + w.bytes;
+  const size_t bE = sizeof(double2) * n_items, bT = sizeof(double2) * size_t(n_items) * h->nb * (h->lmax + 1);
+  const size_t bTau = sizeof(double2) * size_t(n_items) * h->nb * h->nL * h->nL, bS = sizeof(int) * n_items;
+  const double2* Ed = reinterpret_cast<const double2*>(E);
+  const double2* Td = reinterpret_cast<const double2*>(tinv);
+  double2* taud = reinterpret_cast<double2*>(tau);
+  int* std_ = status;
+  const bool hostE = !must_is_device_ptr(E), hostT = !must_is_device_ptr(tinv), hostTau = !must_is_device_ptr(tau);
+  const bool hostS = status && !must_is_device_ptr(status);
+  cudaError_t e = cudaSuccess;
+  if (hostE) {
+    e = cudaMemcpyAsync(stage, E, bE, cudaMemcpyHostToDevice, st);
+    Ed = reinterpret_cast<const double2*>(stage);
+  }
+  stage += a256(bE);
+  if (e == cudaSuccess && hostT) {
+    e = cudaMemcpyAsync(stage, tinv, bT, cudaMemcpyHostToDevice, st);
+    Td = reinterpret_cast<const double2*>(stage);
+  }
+  stage += a256(bT);
+  if (hostTau) taud = reinterpret_cast<double2*>(stage);
+  stage += a256(bTau);
+  if (hostS) std_ = reinterpret_cast<int*>(stage);
+  if (e != cudaSuccess) { must_set_error("must_kkr_tau: %s", cudaGetErrorString(e)); return MUST_ECUDA; }
+
+  const KkrDev K = dev_view(h);
+  kkr_status_init_kernel<<<(n_items + 255) / 256, 256, 0, st>>>(n_items, w.status);
+  prof_launched(PH_OTHER, 1);
+  {
+    ProfScope ps(PH_KKR_TERMS, st);
+    dim3 g0((h->n_pts + 127) / 128, n_items);
+    kkr_real_terms_kernel<<<g0, 128, 0, st>>>(K, n_items, Ed, w.T, w.status);
+    prof_launched(PH_KKR_TERMS, 1, n_items);
+  }
+  {
+    ProfScope ps(PH_KKR_RECIP, st);
+    dim3 g1(h->n_kpts, n_items);
+    kkr_recip_kernel<<<g1, RECIP_THREADS, recip_smem(h), st>>>(K, n_items, Ed, w.Dk);
+    prof_launched(PH_KKR_RECIP, 1, n_items);
+  }
+  {
+    ProfScope ps(PH_KKR_REALSUM, st);
+    dim3 g2((h->n_kpts + KKR_KB - 1) / KKR_KB, h->n_disp, n_items);
+    kkr_realsum_kernel<<<g2, RSUM_THREADS, realsum_smem(h), st>>>(K, n_items, w.T, w.Dk);
+    prof_launched(PH_KKR_REALSUM, 1, n_items);
+  }
+  {
+    ProfScope ps(PH_KKR_INVERT, st);
+    dim3 g3(h->n_kg, n_items);
+    kkr_invert_kernel<<<g3, INV_THREADS, invert_smem(h), st>>>(K, n_items, Ed, Td, w.Dk, w.part, w.status);
+    const int tot = n_items * h->nb * h->nL * h->nL;
+    kkr_bz_sum_kernel<<<(tot + 255) / 256, 256, 0, st>>>(K, n_items, w.part, taud, w.status);
+    prof_launched(PH_KKR_INVERT, 2, n_items);
+  }
+  if (std_) {
+    kkr_status_out_kernel<<<(n_items + 255) / 256, 256, 0, st>>>(n_items, w.status, std_);
+    prof_launched(PH_OTHER, 1);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess && hostTau) e = cudaMemcpyAsync(tau, taud, bTau, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && hostS) e = cudaMemcpyAsync(status, std_, bS, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && (hostTau || hostS)) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { must_set_error("must_kkr_tau: %s", cudaGetErrorString(e)); return MUST_ECUDA; }
+  return MUST_OK;
+}

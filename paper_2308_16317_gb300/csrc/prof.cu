@@ -25,7 +25,8 @@ long long g_phase_items[PH_COUNT] = {0};
 unsigned long long* g_dwork = nullptr;   // device counters of items processed (data-dependent phases)
 
 const char* kNames[PH_COUNT] = {"assemble", "panel", "row_swap", "trsm", "pack", "trailing_update",
-                                "schur_inverse", "residual", "correction", "other"};
+                                "schur_inverse", "residual", "correction", "other", "kkr_real_terms",
+                                "kkr_recip", "kkr_realsum", "kkr_invert"};
 
 cudaEvent_t take_event() {
   if (!g_pool.empty()) {

@@ -13,6 +13,10 @@ enum MustPhase {
   PH_RESIDUAL,
   PH_CORRECT,
   PH_OTHER,
+  PH_KKR_TERMS,    // full KKR: k-independent real-space Ewald terms
+  PH_KKR_RECIP,    // full KKR: reciprocal-space Ewald sums
+  PH_KKR_REALSUM,  // full KKR: real-space Ewald sums
+  PH_KKR_INVERT,   // full KKR: M(k) assembly, inversion, Brillouin-zone sum
   PH_COUNT
 };
 

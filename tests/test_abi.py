@@ -190,3 +190,24 @@ def test_tuning_knobs_validate_and_round_trip():
             B.must_tune_set(knob, old)
     with pytest.raises(B.MustError):
         B.must_tune_set(99, 1)
+
+
+def test_kkr_build_rejects_bad_arguments_on_the_host():
+    """must_kkr_build validates its arguments before any CUDA call."""
+    import numpy as np
+    from paper_2308_16317_gb300 import binding as B
+    from paper_2308_16317_gb300 import workload as wl
+    c = wl.l12_crystal()
+    bad = [
+        (c.lattice, np.vstack([c.basis, c.basis[:1] + c.lattice[0]]), 1, 4),   # sites coincide modulo the lattice
+        (c.lattice, c.basis, 4, 4),                                            # 4 x 25 > 64
+        (np.zeros((3, 3)), c.basis, 1, 4),                                     # degenerate lattice
+        (c.lattice, c.basis, 3, 0),                                            # n_k < 1
+        (c.lattice, c.basis, 5, 4),                                            # lmax > 4
+    ]
+    for lat, bas, lmax, nk in bad:
+        with pytest.raises(B.MustError) as ei:
+            B.must_kkr_build(lat, bas, lmax, nk)
+        assert ei.value.code == 1
+    with pytest.raises(B.MustError):
+        B.must_kkr_build(c.lattice, c.basis, 3, 4, eta=-1.0)
