@@ -1101,7 +1101,8 @@ def run_kkr(args):
         err = np.linalg.norm(got - ref, axis=(-2, -1)) / np.linalg.norm(ref, axis=(-2, -1))
         results[c.name] = {
             "value": items / (ms / 1e3), "unit": "tau solves/s (all sites of the cell per (E, spin))",
-            "ms_per_step": ms, "items_per_step": items, "n": h.n, "k_points": h.n_kpts,
+            "ms_per_step": ms, "items_per_step": items, "n": h.n, "k_points": h.n_mesh,
+            "k_points_evaluated": h.n_kpts,
             "inversions_per_s": items * h.n_kpts / (ms / 1e3),
             "gpu_launches": launches, "kernels": kern,
             "roofline": {"kernel_phase": dom, "bound": "alu", "unit": "TFLOP/s",

@@ -439,8 +439,11 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * Asynchronous on `stream` for device outputs; returns after the final copy
  * for host outputs.  Errors: MUST_EINVAL, MUST_ENOMEM, MUST_ECUDA.
  *
- * must_kkr_info: info[6] = {M(k) order, k points, distinct displacements,
- * real-space points, (k, K) reciprocal terms, k groups}; must_kkr_eta: the
+ * must_kkr_info: info[7] = {M(k) order, k points evaluated, distinct
+ * displacements, real-space points, (k, K) reciprocal terms, k groups, mesh
+ * points n_k^3}.  Only one point of each pair {k, -k} of the mesh is
+ * evaluated: M(-k) = M(k)^T (the reciprocity G_{LL'}(rho) = G_{L'L}(-rho)), so
+ * its diagonal blocks enter the average transposed.  must_kkr_eta: the
  * splitting parameter in use.
  */
 typedef struct must_kkr must_kkr;

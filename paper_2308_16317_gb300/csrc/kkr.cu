@@ -40,6 +40,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -70,41 +71,51 @@ __device__ __forceinline__ int l_of_L(int L) {
   return l;
 }
 
-// Real solid harmonics YS_L(v) = |v|^l Y_L(v^), L < (lmax+1)^2, same basis as
-// the library's Y_L (no Condon-Shortley phase), evaluated as polynomials so
-// that v = 0 needs no special case:
-//   YS_lm = N_lm {sqrt2 Re (x+iy)^m | 1 | sqrt2 Im (x+iy)^|m|} q_l^|m|(z, r^2),
+// Normalisation of the real harmonics, c_ynorm[l*l + l + m] for m >= 0:
+// sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), times sqrt2 for m > 0 (set by must_kkr_build).
+__constant__ double c_ynorm[KKR_MAX_NL2];
+// 1/n for n = 0..KKR_MAX_L2 (entry 0 unused): the recurrence below divides by l - m
+__constant__ double c_recip[KKR_MAX_L2 + 1];
+
+// One column m >= 0 of the real solid harmonics YS_L(v) = |v|^l Y_L(v^)
+// (same basis as the library's Y_L, no Condon-Shortley phase), l = m..lmax,
+// evaluated as polynomials so that v = 0 needs no special case:
+//   YS_lm = c_ynorm {Re (x+iy)^m | Im (x+iy)^|m|} q_l^m(z, r^2),
 //   q_m^m = (2m-1)!!, q_{m+1}^m = (2m+1) z q_m^m,
 //   q_l^m = [(2l-1) z q_{l-1}^m - (l+m-1) r^2 q_{l-2}^m] / (l-m).
-__device__ void solid_harmonics(int lmax, double x, double y, double z, double* out) {
-  const double r2 = x * x + y * y + z * z;
-  double cr = 1.0, ci = 0.0;     // (x + i y)^m
-  double dfact = 1.0;            // (2m-1)!!
-  for (int m = 0; m <= lmax; ++m) {
-    if (m > 0) {
-      const double nr = cr * x - ci * y, ni = cr * y + ci * x;
-      cr = nr; ci = ni;
-      dfact *= (2.0 * m - 1.0);
-    }
-    double qm2 = 0.0, qm1 = 0.0;
-    for (int l = m; l <= lmax; ++l) {
-      double q;
-      if (l == m) q = dfact;
-      else if (l == m + 1) q = (2.0 * m + 1.0) * z * dfact;
-      else q = ((2.0 * l - 1.0) * z * qm1 - (l + m - 1.0) * r2 * qm2) / double(l - m);
-      qm2 = qm1;
-      qm1 = q;
-      double ratio = 1.0;
-      for (int k = l - m + 1; k <= l + m; ++k) ratio /= double(k);
-      const double N = sqrt((2.0 * l + 1.0) / (4.0 * kPi) * ratio);
-      if (m == 0) {
-        out[l * l + l] = N * q;
-      } else {
-        out[l * l + l + m] = 1.41421356237309504880 * N * q * cr;
-        out[l * l + l - m] = 1.41421356237309504880 * N * q * ci;
-      }
+// emit(l, L, value) receives YS_L for L = l*l + l + m and l*l + l - m.
+template <class Emit>
+__device__ __forceinline__ void solid_harmonic_column(int lmax, int m, double x, double y, double z, double r2,
+                                                      Emit emit) {
+  double cr = 1.0, ci = 0.0, dfact = 1.0;   // (x + i y)^m, (2m-1)!!
+  for (int p = 1; p <= m; ++p) {
+    const double nr = cr * x - ci * y, ni = cr * y + ci * x;
+    cr = nr;
+    ci = ni;
+    dfact *= (2.0 * p - 1.0);
+  }
+  double qm2 = 0.0, qm1 = 0.0;
+  for (int l = m; l <= lmax; ++l) {
+    double q;
+    if (l == m) q = dfact;
+    else if (l == m + 1) q = (2.0 * m + 1.0) * z * dfact;
+    else q = ((2.0 * l - 1.0) * z * qm1 - (l + m - 1.0) * r2 * qm2) * c_recip[l - m];
+    qm2 = qm1;
+    qm1 = q;
+    const double nq = c_ynorm[l * l + l + m] * q;
+    if (m == 0) {
+      emit(l, l * l + l, nq);
+    } else {
+      emit(l, l * l + l + m, nq * cr);
+      emit(l, l * l + l - m, nq * ci);
     }
   }
+}
+
+__device__ void solid_harmonics(int lmax, double x, double y, double z, double* out) {
+  const double r2 = x * x + y * y + z * z;
+  for (int m = 0; m <= lmax; ++m)
+    solid_harmonic_column(lmax, m, x, y, z, r2, [&](int, int L, double v) { out[L] = v; });
 }
 
 __device__ __forceinline__ cd cexp_d(cd z) {
@@ -126,8 +137,10 @@ __device__ __forceinline__ cd ipow_d(int l) {
 
 struct KkrDev {
   int nb, lmax, nL, l2max, nL2, n, n_kpts, n_disp, n_pts, n_kg;
+  int n_mesh;             // n_k^3: the mesh the average is taken over
   double eta, omega;
-  const double* kpts;     // [n_kpts][3]
+  const double* kpts;     // [n_kpts][3]: one point of each pair {k, -k} of the mesh
+  const int* kpair;       // [n_kpts]: 1 if -k is a different mesh point (counted as the transpose)
   const double* Kvec;     // [nK][3]
   const int* kK_start;    // [n_kpts + 1]
   const int* kK_idx;      // reciprocal vectors of each k with |k + K|^2 <= qmax^2
@@ -156,12 +169,12 @@ __global__ void kkr_real_terms_kernel(KkrDev K, int items, const double2* __rest
     if (pt == 0) atomicMax(status + it, int(MUST_EUNSUPPORTED));
   }
   const double* pr = K.pt_rho + size_t(pt) * 4;
-  const double r = pr[3], r2 = r * r;
+  const double r = pr[3], r2 = r * r, inv_r2 = 1.0 / r2;
   const double xi02 = 0.25 * K.eta;
   cd I[KKR_MAX_L2 + 1];
   for (int l = 0; l <= K.l2max; ++l) I[l] = mk(0.0, 0.0);
   for (int j = 0; j < KKR_QUAD; ++j) {
-    const double xi2 = xi02 + K.quad_u[j] / r2;
+    const double xi2 = xi02 + K.quad_u[j] * inv_r2;
     const double inv_xi2 = 1.0 / xi2;
     const cd g = K.quad_w[j] * cexp_d(mk(0.25 * e.x * inv_xi2, 0.25 * e.y * inv_xi2));
     double p = rsqrt(xi2);               // xi^{2l-1}, l = 0
@@ -188,80 +201,117 @@ __global__ void kkr_real_terms_kernel(KkrDev K, int items, const double2* __rest
 // -------------------------------------------------------------------------
 // A_L + C_L for every displacement, one CTA per (k, item):
 //   Dk[item][k][d][L] = (4 pi/Omega) i^l sum_K e^{iq.x_d} YS_L(q) e^{(E-q^2)/eta}/(q^2-E) + C_L
+// Per chunk of KKR_KCHUNK reciprocal vectors: 64 threads form q and the weight,
+// all threads form the harmonics (four m columns per vector) and the phases,
+// then each thread accumulates its outputs (d, L) -- over every vector of the
+// chunk, or, when the outputs are fewer than the threads, over one of G
+// interleaved subsets, the G partial sums being added in order at the end.
 constexpr int RECIP_THREADS = 256;
 constexpr int RECIP_OUT = (KKR_MAX_DISP * KKR_MAX_NL2 + RECIP_THREADS - 1) / RECIP_THREADS;
+constexpr int RECIP_MPARTS = RECIP_THREADS / KKR_KCHUNK;
 
 __global__ void __launch_bounds__(RECIP_THREADS) kkr_recip_kernel(KkrDev K, int items, const double2* __restrict__ E,
                                                                   double2* __restrict__ Dk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* F = reinterpret_cast<double2*>(smem_raw);                 // [KCHUNK][nL2]
-  double2* P = F + KKR_KCHUNK * K.nL2;                                 // [n_disp][KCHUNK]
-  double* qv = reinterpret_cast<double*>(P + K.n_disp * KKR_KCHUNK);  // [KCHUNK][3]
+  double2* F = reinterpret_cast<double2*>(smem_raw);                 // [KCHUNK][nL2], >= RECIP_THREADS
+  double2* P = F + max(KKR_KCHUNK * K.nL2, RECIP_THREADS);            // [n_disp][KCHUNK]
+  double2* wv = P + K.n_disp * KKR_KCHUNK;                             // [KCHUNK]
+  double* qv = reinterpret_cast<double*>(wv + KKR_KCHUNK);            // [KCHUNK][4]: q, |q|^2
   const int ik = blockIdx.x, it = blockIdx.y, tid = threadIdx.x;
   const cd e = mk(E[it].x, E[it].y);
   const double* kp = K.kpts + size_t(ik) * 3;
   const int k0 = K.kK_start[ik], k1 = K.kK_start[ik + 1];
   const int n_out = K.n_disp * K.nL2;
+  const int G = (n_out <= RECIP_THREADS) ? RECIP_THREADS / n_out : 1;
   cd acc[RECIP_OUT];
 #pragma unroll
   for (int j = 0; j < RECIP_OUT; ++j) acc[j] = mk(0.0, 0.0);
-  const double wpre = 4.0 * kPi / K.omega;
+  const double inv_eta = 1.0 / K.eta;
+  // (4 pi / Omega) e^{E/eta}; each term then needs the real e^{-q^2/eta}
+  const cd wpre = (4.0 * kPi / K.omega) * cexp_d(mk(e.x * inv_eta, e.y * inv_eta));
   for (int c0 = k0; c0 < k1; c0 += KKR_KCHUNK) {
     const int cn = min(KKR_KCHUNK, k1 - c0);
     if (tid < KKR_KCHUNK) {
-      double2* f = F + tid * K.nL2;
+      double q0 = 0.0, q1 = 0.0, q2v = 0.0, qq = 0.0;
+      cd w = mk(0.0, 0.0);
       if (tid < cn) {
         const double* Kv = K.Kvec + size_t(K.kK_idx[c0 + tid]) * 3;
-        const double q0 = kp[0] + Kv[0], q1 = kp[1] + Kv[1], q2v = kp[2] + Kv[2];
-        const double qq = q0 * q0 + q1 * q1 + q2v * q2v;
-        qv[tid * 3] = q0; qv[tid * 3 + 1] = q1; qv[tid * 3 + 2] = q2v;
-        // w = wpre e^{(E - q^2)/eta} / (q^2 - E)
-        const cd ex = cexp_d(mk((e.x - qq) / K.eta, e.y / K.eta));
-        const cd w = wpre * (ex * cinv(mk(qq - e.x, -e.y)));
-        double Y[KKR_MAX_NL2];
-        solid_harmonics(K.l2max, q0, q1, q2v, Y);
-        for (int l = 0; l <= K.l2max; ++l) {
-          const cd wl = ipow_d(l) * w;
-          for (int m = -l; m <= l; ++m) {
-            const int L = l * l + l + m;
-            f[L] = make_double2(wl.x * Y[L], wl.y * Y[L]);
-          }
-        }
-      } else {
-        for (int L = 0; L < K.nL2; ++L) f[L] = make_double2(0.0, 0.0);
-        qv[tid * 3] = 0.0; qv[tid * 3 + 1] = 0.0; qv[tid * 3 + 2] = 0.0;
+        q0 = kp[0] + Kv[0]; q1 = kp[1] + Kv[1]; q2v = kp[2] + Kv[2];
+        qq = q0 * q0 + q1 * q1 + q2v * q2v;
+        // w = (4 pi / Omega) e^{(E - q^2)/eta} / (q^2 - E)
+        w = exp(-qq * inv_eta) * (wpre * cinv(mk(qq - e.x, -e.y)));
       }
+      qv[tid * 4] = q0; qv[tid * 4 + 1] = q1; qv[tid * 4 + 2] = q2v; qv[tid * 4 + 3] = qq;
+      wv[tid] = make_double2(w.x, w.y);
     }
     __syncthreads();
+    {
+      const int j = tid % KKR_KCHUNK, part = tid / KKR_KCHUNK;
+      const double q0 = qv[j * 4], q1 = qv[j * 4 + 1], q2v = qv[j * 4 + 2], qq = qv[j * 4 + 3];
+      const cd w = mk(wv[j].x, wv[j].y);
+      double2* f = F + j * K.nL2;
+      for (int m = part; m <= K.l2max; m += RECIP_MPARTS)
+        solid_harmonic_column(K.l2max, m, q0, q1, q2v, qq, [&](int l, int L, double v) {
+          const cd wl = ipow_d(l) * w;
+          f[L] = make_double2(wl.x * v, wl.y * v);
+        });
+    }
     for (int p = tid; p < K.n_disp * KKR_KCHUNK; p += RECIP_THREADS) {
       const int d = p / KKR_KCHUNK, j = p % KKR_KCHUNK;
-      const double* x = K.disp + d * 3;
-      double s, c;
-      sincos(qv[j * 3] * x[0] + qv[j * 3 + 1] * x[1] + qv[j * 3 + 2] * x[2], &s, &c);
+      double s = 0.0, c = 1.0;              // displacement 0 is x = 0
+      if (d > 0) {
+        const double* x = K.disp + d * 3;
+        sincos(qv[j * 4] * x[0] + qv[j * 4 + 1] * x[1] + qv[j * 4 + 2] * x[2], &s, &c);
+      }
       P[d * KKR_KCHUNK + j] = make_double2(c, s);
     }
     __syncthreads();
-#pragma unroll
-    for (int jj = 0; jj < RECIP_OUT; ++jj) {
-      const int o = tid + jj * RECIP_THREADS;
-      if (o < n_out) {
+    if (G > 1) {
+      if (tid < G * n_out) {
+        const int o = tid % n_out, g = tid / n_out;
         const int d = o / K.nL2, L = o % K.nL2;
-        cd a = acc[jj];
-        for (int j = 0; j < cn; ++j) {
+        cd a = acc[0];
+        for (int j = g; j < cn; j += G) {
           const double2 pp = P[d * KKR_KCHUNK + j], ff = F[j * K.nL2 + L];
           a.x = fma(pp.x, ff.x, fma(-pp.y, ff.y, a.x));
           a.y = fma(pp.x, ff.y, fma(pp.y, ff.x, a.y));
         }
-        acc[jj] = a;
+        acc[0] = a;
+      }
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < RECIP_OUT; ++jj) {
+        const int o = tid + jj * RECIP_THREADS;
+        if (o < n_out) {
+          const int d = o / K.nL2, L = o % K.nL2;
+          cd a = acc[jj];
+          for (int j = 0; j < cn; ++j) {
+            const double2 pp = P[d * KKR_KCHUNK + j], ff = F[j * K.nL2 + L];
+            a.x = fma(pp.x, ff.x, fma(-pp.y, ff.y, a.x));
+            a.y = fma(pp.x, ff.y, fma(pp.y, ff.x, a.y));
+          }
+          acc[jj] = a;
+        }
       }
     }
     __syncthreads();
+  }
+  if (G > 1) {
+    // partial sums of the G subsets, added in order
+    double2* red = F;
+    if (tid < G * n_out) red[tid] = make_double2(acc[0].x, acc[0].y);
+    __syncthreads();
+    if (tid < n_out) {
+      cd a = mk(0.0, 0.0);
+      for (int g = 0; g < G; ++g) a = a + mk(red[g * n_out + tid].x, red[g * n_out + tid].y);
+      acc[0] = a;
+    }
   }
   double2* out = Dk + (size_t(it) * K.n_kpts + ik) * n_out;
 #pragma unroll
   for (int jj = 0; jj < RECIP_OUT; ++jj) {
     const int o = tid + jj * RECIP_THREADS;
-    if (o < n_out) {
+    if (o < n_out && (G == 1 || jj == 0)) {
       cd a = acc[jj];
       if (o == 0) {
         // C_0 of displacement 0 (x = 0): the R = 0 term of the reciprocal sum removed
@@ -349,24 +399,39 @@ __global__ void __launch_bounds__(RSUM_THREADS) kkr_realsum_kernel(KkrDev K, int
 // M(k) = t^{-1} - G(k) in shared memory, inverted in place; the diagonal
 // blocks of M(k)^{-1} of KKR_KG k points summed in order into
 //   part[item][group][s][L][L'].
+// NM matrices (NM = kkr_matrices_per_pass(n): 1 at n = 64, up to 8 for n <= 22)
+// are factored side by side so that small orders still fill the CTA: warp m
+// searches matrix m's pivot column, and each matrix's update is spread over
+// 256 / NM threads (column j, rows rg, rg + RG, ..., four at a time).
 constexpr int INV_THREADS = 256;
+
+__host__ __device__ inline int kkr_matrices_per_pass(int n) {
+  int nm = 8;
+  while (nm > 1 && (nm * n * n > KKR_MAX_N * KKR_MAX_N || INV_THREADS / nm < n)) nm >>= 1;
+  return nm;
+}
 
 __global__ void __launch_bounds__(INV_THREADS) kkr_invert_kernel(KkrDev K, int items, const double2* __restrict__ E,
                                                                  const double2* __restrict__ tinv,
                                                                  const double2* __restrict__ Dk,
                                                                  double2* __restrict__ part, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = K.n, ldA = n + 1;
-  double2* A = reinterpret_cast<double2*>(smem_raw);        // [n][n+1] row-major
-  double2* Ds = A + n * ldA;                                 // [n_disp][nL2]
-  double2* acc = Ds + K.n_disp * K.nL2;                      // [nb][nL][nL]
-  double2* colk = acc + K.nb * K.nL * K.nL;                  // [n]
-  double* sc = reinterpret_cast<double*>(colk + n);          // [n]
-  int* perm = reinterpret_cast<int*>(sc + n);                // [n]
-  int* sigma = perm + n;                                     // [n]
+  const int n = K.n, ldA = n + 1, nn = n * ldA;
+  const int NM = kkr_matrices_per_pass(n);
+  const int TPM = INV_THREADS / NM;                          // threads per matrix
+  const int RG = TPM / n;                                    // row groups of the update (>= 1)
+  const int nDL = K.n_disp * K.nL2;
+  double2* A = reinterpret_cast<double2*>(smem_raw);        // [NM][n][n+1] row-major
+  double2* Ds = A + NM * nn;                                 // [NM][n_disp][nL2]
+  double2* acc = Ds + NM * nDL;                              // [nb][nL][nL]
+  double2* colk = acc + K.nb * K.nL * K.nL;                  // [NM][n]
+  double2* pinv_s = colk + NM * n;                           // [NM]
+  double* sc = reinterpret_cast<double*>(pinv_s + NM);       // [NM][n]
+  int* perm = reinterpret_cast<int*>(sc + NM * n);           // [NM][n]
+  int* sigma = perm + NM * n;                                // [NM][n]
+  int* piv_s = sigma + NM * n;                               // [NM]
   __shared__ double2 fl[KKR_MAX_L2 + 1];
   __shared__ double2 ti_s[KKR_MAX_N];
-  __shared__ int piv_s;
   __shared__ int singular;
   const int g = blockIdx.x, it = blockIdx.y, tid = threadIdx.x;
   const int nL = K.nL, nb = K.nb;
@@ -387,19 +452,21 @@ __global__ void __launch_bounds__(INV_THREADS) kkr_invert_kernel(KkrDev K, int i
   if (tid == 0) singular = 0;
   __syncthreads();
   const int kbeg = g * KKR_KG, kend = min(K.n_kpts, kbeg + KKR_KG);
-  for (int ik = kbeg; ik < kend; ++ik) {
-    const double2* src = Dk + (size_t(it) * K.n_kpts + ik) * K.n_disp * K.nL2;
-    for (int q = tid; q < K.n_disp * K.nL2; q += INV_THREADS) {
-      const int L = q % K.nL2;
-      const cd v = mk(src[q].x, src[q].y) * mk(fl[l_of_L(L)].x, fl[l_of_L(L)].y);
+  for (int kb = kbeg; kb < kend; kb += NM) {
+    const int nm = min(NM, kend - kb);
+    for (int q = tid; q < nm * nDL; q += INV_THREADS) {
+      const int m = q / nDL, r = q % nDL, L = r % K.nL2;
+      const double2 v0 = Dk[(size_t(it) * K.n_kpts + kb + m) * nDL + r];
+      const double2 f = fl[l_of_L(L)];
+      const cd v = mk(v0.x, v0.y) * mk(f.x, f.y);
       Ds[q] = make_double2(v.x, v.y);
     }
     __syncthreads();
     // A = t^{-1} - G, G_{LL'} = sum_{L''} c D_{L''} (prefactors folded into Ds)
-    for (int q = tid; q < n * n; q += INV_THREADS) {
-      const int i = q / n, j = q % n;
+    for (int q = tid; q < nm * n * n; q += INV_THREADS) {
+      const int m = q / (n * n), i = (q / n) % n, j = q % n;
       const int s = i / nL, L = i % nL, t = j / nL, Lp = j % nL;
-      const double2* Dd = Ds + K.pair_disp[s * nb + t] * K.nL2;
+      const double2* Dd = Ds + m * nDL + K.pair_disp[s * nb + t] * K.nL2;
       cd gsum = mk(0.0, 0.0);
       for (int p = K.g_start[L * nL + Lp]; p < K.g_start[L * nL + Lp + 1]; ++p) {
         const double c = K.g_c[p];
@@ -409,98 +476,152 @@ __global__ void __launch_bounds__(INV_THREADS) kkr_invert_kernel(KkrDev K, int i
       }
       cd a = mk(-gsum.x, -gsum.y);
       if (i == j) a = a + mk(ti_s[i].x, ti_s[i].y);
-      A[i * ldA + j] = make_double2(a.x, a.y);
+      A[m * nn + i * ldA + j] = make_double2(a.x, a.y);
     }
     __syncthreads();
     // symmetric equilibration D A D, D = |diag A|^{-1/2}
-    if (tid < n) {
-      const double2 d = A[tid * ldA + tid];
-      const double m = sqrt(d.x * d.x + d.y * d.y);
-      sc[tid] = (m > 0.0 && isfinite(m)) ? 1.0 / sqrt(m) : 1.0;
+    for (int q = tid; q < nm * n; q += INV_THREADS) {
+      const int m = q / n, i = q % n;
+      const double2 d = A[m * nn + i * ldA + i];
+      const double mg = sqrt(d.x * d.x + d.y * d.y);
+      sc[q] = (mg > 0.0 && isfinite(mg)) ? 1.0 / sqrt(mg) : 1.0;
     }
     __syncthreads();
-    for (int q = tid; q < n * n; q += INV_THREADS) {
-      const int i = q / n, j = q % n;
-      const double f = sc[i] * sc[j];
-      double2 v = A[i * ldA + j];
-      A[i * ldA + j] = make_double2(v.x * f, v.y * f);
+    for (int q = tid; q < nm * n * n; q += INV_THREADS) {
+      const int m = q / (n * n), i = (q / n) % n, j = q % n;
+      const double f = sc[m * n + i] * sc[m * n + j];
+      double2 v = A[m * nn + i * ldA + j];
+      A[m * nn + i * ldA + j] = make_double2(v.x * f, v.y * f);
     }
     __syncthreads();
-    // Gauss-Jordan in place with partial (row) pivoting
+    // Gauss-Jordan in place with partial (row) pivoting, all nm matrices in step
     for (int k = 0; k < n; ++k) {
-      if (tid < 32) {
-        double best = -1.0;
-        int bi = k;
-        for (int i = k + tid; i < n; i += 32) {
-          const double2 v = A[i * ldA + k];
-          const double m = fabs(v.x) + fabs(v.y);
-          if (m > best) { best = m; bi = i; }
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-          const double ob = __shfl_down_sync(0xffffffffu, best, off);
-          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (tid == 0) {
-          piv_s = bi;
-          perm[k] = bi;
-          if (!(best > 0.0)) singular = 1;
+      {
+        const int w = tid >> 5, lane = tid & 31;
+        if (w < nm) {
+          const double2* Am = A + w * nn;
+          double best = -1.0;
+          int bi = k;
+          for (int i = k + lane; i < n; i += 32) {
+            const double2 v = Am[i * ldA + k];
+            const double mg = fabs(v.x) + fabs(v.y);
+            if (mg > best) { best = mg; bi = i; }
+          }
+          for (int off = 16; off > 0; off >>= 1) {
+            const double ob = __shfl_down_sync(0xffffffffu, best, off);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+          }
+          if (lane == 0) {
+            piv_s[w] = bi;
+            perm[w * n + k] = bi;
+            if (!(best > 0.0)) singular = 1;
+            // the pivot's reciprocal, formed once (read before the interchange)
+            const double2 pv = Am[bi * ldA + k];
+            const cd r = (pv.x == 0.0 && pv.y == 0.0) ? mk(0.0, 0.0) : cinv(mk(pv.x, pv.y));
+            pinv_s[w] = make_double2(r.x, r.y);
+          }
         }
       }
       __syncthreads();
-      const int p = piv_s;
-      if (p != k)
-        for (int j = tid; j < n; j += INV_THREADS) {
-          const double2 t0 = A[k * ldA + j];
-          A[k * ldA + j] = A[p * ldA + j];
-          A[p * ldA + j] = t0;
+      for (int q = tid; q < nm * n; q += INV_THREADS) {
+        const int m = q / n, j = q % n, p = piv_s[m];
+        if (p != k) {
+          double2* Am = A + m * nn;
+          const double2 t0 = Am[k * ldA + j];
+          Am[k * ldA + j] = Am[p * ldA + j];
+          Am[p * ldA + j] = t0;
         }
-      __syncthreads();
-      const double2 pv = A[k * ldA + k];
-      const cd pinv = (pv.x == 0.0 && pv.y == 0.0) ? mk(0.0, 0.0) : cinv(mk(pv.x, pv.y));
-      for (int j = tid; j < n; j += INV_THREADS) {
-        if (j == k) continue;
-        const cd v = mk(A[k * ldA + j].x, A[k * ldA + j].y) * pinv;
-        A[k * ldA + j] = make_double2(v.x, v.y);
       }
-      if (tid < n) colk[tid] = A[tid * ldA + k];
       __syncthreads();
-      for (int q = tid; q < n * n; q += INV_THREADS) {
-        const int i = q / n, j = q % n;
-        if (i == k) {
-          if (j == k) A[k * ldA + k] = make_double2(pinv.x, pinv.y);
-          continue;
+      for (int q = tid; q < nm * n; q += INV_THREADS) {
+        const int m = q / n, j = q % n;
+        double2* Am = A + m * nn;
+        if (j != k) {
+          const cd v = mk(Am[k * ldA + j].x, Am[k * ldA + j].y) * mk(pinv_s[m].x, pinv_s[m].y);
+          Am[k * ldA + j] = make_double2(v.x, v.y);
         }
-        const cd f = mk(colk[i].x, colk[i].y);
-        if (j == k) {
-          const cd v = f * pinv;
-          A[i * ldA + k] = make_double2(-v.x, -v.y);
-        } else {
-          cd a = mk(A[i * ldA + j].x, A[i * ldA + j].y);
-          const double2 rk = A[k * ldA + j];
-          cfms(a, f, mk(rk.x, rk.y));
-          A[i * ldA + j] = make_double2(a.x, a.y);
+        colk[q] = Am[j * ldA + k];
+      }
+      __syncthreads();
+      // every row i != k: A[i][j] -= colk[i] A[k][j] (j != k), A[i][k] = -colk[i] / pivot
+      {
+        const int m = tid / TPM, r = tid % TPM;
+        if (m < nm && r < RG * n) {
+          double2* Am = A + m * nn;
+          const double2* cm = colk + m * n;
+          const cd pinv = mk(pinv_s[m].x, pinv_s[m].y);
+          const int j = r % n, rg = r / n;
+          if (j == k) {
+            for (int i = rg; i < n; i += RG) {
+              if (i == k) {
+                Am[k * ldA + k] = make_double2(pinv.x, pinv.y);
+              } else {
+                const cd v = mk(cm[i].x, cm[i].y) * pinv;
+                Am[i * ldA + k] = make_double2(-v.x, -v.y);
+              }
+            }
+          } else {
+            const cd rk = mk(Am[k * ldA + j].x, Am[k * ldA + j].y);
+            int i = rg;
+            for (; i + 3 * RG < n; i += 4 * RG) {
+              double2 a[4], c[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                a[u] = Am[(i + u * RG) * ldA + j];
+                c[u] = cm[i + u * RG];
+              }
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                if (i + u * RG == k) continue;
+                cd v = mk(a[u].x, a[u].y);
+                cfms(v, mk(c[u].x, c[u].y), rk);
+                Am[(i + u * RG) * ldA + j] = make_double2(v.x, v.y);
+              }
+            }
+            for (; i < n; i += RG) {
+              if (i == k) continue;
+              cd v = mk(Am[i * ldA + j].x, Am[i * ldA + j].y);
+              cfms(v, mk(cm[i].x, cm[i].y), rk);
+              Am[i * ldA + j] = make_double2(v.x, v.y);
+            }
+          }
         }
       }
       __syncthreads();
     }
     // column j of the inverse is column sigma(j) of the in-place result
-    if (tid < n) {
-      int v = tid;
+    for (int q = tid; q < nm * n; q += INV_THREADS) {
+      const int m = q / n;
+      int v = q % n;
       for (int k = 0; k < n; ++k) {
-        const int pk = perm[k];
+        const int pk = perm[m * n + k];
         if (v == k) v = pk;
         else if (v == pk) v = k;
       }
-      sigma[tid] = v;
+      sigma[q] = v;
     }
     __syncthreads();
+    // [M(k)^{-1}]^{ss}, and for a paired point also [M(-k)^{-1}]^{ss} = ([M(k)^{-1}]^{ss})^T
+    // (M(-k) = M(k)^T by the reciprocity G_{LL'}(rho) = G_{L'L}(-rho)); k points in order
     for (int q = tid; q < nb * nL * nL; q += INV_THREADS) {
       const int s = q / (nL * nL), L = (q / nL) % nL, Lp = q % nL;
       const int i = s * nL + L, j = s * nL + Lp;
-      const double2 x = A[i * ldA + sigma[j]];
-      const double f = sc[i] * sc[j];
-      acc[q] = make_double2(acc[q].x + f * x.x, acc[q].y + f * x.y);
+      double ax = acc[q].x, ay = acc[q].y;
+      for (int m = 0; m < nm; ++m) {
+        const double2* Am = A + m * nn;
+        const int* sg = sigma + m * n;
+        const double f = sc[m * n + i] * sc[m * n + j];
+        const double2 x = Am[i * ldA + sg[j]];
+        ax += f * x.x;
+        ay += f * x.y;
+        if (K.kpair[kb + m]) {
+          const double2 y = Am[j * ldA + sg[i]];
+          ax += f * y.x;
+          ay += f * y.y;
+        }
+      }
+      acc[q] = make_double2(ax, ay);
     }
     __syncthreads();
   }
@@ -523,7 +644,7 @@ __global__ void kkr_bz_sum_kernel(KkrDev K, int items, const double2* __restrict
     sx += v.x;
     sy += v.y;
   }
-  const double w = 1.0 / double(K.n_kpts);
+  const double w = 1.0 / double(K.n_mesh);
   sx *= w;
   sy *= w;
   if (!isfinite(sx) || !isfinite(sy)) atomicMax(status + it, int(MUST_ENONFINITE));
@@ -585,9 +706,10 @@ void points_within(const double V[3][3], const double W[3][3], const double* c, 
 }  // namespace
 
 struct must_kkr {
-  int nb, lmax, nL, l2max, nL2, n, n_k, n_kpts, n_disp, n_pts, n_K, n_kK, n_kg, device;
+  int nb, lmax, nL, l2max, nL2, n, n_k, n_kpts, n_mesh, n_disp, n_pts, n_K, n_kK, n_kg, device;
   double eta, omega;
   double* d_kpts;
+  int* d_kpair;
   double* d_K;
   int* d_kK_start;
   int* d_kK_idx;
@@ -608,9 +730,9 @@ namespace {
 KkrDev dev_view(const must_kkr* h) {
   KkrDev K;
   K.nb = h->nb; K.lmax = h->lmax; K.nL = h->nL; K.l2max = h->l2max; K.nL2 = h->nL2; K.n = h->n;
-  K.n_kpts = h->n_kpts; K.n_disp = h->n_disp; K.n_pts = h->n_pts; K.n_kg = h->n_kg;
+  K.n_kpts = h->n_kpts; K.n_mesh = h->n_mesh; K.n_disp = h->n_disp; K.n_pts = h->n_pts; K.n_kg = h->n_kg;
   K.eta = h->eta; K.omega = h->omega;
-  K.kpts = h->d_kpts; K.Kvec = h->d_K; K.kK_start = h->d_kK_start; K.kK_idx = h->d_kK_idx;
+  K.kpts = h->d_kpts; K.kpair = h->d_kpair; K.Kvec = h->d_K; K.kK_start = h->d_kK_start; K.kK_idx = h->d_kK_idx;
   K.disp = h->d_disp; K.pair_disp = h->d_pair_disp; K.pt_start = h->d_pt_start; K.pt_R = h->d_pt_R;
   K.pt_rho = h->d_pt_rho; K.quad_u = h->d_quad_u; K.quad_w = h->d_quad_w;
   K.g_start = h->d_g_start; K.g_L2 = h->d_g_L2; K.g_c = h->d_g_c;
@@ -618,8 +740,9 @@ KkrDev dev_view(const must_kkr* h) {
 }
 
 size_t recip_smem(const must_kkr* h) {
-  return sizeof(double2) * (size_t(KKR_KCHUNK) * h->nL2 + size_t(h->n_disp) * KKR_KCHUNK) +
-         sizeof(double) * 3 * KKR_KCHUNK;
+  return sizeof(double2) * (std::max<size_t>(size_t(KKR_KCHUNK) * h->nL2, RECIP_THREADS) +
+                            size_t(h->n_disp) * KKR_KCHUNK + KKR_KCHUNK) +
+         sizeof(double) * 4 * KKR_KCHUNK;
 }
 
 size_t realsum_smem(const must_kkr* h) {
@@ -627,9 +750,9 @@ size_t realsum_smem(const must_kkr* h) {
 }
 
 size_t invert_smem(const must_kkr* h) {
-  return sizeof(double2) * (size_t(h->n) * (h->n + 1) + size_t(h->n_disp) * h->nL2 + size_t(h->nb) * h->nL * h->nL +
-                            h->n) +
-         sizeof(double) * h->n + sizeof(int) * 2 * h->n;
+  const size_t NM = size_t(kkr_matrices_per_pass(h->n)), n = size_t(h->n);
+  return sizeof(double2) * (NM * n * (n + 1) + NM * h->n_disp * h->nL2 + size_t(h->nb) * h->nL * h->nL + NM * n + NM) +
+         sizeof(double) * NM * n + sizeof(int) * (2 * NM * n + NM);
 }
 
 struct KkrWs {
@@ -732,12 +855,18 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
     must_set_error("must_kkr_build: %d distinct site displacements exceed %d", n_disp, KKR_MAX_DISP);
     return MUST_EINVAL;
   }
-  // Gamma-centred mesh, folded to m_i in (-n_k/2, n_k/2]
+  // Gamma-centred mesh, folded to m_i in (-n_k/2, n_k/2]; one point of each
+  // pair {m, -m mod n_k} is kept (M(-k) = M(k)^T), flagged when -m differs
   std::vector<double> kpts;
+  std::vector<int> kpair;
   double kmax = 0.0;
   for (int m1 = 0; m1 < n_k; ++m1)
     for (int m2 = 0; m2 < n_k; ++m2)
       for (int m3 = 0; m3 < n_k; ++m3) {
+        const int idx = (m1 * n_k + m2) * n_k + m3;
+        const int nidx = (((n_k - m1) % n_k) * n_k + (n_k - m2) % n_k) * n_k + (n_k - m3) % n_k;
+        if (nidx < idx) continue;   // its partner is kept
+        kpair.push_back(nidx != idx ? 1 : 0);
         const int f1 = (2 * m1 > n_k) ? m1 - n_k : m1, f2 = (2 * m2 > n_k) ? m2 - n_k : m2,
                   f3 = (2 * m3 > n_k) ? m3 - n_k : m3;
         double k[3];
@@ -745,7 +874,7 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
         kmax = std::max(kmax, norm3(k));
         kpts.insert(kpts.end(), k, k + 3);
       }
-  const int n_kpts = n_k * n_k * n_k;
+  const int n_kpts = int(kpair.size());
   // reciprocal vectors: |k + K|^2 <= eta cut + E_cap for each k
   const double qmax = std::sqrt(eta * KKR_CUT + KKR_ECAP);
   std::vector<double> Kv;
@@ -794,7 +923,7 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
   must_kkr* h = new must_kkr();
   std::memset(h, 0, sizeof(*h));
   h->nb = n_basis; h->lmax = lmax; h->nL = nL; h->l2max = l2max; h->nL2 = nL2; h->n = n_basis * nL;
-  h->n_k = n_k; h->n_kpts = n_kpts; h->n_disp = n_disp; h->n_pts = n_pts; h->n_K = n_K;
+  h->n_k = n_k; h->n_kpts = n_kpts; h->n_mesh = n_k * n_k * n_k; h->n_disp = n_disp; h->n_pts = n_pts; h->n_K = n_K;
   h->n_kK = int(kK_idx.size()); h->n_kg = (n_kpts + KKR_KG - 1) / KKR_KG;
   h->eta = eta; h->omega = omega;
   cudaGetDevice(&h->device);
@@ -806,6 +935,7 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st);
   };
   up(reinterpret_cast<void**>(&h->d_kpts), kpts.data(), sizeof(double) * kpts.size());
+  up(reinterpret_cast<void**>(&h->d_kpair), kpair.data(), sizeof(int) * kpair.size());
   up(reinterpret_cast<void**>(&h->d_K), Kv.data(), sizeof(double) * Kv.size());
   up(reinterpret_cast<void**>(&h->d_kK_start), kK_start.data(), sizeof(int) * kK_start.size());
   up(reinterpret_cast<void**>(&h->d_kK_idx), kK_idx.data(), sizeof(int) * kK_idx.size());
@@ -819,26 +949,41 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
   up(reinterpret_cast<void**>(&h->d_g_start), gs.data(), sizeof(int) * gs.size());
   up(reinterpret_cast<void**>(&h->d_g_L2), gl.data(), sizeof(int) * gl.size());
   up(reinterpret_cast<void**>(&h->d_g_c), gc.data(), sizeof(double) * gc.size());
+  if (e == cudaSuccess) {
+    double ynorm[KKR_MAX_NL2] = {0.0};
+    for (int l = 0; l <= KKR_MAX_L2; ++l)
+      for (int m = 0; m <= l; ++m) {
+        double ratio = 1.0;
+        for (int q = l - m + 1; q <= l + m; ++q) ratio /= double(q);
+        ynorm[l * l + l + m] = std::sqrt((2.0 * l + 1.0) / (4.0 * kPi) * ratio) * (m > 0 ? std::sqrt(2.0) : 1.0);
+      }
+    e = cudaMemcpyToSymbolAsync(c_ynorm, ynorm, sizeof(ynorm), 0, cudaMemcpyHostToDevice, st);
+    double rec[KKR_MAX_L2 + 1] = {0.0};
+    for (int q = 1; q <= KKR_MAX_L2; ++q) rec[q] = 1.0 / q;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_recip, rec, sizeof(rec), 0, cudaMemcpyHostToDevice, st);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) {
-    // the largest dynamic shared memory any handle can need (a handle built
-    // later must not lower the limit an earlier one relies on)
-    const size_t rs = sizeof(double2) * (size_t(KKR_KCHUNK) * KKR_MAX_NL2 + size_t(KKR_MAX_DISP) * KKR_KCHUNK) +
-                      sizeof(double) * 3 * KKR_KCHUNK;
-    const size_t is = sizeof(double2) * (size_t(KKR_MAX_N) * (KKR_MAX_N + 1) + size_t(KKR_MAX_DISP) * KKR_MAX_NL2 +
-                                         size_t(KKR_MAX_N) * 25 + KKR_MAX_N) +
-                      sizeof(double) * KKR_MAX_N + sizeof(int) * 2 * KKR_MAX_N;
-    const size_t ss = sizeof(double2) * (size_t(KKR_RCHUNK) * KKR_MAX_NL2 + size_t(KKR_KB) * KKR_RCHUNK);
-    if (recip_smem(h) > rs || invert_smem(h) > is || realsum_smem(h) > ss) {
-      must_set_error("must_kkr_build: shared-memory bound violated");
+    // dynamic shared memory: raised to this handle's need per device, never
+    // lowered (a handle built later must not cut the limit an earlier one uses)
+    const size_t need[3] = {recip_smem(h), invert_smem(h), realsum_smem(h)};
+    if (need[0] > 227 * 1024 || need[1] > 227 * 1024 || need[2] > 227 * 1024) {
+      must_set_error("must_kkr_build: shared memory per CTA exceeded");
       must_kkr_free(h);
       return MUST_EINVAL;
     }
-    e = cudaFuncSetAttribute(kkr_recip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rs));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(kkr_invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(is));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(kkr_realsum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ss));
+    static std::mutex mu;
+    static size_t granted[64][3] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    const int dv = (h->device >= 0 && h->device < 64) ? h->device : 0;
+    const void* fns[3] = {reinterpret_cast<const void*>(kkr_recip_kernel),
+                          reinterpret_cast<const void*>(kkr_invert_kernel),
+                          reinterpret_cast<const void*>(kkr_realsum_kernel)};
+    for (int f = 0; f < 3 && e == cudaSuccess; ++f)
+      if (need[f] > granted[dv][f]) {
+        e = cudaFuncSetAttribute(fns[f], cudaFuncAttributeMaxDynamicSharedMemorySize, int(need[f]));
+        if (e == cudaSuccess) granted[dv][f] = need[f];
+      }
   }
   if (e != cudaSuccess) {
     must_set_error("must_kkr_build: %s", cudaGetErrorString(e));
@@ -852,7 +997,7 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
 
 extern "C" void must_kkr_free(must_kkr* h) {
   if (!h) return;
-  void* ptrs[] = {h->d_kpts, h->d_K, h->d_kK_start, h->d_kK_idx, h->d_disp, h->d_pair_disp, h->d_pt_start,
+  void* ptrs[] = {h->d_kpts, h->d_kpair, h->d_K, h->d_kK_start, h->d_kK_idx, h->d_disp, h->d_pair_disp, h->d_pt_start,
                   h->d_pt_R, h->d_pt_rho, h->d_quad_u, h->d_quad_w, h->d_g_start, h->d_g_L2, h->d_g_c};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -867,6 +1012,7 @@ extern "C" must_status must_kkr_info(const must_kkr* h, int32_t* info) {
   info[3] = h->n_pts;
   info[4] = h->n_kK;
   info[5] = h->n_kg;
+  info[6] = h->n_mesh;
   return MUST_OK;
 }
 

@@ -69,7 +69,7 @@ def test_kkr_fcc_primitive_vs_oracle(B, orc):
     picks = [(0, 0), (1, 0), (0, 5), (1, 16), (0, nE - 1)]
     E, ti = _items(orc, c, picks)
     got, st, h = _gpu(B, c, E, ti)
-    assert h.n == 16 and h.n_kpts == 216
+    assert h.n == 16 and h.n_mesh == 216 and h.n_kpts == (216 + 8) // 2   # k and -k paired
     _check(orc, c, E, ti, got, st, h)
 
 
@@ -80,7 +80,7 @@ def test_kkr_l12_cell_vs_oracle(B, orc):
     picks = [(0, 0), (1, nE // 2), (0, nE - 1)]
     E, ti = _items(orc, c, picks)
     got, st, h = _gpu(B, c, E, ti)
-    assert h.n == 64 and h.n_kpts == 64
+    assert h.n == 64 and h.n_mesh == 64 and h.n_kpts == (64 + 8) // 2
     _check(orc, c, E, ti, got, st, h)
     # the three face-centred A sites are equivalent under the cubic symmetry
     for s in (2, 3):
