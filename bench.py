@@ -1018,7 +1018,11 @@ def run_kkr(args):
     dev = torch.device("cuda")
     stream = torch.cuda.current_stream()
     cores = min(16, os.cpu_count() or 1)
-    crystals = [wl.l12_crystal(n_k=8, n_e=args.n_energies), wl.fcc_crystal(n_k=16, n_e=args.n_energies)]
+    crystals = []
+    if args.kkr_cells in ("both", "l12"):
+        crystals.append(wl.l12_crystal(n_k=8, n_e=args.n_energies))
+    if args.kkr_cells in ("both", "fcc1"):
+        crystals.append(wl.fcc_crystal(n_k=16, n_e=args.n_energies))
     results = {}
     for c in crystals:
         h = B.must_kkr_build(c.lattice, c.basis, c.lmax, c.n_k)
@@ -1090,6 +1094,10 @@ def run_kkr(args):
         torch.cuda.synchronize()
         ms_e2e = g0.elapsed_time(g1) / args.steps
         # the oracle on the host cores, on a bounded sample of the same items
+        if args.no_cpu_baseline:
+            results[c.name] = {"value": items / (ms / 1e3), "unit": "tau solves/s", "ms_per_step": ms,
+                               "kernels": kern, "gpu_launches": launches, "clocks": clocks}
+            continue
         sample = [picks[(k * 11) % items] for k in range(cores if c.n_basis == 1 else max(2, cores // 4))]
         si = [picks.index(p) for p in sample]
         Es = np.array([c.energies[e] for _, e in sample])
@@ -1194,6 +1202,8 @@ def main():
                     help="liz135: the benchmark workload; supercell: per-site LIZs of the 256-site supercell "
                          "with vacancies (uneven n), batched and replayed as a captured plan")
     ap.add_argument("--n-lizs", type=int, default=32, help="supercell / warmstart mode: evaluation LIZs")
+    ap.add_argument("--kkr-cells", default="both", choices=["both", "l12", "fcc1"],
+                    help="kkr mode: the L1_2 4-site cell, the primitive fcc cell, or both")
     ap.add_argument("--chunk-lizs", type=int, default=2,
                     help="supercell: workspace for this many LIZs per launch (more LIZs share launches; "
                          "2 measured 5%% faster than 1, 4 no faster than 2)")

@@ -404,6 +404,7 @@ __global__ void __launch_bounds__(RSUM_THREADS) kkr_realsum_kernel(KkrDev K, int
 // searches matrix m's pivot column, and each matrix's update is spread over
 // 256 / NM threads (column j, rows rg, rg + RG, ..., four at a time).
 constexpr int INV_THREADS = 256;
+constexpr int INV_ACC = (KKR_MAX_N * 25 + INV_THREADS - 1) / INV_THREADS;   // nb nL^2 <= n nL <= 64 x 25
 
 __host__ __device__ inline int kkr_matrices_per_pass(int n) {
   int nm = 8;
@@ -422,9 +423,7 @@ __global__ void __launch_bounds__(INV_THREADS) kkr_invert_kernel(KkrDev K, int i
   const int RG = TPM / n;                                    // row groups of the update (>= 1)
   const int nDL = K.n_disp * K.nL2;
   double2* A = reinterpret_cast<double2*>(smem_raw);        // [NM][n][n+1] row-major
-  double2* Ds = A + NM * nn;                                 // [NM][n_disp][nL2]
-  double2* acc = Ds + NM * nDL;                              // [nb][nL][nL]
-  double2* colk = acc + K.nb * K.nL * K.nL;                  // [NM][n]
+  double2* colk = A + NM * nn;                               // [NM][n]
   double2* pinv_s = colk + NM * n;                           // [NM]
   double* sc = reinterpret_cast<double*>(pinv_s + NM);       // [NM][n]
   int* perm = reinterpret_cast<int*>(sc + NM * n);           // [NM][n]
@@ -448,31 +447,27 @@ __global__ void __launch_bounds__(INV_THREADS) kkr_invert_kernel(KkrDev K, int i
     const int s = tid / nL, L = tid % nL, l = l_of_L(L);
     ti_s[tid] = tinv[(size_t(it) * nb + s) * (K.lmax + 1) + l];
   }
-  for (int q = tid; q < nb * nL * nL; q += INV_THREADS) acc[q] = make_double2(0.0, 0.0);
+  // the sum of the diagonal blocks, element q = tid + u * INV_THREADS of [nb][nL][nL]
+  cd acc[INV_ACC];
+#pragma unroll
+  for (int u = 0; u < INV_ACC; ++u) acc[u] = mk(0.0, 0.0);
   if (tid == 0) singular = 0;
   __syncthreads();
   const int kbeg = g * KKR_KG, kend = min(K.n_kpts, kbeg + KKR_KG);
   for (int kb = kbeg; kb < kend; kb += NM) {
     const int nm = min(NM, kend - kb);
-    for (int q = tid; q < nm * nDL; q += INV_THREADS) {
-      const int m = q / nDL, r = q % nDL, L = r % K.nL2;
-      const double2 v0 = Dk[(size_t(it) * K.n_kpts + kb + m) * nDL + r];
-      const double2 f = fl[l_of_L(L)];
-      const cd v = mk(v0.x, v0.y) * mk(f.x, f.y);
-      Ds[q] = make_double2(v.x, v.y);
-    }
-    __syncthreads();
-    // A = t^{-1} - G, G_{LL'} = sum_{L''} c D_{L''} (prefactors folded into Ds)
+    // A = t^{-1} - G, G_{LL'} = sum_{L''} c f_{l''} D_{L''} (D read from the lattice sums)
     for (int q = tid; q < nm * n * n; q += INV_THREADS) {
       const int m = q / (n * n), i = (q / n) % n, j = q % n;
       const int s = i / nL, L = i % nL, t = j / nL, Lp = j % nL;
-      const double2* Dd = Ds + m * nDL + K.pair_disp[s * nb + t] * K.nL2;
+      const double2* Dd = Dk + (size_t(it) * K.n_kpts + kb + m) * nDL + K.pair_disp[s * nb + t] * K.nL2;
       cd gsum = mk(0.0, 0.0);
       for (int p = K.g_start[L * nL + Lp]; p < K.g_start[L * nL + Lp + 1]; ++p) {
-        const double c = K.g_c[p];
-        const double2 dv = Dd[K.g_L2[p]];
-        gsum.x = fma(c, dv.x, gsum.x);
-        gsum.y = fma(c, dv.y, gsum.y);
+        const int L2 = K.g_L2[p];
+        const double2 dv = Dd[L2];
+        const double2 f = fl[l_of_L(L2)];
+        const cd v = K.g_c[p] * (mk(dv.x, dv.y) * mk(f.x, f.y));
+        gsum = gsum + v;
       }
       cd a = mk(-gsum.x, -gsum.y);
       if (i == j) a = a + mk(ti_s[i].x, ti_s[i].y);
@@ -604,10 +599,13 @@ __global__ void __launch_bounds__(INV_THREADS) kkr_invert_kernel(KkrDev K, int i
     __syncthreads();
     // [M(k)^{-1}]^{ss}, and for a paired point also [M(-k)^{-1}]^{ss} = ([M(k)^{-1}]^{ss})^T
     // (M(-k) = M(k)^T by the reciprocity G_{LL'}(rho) = G_{L'L}(-rho)); k points in order
-    for (int q = tid; q < nb * nL * nL; q += INV_THREADS) {
+#pragma unroll
+    for (int u = 0; u < INV_ACC; ++u) {
+      const int q = tid + u * INV_THREADS;
+      if (q >= nb * nL * nL) break;
       const int s = q / (nL * nL), L = (q / nL) % nL, Lp = q % nL;
       const int i = s * nL + L, j = s * nL + Lp;
-      double ax = acc[q].x, ay = acc[q].y;
+      double ax = acc[u].x, ay = acc[u].y;
       for (int m = 0; m < nm; ++m) {
         const double2* Am = A + m * nn;
         const int* sg = sigma + m * n;
@@ -621,12 +619,16 @@ __global__ void __launch_bounds__(INV_THREADS) kkr_invert_kernel(KkrDev K, int i
           ay += f * y.y;
         }
       }
-      acc[q] = make_double2(ax, ay);
+      acc[u] = mk(ax, ay);
     }
     __syncthreads();
   }
   double2* dst = part + (size_t(it) * K.n_kg + g) * nb * nL * nL;
-  for (int q = tid; q < nb * nL * nL; q += INV_THREADS) dst[q] = acc[q];
+#pragma unroll
+  for (int u = 0; u < INV_ACC; ++u) {
+    const int q = tid + u * INV_THREADS;
+    if (q < nb * nL * nL) dst[q] = make_double2(acc[u].x, acc[u].y);
+  }
   if (tid == 0 && singular) atomicMax(status + it, int(MUST_ESINGULAR));
 }
 
@@ -751,8 +753,7 @@ size_t realsum_smem(const must_kkr* h) {
 
 size_t invert_smem(const must_kkr* h) {
   const size_t NM = size_t(kkr_matrices_per_pass(h->n)), n = size_t(h->n);
-  return sizeof(double2) * (NM * n * (n + 1) + NM * h->n_disp * h->nL2 + size_t(h->nb) * h->nL * h->nL + NM * n + NM) +
-         sizeof(double) * NM * n + sizeof(int) * (2 * NM * n + NM);
+  return sizeof(double2) * (NM * n * (n + 1) + NM * n + NM) + sizeof(double) * NM * n + sizeof(int) * (2 * NM * n + NM);
 }
 
 struct KkrWs {
