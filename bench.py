@@ -584,26 +584,58 @@ def run_supercell(args):
             import torch.distributed as dist
             dist.barrier()
 
-    def timed_plan(opts, steps, warm):
+    def timed_plan(opts, steps, warm, parts=1):
         # the minimum holds one LIZ's items at the largest order; a multiple lets
-        # that many LIZs share every launch
-        nbytes = B.must_batch_workspace_bytes(s.lizs, len(w.energies) * s.nspin, opts) * max(1, args.chunk_lizs)
-        wsp = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-        tau, st = s.alloc_out(len(lizs))
-        plan = B.must_plan_batch(s.lizs, s.E, s.tinv, s.n_species, s.nspin, opts, wsp, nbytes, tau, st)
+        # that many LIZs share every launch.  parts > 1: the LIZs split into that
+        # many cost-balanced parts (sum of n^3), each captured as its own plan with
+        # its own workspace and outputs (the inputs E, t^-1 are shared read-only)
+        # and replayed on its own stream, so that independent chunks are in flight
+        # at once; every step still covers the whole batch.
+        idx_parts = shard.balanced_shards([z.n for z in s.lizs], parts) if parts > 1 else [list(range(len(s.lizs)))]
+        idx_parts = [ix for ix in idx_parts if ix]
+        stream = torch.cuda.current_stream(dev)
+        streams = [torch.cuda.Stream(device=dev) for _ in idx_parts] if len(idx_parts) > 1 else [stream]
+        plans, outs, keep = [], [], []
+        for ix in idx_parts:
+            sub = [s.lizs[i] for i in ix]
+            nbytes = B.must_batch_workspace_bytes(sub, len(w.energies) * s.nspin, opts) * max(1, args.chunk_lizs)
+            wsp = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            tau_p, st_p = s.alloc_out(len(sub))
+            plans.append(B.must_plan_batch(sub, s.E, s.tinv, s.n_species, s.nspin, opts, wsp, nbytes, tau_p, st_p))
+            outs.append((tau_p, st_p))
+            keep.append(wsp)
+
+        def launch_all():
+            if len(plans) == 1:
+                B.must_plan_launch(plans[0], stream=stream)
+                return
+            for x in streams:
+                x.wait_stream(stream)
+            for pl, x in zip(plans, streams):
+                B.must_plan_launch(pl, stream=x)
+            for x in streams:
+                stream.wait_stream(x)
+
         for _ in range(warm):
-            B.must_plan_launch(plan)
+            launch_all()
         barrier()
         torch.cuda.synchronize(dev)
         l0 = B.must_launch_count()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
+        e0.record(stream)
         for _ in range(steps):
-            B.must_plan_launch(plan)
-        e1.record()
+            launch_all()
+        e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
+        # outputs back in the batch's LIZ order
+        tau, st = s.alloc_out(len(lizs))
+        for ix, (tau_p, st_p) in zip(idx_parts, outs):
+            for k, i in enumerate(ix):
+                tau[i].copy_(tau_p[k])
+                st[i].copy_(st_p[k])
+        del keep
         return max_over_ranks(e0.elapsed_time(e1)), B.must_launch_count() - l0, tau, st
 
     prec = args.precision
@@ -618,7 +650,7 @@ def run_supercell(args):
     sampler = ClockSampler(local)
     if rank == 0:
         sampler.start()
-    ms, launches, tau, st = timed_plan(opts, args.steps, args.warmup)
+    ms, launches, tau, st = timed_plan(opts, args.steps, args.warmup, parts=max(1, args.sc_parts))
     clocks = sampler.stop() if rank == 0 else None
     total_items = items
     if ws > 1:
@@ -634,7 +666,11 @@ def run_supercell(args):
         a, b = blocks_to_numpy(tau), blocks_to_numpy(tau64)
         err = float((np.linalg.norm(a - b, axis=(-2, -1)) / np.linalg.norm(b, axis=(-2, -1))).max())
     sizes = [z.n for z in s.lizs]
+    # algorithmic work of the step (8/3 n^3 real flops per solve): LIZ mixes of
+    # different sizes compare by this rate, not by solves/s
+    work = sum(8.0 / 3.0 * float(n) ** 3 for n in sizes) * len(w.energies) * s.nspin
     line = {"metric": "tau_00 solves/sec, batched uneven LIZs (supercell, n %d..%d)" % (min(sizes), max(sizes)),
+            "tflops_8_3_n3": work * args.steps / (ms / 1e3) / 1e12,
             "value": total_items * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "strong" if args.shard == "balanced" else "weak",
@@ -645,6 +681,7 @@ def run_supercell(args):
                        "energies": len(w.energies), "spins": s.nspin, "solves_per_step": items,
                        "n_min": min(sizes), "n_max": max(sizes), "precision": prec, "residual": args.residual,
                        "launch": "captured CUDA graph (must_plan_batch), replayed per step",
+                       "parts_in_flight": max(1, args.sc_parts),
                        "bucket_sites": B.must_tune_get(0), "tile_n": B.must_tune_get(1)},
             "gpu_launches": int(launches), "clocks": clocks, "plain_fp64_batched": fp64,
             "max_rel_err_vs_fp64": err, "status_ok": bool((st.cpu().numpy() == 0).all()), "autotune": tuned}
@@ -1204,6 +1241,9 @@ def main():
     ap.add_argument("--n-lizs", type=int, default=32, help="supercell / warmstart mode: evaluation LIZs")
     ap.add_argument("--kkr-cells", default="both", choices=["both", "l12", "fcc1"],
                     help="kkr mode: the L1_2 4-site cell, the primitive fcc cell, or both")
+    ap.add_argument("--sc-parts", type=int, default=1,
+                    help="supercell: split the batch into this many cost-balanced parts, each a captured plan "
+                         "with its own workspace replayed on its own stream (independent chunks in flight)")
     ap.add_argument("--chunk-lizs", type=int, default=2,
                     help="supercell: workspace for this many LIZs per launch (more LIZs share launches; "
                          "2 measured 5%% faster than 1, 4 no faster than 2)")
