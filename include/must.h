@@ -439,9 +439,11 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * Asynchronous on `stream` for device outputs; returns after the final copy
  * for host outputs.  Errors: MUST_EINVAL, MUST_ENOMEM, MUST_ECUDA.
  *
- * must_kkr_info: info[7] = {M(k) order, k points evaluated, distinct
- * displacements, real-space points, (k, K) reciprocal terms, k groups, mesh
- * points n_k^3}.  Only one point of each pair {k, -k} of the mesh is
+ * must_kkr_info: info[8] = {M(k) order, k points evaluated, distinct
+ * displacements, real-space points stored, (k, K) reciprocal terms, k groups,
+ * mesh points n_k^3, real-space points of the zero displacement}.  The
+ * displacements x != 0 come in pairs (x, -x) and the real-space points of x = 0
+ * in pairs (R, -R); one member of each is stored and summed for both.  Only one point of each pair {k, -k} of the mesh is
  * evaluated: M(-k) = M(k)^T (the reciprocity G_{LL'}(rho) = G_{L'L}(-rho)), so
  * its diagonal blocks enter the average transposed.  must_kkr_eta: the
  * splitting parameter in use.

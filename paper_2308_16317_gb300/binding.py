@@ -409,9 +409,10 @@ class Kkr:
         self.handle = handle
         self.n_basis, self.lmax = n_basis, lmax
         self.kap = (lmax + 1) ** 2
-        info = np.zeros(7, np.int32)
+        info = np.zeros(8, np.int32)
         _check(load().must_kkr_info(handle, _ptr(info)))
-        self.n, self.n_kpts, self.n_disp, self.n_pts, self.n_kK, self.n_kg, self.n_mesh = (int(v) for v in info)
+        (self.n, self.n_kpts, self.n_disp, self.n_pts, self.n_kK, self.n_kg, self.n_mesh,
+         self.n_pts0) = (int(v) for v in info)
         self.eta = float(load().must_kkr_eta(handle))
 
     def __del__(self):

@@ -146,7 +146,7 @@ struct KkrDev {
   const int* kK_idx;      // reciprocal vectors of each k with |k + K|^2 <= qmax^2
   const double* disp;     // [n_disp][3], disp 0 = 0
   const int* pair_disp;   // [nb * nb]
-  const int* pt_start;    // [n_disp + 1]
+  const int* pt_start;    // [n_groups + 1]: points of each displacement group
   const double* pt_R;     // [n_pts][3] lattice vector R
   const double* pt_rho;   // [n_pts][4] rho = x - R and |rho|
   const double* quad_u;   // [KKR_QUAD] nodes in u
@@ -199,33 +199,51 @@ __global__ void kkr_real_terms_kernel(KkrDev K, int items, const double2* __rest
 }
 
 // -------------------------------------------------------------------------
+// Displacement groups.  Displacement 0 is x = 0; the others come in pairs
+// (x, -x) at indices 2g-1, 2g (group g >= 1).  Both sums use the pairing:
+// with the real solid harmonics YS_L(-v) = (-1)^l YS_L(v),
+//   reciprocal:  A^{x}_L = i^l (U_L + i V_L),  A^{-x}_L = i^l (U_L - i V_L),
+//                U_L = sum_K cos(q.x) w_K YS_L(q), V_L = sum_K sin(q.x) w_K YS_L(q);
+//   real space:  the points of -x are those of x negated, so with
+//                C_L = sum_R cos(k.R) T_L(R), S_L = sum_R sin(k.R) T_L(R) over the points of x,
+//                B^{x}_L = C_L + i S_L,  B^{-x}_L = (-1)^l (C_L - i S_L);
+//                for x = 0 only one point of each pair {R, -R} is kept and
+//                B^{0}_L = 2 C_L (l even), 2 i S_L (l odd).
+// Every accumulation is then a real coefficient times a complex term (or a
+// complex coefficient times a real harmonic): two FMAs instead of four.
+
+// -------------------------------------------------------------------------
 // A_L + C_L for every displacement, one CTA per (k, item):
 //   Dk[item][k][d][L] = (4 pi/Omega) i^l sum_K e^{iq.x_d} YS_L(q) e^{(E-q^2)/eta}/(q^2-E) + C_L
-// Per chunk of KKR_KCHUNK reciprocal vectors: 64 threads form q and the weight,
-// all threads form the harmonics (four m columns per vector) and the phases,
-// then each thread accumulates its outputs (d, L) -- over every vector of the
+// Per chunk of KKR_KCHUNK reciprocal vectors: 64 threads form q and the
+// weight, all threads form the harmonics (four m columns per vector) and the
+// coefficients (w for group 0, cos(q.x) w and sin(q.x) w for the pairs), then
+// each thread accumulates its outputs (group, L) -- over every vector of the
 // chunk, or, when the outputs are fewer than the threads, over one of G
 // interleaved subsets, the G partial sums being added in order at the end.
 constexpr int RECIP_THREADS = 256;
-constexpr int RECIP_OUT = (KKR_MAX_DISP * KKR_MAX_NL2 + RECIP_THREADS - 1) / RECIP_THREADS;
+constexpr int KKR_MAX_GROUPS = 1 + (KKR_MAX_DISP - 1) / 2;
+constexpr int RECIP_OUT = (KKR_MAX_GROUPS * KKR_MAX_NL2 + RECIP_THREADS - 1) / RECIP_THREADS;
 constexpr int RECIP_MPARTS = RECIP_THREADS / KKR_KCHUNK;
 
 __global__ void __launch_bounds__(RECIP_THREADS) kkr_recip_kernel(KkrDev K, int items, const double2* __restrict__ E,
                                                                   double2* __restrict__ Dk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* F = reinterpret_cast<double2*>(smem_raw);                 // [KCHUNK][nL2], >= RECIP_THREADS
-  double2* P = F + max(KKR_KCHUNK * K.nL2, RECIP_THREADS);            // [n_disp][KCHUNK]
-  double2* wv = P + K.n_disp * KKR_KCHUNK;                             // [KCHUNK]
+  const int n_groups = 1 + (K.n_disp - 1) / 2;
+  const int n_out = n_groups * K.nL2;
+  double* Y = reinterpret_cast<double*>(smem_raw);                    // [KCHUNK][nL2] real harmonics
+  double2* W = reinterpret_cast<double2*>(Y + KKR_KCHUNK * K.nL2);    // [n_disp][KCHUNK] coefficients
+  double2* wv = W + K.n_disp * KKR_KCHUNK;                             // [KCHUNK]
   double* qv = reinterpret_cast<double*>(wv + KKR_KCHUNK);            // [KCHUNK][4]: q, |q|^2
+  double2* red = reinterpret_cast<double2*>(qv + 4 * KKR_KCHUNK);     // [2][RECIP_THREADS] partial sums
   const int ik = blockIdx.x, it = blockIdx.y, tid = threadIdx.x;
   const cd e = mk(E[it].x, E[it].y);
   const double* kp = K.kpts + size_t(ik) * 3;
   const int k0 = K.kK_start[ik], k1 = K.kK_start[ik + 1];
-  const int n_out = K.n_disp * K.nL2;
   const int G = (n_out <= RECIP_THREADS) ? RECIP_THREADS / n_out : 1;
-  cd acc[RECIP_OUT];
+  cd accU[RECIP_OUT], accV[RECIP_OUT];
 #pragma unroll
-  for (int j = 0; j < RECIP_OUT; ++j) acc[j] = mk(0.0, 0.0);
+  for (int j = 0; j < RECIP_OUT; ++j) { accU[j] = mk(0.0, 0.0); accV[j] = mk(0.0, 0.0); }
   const double inv_eta = 1.0 / K.eta;
   // (4 pi / Omega) e^{E/eta}; each term then needs the real e^{-q^2/eta}
   const cd wpre = (4.0 * kPi / K.omega) * cexp_d(mk(e.x * inv_eta, e.y * inv_eta));
@@ -247,94 +265,117 @@ __global__ void __launch_bounds__(RECIP_THREADS) kkr_recip_kernel(KkrDev K, int 
     __syncthreads();
     {
       const int j = tid % KKR_KCHUNK, part = tid / KKR_KCHUNK;
-      const double q0 = qv[j * 4], q1 = qv[j * 4 + 1], q2v = qv[j * 4 + 2], qq = qv[j * 4 + 3];
-      const cd w = mk(wv[j].x, wv[j].y);
-      double2* f = F + j * K.nL2;
+      double* y = Y + j * K.nL2;
       for (int m = part; m <= K.l2max; m += RECIP_MPARTS)
-        solid_harmonic_column(K.l2max, m, q0, q1, q2v, qq, [&](int l, int L, double v) {
-          const cd wl = ipow_d(l) * w;
-          f[L] = make_double2(wl.x * v, wl.y * v);
-        });
+        solid_harmonic_column(K.l2max, m, qv[j * 4], qv[j * 4 + 1], qv[j * 4 + 2], qv[j * 4 + 3],
+                              [&](int, int L, double v) { y[L] = v; });
     }
     for (int p = tid; p < K.n_disp * KKR_KCHUNK; p += RECIP_THREADS) {
       const int d = p / KKR_KCHUNK, j = p % KKR_KCHUNK;
-      double s = 0.0, c = 1.0;              // displacement 0 is x = 0
-      if (d > 0) {
-        const double* x = K.disp + d * 3;
-        sincos(qv[j * 4] * x[0] + qv[j * 4 + 1] * x[1] + qv[j * 4 + 2] * x[2], &s, &c);
+      const double2 w = wv[j];
+      if (d == 0) {
+        W[p] = w;
+      } else {
+        const double* x = K.disp + ((d - 1) / 2 * 2 + 1) * 3;   // the x of the pair
+        double sn, cs;
+        sincos(qv[j * 4] * x[0] + qv[j * 4 + 1] * x[1] + qv[j * 4 + 2] * x[2], &sn, &cs);
+        const double f = (d & 1) ? cs : sn;                     // row 2g-1: cos, row 2g: sin
+        W[p] = make_double2(f * w.x, f * w.y);
       }
-      P[d * KKR_KCHUNK + j] = make_double2(c, s);
     }
     __syncthreads();
-    if (G > 1) {
-      if (tid < G * n_out) {
-        const int o = tid % n_out, g = tid / n_out;
-        const int d = o / K.nL2, L = o % K.nL2;
-        cd a = acc[0];
-        for (int j = g; j < cn; j += G) {
-          const double2 pp = P[d * KKR_KCHUNK + j], ff = F[j * K.nL2 + L];
-          a.x = fma(pp.x, ff.x, fma(-pp.y, ff.y, a.x));
-          a.y = fma(pp.x, ff.y, fma(pp.y, ff.x, a.y));
-        }
-        acc[0] = a;
-      }
-    } else {
+    const int sub = (G > 1) ? tid / n_out : 0;
+    const int nloop = (G > 1) ? 1 : RECIP_OUT;
 #pragma unroll
-      for (int jj = 0; jj < RECIP_OUT; ++jj) {
-        const int o = tid + jj * RECIP_THREADS;
-        if (o < n_out) {
-          const int d = o / K.nL2, L = o % K.nL2;
-          cd a = acc[jj];
-          for (int j = 0; j < cn; ++j) {
-            const double2 pp = P[d * KKR_KCHUNK + j], ff = F[j * K.nL2 + L];
-            a.x = fma(pp.x, ff.x, fma(-pp.y, ff.y, a.x));
-            a.y = fma(pp.x, ff.y, fma(pp.y, ff.x, a.y));
-          }
-          acc[jj] = a;
+    for (int jj = 0; jj < RECIP_OUT; ++jj) {
+      if (jj >= nloop) break;
+      const int o = (G > 1) ? tid % n_out : tid + jj * RECIP_THREADS;
+      if (o >= n_out || (G > 1 && tid >= G * n_out)) continue;
+      const int g = o / K.nL2, L = o % K.nL2;
+      const int step = (G > 1) ? G : 1;
+      if (g == 0) {
+        cd u = accU[jj];
+        for (int j = sub; j < cn; j += step) {
+          const double yv = Y[j * K.nL2 + L];
+          const double2 c = W[j];
+          u.x = fma(c.x, yv, u.x);
+          u.y = fma(c.y, yv, u.y);
         }
+        accU[jj] = u;
+      } else {
+        cd u = accU[jj], v = accV[jj];
+        const double2* Wc = W + (2 * g - 1) * KKR_KCHUNK;
+        const double2* Ws = Wc + KKR_KCHUNK;
+        for (int j = sub; j < cn; j += step) {
+          const double yv = Y[j * K.nL2 + L];
+          const double2 c = Wc[j], sv = Ws[j];
+          u.x = fma(c.x, yv, u.x);
+          u.y = fma(c.y, yv, u.y);
+          v.x = fma(sv.x, yv, v.x);
+          v.y = fma(sv.y, yv, v.y);
+        }
+        accU[jj] = u;
+        accV[jj] = v;
       }
     }
     __syncthreads();
   }
   if (G > 1) {
     // partial sums of the G subsets, added in order
-    double2* red = F;
-    if (tid < G * n_out) red[tid] = make_double2(acc[0].x, acc[0].y);
+    if (tid < G * n_out) {
+      red[tid] = make_double2(accU[0].x, accU[0].y);
+      red[RECIP_THREADS + tid] = make_double2(accV[0].x, accV[0].y);
+    }
     __syncthreads();
     if (tid < n_out) {
-      cd a = mk(0.0, 0.0);
-      for (int g = 0; g < G; ++g) a = a + mk(red[g * n_out + tid].x, red[g * n_out + tid].y);
-      acc[0] = a;
+      cd u = mk(0.0, 0.0), v = mk(0.0, 0.0);
+      for (int g = 0; g < G; ++g) {
+        u = u + mk(red[g * n_out + tid].x, red[g * n_out + tid].y);
+        v = v + mk(red[RECIP_THREADS + g * n_out + tid].x, red[RECIP_THREADS + g * n_out + tid].y);
+      }
+      accU[0] = u;
+      accV[0] = v;
     }
   }
-  double2* out = Dk + (size_t(it) * K.n_kpts + ik) * n_out;
+  double2* out = Dk + (size_t(it) * K.n_kpts + ik) * K.n_disp * K.nL2;
+  const int nwrite = (G > 1) ? 1 : RECIP_OUT;
 #pragma unroll
   for (int jj = 0; jj < RECIP_OUT; ++jj) {
+    if (jj >= nwrite) break;
     const int o = tid + jj * RECIP_THREADS;
-    if (o < n_out && (G == 1 || jj == 0)) {
-      cd a = acc[jj];
-      if (o == 0) {
+    if (o >= n_out) continue;
+    const int g = o / K.nL2, L = o % K.nL2, l = l_of_L(L);
+    const cd il = ipow_d(l);
+    if (g == 0) {
+      cd a = il * accU[jj];
+      if (L == 0) {
         // C_0 of displacement 0 (x = 0): the R = 0 term of the reciprocal sum removed
         const cd kap = csqrt_p(e);
-        const cd z = mk(e.x / K.eta, e.y / K.eta);
-        cd s = mk(0.0, 0.0), term = mk(1.0, 0.0);   // (E/eta)^n / n!
+        const cd z = mk(e.x * inv_eta, e.y * inv_eta);
+        cd sm = mk(0.0, 0.0), term = mk(1.0, 0.0);   // (E/eta)^n / n!
         for (int n = 0; n < 400; ++n) {
           const cd add = (1.0 / double(2 * n - 1)) * term;
-          s = s + add;
-          if (n > 4 && cnorm(add) < 1e-36 * cnorm(s)) break;
+          sm = sm + add;
+          if (n > 4 && cnorm(add) < 1e-36 * cnorm(sm)) break;
           term = (1.0 / double(n + 1)) * (term * z);
         }
-        const cd f1 = mk(-kap.y, kap.x) - sqrt(K.eta / kPi) * s;
+        const cd f1 = mk(-kap.y, kap.x) - sqrt(K.eta / kPi) * sm;
         a = a - (1.0 / sqrt(4.0 * kPi)) * f1;
       }
-      out[o] = make_double2(a.x, a.y);
+      out[L] = make_double2(a.x, a.y);
+    } else {
+      const cd u = accU[jj], v = accV[jj];
+      const cd p = il * mk(u.x - v.y, u.y + v.x);   // i^l (U + i V)
+      const cd m = il * mk(u.x + v.y, u.y - v.x);   // i^l (U - i V)
+      out[(2 * g - 1) * K.nL2 + L] = make_double2(p.x, p.y);
+      out[(2 * g) * K.nL2 + L] = make_double2(m.x, m.y);
     }
   }
 }
 
 // -------------------------------------------------------------------------
-// Adds B_L: Dk[item][k][d][L] += sum_{pt of d} e^{ik.R_pt} T[item][pt][L], one CTA
-// per (block of KKR_KB k points, displacement, item).
+// Adds B_L, one CTA per (block of KKR_KB k points, displacement group, item):
+// the cosine and sine sums C_L, S_L of the group's points (see above).
 constexpr int RSUM_THREADS = 256;
 constexpr int RSUM_OUT = (KKR_KB * KKR_MAX_NL2 + RSUM_THREADS - 1) / RSUM_THREADS;
 
@@ -343,15 +384,15 @@ __global__ void __launch_bounds__(RSUM_THREADS) kkr_realsum_kernel(KkrDev K, int
                                                                    double2* __restrict__ Dk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* Ts = reinterpret_cast<double2*>(smem_raw);   // [RCHUNK][nL2]
-  double2* ph = Ts + KKR_RCHUNK * K.nL2;                 // [KB][RCHUNK]
-  const int kb = blockIdx.x, d = blockIdx.y, it = blockIdx.z, tid = threadIdx.x;
+  double2* ph = Ts + KKR_RCHUNK * K.nL2;                 // [KB][RCHUNK]: (cos, sin)
+  const int kb = blockIdx.x, g = blockIdx.y, it = blockIdx.z, tid = threadIdx.x;
   const int kbase = kb * KKR_KB;
   const int nkb = min(KKR_KB, K.n_kpts - kbase);
-  const int p0 = K.pt_start[d], p1 = K.pt_start[d + 1];
+  const int p0 = K.pt_start[g], p1 = K.pt_start[g + 1];
   const int n_out = nkb * K.nL2;
-  cd acc[RSUM_OUT];
+  cd accC[RSUM_OUT], accS[RSUM_OUT];
 #pragma unroll
-  for (int j = 0; j < RSUM_OUT; ++j) acc[j] = mk(0.0, 0.0);
+  for (int j = 0; j < RSUM_OUT; ++j) { accC[j] = mk(0.0, 0.0); accS[j] = mk(0.0, 0.0); }
   const double2* Tit = T + size_t(it) * K.n_pts * K.nL2;
   for (int c0 = p0; c0 < p1; c0 += KKR_RCHUNK) {
     const int cn = min(KKR_RCHUNK, p1 - c0);
@@ -361,9 +402,9 @@ __global__ void __launch_bounds__(RSUM_THREADS) kkr_realsum_kernel(KkrDev K, int
       if (kk < nkb && j < cn) {
         const double* kp = K.kpts + size_t(kbase + kk) * 3;
         const double* R = K.pt_R + size_t(c0 + j) * 3;
-        double s, c;
-        sincos(kp[0] * R[0] + kp[1] * R[1] + kp[2] * R[2], &s, &c);
-        ph[q] = make_double2(c, s);
+        double sn, cs;
+        sincos(kp[0] * R[0] + kp[1] * R[1] + kp[2] * R[2], &sn, &cs);
+        ph[q] = make_double2(cs, sn);
       }
     }
     __syncthreads();
@@ -372,13 +413,29 @@ __global__ void __launch_bounds__(RSUM_THREADS) kkr_realsum_kernel(KkrDev K, int
       const int o = tid + jj * RSUM_THREADS;
       if (o < n_out) {
         const int kk = o / K.nL2, L = o % K.nL2;
-        cd a = acc[jj];
-        for (int j = 0; j < cn; ++j) {
-          const double2 pp = ph[kk * KKR_RCHUNK + j], tt = Ts[j * K.nL2 + L];
-          a.x = fma(pp.x, tt.x, fma(-pp.y, tt.y, a.x));
-          a.y = fma(pp.x, tt.y, fma(pp.y, tt.x, a.y));
+        if (g == 0) {
+          // x = 0: only the cosine sum (l even) or the sine sum (l odd) is needed
+          const int odd = l_of_L(L) & 1;
+          cd a = accC[jj];
+          for (int j = 0; j < cn; ++j) {
+            const double2 pp = ph[kk * KKR_RCHUNK + j], tt = Ts[j * K.nL2 + L];
+            const double f = odd ? pp.y : pp.x;
+            a.x = fma(f, tt.x, a.x);
+            a.y = fma(f, tt.y, a.y);
+          }
+          accC[jj] = a;
+        } else {
+          cd a = accC[jj], b = accS[jj];
+          for (int j = 0; j < cn; ++j) {
+            const double2 pp = ph[kk * KKR_RCHUNK + j], tt = Ts[j * K.nL2 + L];
+            a.x = fma(pp.x, tt.x, a.x);
+            a.y = fma(pp.x, tt.y, a.y);
+            b.x = fma(pp.y, tt.x, b.x);
+            b.y = fma(pp.y, tt.y, b.y);
+          }
+          accC[jj] = a;
+          accS[jj] = b;
         }
-        acc[jj] = a;
       }
     }
     __syncthreads();
@@ -387,10 +444,23 @@ __global__ void __launch_bounds__(RSUM_THREADS) kkr_realsum_kernel(KkrDev K, int
   for (int jj = 0; jj < RSUM_OUT; ++jj) {
     const int o = tid + jj * RSUM_THREADS;
     if (o < n_out) {
-      const int kk = o / K.nL2, L = o % K.nL2;
-      double2* dst = Dk + ((size_t(it) * K.n_kpts + kbase + kk) * K.n_disp + d) * K.nL2 + L;
-      const double2 v = *dst;
-      *dst = make_double2(v.x + acc[jj].x, v.y + acc[jj].y);
+      const int kk = o / K.nL2, L = o % K.nL2, l = l_of_L(L);
+      double2* row = Dk + (size_t(it) * K.n_kpts + kbase + kk) * K.n_disp * K.nL2;
+      const cd c = accC[jj], sv = accS[jj];
+      if (g == 0) {
+        const cd add = (l & 1) ? mk(-2.0 * c.y, 2.0 * c.x) : mk(2.0 * c.x, 2.0 * c.y);   // 2 i S or 2 C
+        const double2 v = row[L];
+        row[L] = make_double2(v.x + add.x, v.y + add.y);
+      } else {
+        const cd plus = mk(c.x - sv.y, c.y + sv.x);             // C + i S
+        const double sg = (l & 1) ? -1.0 : 1.0;
+        const cd minus = mk(sg * (c.x + sv.y), sg * (c.y - sv.x));   // (-1)^l (C - i S)
+        double2* dp = row + (2 * g - 1) * K.nL2 + L;
+        double2* dm = row + (2 * g) * K.nL2 + L;
+        const double2 vp = *dp, vm = *dm;
+        *dp = make_double2(vp.x + plus.x, vp.y + plus.y);
+        *dm = make_double2(vm.x + minus.x, vm.y + minus.y);
+      }
     }
   }
 }
@@ -708,7 +778,7 @@ void points_within(const double V[3][3], const double W[3][3], const double* c, 
 }  // namespace
 
 struct must_kkr {
-  int nb, lmax, nL, l2max, nL2, n, n_k, n_kpts, n_mesh, n_disp, n_pts, n_K, n_kK, n_kg, device;
+  int nb, lmax, nL, l2max, nL2, n, n_k, n_kpts, n_mesh, n_disp, n_pts, n_pts0, n_K, n_kK, n_kg, device;
   double eta, omega;
   double* d_kpts;
   int* d_kpair;
@@ -742,9 +812,8 @@ KkrDev dev_view(const must_kkr* h) {
 }
 
 size_t recip_smem(const must_kkr* h) {
-  return sizeof(double2) * (std::max<size_t>(size_t(KKR_KCHUNK) * h->nL2, RECIP_THREADS) +
-                            size_t(h->n_disp) * KKR_KCHUNK + KKR_KCHUNK) +
-         sizeof(double) * 4 * KKR_KCHUNK;
+  return sizeof(double) * (size_t(KKR_KCHUNK) * h->nL2 + 4 * KKR_KCHUNK) +
+         sizeof(double2) * (size_t(h->n_disp) * KKR_KCHUNK + KKR_KCHUNK + 2 * RECIP_THREADS);
 }
 
 size_t realsum_smem(const must_kkr* h) {
@@ -835,19 +904,25 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
     }
   if (eta == 0.0) eta = 4.0 * kPi / std::pow(omega, 2.0 / 3.0);   // balances the two sums
   const int l2max = 2 * lmax, nL2 = (l2max + 1) * (l2max + 1);
-  // distinct displacements, 0 first
+  // distinct displacements: 0 first, then each x != 0 followed by -x
   std::vector<double> disp = {0.0, 0.0, 0.0};
   std::vector<int> pair_disp(size_t(n_basis) * n_basis);
+  auto find_disp = [&](const double* x) {
+    for (size_t d = 0; d < disp.size() / 3; ++d)
+      if (disp[3 * d] == x[0] && disp[3 * d + 1] == x[1] && disp[3 * d + 2] == x[2]) return int(d);
+    return -1;
+  };
   for (int s = 0; s < n_basis; ++s)
     for (int t = 0; t < n_basis; ++t) {
       const double x[3] = {basis[3 * s] - basis[3 * t], basis[3 * s + 1] - basis[3 * t + 1],
                            basis[3 * s + 2] - basis[3 * t + 2]};
-      int found = -1;
-      for (size_t d = 0; d < disp.size() / 3; ++d)
-        if (disp[3 * d] == x[0] && disp[3 * d + 1] == x[1] && disp[3 * d + 2] == x[2]) { found = int(d); break; }
+      int found = find_disp(x);
       if (found < 0) {
+        // fl(b_t - b_s) = -fl(b_s - b_t) exactly, so -x is the displacement of (t, s)
+        const double mx[3] = {-x[0], -x[1], -x[2]};
         found = int(disp.size() / 3);
         disp.insert(disp.end(), x, x + 3);
+        disp.insert(disp.end(), mx, mx + 3);
       }
       pair_disp[size_t(s) * n_basis + t] = found;
     }
@@ -892,19 +967,29 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
     }
   }
   kK_start[n_kpts] = int(kK_idx.size());
-  // real-space points of each displacement: 0 < |x - R| <= rho_max
+  // real-space points per displacement group: for x = 0 one point of each pair
+  // {R, -R} with 0 < |R| <= rho_max (the first nonzero coordinate positive); for
+  // a pair (x, -x) the points of x, 0 < |x - R| <= rho_max (those of -x are
+  // their negatives)
   const double rho_max = std::sqrt(4.0 * (KKR_CUT + KKR_ECAP / eta) / eta);
-  std::vector<int> pt_start(n_disp + 1, 0);
+  const int n_groups = 1 + (n_disp - 1) / 2;
+  std::vector<int> pt_start(n_groups + 1, 0);
   std::vector<double> pt_R, pt_rho, pts;
-  for (int d = 0; d < n_disp; ++d) {
-    pt_start[d] = int(pt_R.size() / 3);
-    const double* x = &disp[3 * d];
+  for (int g = 0; g < n_groups; ++g) {
+    pt_start[g] = int(pt_R.size() / 3);
+    const double* x = &disp[3 * (g == 0 ? 0 : 2 * g - 1)];
     const double mx[3] = {-x[0], -x[1], -x[2]};
     points_within(A, B, mx, rho_max, pts);
+    const double tiny = 1e-9 * norm3(A[0]);
     for (size_t p = 0; p < pts.size(); p += 3) {
       const double rho[3] = {x[0] - pts[p], x[1] - pts[p + 1], x[2] - pts[p + 2]};
       const double r = norm3(rho);
       if (r < 1e-10) continue;
+      if (g == 0) {
+        const double* R = &pts[p];
+        const int lead = (std::fabs(R[0]) > tiny) ? 0 : (std::fabs(R[1]) > tiny) ? 1 : 2;
+        if (R[lead] < 0.0) continue;   // its partner -R is kept
+      }
       pt_R.insert(pt_R.end(), pts.begin() + p, pts.begin() + p + 3);
       pt_rho.push_back(rho[0]);
       pt_rho.push_back(rho[1]);
@@ -913,7 +998,7 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
     }
   }
   const int n_pts = int(pt_R.size() / 3);
-  pt_start[n_disp] = n_pts;
+  pt_start[n_groups] = n_pts;
   std::vector<double> lu, lw;
   quadrature_u(lu, lw);
   if (int(lu.size()) != KKR_QUAD) { must_set_error("must_kkr_build: quadrature size"); return MUST_ECUDA; }
@@ -924,7 +1009,7 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
   must_kkr* h = new must_kkr();
   std::memset(h, 0, sizeof(*h));
   h->nb = n_basis; h->lmax = lmax; h->nL = nL; h->l2max = l2max; h->nL2 = nL2; h->n = n_basis * nL;
-  h->n_k = n_k; h->n_kpts = n_kpts; h->n_mesh = n_k * n_k * n_k; h->n_disp = n_disp; h->n_pts = n_pts; h->n_K = n_K;
+  h->n_k = n_k; h->n_kpts = n_kpts; h->n_mesh = n_k * n_k * n_k; h->n_disp = n_disp; h->n_pts0 = pt_start[1]; h->n_pts = n_pts; h->n_K = n_K;
   h->n_kK = int(kK_idx.size()); h->n_kg = (n_kpts + KKR_KG - 1) / KKR_KG;
   h->eta = eta; h->omega = omega;
   cudaGetDevice(&h->device);
@@ -1014,6 +1099,7 @@ extern "C" must_status must_kkr_info(const must_kkr* h, int32_t* info) {
   info[4] = h->n_kK;
   info[5] = h->n_kg;
   info[6] = h->n_mesh;
+  info[7] = h->n_pts0;
   return MUST_OK;
 }
 
@@ -1087,7 +1173,7 @@ extern "C" must_status must_kkr_tau(const must_kkr* h, int32_t n_items, const do
   }
   {
     ProfScope ps(PH_KKR_REALSUM, st);
-    dim3 g2((h->n_kpts + KKR_KB - 1) / KKR_KB, h->n_disp, n_items);
+    dim3 g2((h->n_kpts + KKR_KB - 1) / KKR_KB, 1 + (h->n_disp - 1) / 2, n_items);
     kkr_realsum_kernel<<<g2, RSUM_THREADS, realsum_smem(h), st>>>(K, n_items, w.T, w.Dk);
     prof_launched(PH_KKR_REALSUM, 1, n_items);
   }
