@@ -1023,13 +1023,15 @@ FP64_DFMA_MEASURED = 1.058   # TFLOP/s, the library's DFMA probe on this GPU (pr
 
 
 def kkr_work(h, c, items):
-    """Algorithmic FP64 flops of one must_kkr_tau call, per kernel: complex
-    multiply-adds (8 real flops) of the reciprocal sums (every (k, K) term for
-    every displacement and L''), of the real-space sums (every (k, point) term
-    for every L''), and n^3 of the in-place Gauss-Jordan inversion of each M(k)."""
+    """Algorithmic FP64 flops of one must_kkr_tau call, per kernel, as the
+    kernels compute them: 4 real flops per multiply-add of a real number into a
+    complex sum -- the reciprocal sums (every (k, K) term, every displacement
+    and L''), the real-space sums (every (k, point, L''), a pair (x, -x) counting
+    for both) -- and 8 per complex multiply-add of the in-place Gauss-Jordan
+    inversion (n^3 per evaluated k point)."""
     nL2 = (2 * c.lmax + 1) ** 2
-    return {"kkr_recip": 8.0 * items * h.n_kK * h.n_disp * nL2,
-            "kkr_realsum": 8.0 * items * h.n_kpts * h.n_pts * nL2,
+    return {"kkr_recip": 4.0 * items * h.n_kK * h.n_disp * nL2,
+            "kkr_realsum": 4.0 * items * h.n_kpts * nL2 * (h.n_pts0 + 2 * (h.n_pts - h.n_pts0)),
             "kkr_invert": 8.0 * items * h.n_kpts * h.n ** 3}
 
 
@@ -1062,7 +1064,11 @@ def run_kkr(args):
         crystals.append(wl.fcc_crystal(n_k=16, n_e=args.n_energies))
     results = {}
     for c in crystals:
-        h = B.must_kkr_build(c.lattice, c.basis, c.lmax, c.n_k)
+        eta = 0.0
+        if args.kkr_eta_scale != 1.0:
+            # a multiple of 4 pi / Omega^(2/3) (the library's default is 1.0 of it, 0.7 with one site)
+            eta = args.kkr_eta_scale * 4.0 * np.pi / abs(np.linalg.det(c.lattice)) ** (2.0 / 3.0)
+        h = B.must_kkr_build(c.lattice, c.basis, c.lmax, c.n_k, eta=eta)
         nE = len(c.energies)
         picks = [(sp, e) for sp in range(c.nspin) for e in range(nE)]
         items = len(picks)
@@ -1239,6 +1245,9 @@ def main():
                     help="liz135: the benchmark workload; supercell: per-site LIZs of the 256-site supercell "
                          "with vacancies (uneven n), batched and replayed as a captured plan")
     ap.add_argument("--n-lizs", type=int, default=32, help="supercell / warmstart mode: evaluation LIZs")
+    ap.add_argument("--kkr-eta-scale", type=float, default=1.0,
+                    help="kkr mode: Ewald splitting parameter as a multiple of 4 pi / Omega^(2/3) (1.0: the "
+                         "library's default)")
     ap.add_argument("--kkr-cells", default="both", choices=["both", "l12", "fcc1"],
                     help="kkr mode: the L1_2 4-site cell, the primitive fcc cell, or both")
     ap.add_argument("--sc-parts", type=int, default=1,

@@ -423,7 +423,9 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * [0, 4] with n_basis (lmax+1)^2 <= 64 (one M(k) is inverted in one CTA's
  * shared memory) and at most 32 distinct site displacements b_s - b_t; n_k in
  * [1, 64]; eta: Ewald splitting parameter (bohr^-2), 0 = 4 pi / Omega^(2/3)
- * (balances the two sums; the result does not depend on it).  Host arrays,
+ * (0.7 of that with one site per cell), which keeps the two sums about equally
+ * costly; the result does not depend on it, but below ~0.4 of that value the
+ * factor e^{E/eta} starts to cost digits.  Host arrays,
  * read during the call.  Builds the k mesh, the reciprocal and real-space
  * vector lists and the Gaunt table on the device (synchronises `stream`).
  * Errors: MUST_EINVAL, MUST_ENOMEM, MUST_ECUDA.

@@ -114,3 +114,37 @@ def test_kkr_status_above_energy_cap(B, orc):
     ti = np.array([[orc.square_well(1, e, -1.0, c.r_mt)[1]] for e in E])
     _, st, _ = _gpu(B, c, E, ti)
     assert st[0] == 0 and st[1] == 8      # MUST_EUNSUPPORTED
+
+
+def test_lsms_tau00_converges_to_the_crystal_tau_on_the_gpu(B):
+    """The LIZ is the crystal truncated (Sec. 2.2): the library's FP64 LSMS
+    tau_00 of a pure fcc element approaches the library's full-KKR tau as the
+    LIZ grows, at Im kappa ~ 0.75 and lmax 3 (the oracle gives 1.8e-5 for 43
+    sites and 1.05e-7 for 135); both paths take the same t^-1 from the
+    library's square-well kernel."""
+    import torch
+    from paper_2308_16317_gb300.runner import Session, blocks_to_numpy
+    lmax = 3
+    E = np.array([-0.1 + 1.0j])
+    c = wl.fcc_crystal(lmax=lmax, n_k=10)
+    tk = None
+    errs = []
+    for S in (3, 7):
+        pos, _ = wl.fcc_cluster(S)
+        w = wl.Workload("pure_fcc", lmax, [wl.Liz(pos, np.zeros(len(pos), np.int32))], E, np.array([[-1.0]]),
+                        wl.R_MT)
+        s = Session(w)
+        tau, st = s.solve(B.must_default_opts(B.MUST_FP64))
+        torch.cuda.synchronize()
+        assert (st.cpu().numpy() == 0).all()
+        tl = blocks_to_numpy(tau)[0, 0]
+        if tk is None:
+            h = B.must_kkr_build(c.lattice, c.basis, lmax, c.n_k)
+            ti = s.tinv.reshape(1, 1, lmax + 1).contiguous()
+            ws = torch.empty(B.must_kkr_workspace_bytes(h, 1), dtype=torch.uint8, device="cuda")
+            out = torch.zeros((1, 1, h.kap, h.kap), dtype=torch.complex128, device="cuda")
+            B.must_kkr_tau(h, s.E, ti, ws, out)
+            torch.cuda.synchronize()
+            tk = np.swapaxes(out.cpu().numpy(), -1, -2)[0, 0]
+        errs.append(np.linalg.norm(tl - tk) / np.linalg.norm(tk))
+    assert errs[1] < 1e-6 and errs[0] > 10 * errs[1], errs
