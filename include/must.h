@@ -425,7 +425,14 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * [1, 64]; eta: Ewald splitting parameter (bohr^-2), 0 = 4 pi / Omega^(2/3)
  * (0.7 of that with one site per cell), which keeps the two sums about equally
  * costly; the result does not depend on it, but below ~0.4 of that value the
- * factor e^{E/eta} starts to cost digits.  Host arrays,
+ * factor e^{E/eta} starts to cost digits.  flags: 0, or MUST_KKR_NO_SYMMETRY.  With one site per
+ * cell and flags 0 the lattice's point group (the signed permutations of the
+ * Cartesian axes that map the lattice onto itself, 48 for cubic lattices) is
+ * used: M(gk) = D(g) M(k) D(g)^T with D(g) the real-harmonic representation of
+ * g, so one point of each orbit of the mesh is inverted, weighted by the orbit's
+ * size, and the sum is symmetrised, (1/|G|) sum_g D(g) S D(g)^T.  Otherwise
+ * (several sites, whose symmetry depends on their t^-1, or the flag) one point
+ * of each pair {k, -k} is evaluated.  Host arrays,
  * read during the call.  Builds the k mesh, the reciprocal and real-space
  * vector lists and the Gaunt table on the device (synchronises `stream`).
  * Errors: MUST_EINVAL, MUST_ENOMEM, MUST_ECUDA.
@@ -441,9 +448,10 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * Asynchronous on `stream` for device outputs; returns after the final copy
  * for host outputs.  Errors: MUST_EINVAL, MUST_ENOMEM, MUST_ECUDA.
  *
- * must_kkr_info: info[8] = {M(k) order, k points evaluated, distinct
+ * must_kkr_info: info[9] = {M(k) order, k points evaluated, distinct
  * displacements, real-space points stored, (k, K) reciprocal terms, k groups,
- * mesh points n_k^3, real-space points of the zero displacement}.  The
+ * mesh points n_k^3, real-space points of the zero displacement, point-group
+ * operations used (0: k / -k pairing)}.  The
  * displacements x != 0 come in pairs (x, -x) and the real-space points of x = 0
  * in pairs (R, -R); one member of each is stored and summed for both.  Only one point of each pair {k, -k} of the mesh is
  * evaluated: M(-k) = M(k)^T (the reciprocity G_{LL'}(rho) = G_{L'L}(-rho)), so
@@ -451,8 +459,9 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * splitting parameter in use.
  */
 typedef struct must_kkr must_kkr;
+#define MUST_KKR_NO_SYMMETRY 1   /* flags: evaluate one point of each {k, -k} pair only */
 must_status must_kkr_build(const double* lattice, const double* basis, int32_t n_basis, int32_t lmax, int32_t n_k,
-                           double eta, void* stream, must_kkr** out);
+                           double eta, int32_t flags, void* stream, must_kkr** out);
 void must_kkr_free(must_kkr* kkr);
 size_t must_kkr_workspace_bytes(const must_kkr* kkr, int32_t n_items);
 must_status must_kkr_tau(const must_kkr* kkr, int32_t n_items, const double* E, const double* tinv,

@@ -38,6 +38,7 @@
 //                          diagonal blocks of M(k)^{-1} summed over the group in a fixed order
 //   kkr_bz_sum_kernel      per output element: the groups summed in a fixed order, / N_k
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -141,6 +142,9 @@ struct KkrDev {
   double eta, omega;
   const double* kpts;     // [n_kpts][3]: one point of each pair {k, -k} of the mesh
   const int* kpair;       // [n_kpts]: 1 if -k is a different mesh point (counted as the transpose)
+  const int* kwt;         // [n_kpts]: orbit size of the point under the point group (point-group mode)
+  int n_ops;              // point-group operations (0: k / -k pairing only)
+  const double* Dop;      // [n_ops][nL][nL]: real-harmonic representation of each operation
   const double* Kvec;     // [nK][3]
   const int* kK_start;    // [n_kpts + 1]
   const int* kK_idx;      // reciprocal vectors of each k with |k + K|^2 <= qmax^2
@@ -681,12 +685,19 @@ __global__ void __launch_bounds__(INV_THREADS) kkr_invert_kernel(KkrDev K, int i
         const int* sg = sigma + m * n;
         const double f = sc[m * n + i] * sc[m * n + j];
         const double2 x = Am[i * ldA + sg[j]];
-        ax += f * x.x;
-        ay += f * x.y;
-        if (K.kpair[kb + m]) {
-          const double2 y = Am[j * ldA + sg[i]];
-          ax += f * y.x;
-          ay += f * y.y;
+        if (K.n_ops > 0) {
+          // point-group mode: the point stands for its orbit (symmetrised at the end)
+          const double fw = f * double(K.kwt[kb + m]);
+          ax += fw * x.x;
+          ay += fw * x.y;
+        } else {
+          ax += f * x.x;
+          ay += f * x.y;
+          if (K.kpair[kb + m]) {
+            const double2 y = Am[j * ldA + sg[i]];
+            ax += f * y.x;
+            ay += f * y.y;
+          }
         }
       }
       acc[u] = mk(ax, ay);
@@ -702,25 +713,79 @@ __global__ void __launch_bounds__(INV_THREADS) kkr_invert_kernel(KkrDev K, int i
   if (tid == 0 && singular) atomicMax(status + it, int(MUST_ESINGULAR));
 }
 
-// tau[item][s] (column-major kap x kap) = (1/N_k) sum over groups, in order.
-__global__ void kkr_bz_sum_kernel(KkrDev K, int items, const double2* __restrict__ part, double2* __restrict__ tau,
-                                  int* __restrict__ status) {
-  const int nLL = K.nL * K.nL;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= items * K.nb * nLL) return;
-  const int it = q / (K.nb * nLL), r = q % (K.nb * nLL);
-  const int s = r / nLL, L = (r / K.nL) % K.nL, Lp = r % K.nL;
-  double sx = 0.0, sy = 0.0;
-  for (int g = 0; g < K.n_kg; ++g) {
-    const double2 v = part[(size_t(it) * K.n_kg + g) * K.nb * nLL + r];
-    sx += v.x;
-    sy += v.y;
+// tau[item][s] (column-major kap x kap) = (1/N_k) sum over groups, in order;
+// in point-group mode additionally (1/|G|) sum_g D(g) S D(g)^T, which turns
+// the orbit-weighted sum over the irreducible points into the sum over the
+// whole mesh (M(gk) = D(g) M(k) D(g)^T for a lattice with one site per cell).
+// One CTA per (item, site).
+constexpr int BZ_THREADS = 256;
+
+__global__ void __launch_bounds__(BZ_THREADS) kkr_bz_sum_kernel(KkrDev K, int items, const double2* __restrict__ part,
+                                                                double2* __restrict__ tau, int* __restrict__ status) {
+  __shared__ double2 S[25 * 25];
+  __shared__ double2 T[25 * 25];
+  const int nL = K.nL, nLL = nL * nL;
+  const int it = blockIdx.y, s = blockIdx.x, tid = threadIdx.x;
+  for (int r = tid; r < nLL; r += BZ_THREADS) {
+    double sx = 0.0, sy = 0.0;
+    for (int g = 0; g < K.n_kg; ++g) {
+      const double2 v = part[((size_t(it) * K.n_kg + g) * K.nb + s) * nLL + r];
+      sx += v.x;
+      sy += v.y;
+    }
+    S[r] = make_double2(sx, sy);
   }
-  const double w = 1.0 / double(K.n_mesh);
-  sx *= w;
-  sy *= w;
-  if (!isfinite(sx) || !isfinite(sy)) atomicMax(status + it, int(MUST_ENONFINITE));
-  tau[(size_t(it) * K.nb + s) * nLL + L + Lp * K.nL] = make_double2(sx, sy);
+  __syncthreads();
+  double scale = 1.0 / double(K.n_mesh);
+  double2 out[(25 * 25 + BZ_THREADS - 1) / BZ_THREADS];
+  constexpr int NOUT = (25 * 25 + BZ_THREADS - 1) / BZ_THREADS;
+#pragma unroll
+  for (int u = 0; u < NOUT; ++u) {
+    const int r = tid + u * BZ_THREADS;
+    out[u] = (K.n_ops > 0 || r >= nLL) ? make_double2(0.0, 0.0) : S[r];
+  }
+  if (K.n_ops > 0) {
+    scale /= double(K.n_ops);
+    for (int op = 0; op < K.n_ops; ++op) {
+      const double* D = K.Dop + size_t(op) * nLL;
+      for (int r = tid; r < nLL; r += BZ_THREADS) {   // T = D S
+        const int L = r / nL, B = r % nL;
+        double tx = 0.0, ty = 0.0;
+        for (int A = 0; A < nL; ++A) {
+          const double d = D[L * nL + A];
+          tx = fma(d, S[A * nL + B].x, tx);
+          ty = fma(d, S[A * nL + B].y, ty);
+        }
+        T[r] = make_double2(tx, ty);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < NOUT; ++u) {                  // out += T D^T
+        const int r = tid + u * BZ_THREADS;
+        if (r < nLL) {
+          const int L = r / nL, Lp = r % nL;
+          double ox = out[u].x, oy = out[u].y;
+          for (int B = 0; B < nL; ++B) {
+            const double d = D[Lp * nL + B];
+            ox = fma(T[L * nL + B].x, d, ox);
+            oy = fma(T[L * nL + B].y, d, oy);
+          }
+          out[u] = make_double2(ox, oy);
+        }
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NOUT; ++u) {
+    const int r = tid + u * BZ_THREADS;
+    if (r < nLL) {
+      const int L = r / nL, Lp = r % nL;
+      const double sx = out[u].x * scale, sy = out[u].y * scale;
+      if (!isfinite(sx) || !isfinite(sy)) atomicMax(status + it, int(MUST_ENONFINITE));
+      tau[(size_t(it) * K.nb + s) * nLL + L + Lp * nL] = make_double2(sx, sy);
+    }
+  }
 }
 
 __global__ void kkr_status_init_kernel(int items, int* status) {
@@ -775,13 +840,71 @@ void points_within(const double V[3][3], const double W[3][3], const double* c, 
       }
 }
 
+
+// Real spherical harmonics on the host (the library's basis: no Condon-Shortley
+// phase, sqrt2 cos / sin combinations), for the point-group matrices only.
+void ylm_host(int lmax, double x, double y, double z, double* out) {
+  const double r = std::sqrt(x * x + y * y + z * z);
+  const double ct = z / r, rho = std::sqrt(x * x + y * y), st = rho / r;
+  const double phi = rho > 0.0 ? std::atan2(y, x) : 0.0;
+  for (int m = 0; m <= lmax; ++m) {
+    double pmm = 1.0;
+    for (int i = 1; i <= m; ++i) pmm *= (2.0 * i - 1.0) * st;
+    double p2 = 0.0, p1 = pmm;
+    for (int l = m; l <= lmax; ++l) {
+      double pl;
+      if (l == m) pl = pmm;
+      else if (l == m + 1) pl = (2.0 * m + 1.0) * ct * pmm;
+      else pl = ((2.0 * l - 1.0) * ct * p1 - (l + m - 1.0) * p2) / double(l - m);
+      if (l > m) { p2 = p1; p1 = pl; }
+      double ratio = 1.0;
+      for (int q = l - m + 1; q <= l + m; ++q) ratio /= double(q);
+      const double N = std::sqrt((2.0 * l + 1.0) / (4.0 * kPi) * ratio);
+      if (m == 0) {
+        out[l * l + l] = N * pl;
+      } else {
+        out[l * l + l + m] = std::sqrt(2.0) * N * pl * std::cos(m * phi);
+        out[l * l + l - m] = std::sqrt(2.0) * N * pl * std::sin(m * phi);
+      }
+    }
+  }
+}
+
+// D(g)_{LM} = int Y_L(g r) Y_M(r) dOmega for l <= lmax (exact product rule:
+// Gauss-Legendre in cos theta, uniform in phi).
+void harmonic_rep(int lmax, const double g[3][3], std::vector<double>& D) {
+  const int nL = (lmax + 1) * (lmax + 1);
+  const int nt = lmax + 2, np = 2 * lmax + 3;
+  std::vector<double> xt, wt;
+  must_gauss_legendre_nodes(nt, xt, wt);
+  D.assign(size_t(nL) * nL, 0.0);
+  std::vector<double> Ya(nL), Yb(nL);
+  for (int a = 0; a < nt; ++a) {
+    const double ct = xt[a], st = std::sqrt(1.0 - ct * ct);
+    for (int b = 0; b < np; ++b) {
+      const double ph = 2.0 * kPi * b / np, w = wt[a] * 2.0 * kPi / np;
+      const double r[3] = {st * std::cos(ph), st * std::sin(ph), ct};
+      double gr[3];
+      for (int i = 0; i < 3; ++i) gr[i] = g[i][0] * r[0] + g[i][1] * r[1] + g[i][2] * r[2];
+      ylm_host(lmax, gr[0], gr[1], gr[2], Ya.data());
+      ylm_host(lmax, r[0], r[1], r[2], Yb.data());
+      for (int L = 0; L < nL; ++L)
+        for (int M = 0; M < nL; ++M) D[size_t(L) * nL + M] += w * Ya[L] * Yb[M];
+    }
+  }
+  for (double& v : D)
+    if (std::fabs(v) < 1e-14) v = 0.0;
+}
+
 }  // namespace
 
 struct must_kkr {
-  int nb, lmax, nL, l2max, nL2, n, n_k, n_kpts, n_mesh, n_disp, n_pts, n_pts0, n_K, n_kK, n_kg, device;
+  int nb, lmax, nL, l2max, nL2, n, n_k, n_kpts, n_mesh, n_disp, n_pts, n_pts0, n_K, n_kK, n_kg, n_ops, device;
   double eta, omega;
   double* d_kpts;
   int* d_kpair;
+  int* d_kwt;
+  double* d_Dop;
   double* d_K;
   int* d_kK_start;
   int* d_kK_idx;
@@ -804,7 +927,7 @@ KkrDev dev_view(const must_kkr* h) {
   K.nb = h->nb; K.lmax = h->lmax; K.nL = h->nL; K.l2max = h->l2max; K.nL2 = h->nL2; K.n = h->n;
   K.n_kpts = h->n_kpts; K.n_mesh = h->n_mesh; K.n_disp = h->n_disp; K.n_pts = h->n_pts; K.n_kg = h->n_kg;
   K.eta = h->eta; K.omega = h->omega;
-  K.kpts = h->d_kpts; K.kpair = h->d_kpair; K.Kvec = h->d_K; K.kK_start = h->d_kK_start; K.kK_idx = h->d_kK_idx;
+  K.kpts = h->d_kpts; K.kpair = h->d_kpair; K.kwt = h->d_kwt; K.n_ops = h->n_ops; K.Dop = h->d_Dop; K.Kvec = h->d_K; K.kK_start = h->d_kK_start; K.kK_idx = h->d_kK_idx;
   K.disp = h->d_disp; K.pair_disp = h->d_pair_disp; K.pt_start = h->d_pt_start; K.pt_R = h->d_pt_R;
   K.pt_rho = h->d_pt_rho; K.quad_u = h->d_quad_u; K.quad_w = h->d_quad_w;
   K.g_start = h->d_g_start; K.g_L2 = h->d_g_L2; K.g_c = h->d_g_c;
@@ -853,10 +976,11 @@ size_t staging_bytes(const must_kkr* h, int items) {
 }  // namespace
 
 extern "C" must_status must_kkr_build(const double* lattice, const double* basis, int32_t n_basis, int32_t lmax,
-                                      int32_t n_k, double eta, void* stream, must_kkr** out) {
+                                      int32_t n_k, double eta, int32_t flags, void* stream, must_kkr** out) {
   if (!out) { must_set_error("must_kkr_build: out is NULL"); return MUST_EINVAL; }
   *out = nullptr;
-  if (!lattice || !basis || n_basis < 1 || lmax < 0 || lmax > 4 || n_k < 1 || n_k > 64 || !(eta >= 0.0)) {
+  if (!lattice || !basis || n_basis < 1 || lmax < 0 || lmax > 4 || n_k < 1 || n_k > 64 || !(eta >= 0.0) ||
+      (flags & ~MUST_KKR_NO_SYMMETRY)) {
     must_set_error("must_kkr_build: bad argument (lattice/basis NULL, n_basis < 1, lmax outside 0..4, n_k outside "
                    "1..64 or eta < 0)");
     return MUST_EINVAL;
@@ -937,18 +1061,73 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
     must_set_error("must_kkr_build: %d distinct site displacements exceed %d", n_disp, KKR_MAX_DISP);
     return MUST_EINVAL;
   }
-  // Gamma-centred mesh, folded to m_i in (-n_k/2, n_k/2]; one point of each
-  // pair {m, -m mod n_k} is kept (M(-k) = M(k)^T), flagged when -m differs
+  // Point group (one site per cell only: then every lattice symmetry leaves M(k)
+  // invariant up to D(g), whatever t^-1): the signed permutations g of the
+  // Cartesian axes that map the lattice onto itself; Q_g[i][j] = (g b_i).a_j / 2 pi
+  // is their integer action on mesh coordinates.
+  std::vector<std::array<int, 9>> Qops;
+  std::vector<double> Dops;
+  if (n_basis == 1 && !(flags & MUST_KKR_NO_SYMMETRY)) {
+    const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (int pi = 0; pi < 6; ++pi)
+      for (int sg = 0; sg < 8; ++sg) {
+        double g[3][3] = {{0.0}};
+        for (int r = 0; r < 3; ++r) g[r][perms[pi][r]] = ((sg >> r) & 1) ? -1.0 : 1.0;
+        bool ok = true;
+        std::array<int, 9> Q{};
+        for (int i = 0; i < 3 && ok; ++i) {
+          double ga[3], gb[3];
+          for (int r = 0; r < 3; ++r) {
+            ga[r] = g[r][0] * A[i][0] + g[r][1] * A[i][1] + g[r][2] * A[i][2];
+            gb[r] = g[r][0] * B[i][0] + g[r][1] * B[i][1] + g[r][2] * B[i][2];
+          }
+          for (int j = 0; j < 3 && ok; ++j) {
+            const double ca = dot3(ga, B[j]) / (2.0 * kPi), cb = dot3(gb, A[j]) / (2.0 * kPi);
+            if (std::fabs(ca - std::round(ca)) > 1e-8 || std::fabs(cb - std::round(cb)) > 1e-8) ok = false;
+            Q[3 * i + j] = int(std::lround(cb));
+          }
+        }
+        if (!ok) continue;
+        Qops.push_back(Q);
+        std::vector<double> D;
+        harmonic_rep(lmax, g, D);
+        Dops.insert(Dops.end(), D.begin(), D.end());
+      }
+  }
+  const int n_ops = int(Qops.size());
+  // Gamma-centred mesh, folded to m_i in (-n_k/2, n_k/2].  Point-group mode: one
+  // point of each orbit, weighted by the orbit's size.  Otherwise one point of
+  // each pair {m, -m mod n_k} (M(-k) = M(k)^T), flagged when -m differs.
   std::vector<double> kpts;
-  std::vector<int> kpair;
+  std::vector<int> kpair, kwt;
   double kmax = 0.0;
+  std::vector<char> seen(size_t(n_k) * n_k * n_k, 0);
   for (int m1 = 0; m1 < n_k; ++m1)
     for (int m2 = 0; m2 < n_k; ++m2)
       for (int m3 = 0; m3 < n_k; ++m3) {
         const int idx = (m1 * n_k + m2) * n_k + m3;
-        const int nidx = (((n_k - m1) % n_k) * n_k + (n_k - m2) % n_k) * n_k + (n_k - m3) % n_k;
-        if (nidx < idx) continue;   // its partner is kept
-        kpair.push_back(nidx != idx ? 1 : 0);
+        if (n_ops > 0) {
+          if (seen[idx]) continue;
+          int orbit = 0;
+          const int mv[3] = {m1, m2, m3};
+          for (const auto& Q : Qops) {
+            int mm[3];
+            for (int j = 0; j < 3; ++j) {
+              long v = 0;
+              for (int i = 0; i < 3; ++i) v += long(mv[i]) * Q[3 * i + j];
+              mm[j] = int(((v % n_k) + n_k) % n_k);
+            }
+            const int id2 = (mm[0] * n_k + mm[1]) * n_k + mm[2];
+            if (!seen[id2]) { seen[id2] = 1; ++orbit; }
+          }
+          kwt.push_back(orbit);
+          kpair.push_back(0);
+        } else {
+          const int nidx = (((n_k - m1) % n_k) * n_k + (n_k - m2) % n_k) * n_k + (n_k - m3) % n_k;
+          if (nidx < idx) continue;   // its partner is kept
+          kpair.push_back(nidx != idx ? 1 : 0);
+          kwt.push_back(1);
+        }
         const int f1 = (2 * m1 > n_k) ? m1 - n_k : m1, f2 = (2 * m2 > n_k) ? m2 - n_k : m2,
                   f3 = (2 * m3 > n_k) ? m3 - n_k : m3;
         double k[3];
@@ -956,6 +1135,14 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
         kmax = std::max(kmax, norm3(k));
         kpts.insert(kpts.end(), k, k + 3);
       }
+  if (n_ops > 0) {
+    long total = 0;
+    for (int v : kwt) total += v;
+    if (total != long(n_k) * n_k * n_k) {
+      must_set_error("must_kkr_build: point-group orbits do not cover the mesh");
+      return MUST_EINVAL;
+    }
+  }
   const int n_kpts = int(kpair.size());
   // reciprocal vectors: |k + K|^2 <= eta cut + E_cap for each k
   const double qmax = std::sqrt(eta * KKR_CUT + KKR_ECAP);
@@ -1016,7 +1203,7 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
   std::memset(h, 0, sizeof(*h));
   h->nb = n_basis; h->lmax = lmax; h->nL = nL; h->l2max = l2max; h->nL2 = nL2; h->n = n_basis * nL;
   h->n_k = n_k; h->n_kpts = n_kpts; h->n_mesh = n_k * n_k * n_k; h->n_disp = n_disp; h->n_pts0 = pt_start[1]; h->n_pts = n_pts; h->n_K = n_K;
-  h->n_kK = int(kK_idx.size()); h->n_kg = (n_kpts + KKR_KG - 1) / KKR_KG;
+  h->n_kK = int(kK_idx.size()); h->n_kg = (n_kpts + KKR_KG - 1) / KKR_KG; h->n_ops = n_ops;
   h->eta = eta; h->omega = omega;
   cudaGetDevice(&h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1028,6 +1215,8 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
   };
   up(reinterpret_cast<void**>(&h->d_kpts), kpts.data(), sizeof(double) * kpts.size());
   up(reinterpret_cast<void**>(&h->d_kpair), kpair.data(), sizeof(int) * kpair.size());
+  up(reinterpret_cast<void**>(&h->d_kwt), kwt.data(), sizeof(int) * kwt.size());
+  up(reinterpret_cast<void**>(&h->d_Dop), Dops.data(), sizeof(double) * Dops.size());
   up(reinterpret_cast<void**>(&h->d_K), Kv.data(), sizeof(double) * Kv.size());
   up(reinterpret_cast<void**>(&h->d_kK_start), kK_start.data(), sizeof(int) * kK_start.size());
   up(reinterpret_cast<void**>(&h->d_kK_idx), kK_idx.data(), sizeof(int) * kK_idx.size());
@@ -1089,7 +1278,7 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
 
 extern "C" void must_kkr_free(must_kkr* h) {
   if (!h) return;
-  void* ptrs[] = {h->d_kpts, h->d_kpair, h->d_K, h->d_kK_start, h->d_kK_idx, h->d_disp, h->d_pair_disp, h->d_pt_start,
+  void* ptrs[] = {h->d_kpts, h->d_kpair, h->d_kwt, h->d_Dop, h->d_K, h->d_kK_start, h->d_kK_idx, h->d_disp, h->d_pair_disp, h->d_pt_start,
                   h->d_pt_R, h->d_pt_rho, h->d_quad_u, h->d_quad_w, h->d_g_start, h->d_g_L2, h->d_g_c};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1106,6 +1295,7 @@ extern "C" must_status must_kkr_info(const must_kkr* h, int32_t* info) {
   info[5] = h->n_kg;
   info[6] = h->n_mesh;
   info[7] = h->n_pts0;
+  info[8] = h->n_ops;
   return MUST_OK;
 }
 
@@ -1187,8 +1377,8 @@ extern "C" must_status must_kkr_tau(const must_kkr* h, int32_t n_items, const do
     ProfScope ps(PH_KKR_INVERT, st);
     dim3 g3(h->n_kg, n_items);
     kkr_invert_kernel<<<g3, INV_THREADS, invert_smem(h), st>>>(K, n_items, Ed, Td, w.Dk, w.part, w.status);
-    const int tot = n_items * h->nb * h->nL * h->nL;
-    kkr_bz_sum_kernel<<<(tot + 255) / 256, 256, 0, st>>>(K, n_items, w.part, taud, w.status);
+    dim3 g4(h->nb, n_items);
+    kkr_bz_sum_kernel<<<g4, BZ_THREADS, 0, st>>>(K, n_items, w.part, taud, w.status);
     prof_launched(PH_KKR_INVERT, 2, n_items);
   }
   if (std_) {

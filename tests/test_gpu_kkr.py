@@ -55,6 +55,32 @@ def _gpu(B, c, E, ti, n_k=None, host=False, status_out=False):
     return np.swapaxes(tau, -1, -2), st, h
 
 
+def _orbit_count(lattice, n_k):
+    """Orbits of the Gamma-centred n_k^3 mesh under the 48 signed axis
+    permutations, counted in numpy (independent of the library's host code)."""
+    import itertools
+    B = 2 * np.pi * np.linalg.inv(np.asarray(lattice, float)).T     # rows: reciprocal vectors
+    m = np.array(list(itertools.product(range(n_k), repeat=3)))
+    seen, orbits = set(), 0
+    ops = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            g = np.zeros((3, 3))
+            for r in range(3):
+                g[r, perm[r]] = signs[r]
+            ops.append(g)
+    for mv in m:
+        key = tuple(mv)
+        if key in seen:
+            continue
+        orbits += 1
+        k = (mv / n_k) @ B
+        for g in ops:
+            f = np.asarray(lattice) @ (g @ k) / (2 * np.pi) * n_k      # mesh coordinates of g k
+            seen.add(tuple(int(round(x)) % n_k for x in f))
+    return orbits
+
+
 def _check(orc, c, E, ti, got, st, h):
     ref, _ = orc.kkr_tau(c.lmax, c.lattice, c.basis, E, ti, c.n_k, h.eta)
     assert (st == 0).all(), st
@@ -69,7 +95,8 @@ def test_kkr_fcc_primitive_vs_oracle(B, orc):
     picks = [(0, 0), (1, 0), (0, 5), (1, 16), (0, nE - 1)]
     E, ti = _items(orc, c, picks)
     got, st, h = _gpu(B, c, E, ti)
-    assert h.n == 16 and h.n_mesh == 216 and h.n_kpts == (216 + 8) // 2   # k and -k paired
+    assert h.n == 16 and h.n_mesh == 216 and h.n_ops == 48
+    assert h.n_kpts == _orbit_count(c.lattice, 6)        # one point per orbit of the cubic group
     _check(orc, c, E, ti, got, st, h)
 
 
@@ -148,3 +175,24 @@ def test_lsms_tau00_converges_to_the_crystal_tau_on_the_gpu(B):
             tk = np.swapaxes(out.cpu().numpy(), -1, -2)[0, 0]
         errs.append(np.linalg.norm(tl - tk) / np.linalg.norm(tk))
     assert errs[1] < 1e-6 and errs[0] > 10 * errs[1], errs
+
+
+@pytest.mark.parametrize("lmax,n_k", [(3, 6), (4, 4), (2, 5)])
+def test_kkr_point_group_reduction_equals_the_full_mesh(B, orc, lmax, n_k):
+    """One site per cell: inverting one point per orbit of the cubic group and
+    symmetrising with the real-harmonic representation gives the same tau as
+    the k / -k paired mesh (odd and even meshes, up to lmax 4)."""
+    c = wl.fcc_crystal(lmax=lmax, n_k=n_k)
+    E, ti = _items(orc, c, [(0, 0), (1, 9), (0, 31)])
+    a, sa, ha = _gpu(B, c, E, ti)
+    import torch
+    hb = B.must_kkr_build(c.lattice, c.basis, lmax, n_k, flags=B.MUST_KKR_NO_SYMMETRY)
+    assert ha.n_ops == 48 and hb.n_ops == 0 and ha.n_kpts < hb.n_kpts
+    ws = torch.empty(B.must_kkr_workspace_bytes(hb, len(E)), dtype=torch.uint8, device="cuda")
+    tau = torch.zeros((len(E), 1, hb.kap, hb.kap), dtype=torch.complex128, device="cuda")
+    B.must_kkr_tau(hb, torch.from_numpy(E).cuda(), torch.from_numpy(np.ascontiguousarray(ti)).cuda(), ws, tau)
+    torch.cuda.synchronize()
+    b = np.swapaxes(tau.cpu().numpy(), -1, -2)
+    assert (sa == 0).all()
+    err = rel_fro(a, b)
+    assert err.max() <= 1e-12, err
