@@ -29,14 +29,21 @@
 // u = 0 for near-neighbour rho and small eta, which a Gauss-Laguerre rule
 // resolves only to ~1e-11; the graded panels reach ~1e-15).
 //
+// Only part of the mesh is evaluated: with one site per cell one point per
+// orbit of the lattice's point group (the sum symmetrised at the end with the
+// real-harmonic representation D(g), M(gk) = D(g) M(k) D(g)^T); otherwise one
+// point of each pair {k, -k} (M(-k) = M(k)^T, its blocks added transposed).
+//
 // Kernels (all FP64):
 //   kkr_real_terms_kernel  per (item, real-space point): the k-independent factor of B_L
-//   kkr_recip_kernel       per (item, k): A_L + C_L for every distinct displacement x
-//   kkr_realsum_kernel     per (item, displacement, 32 k points): adds B_L
-//   kkr_invert_kernel      per (item, group of k points): M(k) by the Gaunt contraction in
-//                          shared memory, equilibrated, Gauss-Jordan with partial pivoting,
-//                          diagonal blocks of M(k)^{-1} summed over the group in a fixed order
-//   kkr_bz_sum_kernel      per output element: the groups summed in a fixed order, / N_k
+//   kkr_recip_kernel       per (item, k): A_L + C_L for every displacement (x and -x paired)
+//   kkr_realsum_kernel     per (item, displacement group, 32 k points): adds B_L
+//   kkr_invert_kernel      per (item, group of 8 k points): M(k) by the Gaunt contraction,
+//                          equilibrated, in-place Gauss-Jordan with partial pivoting in
+//                          shared memory (up to 8 small M(k) side by side), diagonal blocks
+//                          of M(k)^{-1} summed over the group in a fixed order
+//   kkr_bz_sum_kernel      per (item, site): the groups summed in a fixed order, / N_k,
+//                          symmetrised over the point group when it is used
 #include <algorithm>
 #include <array>
 #include <cmath>
