@@ -1068,7 +1068,7 @@ def run_kkr(args):
         if args.kkr_eta_scale != 1.0:
             # a multiple of 4 pi / Omega^(2/3) (the library's default is 1.0 of it, 0.7 with one site)
             eta = args.kkr_eta_scale * 4.0 * np.pi / abs(np.linalg.det(c.lattice)) ** (2.0 / 3.0)
-        h = B.must_kkr_build(c.lattice, c.basis, c.lmax, c.n_k, eta=eta)
+        h = B.must_kkr_build(c.lattice, c.basis, c.lmax, c.n_k, eta=eta, site_class=c.species)
         nE = len(c.energies)
         picks = [(sp, e) for sp in range(c.nspin) for e in range(nE)]
         items = len(picks)
@@ -1153,7 +1153,7 @@ def run_kkr(args):
         results[c.name] = {
             "value": items / (ms / 1e3), "unit": "tau solves/s (all sites of the cell per (E, spin))",
             "ms_per_step": ms, "items_per_step": items, "n": h.n, "k_points": h.n_mesh,
-            "k_points_evaluated": h.n_kpts,
+            "k_points_evaluated": h.n_kpts, "point_group_ops": h.n_ops,
             "inversions_per_s": items * h.n_kpts / (ms / 1e3),
             "gpu_launches": launches, "kernels": kern,
             "roofline": {"kernel_phase": dom, "bound": "alu", "unit": "TFLOP/s",

@@ -419,20 +419,25 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * (items above it get MUST_EUNSUPPORTED in their status).  Everything is FP64.
  *
  * must_kkr_build: lattice: 3 x 3 row-major, rows a_1, a_2, a_3 (bohr); basis:
- * n_basis x 3 site positions (bohr), distinct modulo the lattice; lmax in
+ * n_basis x 3 site positions (bohr), distinct modulo the lattice; site_class:
+ * n_basis ints or NULL -- sites of one class are promised equal t^-1 in every
+ * call (must_kkr_tau checks it and flags an item that breaks it with
+ * MUST_EINVAL in its status); NULL makes every site its own class; lmax in
  * [0, 4] with n_basis (lmax+1)^2 <= 64 (one M(k) is inverted in one CTA's
  * shared memory) and at most 32 distinct site displacements b_s - b_t; n_k in
  * [1, 64]; eta: Ewald splitting parameter (bohr^-2), 0 = 4 pi / Omega^(2/3)
  * (0.7 of that with one site per cell), which keeps the two sums about equally
  * costly; the result does not depend on it, but below ~0.4 of that value the
- * factor e^{E/eta} starts to cost digits.  flags: 0, or MUST_KKR_NO_SYMMETRY.  With one site per
- * cell and flags 0 the lattice's point group (the signed permutations of the
- * Cartesian axes that map the lattice onto itself, 48 for cubic lattices) is
- * used: M(gk) = D(g) M(k) D(g)^T with D(g) the real-harmonic representation of
- * g, so one point of each orbit of the mesh is inverted, weighted by the orbit's
- * size, and the sum is symmetrised, (1/|G|) sum_g D(g) S D(g)^T.  Otherwise
- * (several sites, whose symmetry depends on their t^-1, or the flag) one point
- * of each pair {k, -k} is evaluated.  Host arrays,
+ * factor e^{E/eta} starts to cost digits.  flags: 0, or MUST_KKR_NO_SYMMETRY.  With flags 0 the
+ * crystal's point group is used: the signed permutations g of the Cartesian
+ * axes that map the lattice onto itself and each site onto a site of its class
+ * (48 for the fcc lattice with one site, or the L1_2 cell with the corner in a
+ * class of its own).  The diagonal blocks obey [M(gk)^{-1}]^{ss} = D(g)
+ * [M(k)^{-1}]^{tt} D(g)^T, g b_t = b_s, with D(g) the real-harmonic
+ * representation of g, so one point of each orbit of the mesh is inverted,
+ * weighted by the orbit's size, and the sum is symmetrised,
+ * tau^s = (1/|G|) sum_g D(g) S^{t} D(g)^T.  With the flag, or when only the
+ * identity qualifies, one point of each pair {k, -k} is evaluated.  Host arrays,
  * read during the call.  Builds the k mesh, the reciprocal and real-space
  * vector lists and the Gaunt table on the device (synchronises `stream`).
  * Errors: MUST_EINVAL, MUST_ENOMEM, MUST_ECUDA.
@@ -460,8 +465,8 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  */
 typedef struct must_kkr must_kkr;
 #define MUST_KKR_NO_SYMMETRY 1   /* flags: evaluate one point of each {k, -k} pair only */
-must_status must_kkr_build(const double* lattice, const double* basis, int32_t n_basis, int32_t lmax, int32_t n_k,
-                           double eta, int32_t flags, void* stream, must_kkr** out);
+must_status must_kkr_build(const double* lattice, const double* basis, const int32_t* site_class, int32_t n_basis,
+                           int32_t lmax, int32_t n_k, double eta, int32_t flags, void* stream, must_kkr** out);
 void must_kkr_free(must_kkr* kkr);
 size_t must_kkr_workspace_bytes(const must_kkr* kkr, int32_t n_items);
 must_status must_kkr_tau(const must_kkr* kkr, int32_t n_items, const double* E, const double* tinv,

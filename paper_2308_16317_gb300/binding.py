@@ -80,7 +80,7 @@ def load():
         "must_site_charge": (I32, [I32, I32, P, P, I32, P, D, P, P, P, P]),
         "must_site_density": (I32, [I32, I32, P, P, I32, P, D, P, I32, P, P, P]),
         "must_static_scratch_bytes": (SZ, []),
-        "must_kkr_build": (I32, [P, P, I32, I32, I32, D, I32, P, ctypes.POINTER(P)]),
+        "must_kkr_build": (I32, [P, P, P, I32, I32, I32, D, I32, P, ctypes.POINTER(P)]),
         "must_kkr_free": (None, [P]),
         "must_kkr_workspace_bytes": (SZ, [P, I32]),
         "must_kkr_tau": (I32, [P, I32, P, P, P, SZ, P, P, P]),
@@ -409,7 +409,7 @@ class Kkr:
         self.handle = handle
         self.n_basis, self.lmax = n_basis, lmax
         self.kap = (lmax + 1) ** 2
-        info = np.zeros(9, np.int32)
+        info = np.zeros(9, np.int32)   # see must_kkr_info
         _check(load().must_kkr_info(handle, _ptr(info)))
         (self.n, self.n_kpts, self.n_disp, self.n_pts, self.n_kK, self.n_kg, self.n_mesh,
          self.n_pts0, self.n_ops) = (int(v) for v in info)
@@ -424,12 +424,14 @@ class Kkr:
 MUST_KKR_NO_SYMMETRY = 1
 
 
-def must_kkr_build(lattice, basis, lmax: int, n_k: int, eta: float = 0.0, flags: int = 0, stream=None) -> Kkr:
+def must_kkr_build(lattice, basis, lmax: int, n_k: int, eta: float = 0.0, flags: int = 0, site_class=None,
+                   stream=None) -> Kkr:
     lat = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(3, 3))
     bas = np.ascontiguousarray(np.asarray(basis, dtype=np.float64).reshape(-1, 3))
+    cls = None if site_class is None else np.ascontiguousarray(np.asarray(site_class, dtype=np.int32))
     out = ctypes.c_void_p()
-    _check(load().must_kkr_build(_ptr(lat), _ptr(bas), int(bas.shape[0]), int(lmax), int(n_k), float(eta),
-                                 int(flags), _stream(stream), ctypes.byref(out)))
+    _check(load().must_kkr_build(_ptr(lat), _ptr(bas), _ptr(cls), int(bas.shape[0]), int(lmax), int(n_k),
+                                 float(eta), int(flags), _stream(stream), ctypes.byref(out)))
     return Kkr(out, int(bas.shape[0]), int(lmax))
 
 

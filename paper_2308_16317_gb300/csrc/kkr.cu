@@ -29,21 +29,22 @@
 // u = 0 for near-neighbour rho and small eta, which a Gauss-Laguerre rule
 // resolves only to ~1e-11; the graded panels reach ~1e-15).
 //
-// Only part of the mesh is evaluated: with one site per cell one point per
-// orbit of the lattice's point group (the sum symmetrised at the end with the
-// real-harmonic representation D(g), M(gk) = D(g) M(k) D(g)^T); otherwise one
-// point of each pair {k, -k} (M(-k) = M(k)^T, its blocks added transposed).
+// Only part of the mesh is evaluated: one point per orbit of the crystal's
+// point group (operations that map each site onto a site of its class; the sum
+// symmetrised at the end with the real-harmonic representation D(g)), or, when
+// only the identity qualifies, one point of each pair {k, -k} (M(-k) = M(k)^T,
+// its blocks added transposed).
 //
 // Kernels (all FP64):
 //   kkr_real_terms_kernel  per (item, real-space point): the k-independent factor of B_L
 //   kkr_recip_kernel       per (item, k): A_L + C_L for every displacement (x and -x paired)
 //   kkr_realsum_kernel     per (item, displacement group, 32 k points): adds B_L
-//   kkr_invert_kernel      per (item, group of 8 k points): M(k) by the Gaunt contraction,
+//   kkr_invert_kernel      per (item, group of <= 8 k points): M(k) by the Gaunt contraction,
 //                          equilibrated, in-place Gauss-Jordan with partial pivoting in
 //                          shared memory (up to 8 small M(k) side by side), diagonal blocks
 //                          of M(k)^{-1} summed over the group in a fixed order
-//   kkr_bz_sum_kernel      per (item, site): the groups summed in a fixed order, / N_k,
-//                          symmetrised over the point group when it is used
+//   kkr_bz_sum_kernel      per output element: the groups summed in a fixed order, / N_k
+//   kkr_symmetrise_kernel  per (site, item), point-group mode: (1/|G|) sum_g D(g) S^{t_g(s)} D(g)^T
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -69,7 +70,7 @@ constexpr int KKR_QUAD = 112;          // quadrature nodes for I_l (7 panels x 1
 constexpr int KKR_KCHUNK = 64;         // reciprocal vectors per shared-memory chunk
 constexpr int KKR_KB = 32;             // k points per real-space block
 constexpr int KKR_RCHUNK = 32;         // real-space points per chunk
-constexpr int KKR_KG = 8;              // k points per inversion CTA
+constexpr int KKR_KG_MAX = 8;          // most k points per inversion CTA
 constexpr double KKR_CUT = 40.0;       // both sums cut where their Gaussian factor < e^{-cut}
 constexpr double KKR_ECAP = 1.5;       // sums are cut for Re E <= KKR_ECAP (Ry)
 
@@ -145,6 +146,7 @@ __device__ __forceinline__ cd ipow_d(int l) {
 
 struct KkrDev {
   int nb, lmax, nL, l2max, nL2, n, n_kpts, n_disp, n_pts, n_kg;
+  int kg;                 // k points per inversion CTA (a multiple of the matrices per pass)
   int n_mesh;             // n_k^3: the mesh the average is taken over
   double eta, omega;
   const double* kpts;     // [n_kpts][3]: one point of each pair {k, -k} of the mesh
@@ -152,6 +154,8 @@ struct KkrDev {
   const int* kwt;         // [n_kpts]: orbit size of the point under the point group (point-group mode)
   int n_ops;              // point-group operations (0: k / -k pairing only)
   const double* Dop;      // [n_ops][nL][nL]: real-harmonic representation of each operation
+  const int* op_src;      // [n_ops][nb]: site t with g b_t = b_s (mod lattice), for each site s
+  const int* site_class;  // [nb]: sites of one class carry equal t^-1 (checked per item)
   const double* Kvec;     // [nK][3]
   const int* kK_start;    // [n_kpts + 1]
   const int* kK_idx;      // reciprocal vectors of each k with |k + K|^2 <= qmax^2
@@ -478,7 +482,7 @@ __global__ void __launch_bounds__(RSUM_THREADS) kkr_realsum_kernel(KkrDev K, int
 
 // -------------------------------------------------------------------------
 // M(k) = t^{-1} - G(k) in shared memory, inverted in place; the diagonal
-// blocks of M(k)^{-1} of KKR_KG k points summed in order into
+// blocks of M(k)^{-1} of K.kg k points summed in order into
 //   part[item][group][s][L][L'].
 // NM matrices (NM = kkr_matrices_per_pass(n): 1 at n = 64, up to 8 for n <= 22)
 // are factored side by side so that small orders still fill the CTA: warp m
@@ -534,7 +538,7 @@ __global__ void __launch_bounds__(INV_THREADS) kkr_invert_kernel(KkrDev K, int i
   for (int u = 0; u < INV_ACC; ++u) acc[u] = mk(0.0, 0.0);
   if (tid == 0) singular = 0;
   __syncthreads();
-  const int kbeg = g * KKR_KG, kend = min(K.n_kpts, kbeg + KKR_KG);
+  const int kbeg = g * K.kg, kend = min(K.n_kpts, kbeg + K.kg);
   for (int kb = kbeg; kb < kend; kb += NM) {
     const int nm = min(NM, kend - kb);
     // A = t^{-1} - G, G_{LL'} = sum_{L''} c f_{l''} D_{L''} (D read from the lattice sums)
@@ -720,77 +724,103 @@ __global__ void __launch_bounds__(INV_THREADS) kkr_invert_kernel(KkrDev K, int i
   if (tid == 0 && singular) atomicMax(status + it, int(MUST_ESINGULAR));
 }
 
-// tau[item][s] (column-major kap x kap) = (1/N_k) sum over groups, in order;
-// in point-group mode additionally (1/|G|) sum_g D(g) S D(g)^T, which turns
-// the orbit-weighted sum over the irreducible points into the sum over the
-// whole mesh (M(gk) = D(g) M(k) D(g)^T for a lattice with one site per cell).
-// One CTA per (item, site).
-constexpr int BZ_THREADS = 256;
+// Sum of the k groups in a fixed order, / N_k: written as tau[item][s]
+// (column-major kap x kap), or, in point-group mode, as the orbit-weighted sum
+// S[item][s] (row-major) that kkr_symmetrise_kernel turns into tau.
+__global__ void kkr_bz_sum_kernel(KkrDev K, int items, const double2* __restrict__ part, double2* __restrict__ tau,
+                                  double2* __restrict__ S, int* __restrict__ status) {
+  const int nLL = K.nL * K.nL;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= items * K.nb * nLL) return;
+  const int it = q / (K.nb * nLL), r = q % (K.nb * nLL);
+  const int s = r / nLL, L = (r / K.nL) % K.nL, Lp = r % K.nL;
+  double sx = 0.0, sy = 0.0;
+  for (int g = 0; g < K.n_kg; ++g) {
+    const double2 v = part[(size_t(it) * K.n_kg + g) * K.nb * nLL + r];
+    sx += v.x;
+    sy += v.y;
+  }
+  const double w = 1.0 / double(K.n_mesh);
+  sx *= w;
+  sy *= w;
+  if (!isfinite(sx) || !isfinite(sy)) atomicMax(status + it, int(MUST_ENONFINITE));
+  if (K.n_ops > 0) S[size_t(it) * K.nb * nLL + r] = make_double2(sx, sy);
+  else tau[(size_t(it) * K.nb + s) * nLL + L + Lp * K.nL] = make_double2(sx, sy);
+}
 
-__global__ void __launch_bounds__(BZ_THREADS) kkr_bz_sum_kernel(KkrDev K, int items, const double2* __restrict__ part,
-                                                                double2* __restrict__ tau, int* __restrict__ status) {
-  __shared__ double2 S[25 * 25];
+// Point-group mode: tau^{s} = (1/|G|) sum_g D(g) S^{t_g(s)} D(g)^T, t_g(s) the site
+// that g carries onto s ([M(gk)^{-1}]^{ss'} blocks of sites related by g are
+// D(g) [M(k)^{-1}]^{tt} D(g)^T: the Bloch phases of the permutation cancel on the
+// diagonal).  Also checks, per item, that sites of one class carry equal t^-1.
+// One CTA per (site, item).
+constexpr int SYM_THREADS = 256;
+constexpr int SYM_OUT = (25 * 25 + SYM_THREADS - 1) / SYM_THREADS;
+
+__global__ void __launch_bounds__(SYM_THREADS) kkr_symmetrise_kernel(KkrDev K, int items,
+                                                                      const double2* __restrict__ S,
+                                                                      const double2* __restrict__ tinv,
+                                                                      double2* __restrict__ tau,
+                                                                      int* __restrict__ status) {
+  __shared__ double2 Ssrc[25 * 25];
   __shared__ double2 T[25 * 25];
   const int nL = K.nL, nLL = nL * nL;
-  const int it = blockIdx.y, s = blockIdx.x, tid = threadIdx.x;
-  for (int r = tid; r < nLL; r += BZ_THREADS) {
-    double sx = 0.0, sy = 0.0;
-    for (int g = 0; g < K.n_kg; ++g) {
-      const double2 v = part[((size_t(it) * K.n_kg + g) * K.nb + s) * nLL + r];
-      sx += v.x;
-      sy += v.y;
-    }
-    S[r] = make_double2(sx, sy);
-  }
-  __syncthreads();
-  double scale = 1.0 / double(K.n_mesh);
-  double2 out[(25 * 25 + BZ_THREADS - 1) / BZ_THREADS];
-  constexpr int NOUT = (25 * 25 + BZ_THREADS - 1) / BZ_THREADS;
-#pragma unroll
-  for (int u = 0; u < NOUT; ++u) {
-    const int r = tid + u * BZ_THREADS;
-    out[u] = (K.n_ops > 0 || r >= nLL) ? make_double2(0.0, 0.0) : S[r];
-  }
-  if (K.n_ops > 0) {
-    scale /= double(K.n_ops);
-    for (int op = 0; op < K.n_ops; ++op) {
-      const double* D = K.Dop + size_t(op) * nLL;
-      for (int r = tid; r < nLL; r += BZ_THREADS) {   // T = D S
-        const int L = r / nL, B = r % nL;
-        double tx = 0.0, ty = 0.0;
-        for (int A = 0; A < nL; ++A) {
-          const double d = D[L * nL + A];
-          tx = fma(d, S[A * nL + B].x, tx);
-          ty = fma(d, S[A * nL + B].y, ty);
-        }
-        T[r] = make_double2(tx, ty);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < NOUT; ++u) {                  // out += T D^T
-        const int r = tid + u * BZ_THREADS;
-        if (r < nLL) {
-          const int L = r / nL, Lp = r % nL;
-          double ox = out[u].x, oy = out[u].y;
-          for (int B = 0; B < nL; ++B) {
-            const double d = D[Lp * nL + B];
-            ox = fma(T[L * nL + B].x, d, ox);
-            oy = fma(T[L * nL + B].y, d, oy);
+  const int s = blockIdx.x, it = blockIdx.y, tid = threadIdx.x;
+  if (s == 0 && tid == 0) {
+    // the promise the symmetry rests on: equal t^-1 within each class
+    bool ok = true;
+    for (int a = 0; a < K.nb; ++a)
+      for (int b2 = a + 1; b2 < K.nb; ++b2)
+        if (K.site_class[a] == K.site_class[b2])
+          for (int l = 0; l <= K.lmax; ++l) {
+            const double2 x = tinv[(size_t(it) * K.nb + a) * (K.lmax + 1) + l];
+            const double2 y = tinv[(size_t(it) * K.nb + b2) * (K.lmax + 1) + l];
+            if (x.x != y.x || x.y != y.y) ok = false;
           }
-          out[u] = make_double2(ox, oy);
-        }
-      }
-      __syncthreads();
-    }
+    if (!ok) atomicMax(status + it, int(MUST_EINVAL));
   }
+  double2 out[SYM_OUT];
 #pragma unroll
-  for (int u = 0; u < NOUT; ++u) {
-    const int r = tid + u * BZ_THREADS;
+  for (int u = 0; u < SYM_OUT; ++u) out[u] = make_double2(0.0, 0.0);
+  for (int op = 0; op < K.n_ops; ++op) {
+    const int t = K.op_src[op * K.nb + s];
+    const double2* St = S + (size_t(it) * K.nb + t) * nLL;
+    for (int r = tid; r < nLL; r += SYM_THREADS) Ssrc[r] = St[r];
+    __syncthreads();
+    const double* D = K.Dop + size_t(op) * nLL;
+    for (int r = tid; r < nLL; r += SYM_THREADS) {   // T = D S
+      const int L = r / nL, B = r % nL;
+      double tx = 0.0, ty = 0.0;
+      for (int A = 0; A < nL; ++A) {
+        const double d = D[L * nL + A];
+        tx = fma(d, Ssrc[A * nL + B].x, tx);
+        ty = fma(d, Ssrc[A * nL + B].y, ty);
+      }
+      T[r] = make_double2(tx, ty);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < SYM_OUT; ++u) {              // out += T D^T
+      const int r = tid + u * SYM_THREADS;
+      if (r < nLL) {
+        const int L = r / nL, Lp = r % nL;
+        double ox = out[u].x, oy = out[u].y;
+        for (int B = 0; B < nL; ++B) {
+          const double d = D[Lp * nL + B];
+          ox = fma(T[L * nL + B].x, d, ox);
+          oy = fma(T[L * nL + B].y, d, oy);
+        }
+        out[u] = make_double2(ox, oy);
+      }
+    }
+    __syncthreads();
+  }
+  const double scale = 1.0 / double(K.n_ops);
+#pragma unroll
+  for (int u = 0; u < SYM_OUT; ++u) {
+    const int r = tid + u * SYM_THREADS;
     if (r < nLL) {
       const int L = r / nL, Lp = r % nL;
-      const double sx = out[u].x * scale, sy = out[u].y * scale;
-      if (!isfinite(sx) || !isfinite(sy)) atomicMax(status + it, int(MUST_ENONFINITE));
-      tau[(size_t(it) * K.nb + s) * nLL + L + Lp * nL] = make_double2(sx, sy);
+      tau[(size_t(it) * K.nb + s) * nLL + L + Lp * nL] = make_double2(out[u].x * scale, out[u].y * scale);
     }
   }
 }
@@ -906,12 +936,14 @@ void harmonic_rep(int lmax, const double g[3][3], std::vector<double>& D) {
 }  // namespace
 
 struct must_kkr {
-  int nb, lmax, nL, l2max, nL2, n, n_k, n_kpts, n_mesh, n_disp, n_pts, n_pts0, n_K, n_kK, n_kg, n_ops, device;
+  int nb, lmax, nL, l2max, nL2, n, n_k, n_kpts, n_mesh, n_disp, n_pts, n_pts0, n_K, n_kK, n_kg, kg, n_ops, device;
   double eta, omega;
   double* d_kpts;
   int* d_kpair;
   int* d_kwt;
   double* d_Dop;
+  int* d_op_src;
+  int* d_class;
   double* d_K;
   int* d_kK_start;
   int* d_kK_idx;
@@ -932,9 +964,9 @@ namespace {
 KkrDev dev_view(const must_kkr* h) {
   KkrDev K;
   K.nb = h->nb; K.lmax = h->lmax; K.nL = h->nL; K.l2max = h->l2max; K.nL2 = h->nL2; K.n = h->n;
-  K.n_kpts = h->n_kpts; K.n_mesh = h->n_mesh; K.n_disp = h->n_disp; K.n_pts = h->n_pts; K.n_kg = h->n_kg;
+  K.n_kpts = h->n_kpts; K.n_mesh = h->n_mesh; K.n_disp = h->n_disp; K.n_pts = h->n_pts; K.n_kg = h->n_kg; K.kg = h->kg;
   K.eta = h->eta; K.omega = h->omega;
-  K.kpts = h->d_kpts; K.kpair = h->d_kpair; K.kwt = h->d_kwt; K.n_ops = h->n_ops; K.Dop = h->d_Dop; K.Kvec = h->d_K; K.kK_start = h->d_kK_start; K.kK_idx = h->d_kK_idx;
+  K.kpts = h->d_kpts; K.kpair = h->d_kpair; K.kwt = h->d_kwt; K.n_ops = h->n_ops; K.Dop = h->d_Dop; K.op_src = h->d_op_src; K.site_class = h->d_class; K.Kvec = h->d_K; K.kK_start = h->d_kK_start; K.kK_idx = h->d_kK_idx;
   K.disp = h->d_disp; K.pair_disp = h->d_pair_disp; K.pt_start = h->d_pt_start; K.pt_R = h->d_pt_R;
   K.pt_rho = h->d_pt_rho; K.quad_u = h->d_quad_u; K.quad_w = h->d_quad_w;
   K.g_start = h->d_g_start; K.g_L2 = h->d_g_L2; K.g_c = h->d_g_c;
@@ -959,6 +991,7 @@ struct KkrWs {
   double2* T;
   double2* Dk;
   double2* part;
+  double2* S;
   int* status;
   size_t bytes;
 };
@@ -970,6 +1003,7 @@ KkrWs carve(const must_kkr* h, int items, char* base) {
   w.T = reinterpret_cast<double2*>(take(sizeof(double2) * size_t(items) * h->n_pts * h->nL2));
   w.Dk = reinterpret_cast<double2*>(take(sizeof(double2) * size_t(items) * h->n_kpts * h->n_disp * h->nL2));
   w.part = reinterpret_cast<double2*>(take(sizeof(double2) * size_t(items) * h->n_kg * h->nb * h->nL * h->nL));
+  w.S = reinterpret_cast<double2*>(take(sizeof(double2) * size_t(items) * h->nb * h->nL * h->nL));
   w.status = reinterpret_cast<int*>(take(sizeof(int) * size_t(items)));
   w.bytes = off;
   return w;
@@ -982,8 +1016,9 @@ size_t staging_bytes(const must_kkr* h, int items) {
 
 }  // namespace
 
-extern "C" must_status must_kkr_build(const double* lattice, const double* basis, int32_t n_basis, int32_t lmax,
-                                      int32_t n_k, double eta, int32_t flags, void* stream, must_kkr** out) {
+extern "C" must_status must_kkr_build(const double* lattice, const double* basis, const int32_t* site_class,
+                                      int32_t n_basis, int32_t lmax, int32_t n_k, double eta, int32_t flags,
+                                      void* stream, must_kkr** out) {
   if (!out) { must_set_error("must_kkr_build: out is NULL"); return MUST_EINVAL; }
   *out = nullptr;
   if (!lattice || !basis || n_basis < 1 || lmax < 0 || lmax > 4 || n_k < 1 || n_k > 64 || !(eta >= 0.0) ||
@@ -1068,13 +1103,18 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
     must_set_error("must_kkr_build: %d distinct site displacements exceed %d", n_disp, KKR_MAX_DISP);
     return MUST_EINVAL;
   }
-  // Point group (one site per cell only: then every lattice symmetry leaves M(k)
-  // invariant up to D(g), whatever t^-1): the signed permutations g of the
-  // Cartesian axes that map the lattice onto itself; Q_g[i][j] = (g b_i).a_j / 2 pi
-  // is their integer action on mesh coordinates.
+  // Point group: the signed permutations g of the Cartesian axes that map the
+  // lattice onto itself and every site onto a site of its class (modulo the
+  // lattice); sites of one class are promised equal t^-1 (checked per item).
+  // Without classes every site is its own class.  Q_g[i][j] = (g b*_i).a_j / 2 pi
+  // is g's integer action on mesh coordinates; src_g[s] the site t with
+  // g b_t = b_s (mod lattice).
+  std::vector<int> cls(n_basis);
+  for (int i = 0; i < n_basis; ++i) cls[i] = site_class ? site_class[i] : i;
   std::vector<std::array<int, 9>> Qops;
   std::vector<double> Dops;
-  if (n_basis == 1 && !(flags & MUST_KKR_NO_SYMMETRY)) {
+  std::vector<int> src_ops;
+  if (!(flags & MUST_KKR_NO_SYMMETRY)) {
     const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
     for (int pi = 0; pi < 6; ++pi)
       for (int sg = 0; sg < 8; ++sg) {
@@ -1094,13 +1134,33 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
             Q[3 * i + j] = int(std::lround(cb));
           }
         }
+        std::vector<int> src(n_basis, -1);
+        for (int t = 0; t < n_basis && ok; ++t) {
+          double gbt[3];
+          for (int r = 0; r < 3; ++r)
+            gbt[r] = g[r][0] * basis[3 * t] + g[r][1] * basis[3 * t + 1] + g[r][2] * basis[3 * t + 2];
+          int hit = -1;
+          for (int u = 0; u < n_basis && hit < 0; ++u) {
+            const double d[3] = {gbt[0] - basis[3 * u], gbt[1] - basis[3 * u + 1], gbt[2] - basis[3 * u + 2]};
+            bool lat = true;
+            for (int j = 0; j < 3; ++j) {
+              const double f = dot3(d, B[j]) / (2.0 * kPi);
+              if (std::fabs(f - std::round(f)) > 1e-8) lat = false;
+            }
+            if (lat) hit = u;
+          }
+          if (hit < 0 || cls[hit] != cls[t] || src[hit] >= 0) ok = false;
+          else src[hit] = t;
+        }
         if (!ok) continue;
         Qops.push_back(Q);
+        src_ops.insert(src_ops.end(), src.begin(), src.end());
         std::vector<double> D;
         harmonic_rep(lmax, g, D);
         Dops.insert(Dops.end(), D.begin(), D.end());
       }
   }
+  if (Qops.size() <= 1) { Qops.clear(); Dops.clear(); src_ops.clear(); }   // identity only: k / -k pairing
   const int n_ops = int(Qops.size());
   // Gamma-centred mesh, folded to m_i in (-n_k/2, n_k/2].  Point-group mode: one
   // point of each orbit, weighted by the orbit's size.  Otherwise one point of
@@ -1210,7 +1270,15 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
   std::memset(h, 0, sizeof(*h));
   h->nb = n_basis; h->lmax = lmax; h->nL = nL; h->l2max = l2max; h->nL2 = nL2; h->n = n_basis * nL;
   h->n_k = n_k; h->n_kpts = n_kpts; h->n_mesh = n_k * n_k * n_k; h->n_disp = n_disp; h->n_pts0 = pt_start[1]; h->n_pts = n_pts; h->n_K = n_K;
-  h->n_kK = int(kK_idx.size()); h->n_kg = (n_kpts + KKR_KG - 1) / KKR_KG; h->n_ops = n_ops;
+  {
+    // k points per inversion CTA: whole passes of side-by-side matrices, at most
+    // KKR_KG_MAX, and few enough that small (symmetry-reduced) meshes still give
+    // each item ~32 CTAs
+    const int nm = kkr_matrices_per_pass(n_basis * nL);
+    const int want = nm * ((n_kpts + 32 * nm - 1) / (32 * nm));
+    h->kg = std::max(nm, std::min(std::max(KKR_KG_MAX, nm), want));
+  }
+  h->n_kK = int(kK_idx.size()); h->n_kg = (n_kpts + h->kg - 1) / h->kg; h->n_ops = n_ops;
   h->eta = eta; h->omega = omega;
   cudaGetDevice(&h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1224,6 +1292,8 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
   up(reinterpret_cast<void**>(&h->d_kpair), kpair.data(), sizeof(int) * kpair.size());
   up(reinterpret_cast<void**>(&h->d_kwt), kwt.data(), sizeof(int) * kwt.size());
   up(reinterpret_cast<void**>(&h->d_Dop), Dops.data(), sizeof(double) * Dops.size());
+  up(reinterpret_cast<void**>(&h->d_op_src), src_ops.data(), sizeof(int) * src_ops.size());
+  up(reinterpret_cast<void**>(&h->d_class), cls.data(), sizeof(int) * cls.size());
   up(reinterpret_cast<void**>(&h->d_K), Kv.data(), sizeof(double) * Kv.size());
   up(reinterpret_cast<void**>(&h->d_kK_start), kK_start.data(), sizeof(int) * kK_start.size());
   up(reinterpret_cast<void**>(&h->d_kK_idx), kK_idx.data(), sizeof(int) * kK_idx.size());
@@ -1285,7 +1355,7 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
 
 extern "C" void must_kkr_free(must_kkr* h) {
   if (!h) return;
-  void* ptrs[] = {h->d_kpts, h->d_kpair, h->d_kwt, h->d_Dop, h->d_K, h->d_kK_start, h->d_kK_idx, h->d_disp, h->d_pair_disp, h->d_pt_start,
+  void* ptrs[] = {h->d_kpts, h->d_kpair, h->d_kwt, h->d_Dop, h->d_op_src, h->d_class, h->d_K, h->d_kK_start, h->d_kK_idx, h->d_disp, h->d_pair_disp, h->d_pt_start,
                   h->d_pt_R, h->d_pt_rho, h->d_quad_u, h->d_quad_w, h->d_g_start, h->d_g_L2, h->d_g_c};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1384,9 +1454,13 @@ extern "C" must_status must_kkr_tau(const must_kkr* h, int32_t n_items, const do
     ProfScope ps(PH_KKR_INVERT, st);
     dim3 g3(h->n_kg, n_items);
     kkr_invert_kernel<<<g3, INV_THREADS, invert_smem(h), st>>>(K, n_items, Ed, Td, w.Dk, w.part, w.status);
-    dim3 g4(h->nb, n_items);
-    kkr_bz_sum_kernel<<<g4, BZ_THREADS, 0, st>>>(K, n_items, w.part, taud, w.status);
-    prof_launched(PH_KKR_INVERT, 2, n_items);
+    const int tot = n_items * h->nb * h->nL * h->nL;
+    kkr_bz_sum_kernel<<<(tot + 255) / 256, 256, 0, st>>>(K, n_items, w.part, taud, w.S, w.status);
+    if (h->n_ops > 0) {
+      dim3 g4(h->nb, n_items);
+      kkr_symmetrise_kernel<<<g4, SYM_THREADS, 0, st>>>(K, n_items, w.S, Td, taud, w.status);
+    }
+    prof_launched(PH_KKR_INVERT, h->n_ops > 0 ? 3 : 2, n_items);
   }
   if (std_) {
     kkr_status_out_kernel<<<(n_items + 255) / 256, 256, 0, st>>>(n_items, w.status, std_);

@@ -32,9 +32,10 @@ def _items(orc, c, picks):
     return E, ti
 
 
-def _gpu(B, c, E, ti, n_k=None, host=False, status_out=False):
+def _gpu(B, c, E, ti, n_k=None, host=False, flags=0, classes=True):
     import torch
-    h = B.must_kkr_build(c.lattice, c.basis, c.lmax, n_k or c.n_k)
+    h = B.must_kkr_build(c.lattice, c.basis, c.lmax, n_k or c.n_k, flags=flags,
+                         site_class=c.species if classes else None)
     n = len(E)
     ws = torch.empty(B.must_kkr_workspace_bytes(h, n), dtype=torch.uint8, device="cuda")
     if host:
@@ -107,7 +108,8 @@ def test_kkr_l12_cell_vs_oracle(B, orc):
     picks = [(0, 0), (1, nE // 2), (0, nE - 1)]
     E, ti = _items(orc, c, picks)
     got, st, h = _gpu(B, c, E, ti)
-    assert h.n == 64 and h.n_mesh == 64 and h.n_kpts == (64 + 8) // 2
+    assert h.n == 64 and h.n_mesh == 64 and h.n_ops == 48
+    assert h.n_kpts == _orbit_count(c.lattice, 4)        # the corner in its own class: full cubic group
     _check(orc, c, E, ti, got, st, h)
     # the three face-centred A sites are equivalent under the cubic symmetry
     for s in (2, 3):
@@ -177,22 +179,59 @@ def test_lsms_tau00_converges_to_the_crystal_tau_on_the_gpu(B):
     assert errs[1] < 1e-6 and errs[0] > 10 * errs[1], errs
 
 
-@pytest.mark.parametrize("lmax,n_k", [(3, 6), (4, 4), (2, 5)])
-def test_kkr_point_group_reduction_equals_the_full_mesh(B, orc, lmax, n_k):
-    """One site per cell: inverting one point per orbit of the cubic group and
-    symmetrising with the real-harmonic representation gives the same tau as
-    the k / -k paired mesh (odd and even meshes, up to lmax 4)."""
-    c = wl.fcc_crystal(lmax=lmax, n_k=n_k)
+@pytest.mark.parametrize("maker,lmax,n_k", [(wl.fcc_crystal, 3, 6), (wl.fcc_crystal, 4, 4), (wl.fcc_crystal, 2, 5),
+                                             (wl.l12_crystal, 3, 4), (wl.l12_crystal, 2, 5)])
+def test_kkr_point_group_reduction_equals_the_full_mesh(B, orc, maker, lmax, n_k):
+    """Inverting one point per orbit of the crystal's point group and
+    symmetrising with the real-harmonic representation (sites permuted within
+    their classes) gives the same tau as the k / -k paired mesh; for the L1_2
+    cell also without classes (every site its own class: the 8 sign changes)."""
+    c = maker(lmax=lmax, n_k=n_k)
     E, ti = _items(orc, c, [(0, 0), (1, 9), (0, 31)])
     a, sa, ha = _gpu(B, c, E, ti)
-    import torch
-    hb = B.must_kkr_build(c.lattice, c.basis, lmax, n_k, flags=B.MUST_KKR_NO_SYMMETRY)
+    b, sb, hb = _gpu(B, c, E, ti, flags=B.MUST_KKR_NO_SYMMETRY)
     assert ha.n_ops == 48 and hb.n_ops == 0 and ha.n_kpts < hb.n_kpts
-    ws = torch.empty(B.must_kkr_workspace_bytes(hb, len(E)), dtype=torch.uint8, device="cuda")
-    tau = torch.zeros((len(E), 1, hb.kap, hb.kap), dtype=torch.complex128, device="cuda")
-    B.must_kkr_tau(hb, torch.from_numpy(E).cuda(), torch.from_numpy(np.ascontiguousarray(ti)).cuda(), ws, tau)
+    assert (sa == 0).all() and (sb == 0).all()
+    assert rel_fro(a, b).max() <= 1e-12
+    if c.n_basis > 1:
+        d, sd, hd = _gpu(B, c, E, ti, classes=False)
+        assert hd.n_ops == 8 and (sd == 0).all()
+        assert rel_fro(d, b).max() <= 1e-12
+
+
+def test_kkr_site_class_promise_is_checked(B, orc):
+    """Sites declared equal must carry equal t^-1: an item that breaks it gets
+    MUST_EINVAL in its status instead of a silently wrong tau."""
+    import torch
+    c = wl.l12_crystal(lmax=1, n_k=2)
+    E, ti = _items(orc, c, [(0, 3)])      # species 1 at the corner, 0 on the faces: unequal t^-1
+    h = B.must_kkr_build(c.lattice, c.basis, c.lmax, c.n_k, site_class=[0, 0, 0, 0])
+    ws = torch.empty(B.must_kkr_workspace_bytes(h, 1), dtype=torch.uint8, device="cuda")
+    tau = torch.zeros((1, 4, h.kap, h.kap), dtype=torch.complex128, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.must_kkr_tau(h, torch.from_numpy(E).cuda(), torch.from_numpy(np.ascontiguousarray(ti)).cuda(), ws, tau, st)
     torch.cuda.synchronize()
-    b = np.swapaxes(tau.cpu().numpy(), -1, -2)
-    assert (sa == 0).all()
-    err = rel_fro(a, b)
-    assert err.max() <= 1e-12, err
+    assert int(st.cpu()[0]) == 1      # MUST_EINVAL
+
+
+def test_kkr_edge_cases(B, orc):
+    """No items is a no-op; the one-point mesh (k = 0 only) and the largest
+    order one CTA inverts (two sites at lmax 4, n = 50) match the oracle."""
+    import torch
+    c = wl.fcc_crystal(lmax=2, n_k=2)
+    h = B.must_kkr_build(c.lattice, c.basis, c.lmax, c.n_k)
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    B.must_kkr_tau(h, torch.zeros(0, dtype=torch.complex128, device="cuda"),
+                   torch.zeros(0, dtype=torch.complex128, device="cuda"), ws,
+                   torch.zeros(0, dtype=torch.complex128, device="cuda"))
+    for cc in (wl.fcc_crystal(lmax=2, n_k=1), wl.l12_crystal(lmax=2, n_k=1)):
+        E, ti = _items(orc, cc, [(0, 4), (1, 27)])
+        got, st, hh = _gpu(B, cc, E, ti)
+        assert hh.n_mesh == 1
+        _check(orc, cc, E, ti, got, st, hh)
+    two = wl.Crystal("two_site_lmax4", wl.A_LAT * np.eye(3), wl.FCC_CUBIC_BASIS[:2].copy(), np.array([0, 1], np.int32),
+                     4, 2, wl.semicircle_contour(8, im_min=0.005), wl.spin_depths(2), wl.R_MT)
+    E, ti = _items(orc, two, [(0, 0), (1, 5)])
+    got, st, hh = _gpu(B, two, E, ti)
+    assert hh.n == 50
+    _check(orc, two, E, ti, got, st, hh)
