@@ -211,3 +211,20 @@ def test_kkr_build_rejects_bad_arguments_on_the_host():
         assert ei.value.code == 1
     with pytest.raises(B.MustError):
         B.must_kkr_build(c.lattice, c.basis, 3, 4, eta=-1.0)
+
+
+def test_bench_kkr_work_counts():
+    """bench.kkr_work: 4 flops per real-by-complex multiply-add of the lattice
+    sums (a pair group's stored point counting for both displacements) and 8 n^3
+    per inverted k point; checked against a direct count for a fake handle."""
+    import types
+    import bench
+    from paper_2308_16317_gb300 import workload as wl
+    c = wl.l12_crystal(lmax=2)
+    h = types.SimpleNamespace(n_kK=1000, n_disp=13, n_kpts=35, n_pts=3000, n_pts0=200, n=36)
+    w = bench.kkr_work(h, c, 64)
+    nL2 = 25
+    assert w["kkr_recip"] == 4.0 * 64 * 1000 * 13 * nL2
+    # 200 points of x = 0 (one displacement each), 2800 of the six pair groups (two each)
+    assert w["kkr_realsum"] == 4.0 * 64 * 35 * nL2 * (200 + 2 * 2800)
+    assert w["kkr_invert"] == 8.0 * 64 * 35 * 36 ** 3
