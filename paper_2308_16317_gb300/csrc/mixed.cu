@@ -1464,7 +1464,12 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
   cudaStream_t ss = nullptr;
   cudaEvent_t ev_next = nullptr, ev_panel = nullptr;
   const bool lookahead = g_lookahead && side_stream(&ss, &ev_next, &ev_panel);
-  const size_t panel_smem = std::max(size_t(leaf_width(n)) * n, size_t(64 * 65)) * sizeof(float2);
+  // the leaf buffer holds the leaf's rows [c0, n) (at most n - k of them at step k)
+  // and the 64 x 65 block of L11; sizing it per step lets the later, smaller
+  // panels take less of an SM
+  auto panel_smem = [&](int k) {
+    return std::max(size_t(leaf_width(n)) * size_t(n - k), size_t(64 * 65)) * sizeof(float2);
+  };
   // columns of the look-ahead's first update launch: the next panel alone
   // when the update's tiles are one panel wide (the streamed kernels of the
   // BF16 splits), else one tile
@@ -1481,7 +1486,7 @@ must_status mixed_solve_chunk(const MixedChunk& c, cudaStream_t st) {
     if (apack == 2 && !(tc_pack_a_target(c.opts.precision, n, k, w, items, packs, slot, &pa) && pa.Kp == 128))
       pa.hi = pa.lo = nullptr;
     ProfScope ps(PH_PANEL, s);
-    panel32_kernel<<<items, PPT, panel_smem, s>>>(M32, stride, ld, n, r, k, w, c.piv, c.status, conv, Linv, pa.hi,
+    panel32_kernel<<<items, PPT, panel_smem(k), s>>>(M32, stride, ld, n, r, k, w, c.piv, c.status, conv, Linv, pa.hi,
                                                   pa.lo, pa.Kp, pa.item_rows);
     prof_launched(PH_PANEL, 1, items);
     return pa.hi != nullptr;
