@@ -442,7 +442,7 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * vector lists and the Gaunt table on the device (synchronises `stream`).
  * Errors: MUST_EINVAL, MUST_ENOMEM, MUST_ECUDA.
  *
- * must_kkr_tau: n_items independent (energy, potential) items.  E: n_items
+ * must_kkr_tau: n_items (<= 65535) independent (energy, potential) items.  E: n_items
  * complex; tinv: [n_items][n_basis][lmax+1] complex t^{-1}_l of each site;
  * tau: [n_items][n_basis][kap][kap] complex, column-major blocks, kap =
  * (lmax+1)^2; status: optional int32 per item (MUST_OK, MUST_ESINGULAR for an

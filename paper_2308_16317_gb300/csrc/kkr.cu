@@ -1391,6 +1391,10 @@ extern "C" must_status must_kkr_tau(const must_kkr* h, int32_t n_items, const do
     return MUST_EINVAL;
   }
   if (n_items == 0) return MUST_OK;
+  if (n_items > 65535) {   // items are a grid dimension of every launch
+    must_set_error("must_kkr_tau: at most 65535 items per call");
+    return MUST_EINVAL;
+  }
   if (workspace_bytes < must_kkr_workspace_bytes(h, n_items)) {
     must_set_error("must_kkr_tau: workspace too small: need %zu bytes", must_kkr_workspace_bytes(h, n_items));
     return MUST_ENOMEM;
