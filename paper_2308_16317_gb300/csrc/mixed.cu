@@ -406,6 +406,7 @@ __global__ void __launch_bounds__(256) trsm_inv_kernel(float2* __restrict__ A0, 
   cf y0[CPT], y1[CPT];
 #pragma unroll
   for (int q = 0; q < CPT; ++q) y0[q] = y1[q] = mkf(0.f, 0.f);
+#pragma unroll 4
   for (int j = 0; j < 32; ++j) {
     const cf l1 = Li[j][i1];
     const cf l0 = Li[j][i0];
@@ -416,6 +417,7 @@ __global__ void __launch_bounds__(256) trsm_inv_kernel(float2* __restrict__ A0, 
       cfmaf_acc(y0[q], l0, a);
     }
   }
+#pragma unroll 4
   for (int j = 32; j < 64; ++j) {
     const cf l1 = Li[j][i1];
 #pragma unroll
@@ -507,6 +509,7 @@ __global__ void __launch_bounds__(256) trsm_inv_persist_kernel(float2* __restric
     cf y0[CPT], y1[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) y0[q] = y1[q] = mkf(0.f, 0.f);
+#pragma unroll 4
     for (int j = 0; j < 32; ++j) {
       const cf l1 = Li[j][i1];
       const cf l0 = Li[j][i0];
@@ -517,6 +520,7 @@ __global__ void __launch_bounds__(256) trsm_inv_persist_kernel(float2* __restric
         cfmaf_acc(y0[q], l0, a);
       }
     }
+#pragma unroll 4
     for (int j = 32; j < 64; ++j) {
       const cf l1 = Li[j][i1];
 #pragma unroll
