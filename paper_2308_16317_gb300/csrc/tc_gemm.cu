@@ -878,6 +878,46 @@ __global__ void pack_a_kernel(const float2* __restrict__ C0, size_t stride, int 
   }
 }
 
+// The same A'-pack for the BF16 splits through a shared-memory tile of
+// PACK_ROWS matrix rows x the panel's K per CTA: read down the columns
+// (consecutive threads take consecutive rows of one column) and written along
+// K as BF16 pairs (consecutive threads take consecutive K pairs of one row),
+// so both sides are coalesced; every element is split exactly as above.
+constexpr int PACK_ROWS = 16;
+
+__global__ void __launch_bounds__(256) pack_a_bf16_tiled_kernel(const float2* __restrict__ C0, size_t stride, int ld,
+                                                                int n, int k0, int nbe, int base, int Kp, int rows_pad,
+                                                                uint16_t* __restrict__ hi0, uint16_t* __restrict__ lo0) {
+  __shared__ float2 tile[64][PACK_ROWS + 1];   // [p][row]
+  const int item = blockIdx.y;
+  const int half = Kp / 2;                     // complex K of the pack (<= 64)
+  const int i0 = base + blockIdx.x * PACK_ROWS;
+  const float2* C = C0 + size_t(item) * stride;
+  for (int t = threadIdx.x; t < half * PACK_ROWS; t += blockDim.x) {
+    const int p = t / PACK_ROWS, r = t % PACK_ROWS, i = i0 + r;
+    float2 v = make_float2(0.f, 0.f);
+    if (p < nbe && i < n) v = C[size_t(k0 + p) * ld + i];
+    tile[p][r] = v;
+  }
+  __syncthreads();
+  uint16_t* hi = hi0 + size_t(item) * rows_pad * Kp;
+  uint16_t* lo = lo0 + size_t(item) * rows_pad * Kp;
+  for (int t = threadIdx.x; t < PACK_ROWS * half; t += blockDim.x) {
+    const int r = t / half, p = t % half, i = i0 + r;
+    if (i >= n) continue;
+    const float2 v = tile[p][r];
+    const float e[4] = {v.x, -v.y, v.y, v.x};   // row 2i: (Lr, -Li); row 2i+1: (Li, Lr)
+    __nv_bfloat16_raw h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) split_bf16(e[q], h[q], l[q]);
+    const size_t o0 = size_t(2 * i) * Kp + 2 * p, o1 = o0 + Kp;
+    *reinterpret_cast<uint32_t*>(hi + o0) = uint32_t(h[0].x) | (uint32_t(h[1].x) << 16);
+    *reinterpret_cast<uint32_t*>(lo + o0) = uint32_t(l[0].x) | (uint32_t(l[1].x) << 16);
+    *reinterpret_cast<uint32_t*>(hi + o1) = uint32_t(h[2].x) | (uint32_t(h[3].x) << 16);
+    *reinterpret_cast<uint32_t*>(lo + o1) = uint32_t(l[2].x) | (uint32_t(l[3].x) << 16);
+  }
+}
+
 // B'-pack row j (matrix column j in [base, n)): K = 2p -> Ur(p,j), 2p+1 -> Ui(p,j).
 template <typename T>
 __global__ void pack_b_kernel(const float2* __restrict__ C0, size_t stride, int ld, int n, int k0, int nbe, int base,
@@ -1160,9 +1200,9 @@ bool tc_pack(int precision, float2* A, size_t stride, int ld, int n, int k0, int
                                                  reinterpret_cast<float*>(g.pa_hi), reinterpret_cast<float*>(g.pa_lo),
                                                  1);
     else
-      pack_a_kernel<uint16_t><<<grid, 256, 0, st>>>(A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows,
-                                                    reinterpret_cast<uint16_t*>(g.pa_hi) + aoff,
-                                                    reinterpret_cast<uint16_t*>(g.pa_lo) + aoff, 0);
+      pack_a_bf16_tiled_kernel<<<dim3((g.m + PACK_ROWS - 1) / PACK_ROWS, items), 256, 0, st>>>(
+          A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows, reinterpret_cast<uint16_t*>(g.pa_hi) + aoff,
+          reinterpret_cast<uint16_t*>(g.pa_lo) + aoff);
     prof_launched(PH_PACK, 1, items);
     return true;
   }
@@ -1172,9 +1212,9 @@ bool tc_pack(int precision, float2* A, size_t stride, int ld, int n, int k0, int
     pack_b_kernel<float><<<grid, 256, 0, st>>>(A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows,
                                                reinterpret_cast<float*>(g.pb_hi), reinterpret_cast<float*>(g.pb_lo), 1);
   } else {
-    pack_a_kernel<uint16_t><<<grid, 256, 0, st>>>(A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows,
-                                                  reinterpret_cast<uint16_t*>(g.pa_hi),
-                                                  reinterpret_cast<uint16_t*>(g.pa_lo), 0);
+    pack_a_bf16_tiled_kernel<<<dim3((g.m + PACK_ROWS - 1) / PACK_ROWS, items), 256, 0, st>>>(
+        A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows, reinterpret_cast<uint16_t*>(g.pa_hi),
+        reinterpret_cast<uint16_t*>(g.pa_lo));
     pack_b_kernel<uint16_t><<<grid, 256, 0, st>>>(A, stride, ld, n, k0, nbe, g.base, g.Kp, g.item_rows,
                                                   reinterpret_cast<uint16_t*>(g.pb_hi),
                                                   reinterpret_cast<uint16_t*>(g.pb_lo), 0);
