@@ -462,6 +462,12 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * evaluated: M(-k) = M(k)^T (the reciprocity G_{LL'}(rho) = G_{L'L}(-rho)), so
  * its diagonal blocks enter the average transposed.  must_kkr_eta: the
  * splitting parameter in use.
+ *
+ * must_kkr_geometry: the host half of must_kkr_build, with the same arguments
+ * and checks but no device and no CUDA call: fills info[9] as must_kkr_info
+ * would for the handle that build makes, and *eta_used (may be NULL) with the
+ * splitting parameter.  Lets a host test the point group, the orbits of the
+ * mesh and the vector lists without a GPU.  Errors: MUST_EINVAL.
  */
 typedef struct must_kkr must_kkr;
 #define MUST_KKR_NO_SYMMETRY 1   /* flags: evaluate one point of each {k, -k} pair only */
@@ -473,6 +479,9 @@ must_status must_kkr_tau(const must_kkr* kkr, int32_t n_items, const double* E, 
                          void* workspace, size_t ws_bytes, double* tau, int32_t* status, void* stream);
 must_status must_kkr_info(const must_kkr* kkr, int32_t* info);
 double must_kkr_eta(const must_kkr* kkr);
+must_status must_kkr_geometry(const double* lattice, const double* basis, const int32_t* site_class,
+                              int32_t n_basis, int32_t lmax, int32_t n_k, double eta, int32_t flags,
+                              int32_t* info, double* eta_used);
 
 void must_profile_enable(int on);
 int must_profile_read(double* ms, long long* launches, long long* items, int n_phases);

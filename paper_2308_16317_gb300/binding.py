@@ -86,6 +86,7 @@ def load():
         "must_kkr_tau": (I32, [P, I32, P, P, P, SZ, P, P, P]),
         "must_kkr_info": (I32, [P, P]),
         "must_kkr_eta": (D, [P]),
+        "must_kkr_geometry": (I32, [P, P, P, I32, I32, I32, D, I32, P, P]),
         "must_profile_enable": (None, [ctypes.c_int]),
         "must_profile_read": (ctypes.c_int, [P, P, P, ctypes.c_int]),
         "must_launch_count": (ctypes.c_longlong, []),
@@ -114,7 +115,7 @@ def exported_symbols():
                         "must_mlp_save", "must_mlp_load", "must_mlp_features", "must_mlp_apply", "must_mlp_targets",
                         "must_tau00_solve_seeded", "must_contour_weights", "must_site_charge", "must_site_density",
                         "must_peak_probe", "must_kkr_build", "must_kkr_free", "must_kkr_workspace_bytes",
-                        "must_kkr_tau", "must_kkr_info", "must_kkr_eta")]
+                        "must_kkr_tau", "must_kkr_info", "must_kkr_eta", "must_kkr_geometry")]
 
 
 def _ptr(a):
@@ -433,6 +434,25 @@ def must_kkr_build(lattice, basis, lmax: int, n_k: int, eta: float = 0.0, flags:
     _check(load().must_kkr_build(_ptr(lat), _ptr(bas), _ptr(cls), int(bas.shape[0]), int(lmax), int(n_k),
                                  float(eta), int(flags), _stream(stream), ctypes.byref(out)))
     return Kkr(out, int(bas.shape[0]), int(lmax))
+
+
+KKR_INFO_FIELDS = ("n", "n_kpts", "n_disp", "n_pts", "n_kK", "n_kg", "n_mesh", "n_pts0", "n_ops")
+
+
+def must_kkr_geometry(lattice, basis, lmax: int, n_k: int, eta: float = 0.0, flags: int = 0,
+                      site_class=None) -> dict:
+    """Host half of must_kkr_build (no device): the sizes must_kkr_info would
+    report, keyed by KKR_INFO_FIELDS, plus 'eta'."""
+    lat = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(3, 3))
+    bas = np.ascontiguousarray(np.asarray(basis, dtype=np.float64).reshape(-1, 3))
+    cls = None if site_class is None else np.ascontiguousarray(np.asarray(site_class, dtype=np.int32))
+    info = np.zeros(9, np.int32)
+    eta_used = np.zeros(1, np.float64)
+    _check(load().must_kkr_geometry(_ptr(lat), _ptr(bas), _ptr(cls), int(bas.shape[0]), int(lmax), int(n_k),
+                                    float(eta), int(flags), _ptr(info), _ptr(eta_used)))
+    out = {k: int(v) for k, v in zip(KKR_INFO_FIELDS, info)}
+    out["eta"] = float(eta_used[0])
+    return out
 
 
 def must_kkr_workspace_bytes(kkr: Kkr, n_items: int) -> int:

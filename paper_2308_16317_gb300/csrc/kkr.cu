@@ -1016,11 +1016,15 @@ size_t staging_bytes(const must_kkr* h, int items) {
 
 }  // namespace
 
-extern "C" must_status must_kkr_build(const double* lattice, const double* basis, const int32_t* site_class,
-                                      int32_t n_basis, int32_t lmax, int32_t n_k, double eta, int32_t flags,
-                                      void* stream, must_kkr** out) {
-  if (!out) { must_set_error("must_kkr_build: out is NULL"); return MUST_EINVAL; }
-  *out = nullptr;
+// The host set-up (argument checks, lattice, point group, mesh and its orbits,
+// reciprocal and real-space vector lists, quadrature, Gaunt table), then the
+// device tables.  With dry_info the set-up's sizes are returned instead and no
+// CUDA call is made (must_kkr_geometry).
+static must_status kkr_build_impl(const double* lattice, const double* basis, const int32_t* site_class,
+                                  int32_t n_basis, int32_t lmax, int32_t n_k, double eta, int32_t flags,
+                                  void* stream, must_kkr** out, int32_t* dry_info, double* dry_eta) {
+  if (!out && !dry_info) { must_set_error("must_kkr_build: out is NULL"); return MUST_EINVAL; }
+  if (out) *out = nullptr;
   if (!lattice || !basis || n_basis < 1 || lmax < 0 || lmax > 4 || n_k < 1 || n_k > 64 || !(eta >= 0.0) ||
       (flags & ~MUST_KKR_NO_SYMMETRY)) {
     must_set_error("must_kkr_build: bad argument (lattice/basis NULL, n_basis < 1, lmax outside 0..4, n_k outside "
@@ -1266,18 +1270,34 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
   std::vector<double> gc;
   must_gaunt_csr(lmax, gs, gl, gc);
 
+  // k points per inversion CTA: whole passes of side-by-side matrices, at most
+  // KKR_KG_MAX, and few enough that small (symmetry-reduced) meshes still give
+  // each item ~32 CTAs
+  int kg_val;
+  {
+    const int nm = kkr_matrices_per_pass(n_basis * nL);
+    const int want = nm * ((n_kpts + 32 * nm - 1) / (32 * nm));
+    kg_val = std::max(nm, std::min(std::max(KKR_KG_MAX, nm), want));
+  }
+  if (dry_info) {
+    dry_info[0] = n_basis * nL;
+    dry_info[1] = n_kpts;
+    dry_info[2] = n_disp;
+    dry_info[3] = n_pts;
+    dry_info[4] = int(kK_idx.size());
+    dry_info[5] = (n_kpts + kg_val - 1) / kg_val;
+    dry_info[6] = n_k * n_k * n_k;
+    dry_info[7] = pt_start[1];
+    dry_info[8] = n_ops;
+    if (dry_eta) *dry_eta = eta;
+    return MUST_OK;
+  }
+
   must_kkr* h = new must_kkr();
   std::memset(h, 0, sizeof(*h));
   h->nb = n_basis; h->lmax = lmax; h->nL = nL; h->l2max = l2max; h->nL2 = nL2; h->n = n_basis * nL;
   h->n_k = n_k; h->n_kpts = n_kpts; h->n_mesh = n_k * n_k * n_k; h->n_disp = n_disp; h->n_pts0 = pt_start[1]; h->n_pts = n_pts; h->n_K = n_K;
-  {
-    // k points per inversion CTA: whole passes of side-by-side matrices, at most
-    // KKR_KG_MAX, and few enough that small (symmetry-reduced) meshes still give
-    // each item ~32 CTAs
-    const int nm = kkr_matrices_per_pass(n_basis * nL);
-    const int want = nm * ((n_kpts + 32 * nm - 1) / (32 * nm));
-    h->kg = std::max(nm, std::min(std::max(KKR_KG_MAX, nm), want));
-  }
+  h->kg = kg_val;
   h->n_kK = int(kK_idx.size()); h->n_kg = (n_kpts + h->kg - 1) / h->kg; h->n_ops = n_ops;
   h->eta = eta; h->omega = omega;
   cudaGetDevice(&h->device);
@@ -1351,6 +1371,20 @@ extern "C" must_status must_kkr_build(const double* lattice, const double* basis
   }
   *out = h;
   return MUST_OK;
+}
+
+extern "C" must_status must_kkr_build(const double* lattice, const double* basis, const int32_t* site_class,
+                                      int32_t n_basis, int32_t lmax, int32_t n_k, double eta, int32_t flags,
+                                      void* stream, must_kkr** out) {
+  return kkr_build_impl(lattice, basis, site_class, n_basis, lmax, n_k, eta, flags, stream, out, nullptr, nullptr);
+}
+
+extern "C" must_status must_kkr_geometry(const double* lattice, const double* basis, const int32_t* site_class,
+                                         int32_t n_basis, int32_t lmax, int32_t n_k, double eta, int32_t flags,
+                                         int32_t* info, double* eta_used) {
+  if (!info) { must_set_error("must_kkr_geometry: info is NULL"); return MUST_EINVAL; }
+  return kkr_build_impl(lattice, basis, site_class, n_basis, lmax, n_k, eta, flags, nullptr, nullptr, info,
+                        eta_used);
 }
 
 extern "C" void must_kkr_free(must_kkr* h) {

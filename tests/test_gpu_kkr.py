@@ -98,6 +98,8 @@ def test_kkr_fcc_primitive_vs_oracle(B, orc):
     got, st, h = _gpu(B, c, E, ti)
     assert h.n == 16 and h.n_mesh == 216 and h.n_ops == 48
     assert h.n_kpts == _orbit_count(c.lattice, 6)        # one point per orbit of the cubic group
+    geo = B.must_kkr_geometry(c.lattice, c.basis, c.lmax, 6, site_class=c.species)
+    assert geo == dict({k: getattr(h, k) for k in B.KKR_INFO_FIELDS}, eta=h.eta)   # the host half agrees
     _check(orc, c, E, ti, got, st, h)
 
 
