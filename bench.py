@@ -1154,6 +1154,7 @@ def run_kkr(args):
             "value": items / (ms / 1e3), "unit": "tau solves/s (all sites of the cell per (E, spin))",
             "ms_per_step": ms, "items_per_step": items, "n": h.n, "k_points": h.n_mesh,
             "k_points_evaluated": h.n_kpts, "point_group_ops": h.n_ops,
+            "reciprocal_table_bytes": h.table_bytes,
             "inversions_per_s": items * h.n_kpts / (ms / 1e3),
             "gpu_launches": launches, "kernels": kern,
             "roofline": {"kernel_phase": dom, "bound": "alu", "unit": "TFLOP/s",

@@ -428,7 +428,8 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * [1, 64]; eta: Ewald splitting parameter (bohr^-2), 0 = 4 pi / Omega^(2/3)
  * (0.7 of that with one site per cell), which keeps the two sums about equally
  * costly; the result does not depend on it, but below ~0.4 of that value the
- * factor e^{E/eta} starts to cost digits.  flags: 0, or MUST_KKR_NO_SYMMETRY.  With flags 0 the
+ * factor e^{E/eta} starts to cost digits.  flags: 0, or MUST_KKR_NO_SYMMETRY
+ * and/or MUST_KKR_NO_TABLE (below).  Without MUST_KKR_NO_SYMMETRY the
  * crystal's point group is used: the signed permutations g of the Cartesian
  * axes that map the lattice onto itself and each site onto a site of its class
  * (48 for the fcc lattice with one site, or the L1_2 cell with the corner in a
@@ -463,6 +464,15 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * its diagonal blocks enter the average transposed.  must_kkr_eta: the
  * splitting parameter in use.
  *
+ * Reciprocal-term table: the factors of each reciprocal term that do not
+ * depend on the energy (e^{-q^2/eta} YS_L(q), the phases cos(q.x) and sin(q.x)
+ * of the displacements, q^2) are computed once by must_kkr_build and kept on
+ * the device, 8 (2 lmax+1)^2 + 16 (number of displacement pairs) + 8 bytes per
+ * (k, K) term (info[4] terms), when that is at most 512 MiB; every item of
+ * must_kkr_tau then forms only 1/(q^2 - E) per term.  flags |=
+ * MUST_KKR_NO_TABLE forms all factors per item instead (same results to
+ * rounding).  must_kkr_table_bytes: the table's size, 0 when none is kept.
+ *
  * must_kkr_geometry: the host half of must_kkr_build, with the same arguments
  * and checks but no device and no CUDA call: fills info[9] as must_kkr_info
  * would for the handle that build makes, and *eta_used (may be NULL) with the
@@ -471,6 +481,7 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  */
 typedef struct must_kkr must_kkr;
 #define MUST_KKR_NO_SYMMETRY 1   /* flags: evaluate one point of each {k, -k} pair only */
+#define MUST_KKR_NO_TABLE 2      /* flags: form the reciprocal terms' harmonics per item, keep no table */
 must_status must_kkr_build(const double* lattice, const double* basis, const int32_t* site_class, int32_t n_basis,
                            int32_t lmax, int32_t n_k, double eta, int32_t flags, void* stream, must_kkr** out);
 void must_kkr_free(must_kkr* kkr);
@@ -479,6 +490,7 @@ must_status must_kkr_tau(const must_kkr* kkr, int32_t n_items, const double* E, 
                          void* workspace, size_t ws_bytes, double* tau, int32_t* status, void* stream);
 must_status must_kkr_info(const must_kkr* kkr, int32_t* info);
 double must_kkr_eta(const must_kkr* kkr);
+size_t must_kkr_table_bytes(const must_kkr* kkr);
 must_status must_kkr_geometry(const double* lattice, const double* basis, const int32_t* site_class,
                               int32_t n_basis, int32_t lmax, int32_t n_k, double eta, int32_t flags,
                               int32_t* info, double* eta_used);

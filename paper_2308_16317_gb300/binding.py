@@ -87,6 +87,7 @@ def load():
         "must_kkr_info": (I32, [P, P]),
         "must_kkr_eta": (D, [P]),
         "must_kkr_geometry": (I32, [P, P, P, I32, I32, I32, D, I32, P, P]),
+        "must_kkr_table_bytes": (SZ, [P]),
         "must_profile_enable": (None, [ctypes.c_int]),
         "must_profile_read": (ctypes.c_int, [P, P, P, ctypes.c_int]),
         "must_launch_count": (ctypes.c_longlong, []),
@@ -115,7 +116,7 @@ def exported_symbols():
                         "must_mlp_save", "must_mlp_load", "must_mlp_features", "must_mlp_apply", "must_mlp_targets",
                         "must_tau00_solve_seeded", "must_contour_weights", "must_site_charge", "must_site_density",
                         "must_peak_probe", "must_kkr_build", "must_kkr_free", "must_kkr_workspace_bytes",
-                        "must_kkr_tau", "must_kkr_info", "must_kkr_eta", "must_kkr_geometry")]
+                        "must_kkr_tau", "must_kkr_info", "must_kkr_eta", "must_kkr_geometry", "must_kkr_table_bytes")]
 
 
 def _ptr(a):
@@ -415,6 +416,7 @@ class Kkr:
         (self.n, self.n_kpts, self.n_disp, self.n_pts, self.n_kK, self.n_kg, self.n_mesh,
          self.n_pts0, self.n_ops) = (int(v) for v in info)
         self.eta = float(load().must_kkr_eta(handle))
+        self.table_bytes = int(load().must_kkr_table_bytes(handle))   # 0: no reciprocal-term table
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
@@ -423,6 +425,7 @@ class Kkr:
 
 
 MUST_KKR_NO_SYMMETRY = 1
+MUST_KKR_NO_TABLE = 2
 
 
 def must_kkr_build(lattice, basis, lmax: int, n_k: int, eta: float = 0.0, flags: int = 0, site_class=None,

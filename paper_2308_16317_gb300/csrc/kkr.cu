@@ -37,6 +37,8 @@
 //
 // Kernels (all FP64):
 //   kkr_real_terms_kernel  per (item, real-space point): the k-independent factor of B_L
+//   kkr_recip_table_kernel at build, per k: the energy-independent factors of every
+//                          reciprocal term, e^{-q^2/eta} YS_L(q), cos(q.x), sin(q.x), q^2
 //   kkr_recip_kernel       per (item, k): A_L + C_L for every displacement (x and -x paired)
 //   kkr_realsum_kernel     per (item, displacement group, 32 k points): adds B_L
 //   kkr_invert_kernel      per (item, group of <= 8 k points): M(k) by the Gaunt contraction,
@@ -73,6 +75,7 @@ constexpr int KKR_RCHUNK = 32;         // real-space points per chunk
 constexpr int KKR_KG_MAX = 8;          // most k points per inversion CTA
 constexpr double KKR_CUT = 40.0;       // both sums cut where their Gaussian factor < e^{-cut}
 constexpr double KKR_ECAP = 1.5;       // sums are cut for Re E <= KKR_ECAP (Ry)
+constexpr size_t KKR_TAB_CAP = size_t(512) << 20;   // largest reciprocal-term table kept on the device
 
 __device__ __forceinline__ int l_of_L(int L) {
   int l = 0;
@@ -169,6 +172,9 @@ struct KkrDev {
   const int* g_start;     // Gaunt CSR, rows (L, L')
   const int* g_L2;
   const double* g_c;
+  const double* tab;      // [n_kK][tab_w] or NULL: per (k, K) term, e^{-q^2/eta} YS_L(q) (nL2),
+                          // cos(q.x), sin(q.x) of each pair group's x, then q^2
+  int tab_w;              // nL2 + 2 (n_groups - 1) + 1
 };
 
 // -------------------------------------------------------------------------
@@ -237,6 +243,37 @@ __global__ void kkr_real_terms_kernel(KkrDev K, int items, const double2* __rest
 // chunk, or, when the outputs are fewer than the threads, over one of G
 // interleaved subsets, the G partial sums being added in order at the end.
 constexpr int RECIP_THREADS = 256;
+
+// The energy-independent factors of the reciprocal terms, one row per (k, K)
+// in the order of kK_idx: e^{-q^2/eta} YS_L(q) for every L, then cos(q.x) and
+// sin(q.x) for the x of each pair group, then q^2.  One CTA per k point.  The
+// items of every call then form only 1/(q^2 - E) per term.
+constexpr int TAB_THREADS = 128;
+__global__ void __launch_bounds__(TAB_THREADS) kkr_recip_table_kernel(KkrDev K, double* __restrict__ tab) {
+  const int ik = blockIdx.x;
+  const double* kp = K.kpts + size_t(ik) * 3;
+  const int k0 = K.kK_start[ik], k1 = K.kK_start[ik + 1];
+  const int n_groups = 1 + (K.n_disp - 1) / 2;
+  const double inv_eta = 1.0 / K.eta;
+  for (int p = k0 + threadIdx.x; p < k1; p += TAB_THREADS) {
+    const double* Kv = K.Kvec + size_t(K.kK_idx[p]) * 3;
+    const double q0 = kp[0] + Kv[0], q1 = kp[1] + Kv[1], q2v = kp[2] + Kv[2];
+    const double qq = q0 * q0 + q1 * q1 + q2v * q2v;
+    const double g = exp(-qq * inv_eta);
+    double* row = tab + size_t(p) * K.tab_w;
+    for (int m = 0; m <= K.l2max; ++m)
+      solid_harmonic_column(K.l2max, m, q0, q1, q2v, qq, [&](int, int L, double v) { row[L] = g * v; });
+    for (int gi = 1; gi < n_groups; ++gi) {
+      const double* x = K.disp + (2 * gi - 1) * 3;
+      double sn, cs;
+      sincos(q0 * x[0] + q1 * x[1] + q2v * x[2], &sn, &cs);
+      row[K.nL2 + 2 * (gi - 1)] = cs;
+      row[K.nL2 + 2 * (gi - 1) + 1] = sn;
+    }
+    row[K.tab_w - 1] = qq;
+  }
+}
+
 constexpr int KKR_MAX_GROUPS = 1 + (KKR_MAX_DISP - 1) / 2;
 constexpr int RECIP_OUT = (KKR_MAX_GROUPS * KKR_MAX_NL2 + RECIP_THREADS - 1) / RECIP_THREADS;
 constexpr int RECIP_MPARTS = RECIP_THREADS / KKR_KCHUNK;
@@ -264,21 +301,35 @@ __global__ void __launch_bounds__(RECIP_THREADS) kkr_recip_kernel(KkrDev K, int 
   const cd wpre = (4.0 * kPi / K.omega) * cexp_d(mk(e.x * inv_eta, e.y * inv_eta));
   for (int c0 = k0; c0 < k1; c0 += KKR_KCHUNK) {
     const int cn = min(KKR_KCHUNK, k1 - c0);
+    const double* trow = K.tab ? K.tab + size_t(c0) * K.tab_w : nullptr;   // the chunk's table rows
     if (tid < KKR_KCHUNK) {
       double q0 = 0.0, q1 = 0.0, q2v = 0.0, qq = 0.0;
       cd w = mk(0.0, 0.0);
       if (tid < cn) {
-        const double* Kv = K.Kvec + size_t(K.kK_idx[c0 + tid]) * 3;
-        q0 = kp[0] + Kv[0]; q1 = kp[1] + Kv[1]; q2v = kp[2] + Kv[2];
-        qq = q0 * q0 + q1 * q1 + q2v * q2v;
-        // w = (4 pi / Omega) e^{(E - q^2)/eta} / (q^2 - E)
-        w = exp(-qq * inv_eta) * (wpre * cinv(mk(qq - e.x, -e.y)));
+        if (trow) {
+          // w = (4 pi / Omega) e^{E/eta} / (q^2 - E); e^{-q^2/eta} is in the tabulated harmonics
+          qq = trow[size_t(tid) * K.tab_w + K.tab_w - 1];
+          w = wpre * cinv(mk(qq - e.x, -e.y));
+        } else {
+          const double* Kv = K.Kvec + size_t(K.kK_idx[c0 + tid]) * 3;
+          q0 = kp[0] + Kv[0]; q1 = kp[1] + Kv[1]; q2v = kp[2] + Kv[2];
+          qq = q0 * q0 + q1 * q1 + q2v * q2v;
+          // w = (4 pi / Omega) e^{(E - q^2)/eta} / (q^2 - E)
+          w = exp(-qq * inv_eta) * (wpre * cinv(mk(qq - e.x, -e.y)));
+        }
       }
       qv[tid * 4] = q0; qv[tid * 4 + 1] = q1; qv[tid * 4 + 2] = q2v; qv[tid * 4 + 3] = qq;
       wv[tid] = make_double2(w.x, w.y);
     }
+    if (trow) {
+      // the chunk's harmonic rows: cn x nL2 doubles copied as they lie in the table
+      for (int i = tid; i < cn * K.nL2; i += RECIP_THREADS) {
+        const int j = i / K.nL2, L = i - j * K.nL2;
+        Y[i] = trow[size_t(j) * K.tab_w + L];
+      }
+    }
     __syncthreads();
-    {
+    if (!trow) {
       const int j = tid % KKR_KCHUNK, part = tid / KKR_KCHUNK;
       double* y = Y + j * K.nL2;
       for (int m = part; m <= K.l2max; m += RECIP_MPARTS)
@@ -290,6 +341,10 @@ __global__ void __launch_bounds__(RECIP_THREADS) kkr_recip_kernel(KkrDev K, int 
       const double2 w = wv[j];
       if (d == 0) {
         W[p] = w;
+      } else if (trow) {
+        // row 2g-1: cos, row 2g: sin (zero past the chunk's end, where w is zero too)
+        const double f = (j < cn) ? trow[size_t(j) * K.tab_w + K.nL2 + 2 * ((d - 1) / 2) + ((d & 1) ? 0 : 1)] : 0.0;
+        W[p] = make_double2(f * w.x, f * w.y);
       } else {
         const double* x = K.disp + ((d - 1) / 2 * 2 + 1) * 3;   // the x of the pair
         double sn, cs;
@@ -957,6 +1012,9 @@ struct must_kkr {
   int* d_g_start;
   int* d_g_L2;
   double* d_g_c;
+  double* d_tab;          // reciprocal-term table (NULL: the terms are formed per item)
+  int tab_w;
+  size_t tab_bytes;
 };
 
 namespace {
@@ -970,6 +1028,7 @@ KkrDev dev_view(const must_kkr* h) {
   K.disp = h->d_disp; K.pair_disp = h->d_pair_disp; K.pt_start = h->d_pt_start; K.pt_R = h->d_pt_R;
   K.pt_rho = h->d_pt_rho; K.quad_u = h->d_quad_u; K.quad_w = h->d_quad_w;
   K.g_start = h->d_g_start; K.g_L2 = h->d_g_L2; K.g_c = h->d_g_c;
+  K.tab = h->d_tab; K.tab_w = h->tab_w;
   return K;
 }
 
@@ -1026,7 +1085,7 @@ static must_status kkr_build_impl(const double* lattice, const double* basis, co
   if (!out && !dry_info) { must_set_error("must_kkr_build: out is NULL"); return MUST_EINVAL; }
   if (out) *out = nullptr;
   if (!lattice || !basis || n_basis < 1 || lmax < 0 || lmax > 4 || n_k < 1 || n_k > 64 || !(eta >= 0.0) ||
-      (flags & ~MUST_KKR_NO_SYMMETRY)) {
+      (flags & ~(MUST_KKR_NO_SYMMETRY | MUST_KKR_NO_TABLE))) {
     must_set_error("must_kkr_build: bad argument (lattice/basis NULL, n_basis < 1, lmax outside 0..4, n_k outside "
                    "1..64 or eta < 0)");
     return MUST_EINVAL;
@@ -1340,6 +1399,22 @@ static must_status kkr_build_impl(const double* lattice, const double* basis, co
     for (int q = 1; q <= KKR_MAX_L2; ++q) rec[q] = 1.0 / q;
     if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_recip, rec, sizeof(rec), 0, cudaMemcpyHostToDevice, st);
   }
+  {
+    // reciprocal-term table, unless asked not to or larger than KKR_TAB_CAP
+    const int n_groups = 1 + (n_disp - 1) / 2;
+    h->tab_w = nL2 + 2 * (n_groups - 1) + 1;
+    const size_t tb = sizeof(double) * size_t(h->n_kK) * size_t(h->tab_w);
+    if (e == cudaSuccess && !(flags & MUST_KKR_NO_TABLE) && h->n_kK > 0 && tb <= KKR_TAB_CAP) {
+      e = cudaMalloc(reinterpret_cast<void**>(&h->d_tab), tb);
+      if (e == cudaSuccess) {
+        h->tab_bytes = tb;
+        KkrDev K = dev_view(h);
+        K.tab = nullptr;   // the kernel writes the table through its own argument
+        kkr_recip_table_kernel<<<h->n_kpts, TAB_THREADS, 0, st>>>(K, h->d_tab);
+        e = cudaGetLastError();
+      }
+    }
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) {
     // dynamic shared memory: raised to this handle's need per device, never
@@ -1390,11 +1465,13 @@ extern "C" must_status must_kkr_geometry(const double* lattice, const double* ba
 extern "C" void must_kkr_free(must_kkr* h) {
   if (!h) return;
   void* ptrs[] = {h->d_kpts, h->d_kpair, h->d_kwt, h->d_Dop, h->d_op_src, h->d_class, h->d_K, h->d_kK_start, h->d_kK_idx, h->d_disp, h->d_pair_disp, h->d_pt_start,
-                  h->d_pt_R, h->d_pt_rho, h->d_quad_u, h->d_quad_w, h->d_g_start, h->d_g_L2, h->d_g_c};
+                  h->d_pt_R, h->d_pt_rho, h->d_quad_u, h->d_quad_w, h->d_g_start, h->d_g_L2, h->d_g_c, h->d_tab};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
 }
+
+extern "C" size_t must_kkr_table_bytes(const must_kkr* h) { return h ? h->tab_bytes : 0; }
 
 extern "C" must_status must_kkr_info(const must_kkr* h, int32_t* info) {
   if (!h || !info) { must_set_error("must_kkr_info: NULL argument"); return MUST_EINVAL; }

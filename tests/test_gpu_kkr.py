@@ -103,6 +103,28 @@ def test_kkr_fcc_primitive_vs_oracle(B, orc):
     _check(orc, c, E, ti, got, st, h)
 
 
+@pytest.mark.parametrize("cell,lmax,n_k", [("fcc", 3, 6), ("l12", 2, 4), ("fcc", 4, 5)])
+def test_kkr_reciprocal_table_and_per_item_terms_agree(B, orc, cell, lmax, n_k):
+    """The reciprocal terms' energy-independent factors tabulated at build (the
+    default) and formed per item (MUST_KKR_NO_TABLE) both give the oracle's
+    tau within the parity tolerance; the table holds one row of
+    (2 lmax+1)^2 + 2 (pair groups) + 1 doubles per (k, K) term.  (The two
+    round differently; at the Im E = 0.005 end of the contour M(k) is nearly
+    singular and they differ by up to ~5e-13, so they are held to the same
+    1e-11 as against the oracle.)"""
+    c = wl.fcc_crystal(lmax=lmax, n_k=n_k) if cell == "fcc" else wl.l12_crystal(lmax=lmax, n_k=n_k)
+    nE = len(c.energies)
+    E, ti = _items(orc, c, [(0, 0), (1, nE - 1)])
+    got_t, st_t, h_t = _gpu(B, c, E, ti)
+    got_n, st_n, h_n = _gpu(B, c, E, ti, flags=B.MUST_KKR_NO_TABLE)
+    groups = (h_t.n_disp - 1) // 2
+    assert h_t.table_bytes == 8 * h_t.n_kK * ((2 * lmax + 1) ** 2 + 2 * groups + 1)
+    assert h_n.table_bytes == 0 and h_n.n_kpts == h_t.n_kpts
+    _check(orc, c, E, ti, got_t, st_t, h_t)
+    _check(orc, c, E, ti, got_n, st_n, h_n)
+    assert rel_fro(got_t, got_n).max() <= TOL
+
+
 def test_kkr_l12_cell_vs_oracle(B, orc):
     """Four sites per cell (M(k) of order 64), two species, both contour ends."""
     c = wl.l12_crystal(n_k=4)

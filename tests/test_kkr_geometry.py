@@ -169,3 +169,8 @@ def test_kkr_geometry_explicit_eta_and_rejections(B):
         B.must_kkr_geometry(c.lattice, c.basis, 4, 4)                     # 4 x 25 > 64
     with pytest.raises(B.MustError):
         B.must_kkr_geometry(c.lattice, np.vstack([c.basis, c.basis[:1] + c.lattice[1]]), 1, 4)
+    # the table switch does not change the set-up; unknown flag bits are rejected
+    assert B.must_kkr_geometry(c.lattice, c.basis, 1, 4, flags=B.MUST_KKR_NO_TABLE) == \
+        B.must_kkr_geometry(c.lattice, c.basis, 1, 4)
+    with pytest.raises(B.MustError):
+        B.must_kkr_geometry(c.lattice, c.basis, 1, 4, flags=4)
