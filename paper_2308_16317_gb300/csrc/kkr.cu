@@ -39,7 +39,7 @@
 //   kkr_real_terms_kernel  per (item, real-space point): the k-independent factor of B_L
 //   kkr_recip_table_kernel at build, per k: the energy-independent factors of every
 //                          reciprocal term, e^{-q^2/eta} YS_L(q), cos(q.x), sin(q.x), q^2
-//   kkr_recip_kernel       per (item, k): A_L + C_L for every displacement (x and -x paired)
+//   kkr_recip_kernel       per (k, group of items): A_L + C_L for every displacement (x and -x paired)
 //   kkr_realsum_kernel     per (item, displacement group, 32 k points): adds B_L
 //   kkr_invert_kernel      per (item, group of <= 8 k points): M(k) by the Gaunt contraction,
 //                          equilibrated, in-place Gauss-Jordan with partial pivoting in
@@ -234,14 +234,17 @@ __global__ void kkr_real_terms_kernel(KkrDev K, int items, const double2* __rest
 // complex coefficient times a real harmonic): two FMAs instead of four.
 
 // -------------------------------------------------------------------------
-// A_L + C_L for every displacement, one CTA per (k, item):
+// A_L + C_L for every displacement, one CTA per (k, group of IB items):
 //   Dk[item][k][d][L] = (4 pi/Omega) i^l sum_K e^{iq.x_d} YS_L(q) e^{(E-q^2)/eta}/(q^2-E) + C_L
-// Per chunk of KKR_KCHUNK reciprocal vectors: 64 threads form q and the
-// weight, all threads form the harmonics (four m columns per vector) and the
-// coefficients (w for group 0, cos(q.x) w and sin(q.x) w for the pairs), then
-// each thread accumulates its outputs (group, L) -- over every vector of the
+// Per chunk of KKR_KCHUNK reciprocal vectors: the harmonics come from the
+// table (or are formed, four m columns per vector), shared by the CTA's
+// items; each (item, vector) gets its weight and its coefficients (w for
+// group 0, cos(q.x) w and sin(q.x) w for the pairs); then each thread
+// accumulates its outputs (item, group, L) -- over every vector of the
 // chunk, or, when the outputs are fewer than the threads, over one of G
 // interleaved subsets, the G partial sums being added in order at the end.
+// IB is fixed per handle, so an item's summation order does not depend on
+// the other items of the call.
 constexpr int RECIP_THREADS = 256;
 
 // The energy-independent factors of the reciprocal terms, one row per (k, K)
@@ -275,51 +278,59 @@ __global__ void __launch_bounds__(TAB_THREADS) kkr_recip_table_kernel(KkrDev K, 
 }
 
 constexpr int KKR_MAX_GROUPS = 1 + (KKR_MAX_DISP - 1) / 2;
-constexpr int RECIP_OUT = (KKR_MAX_GROUPS * KKR_MAX_NL2 + RECIP_THREADS - 1) / RECIP_THREADS;
+constexpr int RECIP_OUT = 6;        // outputs (item, group, L) per thread at most
+constexpr int RECIP_IB_MAX = 8;     // items per CTA at most
 constexpr int RECIP_MPARTS = RECIP_THREADS / KKR_KCHUNK;
+static_assert(KKR_MAX_GROUPS * KKR_MAX_NL2 <= RECIP_OUT * RECIP_THREADS, "one item's outputs per CTA");
 
-__global__ void __launch_bounds__(RECIP_THREADS) kkr_recip_kernel(KkrDev K, int items, const double2* __restrict__ E,
+__global__ void __launch_bounds__(RECIP_THREADS) kkr_recip_kernel(KkrDev K, int items, int IB,
+                                                                  const double2* __restrict__ E,
                                                                   double2* __restrict__ Dk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double2 s_e[RECIP_IB_MAX], s_pre[RECIP_IB_MAX];   // E and (4 pi/Omega) e^{E/eta} of each item
   const int n_groups = 1 + (K.n_disp - 1) / 2;
-  const int n_out = n_groups * K.nL2;
+  const int n_out = n_groups * K.nL2;             // outputs of one item
+  const int n_tot = IB * n_out;                   // outputs of the CTA, item-major
   double* Y = reinterpret_cast<double*>(smem_raw);                    // [KCHUNK][nL2] real harmonics
-  double2* W = reinterpret_cast<double2*>(Y + KKR_KCHUNK * K.nL2);    // [n_disp][KCHUNK] coefficients
-  double2* wv = W + K.n_disp * KKR_KCHUNK;                             // [KCHUNK]
-  double* qv = reinterpret_cast<double*>(wv + KKR_KCHUNK);            // [KCHUNK][4]: q, |q|^2
-  double2* red = reinterpret_cast<double2*>(qv + 4 * KKR_KCHUNK);     // [2][RECIP_THREADS] partial sums
-  const int ik = blockIdx.x, it = blockIdx.y, tid = threadIdx.x;
-  const cd e = mk(E[it].x, E[it].y);
+  double* qv = Y + KKR_KCHUNK * K.nL2;                                // [KCHUNK][5]: q, |q|^2, Gaussian
+  double2* W = reinterpret_cast<double2*>(qv + 5 * KKR_KCHUNK);       // [IB][n_disp][KCHUNK] coefficients
+  double2* wv = W + size_t(IB) * K.n_disp * KKR_KCHUNK;               // [IB][KCHUNK]
+  double2* red = wv + IB * KKR_KCHUNK;                                // [2][RECIP_THREADS] partial sums
+  const int ik = blockIdx.x, it0 = blockIdx.y * IB, tid = threadIdx.x;
+  const int nb_here = min(IB, items - it0);
   const double* kp = K.kpts + size_t(ik) * 3;
   const int k0 = K.kK_start[ik], k1 = K.kK_start[ik + 1];
-  const int G = (n_out <= RECIP_THREADS) ? RECIP_THREADS / n_out : 1;
+  const int G = (n_tot <= RECIP_THREADS) ? RECIP_THREADS / n_tot : 1;
+  const double inv_eta = 1.0 / K.eta;
+  if (tid < IB) {
+    const double2 ev = E[it0 + min(tid, nb_here - 1)];
+    const cd e = mk(ev.x, ev.y);
+    // (4 pi / Omega) e^{E/eta}; each term then needs the real e^{-q^2/eta}
+    const cd wpre = (4.0 * kPi / K.omega) * cexp_d(mk(e.x * inv_eta, e.y * inv_eta));
+    s_e[tid] = ev;
+    s_pre[tid] = make_double2(wpre.x, wpre.y);
+  }
+  __syncthreads();
   cd accU[RECIP_OUT], accV[RECIP_OUT];
 #pragma unroll
   for (int j = 0; j < RECIP_OUT; ++j) { accU[j] = mk(0.0, 0.0); accV[j] = mk(0.0, 0.0); }
-  const double inv_eta = 1.0 / K.eta;
-  // (4 pi / Omega) e^{E/eta}; each term then needs the real e^{-q^2/eta}
-  const cd wpre = (4.0 * kPi / K.omega) * cexp_d(mk(e.x * inv_eta, e.y * inv_eta));
   for (int c0 = k0; c0 < k1; c0 += KKR_KCHUNK) {
     const int cn = min(KKR_KCHUNK, k1 - c0);
     const double* trow = K.tab ? K.tab + size_t(c0) * K.tab_w : nullptr;   // the chunk's table rows
     if (tid < KKR_KCHUNK) {
-      double q0 = 0.0, q1 = 0.0, q2v = 0.0, qq = 0.0;
-      cd w = mk(0.0, 0.0);
+      double q0 = 0.0, q1 = 0.0, q2v = 0.0, qq = 0.0, gq = 0.0;
       if (tid < cn) {
         if (trow) {
-          // w = (4 pi / Omega) e^{E/eta} / (q^2 - E); e^{-q^2/eta} is in the tabulated harmonics
           qq = trow[size_t(tid) * K.tab_w + K.tab_w - 1];
-          w = wpre * cinv(mk(qq - e.x, -e.y));
+          gq = 1.0;   // e^{-q^2/eta} is in the tabulated harmonics
         } else {
           const double* Kv = K.Kvec + size_t(K.kK_idx[c0 + tid]) * 3;
           q0 = kp[0] + Kv[0]; q1 = kp[1] + Kv[1]; q2v = kp[2] + Kv[2];
           qq = q0 * q0 + q1 * q1 + q2v * q2v;
-          // w = (4 pi / Omega) e^{(E - q^2)/eta} / (q^2 - E)
-          w = exp(-qq * inv_eta) * (wpre * cinv(mk(qq - e.x, -e.y)));
+          gq = exp(-qq * inv_eta);
         }
       }
-      qv[tid * 4] = q0; qv[tid * 4 + 1] = q1; qv[tid * 4 + 2] = q2v; qv[tid * 4 + 3] = qq;
-      wv[tid] = make_double2(w.x, w.y);
+      qv[tid * 5] = q0; qv[tid * 5 + 1] = q1; qv[tid * 5 + 2] = q2v; qv[tid * 5 + 3] = qq; qv[tid * 5 + 4] = gq;
     }
     if (trow) {
       // the chunk's harmonic rows: cn x nL2 doubles copied as they lie in the table
@@ -329,52 +340,67 @@ __global__ void __launch_bounds__(RECIP_THREADS) kkr_recip_kernel(KkrDev K, int 
       }
     }
     __syncthreads();
+    // w = (4 pi / Omega) e^{(E - q^2)/eta} / (q^2 - E) per (item, vector); zero past the chunk's end
+    for (int p = tid; p < IB * KKR_KCHUNK; p += RECIP_THREADS) {
+      const int b = p / KKR_KCHUNK, j = p - b * KKR_KCHUNK;
+      cd w = mk(0.0, 0.0);
+      if (j < cn && b < nb_here) {
+        const double2 ev = s_e[b], pr = s_pre[b];
+        w = qv[j * 5 + 4] * (mk(pr.x, pr.y) * cinv(mk(qv[j * 5 + 3] - ev.x, -ev.y)));
+      }
+      wv[p] = make_double2(w.x, w.y);
+    }
     if (!trow) {
       const int j = tid % KKR_KCHUNK, part = tid / KKR_KCHUNK;
       double* y = Y + j * K.nL2;
       for (int m = part; m <= K.l2max; m += RECIP_MPARTS)
-        solid_harmonic_column(K.l2max, m, qv[j * 4], qv[j * 4 + 1], qv[j * 4 + 2], qv[j * 4 + 3],
+        solid_harmonic_column(K.l2max, m, qv[j * 5], qv[j * 5 + 1], qv[j * 5 + 2], qv[j * 5 + 3],
                               [&](int, int L, double v) { y[L] = v; });
     }
-    for (int p = tid; p < K.n_disp * KKR_KCHUNK; p += RECIP_THREADS) {
-      const int d = p / KKR_KCHUNK, j = p % KKR_KCHUNK;
-      const double2 w = wv[j];
+    __syncthreads();
+    for (int p = tid; p < IB * K.n_disp * KKR_KCHUNK; p += RECIP_THREADS) {
+      const int b = p / (K.n_disp * KKR_KCHUNK), r = p - b * (K.n_disp * KKR_KCHUNK);
+      const int d = r / KKR_KCHUNK, j = r - d * KKR_KCHUNK;
+      const double2 w = wv[b * KKR_KCHUNK + j];
       if (d == 0) {
         W[p] = w;
-      } else if (trow) {
-        // row 2g-1: cos, row 2g: sin (zero past the chunk's end, where w is zero too)
-        const double f = (j < cn) ? trow[size_t(j) * K.tab_w + K.nL2 + 2 * ((d - 1) / 2) + ((d & 1) ? 0 : 1)] : 0.0;
-        W[p] = make_double2(f * w.x, f * w.y);
       } else {
-        const double* x = K.disp + ((d - 1) / 2 * 2 + 1) * 3;   // the x of the pair
-        double sn, cs;
-        sincos(qv[j * 4] * x[0] + qv[j * 4 + 1] * x[1] + qv[j * 4 + 2] * x[2], &sn, &cs);
-        const double f = (d & 1) ? cs : sn;                     // row 2g-1: cos, row 2g: sin
+        double f;   // row 2g-1: cos(q.x), row 2g: sin(q.x)
+        if (trow) {
+          f = (j < cn) ? trow[size_t(j) * K.tab_w + K.nL2 + 2 * ((d - 1) / 2) + ((d & 1) ? 0 : 1)] : 0.0;
+        } else {
+          const double* x = K.disp + ((d - 1) / 2 * 2 + 1) * 3;   // the x of the pair
+          double sn, cs;
+          sincos(qv[j * 5] * x[0] + qv[j * 5 + 1] * x[1] + qv[j * 5 + 2] * x[2], &sn, &cs);
+          f = (d & 1) ? cs : sn;
+        }
         W[p] = make_double2(f * w.x, f * w.y);
       }
     }
     __syncthreads();
-    const int sub = (G > 1) ? tid / n_out : 0;
+    const int sub = (G > 1) ? tid / n_tot : 0;
     const int nloop = (G > 1) ? 1 : RECIP_OUT;
 #pragma unroll
     for (int jj = 0; jj < RECIP_OUT; ++jj) {
       if (jj >= nloop) break;
-      const int o = (G > 1) ? tid % n_out : tid + jj * RECIP_THREADS;
-      if (o >= n_out || (G > 1 && tid >= G * n_out)) continue;
-      const int g = o / K.nL2, L = o % K.nL2;
+      const int ot = (G > 1) ? tid % n_tot : tid + jj * RECIP_THREADS;
+      if (ot >= n_tot || (G > 1 && tid >= G * n_tot)) continue;
+      const int b = ot / n_out, o = ot - b * n_out;
+      const int g = o / K.nL2, L = o - g * K.nL2;
       const int step = (G > 1) ? G : 1;
+      const double2* Wb = W + size_t(b) * K.n_disp * KKR_KCHUNK;
       if (g == 0) {
         cd u = accU[jj];
         for (int j = sub; j < cn; j += step) {
           const double yv = Y[j * K.nL2 + L];
-          const double2 c = W[j];
+          const double2 c = Wb[j];
           u.x = fma(c.x, yv, u.x);
           u.y = fma(c.y, yv, u.y);
         }
         accU[jj] = u;
       } else {
         cd u = accU[jj], v = accV[jj];
-        const double2* Wc = W + (2 * g - 1) * KKR_KCHUNK;
+        const double2* Wc = Wb + (2 * g - 1) * KKR_KCHUNK;
         const double2* Ws = Wc + KKR_KCHUNK;
         for (int j = sub; j < cn; j += step) {
           const double yv = Y[j * K.nL2 + L];
@@ -392,34 +418,37 @@ __global__ void __launch_bounds__(RECIP_THREADS) kkr_recip_kernel(KkrDev K, int 
   }
   if (G > 1) {
     // partial sums of the G subsets, added in order
-    if (tid < G * n_out) {
+    if (tid < G * n_tot) {
       red[tid] = make_double2(accU[0].x, accU[0].y);
       red[RECIP_THREADS + tid] = make_double2(accV[0].x, accV[0].y);
     }
     __syncthreads();
-    if (tid < n_out) {
+    if (tid < n_tot) {
       cd u = mk(0.0, 0.0), v = mk(0.0, 0.0);
       for (int g = 0; g < G; ++g) {
-        u = u + mk(red[g * n_out + tid].x, red[g * n_out + tid].y);
-        v = v + mk(red[RECIP_THREADS + g * n_out + tid].x, red[RECIP_THREADS + g * n_out + tid].y);
+        u = u + mk(red[g * n_tot + tid].x, red[g * n_tot + tid].y);
+        v = v + mk(red[RECIP_THREADS + g * n_tot + tid].x, red[RECIP_THREADS + g * n_tot + tid].y);
       }
       accU[0] = u;
       accV[0] = v;
     }
   }
-  double2* out = Dk + (size_t(it) * K.n_kpts + ik) * K.n_disp * K.nL2;
   const int nwrite = (G > 1) ? 1 : RECIP_OUT;
 #pragma unroll
   for (int jj = 0; jj < RECIP_OUT; ++jj) {
     if (jj >= nwrite) break;
-    const int o = tid + jj * RECIP_THREADS;
-    if (o >= n_out) continue;
-    const int g = o / K.nL2, L = o % K.nL2, l = l_of_L(L);
+    const int ot = tid + jj * RECIP_THREADS;
+    if (ot >= n_tot) continue;
+    const int b = ot / n_out, o = ot - b * n_out;
+    if (b >= nb_here) continue;
+    const int g = o / K.nL2, L = o - g * K.nL2, l = l_of_L(L);
     const cd il = ipow_d(l);
+    double2* out = Dk + (size_t(it0 + b) * K.n_kpts + ik) * K.n_disp * K.nL2;
     if (g == 0) {
       cd a = il * accU[jj];
       if (L == 0) {
         // C_0 of displacement 0 (x = 0): the R = 0 term of the reciprocal sum removed
+        const cd e = mk(s_e[b].x, s_e[b].y);
         const cd kap = csqrt_p(e);
         const cd z = mk(e.x * inv_eta, e.y * inv_eta);
         cd sm = mk(0.0, 0.0), term = mk(1.0, 0.0);   // (E/eta)^n / n!
@@ -1032,10 +1061,22 @@ KkrDev dev_view(const must_kkr* h) {
   return K;
 }
 
-size_t recip_smem(const must_kkr* h) {
-  return sizeof(double) * (size_t(KKR_KCHUNK) * h->nL2 + 4 * KKR_KCHUNK) +
-         sizeof(double2) * (size_t(h->n_disp) * KKR_KCHUNK + KKR_KCHUNK + 2 * RECIP_THREADS);
+size_t recip_smem_ib(const must_kkr* h, int ib) {
+  return sizeof(double) * (size_t(KKR_KCHUNK) * h->nL2 + 5 * KKR_KCHUNK) +
+         sizeof(double2) * (size_t(ib) * (size_t(h->n_disp) + 1) * KKR_KCHUNK + 2 * RECIP_THREADS);
 }
+
+// Items per CTA of the reciprocal sums: as many as the output registers
+// (RECIP_OUT per thread) and ~100 KB of shared memory (two CTAs per SM) allow,
+// at most RECIP_IB_MAX.
+int recip_ib(const must_kkr* h) {
+  const int n_out = (1 + (h->n_disp - 1) / 2) * h->nL2;
+  int ib = std::max(1, std::min(RECIP_IB_MAX, (RECIP_OUT * RECIP_THREADS) / n_out));
+  while (ib > 1 && recip_smem_ib(h, ib) > size_t(100) * 1024) --ib;
+  return ib;
+}
+
+size_t recip_smem(const must_kkr* h) { return recip_smem_ib(h, recip_ib(h)); }
 
 size_t realsum_smem(const must_kkr* h) {
   return sizeof(double2) * (size_t(KKR_RCHUNK) * h->nL2 + size_t(KKR_KB) * KKR_RCHUNK);
@@ -1555,8 +1596,9 @@ extern "C" must_status must_kkr_tau(const must_kkr* h, int32_t n_items, const do
   }
   {
     ProfScope ps(PH_KKR_RECIP, st);
-    dim3 g1(h->n_kpts, n_items);
-    kkr_recip_kernel<<<g1, RECIP_THREADS, recip_smem(h), st>>>(K, n_items, Ed, w.Dk);
+    const int ib = recip_ib(h);
+    dim3 g1(h->n_kpts, (n_items + ib - 1) / ib);
+    kkr_recip_kernel<<<g1, RECIP_THREADS, recip_smem(h), st>>>(K, n_items, ib, Ed, w.Dk);
     prof_launched(PH_KKR_RECIP, 1, n_items);
   }
   {
