@@ -468,7 +468,8 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * depend on the energy (e^{-q^2/eta} YS_L(q), the phases cos(q.x) and sin(q.x)
  * of the displacements, q^2) are computed once by must_kkr_build and kept on
  * the device, 8 (2 lmax+1)^2 + 16 (number of displacement pairs) + 8 bytes per
- * (k, K) term (info[4] terms), when that is at most 512 MiB; every item of
+ * (k, K) term (info[4] terms), when that is at most 512 MiB and the device
+ * has room for it (otherwise the build goes on without it); every item of
  * must_kkr_tau then forms only 1/(q^2 - E) per term.  flags |=
  * MUST_KKR_NO_TABLE forms all factors per item instead (same results to
  * rounding).  must_kkr_table_bytes: the table's size, 0 when none is kept.

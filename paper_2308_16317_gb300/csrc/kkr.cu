@@ -1447,7 +1447,12 @@ static must_status kkr_build_impl(const double* lattice, const double* basis, co
     const size_t tb = sizeof(double) * size_t(h->n_kK) * size_t(h->tab_w);
     if (e == cudaSuccess && !(flags & MUST_KKR_NO_TABLE) && h->n_kK > 0 && tb <= KKR_TAB_CAP) {
       e = cudaMalloc(reinterpret_cast<void**>(&h->d_tab), tb);
-      if (e == cudaSuccess) {
+      if (e == cudaErrorMemoryAllocation) {
+        // no room for the table: the items form the factors themselves
+        cudaGetLastError();
+        h->d_tab = nullptr;
+        e = cudaSuccess;
+      } else if (e == cudaSuccess) {
         h->tab_bytes = tb;
         KkrDev K = dev_view(h);
         K.tab = nullptr;   // the kernel writes the table through its own argument
