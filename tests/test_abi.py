@@ -228,3 +228,34 @@ def test_bench_kkr_work_counts():
     # 200 points of x = 0 (one displacement each), 2800 of the six pair groups (two each)
     assert w["kkr_realsum"] == 4.0 * 64 * 35 * nL2 * (200 + 2 * 2800)
     assert w["kkr_invert"] == 8.0 * 64 * 35 * 36 ** 3
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding's copies of the header's enumerators and #define
+    flags (precisions, status codes, full-KKR flags) carry the same values,
+    and the library names each status code as the header does."""
+    from paper_2308_16317_gb300 import binding as B
+    text = open(os.path.join(ROOT, "include", "must.h")).read()
+    text_nc = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    enums = {}
+    for body in re.findall(r"typedef enum\s*\{(.*?)\}", text_nc, flags=re.S):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            if "=" in item:
+                name, val = (x.strip() for x in item.split("="))
+                nxt = int(val)
+            else:
+                name = item
+            enums[name] = nxt
+            nxt += 1
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(MUST_\w+)\s+(\d+)", text)}
+    for name in ("MUST_FP64", "MUST_MIXED_BF16X3", "MUST_MIXED_TF32X3"):
+        assert getattr(B, name) == enums[name], name
+    for code, name in B.STATUS.items():
+        assert enums[name] == code, name
+        assert B.load().must_status_string(code).decode() == name
+    for name in ("MUST_KKR_NO_SYMMETRY", "MUST_KKR_NO_TABLE"):
+        assert getattr(B, name) == defines[name], name
