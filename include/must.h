@@ -459,7 +459,8 @@ must_status must_peak_probe(int32_t kind, int32_t blocks, int64_t iters, double*
  * mesh points n_k^3, real-space points of the zero displacement, point-group
  * operations used (0: k / -k pairing)}.  The
  * displacements x != 0 come in pairs (x, -x) and the real-space points of x = 0
- * in pairs (R, -R); one member of each is stored and summed for both.  Only one point of each pair {k, -k} of the mesh is
+ * in pairs (R, -R); one member of each is stored and summed for both.  In
+ * the k / -k mode only one point of each pair {k, -k} of the mesh is
  * evaluated: M(-k) = M(k)^T (the reciprocity G_{LL'}(rho) = G_{L'L}(-rho)), so
  * its diagonal blocks enter the average transposed.  must_kkr_eta: the
  * splitting parameter in use.
